@@ -1,0 +1,208 @@
+"""Pins for the oracle's full ADER-DG scheme: convergence, LTS, energy, attenuation,
+receivers and source (Sec. III-A, Sec. V-B)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.lts import normalise
+from oracle.mesh import Mesh
+from oracle.scheme import Solver, ricker
+from paper_2202_10313_gb300 import synth
+
+RHO, VP, VS = 2700.0, 6000.0, 3464.0
+KVEC = 2 * np.pi * np.array([1.0, 1.0, 1.0])
+
+
+def _cube_solver(n, order, m=0, qs=None):
+    mm = synth.periodic_cube(n)
+    mesh = Mesh(mm["xyz"], mm["tet"], mm["face_bc"], mm["period"])
+    K = mesh.K
+    kw = {}
+    if m:
+        kw = dict(qp=np.full(K, 2 * qs), qs=np.full(K, qs))
+    return Solver(order, m, mesh, np.full(K, RHO), np.full(K, VP), np.full(K, VS), **kw), mesh
+
+
+def _rel_err(a, b, rows):
+    return np.sqrt(np.sum((a[:, rows] - b[:, rows]) ** 2) / np.sum(b[:, rows] ** 2))
+
+
+@pytest.mark.parametrize("order", [3, 4, 5])
+def test_plane_wave_convergence(order):
+    """P plane wave on the periodic cube: L2 error drops at rate ~O (3x3x3 -> 6x6x6 hexes)."""
+    pw = synth.p_plane_wave(RHO, VP, VS, KVEC)
+    tend = 0.25 / (VP * np.linalg.norm(KVEC) / (2 * np.pi))
+    errs = []
+    for n in (3, 6):
+        s, mesh = _cube_solver(n, order)
+        s.project(lambda x: pw(x, 0.0))
+        dt = s.time_step_gts(0.5)
+        nst = int(math.ceil(tend / dt))
+        s.run_gts(tend / nst, nst)
+        ex, _ = _cube_solver(n, order)
+        ex.project(lambda x: pw(x, tend))
+        errs.append(_rel_err(s.Q, ex.Q, slice(6, 9)))
+    rate = math.log2(errs[0] / errs[1])
+    assert rate > order - 0.6, (errs, rate)
+
+
+def test_lts_single_cluster_equals_gts_bitwise():
+    pw = synth.p_plane_wave(RHO, VP, VS, KVEC)
+    a, _ = _cube_solver(3, 3)
+    b, _ = _cube_solver(3, 3)
+    a.project(lambda x: pw(x, 0.0))
+    b.project(lambda x: pw(x, 0.0))
+    dt = a.time_step_gts(0.5)
+    a.run_gts(dt, 7)
+    b.setup_clusters(1, 0.5)
+    assert b.lam_lts == 1.0 and b.delta == dt
+    b.run_lts(7)
+    assert np.array_equal(a.Q, b.Q)
+
+
+def test_forced_three_cluster_lts_converges_and_tracks_gts():
+    pw = synth.p_plane_wave(RHO, VP, VS, KVEC)
+    tend = 0.25 / (VP * np.sqrt(3))
+    errs, gaps = [], []
+    for n in (3, 6):
+        s, mesh = _cube_solver(n, 3)
+        s.project(lambda x: pw(x, 0.0))
+        x = mesh.centroid[:, 0]
+        c = normalise(np.digitize(x, [1 / 3, 2 / 3]), mesh.nbr)
+        assert set(c.tolist()) == {0, 1, 2}
+        s.setup_clusters(3, 0.125, lam=1.0, clusters=c)
+        nper = int(math.ceil(tend / (4 * s.delta)))
+        s.delta = tend / (4 * nper)
+        s.run_lts(4 * nper)
+        g, _ = _cube_solver(n, 3)
+        g.project(lambda x: pw(x, 0.0))
+        g.run_gts(tend / (4 * nper), 4 * nper)
+        ex, _ = _cube_solver(n, 3)
+        ex.project(lambda x: pw(x, tend))
+        errs.append(_rel_err(s.Q, ex.Q, slice(6, 9)))
+        gaps.append(_rel_err(s.Q, g.Q, slice(6, 9)))
+    assert math.log2(errs[0] / errs[1]) > 2.4
+    # LTS differs from GTS by less than the discretisation error
+    assert gaps[1] < errs[1]
+
+
+@pytest.mark.parametrize("order", [3, 4])
+def test_energy_non_increasing_periodic(order):
+    pw = synth.p_plane_wave(RHO, VP, VS, KVEC)
+    s, _ = _cube_solver(3, order)
+    s.project(lambda x: pw(x, 0.0))
+    dt = s.time_step_gts(0.5)
+    e = [s.energy()]
+    for _ in range(30):
+        s.run_gts(dt, 1)
+        e.append(s.energy())
+    assert np.all(np.diff(e) <= 1e-13 * e[0])
+    assert e[-1] < e[0]
+
+
+def test_energy_non_increasing_free_surface_and_absorbing_box():
+    m = synth.graded_box(3, 3, 3, 100.0, 60.0, seed=9)
+    mesh = Mesh(m["xyz"], m["tet"], m["face_bc"])
+    mat = synth.layered(m, [60.0], [1500.0, 2500.0])
+    s = Solver(3, 0, mesh, mat["rho"], mat["vp"], mat["vs"])
+    s.project(synth.gaussian_pulse([150.0, 150.0, -100.0], 80.0, 9))
+    dt = s.time_step_gts(0.5)
+    e = [s.energy()]
+    for _ in range(30):
+        s.run_gts(dt, 1)
+        e.append(s.energy())
+    assert np.all(np.diff(e) <= 1e-13 * e[0])
+    assert e[-1] < 0.999 * e[0]
+
+
+def test_infinite_q_anelastic_equals_elastic_bitwise():
+    pw = synth.p_plane_wave(RHO, VP, VS, KVEC)
+    a, _ = _cube_solver(3, 3)
+    b, _ = _cube_solver(3, 3, m=3, qs=np.inf)
+    a.project(lambda x: pw(x, 0.0))
+    b.project(lambda x: np.concatenate([pw(x, 0.0), np.zeros((len(x), 18))], axis=1))
+    dt = a.time_step_gts(0.5)
+    a.run_gts(dt, 5)
+    b.run_gts(dt, 5)
+    assert np.array_equal(a.Q, b.Q[:, :9])
+
+
+def test_anelastic_plane_wave_decays_at_target_q():
+    """Uniform attenuating medium: an S plane wave's velocity amplitude decays like
+    exp(-w t / (2 Q)) up to discretisation error (low-loss limit)."""
+    qs = 20.0
+    kvec = 2 * np.pi * np.array([1.0, 0.0, 0.0])
+    w = np.linalg.norm(kvec) * VS
+    s, mesh = _cube_solver(3, 4, m=3, qs=qs)
+    # relaxation band around the wave frequency
+    from oracle import physics as ph
+    s.omega = ph.relaxation_frequencies(3, 0.1 * w / (2 * np.pi), 10 * w / (2 * np.pi))
+    lam, mu = ph.lame(RHO, VP, VS)
+    ylam, ymu = ph.anelastic_coefficients(lam, mu, 2 * qs, qs, s.omega)
+    for k in range(mesh.K):
+        for l in range(3):
+            s.E[k, l] = ph.coupling_matrix(lam, mu, ylam[l], ymu[l])
+    sw = synth.s_plane_wave(RHO, VS, kvec, [0.0, 1.0, 0.0])
+    s.project(lambda x: np.concatenate([sw(x, 0.0), np.zeros((len(x), 18))], axis=1))
+    a0 = np.sqrt(np.sum(s.Q[:, 6:9] ** 2) + np.sum(s.Q[:, :6] ** 2) / (RHO * VS) ** 2)
+    tend = 2 * 2 * np.pi / w
+    dt = s.time_step_gts(0.4)
+    nst = int(math.ceil(tend / dt))
+    s.run_gts(tend / nst, nst)
+    a1 = np.sqrt(np.sum(s.Q[:, 6:9] ** 2) + np.sum(s.Q[:, :6] ** 2) / (RHO * VS) ** 2)
+    want = math.exp(-w * tend / (2 * qs))
+    assert abs(a1 / a0 / want - 1) < 0.05, (a1 / a0, want)
+
+
+def test_receiver_is_exact_point_evaluation():
+    """Sampled at the start of each step, the receiver equals the DG polynomial of
+    Q^n at the receiver point; mid-step samples come from the Taylor series."""
+    pw = synth.p_plane_wave(RHO, VP, VS, KVEC)
+    s, mesh = _cube_solver(3, 3)
+    s.project(lambda x: pw(x, 0.0))
+    dt = s.time_step_gts(0.5)
+    xr = np.array([0.31, 0.47, 0.62])
+    rid = s.add_receiver(xr, dt)
+    k = mesh.locate(xr)
+    phi = s.basis.phi(mesh.xi_of(k, xr)[None, :])[0]
+    vals = []
+    for _ in range(4):
+        vals.append(s.Q[k, :9] @ phi)
+        s.run_gts(dt, 1)
+    t, v = s.seismogram(rid)
+    assert np.allclose(t, dt * np.arange(4))
+    assert np.abs(v - np.array(vals)).max() <= 1e-13 * np.abs(vals).max()
+    # Taylor evaluation at mid-step approximates the exact wave to discretisation error
+    s2, _ = _cube_solver(3, 3)
+    s2.project(lambda x: pw(x, 0.0))
+    rid = s2.add_receiver(xr, dt / 2)
+    s2.run_gts(dt, 4)
+    t, v = s2.seismogram(rid)
+    ex = np.array([pw(xr[None, :], ti)[0] for ti in t])
+    assert np.abs(v[:, 6:] - ex[:, 6:]).max() < 0.1
+
+
+def test_source_injection_matches_closed_form_time_integral():
+    """Q = 0, one step: the source element gains -M (int s dt) phi(xi_s)/|det J|; the
+    O-point Gauss-Legendre integral matches the Ricker antiderivative t e^(-pi^2 f0^2 t^2)."""
+    s, mesh = _cube_solver(3, 3)
+    dt = s.time_step_gts(0.5)
+    xs = np.array([0.52, 0.41, 0.33])
+    m6 = np.array([1.0, -0.5, 0.25, 0.3, -0.2, 0.1])
+    f0, t0 = 2000.0, 2.5e-4
+    s.add_point_source(xs, m6, f0, t0, m0=1e9)
+    s.run_gts(dt, 1)
+    k = mesh.locate(xs)
+    phi = s.basis.phi(mesh.xi_of(k, xs)[None, :])[0]
+
+    def anti(t):
+        tau = t - t0
+        return tau * np.exp(-(np.pi * f0 * tau) ** 2)
+
+    integ = anti(dt) - anti(0.0)
+    want = -(m6 * 1e9 * integ)[:, None] * (phi / mesh.detJ[k])[None, :]
+    assert np.abs(s.Q[k, :6] - want).max() <= 1e-6 * np.abs(want).max()
+    others = np.delete(np.arange(mesh.K), k)
+    assert np.all(s.Q[others] == 0)
+    assert abs(ricker(t0, f0, t0) - 1.0) < 1e-15
