@@ -1,0 +1,302 @@
+"""Throughput of the order-5 anelastic clustered-LTS ADER-DG update on one GB300.
+
+Workload: 96 x 96 x 38 hexes x 6 = 2,101,248 jittered graded tetrahedra (h = 250 m,
+z spacing 125 -> 500 m), 8 random layers vs ~ U[500, 4000] m/s (vp = sqrt(3) vs,
+rho = 2700, Qs = 50 vs[km/s], Qp = 2 Qs), 3 relaxation mechanisms over 0.1-5 Hz, order
+5, 5 LTS clusters with the lambda search, CFL 0.5, a moment-tensor Ricker source and
+64 surface receivers. One step = one macro step (16 finest steps: every cluster
+completes its 2^(4-l) steps). The metric is element updates per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the only reference there is) on the box's
+host cores on a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "element-updates/s and % HBM roofline, order-5 anelastic LTS, 1 GB300 (vs plain FP32)"
+UNIT = "element-updates/s"
+ORDER, NMECH, NCLUSTERS, CFL = 5, 3, 5, 0.5
+FULL = dict(nx=96, ny=96, nz=38, h=250.0, hz=125.0)
+SAMPLE = dict(nx=12, ny=12, nz=5, h=250.0, hz=125.0)   # bounded CPU sample of the same generator
+
+
+def make_workload(nx, ny, nz, h, hz):
+    from paper_2202_10313_gb300 import synth
+    mesh = synth.graded_box(nx, ny, nz, h, hz)
+    mat = synth.random_layers(mesh)
+    lx, ly, depth = nx * h, ny * h, mesh["depth"]
+    src = dict(x=np.array([0.5 * lx + 17.0, 0.5 * ly - 23.0, -2000.0 if depth > 2500 else -0.4 * depth]),
+               m6=np.array([0.0, 0.0, 0.0, 1.0, 0.0, 0.0]), f0=2.0, t0=0.6, m0=1e15)
+    recs = synth.surface_receiver_grid(8, 8, (0.0, lx), (0.0, ly), depth=1.0)
+    return mesh, mat, src, recs
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6778.0), d.get("sm_max_mhz", 2070.0), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.proc = None
+        self.index = index
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("kernels.cuh", "launch.h"):
+        h.update(open(os.path.join(ROOT, "paper_2202_10313_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def oracle_sample(seconds_cap=25.0, steps=None):
+    """Element updates/s of the FP64 oracle on the bounded sample (one macro step each)."""
+    import oracle  # noqa: F401  (test infrastructure: only this leg and --impl reference use it)
+    from oracle.mesh import Mesh
+    from oracle.scheme import Solver as Oracle
+    mesh, mat, src, recs = make_workload(**SAMPLE)
+    om = Mesh(mesh["xyz"], mesh["tet"], mesh["face_bc"])
+    o = Oracle(ORDER, NMECH, om, mat["rho"], mat["vp"], mat["vs"], mat["qp"], mat["qs"])
+    o.setup_clusters(NCLUSTERS, CFL)
+    o.add_point_source(src["x"], src["m6"], src["f0"], src["t0"], src["m0"])
+    period = 2 ** (NCLUSTERS - 1)
+    per_macro = o.element_updates(period)
+    times = []
+    t_all = time.time()
+    n = steps if steps is not None else 10 ** 9
+    for _ in range(n):
+        t0 = time.perf_counter()
+        o.run_lts(period)
+        times.append(time.perf_counter() - t0)
+        if steps is None and time.time() - t_all > seconds_cap:
+            break
+    return per_macro, times, om.K
+
+
+def threads_used():
+    try:
+        from threadpoolctl import threadpool_info
+        return max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    per_macro, times, K = oracle_sample(steps=args.warmup + args.steps)
+    timed = times[args.warmup:]
+    total = sum(timed)
+    value = per_macro * len(timed) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / len(timed),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "anelastic O5 m3 LTS Nc=5, bounded sample %d tets of the same generator" % K,
+                   "elements": K, "order": ORDER, "n_mech": NMECH, "clusters": NCLUSTERS},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads_used(), "kind": "oracle",
+                         "sample": "%d-tet mesh (12x12x5 hexes) of the same generator, one macro step per step" % K},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2202_10313_gb300 import binding, build, perfmodel
+    torch.cuda.set_device(local_rank)
+    build.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    cfg = FULL if not args.small else dict(nx=24, ny=24, nz=10, h=250.0, hz=125.0)
+    mesh, mat, src, recs = make_workload(**cfg)
+    K = mesh["tet"].shape[0]
+    s = binding.Solver(ORDER, NMECH, device=local_rank)
+    s.set_mesh(mesh["xyz"], mesh["tet"], mesh["face_bc"])
+    s.set_material(mat["rho"], mat["vp"], mat["vs"], mat["qp"], mat["qs"], 0.1, 5.0)
+    s.add_point_source(src["x"], src["m6"], src["f0"], src["t0"], src["m0"])
+    dt_rec = 0.01
+    for r in recs:
+        s.add_receiver(r, dt_rec)
+    s.use_torch_memory(NCLUSTERS)
+    _, lam, speedup = s.setup_clusters(NCLUSTERS, CFL)
+    info = s.info()
+    period = 2 ** (NCLUSTERS - 1)
+    per_macro = int(info["updates_per_macro"].sum())
+    stream = torch.cuda.current_stream()
+    # warm-up
+    s.advance_steps(period * args.warmup, stream)
+    torch.cuda.synchronize()
+    # timed region: device-resident state
+    clocks = ClockSampler(local_rank)
+    s.set_profiling(True)
+    launches0 = s.info()["launches"]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        s.advance_steps(period, stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ck = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    launches = s.info()["launches"] - launches0
+    kst = s.kernel_stats()
+    s.set_profiling(False)
+    # end to end through the public API: advance + seismogram read-back every step
+    h2d0, d2h0 = s.transfer_bytes()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.advance(s.info()["time"] + period * info["finest_dt"] * (1 + 1e-6), stream)
+        for rid in range(len(recs)):
+            s.seismogram(rid)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    h2d1, d2h1 = s.transfer_bytes()
+    ms_t = torch.tensor([ms, e2e_s * 1000.0], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms, e2e_ms = float(ms_t[0]), float(ms_t[1])
+    if rank != 0:
+        return
+    total_updates = per_macro * args.steps * world
+    value = total_updates / (ms / 1000.0)
+    hbm_gbs, sm_max, peak_src = peaks()
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12     # TFLOP/s at the maximum SM clock
+    # dominant kernel by device time
+    kind = int(np.argmax(kst["ms"]))
+    name = ["k_predict_local", "k_neighbour"][kind]
+    avg_ms = kst["ms"][kind] / max(kst["launches"][kind], 1)
+    elems_per_launch = kst["elems"][kind] / max(kst["launches"][kind], 1)
+    fl = perfmodel.flops_predict(ORDER, NMECH) if kind == 0 else perfmodel.flops_neighbour(ORDER, NMECH)
+    by = perfmodel.bytes_predict(ORDER, NMECH) if kind == 0 else perfmodel.bytes_neighbour(ORDER, NMECH)
+    achieved_tf = fl * elems_per_launch / (avg_ms / 1000.0) / 1e12
+    achieved_gbs = by * elems_per_launch / (avg_ms / 1000.0) / 1e9
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tp):
+        t = json.load(open(tp))
+        ent = t.get(name)
+        if ent and ent.get("kernel_hash") == kernel_hash():
+            traffic = ent["dram_bytes_per_element"] * elems_per_launch
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "anelastic O5 m3 LTS, %d jittered graded tets, Nc=%d, lambda=%.2f, CFL %.1f, "
+                               "1 moment-tensor source, 64 receivers; step = 1 macro step (%d finest steps)"
+                               % (K, NCLUSTERS, lam, CFL, period),
+                   "elements": K, "updates_per_step": per_macro, "cluster_elems": info["cluster_elems"].tolist(),
+                   "theoretical_lts_speedup": speedup, "l2": "inputs larger than L2 (DOFs %.1f GB)" % (K * 945 * 4 / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "alu", "kernel": name, "achieved": achieved_tf, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved_tf / fp32_peak, "traffic": traffic,
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (derived)" % sm_max,
+                     "flops_per_element": fl, "elements_per_launch": elems_per_launch, "avg_launch_ms": avg_ms},
+        "hbm": {"kernel": name, "achieved": achieved_gbs, "peak": hbm_gbs, "unit": "GB/s",
+                "frac": achieved_gbs / hbm_gbs, "peak_source": peak_src, "bytes_per_element": by},
+        "kernel_ms": {"k_predict_local": kst["ms"][0], "k_neighbour": kst["ms"][1],
+                      "launches": kst["launches"].tolist()},
+        "gpu_launches": int(launches),
+        "e2e": {"value": total_updates / (e2e_ms / 1000.0), "unit": UNIT,
+                "h2d_bytes_per_step": (h2d1 - h2d0) / args.steps, "d2h_bytes_per_step": (d2h1 - d2h0) / args.steps},
+        "clocks": ck,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        per_m, times, Ks = oracle_sample(seconds_cap=20.0)
+        v = per_m * len(times) / sum(times)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads_used(), "kind": "oracle",
+                                "sample": "%d macro steps of a %d-tet mesh (12x12x5 hexes) of the same generator"
+                                          % (len(times), Ks)}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--small", action="store_true", help="small mesh (quick check / profiling)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

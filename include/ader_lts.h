@@ -1,0 +1,195 @@
+/*
+ * ader_lts.h -- C ABI of the GB300 ADER-DG solver with clustered local time stepping.
+ *
+ * Method: "Next-Generation Local Time Stepping for the ADER-DG Finite Element Method"
+ * (Breuer & Heinecke). The library advances the 3D elastic (n_mech = 0) or anelastic
+ * (n_mech relaxation mechanisms) wave equations, Eq. (1) of Sec. III, on unstructured
+ * tetrahedra with the ADER-DG time, volume and surface kernels of Sec. III-A, driven by
+ * the rate-2 clustered LTS scheme with buffers B1/B2/B3 of Sec. V. All bulk arithmetic
+ * runs in FP32 in CUDA kernels; set-up runs in FP64 on the host.
+ *
+ * Conventions shared by every call
+ *  - Every function returns an int status: LTS_OK (0) or a negative LTS_ERR_* code.
+ *    No C++ exception crosses this boundary. lts_last_error() describes the last
+ *    failure on a handle (the string stays valid until the next call on it).
+ *  - Host arrays are owned by the caller; the library copies what it needs before
+ *    returning. Nothing is retained by pointer except the device block given to
+ *    lts_bind_device_memory (caller-owned, must outlive the handle's use of it).
+ *  - Elements are identified by their index in the caller's tetrahedron array
+ *    (original order); the library's internal reordering is never visible.
+ *  - Reference tetrahedron v0=(0,0,0), v1=(1,0,0), v2=(0,1,0), v3=(0,0,1); face i of a
+ *    tetrahedron (t0,t1,t2,t3) is the vertex triple {(t0,t2,t1), (t0,t1,t3), (t0,t3,t2),
+ *    (t1,t2,t3)}[i], i.e. the face opposite local vertex 3-i.
+ *  - Quantities per element (rows): sxx, syy, szz, sxy, syz, sxz, u, v, w, then 6
+ *    memory variables (xx, yy, zz, xy, yz, xz) per relaxation mechanism.
+ *  - DOFs are coefficients of the orthonormal modal (Dubiner) basis of Sec. III-A:
+ *    mode (i,j,k) = [s1^i P_i(a)] [s2^j P_j^(2i+1,0)(b)] P_k^(2i+2j+2,0)(c) with
+ *    s1 = 1-x2-x3, s2 = 1-x3, a = 2x1/s1-1, b = 2x2/s2-1, c = 2x3-1, unit L2 norm on the
+ *    reference tetrahedron; modes ordered by degree i+j+k, then k, then j.
+ *    DOF arrays are [element][quantity][mode], row-major, double.
+ */
+#ifndef ADER_LTS_H
+#define ADER_LTS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lts_solver lts_t;
+
+enum {
+    LTS_OK = 0,
+    LTS_ERR_ARG = -1,      /* invalid argument or unsupported configuration            */
+    LTS_ERR_MESH = -2,     /* invalid mesh (orientation, non-conforming or open faces)   */
+    LTS_ERR_CUDA = -3,     /* a CUDA runtime call failed                                */
+    LTS_ERR_OOM = -4,      /* host or device allocation failed / bound block too small  */
+    LTS_ERR_STATE = -5,    /* call out of order (e.g. advance before cluster set-up)   */
+    LTS_ERR_TIMEOUT = -6   /* a bounded device-side wait gave up                       */
+};
+
+/* Face boundary codes (per tetrahedron face). */
+enum { LTS_BC_INTERIOR = 0, LTS_BC_ABSORBING = 1, LTS_BC_FREE_SURFACE = 2, LTS_BC_PERIODIC = 3 };
+
+/* Create a solver. order O in {3,4,5} (B(O) = O(O+1)(O+2)/6 modes, Sec. III-A);
+ * n_mech in {0, 3} (N^q = 9 + 6 n_mech quantities, Sec. III); n_fused must be 1.
+ * Selects CUDA device `device` for all later calls on the handle. device < 0 creates a
+ * host-only handle: mesh, material and cluster set-up run (lts_setup_clusters reports
+ * clusters, lambda and speedup) but no device state exists, so calls that need it
+ * return LTS_ERR_STATE. *out is set only on success. Errors: LTS_ERR_ARG, LTS_ERR_CUDA,
+ * LTS_ERR_OOM. */
+int lts_create(int order, int n_mech, int n_fused, int device, lts_t** out);
+
+/* Release the handle, its device memory (unless caller-bound) and host tables. NULL is a no-op. */
+void lts_destroy(lts_t* h);
+
+/* Message describing the last error on h (empty string if none). */
+const char* lts_last_error(lts_t* h);
+
+/* Mesh (Sec. III-A: conforming unstructured tetrahedra). xyz[3*n_vert] coordinates,
+ * tet[4*n_tet] vertex ids (each tetrahedron positively oriented), face_bc[4*n_tet]
+ * LTS_BC_* per face (interior faces 0). period[3] box lengths for periodic faces
+ * (matched by vertex position modulo the box), NULL if none. Errors: LTS_ERR_MESH for
+ * non-positive orientation, faces shared by != 2 elements, inconsistent orientation or
+ * an interior/periodic face without partner; LTS_ERR_ARG for bad sizes or codes. */
+int lts_set_mesh(lts_t* h, int64_t n_vert, const double* xyz, int64_t n_tet, const int64_t* tet,
+                 const int32_t* face_bc, const double* period);
+
+/* Material per element (Sec. VII-B lists rho, vp, vs, Qp, Qs): unrelaxed velocities.
+ * qp/qs are required when n_mech > 0 (constant-Q fit over [f_min, f_max] Hz with
+ * log-spaced relaxation frequencies, collocated at those frequencies), ignored
+ * otherwise. Errors: LTS_ERR_ARG (non-positive values, missing Q), LTS_ERR_STATE (no mesh). */
+int lts_set_material(lts_t* h, const double* rho, const double* vp, const double* vs,
+                     const double* qp, const double* qs, double f_min, double f_max);
+
+/* Cluster set-up (Sec. V-A). dt_k = cfl * d_k / ((2O-1) vp_k), d_k the insphere
+ * diameter; clusters C_l = [2^(l-1) lam dt_min, 2^l lam dt_min), last open-ended;
+ * normalised so face neighbours differ by at most one cluster. lambda <= 0 searches
+ * lambda in {0.51, ..., 1.00} (steps of 0.01, ties to the larger) maximising the
+ * theoretical speedup. n_clusters = 1 is global time stepping. Outputs (each may be
+ * NULL): cluster_out[n_tet] (0-based), lambda_out, speedup_out (GTS cost / LTS cost).
+ * Allocates and uploads all device state; resets time to 0 and DOFs to zero.
+ * Errors: LTS_ERR_ARG, LTS_ERR_STATE (no material), LTS_ERR_CUDA, LTS_ERR_OOM. */
+int lts_setup_clusters(lts_t* h, int n_clusters, double cfl, double lambda,
+                       int32_t* cluster_out, double* lambda_out, double* speedup_out);
+
+/* As lts_setup_clusters, with the cluster of every element given (0-based, normalised
+ * by the caller) and lambda fixed (1.0 if <= 0). Errors additionally: LTS_ERR_ARG if
+ * face neighbours differ by more than one cluster. */
+int lts_force_clusters(lts_t* h, int n_clusters, const int32_t* clusters, double cfl, double lambda);
+
+/* Device bytes the state needs after cluster set-up would allocate it; call after
+ * lts_set_material. The caller may then hand a block of at least that size (256-byte
+ * aligned) to lts_bind_device_memory before lts_setup_clusters; otherwise the library
+ * allocates its own block. Errors: LTS_ERR_STATE. */
+int lts_state_bytes(lts_t* h, int n_clusters, int64_t* bytes);
+int lts_bind_device_memory(lts_t* h, void* dev, int64_t bytes);
+
+/* Physical quadrature points of the projection rule: n_per_elem points per element,
+ * xyz_out[n_tet][n_per_elem][3] (NULL to query the count only). */
+int lts_quadrature_points(lts_t* h, int64_t* n_per_elem, double* xyz_out);
+
+/* L2 projection of point values: values[n_tet][n_per_elem][n_q] at the points of
+ * lts_quadrature_points become the DOFs (orthonormal basis, Sec. III-A). */
+int lts_project_initial(lts_t* h, const double* values);
+
+/* Raw DOFs [n_tet][n_q][B] (double on the host, FP32 on the device). lts_get_dofs
+ * synchronises the solver's stream. */
+int lts_set_dofs(lts_t* h, const double* dofs);
+int lts_get_dofs(lts_t* h, double* dofs);
+
+/* Moment-tensor point source (reading of Sec. VII-B's point sources): moment rate
+ * m0 * m6 * s(t), s the Ricker wavelet (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2),
+ * m6 = (xx, yy, zz, xy, yz, xz). The containing element (lowest index whose closed
+ * tetrahedron holds x) gains -m0 m6 (int s dt) phi_b(xi)/|det J| on its stress DOFs at
+ * the end of each of its steps (O-point Gauss-Legendre in time). fused_idx must be 0.
+ * Errors: LTS_ERR_ARG (point outside the mesh). Call before lts_setup_clusters. */
+int lts_add_point_source(lts_t* h, int fused_idx, const double x[3], const double m6[6],
+                         double f0, double t0, double m0);
+
+/* Receiver at x sampled every dt_sample seconds (t_j = j dt_sample): each sample inside a
+ * step [t_n, t_n + dt) of the receiver's element is the Taylor series
+ * sum_d (t_j - t_n)^d / d! d^dQ evaluated at x (9 elastic quantities). *id receives its
+ * index. Errors: LTS_ERR_ARG (outside mesh). Call before lts_setup_clusters. */
+int lts_add_receiver(lts_t* h, const double x[3], double dt_sample, int* id);
+
+/* Advance whole macro steps (2^(N_c-1) finest steps of lam*dt_min each) until the time is
+ * the largest multiple of the macro step not above t_end (plus a 1e-9 relative slack),
+ * asynchronously on `cuda_stream` (a cudaStream_t; NULL = legacy default stream). */
+int lts_advance(lts_t* h, double t_end, void* cuda_stream);
+
+/* Advance n_finest finest steps (a multiple of 2^(N_c-1)) on `cuda_stream`. */
+int lts_advance_steps(lts_t* h, int64_t n_finest, void* cuda_stream);
+
+/* Copy receiver `id`'s samples so far: t_out[n] times and v_out[n][9] values (either may
+ * be NULL); *n receives the number of samples (at most cap are written). Synchronises. */
+int lts_get_seismogram(lts_t* h, int id, int fused_idx, double* t_out, double* v_out,
+                       int64_t cap, int64_t* n);
+
+/* Discrete elastic energy sum_k |det J_k| sum_b (rho |v_b|^2/2 + sigma_b : C^-1 sigma_b / 2),
+ * reduced in FP64 on the device. Synchronises. */
+int lts_energy(lts_t* h, double* e);
+
+/* Run information. n_clusters_out; per cluster (arrays of length >= 8, may be NULL):
+ * elements, and element updates per macro step; dt_min; lambda; finest step; current
+ * time; kernel launches issued so far. */
+int lts_info(lts_t* h, int* n_clusters_out, int64_t* cluster_elems, int64_t* updates_per_macro,
+             double* dt_min, double* lambda, double* finest_dt, double* time_now, int64_t* launches);
+
+/* Kernel timing. With profiling enabled, every predict+local and neighbour launch is
+ * bracketed by CUDA events recorded on the launch stream (no synchronisation).
+ * lts_kernel_stats synchronises on the last event and returns, per kind (index 0
+ * predict+local, 1 neighbour), the summed milliseconds, the number of launches and the
+ * elements processed since profiling was enabled or last read; reading resets them. */
+int lts_set_profiling(lts_t* h, int enable);
+int lts_kernel_stats(lts_t* h, double* ms_out2, int64_t* launches_out2, int64_t* elems_out2);
+
+/* Cumulative bytes the library copied host->device in lts_advance / lts_advance_steps
+ * (source and receiver schedules) and device->host in lts_get_seismogram. */
+int lts_transfer_bytes(lts_t* h, int64_t* h2d, int64_t* d2h);
+
+/* Host-only helpers (no handle, no GPU). Reference operators of order O in the basis
+ * described above (Sec. III-A), from exact polynomial integration:
+ *   K[c][i][j]   = int phi_i d(phi_j)/d(xi_c)                     (3 x B x B)
+ *   Ft[f][k][m]  = int_{face f} phi_k psi_m                       (4 x B x F)
+ *   Fb[j*3+h][k][m] = int psi_m(chi) phi_k(xi_j(chi'(chi, h)))    (12 x B x F)
+ * with psi the orthonormal triangle basis (mode (i,j) = [s^i P_i(a)] P_j^(2i+1,0)(b),
+ * s = 1-chi2, a = 2chi1/s-1, b = 2chi2-1, ordered by degree then j), the face parameter
+ * chi of face f (vertices (A,B,C) of the face table: x = A + chi1 (B-A) + chi2 (C-A)), and
+ * for the neighbour matrices the neighbour's face j whose vertex h coincides with the
+ * local face's first vertex (vertex m of the local face at neighbour position
+ * (h, h+2, h+1)[m] mod 3). Any output may be NULL. Errors: LTS_ERR_ARG. */
+int lts_reference_operators(int order, double* K, double* Ft, double* Fb);
+
+/* phi_b(xi_i) for n reference points xi[3n] -> out[n][B]. Errors: LTS_ERR_ARG. */
+int lts_eval_basis(int order, int64_t n, const double* xi, double* out);
+
+/* The projection quadrature rule on the reference tetrahedron (collapsed Gauss-Jacobi):
+ * *n points, xi[3 *n] and weights w[*n] (either may be NULL to query *n). */
+int lts_quadrature_rule(int order, int64_t* n, double* xi, double* w);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ADER_LTS_H */

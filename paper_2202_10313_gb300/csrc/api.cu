@@ -1,0 +1,1012 @@
+// C ABI of the solver: set-up tables, device state and the clustered-LTS schedule.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/ader_lts.h"
+#include "host.h"
+#include "launch.h"
+
+using ltsdev::DevOps;
+using ltsdev::DevState;
+using ltsdev::Launchers;
+using ltsdev::PhaseArgs;
+using ltsdev::RecvItem;
+using ltsdev::SrcItem;
+
+namespace ltsdev {
+bool get_launchers(int order, int m, Launchers* out) {
+  if (m != 0 && m != 3) return false;
+  switch (order) {
+    case 3: *out = launchers_o3(m); return true;
+    case 4: *out = launchers_o4(m); return true;
+    case 5: *out = launchers_o5(m); return true;
+    default: return false;
+  }
+}
+}  // namespace ltsdev
+
+namespace {
+
+struct Source {
+  int64_t elem;          // original index
+  double xi[3];
+  double m6[6];
+  double f0, t0, m0;
+  std::vector<double> phi;
+};
+
+struct Receiver {
+  int64_t elem;
+  double xi[3];
+  double dt;
+  std::vector<double> phi;
+  std::vector<double> t;       // sample times
+  std::vector<int64_t> slot;   // device output slot of each sample
+};
+
+struct Status {
+  int code;
+  std::string msg;
+};
+
+[[noreturn]] void fail(int code, const std::string& msg) { throw Status{code, msg}; }
+
+void ck(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) fail(LTS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+
+struct lts_solver {
+  int order = 0, nmech = 0, device = 0;
+  std::string err;
+  Launchers L{};
+  lts::RefOps ops;
+  lts::Mesh mesh;
+  lts::Material mat;
+  bool has_mesh = false, has_mat = false, ready = false;
+  std::vector<double> lam, mu, omega;       // per element / per mechanism
+  std::vector<double> ylam, ymu;            // [K][m]
+  std::vector<Source> sources;
+  std::vector<Receiver> receivers;
+  // clusters
+  int nc = 1;
+  double lambda = 1.0, dt_min = 0.0, delta = 0.0, speedup = 1.0;
+  std::vector<int32_t> cluster;             // original order
+  std::vector<int64_t> perm, iperm;         // perm[new] = old, iperm[old] = new
+  std::vector<int64_t> cbeg;                // cluster ranges (internal order), nc+1
+  int64_t s_now = 0;
+  int64_t launches = 0;
+  int64_t h2d_bytes = 0, d2h_bytes = 0;      // copies issued by advance / read calls
+  // device
+  void* block = nullptr;
+  bool own_block = false;
+  size_t block_bytes = 0;
+  void* bound = nullptr;
+  size_t bound_bytes = 0;
+  DevOps dops{};
+  DevState dst{};
+  double* d_emat = nullptr;
+  double* d_partial = nullptr;
+  float* d_recv_phi = nullptr;
+  float* d_src_phi = nullptr;
+  int n_partial = 1024;
+  // growable library-owned scratch
+  float* d_seis = nullptr;
+  size_t seis_cap = 0, seis_used = 0;
+  RecvItem* d_ritems = nullptr;
+  size_t ritems_cap = 0;
+  SrcItem* d_sitems = nullptr;
+  size_t sitems_cap = 0;
+  int num_sms = 0;
+  // profiling: event pairs around each predict / neighbour launch, read lazily
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<int> ev_kind;
+  std::vector<int64_t> ev_elems;
+};
+
+namespace {
+
+int run(lts_t* h, const std::function<void()>& fn) {
+  if (!h) return LTS_ERR_ARG;
+  try {
+    h->err.clear();
+    fn();
+    return LTS_OK;
+  } catch (const Status& s) {
+    h->err = s.msg;
+    return s.code;
+  } catch (const std::bad_alloc&) {
+    h->err = "host allocation failed";
+    return LTS_ERR_OOM;
+  } catch (const std::exception& e) {
+    h->err = e.what();
+    return LTS_ERR_ARG;
+  }
+}
+
+struct Layout {
+  size_t Q, B1, B2, B3, edata, ndata, nbr, ncode, meta, emat, partial, K, Ft, Fh, Fb, rphi, sphi, total;
+};
+
+Layout layout_of(const lts_solver* h, int64_t K) {
+  Layout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align256(off + bytes);
+    return o;
+  };
+  const Launchers& X = h->L;
+  L.Q = take(sizeof(float) * K * X.QS);
+  L.B1 = take(sizeof(float) * K * X.BUFS);
+  L.B2 = take(sizeof(float) * K * X.BUFS);
+  L.B3 = take(sizeof(float) * K * X.BUFS);
+  L.edata = take(sizeof(float) * K * ltsdev::ED);
+  L.ndata = take(sizeof(float) * K * ltsdev::ND);
+  L.nbr = take(sizeof(int) * K * 4);
+  L.ncode = take(sizeof(int) * K * 4);
+  L.meta = take(sizeof(int) * K);
+  L.emat = take(sizeof(double) * K * 4);
+  L.partial = take(sizeof(double) * h->n_partial);
+  L.K = take(sizeof(float) * 3 * X.B * X.B);
+  L.Ft = take(sizeof(float) * 4 * X.B * X.F);
+  L.Fh = take(sizeof(float) * 4 * X.F * X.B);
+  L.Fb = take(sizeof(float) * 12 * X.B * X.F);
+  L.rphi = take(sizeof(float) * std::max<size_t>(1, h->receivers.size()) * X.B);
+  L.sphi = take(sizeof(float) * std::max<size_t>(1, h->sources.size()) * X.B);
+  L.total = off;
+  return L;
+}
+
+void release_events(lts_solver* h) {
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  h->ev_pool.clear();
+  h->ev_used = 0;
+  h->ev_kind.clear();
+  h->ev_elems.clear();
+}
+
+cudaEvent_t next_event(lts_solver* h) {
+  if (h->ev_used == h->ev_pool.size()) {
+    cudaEvent_t e;
+    ck(cudaEventCreate(&e), "cudaEventCreate");
+    h->ev_pool.push_back(e);
+  }
+  return h->ev_pool[h->ev_used++];
+}
+
+void free_device(lts_solver* h) {
+  if (h->own_block && h->block) cudaFree(h->block);
+  h->block = nullptr;
+  h->own_block = false;
+  if (h->d_seis) cudaFree(h->d_seis);
+  if (h->d_ritems) cudaFree(h->d_ritems);
+  if (h->d_sitems) cudaFree(h->d_sitems);
+  h->d_seis = nullptr;
+  h->d_ritems = nullptr;
+  h->d_sitems = nullptr;
+  h->seis_cap = h->seis_used = h->ritems_cap = h->sitems_cap = 0;
+  h->ready = false;
+}
+
+// Flux coefficients of one face: (n, a[4], b[4]) for the interior state and for the
+// exterior state, scaled by -2|S|/|det J|. Normal (P) and tangential (S) pairs:
+//   v* = (Z- v- + Z+ v+ + t+ - t-)/(Z- + Z+),  t* = (Z+ t- + Z- t+ + Z- Z+ (v+ - v-))/(Z- + Z+)
+// free surface: t* = 0, v* = v- - t-/Z-; absorbing: exterior state zero, Z+ = Z-.
+void face_coefficients(int bc, double zp_i, double zs_i, double zp_o, double zs_o, double scale, float* loc,
+                       float* nbc) {
+  double a[4], b[4], an[4], bn[4];
+  if (bc == LTS_BC_FREE_SURFACE) {
+    a[0] = 1.0; a[1] = -1.0 / zp_i; a[2] = 0.0; a[3] = 0.0;
+    b[0] = 1.0; b[1] = -1.0 / zs_i; b[2] = 0.0; b[3] = 0.0;
+    for (int i = 0; i < 4; ++i) an[i] = bn[i] = 0.0;
+  } else {
+    if (bc == LTS_BC_ABSORBING) { zp_o = zp_i; zs_o = zs_i; }
+    double sp = zp_i + zp_o, ss = zs_i + zs_o;
+    a[0] = zp_i / sp; a[1] = -1.0 / sp; a[2] = zp_o / sp; a[3] = -zp_i * zp_o / sp;
+    b[0] = zs_i / ss; b[1] = -1.0 / ss; b[2] = zs_o / ss; b[3] = -zs_i * zs_o / ss;
+    an[0] = zp_o / sp; an[1] = 1.0 / sp; an[2] = zp_i / sp; an[3] = zp_i * zp_o / sp;
+    bn[0] = zs_o / ss; bn[1] = 1.0 / ss; bn[2] = zs_i / ss; bn[3] = zs_i * zs_o / ss;
+    if (bc == LTS_BC_ABSORBING)
+      for (int i = 0; i < 4; ++i) an[i] = bn[i] = 0.0;
+  }
+  for (int i = 0; i < 4; ++i) {
+    loc[i] = (float)(scale * a[i]);
+    loc[4 + i] = (float)(scale * b[i]);
+    nbc[i] = (float)(scale * an[i]);
+    nbc[4 + i] = (float)(scale * bn[i]);
+  }
+}
+
+void setup_device(lts_solver* h) {
+  const int64_t K = h->mesh.K;
+  const Launchers& X = h->L;
+  const int m = h->nmech;
+  // ---- permutation: stable sort by cluster
+  h->perm.resize(K);
+  std::iota(h->perm.begin(), h->perm.end(), 0);
+  std::stable_sort(h->perm.begin(), h->perm.end(),
+                   [&](int64_t a, int64_t b) { return h->cluster[a] < h->cluster[b]; });
+  h->iperm.resize(K);
+  for (int64_t i = 0; i < K; ++i) h->iperm[h->perm[i]] = i;
+  h->cbeg.assign(h->nc + 1, 0);
+  for (int64_t i = 0; i < K; ++i) h->cbeg[h->cluster[i] + 1]++;
+  for (int l = 0; l < h->nc; ++l) h->cbeg[l + 1] += h->cbeg[l];
+  // ---- host tables in internal order
+  std::vector<float> edata(K * ltsdev::ED, 0.f), ndata(K * ltsdev::ND, 0.f);
+  std::vector<int> nbr(4 * K, -1), ncode(4 * K, 0), meta(K, 0);
+  std::vector<double> emat(4 * K);
+  const lts::Mesh& M = h->mesh;
+  for (int64_t nk = 0; nk < K; ++nk) {
+    const int64_t k = h->perm[nk];
+    float* ed = &edata[nk * ltsdev::ED];
+    float* nd = &ndata[nk * ltsdev::ND];
+    for (int i = 0; i < 9; ++i) ed[i] = (float)M.Jinv[9 * k + i];
+    const double rho = h->mat.rho[k];
+    ed[9] = (float)h->lam[k];
+    ed[10] = (float)h->mu[k];
+    ed[11] = (float)(1.0 / rho);
+    for (int l = 0; l < m; ++l) {
+      ed[12 + 2 * l] = (float)(h->lam[k] * h->ylam[k * m + l]);
+      ed[13 + 2 * l] = (float)(2.0 * h->mu[k] * h->ymu[k * m + l]);
+    }
+    nd[0] = ed[9];
+    nd[1] = ed[10];
+    nd[2] = ed[11];
+    emat[4 * nk + 0] = h->lam[k];
+    emat[4 * nk + 1] = h->mu[k];
+    emat[4 * nk + 2] = rho;
+    emat[4 * nk + 3] = M.detJ[k];
+    const double zp = std::sqrt((h->lam[k] + 2.0 * h->mu[k]) * rho), zs = std::sqrt(h->mu[k] * rho);
+    int flags = h->cluster[k];
+    for (int f = 0; f < 4; ++f) {
+      const int bc = M.bc[4 * k + f];
+      const int64_t nb = M.nbr[4 * k + f];
+      double zpo = zp, zso = zs;
+      if (nb >= 0) {
+        const double rn = h->mat.rho[nb];
+        zpo = std::sqrt((h->lam[nb] + 2.0 * h->mu[nb]) * rn);
+        zso = std::sqrt(h->mu[nb] * rn);
+      }
+      const double scale = -2.0 * M.area[4 * k + f] / M.detJ[k];
+      float* lf = ed + 20 + 11 * f;
+      float* nf = nd + 4 + 11 * f;
+      for (int d = 0; d < 3; ++d) lf[d] = nf[d] = (float)M.normal[12 * k + 3 * f + d];
+      face_coefficients(bc, zp, zs, zpo, zso, scale, lf + 3, nf + 3);
+      if (nb >= 0) {
+        nbr[4 * nk + f] = (int)h->iperm[nb];
+        const int dc = h->cluster[nb] - h->cluster[k];
+        const int rel = dc == 0 ? 0 : (dc < 0 ? 1 : 2);
+        ncode[4 * nk + f] = (M.nbr_face[4 * k + f] * 3 + M.nbr_orient[4 * k + f]) | (rel << 8);
+        if (dc < 0) flags |= ltsdev::FLAG_FINER;
+        if (dc > 0) flags |= ltsdev::FLAG_COARSER;
+      }
+    }
+    meta[nk] = flags;
+  }
+  // ---- operators (float)
+  const int B = X.B, F = X.F;
+  std::vector<float> hK(3 * B * B), hFt(4 * B * F), hFh(4 * F * B), hFb(12 * B * F);
+  for (int c = 0; c < 3; ++c)
+    for (int i = 0; i < B * B; ++i) hK[c * B * B + i] = (float)h->ops.K[c][i];
+  for (int f = 0; f < 4; ++f)
+    for (int k = 0; k < B; ++k)
+      for (int q = 0; q < F; ++q) {
+        hFt[(f * B + k) * F + q] = (float)h->ops.Ft[f][k * F + q];
+        hFh[(f * F + q) * B + k] = (float)h->ops.Ft[f][k * F + q];
+      }
+  for (int jh = 0; jh < 12; ++jh)
+    for (int i = 0; i < B * F; ++i) hFb[jh * B * F + i] = (float)h->ops.Fb[jh][i];
+  std::vector<float> rphi(std::max<size_t>(1, h->receivers.size()) * B, 0.f);
+  for (size_t r = 0; r < h->receivers.size(); ++r)
+    for (int b = 0; b < B; ++b) rphi[r * B + b] = (float)h->receivers[r].phi[b];
+  std::vector<float> sphi(std::max<size_t>(1, h->sources.size()) * B, 0.f);
+  for (size_t s = 0; s < h->sources.size(); ++s)
+    for (int b = 0; b < B; ++b) sphi[s * B + b] = (float)h->sources[s].phi[b];
+  // ---- device block
+  free_device(h);
+  Layout Lo = layout_of(h, K);
+  if (h->bound) {
+    if (h->bound_bytes < Lo.total) fail(LTS_ERR_OOM, "bound device block too small");
+    h->block = h->bound;
+    h->own_block = false;
+  } else {
+    cudaError_t e = cudaMalloc(&h->block, Lo.total);
+    if (e != cudaSuccess) {
+      h->block = nullptr;
+      fail(LTS_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    h->own_block = true;
+  }
+  h->block_bytes = Lo.total;
+  char* base = static_cast<char*>(h->block);
+  h->dst.Q = reinterpret_cast<float*>(base + Lo.Q);
+  h->dst.B1 = reinterpret_cast<float*>(base + Lo.B1);
+  h->dst.B2 = reinterpret_cast<float*>(base + Lo.B2);
+  h->dst.B3 = reinterpret_cast<float*>(base + Lo.B3);
+  h->dst.edata = reinterpret_cast<float*>(base + Lo.edata);
+  h->dst.ndata = reinterpret_cast<float*>(base + Lo.ndata);
+  h->dst.nbr = reinterpret_cast<int*>(base + Lo.nbr);
+  h->dst.ncode = reinterpret_cast<int*>(base + Lo.ncode);
+  h->dst.meta = reinterpret_cast<int*>(base + Lo.meta);
+  h->d_emat = reinterpret_cast<double*>(base + Lo.emat);
+  h->d_partial = reinterpret_cast<double*>(base + Lo.partial);
+  h->dops.K = reinterpret_cast<float*>(base + Lo.K);
+  h->dops.Ft = reinterpret_cast<float*>(base + Lo.Ft);
+  h->dops.Fh = reinterpret_cast<float*>(base + Lo.Fh);
+  h->dops.Fb = reinterpret_cast<float*>(base + Lo.Fb);
+  h->d_recv_phi = reinterpret_cast<float*>(base + Lo.rphi);
+  h->d_src_phi = reinterpret_cast<float*>(base + Lo.sphi);
+  auto up = [&](const void* dst, const void* src, size_t bytes) {
+    ck(cudaMemcpy(const_cast<void*>(dst), src, bytes, cudaMemcpyHostToDevice), "upload");
+  };
+  ck(cudaMemset(h->dst.Q, 0, sizeof(float) * K * X.QS), "memset Q");
+  ck(cudaMemset(h->dst.B1, 0, sizeof(float) * K * X.BUFS), "memset B1");
+  ck(cudaMemset(h->dst.B2, 0, sizeof(float) * K * X.BUFS), "memset B2");
+  ck(cudaMemset(h->dst.B3, 0, sizeof(float) * K * X.BUFS), "memset B3");
+  up(h->dst.edata, edata.data(), sizeof(float) * edata.size());
+  up(h->dst.ndata, ndata.data(), sizeof(float) * ndata.size());
+  up(h->dst.nbr, nbr.data(), sizeof(int) * nbr.size());
+  up(h->dst.ncode, ncode.data(), sizeof(int) * ncode.size());
+  up(h->dst.meta, meta.data(), sizeof(int) * meta.size());
+  up(h->d_emat, emat.data(), sizeof(double) * emat.size());
+  up(h->dops.K, hK.data(), sizeof(float) * hK.size());
+  up(h->dops.Ft, hFt.data(), sizeof(float) * hFt.size());
+  up(h->dops.Fh, hFh.data(), sizeof(float) * hFh.size());
+  up(h->dops.Fb, hFb.data(), sizeof(float) * hFb.size());
+  up(h->d_recv_phi, rphi.data(), sizeof(float) * rphi.size());
+  up(h->d_src_phi, sphi.data(), sizeof(float) * sphi.size());
+  for (auto& r : h->receivers) {
+    r.t.clear();
+    r.slot.clear();
+  }
+  h->s_now = 0;
+  h->ready = true;
+}
+
+void finish_clusters(lts_solver* h, double* lambda_out, double* speedup_out, int32_t* cluster_out) {
+  const int64_t K = h->mesh.K;
+  for (int64_t k = 0; k < K; ++k)
+    for (int f = 0; f < 4; ++f) {
+      int64_t nb = h->mesh.nbr[4 * k + f];
+      if (nb >= 0 && std::abs(h->cluster[nb] - h->cluster[k]) > 1)
+        fail(LTS_ERR_ARG, "face neighbours differ by more than one cluster");
+    }
+  h->speedup = lts::theoretical_speedup(h->cluster, h->lambda);
+  h->delta = h->lambda * h->dt_min;
+  if (h->device >= 0) setup_device(h);
+  if (lambda_out) *lambda_out = h->lambda;
+  if (speedup_out) *speedup_out = h->speedup;
+  if (cluster_out) std::copy(h->cluster.begin(), h->cluster.end(), cluster_out);
+}
+
+void require_material(lts_solver* h) {
+  if (!h->has_mesh) fail(LTS_ERR_STATE, "no mesh");
+  if (!h->has_mat) fail(LTS_ERR_STATE, "no material");
+}
+
+void ensure_capacity(void** ptr, size_t* cap, size_t need, size_t elem) {
+  if (need <= *cap) return;
+  size_t nc = std::max(need, *cap * 2 + 16);
+  void* p = nullptr;
+  ck(cudaMalloc(&p, nc * elem), "cudaMalloc scratch");
+  if (*ptr) {
+    ck(cudaMemcpy(p, *ptr, *cap * elem, cudaMemcpyDeviceToDevice), "grow copy");
+    cudaFree(*ptr);
+  }
+  *ptr = p;
+  *cap = nc;
+}
+
+double ricker(double t, double f0, double t0) {
+  const double pi = 3.14159265358979323846;
+  double a = pi * f0 * (t - t0);
+  a *= a;
+  return (1.0 - 2.0 * a) * std::exp(-a);
+}
+
+void advance_steps(lts_solver* h, int64_t n_finest, cudaStream_t stream) {
+  if (!h->ready) fail(LTS_ERR_STATE, "clusters not set up");
+  const int nc = h->nc;
+  const int64_t period = int64_t(1) << (nc - 1);
+  if (n_finest < 0 || n_finest % period != 0) fail(LTS_ERR_ARG, "n_finest must be a multiple of 2^(N_c-1)");
+  if (n_finest == 0) return;
+  const Launchers& X = h->L;
+  const int B = X.B;
+  const int64_t s0 = h->s_now, s1 = s0 + n_finest;
+  // Taylor coefficients per cluster
+  PhaseArgs base{};
+  for (int l = 0; l < nc; ++l) {
+    const double dl = h->delta * std::ldexp(1.0, l);
+    double fac = 1.0;
+    for (int d = 0; d < h->order; ++d) {
+      fac *= (d + 1);
+      base.coef[l][d] = (float)(std::pow(dl, d + 1) / fac);
+      base.hcoef[l][d] = (float)(std::pow(0.5 * dl, d + 1) / fac);
+    }
+  }
+  for (int l = 0; l < 3; ++l) base.omega[l] = l < (int)h->omega.size() ? (float)h->omega[l] : 0.f;
+  // ---- host plan: source and receiver items for the whole call
+  struct Phase {
+    int kind;          // 0 neighbour, 1 predict
+    int top;           // clusters 0..top
+    int64_t s;
+    int item_beg, item_end;
+  };
+  std::vector<Phase> plan;
+  std::vector<SrcItem> sitems;
+  std::vector<RecvItem> ritems;
+  std::vector<double> gx, gw;
+  lts::gauss_jacobi(h->order, 0.0, gx, gw);
+  auto top_cluster = [&](int64_t s) {
+    int l = 0;
+    while (l + 1 < nc && s % (int64_t(1) << (l + 1)) == 0) ++l;
+    return l;
+  };
+  size_t seis_need = h->seis_used;
+  for (int64_t s = s0; s <= s1; ++s) {
+    if (s > s0) {
+      Phase ph{0, top_cluster(s), s, (int)sitems.size(), 0};
+      for (size_t si = 0; si < h->sources.size(); ++si) {
+        const Source& src = h->sources[si];
+        const int l = h->cluster[src.elem];
+        if (l > ph.top) continue;
+        const double ta = (s - (int64_t(1) << l)) * h->delta, tb = s * h->delta;
+        double integ = 0.0;
+        for (int q = 0; q < h->order; ++q)
+          integ += gw[q] * ricker(0.5 * (ta + tb) + 0.5 * (tb - ta) * gx[q], src.f0, src.t0);
+        integ *= 0.5 * (tb - ta);
+        SrcItem it{};
+        it.elem = (int)h->iperm[src.elem];
+        it.phi_off = (int)(si * B);
+        for (int r = 0; r < 6; ++r) it.amp[r] = (float)(-src.m0 * src.m6[r] * integ / h->mesh.detJ[src.elem]);
+        sitems.push_back(it);
+      }
+      ph.item_end = (int)sitems.size();
+      plan.push_back(ph);
+    }
+    if (s < s1) {
+      Phase ph{1, top_cluster(s), s, (int)ritems.size(), 0};
+      for (size_t ri = 0; ri < h->receivers.size(); ++ri) {
+        Receiver& rc = h->receivers[ri];
+        const int l = h->cluster[rc.elem];
+        if (l > ph.top) continue;
+        const double ta = s * h->delta, tb = (s + (int64_t(1) << l)) * h->delta;
+        RecvItem it{};
+        it.elem = (int)h->iperm[rc.elem];
+        it.phi_off = (int)(ri * B);
+        it.n = 0;
+        int64_t j = std::max<int64_t>((int64_t)std::floor(ta / rc.dt) - 1, 0);
+        for (; j * rc.dt < tb; ++j) {
+          const double tj = j * rc.dt;
+          if (tj < ta) continue;
+          if (it.n == 8) fail(LTS_ERR_ARG, "more than 8 receiver samples in one element step");
+          it.tau[it.n] = (float)(tj - ta);
+          rc.t.push_back(tj);
+          rc.slot.push_back((int64_t)seis_need);
+          if (it.n == 0) it.out_off = (int)seis_need;
+          ++seis_need;
+          ++it.n;
+        }
+        if (it.n > 0) ritems.push_back(it);
+      }
+      ph.item_end = (int)ritems.size();
+      plan.push_back(ph);
+    }
+  }
+  ensure_capacity(reinterpret_cast<void**>(&h->d_seis), &h->seis_cap, seis_need * 9, sizeof(float));
+  ensure_capacity(reinterpret_cast<void**>(&h->d_ritems), &h->ritems_cap, ritems.size(), sizeof(RecvItem));
+  ensure_capacity(reinterpret_cast<void**>(&h->d_sitems), &h->sitems_cap, sitems.size(), sizeof(SrcItem));
+  if (!ritems.empty())
+    ck(cudaMemcpyAsync(h->d_ritems, ritems.data(), ritems.size() * sizeof(RecvItem), cudaMemcpyHostToDevice, stream),
+       "upload receiver items");
+  if (!sitems.empty())
+    ck(cudaMemcpyAsync(h->d_sitems, sitems.data(), sitems.size() * sizeof(SrcItem), cudaMemcpyHostToDevice, stream),
+       "upload source items");
+  h->h2d_bytes += (int64_t)(ritems.size() * sizeof(RecvItem) + sitems.size() * sizeof(SrcItem));
+  h->seis_used = seis_need;
+  // ---- launches
+  const int grid_cap_p = std::max(1, h->num_sms * std::max(1, X.blocks_predict));
+  const int grid_cap_n = std::max(1, h->num_sms * std::max(1, X.blocks_neighbour));
+  for (const Phase& ph : plan) {
+    PhaseArgs pa = base;
+    pa.begin = 0;
+    pa.end = (int)h->cbeg[ph.top + 1];
+    for (int l = 0; l <= ph.top; ++l) {
+      const int64_t n = ph.kind == 0 ? (ph.s >> l) - 1 : (ph.s >> l);
+      pa.parity[l] = (int)(n & 1);
+    }
+    const int nelem = pa.end - pa.begin;
+    if (nelem <= 0) continue;
+    const int nb = (nelem + X.NE - 1) / X.NE;
+    if (ph.kind == 1 && ph.item_end > ph.item_beg) {
+      X.receivers(h->dops, h->dst.Q, h->dst.edata, h->d_recv_phi, h->d_ritems + ph.item_beg, h->d_seis,
+                  base.omega, ph.item_end - ph.item_beg, stream);
+      ++h->launches;
+    }
+    if (h->profiling) ck(cudaEventRecord(next_event(h), stream), "event record");
+    if (ph.kind == 0)
+      X.neighbour(h->dops, h->dst, pa, std::min(nb, grid_cap_n), stream);
+    else
+      X.predict(h->dops, h->dst, pa, std::min(nb, grid_cap_p), stream);
+    ++h->launches;
+    if (h->profiling) {
+      ck(cudaEventRecord(next_event(h), stream), "event record");
+      h->ev_kind.push_back(ph.kind == 1 ? 0 : 1);
+      h->ev_elems.push_back(nelem);
+    }
+    if (ph.kind == 0 && ph.item_end > ph.item_beg) {
+      X.sources(h->dst.Q, h->d_src_phi, h->d_sitems + ph.item_beg, ph.item_end - ph.item_beg, stream);
+      ++h->launches;
+    }
+  }
+  ck(cudaGetLastError(), "kernel launch");
+  h->s_now = s1;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lts_create(int order, int n_mech, int n_fused, int device, lts_t** out) {
+  if (!out || order < 3 || order > 5 || (n_mech != 0 && n_mech != 3) || n_fused != 1) return LTS_ERR_ARG;
+  lts_solver* h = nullptr;
+  try {
+    h = new lts_solver();
+  } catch (...) {
+    return LTS_ERR_OOM;
+  }
+  int rc = run(h, [&] {
+    h->order = order;
+    h->nmech = n_mech;
+    h->device = device;
+    if (!ltsdev::get_launchers(order, n_mech, &h->L)) fail(LTS_ERR_ARG, "unsupported order / mechanisms");
+    if (device >= 0) {
+      ck(cudaSetDevice(device), "cudaSetDevice");
+      ck(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device), "device attribute");
+      ck(h->L.init(&h->L), "kernel attributes");
+    }
+    h->ops.build(order);
+  });
+  if (rc != LTS_OK) {
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return LTS_OK;
+}
+
+void lts_destroy(lts_t* h) {
+  if (!h) return;
+  if (h->device >= 0) cudaSetDevice(h->device);
+  free_device(h);
+  release_events(h);
+  delete h;
+}
+
+const char* lts_last_error(lts_t* h) { return h ? h->err.c_str() : "null handle"; }
+
+int lts_set_mesh(lts_t* h, int64_t n_vert, const double* xyz, int64_t n_tet, const int64_t* tet, const int32_t* face_bc,
+                 const double* period) {
+  return run(h, [&] {
+    if (n_vert <= 0 || n_tet <= 0 || !xyz || !tet || !face_bc) fail(LTS_ERR_ARG, "bad mesh arguments");
+    if (n_tet > (int64_t(1) << 30)) fail(LTS_ERR_ARG, "too many elements");
+    lts::Mesh m;
+    m.nv = n_vert;
+    m.K = n_tet;
+    m.xyz.assign(xyz, xyz + 3 * n_vert);
+    m.tet.assign(tet, tet + 4 * n_tet);
+    m.bc.assign(face_bc, face_bc + 4 * n_tet);
+    if (period) {
+      m.periodic = true;
+      for (int d = 0; d < 3; ++d) {
+        if (!(period[d] > 0.0)) fail(LTS_ERR_ARG, "period must be positive");
+        m.period[d] = period[d];
+      }
+    }
+    for (int32_t c : m.bc)
+      if (c < 0 || c > 3) fail(LTS_ERR_ARG, "bad face code");
+    lts::Error e{0, ""};
+    if (lts::build_mesh(m, e) != 0) fail(e.code == -1 ? LTS_ERR_ARG : LTS_ERR_MESH, e.msg);
+    free_device(h);
+    h->mesh = std::move(m);
+    h->has_mesh = true;
+    h->has_mat = false;
+    h->sources.clear();
+    h->receivers.clear();
+  });
+}
+
+int lts_set_material(lts_t* h, const double* rho, const double* vp, const double* vs, const double* qp,
+                     const double* qs, double f_min, double f_max) {
+  return run(h, [&] {
+    if (!h->has_mesh) fail(LTS_ERR_STATE, "no mesh");
+    if (!rho || !vp || !vs) fail(LTS_ERR_ARG, "missing material arrays");
+    const int64_t K = h->mesh.K;
+    const int m = h->nmech;
+    if (m > 0 && (!qp || !qs || !(f_min > 0.0) || !(f_max > f_min))) fail(LTS_ERR_ARG, "missing Q model");
+    lts::Material mt;
+    mt.rho.assign(rho, rho + K);
+    mt.vp.assign(vp, vp + K);
+    mt.vs.assign(vs, vs + K);
+    h->lam.resize(K);
+    h->mu.resize(K);
+    for (int64_t k = 0; k < K; ++k) {
+      if (!(rho[k] > 0.0) || !(vp[k] > 0.0) || !(vs[k] > 0.0)) fail(LTS_ERR_ARG, "non-positive material value");
+      h->mu[k] = rho[k] * vs[k] * vs[k];
+      h->lam[k] = rho[k] * vp[k] * vp[k] - 2.0 * h->mu[k];
+    }
+    h->omega.assign(m, 0.0);
+    h->ylam.assign(K * m, 0.0);
+    h->ymu.assign(K * m, 0.0);
+    if (m > 0) {
+      mt.qp.assign(qp, qp + K);
+      mt.qs.assign(qs, qs + K);
+      mt.f_min = f_min;
+      mt.f_max = f_max;
+      lts::relaxation_frequencies(m, f_min, f_max, h->omega.data());
+      std::vector<double> ys(m), yp(m);
+      for (int64_t k = 0; k < K; ++k) {
+        if (!(qp[k] > 0.0) || !(qs[k] > 0.0)) fail(LTS_ERR_ARG, "non-positive Q");
+        if (lts::fit_y(m, qs[k], h->omega.data(), ys.data()) != 0 ||
+            lts::fit_y(m, qp[k], h->omega.data(), yp.data()) != 0)
+          fail(LTS_ERR_ARG, "singular relaxation fit");
+        for (int l = 0; l < m; ++l) {
+          h->ymu[k * m + l] = ys[l];
+          h->ylam[k * m + l] = ((h->lam[k] + 2.0 * h->mu[k]) * yp[l] - 2.0 * h->mu[k] * ys[l]) / h->lam[k];
+        }
+      }
+    }
+    free_device(h);
+    h->mat = std::move(mt);
+    h->has_mat = true;
+  });
+}
+
+int lts_setup_clusters(lts_t* h, int n_clusters, double cfl, double lambda, int32_t* cluster_out, double* lambda_out,
+                       double* speedup_out) {
+  return run(h, [&] {
+    require_material(h);
+    if (n_clusters < 1 || n_clusters > ltsdev::MAXC || !(cfl > 0.0) || lambda > 1.0)
+      fail(LTS_ERR_ARG, "bad cluster arguments");
+    if (lambda > 0.0 && lambda <= 0.5) fail(LTS_ERR_ARG, "lambda must lie in (0.5, 1]");
+    if (h->device >= 0) ck(cudaSetDevice(h->device), "cudaSetDevice");
+    std::vector<double> dt;
+    lts::cfl_time_steps(h->mesh, h->mat, h->order, cfl, dt);
+    h->dt_min = *std::min_element(dt.begin(), dt.end());
+    h->nc = n_clusters;
+    if (lambda <= 0.0) {
+      h->lambda = lts::search_lambda(h->mesh, dt, n_clusters, h->cluster, nullptr);
+    } else {
+      h->lambda = lambda;
+      lts::assign_clusters(dt, lambda, n_clusters, h->cluster);
+      lts::normalise_clusters(h->mesh, h->cluster);
+    }
+    finish_clusters(h, lambda_out, speedup_out, cluster_out);
+  });
+}
+
+int lts_force_clusters(lts_t* h, int n_clusters, const int32_t* clusters, double cfl, double lambda) {
+  return run(h, [&] {
+    require_material(h);
+    if (n_clusters < 1 || n_clusters > ltsdev::MAXC || !clusters || !(cfl > 0.0) || lambda > 1.0)
+      fail(LTS_ERR_ARG, "bad cluster arguments");
+    if (h->device >= 0) ck(cudaSetDevice(h->device), "cudaSetDevice");
+    std::vector<double> dt;
+    lts::cfl_time_steps(h->mesh, h->mat, h->order, cfl, dt);
+    h->dt_min = *std::min_element(dt.begin(), dt.end());
+    h->nc = n_clusters;
+    h->lambda = lambda > 0.0 ? lambda : 1.0;
+    h->cluster.assign(clusters, clusters + h->mesh.K);
+    for (int32_t c : h->cluster)
+      if (c < 0 || c >= n_clusters) fail(LTS_ERR_ARG, "cluster index out of range");
+    finish_clusters(h, nullptr, nullptr, nullptr);
+  });
+}
+
+int lts_state_bytes(lts_t* h, int n_clusters, int64_t* bytes) {
+  return run(h, [&] {
+    require_material(h);
+    (void)n_clusters;
+    if (!bytes) fail(LTS_ERR_ARG, "null output");
+    *bytes = (int64_t)layout_of(h, h->mesh.K).total;
+  });
+}
+
+int lts_bind_device_memory(lts_t* h, void* dev, int64_t bytes) {
+  return run(h, [&] {
+    if (dev && (reinterpret_cast<uintptr_t>(dev) % 256 != 0)) fail(LTS_ERR_ARG, "device block must be 256-byte aligned");
+    free_device(h);
+    h->bound = dev;
+    h->bound_bytes = dev ? (size_t)bytes : 0;
+  });
+}
+
+int lts_quadrature_points(lts_t* h, int64_t* n_per_elem, double* xyz_out) {
+  return run(h, [&] {
+    if (!h->has_mesh) fail(LTS_ERR_STATE, "no mesh");
+    const int64_t np = (int64_t)h->ops.qp.size();
+    if (n_per_elem) *n_per_elem = np;
+    if (!xyz_out) return;
+    const lts::Mesh& M = h->mesh;
+    for (int64_t k = 0; k < M.K; ++k)
+      for (int64_t p = 0; p < np; ++p)
+        for (int d = 0; d < 3; ++d) {
+          const auto& xi = h->ops.qp[p];
+          xyz_out[(k * np + p) * 3 + d] =
+              M.x0[3 * k + d] + M.J[9 * k + d * 3 + 0] * xi[0] + M.J[9 * k + d * 3 + 1] * xi[1] + M.J[9 * k + d * 3 + 2] * xi[2];
+        }
+  });
+}
+
+static void upload_dofs(lts_t* h, const std::vector<double>& dofs) {
+  const int64_t K = h->mesh.K;
+  const int B = h->L.B, NQ = h->L.NQ, QS = h->L.QS;
+  std::vector<float> q((size_t)K * QS, 0.f);
+  for (int64_t k = 0; k < K; ++k) {
+    const int64_t nk = h->iperm[k];
+    for (int r = 0; r < NQ; ++r)
+      for (int b = 0; b < B; ++b) q[nk * QS + r * B + b] = (float)dofs[(k * NQ + r) * B + b];
+  }
+  ck(cudaSetDevice(h->device), "cudaSetDevice");
+  ck(cudaMemcpy(h->dst.Q, q.data(), q.size() * sizeof(float), cudaMemcpyHostToDevice), "upload Q");
+}
+
+int lts_project_initial(lts_t* h, const double* values) {
+  return run(h, [&] {
+    if (!h->ready) fail(LTS_ERR_STATE, "clusters not set up");
+    if (!values) fail(LTS_ERR_ARG, "null values");
+    const int64_t K = h->mesh.K;
+    const int B = h->L.B, NQ = h->L.NQ;
+    const int64_t np = (int64_t)h->ops.qp.size();
+    std::vector<double> phiq(np * B);
+    for (int64_t p = 0; p < np; ++p) h->ops.eval(h->ops.qp[p].data(), &phiq[p * B]);
+    std::vector<double> dofs((size_t)K * NQ * B, 0.0);
+    for (int64_t k = 0; k < K; ++k)
+      for (int64_t p = 0; p < np; ++p) {
+        const double w = h->ops.qw[p];
+        for (int r = 0; r < NQ; ++r) {
+          const double v = w * values[(k * np + p) * NQ + r];
+          for (int b = 0; b < B; ++b) dofs[(k * NQ + r) * B + b] += v * phiq[p * B + b];
+        }
+      }
+    upload_dofs(h, dofs);
+  });
+}
+
+int lts_set_dofs(lts_t* h, const double* dofs) {
+  return run(h, [&] {
+    if (!h->ready) fail(LTS_ERR_STATE, "clusters not set up");
+    if (!dofs) fail(LTS_ERR_ARG, "null dofs");
+    std::vector<double> d(dofs, dofs + (size_t)h->mesh.K * h->L.NQ * h->L.B);
+    upload_dofs(h, d);
+  });
+}
+
+int lts_get_dofs(lts_t* h, double* dofs) {
+  return run(h, [&] {
+    if (!h->ready) fail(LTS_ERR_STATE, "clusters not set up");
+    if (!dofs) fail(LTS_ERR_ARG, "null dofs");
+    const int64_t K = h->mesh.K;
+    const int B = h->L.B, NQ = h->L.NQ, QS = h->L.QS;
+    std::vector<float> q((size_t)K * QS);
+    ck(cudaSetDevice(h->device), "cudaSetDevice");
+    ck(cudaDeviceSynchronize(), "synchronize");
+    ck(cudaMemcpy(q.data(), h->dst.Q, q.size() * sizeof(float), cudaMemcpyDeviceToHost), "download Q");
+    for (int64_t k = 0; k < K; ++k) {
+      const int64_t nk = h->iperm[k];
+      for (int r = 0; r < NQ; ++r)
+        for (int b = 0; b < B; ++b) dofs[(k * NQ + r) * B + b] = q[nk * QS + r * B + b];
+    }
+  });
+}
+
+int lts_add_point_source(lts_t* h, int fused_idx, const double x[3], const double m6[6], double f0, double t0,
+                         double m0) {
+  return run(h, [&] {
+    if (!h->has_mesh) fail(LTS_ERR_STATE, "no mesh");
+    if (fused_idx != 0 || !x || !m6) fail(LTS_ERR_ARG, "bad source arguments");
+    Source s;
+    s.elem = lts::locate(h->mesh, x, s.xi);
+    if (s.elem < 0) fail(LTS_ERR_ARG, "source outside the mesh");
+    std::copy(m6, m6 + 6, s.m6);
+    s.f0 = f0;
+    s.t0 = t0;
+    s.m0 = m0;
+    s.phi.resize(h->L.B);
+    h->ops.eval(s.xi, s.phi.data());
+    h->sources.push_back(std::move(s));
+    h->ready = false;
+  });
+}
+
+int lts_add_receiver(lts_t* h, const double x[3], double dt_sample, int* id) {
+  return run(h, [&] {
+    if (!h->has_mesh) fail(LTS_ERR_STATE, "no mesh");
+    if (!x || !(dt_sample > 0.0)) fail(LTS_ERR_ARG, "bad receiver arguments");
+    Receiver r;
+    r.elem = lts::locate(h->mesh, x, r.xi);
+    if (r.elem < 0) fail(LTS_ERR_ARG, "receiver outside the mesh");
+    r.dt = dt_sample;
+    r.phi.resize(h->L.B);
+    h->ops.eval(r.xi, r.phi.data());
+    h->receivers.push_back(std::move(r));
+    if (id) *id = (int)h->receivers.size() - 1;
+    h->ready = false;
+  });
+}
+
+int lts_advance_steps(lts_t* h, int64_t n_finest, void* cuda_stream) {
+  return run(h, [&] {
+    if (!h->ready) fail(LTS_ERR_STATE, "clusters not set up");
+    ck(cudaSetDevice(h->device), "cudaSetDevice");
+    advance_steps(h, n_finest, static_cast<cudaStream_t>(cuda_stream));
+  });
+}
+
+int lts_advance(lts_t* h, double t_end, void* cuda_stream) {
+  return run(h, [&] {
+    if (!h->ready) fail(LTS_ERR_STATE, "clusters not set up");
+    const int64_t period = int64_t(1) << (h->nc - 1);
+    const double macro = h->delta * period;
+    const double tnow = h->s_now * h->delta;
+    const int64_t nmac = (int64_t)std::floor((t_end - tnow) / macro * (1.0 + 1e-9) + 1e-9);
+    if (nmac <= 0) return;
+    ck(cudaSetDevice(h->device), "cudaSetDevice");
+    advance_steps(h, nmac * period, static_cast<cudaStream_t>(cuda_stream));
+  });
+}
+
+int lts_get_seismogram(lts_t* h, int id, int fused_idx, double* t_out, double* v_out, int64_t cap, int64_t* n) {
+  return run(h, [&] {
+    if (id < 0 || id >= (int)h->receivers.size() || fused_idx != 0) fail(LTS_ERR_ARG, "bad receiver id");
+    const Receiver& r = h->receivers[id];
+    const int64_t ns = (int64_t)r.t.size();
+    if (n) *n = ns;
+    const int64_t m = std::min<int64_t>(ns, cap);
+    if (m <= 0) return;
+    ck(cudaSetDevice(h->device), "cudaSetDevice");
+    ck(cudaDeviceSynchronize(), "synchronize");
+    // the receiver's samples occupy increasing slots; copy the span they cover
+    const int64_t lo = r.slot[0], hi = r.slot[m - 1] + 1;
+    std::vector<float> buf((hi - lo) * 9);
+    ck(cudaMemcpy(buf.data(), h->d_seis + lo * 9, buf.size() * sizeof(float), cudaMemcpyDeviceToHost),
+       "download seismogram");
+    h->d2h_bytes += (int64_t)(buf.size() * sizeof(float));
+    for (int64_t i = 0; i < m; ++i) {
+      if (t_out) t_out[i] = r.t[i];
+      if (v_out)
+        for (int q = 0; q < 9; ++q) v_out[i * 9 + q] = buf[(r.slot[i] - lo) * 9 + q];
+    }
+  });
+}
+
+int lts_energy(lts_t* h, double* e) {
+  return run(h, [&] {
+    if (!h->ready) fail(LTS_ERR_STATE, "clusters not set up");
+    if (!e) fail(LTS_ERR_ARG, "null output");
+    ck(cudaSetDevice(h->device), "cudaSetDevice");
+    const int nb = h->n_partial;
+    h->L.energy(h->dst.Q, h->d_emat, (int)h->mesh.K, h->d_partial, nb, 0);
+    ck(cudaGetLastError(), "energy kernel");
+    std::vector<double> part(nb);
+    ck(cudaMemcpy(part.data(), h->d_partial, nb * sizeof(double), cudaMemcpyDeviceToHost), "download energy");
+    double s = 0.0;
+    for (double v : part) s += v;
+    *e = s;
+  });
+}
+
+int lts_info(lts_t* h, int* n_clusters_out, int64_t* cluster_elems, int64_t* updates_per_macro, double* dt_min,
+             double* lambda, double* finest_dt, double* time_now, int64_t* launches) {
+  return run(h, [&] {
+    if (!h->ready) fail(LTS_ERR_STATE, "clusters not set up");
+    if (n_clusters_out) *n_clusters_out = h->nc;
+    for (int l = 0; l < h->nc; ++l) {
+      const int64_t ne = h->cbeg[l + 1] - h->cbeg[l];
+      if (cluster_elems) cluster_elems[l] = ne;
+      if (updates_per_macro) updates_per_macro[l] = ne * (int64_t(1) << (h->nc - 1 - l));
+    }
+    if (dt_min) *dt_min = h->dt_min;
+    if (lambda) *lambda = h->lambda;
+    if (finest_dt) *finest_dt = h->delta;
+    if (time_now) *time_now = h->s_now * h->delta;
+    if (launches) *launches = h->launches;
+  });
+}
+
+int lts_set_profiling(lts_t* h, int enable) {
+  return run(h, [&] {
+    h->profiling = enable != 0;
+    h->ev_used = 0;
+    h->ev_kind.clear();
+    h->ev_elems.clear();
+  });
+}
+
+int lts_kernel_stats(lts_t* h, double* ms_out, int64_t* launches_out, int64_t* elems_out) {
+  return run(h, [&] {
+    double ms[2] = {0, 0};
+    int64_t nl[2] = {0, 0}, ne[2] = {0, 0};
+    if (h->ev_used > 0) ck(cudaEventSynchronize(h->ev_pool[h->ev_used - 1]), "event sync");
+    for (size_t i = 0; i < h->ev_kind.size(); ++i) {
+      float t = 0.f;
+      ck(cudaEventElapsedTime(&t, h->ev_pool[2 * i], h->ev_pool[2 * i + 1]), "cudaEventElapsedTime");
+      ms[h->ev_kind[i]] += t;
+      nl[h->ev_kind[i]] += 1;
+      ne[h->ev_kind[i]] += h->ev_elems[i];
+    }
+    for (int i = 0; i < 2; ++i) {
+      if (ms_out) ms_out[i] = ms[i];
+      if (launches_out) launches_out[i] = nl[i];
+      if (elems_out) elems_out[i] = ne[i];
+    }
+    h->ev_used = 0;
+    h->ev_kind.clear();
+    h->ev_elems.clear();
+  });
+}
+
+int lts_transfer_bytes(lts_t* h, int64_t* h2d, int64_t* d2h) {
+  return run(h, [&] {
+    if (h2d) *h2d = h->h2d_bytes;
+    if (d2h) *d2h = h->d2h_bytes;
+  });
+}
+
+int lts_reference_operators(int order, double* K, double* Ft, double* Fb) {
+  if (order < 3 || order > 5) return LTS_ERR_ARG;
+  try {
+    lts::RefOps ops;
+    ops.build(order);
+    const int B = ops.B, F = ops.F;
+    for (int c = 0; c < 3 && K; ++c) std::copy(ops.K[c].begin(), ops.K[c].end(), K + c * B * B);
+    for (int f = 0; f < 4 && Ft; ++f) std::copy(ops.Ft[f].begin(), ops.Ft[f].end(), Ft + f * B * F);
+    for (int jh = 0; jh < 12 && Fb; ++jh) std::copy(ops.Fb[jh].begin(), ops.Fb[jh].end(), Fb + jh * B * F);
+  } catch (...) {
+    return LTS_ERR_OOM;
+  }
+  return LTS_OK;
+}
+
+int lts_eval_basis(int order, int64_t n, const double* xi, double* out) {
+  if (order < 3 || order > 5 || n < 0 || (n > 0 && (!xi || !out))) return LTS_ERR_ARG;
+  try {
+    lts::RefOps ops;
+    ops.build(order);
+    for (int64_t i = 0; i < n; ++i) ops.eval(xi + 3 * i, out + i * ops.B);
+  } catch (...) {
+    return LTS_ERR_OOM;
+  }
+  return LTS_OK;
+}
+
+int lts_quadrature_rule(int order, int64_t* n, double* xi, double* w) {
+  if (order < 3 || order > 5 || !n) return LTS_ERR_ARG;
+  try {
+    lts::RefOps ops;
+    ops.build(order);
+    *n = (int64_t)ops.qp.size();
+    for (size_t p = 0; p < ops.qp.size(); ++p) {
+      if (xi)
+        for (int d = 0; d < 3; ++d) xi[3 * p + d] = ops.qp[p][d];
+      if (w) w[p] = ops.qw[p];
+    }
+  } catch (...) {
+    return LTS_ERR_OOM;
+  }
+  return LTS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,159 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same
+seeded inputs. Tolerance: relative L2 of the DOFs <= 1e-4 per quantity group
+(stresses, velocities, memory variables), the bound stated for FP32 against FP64."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2202_10313_gb300 import binding, build, synth
+from gpu_common import initial_field, make_pair, rel_l2_groups
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+
+
+def _check(gpu, ora, tol=TOL):
+    err = rel_l2_groups(gpu.get_dofs(), ora.Q, ora.nq)
+    for k, v in err.items():
+        assert v <= tol, err
+    return err
+
+
+def test_periodic_cube_order3_gts_plane_wave_50_steps():
+    """Periodic unit cube, 8^3 hexes x 6 = 3072 tets, O = 3 elastic, P plane wave,
+    CFL 0.5, global time stepping, 50 steps."""
+    m = synth.permute_vertex_order(synth.periodic_cube(8), seed=1)
+    K = m["tet"].shape[0]
+    mat = synth.homogeneous(K)
+    gpu, ora, _ = make_pair(3, 0, m, mat)
+    pw = synth.p_plane_wave(2700.0, 6000.0, 3464.0, 2 * np.pi * np.array([1.0, 1.0, 1.0]))
+    cl, lam, sp = gpu.setup_clusters(1, 0.5)
+    assert lam == 1.0 and sp == 1.0
+    gpu.project_initial(lambda x: pw(x, 0.0))
+    ora.project(lambda x: pw(x, 0.0))
+    assert rel_l2_groups(gpu.get_dofs(), ora.Q, 9)["all"] < 1e-6
+    dt = ora.time_step_gts(0.5)
+    info = gpu.info()
+    assert abs(info["finest_dt"] / dt - 1) < 1e-12
+    gpu.advance_steps(50)
+    ora.run_gts(dt, 50)
+    _check(gpu, ora)
+    assert abs(gpu.energy() / ora.energy() - 1) < 1e-5
+
+
+@pytest.mark.parametrize("order,n_mech", [(3, 3), (4, 0), (4, 3), (5, 0), (5, 3)])
+def test_graded_box_lts_auto_clusters(order, n_mech):
+    """Jittered graded box with random layers (free surface + absorbing), clusters
+    from the lambda search, two macro steps; ragged element counts."""
+    m = synth.permute_vertex_order(synth.graded_box(5, 5, 3, 250.0, 125.0, seed=12), seed=2)
+    mat = synth.random_layers(m, n_layers=3, seed=5)
+    gpu, ora, om = make_pair(order, n_mech, m, mat)
+    nc = 3
+    cl, lam, sp = gpu.setup_clusters(nc, 0.5)
+    ora.setup_clusters(nc, 0.5)
+    assert lam == ora.lam_lts and np.array_equal(cl, ora.clusters)
+    assert len(np.unique(cl)) == nc
+    fn = initial_field(ora.nq, [600.0, 700.0, -300.0], 400.0)
+    gpu.project_initial(fn)
+    ora.project(fn)
+    n = 2 * 2 ** (nc - 1)
+    gpu.advance_steps(n)
+    ora.run_lts(n)
+    _check(gpu, ora)
+
+
+def test_forced_clusters_with_all_relations():
+    """Forced 3-cluster split of a periodic cube: same, finer and coarser neighbours,
+    B2 first/second half and accumulated B3 reads all occur."""
+    m = synth.permute_vertex_order(synth.periodic_cube(6), seed=3)
+    K = m["tet"].shape[0]
+    mat = synth.homogeneous(K)
+    gpu, ora, om = make_pair(4, 3, m, dict(mat, qp=np.full(K, 60.0), qs=np.full(K, 30.0)), 1000.0, 50000.0)
+    x = om.centroid[:, 0]
+    from oracle.lts import normalise
+    c = normalise(np.digitize(x, [1 / 3, 2 / 3]), om.nbr).astype(np.int32)
+    gpu.force_clusters(c, 3, 0.125)
+    ora.setup_clusters(3, 0.125, lam=1.0, clusters=c)
+    pw = synth.p_plane_wave(2700.0, 6000.0, 3464.0, 2 * np.pi * np.array([1.0, 1.0, 0.0]))
+    fn = lambda x: np.concatenate([pw(x, 0.0), np.zeros((len(x), 18))], axis=1)
+    gpu.project_initial(fn)
+    ora.project(fn)
+    gpu.advance_steps(8)
+    ora.run_lts(8)
+    _check(gpu, ora)
+
+
+def test_source_and_receivers_lts():
+    """Point source + receivers in an anelastic layered box with 3 clusters: DOFs and
+    every seismogram trace match (misfit E of Sec. VII-B <= 1e-8)."""
+    m = synth.graded_box(5, 5, 3, 250.0, 125.0, seed=21)
+    mat = synth.random_layers(m, n_layers=3, seed=8)
+    gpu, ora, om = make_pair(4, 3, m, mat)
+    xs = np.array([610.0, 640.0, -260.0])
+    m6 = np.array([0.2, -0.4, 0.2, 1.0, 0.1, -0.3])
+    f0, t0 = 8.0, 0.06
+    gpu.add_point_source(xs, m6, f0, t0, 1e12)
+    ora.add_point_source(xs, m6, f0, t0, 1e12)
+    recs = [np.array([300.0 + 170.0 * i, 400.0 + 90.0 * i, -40.0 - 30.0 * i]) for i in range(4)]
+    gpu.setup_clusters(3, 0.5)          # ensure dt is known for the sampling interval
+    dt_rec = gpu.info()["finest_dt"] * 1.37
+    rid_g = [gpu.add_receiver(r, dt_rec) for r in recs]
+    rid_o = [ora.add_receiver(r, dt_rec) for r in recs]
+    cl, lam, sp = gpu.setup_clusters(3, 0.5)
+    ora.setup_clusters(3, 0.5)
+    assert np.array_equal(cl, ora.clusters)
+    n = 8 * 4
+    gpu.advance_steps(n)
+    ora.run_lts(n)
+    _check(gpu, ora)
+    for a, b in zip(rid_g, rid_o):
+        tg, vg = gpu.seismogram(a)
+        to, vo = ora.seismogram(b)
+        assert np.array_equal(tg, to)
+        for q in range(9):
+            ref = vo[:, q]
+            den = np.sum(ref ** 2)
+            if den > 0:
+                assert np.sum((vg[:, q] - ref) ** 2) / den <= 1e-8
+
+
+def test_advance_to_time_and_torch_memory():
+    import torch
+    m = synth.graded_box(4, 4, 3, 200.0, 100.0, seed=5)
+    mat = synth.layered(m, [150.0], [1200.0, 2400.0])
+    gpu, ora, _ = make_pair(3, 0, m, mat)
+    gpu.use_torch_memory()
+    gpu.setup_clusters(2, 0.5)
+    ora.setup_clusters(2, 0.5)
+    fn = initial_field(9, [400.0, 400.0, -200.0], 300.0)
+    gpu.project_initial(fn)
+    ora.project(fn)
+    macro = 2 * gpu.info()["finest_dt"]
+    s = torch.cuda.Stream()
+    gpu.advance(3.5 * macro, stream=s)
+    s.synchronize()
+    assert abs(gpu.info()["time"] / (3 * macro) - 1) < 1e-12
+    ora.run_lts(6)
+    _check(gpu, ora)
+
+
+def test_repeatable_bitwise():
+    m = synth.graded_box(4, 4, 3, 200.0, 100.0, seed=6)
+    mat = synth.random_layers(m, n_layers=2, seed=2)
+    outs = []
+    for _ in range(2):
+        gpu, _, _ = make_pair(5, 3, m, mat)
+        gpu.setup_clusters(2, 0.5)
+        gpu.project_initial(initial_field(27, [400.0, 400.0, -200.0], 300.0))
+        gpu.advance_steps(4)
+        outs.append(gpu.get_dofs())
+    assert np.array_equal(outs[0], outs[1])
