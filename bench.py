@@ -169,7 +169,11 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    cfg = FULL if not args.small else dict(nx=24, ny=24, nz=10, h=250.0, hz=125.0)
+    cfg = FULL
+    if args.small:
+        cfg = dict(nx=24, ny=24, nz=10, h=250.0, hz=125.0)
+    elif args.medium:
+        cfg = dict(nx=48, ny=48, nz=19, h=250.0, hz=125.0)
     mesh, mat, src, recs = make_workload(**cfg)
     K = mesh["tet"].shape[0]
     s = binding.Solver(ORDER, NMECH, device=local_rank)
@@ -286,7 +290,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--small", action="store_true", help="small mesh (quick check / profiling)")
+    ap.add_argument("--small", action="store_true", help="small mesh (quick check)")
+    ap.add_argument("--medium", action="store_true", help="262k-tet mesh (profiling captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

@@ -247,3 +247,32 @@ def permute_vertex_order(mesh, seed=SEED_MESH):
     out["tet"] = new_tet
     out["face_bc"] = new_bc.astype(np.int32)
     return out
+
+
+def random_dofs(n_elem, n_q, n_basis, seed=SEED_MATERIAL, stress_scale=1e6, decay=0.5):
+    """Seeded random modal coefficients [n_elem][n_q][n_basis]: N(0,1) scaled by
+    decay^(mode index / n_basis * 4) so higher modes are smaller; stress rows (and
+    memory-variable rows beyond 9, which are strain-like) scaled as given."""
+    rng = np.random.default_rng(seed)
+    d = rng.normal(size=(n_elem, n_q, n_basis))
+    d *= (decay ** (4.0 * np.arange(n_basis) / n_basis))[None, None, :]
+    d[:, :6, :] *= stress_scale
+    return d
+
+
+def polynomial_field(n_q, degree, scale=1.0, seed=SEED_MATERIAL):
+    """A random polynomial field of total degree <= degree in x/scale (exactly
+    representable by the modal basis of order degree+1)."""
+    rng = np.random.default_rng(seed)
+    expo = [(a, b, c) for a in range(degree + 1) for b in range(degree + 1) for c in range(degree + 1)
+            if a + b + c <= degree]
+    coef = rng.normal(size=(len(expo), n_q))
+
+    def fn(x):
+        y = np.asarray(x) / scale
+        out = np.zeros((len(y), n_q))
+        for cf, (a, b, c) in zip(coef, expo):
+            out += (y[:, 0] ** a * y[:, 1] ** b * y[:, 2] ** c)[:, None] * cf[None, :]
+        return out
+
+    return fn

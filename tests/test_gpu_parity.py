@@ -40,7 +40,8 @@ def test_periodic_cube_order3_gts_plane_wave_50_steps():
     assert lam == 1.0 and sp == 1.0
     gpu.project_initial(lambda x: pw(x, 0.0))
     ora.project(lambda x: pw(x, 0.0))
-    assert rel_l2_groups(gpu.get_dofs(), ora.Q, 9)["all"] < 1e-6
+    # the two projection rules differ by their quadrature error on this sine (~2.6e-6)
+    assert rel_l2_groups(gpu.get_dofs(), ora.Q, 9)["all"] < 1e-5
     dt = ora.time_step_gts(0.5)
     info = gpu.info()
     assert abs(info["finest_dt"] / dt - 1) < 1e-12
@@ -143,6 +144,35 @@ def test_advance_to_time_and_torch_memory():
     s.synchronize()
     assert abs(gpu.info()["time"] / (3 * macro) - 1) < 1e-12
     ora.run_lts(6)
+    _check(gpu, ora)
+
+
+@pytest.mark.parametrize("order", [3, 5])
+def test_projection_of_polynomial_field_is_exact(order):
+    """Both projection rules are exact for a degree O-1 polynomial field."""
+    m = synth.graded_box(3, 3, 2, 100.0, 50.0, seed=2)
+    K = m["tet"].shape[0]
+    mat = synth.homogeneous(K)
+    gpu, ora, _ = make_pair(order, 0, m, mat)
+    gpu.setup_clusters(1, 0.5)
+    fn = synth.polynomial_field(9, order - 1, scale=300.0)
+    gpu.project_initial(fn)
+    ora.project(fn)
+    assert rel_l2_groups(gpu.get_dofs(), ora.Q, 9)["all"] < 1e-6      # FP32 storage
+
+
+def test_random_dofs_periodic_gts_and_lts_one_cluster():
+    """Identical seeded modal DOFs on both sides; GTS (N_c = 1) for 20 steps."""
+    m = synth.permute_vertex_order(synth.periodic_cube(4), seed=7)
+    K = m["tet"].shape[0]
+    mat = synth.homogeneous(K)
+    gpu, ora, _ = make_pair(5, 3, m, dict(mat, qp=np.full(K, 80.0), qs=np.full(K, 40.0)), 500.0, 20000.0)
+    gpu.setup_clusters(1, 0.5)
+    d = synth.random_dofs(K, 27, 35, seed=3)
+    gpu.set_dofs(d)
+    ora.Q = d.copy()
+    gpu.advance_steps(20)
+    ora.run_gts(ora.time_step_gts(0.5), 20)
     _check(gpu, ora)
 
 
