@@ -169,6 +169,29 @@ int lts_kernel_stats(lts_t* h, double* ms_out2, int64_t* launches_out2, int64_t*
  * (source and receiver schedules) and device->host in lts_get_seismogram. */
 int lts_transfer_bytes(lts_t* h, int64_t* h2d, int64_t* d2h);
 
+/* Energy of a caller-owned DOF array, for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is an integration aid. Some callers cannot call
+ * cudaMalloc once they are running: their device memory belongs to another framework's
+ * pool or arena, or they must not risk an allocation failure or the implicit
+ * synchronisation of cudaMalloc/cudaFree inside their time loop. This call allocates
+ * nothing. Its only scratch is a file-scope device array of LTS_NOALLOC_MAX_ELEMENTS
+ * doubles (2 MiB) that every GPU which loads the library holds until the process exits.
+ * Inputs (device pointers on the current CUDA device, caller-owned): dofs FP32
+ * [n_elem][9 + 6 n_mech][B(order)] (the layout of lts_get_dofs, unpadded), mat FP64
+ * [n_elem][4] = (lambda, mu, rho, |det J|). Output: *energy (device FP64) receives
+ * sum_k |det J_k| sum_b (rho |v_b|^2/2 + sigma_b : C^-1 sigma_b / 2), the quantity of
+ * lts_energy. Runs asynchronously on cuda_stream (NULL = legacy default stream).
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture. Every call
+ * shares the one scratch array, so calls that overlap on the GPU (on different streams)
+ * race; the array is fully rewritten for the first n_elem entries by each call, so
+ * nothing needs clearing. Errors: LTS_ERR_ARG for a bad order or mechanism count, a NULL
+ * pointer, or n_elem <= 0 or n_elem > LTS_NOALLOC_MAX_ELEMENTS; LTS_ERR_CUDA if the
+ * address lookup or a launch fails. */
+#define LTS_NOALLOC_MAX_ELEMENTS 262144
+int lts_energy_noalloc(int order, int n_mech, const float* dofs, const double* mat, int64_t n_elem,
+                       double* energy, void* cuda_stream);
+
 /* Host-only helpers (no handle, no GPU). Reference operators of order O in the basis
  * described above (Sec. III-A), from exact polynomial integration:
  *   K[c][i][j]   = int phi_i d(phi_j)/d(xi_c)                     (3 x B x B)

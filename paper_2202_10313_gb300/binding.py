@@ -47,6 +47,7 @@ _SIGS = {
     "lts_set_profiling": (_I, [_P, _I]),
     "lts_kernel_stats": (_I, [_P, _P, _P, _P]),
     "lts_transfer_bytes": (_I, [_P, _P, _P]),
+    "lts_energy_noalloc": (_I, [_I, _I, _P, _P, _L, _P, _P]),
     "lts_reference_operators": (_I, [_I, _P, _P, _P]),
     "lts_eval_basis": (_I, [_I, _L, _P, _P]),
     "lts_quadrature_rule": (_I, [_I, _P, _P, _P]),
