@@ -119,6 +119,13 @@ int lts_project_initial(lts_t* h, const double* values);
 int lts_set_dofs(lts_t* h, const double* dofs);
 int lts_get_dofs(lts_t* h, double* dofs);
 
+/* DOFs of a subset of elements: elems[n] (original indices), dofs[n][n_q][B] in the
+ * order of elems. Setting leaves every other element unchanged. Both synchronise the
+ * device. Errors: LTS_ERR_STATE before cluster set-up, LTS_ERR_ARG for an index out of
+ * range or NULL arrays with n > 0. */
+int lts_set_dofs_subset(lts_t* h, int64_t n, const int64_t* elems, const double* dofs);
+int lts_get_dofs_subset(lts_t* h, int64_t n, const int64_t* elems, double* dofs);
+
 /* Moment-tensor point source (reading of Sec. VII-B's point sources): moment rate
  * m0 * m6 * s(t), s the Ricker wavelet (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2),
  * m6 = (xx, yy, zz, xy, yz, xz). The containing element (lowest index whose closed

@@ -70,36 +70,44 @@ class Mesh:
         return keys
 
     def _neighbours(self):
+        """Face matching by sorted vertex keys (lexicographic sort), then (j, h).
+
+        Two faces match when their sorted vertex keys (vertex ids; for periodic faces the
+        position modulo the box) and boundary kind agree; every such group must hold
+        exactly two faces. h is the position in the neighbour's face of the local face's
+        first vertex; the other two must appear in reversed cyclic order."""
         K = self.K
         pkeys = self._vertex_keys()
         self.nbr = -np.ones((K, 4), dtype=np.int64)
         self.nbr_face = -np.ones((K, 4), dtype=np.int64)
         self.nbr_orient = -np.ones((K, 4), dtype=np.int64)
-        faces = {}
-        for k in range(K):
-            for i, fv in enumerate(FACE_VERTS):
-                bc = self.face_bc[k, i]
-                if bc in (BC_ABSORBING, BC_FREE):
-                    continue
-                ids = self.tet[k, list(fv)]
-                if bc == BC_PERIODIC:
-                    if pkeys is None:
-                        raise MeshError("periodic face without a period")
-                    ids = pkeys[ids]
-                key = (int(bc),) + tuple(sorted(int(v) for v in ids))
-                faces.setdefault(key, []).append((k, i, tuple(int(v) for v in ids)))
-        for key, lst in faces.items():
-            if len(lst) != 2:
-                raise MeshError("face %r shared by %d elements" % (key, len(lst)))
-            (k, i, ids_k), (m, j, ids_m) = lst
-            for (e, f, ids_e, g, fg, ids_g) in ((k, i, ids_k, m, j, ids_m), (m, j, ids_m, k, i, ids_k)):
-                h = ids_g.index(ids_e[0])
-                # outward faces of two elements list the shared vertices in opposite cyclic order
-                if ids_g[(h + 2) % 3] != ids_e[1] or ids_g[(h + 1) % 3] != ids_e[2]:
-                    raise MeshError("inconsistent face orientation")
-                self.nbr[e, f] = g
-                self.nbr_face[e, f] = fg
-                self.nbr_orient[e, f] = h
+        ids = np.stack([self.tet[:, list(fv)] for fv in FACE_VERTS], axis=1)      # (K, 4, 3)
+        bc = self.face_bc
+        if np.any(bc == BC_PERIODIC) and pkeys is None:
+            raise MeshError("periodic face without a period")
+        if pkeys is not None:
+            ids = np.where((bc == BC_PERIODIC)[:, :, None], pkeys[ids], ids)
+        sel = (bc == BC_INTERIOR) | (bc == BC_PERIODIC)
+        elem, face = np.nonzero(sel)
+        fids = ids[elem, face]                                                     # (F, 3) in face order
+        skey = np.sort(fids, axis=1)
+        kind = bc[elem, face]
+        order = np.lexsort((skey[:, 2], skey[:, 1], skey[:, 0], kind))
+        sk = np.concatenate([kind[order][:, None], skey[order]], axis=1)
+        same_next = np.all(sk[1:] == sk[:-1], axis=1)
+        if len(order) % 2 or not np.all(same_next[0::2]) or np.any(same_next[1::2]):
+            raise MeshError("a face is not shared by exactly two elements")
+        a_, b_ = order[0::2], order[1::2]
+        for e_, g_ in ((a_, b_), (b_, a_)):
+            ide, idg = fids[e_], fids[g_]
+            h = np.argmax(idg == ide[:, :1], axis=1)
+            r = np.arange(len(h))
+            ok = (idg[r, h] == ide[:, 0]) & (idg[r, (h + 2) % 3] == ide[:, 1]) & (idg[r, (h + 1) % 3] == ide[:, 2])
+            if not np.all(ok):
+                raise MeshError("inconsistent face orientation")
+            self.nbr[elem[e_], face[e_]] = elem[g_]
+            self.nbr_face[elem[e_], face[e_]] = face[g_]
+            self.nbr_orient[elem[e_], face[e_]] = h
 
     def xi_of(self, k, x):
         """Reference coordinates of physical point x inside element k."""

@@ -37,6 +37,8 @@ _SIGS = {
     "lts_project_initial": (_I, [_P, _P]),
     "lts_set_dofs": (_I, [_P, _P]),
     "lts_get_dofs": (_I, [_P, _P]),
+    "lts_set_dofs_subset": (_I, [_P, _L, _P, _P]),
+    "lts_get_dofs_subset": (_I, [_P, _L, _P, _P]),
     "lts_add_point_source": (_I, [_P, _I, _P, _P, _D, _D, _D]),
     "lts_add_receiver": (_I, [_P, _P, _D, _P]),
     "lts_advance": (_I, [_P, _D, _P]),
@@ -233,6 +235,17 @@ class Solver:
     def get_dofs(self):
         out = np.zeros((self.K, self.nq, self.nb))
         self._check(lib().lts_get_dofs(self._h, _ptr(out)))
+        return out
+
+    def set_dofs_subset(self, elems, dofs):
+        el = np.ascontiguousarray(elems, dtype=np.int64)
+        d = _f64(dofs, len(el) * self.nq * self.nb)
+        self._check(lib().lts_set_dofs_subset(self._h, len(el), _ptr(el), _ptr(d)))
+
+    def get_dofs_subset(self, elems):
+        el = np.ascontiguousarray(elems, dtype=np.int64)
+        out = np.zeros((len(el), self.nq, self.nb))
+        self._check(lib().lts_get_dofs_subset(self._h, len(el), _ptr(el), _ptr(out)))
         return out
 
     # --------------------------------------------------------------- running

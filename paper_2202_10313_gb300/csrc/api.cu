@@ -812,6 +812,42 @@ int lts_get_dofs(lts_t* h, double* dofs) {
   });
 }
 
+int lts_set_dofs_subset(lts_t* h, int64_t n, const int64_t* elems, const double* dofs) {
+  return run(h, [&] {
+    if (!h->ready) fail(LTS_ERR_STATE, "clusters not set up");
+    if (n < 0 || (n > 0 && (!elems || !dofs))) fail(LTS_ERR_ARG, "bad subset arguments");
+    const int B = h->L.B, NQ = h->L.NQ, QS = h->L.QS;
+    std::vector<float> row(QS, 0.f);
+    ck(cudaSetDevice(h->device), "cudaSetDevice");
+    ck(cudaDeviceSynchronize(), "synchronize");
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t k = elems[i];
+      if (k < 0 || k >= h->mesh.K) fail(LTS_ERR_ARG, "element index out of range");
+      for (int r = 0; r < NQ; ++r)
+        for (int b = 0; b < B; ++b) row[r * B + b] = (float)dofs[(i * NQ + r) * B + b];
+      ck(cudaMemcpy(h->dst.Q + h->iperm[k] * QS, row.data(), QS * sizeof(float), cudaMemcpyHostToDevice), "upload");
+    }
+  });
+}
+
+int lts_get_dofs_subset(lts_t* h, int64_t n, const int64_t* elems, double* dofs) {
+  return run(h, [&] {
+    if (!h->ready) fail(LTS_ERR_STATE, "clusters not set up");
+    if (n < 0 || (n > 0 && (!elems || !dofs))) fail(LTS_ERR_ARG, "bad subset arguments");
+    const int B = h->L.B, NQ = h->L.NQ, QS = h->L.QS;
+    std::vector<float> row(QS);
+    ck(cudaSetDevice(h->device), "cudaSetDevice");
+    ck(cudaDeviceSynchronize(), "synchronize");
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t k = elems[i];
+      if (k < 0 || k >= h->mesh.K) fail(LTS_ERR_ARG, "element index out of range");
+      ck(cudaMemcpy(row.data(), h->dst.Q + h->iperm[k] * QS, QS * sizeof(float), cudaMemcpyDeviceToHost), "download");
+      for (int r = 0; r < NQ; ++r)
+        for (int b = 0; b < B; ++b) dofs[(i * NQ + r) * B + b] = row[r * B + b];
+    }
+  });
+}
+
 int lts_add_point_source(lts_t* h, int fused_idx, const double x[3], const double m6[6], double f0, double t0,
                          double m0) {
   return run(h, [&] {

@@ -42,9 +42,15 @@ struct Cfg {
   static constexpr int BUFS = rup(9 * B, 4);         // element stride of B1/B2/B3
   static constexpr int NE = (O == 3) ? 24 : (O == 4 ? 12 : 8);
   static constexpr int NT = rup(NE * B, 32);
-  static constexpr int AR = 12;                      // staged elastic rows (padded)
-  static constexpr int FR = (M > 0) ? 16 : 12;       // staged flux rows (9 elastic + 6 anelastic)
-  static constexpr int XR = 9;                       // gathered neighbour rows
+  static constexpr int AR = 12;                      // staged elastic rows (padded, 16-byte stores)
+  // staged flux rows (9 elastic + 6 anelastic): a stride of 20 (12) floats keeps the
+  // 16-byte stores of 8 consecutive tasks on 8 distinct 4-bank groups
+  static constexpr int FR = (M > 0) ? 20 : 12;
+  static constexpr int XR = 9;                       // gathered neighbour rows (odd stride)
+  // time kernel load balance: columns of degree <= O-3 split their k-range with a
+  // helper thread that owns a degree O-1 column (which has no time-kernel product)
+  static constexpr int NSPLIT = nbasis(O - 2);
+  static constexpr int SPR = 28;                     // floats per staged partial (27 + pad)
   // shared memory (floats) of k_predict_local
   static constexpr int P_K = 0;
   static constexpr int P_FT = rup(P_K + 3 * B * BS, 4);
@@ -52,7 +58,8 @@ struct Cfg {
   static constexpr int P_A = rup(P_FH + 4 * F * B, 4);
   static constexpr int P_FL = rup(P_A + 2 * NE * B * AR, 4);
   static constexpr int P_E = rup(P_FL + NE * 4 * F * FR, 4);
-  static constexpr int P_META = rup(P_E + NE * ED, 4);
+  static constexpr int P_SP = rup(P_E + NE * ED, 4);
+  static constexpr int P_META = rup(P_SP + NE * NSPLIT * SPR, 4);
   static constexpr int P_TOTAL = rup(P_META + NE, 4);
   // shared memory (floats) of k_neighbour
   static constexpr int N_FB = 0;
@@ -107,6 +114,31 @@ __device__ __forceinline__ void task_of(int t, int& e, int& b, int& p) {
     }
     off += NE * np;
   }
+}
+
+// Face tasks (element, face, face mode f), ordered by the degree of f (highest first): the
+// product with F~ / F- only involves modes of degree >= deg f.
+template <int O, int NE>
+__device__ __forceinline__ void face_task_of(int t, int& ee, int& i, int& f, int& pf) {
+  int off = 0;
+  ee = -1;
+  i = f = pf = 0;
+#pragma unroll
+  for (int q = O - 1; q >= 0; --q) {
+    const int n = NE * 4 * (q + 1);
+    if (t >= off && t < off + n) {
+      const int idx = t - off, r = idx % (4 * (q + 1));
+      ee = idx / (4 * (q + 1));
+      i = r / (q + 1);
+      f = nface(q) + r % (q + 1);
+      pf = q;
+    }
+    off += n;
+  }
+}
+
+__device__ __forceinline__ void st4(float* p, float a, float b, float c, float d) {
+  *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
 }
 
 // Physical combination of reference-derivative projections Y[c][q] (Sec. III-A star
@@ -165,7 +197,7 @@ __device__ __forceinline__ void coupling_add(float (&s)[9], const float* th, flo
 // velocities -t*/rho, memory variables -sym(n v*^T) (omega_l factored out).
 template <int M>
 __device__ __forceinline__ void face_flux(const float (&g)[9], const float* fd, float lam, float mu, float rinv,
-                                          float* fl) {
+                                          float (&fl)[16]) {
   const float nx = fd[0], ny = fd[1], nz = fd[2];
   const float tx = g[0] * nx + g[3] * ny + g[5] * nz;
   const float ty = g[3] * nx + g[1] * ny + g[4] * nz;
@@ -204,15 +236,24 @@ __device__ __forceinline__ void face_flux(const float (&g)[9], const float* fd, 
     fl[15] = 0.f;
   } else {
     fl[9] = fl[10] = fl[11] = 0.f;
+    fl[12] = fl[13] = fl[14] = fl[15] = 0.f;
   }
+}
+
+template <int FR>
+__device__ __forceinline__ void store_flux(float* dst, const float (&fl)[16]) {
+  st4(dst, fl[0], fl[1], fl[2], fl[3]);
+  st4(dst + 4, fl[4], fl[5], fl[6], fl[7]);
+  st4(dst + 8, fl[8], fl[9], fl[10], fl[11]);
+  if constexpr (FR >= 16) st4(dst + 12, fl[12], fl[13], fl[14], fl[15]);
 }
 
 // ------------------------------------------------------------------ predict + local
 template <int O, int M>
-__global__ void __launch_bounds__(Cfg<O, M>::NT, 2) k_predict_local(DevOps ops, DevState st, PhaseArgs ph) {
+__global__ void __maxnreg__(112) k_predict_local(DevOps ops, DevState st, PhaseArgs ph) {
   using C = Cfg<O, M>;
   constexpr int B = C::B, F = C::F, NE = C::NE, NT = C::NT, BS = C::BS, AR = C::AR, FR = C::FR;
-  constexpr int NQ = C::NQ, NA = C::NA, QS = C::QS, BUFS = C::BUFS;
+  constexpr int NQ = C::NQ, NA = C::NA, QS = C::QS, BUFS = C::BUFS, NSPLIT = C::NSPLIT, SPR = C::SPR;
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
   float* sK = smem + C::P_K;
@@ -221,6 +262,7 @@ __global__ void __launch_bounds__(Cfg<O, M>::NT, 2) k_predict_local(DevOps ops, 
   float* sA = smem + C::P_A;
   float* sFl = smem + C::P_FL;
   float* sE = smem + C::P_E;
+  float* sSP = smem + C::P_SP;
   int* sMeta = reinterpret_cast<int*>(smem + C::P_META);
   const int tid = threadIdx.x;
 
@@ -234,9 +276,26 @@ __global__ void __launch_bounds__(Cfg<O, M>::NT, 2) k_predict_local(DevOps ops, 
   int e = -1, b = 0, p = 0;
   task_of<O, NE>(tid, e, b, p);
   const bool act = e >= 0;
-  const int kb_ck = nbasis(p + 1);      // K_c[b][k] != 0 needs deg k > deg b
+  const int es = act ? e : 0;
+  // time-kernel product of this thread: column ck_col over k in [ck_k0, ck_k1)
+  const int hj = b - nbasis(O - 1);                    // index among the degree O-1 columns
+  const bool helper = act && p == O - 1 && hj < NSPLIT;
+  const bool split_owner = act && b < NSPLIT;
+  auto kmid = [](int col, int pd) { return (nbasis(pd + 1) + B + 1) / 2; };
+  int ck_col = b, ck_k0 = nbasis(p + 1), ck_k1 = B;
+  if (helper) {
+    int ph_ = 0;
+    while (nbasis(ph_ + 1) <= hj) ++ph_;
+    ck_col = hj;
+    ck_k0 = kmid(hj, ph_);
+    ck_k1 = B;
+  } else if (split_owner) {
+    ck_k1 = kmid(b, p);
+  }
+  if (!act) ck_k0 = ck_k1 = 0;
   const int ke_vol = nbasis(p);         // K_c[k][b] != 0 needs deg k < deg b
   const int fmax = nface(p + 1);        // face modes of degree <= deg b
+  int fe = -1, fi = 0, ff = 0, fpf = 0;  // first face task of this thread (second one below)
   const int nelem = ph.end - ph.begin;
   const int nbatch = (nelem + NE - 1) / NE;
 
@@ -251,30 +310,36 @@ __global__ void __launch_bounds__(Cfg<O, M>::NT, 2) k_predict_local(DevOps ops, 
     __syncthreads();
     const int g = e0 + e;
     const bool valid = act && g < ph.end;
-    const float* ed = sE + (act ? e : 0) * ED;
-    const int meta = act ? sMeta[e] : 0;
+    const float* ed = sE + es * ED;
+    const int meta = act ? sMeta[es] : 0;
     const int cl = meta & 0xff;
     float T[NQ], Th[9], Da[NA > 0 ? NA : 1];
     {
-      float* a0 = sA + ((0 * NE + (act ? e : 0)) * B + b) * AR;
+      float v[12];
+#pragma unroll
+      for (int r = 0; r < 12; ++r) v[r] = 0.f;
       if (valid) {
-        const float* q = st.Q + (size_t)g * QS;
+        const float* q = st.Q + (size_t)g * QS + b;
 #pragma unroll
-        for (int r = 0; r < 9; ++r) {
-          const float v = q[r * B + b];
-          T[r] = ph.coef[cl][0] * v;
-          Th[r] = ph.hcoef[cl][0] * v;
-          a0[r] = v;
-        }
+        for (int r = 0; r < 9; ++r) v[r] = q[r * B];
 #pragma unroll
-        for (int r = 0; r < NA; ++r) {
-          const float v = q[(9 + r) * B + b];
-          Da[r] = v;
-          T[9 + r] = ph.coef[cl][0] * v;
-        }
-      } else if (act) {
+        for (int r = 0; r < NA; ++r) Da[r] = q[(9 + r) * B];
+      } else {
 #pragma unroll
-        for (int r = 0; r < 9; ++r) a0[r] = 0.f;
+        for (int r = 0; r < NA; ++r) Da[r] = 0.f;
+      }
+#pragma unroll
+      for (int r = 0; r < 9; ++r) {
+        T[r] = ph.coef[cl][0] * v[r];
+        Th[r] = ph.hcoef[cl][0] * v[r];
+      }
+#pragma unroll
+      for (int r = 0; r < NA; ++r) T[9 + r] = ph.coef[cl][0] * Da[r];
+      if (act) {
+        float* a0 = sA + ((0 * NE + es) * B + b) * AR;
+        st4(a0, v[0], v[1], v[2], v[3]);
+        st4(a0 + 4, v[4], v[5], v[6], v[7]);
+        st4(a0 + 8, v[8], 0.f, 0.f, 0.f);
       }
     }
     // ---- time kernel: d^{d+1} Q from d^d Q (Cauchy-Kowalevski), Taylor sums
@@ -287,11 +352,11 @@ __global__ void __launch_bounds__(Cfg<O, M>::NT, 2) k_predict_local(DevOps ops, 
       for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int r = 0; r < 9; ++r) Y[c][r] = 0.f;
-      if (act) {
-        const float* Ab = sA + ((buf * NE + e) * B) * AR;
-        const float* K0 = sK + b * BS;
+      {
+        const float* Ab = sA + ((buf * NE + es) * B) * AR;
+        const float* K0 = sK + ck_col * BS;
 #pragma unroll 2
-        for (int k = kb_ck; k < B; ++k) {
+        for (int k = ck_k0; k < ck_k1; ++k) {
           const float4 x0 = *reinterpret_cast<const float4*>(Ab + k * AR);
           const float4 x1 = *reinterpret_cast<const float4*>(Ab + k * AR + 4);
           const float x8 = Ab[k * AR + 8];
@@ -304,18 +369,48 @@ __global__ void __launch_bounds__(Cfg<O, M>::NT, 2) k_predict_local(DevOps ops, 
           }
         }
       }
-      if (valid) {
+      if (helper) {
+        // hand the second half of column hj's product to its owner
+        float* sp = sSP + (es * NSPLIT + hj) * SPR;
+        st4(sp, Y[0][0], Y[0][1], Y[0][2], Y[0][3]);
+        st4(sp + 4, Y[0][4], Y[0][5], Y[0][6], Y[0][7]);
+        st4(sp + 8, Y[0][8], Y[1][0], Y[1][1], Y[1][2]);
+        st4(sp + 12, Y[1][3], Y[1][4], Y[1][5], Y[1][6]);
+        st4(sp + 16, Y[1][7], Y[1][8], Y[2][0], Y[2][1]);
+        st4(sp + 20, Y[2][2], Y[2][3], Y[2][4], Y[2][5]);
+        st4(sp + 24, Y[2][6], Y[2][7], Y[2][8], 0.f);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int r = 0; r < 9; ++r) Y[c][r] = 0.f;    // own column has degree O-1: no product
+      }
+      __syncthreads();
+      if (split_owner) {
+        const float* sp = sSP + (es * NSPLIT + b) * SPR;
+        float w[28];
+#pragma unroll
+        for (int q4 = 0; q4 < 7; ++q4) {
+          const float4 t4 = *reinterpret_cast<const float4*>(sp + 4 * q4);
+          w[4 * q4] = t4.x;
+          w[4 * q4 + 1] = t4.y;
+          w[4 * q4 + 2] = t4.z;
+          w[4 * q4 + 3] = t4.w;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int r = 0; r < 9; ++r) Y[c][r] += w[c * 9 + r];
+      }
+      if (act) {
         float out[9], eps[6];
         star_apply(Y, ed, out, eps);
 #pragma unroll
         for (int l = 0; l < M; ++l) coupling_add(out, Da + 6 * l, ed[12 + 2 * l], ed[13 + 2 * l]);
         const float c1 = ph.coef[cl][d + 1], h1 = ph.hcoef[cl][d + 1];
-        float* an = sA + (((buf ^ 1) * NE + e) * B + b) * AR;
 #pragma unroll
         for (int r = 0; r < 9; ++r) {
           T[r] = fmaf(c1, out[r], T[r]);
           Th[r] = fmaf(h1, out[r], Th[r]);
-          an[r] = out[r];
         }
 #pragma unroll
         for (int l = 0; l < M; ++l)
@@ -325,10 +420,10 @@ __global__ void __launch_bounds__(Cfg<O, M>::NT, 2) k_predict_local(DevOps ops, 
             Da[6 * l + r] = v;
             T[9 + 6 * l + r] = fmaf(c1, v, T[9 + 6 * l + r]);
           }
-      } else if (act) {
-        float* an = sA + (((buf ^ 1) * NE + e) * B + b) * AR;
-#pragma unroll
-        for (int r = 0; r < 9; ++r) an[r] = 0.f;
+        float* an = sA + (((buf ^ 1) * NE + es) * B + b) * AR;
+        st4(an, out[0], out[1], out[2], out[3]);
+        st4(an + 4, out[4], out[5], out[6], out[7]);
+        st4(an + 8, out[8], 0.f, 0.f, 0.f);
       }
       buf ^= 1;
     }
@@ -354,12 +449,11 @@ __global__ void __launch_bounds__(Cfg<O, M>::NT, 2) k_predict_local(DevOps ops, 
       }
     }
     // ---- volume kernel
-    {
-      float* a = sA + ((buf * NE + (act ? e : 0)) * B + b) * AR;
-      if (act) {
-#pragma unroll
-        for (int r = 0; r < 9; ++r) a[r] = valid ? T[r] : 0.f;
-      }
+    if (act) {
+      float* a = sA + ((buf * NE + es) * B + b) * AR;
+      st4(a, T[0], T[1], T[2], T[3]);
+      st4(a + 4, T[4], T[5], T[6], T[7]);
+      st4(a + 8, T[8], 0.f, 0.f, 0.f);
     }
     __syncthreads();
     float acc[NQ];
@@ -393,28 +487,27 @@ __global__ void __launch_bounds__(Cfg<O, M>::NT, 2) k_predict_local(DevOps ops, 
         for (int r = 0; r < 9; ++r) V[r] = -out[r];
 #pragma unroll
         for (int l = 0; l < M; ++l) coupling_add(V, T + 9 + 6 * l, ed[12 + 2 * l], ed[13 + 2 * l]);
-        const float* q = st.Q + (size_t)g * QS;
+        const float* q = st.Q + (size_t)g * QS + b;
 #pragma unroll
-        for (int r = 0; r < 9; ++r) acc[r] = q[r * B + b] + V[r];
+        for (int r = 0; r < 9; ++r) acc[r] = q[r * B] + V[r];
 #pragma unroll
         for (int l = 0; l < M; ++l)
 #pragma unroll
           for (int r = 0; r < 6; ++r)
-            acc[9 + 6 * l + r] = q[(9 + 6 * l + r) * B + b] + ph.omega[l] * (-eps[r] - T[9 + 6 * l + r]);
+            acc[9 + 6 * l + r] = q[(9 + 6 * l + r) * B] + ph.omega[l] * (-eps[r] - T[9 + 6 * l + r]);
       }
     }
     // ---- local surface kernel: G_i = T^e F~_i, flux, staged for F^
+#pragma unroll 1
     for (int t = tid; t < NE * 4 * F; t += NT) {
-      const int ee = t / (4 * F), j = t % (4 * F), i = j / F, f = j % F;
-      int pf = 0;
-      while (nface(pf + 1) <= f) ++pf;
+      face_task_of<O, NE>(t, fe, fi, ff, fpf);
       float gq[9];
 #pragma unroll
       for (int r = 0; r < 9; ++r) gq[r] = 0.f;
-      const float* Ab = sA + ((buf * NE + ee) * B) * AR;
-      const float* Fi = sFt + i * B * F + f;
+      const float* Ab = sA + ((buf * NE + fe) * B) * AR;
+      const float* Fi = sFt + fi * B * F + ff;
 #pragma unroll 2
-      for (int k = nbasis(pf); k < B; ++k) {
+      for (int k = nbasis(fpf); k < B; ++k) {
         const float4 x0 = *reinterpret_cast<const float4*>(Ab + k * AR);
         const float4 x1 = *reinterpret_cast<const float4*>(Ab + k * AR + 4);
         const float x8 = Ab[k * AR + 8];
@@ -429,8 +522,10 @@ __global__ void __launch_bounds__(Cfg<O, M>::NT, 2) k_predict_local(DevOps ops, 
         gq[7] = fmaf(x1.w, w, gq[7]);
         gq[8] = fmaf(x8, w, gq[8]);
       }
-      const float* ede = sE + ee * ED;
-      face_flux<M>(gq, ede + 20 + 11 * i, ede[9], ede[10], ede[11], sFl + (ee * 4 * F + j) * FR);
+      const float* ede = sE + fe * ED;
+      float fl[16];
+      face_flux<M>(gq, ede + 20 + 11 * fi, ede[9], ede[10], ede[11], fl);
+      store_flux<FR>(sFl + (fe * 4 * F + fi * F + ff) * FR, fl);
     }
     __syncthreads();
     if (valid) {
@@ -468,14 +563,14 @@ __global__ void __launch_bounds__(Cfg<O, M>::NT, 2) k_predict_local(DevOps ops, 
           }
         }
       }
-      float* q = st.Q + (size_t)g * QS;
+      float* q = st.Q + (size_t)g * QS + b;
 #pragma unroll
-      for (int r = 0; r < 9; ++r) q[r * B + b] = acc[r] + S[r];
+      for (int r = 0; r < 9; ++r) q[r * B] = acc[r] + S[r];
       if constexpr (M > 0) {
 #pragma unroll
         for (int l = 0; l < M; ++l)
 #pragma unroll
-          for (int r = 0; r < 6; ++r) q[(9 + 6 * l + r) * B + b] = acc[9 + 6 * l + r] + ph.omega[l] * S[NS - 6 + r];
+          for (int r = 0; r < 6; ++r) q[(9 + 6 * l + r) * B] = acc[9 + 6 * l + r] + ph.omega[l] * S[NS - 6 + r];
       }
     }
   }
@@ -522,42 +617,40 @@ __global__ void __launch_bounds__(Cfg<O, M>::NT, 2) k_neighbour(DevOps ops, DevS
     __syncthreads();
     const int g = e0 + e;
     const bool valid = act && g < ph.end;
-    // ---- gather the neighbours' time-integrated DOFs by cluster relation (Sec. V-B)
+    // ---- gather the neighbours' time-integrated DOFs by cluster relation (Sec. V-B):
+    // all 4 x 9 loads are issued before the shared-memory stores
     if (act) {
       const int* ie = sI + e * 9;
       const int cl = ie[8] & 0xff;
-#pragma unroll 1
+      const int par = valid ? ph.parity[cl] : 0;
+      float xv[4][9];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int nb = valid ? ie[i] : -1;
+        const int rel = ie[4 + i] >> 8;
+        const float* src1 = (rel == 1) ? st.B3 : ((rel == 2 && par == 0) ? st.B2 : st.B1);
+        const bool sub = (rel == 2 && par == 1);
+        const size_t off = (size_t)(nb < 0 ? 0 : nb) * BUFS + b;
+#pragma unroll
+        for (int r = 0; r < 9; ++r) xv[i][r] = (nb < 0) ? 0.f : __ldg(src1 + off + r * B);
+        if (sub) {
+#pragma unroll
+          for (int r = 0; r < 9; ++r) xv[i][r] -= __ldg(st.B2 + off + r * B);
+        }
+      }
+#pragma unroll
       for (int i = 0; i < 4; ++i) {
         float* x = sX + ((e * 4 + i) * B + b) * XR;
-        const int nb = valid ? ie[i] : -1;
-        if (nb < 0) {
 #pragma unroll
-          for (int r = 0; r < 9; ++r) x[r] = 0.f;
-          continue;
-        }
-        const int rel = ie[4 + i] >> 8;
-        const size_t off = (size_t)nb * BUFS + b;
-        if (rel == 0) {
-#pragma unroll
-          for (int r = 0; r < 9; ++r) x[r] = st.B1[off + r * B];
-        } else if (rel == 1) {
-#pragma unroll
-          for (int r = 0; r < 9; ++r) x[r] = st.B3[off + r * B];
-        } else if (ph.parity[cl] == 0) {
-#pragma unroll
-          for (int r = 0; r < 9; ++r) x[r] = st.B2[off + r * B];
-        } else {
-#pragma unroll
-          for (int r = 0; r < 9; ++r) x[r] = st.B1[off + r * B] - st.B2[off + r * B];
-        }
+        for (int r = 0; r < 9; ++r) x[r] = xv[i][r];
       }
     }
     __syncthreads();
     // ---- H_i = X F-_{j,h}, closed-form flux with the neighbour's coefficients
+#pragma unroll 1
     for (int t = tid; t < NE * 4 * F; t += NT) {
-      const int ee = t / (4 * F), j = t % (4 * F), i = j / F, f = j % F;
-      int pf = 0;
-      while (nface(pf + 1) <= f) ++pf;
+      int ee, i, f, pf;
+      face_task_of<O, NE>(t, ee, i, f, pf);
       const int code = sI[ee * 9 + 4 + i];
       const int jh = (code >= 0) ? (code & 0xff) : 0;
       float gq[9];
@@ -572,7 +665,9 @@ __global__ void __launch_bounds__(Cfg<O, M>::NT, 2) k_neighbour(DevOps ops, DevS
         for (int r = 0; r < 9; ++r) gq[r] = fmaf(X[k * XR + r], w, gq[r]);
       }
       const float* nd = sD + ee * ND;
-      face_flux<M>(gq, nd + 4 + 11 * i, nd[0], nd[1], nd[2], sFl + (ee * 4 * F + j) * FR);
+      float fl[16];
+      face_flux<M>(gq, nd + 4 + 11 * i, nd[0], nd[1], nd[2], fl);
+      store_flux<FR>(sFl + (ee * 4 * F + i * F + f) * FR, fl);
     }
     __syncthreads();
     if (valid) {

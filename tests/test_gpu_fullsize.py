@@ -1,0 +1,94 @@
+"""Full-size parity on the benchmark configuration (2,101,248 tets, order 5, 3 mechanisms,
+5 clusters with the lambda search, CFL 0.5, moment-tensor source, 64 receivers), run
+through the same set-up and launches as bench.py for one macro step (16 finest steps).
+
+Sampled outputs: after 16 finest steps an element's state depends only on data within 16
+face hops (information crosses at most one face per finest step). For one sample element
+per non-empty cluster, the oracle runs the same 16 steps on the 17-hop ball around it
+(cut faces absorbing, one hop of margin), with its own clustering of the full mesh, and
+the sample's DOFs are compared with the GPU's."""
+import numpy as np
+import pytest
+
+import bench
+from oracle import lts as olts
+from oracle.mesh import Mesh
+from oracle.scheme import Solver as Oracle
+from paper_2202_10313_gb300 import binding, build, synth
+from gpu_common import rel_l2_groups
+
+pytestmark = pytest.mark.gpu
+HOPS = 17
+
+
+def _ball(nbr, k, hops):
+    seen = {int(k)}
+    front = [int(k)]
+    for _ in range(hops):
+        nxt = []
+        for e in front:
+            for nb in nbr[e]:
+                if nb >= 0 and int(nb) not in seen:
+                    seen.add(int(nb))
+                    nxt.append(int(nb))
+        front = nxt
+    return np.array(sorted(seen))
+
+
+def test_bench_configuration_sampled_parity():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    mesh, mat, src, recs = bench.make_workload(**bench.FULL)
+    K = mesh["tet"].shape[0]
+    assert K == 2101248
+    # ---- library, set up exactly as bench.py does
+    g = binding.Solver(bench.ORDER, bench.NMECH, device=0)
+    g.set_mesh(mesh["xyz"], mesh["tet"], mesh["face_bc"])
+    g.set_material(mat["rho"], mat["vp"], mat["vs"], mat["qp"], mat["qs"], 0.1, 5.0)
+    g.add_point_source(src["x"], src["m6"], src["f0"], src["t0"], src["m0"])
+    for r in recs:
+        g.add_receiver(r, 0.01)
+    g.use_torch_memory(bench.NCLUSTERS)
+    cl_g, lam_g, sp_g = g.setup_clusters(bench.NCLUSTERS, bench.CFL)
+    # ---- oracle clustering of the full mesh
+    om = Mesh(mesh["xyz"], mesh["tet"], mesh["face_bc"])
+    dt = olts.cfl_time_steps(om.dins, mat["vp"], bench.ORDER, bench.CFL)
+    lam, cl, sp = olts.search_lambda(dt, om.nbr, bench.NCLUSTERS)
+    assert lam == lam_g and np.array_equal(cl, cl_g)
+    delta = lam * dt.min()
+    # ---- samples, one per non-empty cluster, and their balls
+    rng = np.random.default_rng(17)
+    samples = [int(rng.choice(np.nonzero(cl == l)[0])) for l in range(bench.NCLUSTERS) if np.any(cl == l)]
+    balls = [_ball(om.nbr, k, HOPS) for k in samples]
+    union = np.unique(np.concatenate(balls))
+    init = synth.random_dofs(len(union), 27, 35, seed=23)
+    g.set_dofs_subset(union, init)
+    row_of = {int(e): i for i, e in enumerate(union)}
+    src_elem = om.locate(src["x"])
+    # ---- one macro step on the GPU
+    g.advance_steps(2 ** (bench.NCLUSTERS - 1))
+    got = g.get_dofs_subset(np.array(samples))
+    for s_i, (k, ball) in enumerate(zip(samples, balls)):
+        tet = mesh["tet"][ball]
+        uv, inv = np.unique(tet, return_inverse=True)
+        sub_tet = inv.reshape(tet.shape)
+        sub_xyz = mesh["xyz"][uv]
+        bc = mesh["face_bc"][ball].copy()
+        inside = np.isin(om.nbr[ball], ball)
+        cut = (om.nbr[ball] >= 0) & ~inside
+        bc[cut] = 1                                  # cut faces: absorbing, never reach the sample
+        sm = Mesh(sub_xyz, sub_tet, bc)
+        o = Oracle(bench.ORDER, bench.NMECH, sm, mat["rho"][ball], mat["vp"][ball], mat["vs"][ball],
+                   mat["qp"][ball], mat["qs"][ball], 0.1, 5.0)
+        o.setup_clusters(bench.NCLUSTERS, bench.CFL, lam=lam, clusters=cl[ball])
+        o.delta = delta
+        o.Q = init[[row_of[int(e)] for e in ball]].copy()
+        if src_elem in set(ball.tolist()):
+            o.add_point_source(src["x"], src["m6"], src["f0"], src["t0"], src["m0"])
+        o.run_lts(2 ** (bench.NCLUSTERS - 1))
+        want = o.Q[np.searchsorted(ball, k)][None]
+        err = rel_l2_groups(got[s_i][None], want, 27)
+        for name, v in err.items():
+            assert v <= 1e-4, (k, int(cl[k]), err)

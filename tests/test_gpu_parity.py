@@ -187,3 +187,39 @@ def test_repeatable_bitwise():
         gpu.advance_steps(4)
         outs.append(gpu.get_dofs())
     assert np.array_equal(outs[0], outs[1])
+
+
+def test_single_element_mesh():
+    """Degenerate mesh: one tetrahedron, every face absorbing (a batch of 1 element)."""
+    xyz = np.array([[0.0, 0, 0], [100.0, 0, 0], [0, 120.0, 0], [0, 0, 90.0]])
+    tet = np.array([[0, 1, 2, 3]])
+    bc = np.ones((1, 4), dtype=np.int32)
+    m = dict(xyz=xyz, tet=tet, face_bc=bc, period=None)
+    mat = dict(rho=np.array([2500.0]), vp=np.array([3000.0]), vs=np.array([1700.0]),
+               qp=np.array([60.0]), qs=np.array([30.0]))
+    gpu, ora, _ = make_pair(5, 3, m, mat)
+    gpu.setup_clusters(1, 0.5)
+    d = synth.random_dofs(1, 27, 35, seed=2)
+    gpu.set_dofs(d)
+    ora.Q = d.copy()
+    gpu.advance_steps(6)
+    ora.run_gts(ora.time_step_gts(0.5), 6)
+    _check(gpu, ora)
+
+
+def test_empty_clusters():
+    """Homogeneous mesh with 4 clusters requested: the lambda search leaves clusters empty;
+    macro steps of 8 finest steps still advance every element correctly."""
+    m = synth.graded_box(3, 3, 2, 200.0, 200.0, grade=1.0, jitter=0.0, seed=1)
+    K = m["tet"].shape[0]
+    mat = synth.homogeneous(K)
+    gpu, ora, _ = make_pair(4, 0, m, mat)
+    cl, lam, sp = gpu.setup_clusters(4, 0.5)
+    ora.setup_clusters(4, 0.5)
+    assert np.array_equal(cl, ora.clusters) and len(np.unique(cl)) < 4
+    d = synth.random_dofs(K, 9, 20, seed=4)
+    gpu.set_dofs(d)
+    ora.Q = d.copy()
+    gpu.advance_steps(8)
+    ora.run_lts(8)
+    _check(gpu, ora)

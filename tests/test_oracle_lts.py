@@ -163,3 +163,43 @@ def test_fig5_walkthrough_buffers_and_reads():
         assert [g[0] for g in got] == [x[0] for x in exp]
         for (tl, buf), (_, want) in zip(got, exp):
             assert np.abs(buf - want).max() <= tol * np.abs(want).max()
+
+
+def test_dependency_cone_of_n_finest_steps():
+    """After n finest LTS steps an element depends only on data within n face hops: the
+    oracle on the (n+1)-hop ball (cut faces absorbing) reproduces the full-mesh result at
+    the ball's centre. This is the basis of the full-size sampled GPU parity test."""
+    from paper_2202_10313_gb300 import synth
+    m = synth.graded_box(6, 6, 4, 250.0, 125.0, seed=4)
+    mat = synth.random_layers(m, n_layers=3, seed=6)
+    om = Mesh(m["xyz"], m["tet"], m["face_bc"])
+    full = Solver(3, 3, om, mat["rho"], mat["vp"], mat["vs"], mat["qp"], mat["qs"])
+    full.setup_clusters(3, 0.5)
+    n = 4
+    init = np.random.default_rng(1).normal(size=full.Q.shape)
+    full.Q = init.copy()
+    full.run_lts(n)
+    for k in (100, 400, 700):
+        seen, front = {k}, [k]
+        for _ in range(n + 1):
+            nxt = []
+            for e in front:
+                for nb in om.nbr[e]:
+                    if nb >= 0 and int(nb) not in seen:
+                        seen.add(int(nb))
+                        nxt.append(int(nb))
+            front = nxt
+        ball = np.array(sorted(seen))
+        assert len(ball) < om.K
+        tet = m["tet"][ball]
+        uv, inv = np.unique(tet, return_inverse=True)
+        bc = m["face_bc"][ball].copy()
+        bc[(om.nbr[ball] >= 0) & ~np.isin(om.nbr[ball], ball)] = 1
+        sm = Mesh(m["xyz"][uv], inv.reshape(tet.shape), bc)
+        sub = Solver(3, 3, sm, mat["rho"][ball], mat["vp"][ball], mat["vs"][ball], mat["qp"][ball], mat["qs"][ball])
+        sub.setup_clusters(3, 0.5, lam=full.lam_lts, clusters=full.clusters[ball])
+        sub.delta = full.delta
+        sub.Q = init[ball].copy()
+        sub.run_lts(n)
+        got = sub.Q[np.searchsorted(ball, k)]
+        assert np.abs(got - full.Q[k]).max() <= 1e-12 * np.abs(full.Q[k]).max()
