@@ -43,17 +43,17 @@ struct Cfg {
   static constexpr int NE = (O == 3) ? 24 : (O == 4 ? 12 : 8);
   static constexpr int NT = rup(NE * B, 32);
   static constexpr int AR = 12;                      // staged elastic rows (padded, 16-byte stores)
-  // staged flux rows (9 elastic + 6 anelastic): a stride of 20 (12) floats keeps the
+  // staged Riemann states (v*, t*: 6 values) per face mode: a stride of 12 floats keeps the
   // 16-byte stores of 8 consecutive tasks on 8 distinct 4-bank groups
-  static constexpr int FR = (M > 0) ? 20 : 12;
+  static constexpr int FR = 12;
   static constexpr int XR = 9;                       // gathered neighbour rows (odd stride)
   // time kernel load balance: columns of degree <= O-3 split their k-range with a
   // helper thread that owns a degree O-1 column (which has no time-kernel product)
   static constexpr int NSPLIT = nbasis(O - 2);
   static constexpr int SPR = 28;                     // floats per staged partial (27 + pad)
   // shared memory (floats) of k_predict_local
-  static constexpr int P_K = 0;
-  static constexpr int P_FT = rup(P_K + 3 * B * BS, 4);
+  static constexpr int P_K = 0;                      // K_c[row][col] at ((row * BS + col) * 4 + c)
+  static constexpr int P_FT = rup(P_K + 4 * B * BS, 4);
   static constexpr int P_FH = rup(P_FT + 4 * B * F, 4);
   static constexpr int P_A = rup(P_FH + 4 * F * B, 4);
   static constexpr int P_FL = rup(P_A + 2 * NE * B * AR, 4);
@@ -190,14 +190,11 @@ __device__ __forceinline__ void coupling_add(float (&s)[9], const float* th, flo
   s[5] -= ymu2 * th[5];
 }
 
-// Upwind flux of a face state g (9 quantities, xyz components) in closed form.
-// fd = n[3], a[4], b[4]: v*_n = a0 v_n + a1 t_n, t*_n = a2 t_n + a3 v_n (P pair) and the
-// same with b for the tangential (S) parts, t = sigma n; coefficients already carry the
-// -2|S_i|/|det J| scaling. Flux rows: stresses -(lam (n.v*) I + mu (n v*^T + v* n^T)),
-// velocities -t*/rho, memory variables -sym(n v*^T) (omega_l factored out).
-template <int M>
-__device__ __forceinline__ void face_flux(const float (&g)[9], const float* fd, float lam, float mu, float rinv,
-                                          float (&fl)[16]) {
+// Upwind (Godunov) interface state of a face state g (9 quantities, xyz components) in
+// closed form. fd = n[3], a[4], b[4]: v*_n = a0 v_n + a1 t_n, t*_n = a2 t_n + a3 v_n (P pair)
+// and the same with b for the tangential (S) parts, t = sigma n; the coefficients carry the
+// -2|S_i|/|det J| scaling. w = (v*, t*).
+__device__ __forceinline__ void riemann_state(const float (&g)[9], const float* fd, float (&w)[6]) {
   const float nx = fd[0], ny = fd[1], nz = fd[2];
   const float tx = g[0] * nx + g[3] * ny + g[5] * nz;
   const float ty = g[3] * nx + g[1] * ny + g[4] * nz;
@@ -208,44 +205,74 @@ __device__ __forceinline__ void face_flux(const float (&g)[9], const float* fd, 
   const float vTx = g[6] - vn * nx, vTy = g[7] - vn * ny, vTz = g[8] - vn * nz;
   const float vsn = fd[3] * vn + fd[4] * tn;
   const float tsn = fd[5] * tn + fd[6] * vn;
-  const float vsx = vsn * nx + fd[7] * vTx + fd[8] * tTx;
-  const float vsy = vsn * ny + fd[7] * vTy + fd[8] * tTy;
-  const float vsz = vsn * nz + fd[7] * vTz + fd[8] * tTz;
-  const float tsx = tsn * nx + fd[9] * tTx + fd[10] * vTx;
-  const float tsy = tsn * ny + fd[9] * tTy + fd[10] * vTy;
-  const float tsz = tsn * nz + fd[9] * tTz + fd[10] * vTz;
-  const float nv = nx * vsx + ny * vsy + nz * vsz;
-  const float exx = nx * vsx, eyy = ny * vsy, ezz = nz * vsz;
-  const float exy = nx * vsy + ny * vsx, eyz = ny * vsz + nz * vsy, exz = nx * vsz + nz * vsx;
-  fl[0] = -(lam * nv + 2.f * mu * exx);
-  fl[1] = -(lam * nv + 2.f * mu * eyy);
-  fl[2] = -(lam * nv + 2.f * mu * ezz);
-  fl[3] = -mu * exy;
-  fl[4] = -mu * eyz;
-  fl[5] = -mu * exz;
-  fl[6] = -rinv * tsx;
-  fl[7] = -rinv * tsy;
-  fl[8] = -rinv * tsz;
-  if constexpr (M > 0) {
-    fl[9] = -exx;
-    fl[10] = -eyy;
-    fl[11] = -ezz;
-    fl[12] = -0.5f * exy;
-    fl[13] = -0.5f * eyz;
-    fl[14] = -0.5f * exz;
-    fl[15] = 0.f;
-  } else {
-    fl[9] = fl[10] = fl[11] = 0.f;
-    fl[12] = fl[13] = fl[14] = fl[15] = 0.f;
+  w[0] = vsn * nx + fd[7] * vTx + fd[8] * tTx;
+  w[1] = vsn * ny + fd[7] * vTy + fd[8] * tTy;
+  w[2] = vsn * nz + fd[7] * vTz + fd[8] * tTz;
+  w[3] = tsn * nx + fd[9] * tTx + fd[10] * vTx;
+  w[4] = tsn * ny + fd[9] * tTy + fd[10] * vTy;
+  w[5] = tsn * nz + fd[9] * tTz + fd[10] * vTz;
+}
+
+__device__ __forceinline__ void store_state(float* dst, const float (&w)[6]) {
+  st4(dst, w[0], w[1], w[2], w[3]);
+  *reinterpret_cast<float2*>(dst + 4) = make_float2(w[4], w[5]);
+}
+
+// Flux rows of a projected interface state W = (v*, t*) on a face with normal n, added to S:
+// stresses -(lam (n.v*) I + mu (n v*^T + v* n^T)), velocities -t*/rho and, for M > 0, the
+// memory-variable rows -sym(n v*^T) (omega_l factored out) in S[9..14]. The flux is linear
+// in (v*, t*), so projecting these 6 rows through F^ and forming the flux afterwards equals
+// projecting the 15 flux rows.
+template <int NS>
+__device__ __forceinline__ void flux_rows_add(const float (&W)[6], const float* n, float lam, float mu, float rinv,
+                                              float (&S)[NS]) {
+  const float nx = n[0], ny = n[1], nz = n[2];
+  const float nv = nx * W[0] + ny * W[1] + nz * W[2];
+  const float exx = nx * W[0], eyy = ny * W[1], ezz = nz * W[2];
+  const float exy = nx * W[1] + ny * W[0], eyz = ny * W[2] + nz * W[1], exz = nx * W[2] + nz * W[0];
+  const float ln = lam * nv, m2 = 2.f * mu;
+  S[0] -= ln + m2 * exx;
+  S[1] -= ln + m2 * eyy;
+  S[2] -= ln + m2 * ezz;
+  S[3] -= mu * exy;
+  S[4] -= mu * eyz;
+  S[5] -= mu * exz;
+  S[6] -= rinv * W[3];
+  S[7] -= rinv * W[4];
+  S[8] -= rinv * W[5];
+  if constexpr (NS > 9) {
+    S[9] -= exx;
+    S[10] -= eyy;
+    S[11] -= ezz;
+    S[12] -= 0.5f * exy;
+    S[13] -= 0.5f * eyz;
+    S[14] -= 0.5f * exz;
   }
 }
 
-template <int FR>
-__device__ __forceinline__ void store_flux(float* dst, const float (&fl)[16]) {
-  st4(dst, fl[0], fl[1], fl[2], fl[3]);
-  st4(dst + 4, fl[4], fl[5], fl[6], fl[7]);
-  st4(dst + 8, fl[8], fl[9], fl[10], fl[11]);
-  if constexpr (FR >= 16) st4(dst + 12, fl[12], fl[13], fl[14], fl[15]);
+// S[r][b] += sum over faces i and face modes f (deg f <= deg b) of the flux of the staged
+// interface states projected by F^_i[f][b].
+template <int NS, int F, int B, int FR>
+__device__ __forceinline__ void project_faces(const float* Fl, const float* sFh, const float* nrm, int nstride,
+                                              float lam, float mu, float rinv, int fmax, int b, float (&S)[NS]) {
+#pragma unroll 1
+  for (int i = 0; i < 4; ++i) {
+    float W[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 2
+    for (int f = 0; f < fmax; ++f) {
+      const float* fl = Fl + (i * F + f) * FR;
+      const float w = sFh[(i * F + f) * B + b];
+      const float4 y0 = *reinterpret_cast<const float4*>(fl);
+      const float2 y1 = *reinterpret_cast<const float2*>(fl + 4);
+      W[0] = fmaf(y0.x, w, W[0]);
+      W[1] = fmaf(y0.y, w, W[1]);
+      W[2] = fmaf(y0.z, w, W[2]);
+      W[3] = fmaf(y0.w, w, W[3]);
+      W[4] = fmaf(y1.x, w, W[4]);
+      W[5] = fmaf(y1.y, w, W[5]);
+    }
+    flux_rows_add<NS>(W, nrm + nstride * i, lam, mu, rinv, S);
+  }
 }
 
 // ------------------------------------------------------------------ predict + local
@@ -266,9 +293,9 @@ __global__ void __maxnreg__(112) k_predict_local(DevOps ops, DevState st, PhaseA
   int* sMeta = reinterpret_cast<int*>(smem + C::P_META);
   const int tid = threadIdx.x;
 
-  for (int i = tid; i < 3 * B * B; i += NT) {
-    const int c = i / (B * B), r = (i / B) % B, col = i % B;
-    sK[(c * B + r) * BS + col] = ops.K[i];
+  for (int i = tid; i < 4 * B * BS; i += NT) {
+    const int c = i % 4, rc = i / 4, r = rc / BS, col = rc % BS;
+    sK[i] = (c < 3 && col < B) ? ops.K[(c * B + r) * B + col] : 0.f;
   }
   for (int i = tid; i < 4 * B * F; i += NT) sFt[i] = ops.Ft[i];
   for (int i = tid; i < 4 * F * B; i += NT) sFh[i] = ops.Fh[i];
@@ -302,32 +329,33 @@ __global__ void __maxnreg__(112) k_predict_local(DevOps ops, DevState st, PhaseA
   for (int batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
     const int e0 = ph.begin + batch * NE;
     __syncthreads();
+    const int g = e0 + e;
+    const bool valid = act && g < ph.end;
+    // DOF loads are issued together with the element tables, before the barrier
+    float T[NQ], Th[9], Da[NA > 0 ? NA : 1];
+    float v[12];
+#pragma unroll
+    for (int r = 0; r < 12; ++r) v[r] = 0.f;
+    if (valid) {
+      const float* q = st.Q + (size_t)g * QS + b;
+#pragma unroll
+      for (int r = 0; r < 9; ++r) v[r] = q[r * B];
+#pragma unroll
+      for (int r = 0; r < NA; ++r) Da[r] = q[(9 + r) * B];
+    } else {
+#pragma unroll
+      for (int r = 0; r < NA; ++r) Da[r] = 0.f;
+    }
     for (int i = tid; i < NE * ED; i += NT) {
       const int ee = i / ED, gg = e0 + ee;
       sE[i] = (gg < ph.end) ? st.edata[(size_t)gg * ED + (i % ED)] : 0.f;
     }
     if (tid < NE) sMeta[tid] = (e0 + tid < ph.end) ? st.meta[e0 + tid] : 0;
     __syncthreads();
-    const int g = e0 + e;
-    const bool valid = act && g < ph.end;
     const float* ed = sE + es * ED;
     const int meta = act ? sMeta[es] : 0;
     const int cl = meta & 0xff;
-    float T[NQ], Th[9], Da[NA > 0 ? NA : 1];
     {
-      float v[12];
-#pragma unroll
-      for (int r = 0; r < 12; ++r) v[r] = 0.f;
-      if (valid) {
-        const float* q = st.Q + (size_t)g * QS + b;
-#pragma unroll
-        for (int r = 0; r < 9; ++r) v[r] = q[r * B];
-#pragma unroll
-        for (int r = 0; r < NA; ++r) Da[r] = q[(9 + r) * B];
-      } else {
-#pragma unroll
-        for (int r = 0; r < NA; ++r) Da[r] = 0.f;
-      }
 #pragma unroll
       for (int r = 0; r < 9; ++r) {
         T[r] = ph.coef[cl][0] * v[r];
@@ -354,19 +382,19 @@ __global__ void __maxnreg__(112) k_predict_local(DevOps ops, DevState st, PhaseA
         for (int r = 0; r < 9; ++r) Y[c][r] = 0.f;
       {
         const float* Ab = sA + ((buf * NE + es) * B) * AR;
-        const float* K0 = sK + ck_col * BS;
+        const float* K0 = sK + ck_col * BS * 4;
 #pragma unroll 2
         for (int k = ck_k0; k < ck_k1; ++k) {
           const float4 x0 = *reinterpret_cast<const float4*>(Ab + k * AR);
           const float4 x1 = *reinterpret_cast<const float4*>(Ab + k * AR + 4);
           const float x8 = Ab[k * AR + 8];
+          const float4 k4 = *reinterpret_cast<const float4*>(K0 + 4 * k);
           const float xs[9] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w, x8};
+          const float kc[3] = {k4.x, k4.y, k4.z};
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const float kc = K0[c * B * BS + k];
+          for (int c = 0; c < 3; ++c)
 #pragma unroll
-            for (int r = 0; r < 9; ++r) Y[c][r] = fmaf(xs[r], kc, Y[c][r]);
-          }
+            for (int r = 0; r < 9; ++r) Y[c][r] = fmaf(xs[r], kc[c], Y[c][r]);
         }
       }
       if (helper) {
@@ -470,13 +498,13 @@ __global__ void __maxnreg__(112) k_predict_local(DevOps ops, DevState st, PhaseA
           const float4 x0 = *reinterpret_cast<const float4*>(Ab + k * AR);
           const float4 x1 = *reinterpret_cast<const float4*>(Ab + k * AR + 4);
           const float x8 = Ab[k * AR + 8];
+          const float4 k4 = *reinterpret_cast<const float4*>(sK + (k * BS + b) * 4);
           const float xs[9] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w, x8};
+          const float kc[3] = {k4.x, k4.y, k4.z};
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const float kc = sK[(c * B + k) * BS + b];
+          for (int c = 0; c < 3; ++c)
 #pragma unroll
-            for (int r = 0; r < 9; ++r) Z[c][r] = fmaf(xs[r], kc, Z[c][r]);
-          }
+            for (int r = 0; r < 9; ++r) Z[c][r] = fmaf(xs[r], kc[c], Z[c][r]);
         }
       }
       if (valid) {
@@ -522,10 +550,9 @@ __global__ void __maxnreg__(112) k_predict_local(DevOps ops, DevState st, PhaseA
         gq[7] = fmaf(x1.w, w, gq[7]);
         gq[8] = fmaf(x8, w, gq[8]);
       }
-      const float* ede = sE + fe * ED;
-      float fl[16];
-      face_flux<M>(gq, ede + 20 + 11 * fi, ede[9], ede[10], ede[11], fl);
-      store_flux<FR>(sFl + (fe * 4 * F + fi * F + ff) * FR, fl);
+      float w6[6];
+      riemann_state(gq, sE + fe * ED + 20 + 11 * fi, w6);
+      store_state(sFl + (fe * 4 * F + fi * F + ff) * FR, w6);
     }
     __syncthreads();
     if (valid) {
@@ -533,36 +560,7 @@ __global__ void __maxnreg__(112) k_predict_local(DevOps ops, DevState st, PhaseA
       float S[NS];
 #pragma unroll
       for (int r = 0; r < NS; ++r) S[r] = 0.f;
-      const float* Fl = sFl + e * 4 * F * FR;
-#pragma unroll 1
-      for (int i = 0; i < 4; ++i) {
-#pragma unroll 2
-        for (int f = 0; f < fmax; ++f) {
-          const float* fl = Fl + (i * F + f) * FR;
-          const float w = sFh[(i * F + f) * B + b];
-          const float4 y0 = *reinterpret_cast<const float4*>(fl);
-          const float4 y1 = *reinterpret_cast<const float4*>(fl + 4);
-          const float4 y2 = *reinterpret_cast<const float4*>(fl + 8);
-          S[0] = fmaf(y0.x, w, S[0]);
-          S[1] = fmaf(y0.y, w, S[1]);
-          S[2] = fmaf(y0.z, w, S[2]);
-          S[3] = fmaf(y0.w, w, S[3]);
-          S[4] = fmaf(y1.x, w, S[4]);
-          S[5] = fmaf(y1.y, w, S[5]);
-          S[6] = fmaf(y1.z, w, S[6]);
-          S[7] = fmaf(y1.w, w, S[7]);
-          S[8] = fmaf(y2.x, w, S[8]);
-          if constexpr (M > 0) {
-            const float4 y3 = *reinterpret_cast<const float4*>(fl + 12);
-            S[NS - 6] = fmaf(y2.y, w, S[NS - 6]);
-            S[NS - 5] = fmaf(y2.z, w, S[NS - 5]);
-            S[NS - 4] = fmaf(y2.w, w, S[NS - 4]);
-            S[NS - 3] = fmaf(y3.x, w, S[NS - 3]);
-            S[NS - 2] = fmaf(y3.y, w, S[NS - 2]);
-            S[NS - 1] = fmaf(y3.z, w, S[NS - 1]);
-          }
-        }
-      }
+      project_faces<NS, F, B, FR>(sFl + e * 4 * F * FR, sFh, ed + 20, 11, ed[9], ed[10], ed[11], fmax, b, S);
       float* q = st.Q + (size_t)g * QS + b;
 #pragma unroll
       for (int r = 0; r < 9; ++r) q[r * B] = acc[r] + S[r];
@@ -664,10 +662,9 @@ __global__ void __launch_bounds__(Cfg<O, M>::NT, 2) k_neighbour(DevOps ops, DevS
 #pragma unroll
         for (int r = 0; r < 9; ++r) gq[r] = fmaf(X[k * XR + r], w, gq[r]);
       }
-      const float* nd = sD + ee * ND;
-      float fl[16];
-      face_flux<M>(gq, nd + 4 + 11 * i, nd[0], nd[1], nd[2], fl);
-      store_flux<FR>(sFl + (ee * 4 * F + i * F + f) * FR, fl);
+      float w6[6];
+      riemann_state(gq, sD + ee * ND + 4 + 11 * i, w6);
+      store_state(sFl + (ee * 4 * F + i * F + f) * FR, w6);
     }
     __syncthreads();
     if (valid) {
@@ -675,17 +672,8 @@ __global__ void __launch_bounds__(Cfg<O, M>::NT, 2) k_neighbour(DevOps ops, DevS
       float S[NS];
 #pragma unroll
       for (int r = 0; r < NS; ++r) S[r] = 0.f;
-      const float* Fl = sFl + e * 4 * F * FR;
-#pragma unroll 1
-      for (int i = 0; i < 4; ++i) {
-#pragma unroll 2
-        for (int f = 0; f < fmax; ++f) {
-          const float* fl = Fl + (i * F + f) * FR;
-          const float w = sFh[(i * F + f) * B + b];
-#pragma unroll
-          for (int r = 0; r < NS; ++r) S[r] = fmaf(fl[r], w, S[r]);
-        }
-      }
+      const float* nd = sD + e * ND;
+      project_faces<NS, F, B, FR>(sFl + e * 4 * F * FR, sFh, nd + 4, 11, nd[0], nd[1], nd[2], fmax, b, S);
       float* q = st.Q + (size_t)g * QS;
 #pragma unroll
       for (int r = 0; r < 9; ++r) q[r * B + b] += S[r];

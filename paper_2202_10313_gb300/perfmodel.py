@@ -32,23 +32,28 @@ def flops_predict(o, m):
     star = 2 * 54 + 20                              # W_d combinations + Hooke / momentum
     ck_epi = star + m * 24 + m * 12 + 2 * (NQ + 9)  # coupling, relaxation, Taylor sums
     vol_epi = star + m * 24 + m * 12 + NQ
-    surf_g = 2 * 9 * 4 * sum(B - nbasis(p) for p in fdeg)
-    flux = 4 * F * 80
-    ns = 15 if m else 9
-    surf_h = 2 * ns * 4 * sum(nface(p + 1) for p in degs)
+    surf_g, flux, surf_h = _surface(o, m)
     upd = B * (NQ + 2 * 6 * m)
     return (o - 1) * (2 * ck_gemm + B * ck_epi) + 2 * vol_gemm + B * vol_epi + surf_g + flux + surf_h + upd
 
 
-def flops_neighbour(o, m):
-    """Flops of k_neighbour per element (neighbour surface kernel)."""
-    B, F, NQ = nbasis(o), nface(o), 9 + 6 * m
+def _surface(o, m):
+    """Face traces (9 rows x F~ or F-), closed-form interface states (v*, t*), their 6-row
+    projection through F^ and the flux rows rebuilt per face and column."""
+    B, F = nbasis(o), nface(o)
     degs = _col_degrees(o)
     fdeg = [p for p in range(o) for _ in range(p + 1)]
     surf_g = 2 * 9 * 4 * sum(B - nbasis(p) for p in fdeg)
-    flux = 4 * F * 80
-    ns = 15 if m else 9
-    surf_h = 2 * ns * 4 * sum(nface(p + 1) for p in degs)
+    flux = 4 * F * 50
+    rows = 30 + (18 if m else 0)
+    surf_h = 2 * 6 * 4 * sum(nface(p + 1) for p in degs) + B * 4 * rows
+    return surf_g, flux, surf_h
+
+
+def flops_neighbour(o, m):
+    """Flops of k_neighbour per element (neighbour surface kernel)."""
+    B, NQ = nbasis(o), 9 + 6 * m
+    surf_g, flux, surf_h = _surface(o, m)
     return surf_g + flux + surf_h + B * (NQ + 2 * 6 * m)
 
 
