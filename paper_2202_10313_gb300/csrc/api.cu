@@ -529,7 +529,7 @@ void advance_steps(lts_solver* h, int64_t n_finest, cudaStream_t stream) {
     }
     const int nelem = pa.end - pa.begin;
     if (nelem <= 0) continue;
-    const int nb = (nelem + X.NE - 1) / X.NE;
+    const int nb = (nelem + (ph.kind == 0 ? X.NEN : X.NE) - 1) / (ph.kind == 0 ? X.NEN : X.NE);
     if (ph.kind == 1 && ph.item_end > ph.item_beg) {
       X.receivers(h->dops, h->dst.Q, h->dst.edata, h->d_recv_phi, h->d_ritems + ph.item_beg, h->d_seis,
                   base.omega, ph.item_end - ph.item_beg, stream);

@@ -40,7 +40,9 @@ struct Cfg {
   static constexpr int BS = (B % 2) ? B : B + 1;     // odd row stride: conflict-free rows and columns
   static constexpr int QS = rup(NQ * B, 4);          // element stride of Q
   static constexpr int BUFS = rup(9 * B, 4);         // element stride of B1/B2/B3
-  static constexpr int NE = (O == 3) ? 24 : (O == 4 ? 12 : 8);
+  // elements per CTA: 7 x 35 columns = 8 warps at order 5, so two CTAs fit with up to
+  // 128 registers per thread (registers are allocated per SM sub-partition)
+  static constexpr int NE = (O == 3) ? 24 : (O == 4 ? 12 : 7);
   static constexpr int NT = rup(NE * B, 32);
   static constexpr int AR = 12;                      // staged elastic rows (padded, 16-byte stores)
   // staged Riemann states (v*, t*: 6 values) per face mode: a stride of 12 floats keeps the
@@ -61,14 +63,17 @@ struct Cfg {
   static constexpr int P_SP = rup(P_E + NE * ED, 4);
   static constexpr int P_META = rup(P_SP + NE * NSPLIT * SPR, 4);
   static constexpr int P_TOTAL = rup(P_META + NE, 4);
-  // shared memory (floats) of k_neighbour
+  // k_neighbour: its own batch size (kept equal to NE: a third CTA per SM leaves too
+  // little L1 for the neighbour-buffer gathers)
+  static constexpr int NEN = (O == 5) ? 8 : NE;
+  static constexpr int NTN = rup(NEN * B, 32);
   static constexpr int N_FB = 0;
   static constexpr int N_FH = rup(N_FB + 12 * B * F, 4);
   static constexpr int N_X = rup(N_FH + 4 * F * B, 4);
-  static constexpr int N_FL = rup(N_X + NE * 4 * B * XR, 4);
-  static constexpr int N_D = rup(N_FL + NE * 4 * F * FR, 4);
-  static constexpr int N_I = rup(N_D + NE * ND, 4);        // ints: nbr[4], code[4], meta per element
-  static constexpr int N_TOTAL = rup(N_I + NE * 9, 4);
+  static constexpr int N_FL = rup(N_X + NEN * 4 * B * XR, 4);
+  static constexpr int N_D = rup(N_FL + NEN * 4 * F * FR, 4);
+  static constexpr int N_I = rup(N_D + NEN * ND, 4);       // ints: nbr[4], code[4], meta per element
+  static constexpr int N_TOTAL = rup(N_I + NEN * 9, 4);
 };
 
 struct DevOps {
@@ -277,7 +282,7 @@ __device__ __forceinline__ void project_faces(const float* Fl, const float* sFh,
 
 // ------------------------------------------------------------------ predict + local
 template <int O, int M>
-__global__ void __maxnreg__(112) k_predict_local(DevOps ops, DevState st, PhaseArgs ph) {
+__global__ void __launch_bounds__(Cfg<O, M>::NT, 2) k_predict_local(DevOps ops, DevState st, PhaseArgs ph) {
   using C = Cfg<O, M>;
   constexpr int B = C::B, F = C::F, NE = C::NE, NT = C::NT, BS = C::BS, AR = C::AR, FR = C::FR;
   constexpr int NQ = C::NQ, NA = C::NA, QS = C::QS, BUFS = C::BUFS, NSPLIT = C::NSPLIT, SPR = C::SPR;
@@ -576,9 +581,9 @@ __global__ void __maxnreg__(112) k_predict_local(DevOps ops, DevState st, PhaseA
 
 // ------------------------------------------------------------------ neighbour
 template <int O, int M>
-__global__ void __launch_bounds__(Cfg<O, M>::NT, 2) k_neighbour(DevOps ops, DevState st, PhaseArgs ph) {
+__global__ void __launch_bounds__(Cfg<O, M>::NTN, 2) k_neighbour(DevOps ops, DevState st, PhaseArgs ph) {
   using C = Cfg<O, M>;
-  constexpr int B = C::B, F = C::F, NE = C::NE, NT = C::NT, FR = C::FR, XR = C::XR;
+  constexpr int B = C::B, F = C::F, NE = C::NEN, NT = C::NTN, FR = C::FR, XR = C::XR;
   constexpr int QS = C::QS, BUFS = C::BUFS;
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
@@ -644,7 +649,7 @@ __global__ void __launch_bounds__(Cfg<O, M>::NT, 2) k_neighbour(DevOps ops, DevS
       }
     }
     __syncthreads();
-    // ---- H_i = X F-_{j,h}, closed-form flux with the neighbour's coefficients
+    // ---- H_i = X F-_{j,h}, closed-form interface states with the neighbour's coefficients
 #pragma unroll 1
     for (int t = tid; t < NE * 4 * F; t += NT) {
       int ee, i, f, pf;

@@ -7,7 +7,7 @@
 namespace ltsdev {
 
 struct Launchers {
-  int B, F, NQ, QS, BUFS, NE, NT;
+  int B, F, NQ, QS, BUFS, NE, NT, NEN;
   size_t smem_predict, smem_neighbour;
   int blocks_predict, blocks_neighbour;      // resident CTAs per SM (filled by init)
   cudaError_t (*init)(Launchers*);
@@ -30,14 +30,14 @@ struct Impl {
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L->blocks_predict, k_predict_local<O, M>, C::NT, L->smem_predict);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L->blocks_neighbour, k_neighbour<O, M>, C::NT,
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L->blocks_neighbour, k_neighbour<O, M>, C::NTN,
                                                          L->smem_neighbour);
   }
   static void predict(const DevOps& o, const DevState& s, const PhaseArgs& p, int grid, cudaStream_t st) {
     k_predict_local<O, M><<<grid, C::NT, C::P_TOTAL * sizeof(float), st>>>(o, s, p);
   }
   static void neighbour(const DevOps& o, const DevState& s, const PhaseArgs& p, int grid, cudaStream_t st) {
-    k_neighbour<O, M><<<grid, C::NT, C::N_TOTAL * sizeof(float), st>>>(o, s, p);
+    k_neighbour<O, M><<<grid, C::NTN, C::N_TOTAL * sizeof(float), st>>>(o, s, p);
   }
   static void receivers(const DevOps& o, const float* Q, const float* ed, const float* phi, const RecvItem* it,
                         float* out, const float* om, int n, cudaStream_t st) {
@@ -58,6 +58,7 @@ struct Impl {
     L.BUFS = C::BUFS;
     L.NE = C::NE;
     L.NT = C::NT;
+    L.NEN = C::NEN;
     L.smem_predict = C::P_TOTAL * sizeof(float);
     L.smem_neighbour = C::N_TOTAL * sizeof(float);
     L.init = &init;
