@@ -674,19 +674,24 @@ __global__ void __launch_bounds__(Cfg<O, M>::NTN, 2) k_neighbour(DevOps ops, Dev
     __syncthreads();
     if (valid) {
       constexpr int NS = (M > 0) ? 15 : 9;
+      constexpr int NQ = C::NQ;
+      // the DOF loads are issued first so their latency overlaps the F^ product
+      float* q = st.Q + (size_t)g * QS + b;
+      float qv[NQ];
+#pragma unroll
+      for (int r = 0; r < NQ; ++r) qv[r] = q[r * B];
       float S[NS];
 #pragma unroll
       for (int r = 0; r < NS; ++r) S[r] = 0.f;
       const float* nd = sD + e * ND;
       project_faces<NS, F, B, FR>(sFl + e * 4 * F * FR, sFh, nd + 4, 11, nd[0], nd[1], nd[2], fmax, b, S);
-      float* q = st.Q + (size_t)g * QS;
 #pragma unroll
-      for (int r = 0; r < 9; ++r) q[r * B + b] += S[r];
+      for (int r = 0; r < 9; ++r) q[r * B] = qv[r] + S[r];
       if constexpr (M > 0) {
 #pragma unroll
         for (int l = 0; l < M; ++l)
 #pragma unroll
-          for (int r = 0; r < 6; ++r) q[(9 + 6 * l + r) * B + b] += ph.omega[l] * S[NS - 6 + r];
+          for (int r = 0; r < 6; ++r) q[(9 + 6 * l + r) * B] = qv[9 + 6 * l + r] + ph.omega[l] * S[NS - 6 + r];
       }
     }
   }
