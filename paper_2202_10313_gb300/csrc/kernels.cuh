@@ -263,7 +263,7 @@ __device__ __forceinline__ void project_faces(const float* Fl, const float* sFh,
 #pragma unroll 1
   for (int i = 0; i < 4; ++i) {
     float W[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll 2
+#pragma unroll 4
     for (int f = 0; f < fmax; ++f) {
       const float* fl = Fl + (i * F + f) * FR;
       const float w = sFh[(i * F + f) * B + b];
@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(Cfg<O, M>::NT, 2) k_predict_local(DevOps ops, 
       {
         const float* Ab = sA + ((buf * NE + es) * B) * AR;
         const float* K0 = sK + ck_col * BS * 4;
-#pragma unroll 2
+#pragma unroll 4
         for (int k = ck_k0; k < ck_k1; ++k) {
           const float4 x0 = *reinterpret_cast<const float4*>(Ab + k * AR);
           const float4 x1 = *reinterpret_cast<const float4*>(Ab + k * AR + 4);
@@ -498,7 +498,7 @@ __global__ void __launch_bounds__(Cfg<O, M>::NT, 2) k_predict_local(DevOps ops, 
         for (int r = 0; r < 9; ++r) Z[c][r] = 0.f;
       if (act) {
         const float* Ab = sA + ((buf * NE + e) * B) * AR;
-#pragma unroll 2
+#pragma unroll 4
         for (int k = 0; k < ke_vol; ++k) {
           const float4 x0 = *reinterpret_cast<const float4*>(Ab + k * AR);
           const float4 x1 = *reinterpret_cast<const float4*>(Ab + k * AR + 4);
@@ -539,7 +539,7 @@ __global__ void __launch_bounds__(Cfg<O, M>::NT, 2) k_predict_local(DevOps ops, 
       for (int r = 0; r < 9; ++r) gq[r] = 0.f;
       const float* Ab = sA + ((buf * NE + fe) * B) * AR;
       const float* Fi = sFt + fi * B * F + ff;
-#pragma unroll 2
+#pragma unroll 4
       for (int k = nbasis(fpf); k < B; ++k) {
         const float4 x0 = *reinterpret_cast<const float4*>(Ab + k * AR);
         const float4 x1 = *reinterpret_cast<const float4*>(Ab + k * AR + 4);
@@ -661,7 +661,7 @@ __global__ void __launch_bounds__(Cfg<O, M>::NTN, 2) k_neighbour(DevOps ops, Dev
       for (int r = 0; r < 9; ++r) gq[r] = 0.f;
       const float* X = sX + (ee * 4 + i) * B * XR;
       const float* Fm = sFb + jh * B * F + f;
-#pragma unroll 2
+#pragma unroll 4
       for (int k = nbasis(pf); k < B; ++k) {
         const float w = Fm[k * F];
 #pragma unroll
