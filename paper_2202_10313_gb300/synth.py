@@ -276,3 +276,57 @@ def polynomial_field(n_q, degree, scale=1.0, seed=SEED_MATERIAL):
         return out
 
     return fn
+
+
+def layer_over_halfspace(nx, ny, h, layer=1000.0, hz_layer=125.0, nz_below=8, grade=2.0, jitter=0.15,
+                         seed=SEED_MESH):
+    """Layer-over-half-space box in the spirit of the LOH.3 benchmark: vertical spacing
+    hz_layer through the top `layer` metres (so an element face lies on the interface),
+    then nz_below cells growing geometrically by `grade` overall; horizontal spacing h.
+    Free surface at z = 0, absorbing elsewhere. Returns the mesh dict with 'depth'."""
+    n_layer = int(round(layer / hz_layer))
+    r = grade ** (1.0 / max(nz_below - 1, 1))
+    below = hz_layer * r ** np.arange(1, nz_below + 1)
+    hz = np.concatenate([np.full(n_layer, hz_layer), below])
+    depth_lines = np.concatenate([[0.0], np.cumsum(hz)])
+    zs = -depth_lines[::-1]
+    nz = len(hz)
+    rng = np.random.default_rng(seed)
+    xs = h * np.arange(nx + 1, dtype=float)
+    ys = h * np.arange(ny + 1, dtype=float)
+    xyz = _grid_vertices(xs, ys, zs)
+    tet = _kuhn_tets(nx, ny, nz)
+    nv = xyz.shape[0]
+    vi = np.arange(nv) % (nx + 1)
+    vj = (np.arange(nv) // (nx + 1)) % (ny + 1)
+    vk = np.arange(nv) // ((nx + 1) * (ny + 1))
+    dz_lines = np.diff(zs)
+    sz = np.minimum(dz_lines[np.clip(vk - 1, 0, nz - 1)], dz_lines[np.clip(vk, 0, nz - 1)])
+    # the interface plane (and the surface / bottom) keeps its depth: no vertical jitter there
+    on_interface = np.isclose(xyz[:, 2], -layer)
+    free = np.stack([(vi > 0) & (vi < nx), (vj > 0) & (vj < ny), (vk > 0) & (vk < nz) & ~on_interface], axis=1)
+    spacing = np.stack([np.full(nv, h), np.full(nv, h), sz], axis=1)
+    amp = jitter * np.ones(nv)
+    base = xyz.copy()
+    draw = rng.uniform(-1.0, 1.0, size=(nv, 3))
+    for _ in range(20):
+        xyz = base + draw * (amp[:, None] * spacing) * free
+        x = xyz[tet]
+        vol = np.einsum("ki,ki->k", x[:, 1] - x[:, 0], np.cross(x[:, 2] - x[:, 0], x[:, 3] - x[:, 0]))
+        bad = vol <= 0.0
+        if not np.any(bad):
+            break
+        amp[np.unique(tet[bad].ravel())] *= 0.5
+    else:
+        raise RuntimeError("could not untangle jittered mesh")
+    bc = _boundary_codes(tet, nx, ny, nz, [1, 1, 1, 1, 1, 2])
+    return dict(xyz=xyz, tet=tet, face_bc=bc, period=None, depth=float(depth_lines[-1]))
+
+
+def loh3_materials(mesh, layer=1000.0):
+    """LOH.3 model parameters (Sec. VII-B): layer vs 2000, vp 4000, rho 2600, Qs 40, Qp 120;
+    half-space vs 3464, vp 6000, rho 2700, Qs 69.3, Qp 155.9 (by element centroid depth)."""
+    in_layer = -centroids(mesh)[:, 2] < layer
+    return dict(rho=np.where(in_layer, 2600.0, 2700.0), vp=np.where(in_layer, 4000.0, 6000.0),
+                vs=np.where(in_layer, 2000.0, 3464.0), qp=np.where(in_layer, 120.0, 155.9),
+                qs=np.where(in_layer, 40.0, 69.3))
