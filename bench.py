@@ -9,6 +9,11 @@ completes its 2^(4-l) steps). The metric is element updates per second.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+--fused F runs the fused-simulation workload instead: 64 x 64 x 40 hexes x 6 = 983,040
+tetrahedra of the same generator, F simulations (a multiple of 4), each driven by its own
+moment-tensor Ricker source (seeded random positions and orientations, f0 in [1, 4] Hz);
+the metric is then simulation element updates per second.
+
 --impl reference times the FP64 CPU oracle (the only reference there is) on the box's
 host cores on a bounded sample of the same workload.
 """
@@ -29,6 +34,7 @@ METRIC = "element-updates/s and % HBM roofline, order-5 anelastic LTS, 1 GB300 (
 UNIT = "element-updates/s"
 ORDER, NMECH, NCLUSTERS, CFL = 5, 3, 5, 0.5
 FULL = dict(nx=96, ny=96, nz=38, h=250.0, hz=125.0)
+FUSED_FULL = dict(nx=64, ny=64, nz=40, h=250.0, hz=125.0)
 SAMPLE = dict(nx=12, ny=12, nz=5, h=250.0, hz=125.0)   # bounded CPU sample of the same generator
 
 
@@ -162,24 +168,32 @@ def run_reference(args, rank, world):
 
 def run_ours(args, rank, world, local_rank):
     import torch
-    from paper_2202_10313_gb300 import binding, build, perfmodel
+    from paper_2202_10313_gb300 import binding, build, perfmodel, synth
     torch.cuda.set_device(local_rank)
     build.build()
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    cfg = FULL
+    F = max(1, args.fused)
+    cfg = FUSED_FULL if F > 1 else FULL
     if args.small:
         cfg = dict(nx=24, ny=24, nz=10, h=250.0, hz=125.0)
     elif args.medium:
         cfg = dict(nx=48, ny=48, nz=19, h=250.0, hz=125.0)
     mesh, mat, src, recs = make_workload(**cfg)
     K = mesh["tet"].shape[0]
-    s = binding.Solver(ORDER, NMECH, device=local_rank)
+    s = binding.Solver(ORDER, NMECH, device=local_rank, n_fused=F)
     s.set_mesh(mesh["xyz"], mesh["tet"], mesh["face_bc"])
     s.set_material(mat["rho"], mat["vp"], mat["vs"], mat["qp"], mat["qs"], 0.1, 5.0)
-    s.add_point_source(src["x"], src["m6"], src["f0"], src["t0"], src["m0"])
+    if F == 1:
+        s.add_point_source(src["x"], src["m6"], src["f0"], src["t0"], src["m0"])
+    else:
+        lx, ly, depth = cfg["nx"] * cfg["h"], cfg["ny"] * cfg["h"], mesh["depth"]
+        pos, m6s, f0s = synth.random_sources(F, [0.1 * lx, 0.1 * ly, -0.6 * depth], [0.9 * lx, 0.9 * ly, -0.05 * depth],
+                                             f0_range=(1.0, 4.0), seed=7)
+        for f in range(F):
+            s.add_point_source(pos[f], m6s[f], f0s[f], 1.2 / f0s[f], src["m0"], fused_idx=f)
     dt_rec = 0.01
     for r in recs:
         s.add_receiver(r, dt_rec)
@@ -187,7 +201,7 @@ def run_ours(args, rank, world, local_rank):
     _, lam, speedup = s.setup_clusters(NCLUSTERS, CFL)
     info = s.info()
     period = 2 ** (NCLUSTERS - 1)
-    per_macro = int(info["updates_per_macro"].sum())
+    per_macro = int(info["updates_per_macro"].sum()) * F      # simulation element updates
     stream = torch.cuda.current_stream()
     # warm-up
     s.advance_steps(period * args.warmup, stream)
@@ -220,7 +234,8 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.steps):
         s.advance(s.info()["time"] + period * info["finest_dt"] * (1 + 1e-6), stream)
         for rid in range(len(recs)):
-            s.seismogram(rid)
+            for f in range(F):
+                s.seismogram(rid, f)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     h2d1, d2h1 = s.transfer_bytes()
@@ -238,9 +253,10 @@ def run_ours(args, rank, world, local_rank):
     kind = int(np.argmax(kst["ms"]))
     name = ["k_predict_local", "k_neighbour"][kind]
     avg_ms = kst["ms"][kind] / max(kst["launches"][kind], 1)
-    elems_per_launch = kst["elems"][kind] / max(kst["launches"][kind], 1)
+    elems_per_launch = kst["elems"][kind] * F / max(kst["launches"][kind], 1)    # simulation elements
     fl = perfmodel.flops_predict(ORDER, NMECH) if kind == 0 else perfmodel.flops_neighbour(ORDER, NMECH)
-    by = perfmodel.bytes_predict(ORDER, NMECH) if kind == 0 else perfmodel.bytes_neighbour(ORDER, NMECH)
+    by = (perfmodel.bytes_predict(ORDER, NMECH, n_fused=F) if kind == 0
+          else perfmodel.bytes_neighbour(ORDER, NMECH, n_fused=F))
     achieved_tf = fl * elems_per_launch / (avg_ms / 1000.0) / 1e12
     achieved_gbs = by * elems_per_launch / (avg_ms / 1000.0) / 1e9
     traffic = None
@@ -248,17 +264,26 @@ def run_ours(args, rank, world, local_rank):
     if os.path.exists(tp):
         t = json.load(open(tp))
         ent = t.get(name)
+        if F > 1:
+            ent = t.get(name + "_fused%d" % F)
         if ent and ent.get("kernel_hash") == kernel_hash():
             traffic = ent["dram_bytes_per_element"] * elems_per_launch
+    metric, unit = METRIC, UNIT
+    srcs = "1 moment-tensor source"
+    if F > 1:
+        metric = "simulation element-updates/s, order-5 anelastic LTS, %d fused sources, 1 GB300" % F
+        unit = "sim-element-updates/s"
+        srcs = "%d fused simulations, one random moment-tensor source each" % F
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "anelastic O5 m3 LTS, %d jittered graded tets, Nc=%d, lambda=%.2f, CFL %.1f, "
-                               "1 moment-tensor source, 64 receivers; step = 1 macro step (%d finest steps)"
-                               % (K, NCLUSTERS, lam, CFL, period),
-                   "elements": K, "updates_per_step": per_macro, "cluster_elems": info["cluster_elems"].tolist(),
-                   "theoretical_lts_speedup": speedup, "l2": "inputs larger than L2 (DOFs %.1f GB)" % (K * 945 * 4 / 1e9),
+                               "%s, 64 receivers; step = 1 macro step (%d finest steps)"
+                               % (K, NCLUSTERS, lam, CFL, srcs, period),
+                   "elements": K, "fused": F, "updates_per_step": per_macro,
+                   "cluster_elems": info["cluster_elems"].tolist(), "theoretical_lts_speedup": speedup,
+                   "l2": "inputs larger than L2 (DOFs %.1f GB)" % (K * 945 * 4 * F / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "kernel": name, "achieved": achieved_tf, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved_tf / fp32_peak, "traffic": traffic,
@@ -269,14 +294,14 @@ def run_ours(args, rank, world, local_rank):
         "kernel_ms": {"k_predict_local": kst["ms"][0], "k_neighbour": kst["ms"][1],
                       "launches": kst["launches"].tolist()},
         "gpu_launches": int(launches),
-        "e2e": {"value": total_updates / (e2e_ms / 1000.0), "unit": UNIT,
+        "e2e": {"value": total_updates / (e2e_ms / 1000.0), "unit": unit,
                 "h2d_bytes_per_step": (h2d1 - h2d0) / args.steps, "d2h_bytes_per_step": (d2h1 - d2h0) / args.steps},
         "clocks": ck,
     }
     if not args.no_cpu_baseline and world == 1:
         per_m, times, Ks = oracle_sample(seconds_cap=20.0)
         v = per_m * len(times) / sum(times)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads_used(), "kind": "oracle",
+        line["cpu_baseline"] = {"value": v, "unit": unit, "cores": threads_used(), "kind": "oracle",
                                 "sample": "%d macro steps of a %d-tet mesh (12x12x5 hexes) of the same generator"
                                           % (len(times), Ks)}
     print(json.dumps(line), flush=True)
@@ -293,6 +318,7 @@ def main():
     ap.add_argument("--small", action="store_true", help="small mesh (quick check)")
     ap.add_argument("--medium", action="store_true", help="262k-tet mesh (profiling captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fused", type=int, default=1, help="fused simulations (multiple of 4; 1 = single)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

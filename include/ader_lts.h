@@ -49,11 +49,19 @@ enum {
     LTS_ERR_TIMEOUT = -6   /* a bounded device-side wait gave up                       */
 };
 
+/* Fused simulations (Sec. IV-A): n_fused is 1 or a multiple of LTS_FUSED_MULTIPLE up to
+ * LTS_MAX_FUSED. */
+#define LTS_FUSED_MULTIPLE 4
+#define LTS_MAX_FUSED 64
+
 /* Face boundary codes (per tetrahedron face). */
 enum { LTS_BC_INTERIOR = 0, LTS_BC_ABSORBING = 1, LTS_BC_FREE_SURFACE = 2, LTS_BC_PERIODIC = 3 };
 
 /* Create a solver. order O in {3,4,5} (B(O) = O(O+1)(O+2)/6 modes, Sec. III-A);
- * n_mech in {0, 3} (N^q = 9 + 6 n_mech quantities, Sec. III); n_fused must be 1.
+ * n_mech in {0, 3} (N^q = 9 + 6 n_mech quantities, Sec. III); n_fused simulations
+ * share mesh, material and clusters and differ in their sources and initial DOFs (fused
+ * simulations, Sec. IV-A: every scalar DOF becomes a vector of n_fused values; on the
+ * device the simulation index is the innermost one, Q[k][q][b][f]).
  * Selects CUDA device `device` for all later calls on the handle. device < 0 creates a
  * host-only handle: mesh, material and cluster set-up run (lts_setup_clusters reports
  * clusters, lambda and speedup) but no device state exists, so calls that need it
@@ -111,16 +119,17 @@ int lts_bind_device_memory(lts_t* h, void* dev, int64_t bytes);
 int lts_quadrature_points(lts_t* h, int64_t* n_per_elem, double* xyz_out);
 
 /* L2 projection of point values: values[n_tet][n_per_elem][n_q] at the points of
- * lts_quadrature_points become the DOFs (orthonormal basis, Sec. III-A). */
+ * lts_quadrature_points become the DOFs (orthonormal basis, Sec. III-A) of every
+ * fused simulation. */
 int lts_project_initial(lts_t* h, const double* values);
 
-/* Raw DOFs [n_tet][n_q][B] (double on the host, FP32 on the device). lts_get_dofs
- * synchronises the solver's stream. */
+/* Raw DOFs [n_fused][n_tet][n_q][B], simulation-major (double on the host, FP32 on the
+ * device). lts_get_dofs synchronises the solver's stream. */
 int lts_set_dofs(lts_t* h, const double* dofs);
 int lts_get_dofs(lts_t* h, double* dofs);
 
-/* DOFs of a subset of elements: elems[n] (original indices), dofs[n][n_q][B] in the
- * order of elems. Setting leaves every other element unchanged. Both synchronise the
+/* DOFs of a subset of elements: elems[n] (original indices), dofs[n_fused][n][n_q][B]
+ * in the order of elems. Setting leaves every other element unchanged. Both synchronise the
  * device. Errors: LTS_ERR_STATE before cluster set-up, LTS_ERR_ARG for an index out of
  * range or NULL arrays with n > 0. */
 int lts_set_dofs_subset(lts_t* h, int64_t n, const int64_t* elems, const double* dofs);
@@ -130,15 +139,17 @@ int lts_get_dofs_subset(lts_t* h, int64_t n, const int64_t* elems, double* dofs)
  * m0 * m6 * s(t), s the Ricker wavelet (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2),
  * m6 = (xx, yy, zz, xy, yz, xz). The containing element (lowest index whose closed
  * tetrahedron holds x) gains -m0 m6 (int s dt) phi_b(xi)/|det J| on its stress DOFs at
- * the end of each of its steps (O-point Gauss-Legendre in time). fused_idx must be 0.
- * Errors: LTS_ERR_ARG (point outside the mesh). Call before lts_setup_clusters. */
+ * the end of each of its steps (O-point Gauss-Legendre in time), in simulation fused_idx
+ * only (0 <= fused_idx < n_fused). Errors: LTS_ERR_ARG (point outside the mesh, bad
+ * fused_idx). Call before lts_setup_clusters. */
 int lts_add_point_source(lts_t* h, int fused_idx, const double x[3], const double m6[6],
                          double f0, double t0, double m0);
 
 /* Receiver at x sampled every dt_sample seconds (t_j = j dt_sample): each sample inside a
  * step [t_n, t_n + dt) of the receiver's element is the Taylor series
- * sum_d (t_j - t_n)^d / d! d^dQ evaluated at x (9 elastic quantities). *id receives its
- * index. Errors: LTS_ERR_ARG (outside mesh). Call before lts_setup_clusters. */
+ * sum_d (t_j - t_n)^d / d! d^dQ evaluated at x (9 elastic quantities), recorded for every
+ * fused simulation. *id receives its index. Errors: LTS_ERR_ARG (outside mesh). Call
+ * before lts_setup_clusters. */
 int lts_add_receiver(lts_t* h, const double x[3], double dt_sample, int* id);
 
 /* Advance whole macro steps (2^(N_c-1) finest steps of lam*dt_min each) until the time is
@@ -149,13 +160,14 @@ int lts_advance(lts_t* h, double t_end, void* cuda_stream);
 /* Advance n_finest finest steps (a multiple of 2^(N_c-1)) on `cuda_stream`. */
 int lts_advance_steps(lts_t* h, int64_t n_finest, void* cuda_stream);
 
-/* Copy receiver `id`'s samples so far: t_out[n] times and v_out[n][9] values (either may
- * be NULL); *n receives the number of samples (at most cap are written). Synchronises. */
+/* Copy receiver `id`'s samples so far in simulation fused_idx: t_out[n] times and
+ * v_out[n][9] values (either may be NULL); *n receives the number of samples (at most cap
+ * are written). Synchronises. Errors: LTS_ERR_ARG (bad id or fused_idx). */
 int lts_get_seismogram(lts_t* h, int id, int fused_idx, double* t_out, double* v_out,
                        int64_t cap, int64_t* n);
 
 /* Discrete elastic energy sum_k |det J_k| sum_b (rho |v_b|^2/2 + sigma_b : C^-1 sigma_b / 2),
- * reduced in FP64 on the device. Synchronises. */
+ * summed over the fused simulations, reduced in FP64 on the device. Synchronises. */
 int lts_energy(lts_t* h, double* e);
 
 /* Run information. n_clusters_out; per cluster (arrays of length >= 8, may be NULL):

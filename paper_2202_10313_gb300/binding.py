@@ -142,7 +142,9 @@ class Solver:
     """One solver handle (lts_t*). Method names follow the C functions."""
 
     def __init__(self, order, n_mech=0, device=0, n_fused=1):
-        self.order, self.n_mech, self.device = order, n_mech, device
+        """n_fused > 1: fused simulations; DOF arrays then carry a leading simulation axis
+        (n_fused, K, n_q, B) and sources / seismograms take a simulation index."""
+        self.order, self.n_mech, self.device, self.n_fused = order, n_mech, device, n_fused
         self.nq = 9 + 6 * n_mech
         self.nb = order * (order + 1) * (order + 2) // 6
         self._h = ctypes.c_void_p()
@@ -229,22 +231,25 @@ class Solver:
             pts.shape[0], pts.shape[1], self.nq))
         self._check(lib().lts_project_initial(self._h, _ptr(vals)))
 
+    def _dof_shape(self, n):
+        return (n, self.nq, self.nb) if self.n_fused == 1 else (self.n_fused, n, self.nq, self.nb)
+
     def set_dofs(self, dofs):
-        self._check(lib().lts_set_dofs(self._h, _ptr(_f64(dofs, self.K * self.nq * self.nb))))
+        self._check(lib().lts_set_dofs(self._h, _ptr(_f64(dofs, self.n_fused * self.K * self.nq * self.nb))))
 
     def get_dofs(self):
-        out = np.zeros((self.K, self.nq, self.nb))
+        out = np.zeros(self._dof_shape(self.K))
         self._check(lib().lts_get_dofs(self._h, _ptr(out)))
         return out
 
     def set_dofs_subset(self, elems, dofs):
         el = np.ascontiguousarray(elems, dtype=np.int64)
-        d = _f64(dofs, len(el) * self.nq * self.nb)
+        d = _f64(dofs, self.n_fused * len(el) * self.nq * self.nb)
         self._check(lib().lts_set_dofs_subset(self._h, len(el), _ptr(el), _ptr(d)))
 
     def get_dofs_subset(self, elems):
         el = np.ascontiguousarray(elems, dtype=np.int64)
-        out = np.zeros((len(el), self.nq, self.nb))
+        out = np.zeros(self._dof_shape(len(el)))
         self._check(lib().lts_get_dofs_subset(self._h, len(el), _ptr(el), _ptr(out)))
         return out
 
@@ -255,12 +260,12 @@ class Solver:
     def advance(self, t_end, stream=None):
         self._check(lib().lts_advance(self._h, float(t_end), _stream_handle(stream)))
 
-    def seismogram(self, rid):
+    def seismogram(self, rid, fused_idx=0):
         n = ctypes.c_int64()
-        self._check(lib().lts_get_seismogram(self._h, rid, 0, None, None, 0, ctypes.byref(n)))
+        self._check(lib().lts_get_seismogram(self._h, rid, fused_idx, None, None, 0, ctypes.byref(n)))
         t = np.zeros(n.value)
         v = np.zeros((n.value, 9))
-        self._check(lib().lts_get_seismogram(self._h, rid, 0, _ptr(t), _ptr(v), n.value, ctypes.byref(n)))
+        self._check(lib().lts_get_seismogram(self._h, rid, fused_idx, _ptr(t), _ptr(v), n.value, ctypes.byref(n)))
         return t, v
 
     def energy(self):

@@ -20,12 +20,12 @@ using ltsdev::RecvItem;
 using ltsdev::SrcItem;
 
 namespace ltsdev {
-bool get_launchers(int order, int m, Launchers* out) {
+bool get_launchers(int order, int m, bool fused, Launchers* out) {
   if (m != 0 && m != 3) return false;
   switch (order) {
-    case 3: *out = launchers_o3(m); return true;
-    case 4: *out = launchers_o4(m); return true;
-    case 5: *out = launchers_o5(m); return true;
+    case 3: *out = launchers_o3(m, fused); return true;
+    case 4: *out = launchers_o4(m, fused); return true;
+    case 5: *out = launchers_o5(m, fused); return true;
     default: return false;
   }
 }
@@ -35,6 +35,7 @@ namespace {
 
 struct Source {
   int64_t elem;          // original index
+  int sim;               // fused simulation it drives
   double xi[3];
   double m6[6];
   double f0, t0, m0;
@@ -67,6 +68,7 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 struct lts_solver {
   int order = 0, nmech = 0, device = 0;
+  int nsim = 1;                             // fused simulations
   std::string err;
   Launchers L{};
   lts::RefOps ops;
@@ -139,6 +141,13 @@ struct Layout {
   size_t Q, B1, B2, B3, edata, ndata, nbr, ncode, meta, emat, partial, K, Ft, Fh, Fb, rphi, sphi, total;
 };
 
+// Element strides (floats) of Q and of the LTS buffers: [group][q][b][G] per element with
+// the simulations of a group innermost; one simulation keeps the rows padded to 16 bytes.
+int64_t q_stride(const lts_solver* h) {
+  return h->nsim == 1 ? h->L.QS : (int64_t)h->L.NQ * h->L.B * h->nsim;
+}
+int64_t buf_stride(const lts_solver* h) { return h->nsim == 1 ? h->L.BUFS : (int64_t)9 * h->L.B * h->nsim; }
+
 Layout layout_of(const lts_solver* h, int64_t K) {
   Layout L{};
   size_t off = 0;
@@ -148,10 +157,11 @@ Layout layout_of(const lts_solver* h, int64_t K) {
     return o;
   };
   const Launchers& X = h->L;
-  L.Q = take(sizeof(float) * K * X.QS);
-  L.B1 = take(sizeof(float) * K * X.BUFS);
-  L.B2 = take(sizeof(float) * K * X.BUFS);
-  L.B3 = take(sizeof(float) * K * X.BUFS);
+  const size_t qs = (size_t)q_stride(h), bs = (size_t)buf_stride(h);
+  L.Q = take(sizeof(float) * K * qs);
+  L.B1 = take(sizeof(float) * K * bs);
+  L.B2 = take(sizeof(float) * K * bs);
+  L.B3 = take(sizeof(float) * K * bs);
   L.edata = take(sizeof(float) * K * ltsdev::ED);
   L.ndata = take(sizeof(float) * K * ltsdev::ND);
   L.nbr = take(sizeof(int) * K * 4);
@@ -351,10 +361,13 @@ void setup_device(lts_solver* h) {
   auto up = [&](const void* dst, const void* src, size_t bytes) {
     ck(cudaMemcpy(const_cast<void*>(dst), src, bytes, cudaMemcpyHostToDevice), "upload");
   };
-  ck(cudaMemset(h->dst.Q, 0, sizeof(float) * K * X.QS), "memset Q");
-  ck(cudaMemset(h->dst.B1, 0, sizeof(float) * K * X.BUFS), "memset B1");
-  ck(cudaMemset(h->dst.B2, 0, sizeof(float) * K * X.BUFS), "memset B2");
-  ck(cudaMemset(h->dst.B3, 0, sizeof(float) * K * X.BUFS), "memset B3");
+  h->dst.qs = q_stride(h);
+  h->dst.bs = buf_stride(h);
+  h->dst.nsim = h->nsim;
+  ck(cudaMemset(h->dst.Q, 0, sizeof(float) * K * h->dst.qs), "memset Q");
+  ck(cudaMemset(h->dst.B1, 0, sizeof(float) * K * h->dst.bs), "memset B1");
+  ck(cudaMemset(h->dst.B2, 0, sizeof(float) * K * h->dst.bs), "memset B2");
+  ck(cudaMemset(h->dst.B3, 0, sizeof(float) * K * h->dst.bs), "memset B3");
   up(h->dst.edata, edata.data(), sizeof(float) * edata.size());
   up(h->dst.ndata, ndata.data(), sizeof(float) * ndata.size());
   up(h->dst.nbr, nbr.data(), sizeof(int) * nbr.size());
@@ -469,6 +482,7 @@ void advance_steps(lts_solver* h, int64_t n_finest, cudaStream_t stream) {
         integ *= 0.5 * (tb - ta);
         SrcItem it{};
         it.elem = (int)h->iperm[src.elem];
+        it.sim = src.sim;
         it.phi_off = (int)(si * B);
         for (int r = 0; r < 6; ++r) it.amp[r] = (float)(-src.m0 * src.m6[r] * integ / h->mesh.detJ[src.elem]);
         sitems.push_back(it);
@@ -485,6 +499,7 @@ void advance_steps(lts_solver* h, int64_t n_finest, cudaStream_t stream) {
         const double ta = s * h->delta, tb = (s + (int64_t(1) << l)) * h->delta;
         RecvItem it{};
         it.elem = (int)h->iperm[rc.elem];
+        it.sim = 0;
         it.phi_off = (int)(ri * B);
         it.n = 0;
         int64_t j = std::max<int64_t>((int64_t)std::floor(ta / rc.dt) - 1, 0);
@@ -499,13 +514,17 @@ void advance_steps(lts_solver* h, int64_t n_finest, cudaStream_t stream) {
           ++seis_need;
           ++it.n;
         }
-        if (it.n > 0) ritems.push_back(it);
+        // one item per simulation; sample slot j holds nsim x 9 values
+        for (int f = 0; it.n > 0 && f < h->nsim; ++f) {
+          it.sim = f;
+          ritems.push_back(it);
+        }
       }
       ph.item_end = (int)ritems.size();
       plan.push_back(ph);
     }
   }
-  ensure_capacity(reinterpret_cast<void**>(&h->d_seis), &h->seis_cap, seis_need * 9, sizeof(float));
+  ensure_capacity(reinterpret_cast<void**>(&h->d_seis), &h->seis_cap, seis_need * 9 * h->nsim, sizeof(float));
   ensure_capacity(reinterpret_cast<void**>(&h->d_ritems), &h->ritems_cap, ritems.size(), sizeof(RecvItem));
   ensure_capacity(reinterpret_cast<void**>(&h->d_sitems), &h->sitems_cap, sitems.size(), sizeof(SrcItem));
   if (!ritems.empty())
@@ -529,10 +548,12 @@ void advance_steps(lts_solver* h, int64_t n_finest, cudaStream_t stream) {
     }
     const int nelem = pa.end - pa.begin;
     if (nelem <= 0) continue;
-    const int nb = (nelem + (ph.kind == 0 ? X.NEN : X.NE) - 1) / (ph.kind == 0 ? X.NEN : X.NE);
+    // CTA batches: NE elements (one simulation) or one element and FG of its simulations
+    const int nb = X.FG > 1 ? nelem * (h->nsim / X.FG)
+                            : (nelem + (ph.kind == 0 ? X.NEN : X.NE) - 1) / (ph.kind == 0 ? X.NEN : X.NE);
     if (ph.kind == 1 && ph.item_end > ph.item_beg) {
-      X.receivers(h->dops, h->dst.Q, h->dst.edata, h->d_recv_phi, h->d_ritems + ph.item_beg, h->d_seis,
-                  base.omega, ph.item_end - ph.item_beg, stream);
+      X.receivers(h->dops, h->dst.Q, h->dst.qs, h->nsim, X.FG, h->dst.edata, h->d_recv_phi, h->d_ritems + ph.item_beg,
+                  h->d_seis, base.omega, ph.item_end - ph.item_beg, stream);
       ++h->launches;
     }
     if (h->profiling) ck(cudaEventRecord(next_event(h), stream), "event record");
@@ -547,7 +568,8 @@ void advance_steps(lts_solver* h, int64_t n_finest, cudaStream_t stream) {
       h->ev_elems.push_back(nelem);
     }
     if (ph.kind == 0 && ph.item_end > ph.item_beg) {
-      X.sources(h->dst.Q, h->d_src_phi, h->d_sitems + ph.item_beg, ph.item_end - ph.item_beg, stream);
+      X.sources(h->dst.Q, h->dst.qs, X.FG, h->d_src_phi, h->d_sitems + ph.item_beg, ph.item_end - ph.item_beg,
+                stream);
       ++h->launches;
     }
   }
@@ -560,7 +582,8 @@ void advance_steps(lts_solver* h, int64_t n_finest, cudaStream_t stream) {
 extern "C" {
 
 int lts_create(int order, int n_mech, int n_fused, int device, lts_t** out) {
-  if (!out || order < 3 || order > 5 || (n_mech != 0 && n_mech != 3) || n_fused != 1) return LTS_ERR_ARG;
+  const bool fused_ok = n_fused == 1 || (n_fused > 0 && n_fused <= LTS_MAX_FUSED && n_fused % LTS_FUSED_MULTIPLE == 0);
+  if (!out || order < 3 || order > 5 || (n_mech != 0 && n_mech != 3) || !fused_ok) return LTS_ERR_ARG;
   lts_solver* h = nullptr;
   try {
     h = new lts_solver();
@@ -571,7 +594,9 @@ int lts_create(int order, int n_mech, int n_fused, int device, lts_t** out) {
     h->order = order;
     h->nmech = n_mech;
     h->device = device;
-    if (!ltsdev::get_launchers(order, n_mech, &h->L)) fail(LTS_ERR_ARG, "unsupported order / mechanisms");
+    h->nsim = n_fused;
+    if (!ltsdev::get_launchers(order, n_mech, n_fused > 1, &h->L)) fail(LTS_ERR_ARG, "unsupported order / mechanisms");
+    if (n_fused > 1 && n_fused % h->L.FG != 0) fail(LTS_ERR_ARG, "fused count not a multiple of the CTA group");
     if (device >= 0) {
       ck(cudaSetDevice(device), "cudaSetDevice");
       ck(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device), "device attribute");
@@ -750,15 +775,31 @@ int lts_quadrature_points(lts_t* h, int64_t* n_per_elem, double* xyz_out) {
   });
 }
 
-static void upload_dofs(lts_t* h, const std::vector<double>& dofs) {
-  const int64_t K = h->mesh.K;
-  const int B = h->L.B, NQ = h->L.NQ, QS = h->L.QS;
-  std::vector<float> q((size_t)K * QS, 0.f);
-  for (int64_t k = 0; k < K; ++k) {
-    const int64_t nk = h->iperm[k];
+// Host DOF arrays are simulation-major, [F][n][N^q][B] (F = 1: [n][N^q][B]); on the device
+// an element's row holds simulation groups of G = FG: [F/G][N^q][B][G].
+static int64_t row_index(const lts_t* h, int r, int b, int f) {
+  const int B = h->L.B, NQ = h->L.NQ, G = h->L.FG;
+  return (int64_t)(f / G) * NQ * B * G + ((int64_t)r * B + b) * G + f % G;
+}
+
+static void pack_row(const lts_t* h, const double* dofs, int64_t n, int64_t i, float* row) {
+  const int B = h->L.B, NQ = h->L.NQ, F = h->nsim;
+  for (int f = 0; f < F; ++f)
     for (int r = 0; r < NQ; ++r)
-      for (int b = 0; b < B; ++b) q[nk * QS + r * B + b] = (float)dofs[(k * NQ + r) * B + b];
-  }
+      for (int b = 0; b < B; ++b) row[row_index(h, r, b, f)] = (float)dofs[((f * n + i) * NQ + r) * B + b];
+}
+
+static void unpack_row(const lts_t* h, const float* row, int64_t n, int64_t i, double* dofs) {
+  const int B = h->L.B, NQ = h->L.NQ, F = h->nsim;
+  for (int f = 0; f < F; ++f)
+    for (int r = 0; r < NQ; ++r)
+      for (int b = 0; b < B; ++b) dofs[((f * n + i) * NQ + r) * B + b] = row[row_index(h, r, b, f)];
+}
+
+static void upload_dofs(lts_t* h, const double* dofs) {
+  const int64_t K = h->mesh.K, qs = h->dst.qs;
+  std::vector<float> q((size_t)K * qs, 0.f);
+  for (int64_t k = 0; k < K; ++k) pack_row(h, dofs, K, k, &q[h->iperm[k] * qs]);
   ck(cudaSetDevice(h->device), "cudaSetDevice");
   ck(cudaMemcpy(h->dst.Q, q.data(), q.size() * sizeof(float), cudaMemcpyHostToDevice), "upload Q");
 }
@@ -772,7 +813,7 @@ int lts_project_initial(lts_t* h, const double* values) {
     const int64_t np = (int64_t)h->ops.qp.size();
     std::vector<double> phiq(np * B);
     for (int64_t p = 0; p < np; ++p) h->ops.eval(h->ops.qp[p].data(), &phiq[p * B]);
-    std::vector<double> dofs((size_t)K * NQ * B, 0.0);
+    std::vector<double> dofs((size_t)h->nsim * K * NQ * B, 0.0);
     for (int64_t k = 0; k < K; ++k)
       for (int64_t p = 0; p < np; ++p) {
         const double w = h->ops.qw[p];
@@ -781,7 +822,9 @@ int lts_project_initial(lts_t* h, const double* values) {
           for (int b = 0; b < B; ++b) dofs[(k * NQ + r) * B + b] += v * phiq[p * B + b];
         }
       }
-    upload_dofs(h, dofs);
+    const size_t one = (size_t)K * NQ * B;
+    for (int f = 1; f < h->nsim; ++f) std::copy(dofs.begin(), dofs.begin() + one, dofs.begin() + f * one);
+    upload_dofs(h, dofs.data());
   });
 }
 
@@ -789,8 +832,7 @@ int lts_set_dofs(lts_t* h, const double* dofs) {
   return run(h, [&] {
     if (!h->ready) fail(LTS_ERR_STATE, "clusters not set up");
     if (!dofs) fail(LTS_ERR_ARG, "null dofs");
-    std::vector<double> d(dofs, dofs + (size_t)h->mesh.K * h->L.NQ * h->L.B);
-    upload_dofs(h, d);
+    upload_dofs(h, dofs);
   });
 }
 
@@ -798,17 +840,12 @@ int lts_get_dofs(lts_t* h, double* dofs) {
   return run(h, [&] {
     if (!h->ready) fail(LTS_ERR_STATE, "clusters not set up");
     if (!dofs) fail(LTS_ERR_ARG, "null dofs");
-    const int64_t K = h->mesh.K;
-    const int B = h->L.B, NQ = h->L.NQ, QS = h->L.QS;
-    std::vector<float> q((size_t)K * QS);
+    const int64_t K = h->mesh.K, qs = h->dst.qs;
+    std::vector<float> q((size_t)K * qs);
     ck(cudaSetDevice(h->device), "cudaSetDevice");
     ck(cudaDeviceSynchronize(), "synchronize");
     ck(cudaMemcpy(q.data(), h->dst.Q, q.size() * sizeof(float), cudaMemcpyDeviceToHost), "download Q");
-    for (int64_t k = 0; k < K; ++k) {
-      const int64_t nk = h->iperm[k];
-      for (int r = 0; r < NQ; ++r)
-        for (int b = 0; b < B; ++b) dofs[(k * NQ + r) * B + b] = q[nk * QS + r * B + b];
-    }
+    for (int64_t k = 0; k < K; ++k) unpack_row(h, &q[h->iperm[k] * qs], K, k, dofs);
   });
 }
 
@@ -816,16 +853,15 @@ int lts_set_dofs_subset(lts_t* h, int64_t n, const int64_t* elems, const double*
   return run(h, [&] {
     if (!h->ready) fail(LTS_ERR_STATE, "clusters not set up");
     if (n < 0 || (n > 0 && (!elems || !dofs))) fail(LTS_ERR_ARG, "bad subset arguments");
-    const int B = h->L.B, NQ = h->L.NQ, QS = h->L.QS;
-    std::vector<float> row(QS, 0.f);
+    const int64_t qs = h->dst.qs;
+    std::vector<float> row(qs, 0.f);
     ck(cudaSetDevice(h->device), "cudaSetDevice");
     ck(cudaDeviceSynchronize(), "synchronize");
     for (int64_t i = 0; i < n; ++i) {
       const int64_t k = elems[i];
       if (k < 0 || k >= h->mesh.K) fail(LTS_ERR_ARG, "element index out of range");
-      for (int r = 0; r < NQ; ++r)
-        for (int b = 0; b < B; ++b) row[r * B + b] = (float)dofs[(i * NQ + r) * B + b];
-      ck(cudaMemcpy(h->dst.Q + h->iperm[k] * QS, row.data(), QS * sizeof(float), cudaMemcpyHostToDevice), "upload");
+      pack_row(h, dofs, n, i, row.data());
+      ck(cudaMemcpy(h->dst.Q + h->iperm[k] * qs, row.data(), qs * sizeof(float), cudaMemcpyHostToDevice), "upload");
     }
   });
 }
@@ -834,16 +870,15 @@ int lts_get_dofs_subset(lts_t* h, int64_t n, const int64_t* elems, double* dofs)
   return run(h, [&] {
     if (!h->ready) fail(LTS_ERR_STATE, "clusters not set up");
     if (n < 0 || (n > 0 && (!elems || !dofs))) fail(LTS_ERR_ARG, "bad subset arguments");
-    const int B = h->L.B, NQ = h->L.NQ, QS = h->L.QS;
-    std::vector<float> row(QS);
+    const int64_t qs = h->dst.qs;
+    std::vector<float> row(qs);
     ck(cudaSetDevice(h->device), "cudaSetDevice");
     ck(cudaDeviceSynchronize(), "synchronize");
     for (int64_t i = 0; i < n; ++i) {
       const int64_t k = elems[i];
       if (k < 0 || k >= h->mesh.K) fail(LTS_ERR_ARG, "element index out of range");
-      ck(cudaMemcpy(row.data(), h->dst.Q + h->iperm[k] * QS, QS * sizeof(float), cudaMemcpyDeviceToHost), "download");
-      for (int r = 0; r < NQ; ++r)
-        for (int b = 0; b < B; ++b) dofs[(i * NQ + r) * B + b] = row[r * B + b];
+      ck(cudaMemcpy(row.data(), h->dst.Q + h->iperm[k] * qs, qs * sizeof(float), cudaMemcpyDeviceToHost), "download");
+      unpack_row(h, row.data(), n, i, dofs);
     }
   });
 }
@@ -852,8 +887,9 @@ int lts_add_point_source(lts_t* h, int fused_idx, const double x[3], const doubl
                          double m0) {
   return run(h, [&] {
     if (!h->has_mesh) fail(LTS_ERR_STATE, "no mesh");
-    if (fused_idx != 0 || !x || !m6) fail(LTS_ERR_ARG, "bad source arguments");
+    if (fused_idx < 0 || fused_idx >= h->nsim || !x || !m6) fail(LTS_ERR_ARG, "bad source arguments");
     Source s;
+    s.sim = fused_idx;
     s.elem = lts::locate(h->mesh, x, s.xi);
     if (s.elem < 0) fail(LTS_ERR_ARG, "source outside the mesh");
     std::copy(m6, m6 + 6, s.m6);
@@ -906,7 +942,8 @@ int lts_advance(lts_t* h, double t_end, void* cuda_stream) {
 
 int lts_get_seismogram(lts_t* h, int id, int fused_idx, double* t_out, double* v_out, int64_t cap, int64_t* n) {
   return run(h, [&] {
-    if (id < 0 || id >= (int)h->receivers.size() || fused_idx != 0) fail(LTS_ERR_ARG, "bad receiver id");
+    if (id < 0 || id >= (int)h->receivers.size() || fused_idx < 0 || fused_idx >= h->nsim)
+      fail(LTS_ERR_ARG, "bad receiver id");
     const Receiver& r = h->receivers[id];
     const int64_t ns = (int64_t)r.t.size();
     if (n) *n = ns;
@@ -915,15 +952,15 @@ int lts_get_seismogram(lts_t* h, int id, int fused_idx, double* t_out, double* v
     ck(cudaSetDevice(h->device), "cudaSetDevice");
     ck(cudaDeviceSynchronize(), "synchronize");
     // the receiver's samples occupy increasing slots; copy the span they cover
-    const int64_t lo = r.slot[0], hi = r.slot[m - 1] + 1;
-    std::vector<float> buf((hi - lo) * 9);
-    ck(cudaMemcpy(buf.data(), h->d_seis + lo * 9, buf.size() * sizeof(float), cudaMemcpyDeviceToHost),
+    const int64_t lo = r.slot[0], hi = r.slot[m - 1] + 1, F = h->nsim;
+    std::vector<float> buf((hi - lo) * 9 * F);
+    ck(cudaMemcpy(buf.data(), h->d_seis + lo * 9 * F, buf.size() * sizeof(float), cudaMemcpyDeviceToHost),
        "download seismogram");
     h->d2h_bytes += (int64_t)(buf.size() * sizeof(float));
     for (int64_t i = 0; i < m; ++i) {
       if (t_out) t_out[i] = r.t[i];
       if (v_out)
-        for (int q = 0; q < 9; ++q) v_out[i * 9 + q] = buf[(r.slot[i] - lo) * 9 + q];
+        for (int q = 0; q < 9; ++q) v_out[i * 9 + q] = buf[((r.slot[i] - lo) * F + fused_idx) * 9 + q];
     }
   });
 }
@@ -934,7 +971,7 @@ int lts_energy(lts_t* h, double* e) {
     if (!e) fail(LTS_ERR_ARG, "null output");
     ck(cudaSetDevice(h->device), "cudaSetDevice");
     const int nb = h->n_partial;
-    h->L.energy(h->dst.Q, h->d_emat, (int)h->mesh.K, h->d_partial, nb, 0);
+    h->L.energy(h->dst.Q, h->dst.qs, h->nsim, h->L.FG, h->d_emat, (int)h->mesh.K, h->d_partial, nb, 0);
     ck(cudaGetLastError(), "energy kernel");
     std::vector<double> part(nb);
     ck(cudaMemcpy(part.data(), h->d_partial, nb * sizeof(double), cudaMemcpyDeviceToHost), "download energy");

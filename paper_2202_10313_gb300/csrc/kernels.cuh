@@ -31,10 +31,13 @@ __host__ __device__ constexpr int rup(int x, int m) { return (x + m - 1) / m * m
 constexpr int ED = 64;   // floats of per-element data for k_predict_local
 constexpr int ND = 48;   // floats of per-element data for k_neighbour
 constexpr int MAXC = 8;  // max clusters
+constexpr int FUSED_GROUP = 4;   // simulations per CTA in fused mode
 constexpr int FLAG_FINER = 1 << 8;     // element has a finer neighbour: writes B2
 constexpr int FLAG_COARSER = 1 << 9;   // element has a coarser neighbour: writes B3
 
-template <int O, int M>
+// FG = 1: a CTA slot is an element (single simulation). FG > 1: fused simulations, a CTA
+// owns one element and FG of its simulations, one slot per simulation.
+template <int O, int M, int FG = 1>
 struct Cfg {
   static constexpr int B = nbasis(O), F = nface(O), NQ = 9 + 6 * M, NA = 6 * M;
   static constexpr int BS = (B % 2) ? B : B + 1;     // odd row stride: conflict-free rows and columns
@@ -42,8 +45,13 @@ struct Cfg {
   static constexpr int BUFS = rup(9 * B, 4);         // element stride of B1/B2/B3
   // elements per CTA: 7 x 35 columns = 8 warps at order 5, so two CTAs fit with up to
   // 128 registers per thread (registers are allocated per SM sub-partition)
-  static constexpr int NE = (O == 3) ? 24 : (O == 4 ? 12 : 7);
+  static constexpr int NE = (FG > 1) ? FG : ((O == 3) ? 24 : (O == 4 ? 12 : 7));   // slots per CTA
+  static constexpr int NEL = (FG > 1) ? 1 : NE;                                       // elements per CTA
   static constexpr int NT = rup(NE * B, 32);
+  // resident CTAs per SM the register budget is sized for (registers are allocated per
+  // SM sub-partition: 16K per quarter, whole warps)
+  static constexpr int PMIN = (FG > 1) ? 3 : 2;
+  static constexpr int NMIN = (FG > 1) ? 4 : 2;
   static constexpr int AR = 12;                      // staged elastic rows (padded, 16-byte stores)
   // staged Riemann states (v*, t*: 6 values) per face mode: a stride of 12 floats keeps the
   // 16-byte stores of 8 consecutive tasks on 8 distinct 4-bank groups
@@ -59,21 +67,24 @@ struct Cfg {
   static constexpr int P_FH = rup(P_FT + 4 * B * F, 4);
   static constexpr int P_A = rup(P_FH + 4 * F * B, 4);
   static constexpr int P_FL = rup(P_A + 2 * NE * B * AR, 4);
-  static constexpr int P_E = rup(P_FL + NE * 4 * F * FR, 4);
-  static constexpr int P_SP = rup(P_E + NE * ED, 4);
+  // slot stride of the staged Riemann states; odd in 16-byte units when slots vary fastest
+  static constexpr int FLS = 4 * F * FR + ((FG > 1) ? 4 : 0);
+  static constexpr int P_E = rup(P_FL + NE * FLS, 4);
+  static constexpr int P_SP = rup(P_E + NEL * ED, 4);
   static constexpr int P_META = rup(P_SP + NE * NSPLIT * SPR, 4);
-  static constexpr int P_TOTAL = rup(P_META + NE, 4);
+  static constexpr int P_TOTAL = rup(P_META + NEL, 4);
   // k_neighbour: its own batch size (kept equal to NE: a third CTA per SM leaves too
   // little L1 for the neighbour-buffer gathers)
-  static constexpr int NEN = (O == 5) ? 8 : NE;
+  static constexpr int NEN = (FG > 1) ? FG : ((O == 5) ? 8 : NE);
+  static constexpr int NELN = (FG > 1) ? 1 : NEN;
   static constexpr int NTN = rup(NEN * B, 32);
   static constexpr int N_FB = 0;
   static constexpr int N_FH = rup(N_FB + 12 * B * F, 4);
   static constexpr int N_X = rup(N_FH + 4 * F * B, 4);
   static constexpr int N_FL = rup(N_X + NEN * 4 * B * XR, 4);
-  static constexpr int N_D = rup(N_FL + NEN * 4 * F * FR, 4);
-  static constexpr int N_I = rup(N_D + NEN * ND, 4);       // ints: nbr[4], code[4], meta per element
-  static constexpr int N_TOTAL = rup(N_I + NEN * 9, 4);
+  static constexpr int N_D = rup(N_FL + NEN * FLS, 4);
+  static constexpr int N_I = rup(N_D + NELN * ND, 4);      // ints: nbr[4], code[4], meta per element
+  static constexpr int N_TOTAL = rup(N_I + NELN * 9, 4);
 };
 
 struct DevOps {
@@ -84,8 +95,14 @@ struct DevOps {
 };
 
 struct DevState {
-  float* Q;              // [K][QS]
-  float* B1;             // [K][BUFS]
+  // Simulations are blocked in groups of G (G = FUSED_GROUP in fused mode, else 1): element k,
+  // quantity r, mode b, simulation f = G g + j sits at Q[k * qs + g * NQ B G + (r B + b) G + j],
+  // qs = NQ B nsim (one simulation: QS, rows padded); the LTS buffers likewise with 9 rows
+  // and element stride bs.
+  long long qs, bs;
+  int nsim;
+  float* Q;
+  float* B1;
   float* B2;
   float* B3;
   const float* edata;    // [K][ED]
@@ -104,17 +121,19 @@ struct PhaseArgs {
 };
 
 // ------------------------------------------------------------------ helpers
-template <int O, int NE>
+// Tasks ordered by the degree of the mode column, highest first; within a degree the mode
+// varies fastest (SF = false) or the slot does (SF = true: fused simulations, so that
+// neighbouring threads touch neighbouring simulations of one DOF).
+template <int O, int NE, bool SF = false>
 __device__ __forceinline__ void task_of(int t, int& e, int& b, int& p) {
-  // tasks ordered by the degree of the mode column, highest first
   int off = 0;
 #pragma unroll
   for (int q = O - 1; q >= 0; --q) {
     const int np = (q + 1) * (q + 2) / 2;
     if (t >= off && t < off + NE * np) {
       const int idx = t - off;
-      e = idx / np;
-      b = nbasis(q) + idx % np;
+      e = SF ? idx % NE : idx / np;
+      b = nbasis(q) + (SF ? idx / NE : idx % np);
       p = q;
     }
     off += NE * np;
@@ -123,7 +142,7 @@ __device__ __forceinline__ void task_of(int t, int& e, int& b, int& p) {
 
 // Face tasks (element, face, face mode f), ordered by the degree of f (highest first): the
 // product with F~ / F- only involves modes of degree >= deg f.
-template <int O, int NE>
+template <int O, int NE, bool SF = false>
 __device__ __forceinline__ void face_task_of(int t, int& ee, int& i, int& f, int& pf) {
   int off = 0;
   ee = -1;
@@ -132,8 +151,8 @@ __device__ __forceinline__ void face_task_of(int t, int& ee, int& i, int& f, int
   for (int q = O - 1; q >= 0; --q) {
     const int n = NE * 4 * (q + 1);
     if (t >= off && t < off + n) {
-      const int idx = t - off, r = idx % (4 * (q + 1));
-      ee = idx / (4 * (q + 1));
+      const int idx = t - off, r = SF ? idx / NE : idx % (4 * (q + 1));
+      ee = SF ? idx % NE : idx / (4 * (q + 1));
       i = r / (q + 1);
       f = nface(q) + r % (q + 1);
       pf = q;
@@ -281,11 +300,11 @@ __device__ __forceinline__ void project_faces(const float* Fl, const float* sFh,
 }
 
 // ------------------------------------------------------------------ predict + local
-template <int O, int M>
-__global__ void __launch_bounds__(Cfg<O, M>::NT, 2) k_predict_local(DevOps ops, DevState st, PhaseArgs ph) {
-  using C = Cfg<O, M>;
-  constexpr int B = C::B, F = C::F, NE = C::NE, NT = C::NT, BS = C::BS, AR = C::AR, FR = C::FR;
-  constexpr int NQ = C::NQ, NA = C::NA, QS = C::QS, BUFS = C::BUFS, NSPLIT = C::NSPLIT, SPR = C::SPR;
+template <int O, int M, int FG>
+__global__ void __launch_bounds__(Cfg<O, M, FG>::NT, Cfg<O, M, FG>::PMIN) k_predict_local(DevOps ops, DevState st, PhaseArgs ph) {
+  using C = Cfg<O, M, FG>;
+  constexpr int B = C::B, F = C::F, NE = C::NE, NEL = C::NEL, NT = C::NT, BS = C::BS, AR = C::AR, FR = C::FR;
+  constexpr int NQ = C::NQ, NA = C::NA, NSPLIT = C::NSPLIT, SPR = C::SPR;
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
   float* sK = smem + C::P_K;
@@ -306,7 +325,7 @@ __global__ void __launch_bounds__(Cfg<O, M>::NT, 2) k_predict_local(DevOps ops, 
   for (int i = tid; i < 4 * F * B; i += NT) sFh[i] = ops.Fh[i];
 
   int e = -1, b = 0, p = 0;
-  task_of<O, NE>(tid, e, b, p);
+  task_of<O, NE, (FG > 1)>(tid, e, b, p);
   const bool act = e >= 0;
   const int es = act ? e : 0;
   // time-kernel product of this thread: column ck_col over k in [ck_k0, ck_k1)
@@ -329,36 +348,46 @@ __global__ void __launch_bounds__(Cfg<O, M>::NT, 2) k_predict_local(DevOps ops, 
   const int fmax = nface(p + 1);        // face modes of degree <= deg b
   int fe = -1, fi = 0, ff = 0, fpf = 0;  // first face task of this thread (second one below)
   const int nelem = ph.end - ph.begin;
-  const int nbatch = (nelem + NE - 1) / NE;
+  // element strides and simulation count: compile-time constants for one simulation
+  const long long qs = (FG > 1) ? st.qs : C::QS, bs = (FG > 1) ? st.bs : C::BUFS;
+  const int nsim = (FG > 1) ? st.nsim : 1;
+  const int nsg = nsim / FG;                             // simulation groups per element
+  const int nbatch = (FG > 1) ? nelem * nsg : (nelem + NE - 1) / NE;
+  constexpr int rs = B * FG;                             // row stride of Q and the buffers
 
   for (int batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
-    const int e0 = ph.begin + batch * NE;
+    const int e0 = (FG > 1) ? ph.begin + batch / nsg : ph.begin + batch * NE;
+    const int grp = (FG > 1) ? batch % nsg : 0;          // simulation group
     __syncthreads();
-    const int g = e0 + e;
+    const int g = e0 + ((FG > 1) ? 0 : e);
+    const int eb = (FG > 1) ? 0 : es;                    // element slot in the staged tables
+    const int j = (FG > 1) ? es : 0;                     // simulation within the group
     const bool valid = act && g < ph.end;
+    const size_t qoff = (size_t)g * qs + (size_t)grp * (C::NQ * B * FG) + b * FG + j;
+    const size_t boff = (size_t)g * bs + (size_t)grp * (9 * B * FG) + b * FG + j;
     // DOF loads are issued together with the element tables, before the barrier
     float T[NQ], Th[9], Da[NA > 0 ? NA : 1];
     float v[12];
 #pragma unroll
     for (int r = 0; r < 12; ++r) v[r] = 0.f;
     if (valid) {
-      const float* q = st.Q + (size_t)g * QS + b;
+      const float* q = st.Q + qoff;
 #pragma unroll
-      for (int r = 0; r < 9; ++r) v[r] = q[r * B];
+      for (int r = 0; r < 9; ++r) v[r] = q[r * rs];
 #pragma unroll
-      for (int r = 0; r < NA; ++r) Da[r] = q[(9 + r) * B];
+      for (int r = 0; r < NA; ++r) Da[r] = q[(9 + r) * rs];
     } else {
 #pragma unroll
       for (int r = 0; r < NA; ++r) Da[r] = 0.f;
     }
-    for (int i = tid; i < NE * ED; i += NT) {
+    for (int i = tid; i < NEL * ED; i += NT) {
       const int ee = i / ED, gg = e0 + ee;
       sE[i] = (gg < ph.end) ? st.edata[(size_t)gg * ED + (i % ED)] : 0.f;
     }
-    if (tid < NE) sMeta[tid] = (e0 + tid < ph.end) ? st.meta[e0 + tid] : 0;
+    if (tid < NEL) sMeta[tid] = (e0 + tid < ph.end) ? st.meta[e0 + tid] : 0;
     __syncthreads();
-    const float* ed = sE + es * ED;
-    const int meta = act ? sMeta[es] : 0;
+    const float* ed = sE + eb * ED;
+    const int meta = act ? sMeta[eb] : 0;
     const int cl = meta & 0xff;
     {
 #pragma unroll
@@ -462,22 +491,22 @@ __global__ void __launch_bounds__(Cfg<O, M>::NT, 2) k_predict_local(DevOps ops, 
     }
     // ---- LTS buffers (Eq. lts_buffers)
     if (valid) {
-      float* b1 = st.B1 + (size_t)g * BUFS + b;
+      float* b1 = st.B1 + boff;
 #pragma unroll
-      for (int r = 0; r < 9; ++r) b1[r * B] = T[r];
+      for (int r = 0; r < 9; ++r) b1[r * rs] = T[r];
       if (meta & FLAG_FINER) {
-        float* b2 = st.B2 + (size_t)g * BUFS + b;
+        float* b2 = st.B2 + boff;
 #pragma unroll
-        for (int r = 0; r < 9; ++r) b2[r * B] = Th[r];
+        for (int r = 0; r < 9; ++r) b2[r * rs] = Th[r];
       }
       if (meta & FLAG_COARSER) {
-        float* b3 = st.B3 + (size_t)g * BUFS + b;
+        float* b3 = st.B3 + boff;
         if (ph.parity[cl] == 0) {
 #pragma unroll
-          for (int r = 0; r < 9; ++r) b3[r * B] = T[r];
+          for (int r = 0; r < 9; ++r) b3[r * rs] = T[r];
         } else {
 #pragma unroll
-          for (int r = 0; r < 9; ++r) b3[r * B] += T[r];
+          for (int r = 0; r < 9; ++r) b3[r * rs] += T[r];
         }
       }
     }
@@ -520,20 +549,20 @@ __global__ void __launch_bounds__(Cfg<O, M>::NT, 2) k_predict_local(DevOps ops, 
         for (int r = 0; r < 9; ++r) V[r] = -out[r];
 #pragma unroll
         for (int l = 0; l < M; ++l) coupling_add(V, T + 9 + 6 * l, ed[12 + 2 * l], ed[13 + 2 * l]);
-        const float* q = st.Q + (size_t)g * QS + b;
+        const float* q = st.Q + qoff;
 #pragma unroll
-        for (int r = 0; r < 9; ++r) acc[r] = q[r * B] + V[r];
+        for (int r = 0; r < 9; ++r) acc[r] = q[r * rs] + V[r];
 #pragma unroll
         for (int l = 0; l < M; ++l)
 #pragma unroll
           for (int r = 0; r < 6; ++r)
-            acc[9 + 6 * l + r] = q[(9 + 6 * l + r) * B] + ph.omega[l] * (-eps[r] - T[9 + 6 * l + r]);
+            acc[9 + 6 * l + r] = q[(9 + 6 * l + r) * rs] + ph.omega[l] * (-eps[r] - T[9 + 6 * l + r]);
       }
     }
     // ---- local surface kernel: G_i = T^e F~_i, flux, staged for F^
 #pragma unroll 1
     for (int t = tid; t < NE * 4 * F; t += NT) {
-      face_task_of<O, NE>(t, fe, fi, ff, fpf);
+      face_task_of<O, NE, (FG > 1)>(t, fe, fi, ff, fpf);
       float gq[9];
 #pragma unroll
       for (int r = 0; r < 9; ++r) gq[r] = 0.f;
@@ -556,8 +585,8 @@ __global__ void __launch_bounds__(Cfg<O, M>::NT, 2) k_predict_local(DevOps ops, 
         gq[8] = fmaf(x8, w, gq[8]);
       }
       float w6[6];
-      riemann_state(gq, sE + fe * ED + 20 + 11 * fi, w6);
-      store_state(sFl + (fe * 4 * F + fi * F + ff) * FR, w6);
+      riemann_state(gq, sE + ((FG > 1) ? 0 : fe) * ED + 20 + 11 * fi, w6);
+      store_state(sFl + fe * C::FLS + (fi * F + ff) * FR, w6);
     }
     __syncthreads();
     if (valid) {
@@ -565,26 +594,25 @@ __global__ void __launch_bounds__(Cfg<O, M>::NT, 2) k_predict_local(DevOps ops, 
       float S[NS];
 #pragma unroll
       for (int r = 0; r < NS; ++r) S[r] = 0.f;
-      project_faces<NS, F, B, FR>(sFl + e * 4 * F * FR, sFh, ed + 20, 11, ed[9], ed[10], ed[11], fmax, b, S);
-      float* q = st.Q + (size_t)g * QS + b;
+      project_faces<NS, F, B, FR>(sFl + e * C::FLS, sFh, ed + 20, 11, ed[9], ed[10], ed[11], fmax, b, S);
+      float* q = st.Q + qoff;
 #pragma unroll
-      for (int r = 0; r < 9; ++r) q[r * B] = acc[r] + S[r];
+      for (int r = 0; r < 9; ++r) q[r * rs] = acc[r] + S[r];
       if constexpr (M > 0) {
 #pragma unroll
         for (int l = 0; l < M; ++l)
 #pragma unroll
-          for (int r = 0; r < 6; ++r) q[(9 + 6 * l + r) * B] = acc[9 + 6 * l + r] + ph.omega[l] * S[NS - 6 + r];
+          for (int r = 0; r < 6; ++r) q[(9 + 6 * l + r) * rs] = acc[9 + 6 * l + r] + ph.omega[l] * S[NS - 6 + r];
       }
     }
   }
 }
 
 // ------------------------------------------------------------------ neighbour
-template <int O, int M>
-__global__ void __launch_bounds__(Cfg<O, M>::NTN, 2) k_neighbour(DevOps ops, DevState st, PhaseArgs ph) {
-  using C = Cfg<O, M>;
-  constexpr int B = C::B, F = C::F, NE = C::NEN, NT = C::NTN, FR = C::FR, XR = C::XR;
-  constexpr int QS = C::QS, BUFS = C::BUFS;
+template <int O, int M, int FG>
+__global__ void __launch_bounds__(Cfg<O, M, FG>::NTN, Cfg<O, M, FG>::NMIN) k_neighbour(DevOps ops, DevState st, PhaseArgs ph) {
+  using C = Cfg<O, M, FG>;
+  constexpr int B = C::B, F = C::F, NE = C::NEN, NEL = C::NELN, NT = C::NTN, FR = C::FR, XR = C::XR;
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
   float* sFb = smem + C::N_FB;
@@ -598,32 +626,39 @@ __global__ void __launch_bounds__(Cfg<O, M>::NTN, 2) k_neighbour(DevOps ops, Dev
   for (int i = tid; i < 4 * F * B; i += NT) sFh[i] = ops.Fh[i];
 
   int e = -1, b = 0, p = 0;
-  task_of<O, NE>(tid, e, b, p);
+  task_of<O, NE, (FG > 1)>(tid, e, b, p);
   const bool act = e >= 0;
   const int fmax = nface(p + 1);
   const int nelem = ph.end - ph.begin;
-  const int nbatch = (nelem + NE - 1) / NE;
+  const long long qs = (FG > 1) ? st.qs : C::QS, bs = (FG > 1) ? st.bs : C::BUFS;
+  const int nsim = (FG > 1) ? st.nsim : 1;
+  const int nsg = nsim / FG;
+  const int nbatch = (FG > 1) ? nelem * nsg : (nelem + NE - 1) / NE;
+  constexpr int rs = B * FG;
 
   for (int batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
-    const int e0 = ph.begin + batch * NE;
+    const int e0 = (FG > 1) ? ph.begin + batch / nsg : ph.begin + batch * NE;
+    const int grp = (FG > 1) ? batch % nsg : 0;
     __syncthreads();
-    for (int i = tid; i < NE * ND; i += NT) {
+    for (int i = tid; i < NEL * ND; i += NT) {
       const int ee = i / ND, gg = e0 + ee;
       sD[i] = (gg < ph.end) ? st.ndata[(size_t)gg * ND + (i % ND)] : 0.f;
     }
-    for (int i = tid; i < NE * 9; i += NT) {
+    for (int i = tid; i < NEL * 9; i += NT) {
       const int ee = i / 9, c = i % 9, gg = e0 + ee;
       int v = -1;
       if (gg < ph.end) v = (c < 4) ? st.nbr[(size_t)gg * 4 + c] : (c < 8 ? st.ncode[(size_t)gg * 4 + c - 4] : st.meta[gg]);
       sI[i] = v;
     }
     __syncthreads();
-    const int g = e0 + e;
+    const int g = e0 + ((FG > 1) ? 0 : e);
+    const int eb = (FG > 1) ? 0 : e;                     // element slot in the staged tables
+    const int j = (FG > 1) ? e : 0;
     const bool valid = act && g < ph.end;
     // ---- gather the neighbours' time-integrated DOFs by cluster relation (Sec. V-B):
     // all 4 x 9 loads are issued before the shared-memory stores
     if (act) {
-      const int* ie = sI + e * 9;
+      const int* ie = sI + eb * 9;
       const int cl = ie[8] & 0xff;
       const int par = valid ? ph.parity[cl] : 0;
       float xv[4][9];
@@ -633,12 +668,12 @@ __global__ void __launch_bounds__(Cfg<O, M>::NTN, 2) k_neighbour(DevOps ops, Dev
         const int rel = ie[4 + i] >> 8;
         const float* src1 = (rel == 1) ? st.B3 : ((rel == 2 && par == 0) ? st.B2 : st.B1);
         const bool sub = (rel == 2 && par == 1);
-        const size_t off = (size_t)(nb < 0 ? 0 : nb) * BUFS + b;
+        const size_t off = (size_t)(nb < 0 ? 0 : nb) * bs + (size_t)grp * (9 * B * FG) + b * FG + j;
 #pragma unroll
-        for (int r = 0; r < 9; ++r) xv[i][r] = (nb < 0) ? 0.f : __ldg(src1 + off + r * B);
+        for (int r = 0; r < 9; ++r) xv[i][r] = (nb < 0) ? 0.f : __ldg(src1 + off + r * rs);
         if (sub) {
 #pragma unroll
-          for (int r = 0; r < 9; ++r) xv[i][r] -= __ldg(st.B2 + off + r * B);
+          for (int r = 0; r < 9; ++r) xv[i][r] -= __ldg(st.B2 + off + r * rs);
         }
       }
 #pragma unroll
@@ -653,8 +688,9 @@ __global__ void __launch_bounds__(Cfg<O, M>::NTN, 2) k_neighbour(DevOps ops, Dev
 #pragma unroll 1
     for (int t = tid; t < NE * 4 * F; t += NT) {
       int ee, i, f, pf;
-      face_task_of<O, NE>(t, ee, i, f, pf);
-      const int code = sI[ee * 9 + 4 + i];
+      face_task_of<O, NE, (FG > 1)>(t, ee, i, f, pf);
+      const int eel = (FG > 1) ? 0 : ee;
+      const int code = sI[eel * 9 + 4 + i];
       const int jh = (code >= 0) ? (code & 0xff) : 0;
       float gq[9];
 #pragma unroll
@@ -668,30 +704,30 @@ __global__ void __launch_bounds__(Cfg<O, M>::NTN, 2) k_neighbour(DevOps ops, Dev
         for (int r = 0; r < 9; ++r) gq[r] = fmaf(X[k * XR + r], w, gq[r]);
       }
       float w6[6];
-      riemann_state(gq, sD + ee * ND + 4 + 11 * i, w6);
-      store_state(sFl + (ee * 4 * F + i * F + f) * FR, w6);
+      riemann_state(gq, sD + eel * ND + 4 + 11 * i, w6);
+      store_state(sFl + ee * C::FLS + (i * F + f) * FR, w6);
     }
     __syncthreads();
     if (valid) {
       constexpr int NS = (M > 0) ? 15 : 9;
       constexpr int NQ = C::NQ;
       // the DOF loads are issued first so their latency overlaps the F^ product
-      float* q = st.Q + (size_t)g * QS + b;
+      float* q = st.Q + (size_t)g * qs + (size_t)grp * (C::NQ * B * FG) + b * FG + j;
       float qv[NQ];
 #pragma unroll
-      for (int r = 0; r < NQ; ++r) qv[r] = q[r * B];
+      for (int r = 0; r < NQ; ++r) qv[r] = q[r * rs];
       float S[NS];
 #pragma unroll
       for (int r = 0; r < NS; ++r) S[r] = 0.f;
-      const float* nd = sD + e * ND;
-      project_faces<NS, F, B, FR>(sFl + e * 4 * F * FR, sFh, nd + 4, 11, nd[0], nd[1], nd[2], fmax, b, S);
+      const float* nd = sD + eb * ND;
+      project_faces<NS, F, B, FR>(sFl + e * C::FLS, sFh, nd + 4, 11, nd[0], nd[1], nd[2], fmax, b, S);
 #pragma unroll
-      for (int r = 0; r < 9; ++r) q[r * B] = qv[r] + S[r];
+      for (int r = 0; r < 9; ++r) q[r * rs] = qv[r] + S[r];
       if constexpr (M > 0) {
 #pragma unroll
         for (int l = 0; l < M; ++l)
 #pragma unroll
-          for (int r = 0; r < 6; ++r) q[(9 + 6 * l + r) * B] = qv[9 + 6 * l + r] + ph.omega[l] * S[NS - 6 + r];
+          for (int r = 0; r < 6; ++r) q[(9 + 6 * l + r) * rs] = qv[9 + 6 * l + r] + ph.omega[l] * S[NS - 6 + r];
       }
     }
   }
@@ -700,6 +736,7 @@ __global__ void __launch_bounds__(Cfg<O, M>::NTN, 2) k_neighbour(DevOps ops, Dev
 // ------------------------------------------------------------------ receivers
 struct RecvItem {
   int elem;        // internal element index
+  int sim;         // simulation (fused mode), else 0
   int phi_off;     // offset of phi values (B floats) in recv_phi
   int out_off;     // first output sample slot
   int n;           // samples in this step (<= 8)
@@ -710,10 +747,11 @@ struct RecvItem {
 // derivatives from Q (full state at the start of its step) and evaluates
 // sum_d tau^d/d! (d^dQ) phi(xi_r) for the 9 elastic quantities.
 template <int O, int M>
-__global__ void k_receivers(DevOps ops, const float* Q, const float* edata, const float* recv_phi,
-                            const RecvItem* items, float* out, float om0, float om1, float om2) {
+__global__ void k_receivers(DevOps ops, const float* Q, long long qs, int nsim, int fg, const float* edata,
+                            const float* recv_phi, const RecvItem* items, float* out, float om0, float om1,
+                            float om2) {
   using C = Cfg<O, M>;
-  constexpr int B = C::B, NQ = C::NQ, QS = C::QS;
+  constexpr int B = C::B, NQ = C::NQ;
   __shared__ float sA[B * 9];
   __shared__ float sRed[8][9][2];
   const RecvItem it = items[blockIdx.x];
@@ -724,7 +762,9 @@ __global__ void k_receivers(DevOps ops, const float* Q, const float* edata, cons
   float acc[8][9];
   const float phi = (b < B) ? recv_phi[it.phi_off + b] : 0.f;
 #pragma unroll
-  for (int r = 0; r < NQ; ++r) D[r] = (b < B) ? Q[(size_t)it.elem * QS + r * B + b] : 0.f;
+  for (int r = 0; r < NQ; ++r)
+    D[r] = (b < B) ? Q[(size_t)it.elem * qs + (size_t)(it.sim / fg) * NQ * B * fg + (r * B + b) * fg + it.sim % fg]
+                   : 0.f;
 #pragma unroll
   for (int s = 0; s < 8; ++s)
 #pragma unroll
@@ -790,47 +830,54 @@ __global__ void k_receivers(DevOps ops, const float* Q, const float* edata, cons
     const int s = threadIdx.x / 9, r = threadIdx.x % 9;
     float v = sRed[s][r][0];
     if (blockDim.x > 32) v += sRed[s][r][1];
-    out[(size_t)(it.out_off + s) * 9 + r] = v;
+    out[((size_t)(it.out_off + s) * nsim + it.sim) * 9 + r] = v;
   }
 }
 
 // ------------------------------------------------------------------ sources
 struct SrcItem {
   int elem;
+  int sim;         // simulation (fused mode), else 0
   int phi_off;
   float amp[6];    // -m0 m6 (int s dt) / |det J|
 };
 
 template <int O, int M>
-__global__ void k_sources(float* Q, const float* src_phi, const SrcItem* items, int n) {
+__global__ void k_sources(float* Q, long long qs, int fg, const float* src_phi, const SrcItem* items, int n) {
   using C = Cfg<O, M>;
-  constexpr int B = C::B, QS = C::QS;
+  constexpr int B = C::B, NQ = C::NQ;
   for (int s = 0; s < n; ++s) {
     const SrcItem it = items[s];
     for (int i = threadIdx.x; i < 6 * B; i += blockDim.x) {
       const int r = i / B, b = i % B;
-      Q[(size_t)it.elem * QS + r * B + b] += it.amp[r] * src_phi[it.phi_off + b];
+      Q[(size_t)it.elem * qs + (size_t)(it.sim / fg) * NQ * B * fg + (r * B + b) * fg + it.sim % fg] +=
+          it.amp[r] * src_phi[it.phi_off + b];
     }
     __syncthreads();
   }
 }
 
 // ------------------------------------------------------------------ energy
-// sum_k |det J_k| sum_b (rho |v_b|^2 / 2 + sigma_b : C^-1 sigma_b / 2), FP64; one partial
-// sum per block (blockDim.x = 256).
+// sum_k |det J_k| sum_b (rho |v_b|^2 / 2 + sigma_b : C^-1 sigma_b / 2), FP64, summed over
+// all simulations; one partial sum per block (blockDim.x = 256).
 template <int O, int M>
-__global__ void k_energy(const float* Q, const double* emat, int K, double* partial) {
+__global__ void k_energy(const float* Q, long long qs, int nsim, int fg, const double* emat, int K,
+                         double* partial) {
   using C = Cfg<O, M>;
-  constexpr int B = C::B, QS = C::QS;
+  constexpr int B = C::B, NQ = C::NQ;
   double local = 0.0;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)K * B; i += (size_t)gridDim.x * blockDim.x) {
-    const int k = (int)(i / B), b = (int)(i % B);
-    const float* q = Q + (size_t)k * QS;
+  const size_t per = (size_t)B * nsim;
+  const size_t rs = (size_t)B * fg;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)K * per; i += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(i / per);
+    const int bf = (int)(i % per);               // (group, mode, simulation in group)
+    const int grp = bf / (B * fg), rem = bf % (B * fg);
+    const float* q = Q + (size_t)k * qs + (size_t)grp * NQ * B * fg + rem;
     const double* em = emat + (size_t)k * 4;     // lam, mu, rho, |det J|
     const double lam = em[0], mu = em[1], rho = em[2];
     double s[6], v[3];
-    for (int r = 0; r < 6; ++r) s[r] = q[r * B + b];
-    for (int r = 0; r < 3; ++r) v[r] = q[(6 + r) * B + b];
+    for (int r = 0; r < 6; ++r) s[r] = q[r * rs];
+    for (int r = 0; r < 3; ++r) v[r] = q[(6 + r) * rs];
     const double tr = s[0] + s[1] + s[2];
     const double ss = s[0] * s[0] + s[1] * s[1] + s[2] * s[2] + 2.0 * (s[3] * s[3] + s[4] * s[4] + s[5] * s[5]);
     const double pot = 0.5 * (ss / (2.0 * mu) - lam / (2.0 * mu * (3.0 * lam + 2.0 * mu)) * tr * tr);

@@ -57,18 +57,19 @@ def flops_neighbour(o, m):
     return surf_g + flux + surf_h + B * (NQ + 2 * 6 * m)
 
 
-def bytes_predict(o, m, frac_finer=0.0, frac_coarser=0.0):
-    """HBM bytes of k_predict_local per element; frac_* are the shares of elements
-    that also write B2 (a finer neighbour) or B3 (a coarser one)."""
+def bytes_predict(o, m, frac_finer=0.0, frac_coarser=0.0, n_fused=1):
+    """HBM bytes of k_predict_local per element and simulation; frac_* are the shares of
+    elements that also write B2 (a finer neighbour) or B3 (a coarser one); the
+    per-element tables are shared by the n_fused simulations."""
     B, NQ = nbasis(o), 9 + 6 * m
     buf = 4 * 9 * B
-    return 4 * 2 * NQ * B + buf * (1.0 + frac_finer + 1.5 * frac_coarser) + 4 * 64 + 4
+    return 4 * 2 * NQ * B + buf * (1.0 + frac_finer + 1.5 * frac_coarser) + (4 * 64 + 4) / n_fused
 
 
-def bytes_neighbour(o, m):
-    """HBM bytes of k_neighbour per element."""
+def bytes_neighbour(o, m, n_fused=1):
+    """HBM bytes of k_neighbour per element and simulation."""
     B, NQ = nbasis(o), 9 + 6 * m
-    return 4 * 2 * NQ * B + 4 * 9 * B + 4 * 48 + 4 * 9
+    return 4 * 2 * NQ * B + 4 * 9 * B + (4 * 48 + 4 * 9) / n_fused
 
 
 def paper_flops_per_update():

@@ -26,6 +26,7 @@ def test_argument_errors_without_gpu(built):
     h = ctypes.c_void_p()
     assert L.lts_create(7, 0, 1, 0, ctypes.byref(h)) == binding.LTS_ERR_ARG
     assert L.lts_create(5, 2, 1, 0, ctypes.byref(h)) == binding.LTS_ERR_ARG
-    assert L.lts_create(5, 3, 16, 0, ctypes.byref(h)) == binding.LTS_ERR_ARG
+    for bad_fused in (0, 3, 6, 68):
+        assert L.lts_create(5, 3, bad_fused, 0, ctypes.byref(h)) == binding.LTS_ERR_ARG
     assert not h
     L.lts_destroy(None)

@@ -118,3 +118,23 @@ def test_periodic_mesh_neighbours_match_oracle():
     s.set_material(mat["rho"], mat["vp"], mat["vs"])
     cl, lam, sp = s.setup_clusters(1, 0.5)
     assert lam == 1.0 and np.all(cl == 0)
+
+
+def test_fused_handle_host_checks():
+    """A fused handle (16 simulations) sets up like a single one; sources take a
+    simulation index in [0, 16)."""
+    m = synth.graded_box(2, 2, 2, 100.0, 50.0)
+    s = binding.Solver(4, 3, device=-1, n_fused=16)
+    s.set_mesh(m["xyz"], m["tet"], m["face_bc"])
+    K = m["tet"].shape[0]
+    mat = synth.homogeneous(K)
+    s.set_material(mat["rho"], mat["vp"], mat["vs"], np.full(K, 80.0), np.full(K, 40.0), 0.1, 5.0)
+    x = m["xyz"].mean(axis=0)
+    m6 = np.array([1.0, 0, 0, 0, 0, 0])
+    s.add_point_source(x, m6, 2.0, 0.5, fused_idx=15)
+    for bad in (-1, 16):
+        with pytest.raises(binding.LtsError) as ei:
+            s.add_point_source(x, m6, 2.0, 0.5, fused_idx=bad)
+        assert ei.value.code == binding.LTS_ERR_ARG
+    cl, lam, sp = s.setup_clusters(2, 0.5)
+    assert cl.shape == (K,)
