@@ -188,6 +188,25 @@ int lts_kernel_stats(lts_t* h, double* ms_out2, int64_t* launches_out2, int64_t*
  * (source and receiver schedules) and device->host in lts_get_seismogram. */
 int lts_transfer_bytes(lts_t* h, int64_t* h2d, int64_t* d2h);
 
+/* Contraction engine of the time and volume kernels (Sec. IV: the products of the DOFs
+ * with the stiffness matrices K_c). LTS_CONTRACT_FP32: FP32 CUDA cores (default).
+ * LTS_CONTRACT_TF32X3: 5th-generation tensor cores, every operand split into two tf32
+ * parts and the three leading products accumulated in FP32 (FP32-level accuracy).
+ * LTS_CONTRACT_TF32: tensor cores on the rounded tf32 parts only (about 1e-3 relative
+ * error per product). The surface kernels always run on CUDA cores. Takes effect at the
+ * next lts_advance. Errors: LTS_ERR_ARG for an unknown mode or a tensor-core mode the
+ * handle's shape has no kernel for (order 3 with one simulation). A tensor-core wait that
+ * gives up (bounded, about one second) makes the next synchronising call return
+ * LTS_ERR_TIMEOUT. */
+enum { LTS_CONTRACT_FP32 = 0, LTS_CONTRACT_TF32X3 = 1, LTS_CONTRACT_TF32 = 2 };
+int lts_set_contraction(lts_t* h, int mode);
+
+/* Launch shape of the three main kernels, for reports: ctas_per_sm[3] (resident CTAs per
+ * SM from the occupancy query; 0 where the kernel does not exist for this shape) and
+ * threads[3] (threads per CTA), in the order predict+local (CUDA cores), neighbour,
+ * predict+local (tensor cores). Either array may be NULL. */
+int lts_launch_config(lts_t* h, int* ctas_per_sm, int* threads);
+
 /* Energy of a caller-owned DOF array, for callers that cannot allocate device memory.
  * The paper has no counterpart: this is an integration aid. Some callers cannot call
  * cudaMalloc once they are running: their device memory belongs to another framework's

@@ -49,6 +49,8 @@ _SIGS = {
     "lts_set_profiling": (_I, [_P, _I]),
     "lts_kernel_stats": (_I, [_P, _P, _P, _P]),
     "lts_transfer_bytes": (_I, [_P, _P, _P]),
+    "lts_set_contraction": (_I, [_P, _I]),
+    "lts_launch_config": (_I, [_P, _P, _P]),
     "lts_energy_noalloc": (_I, [_I, _I, _P, _P, _L, _P, _P]),
     "lts_reference_operators": (_I, [_I, _P, _P, _P]),
     "lts_eval_basis": (_I, [_I, _L, _P, _P]),
@@ -289,6 +291,18 @@ class Solver:
         a, b = ctypes.c_int64(), ctypes.c_int64()
         self._check(lib().lts_transfer_bytes(self._h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    def launch_config(self):
+        """Resident CTAs per SM and threads per CTA of (predict, neighbour, predict on tensor cores)."""
+        c = np.zeros(3, dtype=np.int32)
+        t = np.zeros(3, dtype=np.int32)
+        self._check(lib().lts_launch_config(self._h, _ptr(c), _ptr(t)))
+        return dict(ctas_per_sm=c.tolist(), threads=t.tolist())
+
+    def set_contraction(self, mode):
+        """'fp32' (CUDA cores), 'tf32x3' (tensor cores, split tf32) or 'tf32' (tensor cores)."""
+        code = {"fp32": 0, "tf32x3": 1, "tf32": 2}[mode]
+        self._check(lib().lts_set_contraction(self._h, code))
 
     def set_profiling(self, on=True):
         self._check(lib().lts_set_profiling(self._h, 1 if on else 0))

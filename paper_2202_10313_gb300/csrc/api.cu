@@ -69,6 +69,7 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 struct lts_solver {
   int order = 0, nmech = 0, device = 0;
   int nsim = 1;                             // fused simulations
+  int contraction = LTS_CONTRACT_FP32;
   std::string err;
   Launchers L{};
   lts::RefOps ops;
@@ -98,6 +99,7 @@ struct lts_solver {
   DevState dst{};
   double* d_emat = nullptr;
   double* d_partial = nullptr;
+  int* d_err = nullptr;                     // set by a kernel whose bounded wait gave up
   float* d_recv_phi = nullptr;
   float* d_src_phi = nullptr;
   int n_partial = 1024;
@@ -138,7 +140,7 @@ int run(lts_t* h, const std::function<void()>& fn) {
 }
 
 struct Layout {
-  size_t Q, B1, B2, B3, edata, ndata, nbr, ncode, meta, emat, partial, K, Ft, Fh, Fb, rphi, sphi, total;
+  size_t Q, B1, B2, B3, edata, ndata, nbr, ncode, meta, emat, partial, err, K, Ft, Fh, Fb, rphi, sphi, total;
 };
 
 // Element strides (floats) of Q and of the LTS buffers: [group][q][b][G] per element with
@@ -169,6 +171,7 @@ Layout layout_of(const lts_solver* h, int64_t K) {
   L.meta = take(sizeof(int) * K);
   L.emat = take(sizeof(double) * K * 4);
   L.partial = take(sizeof(double) * h->n_partial);
+  L.err = take(sizeof(int));
   L.K = take(sizeof(float) * 3 * X.B * X.B);
   L.Ft = take(sizeof(float) * 4 * X.B * X.F);
   L.Fh = take(sizeof(float) * 4 * X.F * X.B);
@@ -352,6 +355,7 @@ void setup_device(lts_solver* h) {
   h->dst.meta = reinterpret_cast<int*>(base + Lo.meta);
   h->d_emat = reinterpret_cast<double*>(base + Lo.emat);
   h->d_partial = reinterpret_cast<double*>(base + Lo.partial);
+  h->d_err = reinterpret_cast<int*>(base + Lo.err);
   h->dops.K = reinterpret_cast<float*>(base + Lo.K);
   h->dops.Ft = reinterpret_cast<float*>(base + Lo.Ft);
   h->dops.Fh = reinterpret_cast<float*>(base + Lo.Fh);
@@ -368,6 +372,7 @@ void setup_device(lts_solver* h) {
   ck(cudaMemset(h->dst.B1, 0, sizeof(float) * K * h->dst.bs), "memset B1");
   ck(cudaMemset(h->dst.B2, 0, sizeof(float) * K * h->dst.bs), "memset B2");
   ck(cudaMemset(h->dst.B3, 0, sizeof(float) * K * h->dst.bs), "memset B3");
+  ck(cudaMemset(h->d_err, 0, sizeof(int)), "memset error word");
   up(h->dst.edata, edata.data(), sizeof(float) * edata.size());
   up(h->dst.ndata, ndata.data(), sizeof(float) * ndata.size());
   up(h->dst.nbr, nbr.data(), sizeof(int) * nbr.size());
@@ -420,6 +425,15 @@ void ensure_capacity(void** ptr, size_t* cap, size_t need, size_t elem) {
   }
   *ptr = p;
   *cap = nc;
+}
+
+// Raises LTS_ERR_TIMEOUT if a kernel reported a bounded wait that gave up (the device
+// must be synchronised).
+void check_device_error(lts_solver* h) {
+  if (!h->d_err) return;
+  int v = 0;
+  ck(cudaMemcpy(&v, h->d_err, sizeof(int), cudaMemcpyDeviceToHost), "read error word");
+  if (v != 0) fail(LTS_ERR_TIMEOUT, "a tensor-core completion wait gave up");
 }
 
 double ricker(double t, double f0, double t0) {
@@ -536,7 +550,9 @@ void advance_steps(lts_solver* h, int64_t n_finest, cudaStream_t stream) {
   h->h2d_bytes += (int64_t)(ritems.size() * sizeof(RecvItem) + sitems.size() * sizeof(SrcItem));
   h->seis_used = seis_need;
   // ---- launches
-  const int grid_cap_p = std::max(1, h->num_sms * std::max(1, X.blocks_predict));
+  const bool use_tc = h->contraction != LTS_CONTRACT_FP32;
+  const int passes = h->contraction == LTS_CONTRACT_TF32X3 ? 3 : 1;
+  const int grid_cap_p = std::max(1, h->num_sms * std::max(1, use_tc ? X.blocks_predict_tc : X.blocks_predict));
   const int grid_cap_n = std::max(1, h->num_sms * std::max(1, X.blocks_neighbour));
   for (const Phase& ph : plan) {
     PhaseArgs pa = base;
@@ -559,6 +575,8 @@ void advance_steps(lts_solver* h, int64_t n_finest, cudaStream_t stream) {
     if (h->profiling) ck(cudaEventRecord(next_event(h), stream), "event record");
     if (ph.kind == 0)
       X.neighbour(h->dops, h->dst, pa, std::min(nb, grid_cap_n), stream);
+    else if (use_tc)
+      X.predict_tc(h->dops, h->dst, pa, std::min(nb, grid_cap_p), passes, h->d_err, stream);
     else
       X.predict(h->dops, h->dst, pa, std::min(nb, grid_cap_p), stream);
     ++h->launches;
@@ -845,6 +863,7 @@ int lts_get_dofs(lts_t* h, double* dofs) {
     ck(cudaSetDevice(h->device), "cudaSetDevice");
     ck(cudaDeviceSynchronize(), "synchronize");
     ck(cudaMemcpy(q.data(), h->dst.Q, q.size() * sizeof(float), cudaMemcpyDeviceToHost), "download Q");
+    check_device_error(h);
     for (int64_t k = 0; k < K; ++k) unpack_row(h, &q[h->iperm[k] * qs], K, k, dofs);
   });
 }
@@ -874,6 +893,7 @@ int lts_get_dofs_subset(lts_t* h, int64_t n, const int64_t* elems, double* dofs)
     std::vector<float> row(qs);
     ck(cudaSetDevice(h->device), "cudaSetDevice");
     ck(cudaDeviceSynchronize(), "synchronize");
+    check_device_error(h);
     for (int64_t i = 0; i < n; ++i) {
       const int64_t k = elems[i];
       if (k < 0 || k >= h->mesh.K) fail(LTS_ERR_ARG, "element index out of range");
@@ -956,6 +976,7 @@ int lts_get_seismogram(lts_t* h, int id, int fused_idx, double* t_out, double* v
     std::vector<float> buf((hi - lo) * 9 * F);
     ck(cudaMemcpy(buf.data(), h->d_seis + lo * 9 * F, buf.size() * sizeof(float), cudaMemcpyDeviceToHost),
        "download seismogram");
+    check_device_error(h);
     h->d2h_bytes += (int64_t)(buf.size() * sizeof(float));
     for (int64_t i = 0; i < m; ++i) {
       if (t_out) t_out[i] = r.t[i];
@@ -975,6 +996,7 @@ int lts_energy(lts_t* h, double* e) {
     ck(cudaGetLastError(), "energy kernel");
     std::vector<double> part(nb);
     ck(cudaMemcpy(part.data(), h->d_partial, nb * sizeof(double), cudaMemcpyDeviceToHost), "download energy");
+    check_device_error(h);
     double s = 0.0;
     for (double v : part) s += v;
     *e = s;
@@ -1028,6 +1050,32 @@ int lts_kernel_stats(lts_t* h, double* ms_out, int64_t* launches_out, int64_t* e
     h->ev_used = 0;
     h->ev_kind.clear();
     h->ev_elems.clear();
+  });
+}
+
+int lts_launch_config(lts_t* h, int* ctas_per_sm, int* threads) {
+  return run(h, [&] {
+    const Launchers& X = h->L;
+    const bool tc = X.predict_tc != nullptr;
+    if (ctas_per_sm) {
+      ctas_per_sm[0] = X.blocks_predict;
+      ctas_per_sm[1] = X.blocks_neighbour;
+      ctas_per_sm[2] = tc ? X.blocks_predict_tc : 0;
+    }
+    if (threads) {
+      threads[0] = X.NT;
+      threads[1] = X.NTN;
+      threads[2] = tc ? X.NT : 0;
+    }
+  });
+}
+
+int lts_set_contraction(lts_t* h, int mode) {
+  return run(h, [&] {
+    if (mode != LTS_CONTRACT_FP32 && mode != LTS_CONTRACT_TF32X3 && mode != LTS_CONTRACT_TF32)
+      fail(LTS_ERR_ARG, "unknown contraction mode");
+    if (mode != LTS_CONTRACT_FP32 && !h->L.predict_tc) fail(LTS_ERR_ARG, "no tensor-core kernel for this shape");
+    h->contraction = mode;
   });
 }
 

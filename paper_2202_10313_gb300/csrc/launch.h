@@ -3,17 +3,23 @@
 #include <cuda_runtime.h>
 
 #include "kernels.cuh"
+#include "kernels_tc.cuh"
 
 namespace ltsdev {
 
 struct Launchers {
-  int B, F, NQ, QS, BUFS, NE, NT, NEN;
+  int B, F, NQ, QS, BUFS, NE, NT, NEN, NTN;
   int FG;                                    // simulations per CTA in fused mode (1: single)
   size_t smem_predict, smem_neighbour;
   int blocks_predict, blocks_neighbour;      // resident CTAs per SM (filled by init)
   cudaError_t (*init)(Launchers*);
   void (*predict)(const DevOps&, const DevState&, const PhaseArgs&, int grid, cudaStream_t);
   void (*neighbour)(const DevOps&, const DevState&, const PhaseArgs&, int grid, cudaStream_t);
+  // tensor-core predict + local kernel (nullptr where the shape has no tensor-core path);
+  // passes 3: split-tf32 products, 1: tf32; err: device word set when a bounded wait gave up
+  void (*predict_tc)(const DevOps&, const DevState&, const PhaseArgs&, int grid, int passes, int* err, cudaStream_t);
+  size_t smem_predict_tc;
+  int blocks_predict_tc;
   // fg: simulation group size of the layout (FG of the fused instantiation, 1 for one simulation)
   void (*receivers)(const DevOps&, const float* Q, long long qs, int nsim, int fg, const float* edata,
                     const float* phi, const RecvItem* items, float* out, const float* omega, int n, cudaStream_t);
@@ -25,16 +31,33 @@ struct Launchers {
 template <int O, int M, int FG>
 struct Impl {
   using C = Cfg<O, M, FG>;
+  // Dynamic shared memory limit; max_carveout also asks for the largest shared-memory
+  // carveout (the CUDA-core kernels keep the default: their gathers live on L1).
+  template <typename K>
+  static cudaError_t smem_attrs(K kernel, size_t bytes, bool max_carveout) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess || !max_carveout) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  }
   static cudaError_t init(Launchers* L) {
-    cudaError_t e = cudaFuncSetAttribute(k_predict_local<O, M, FG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)L->smem_predict);
+    cudaError_t e = smem_attrs(k_predict_local<O, M, FG>, L->smem_predict, false);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_neighbour<O, M, FG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)L->smem_neighbour);
+    e = smem_attrs(k_neighbour<O, M, FG>, L->smem_neighbour, false);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L->blocks_predict, k_predict_local<O, M, FG>, C::NT,
                                                       L->smem_predict);
     if (e != cudaSuccess) return e;
+    if constexpr (TcCfg<O, M, FG>::SUPPORTED) {
+      e = smem_attrs(k_predict_tc<O, M, FG>, L->smem_predict_tc, true);
+      if (e != cudaSuccess) return e;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L->blocks_predict_tc, k_predict_tc<O, M, FG>, C::NT,
+                                                        L->smem_predict_tc);
+      if (e != cudaSuccess) return e;
+      // the occupancy query answers one CTA for this kernel although registers and shared
+      // memory admit two; the persistent grid is sized for two (CTAs are independent and
+      // two fit the 512 tensor-memory columns)
+      L->blocks_predict_tc = 2;
+    }
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L->blocks_neighbour, k_neighbour<O, M, FG>, C::NTN,
                                                          L->smem_neighbour);
   }
@@ -43,6 +66,11 @@ struct Impl {
   }
   static void neighbour(const DevOps& o, const DevState& s, const PhaseArgs& p, int grid, cudaStream_t st) {
     k_neighbour<O, M, FG><<<grid, C::NTN, C::N_TOTAL * sizeof(float), st>>>(o, s, p);
+  }
+  static void predict_tc(const DevOps& o, const DevState& s, const PhaseArgs& p, int grid, int passes, int* err,
+                         cudaStream_t st) {
+    if constexpr (TcCfg<O, M, FG>::SUPPORTED)
+      k_predict_tc<O, M, FG><<<grid, C::NT, TcCfg<O, M, FG>::SMEM_BYTES, st>>>(o, s, p, passes, err);
   }
   static void receivers(const DevOps& o, const float* Q, long long qs, int nsim, int fg, const float* ed,
                         const float* phi, const RecvItem* it, float* out, const float* om, int n, cudaStream_t st) {
@@ -66,10 +94,15 @@ struct Impl {
     L.NE = C::NE;
     L.NT = C::NT;
     L.NEN = C::NEN;
+    L.NTN = C::NTN;
     L.smem_predict = C::P_TOTAL * sizeof(float);
     L.smem_neighbour = C::N_TOTAL * sizeof(float);
     L.init = &init;
     L.predict = &predict;
+    if constexpr (TcCfg<O, M, FG>::SUPPORTED) {
+      L.predict_tc = &predict_tc;
+      L.smem_predict_tc = TcCfg<O, M, FG>::SMEM_BYTES;
+    }
     L.neighbour = &neighbour;
     L.receivers = &receivers;
     L.sources = &sources;

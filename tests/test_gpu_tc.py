@@ -1,0 +1,123 @@
+"""Tensor-core contractions (tcgen05, split tf32): the time and volume kernels' products
+with the stiffness matrices run on the tensor cores. With three passes the result must
+meet the same bar as the FP32 CUDA-core path (relative L2 <= 1e-4 per quantity group
+against the FP64 oracle) and agree with it to FP32 rounding; the single tf32 pass is
+reported against the same oracle with its own, looser bound."""
+import numpy as np
+import pytest
+
+from paper_2202_10313_gb300 import binding, build, synth
+from gpu_common import initial_field, make_pair, rel_l2_groups
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+
+
+def _box():
+    m = synth.permute_vertex_order(synth.graded_box(5, 5, 3, 250.0, 125.0, seed=12), seed=2)
+    return m, synth.random_layers(m, n_layers=3, seed=5)
+
+
+@pytest.mark.parametrize("order,n_mech", [(4, 0), (4, 3), (5, 0), (5, 3)])
+def test_tf32x3_lts_matches_oracle(order, n_mech):
+    """Graded box, 3 clusters from the lambda search, two macro steps, smooth initial
+    field plus a point source: DOFs against the oracle."""
+    m, mat = _box()
+    gpu, ora, _ = make_pair(order, n_mech, m, mat)
+    xs, m6 = np.array([610.0, 640.0, -260.0]), np.array([0.2, -0.4, 0.2, 1.0, 0.1, -0.3])
+    gpu.add_point_source(xs, m6, 8.0, 0.06, 1e12)
+    ora.add_point_source(xs, m6, 8.0, 0.06, 1e12)
+    gpu.set_contraction("tf32x3")
+    cl, lam, _ = gpu.setup_clusters(3, 0.5)
+    ora.setup_clusters(3, 0.5)
+    assert np.array_equal(cl, ora.clusters)
+    fn = initial_field(ora.nq, [600.0, 700.0, -300.0], 400.0)
+    gpu.project_initial(fn)
+    ora.project(fn)
+    gpu.advance_steps(8)
+    ora.run_lts(8)
+    err = rel_l2_groups(gpu.get_dofs(), ora.Q, ora.nq)
+    for k, v in err.items():
+        assert v <= TOL, err
+
+
+def test_tf32x3_agrees_with_fp32_cuda_cores_and_tf32_is_bounded():
+    """Same inputs on the three engines: split tf32 within FP32 rounding of the CUDA-core
+    path; plain tf32 stays within 5e-3 of the oracle after 8 finest steps."""
+    m, mat = _box()
+    K = m["tet"].shape[0]
+    d0 = synth.random_dofs(K, 27, 35, seed=6)
+    out = {}
+    for mode in ("fp32", "tf32x3", "tf32"):
+        gpu, ora, _ = make_pair(5, 3, m, mat)
+        gpu.set_contraction(mode)
+        gpu.setup_clusters(3, 0.5)
+        gpu.set_dofs(d0)
+        gpu.advance_steps(8)
+        out[mode] = gpu.get_dofs()
+        gpu.close()
+    ora.setup_clusters(3, 0.5)
+    ora.Q = d0.copy()
+    ora.run_lts(8)
+    e32 = rel_l2_groups(out["fp32"], ora.Q, 27)["all"]
+    e3 = rel_l2_groups(out["tf32x3"], ora.Q, 27)["all"]
+    e1 = rel_l2_groups(out["tf32"], ora.Q, 27)["all"]
+    diff = rel_l2_groups(out["tf32x3"], out["fp32"], 27)["all"]
+    print("rel L2 vs oracle: fp32 %.2e, tf32x3 %.2e, tf32 %.2e; tf32x3 vs fp32 %.2e" % (e32, e3, e1, diff))
+    assert e3 <= TOL and diff <= 1e-5
+    assert e1 <= 5e-3
+
+
+def test_tf32x3_fused_simulations_match_oracle():
+    """Fused run (8 simulations, one source each) on the tensor cores against the oracle
+    run of every simulation."""
+    m = synth.permute_vertex_order(synth.graded_box(4, 4, 3, 250.0, 125.0, seed=31), seed=4)
+    mat = synth.random_layers(m, n_layers=3, seed=9)
+    F = 8
+    g = binding.Solver(5, 3, device=0, n_fused=F)
+    g.set_mesh(m["xyz"], m["tet"], m["face_bc"])
+    g.set_material(mat["rho"], mat["vp"], mat["vs"], mat["qp"], mat["qs"], 0.1, 5.0)
+    lo, hi = m["xyz"].min(axis=0), m["xyz"].max(axis=0)
+    pos, m6, f0 = synth.random_sources(F, lo + 0.15 * (hi - lo), hi - 0.15 * (hi - lo), f0_range=(4.0, 8.0), seed=5)
+    for f in range(F):
+        g.add_point_source(pos[f], m6[f], f0[f], 0.1, 1e12, fused_idx=f)
+    g.set_contraction("tf32x3")
+    cl, _, _ = g.setup_clusters(3, 0.5)
+    K = m["tet"].shape[0]
+    d0 = np.stack([synth.random_dofs(K, 27, 35, seed=40 + f, stress_scale=1e3) for f in range(F)])
+    g.set_dofs(d0)
+    g.advance_steps(8)
+    got = g.get_dofs()
+    for f in range(F):
+        _, ora, _ = make_pair(5, 3, m, mat)
+        ora.add_point_source(pos[f], m6[f], f0[f], 0.1, 1e12)
+        ora.setup_clusters(3, 0.5)
+        assert np.array_equal(cl, ora.clusters)
+        ora.Q = d0[f].copy()
+        ora.run_lts(8)
+        err = rel_l2_groups(got[f], ora.Q, 27)
+        for k, v in err.items():
+            assert v <= TOL, (f, err)
+
+
+def test_tensor_core_mode_availability():
+    """Order 3 with one simulation has no tensor-core kernel (the accumulator and the
+    operators would need more than 256 tensor-memory columns); fused order 3 has one."""
+    m = synth.graded_box(2, 2, 2, 100.0, 50.0)
+    mat = synth.homogeneous(m["tet"].shape[0])
+    s, _, _ = make_pair(3, 0, m, mat)
+    with pytest.raises(binding.LtsError) as ei:
+        s.set_contraction("tf32x3")
+    assert ei.value.code == binding.LTS_ERR_ARG
+    f = binding.Solver(3, 0, device=0, n_fused=4)
+    f.set_contraction("tf32x3")
+    with pytest.raises(KeyError):
+        f.set_contraction("bf16")
