@@ -198,8 +198,12 @@ def run_ours(args, rank, world, local_rank):
     for r in recs:
         s.add_receiver(r, dt_rec)
     s.use_torch_memory(NCLUSTERS)
-    s.set_contraction(args.contraction)
+    if args.contraction != "auto":
+        s.set_contraction(args.contraction)
     _, lam, speedup = s.setup_clusters(NCLUSTERS, CFL)
+    tuned = None
+    if args.contraction == "auto":
+        tuned = s.autotune(allow_tf32=False, stream=torch.cuda.current_stream())
     info = s.info()
     period = 2 ** (NCLUSTERS - 1)
     per_macro = int(info["updates_per_macro"].sum()) * F      # simulation element updates
@@ -278,7 +282,8 @@ def run_ours(args, rank, world, local_rank):
     line = {
         "metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "contraction": args.contraction, "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "contraction": tuned["contraction"] if tuned else args.contraction, "autotune": tuned,
         "config": {"workload": "anelastic O5 m3 LTS, %d jittered graded tets, Nc=%d, lambda=%.2f, CFL %.1f, "
                                "%s, 64 receivers; step = 1 macro step (%d finest steps)"
                                % (K, NCLUSTERS, lam, CFL, srcs, period),
@@ -321,8 +326,9 @@ def main():
     ap.add_argument("--medium", action="store_true", help="262k-tet mesh (profiling captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fused", type=int, default=1, help="fused simulations (multiple of 4; 1 = single)")
-    ap.add_argument("--contraction", default="fp32", choices=["fp32", "tf32x3", "tf32"],
-                    help="engine of the time/volume contractions: FP32 CUDA cores or tensor cores")
+    ap.add_argument("--contraction", default="auto", choices=["auto", "fp32", "tf32x3", "tf32"],
+                    help="engine of the time/volume contractions: FP32 CUDA cores or tensor cores; auto runs "
+                         "the autotuner over the FP32-accurate engines and the grid shapes")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

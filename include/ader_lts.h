@@ -201,6 +201,20 @@ int lts_transfer_bytes(lts_t* h, int64_t* h2d, int64_t* d2h);
 enum { LTS_CONTRACT_FP32 = 0, LTS_CONTRACT_TF32X3 = 1, LTS_CONTRACT_TF32 = 2 };
 int lts_set_contraction(lts_t* h, int mode);
 
+/* Autotuner over launch configurations: contraction engine (FP32 CUDA cores, split-tf32
+ * tensor cores, and plain tf32 only if allow_tf32) x resident CTAs per SM the predict and
+ * neighbour grids are sized for (the occupancy maximum and one fewer). Each candidate
+ * advances one macro step from a device-side snapshot of the state, timed with CUDA
+ * events on `cuda_stream` after one untimed warm-up step; the state (DOFs, LTS buffers,
+ * time, receiver samples) is restored exactly after every trial, so the simulation is
+ * unchanged. The fastest candidate becomes the handle's configuration. Outputs (each may
+ * be NULL): chosen[3] = (engine, predict CTAs/SM, neighbour CTAs/SM), best_ms, and for
+ * the first `cap` candidates table[cap][4] = (engine, CTAs/SM, CTAs/SM, ms); *n_out the
+ * number of candidates. Needs device memory for one copy of the state (else
+ * LTS_ERR_OOM); synchronises the stream. */
+int lts_autotune(lts_t* h, int allow_tf32, void* cuda_stream, int* chosen, double* best_ms, double* table,
+                 int cap, int* n_out);
+
 /* Launch shape of the three main kernels, for reports: ctas_per_sm[3] (resident CTAs per
  * SM from the occupancy query; 0 where the kernel does not exist for this shape) and
  * threads[3] (threads per CTA), in the order predict+local (CUDA cores), neighbour,

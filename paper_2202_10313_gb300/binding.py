@@ -51,6 +51,7 @@ _SIGS = {
     "lts_transfer_bytes": (_I, [_P, _P, _P]),
     "lts_set_contraction": (_I, [_P, _I]),
     "lts_launch_config": (_I, [_P, _P, _P]),
+    "lts_autotune": (_I, [_P, _I, _P, _P, _P, _P, _I, _P]),
     "lts_energy_noalloc": (_I, [_I, _I, _P, _P, _L, _P, _P]),
     "lts_reference_operators": (_I, [_I, _P, _P, _P]),
     "lts_eval_basis": (_I, [_I, _L, _P, _P]),
@@ -298,6 +299,21 @@ class Solver:
         t = np.zeros(3, dtype=np.int32)
         self._check(lib().lts_launch_config(self._h, _ptr(c), _ptr(t)))
         return dict(ctas_per_sm=c.tolist(), threads=t.tolist())
+
+    def autotune(self, allow_tf32=False, stream=None):
+        """Time the candidate launch configurations on a snapshot of the state and keep the
+        fastest; returns the choice and every candidate's milliseconds per macro step."""
+        chosen = np.zeros(3, dtype=np.int32)
+        best = ctypes.c_double()
+        table = np.zeros((32, 4))
+        n = ctypes.c_int()
+        self._check(lib().lts_autotune(self._h, 1 if allow_tf32 else 0, _stream_handle(stream), _ptr(chosen),
+                                       ctypes.byref(best), _ptr(table), 32, ctypes.byref(n)))
+        names = {0: "fp32", 1: "tf32x3", 2: "tf32"}
+        rows = [dict(contraction=names[int(r[0])], ctas_predict=int(r[1]), ctas_neighbour=int(r[2]), ms=float(r[3]))
+                for r in table[:min(n.value, 32)]]
+        return dict(contraction=names[int(chosen[0])], ctas_predict=int(chosen[1]), ctas_neighbour=int(chosen[2]),
+                    best_ms=best.value, candidates=rows)
 
     def set_contraction(self, mode):
         """'fp32' (CUDA cores), 'tf32x3' (tensor cores, split tf32) or 'tf32' (tensor cores)."""

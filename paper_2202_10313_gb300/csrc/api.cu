@@ -1,5 +1,6 @@
 // C ABI of the solver: set-up tables, device state and the clustered-LTS schedule.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <functional>
@@ -70,6 +71,7 @@ struct lts_solver {
   int order = 0, nmech = 0, device = 0;
   int nsim = 1;                             // fused simulations
   int contraction = LTS_CONTRACT_FP32;
+  int ctas_predict = 0, ctas_neighbour = 0;  // resident CTAs per SM the grids are sized for (0: occupancy)
   std::string err;
   Launchers L{};
   lts::RefOps ops;
@@ -552,8 +554,10 @@ void advance_steps(lts_solver* h, int64_t n_finest, cudaStream_t stream) {
   // ---- launches
   const bool use_tc = h->contraction != LTS_CONTRACT_FP32;
   const int passes = h->contraction == LTS_CONTRACT_TF32X3 ? 3 : 1;
-  const int grid_cap_p = std::max(1, h->num_sms * std::max(1, use_tc ? X.blocks_predict_tc : X.blocks_predict));
-  const int grid_cap_n = std::max(1, h->num_sms * std::max(1, X.blocks_neighbour));
+  const int maxp = std::max(1, use_tc ? X.blocks_predict_tc : X.blocks_predict);
+  const int maxn = std::max(1, X.blocks_neighbour);
+  const int grid_cap_p = h->num_sms * (h->ctas_predict > 0 ? std::min(h->ctas_predict, maxp) : maxp);
+  const int grid_cap_n = h->num_sms * (h->ctas_neighbour > 0 ? std::min(h->ctas_neighbour, maxn) : maxn);
   for (const Phase& ph : plan) {
     PhaseArgs pa = base;
     pa.begin = 0;
@@ -1067,6 +1071,120 @@ int lts_launch_config(lts_t* h, int* ctas_per_sm, int* threads) {
       threads[1] = X.NTN;
       threads[2] = tc ? X.NT : 0;
     }
+  });
+}
+
+int lts_autotune(lts_t* h, int allow_tf32, void* cuda_stream, int* chosen, double* best_ms, double* table, int cap,
+                 int* n_out) {
+  return run(h, [&] {
+    if (!h->ready) fail(LTS_ERR_STATE, "clusters not set up");
+    if (cap < 0 || (cap > 0 && !table)) fail(LTS_ERR_ARG, "bad table arguments");
+    ck(cudaSetDevice(h->device), "cudaSetDevice");
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    const Launchers& X = h->L;
+    const int64_t K = h->mesh.K;
+    const size_t qbytes = sizeof(float) * K * h->dst.qs, bbytes = sizeof(float) * K * h->dst.bs;
+    void* snap = nullptr;
+    if (cudaMalloc(&snap, qbytes + 3 * bbytes) != cudaSuccess) {
+      cudaGetLastError();
+      fail(LTS_ERR_OOM, "no device memory for the autotune snapshot");
+    }
+    struct Free {
+      void* p;
+      ~Free() { cudaFree(p); }
+    } free_snap{snap};
+    char* sp = static_cast<char*>(snap);
+    float* dev[4] = {h->dst.Q, h->dst.B1, h->dst.B2, h->dst.B3};
+    const size_t sz[4] = {qbytes, bbytes, bbytes, bbytes};
+    auto copy_state = [&](bool save) {
+      size_t off = 0;
+      for (int i = 0; i < 4; ++i) {
+        ck(cudaMemcpyAsync(save ? static_cast<void*>(sp + off) : static_cast<void*>(dev[i]),
+                           save ? static_cast<const void*>(dev[i]) : static_cast<const void*>(sp + off), sz[i],
+                           cudaMemcpyDeviceToDevice, stream),
+           "autotune state copy");
+        off += sz[i];
+      }
+    };
+    // host-side state that a trial step changes
+    const int64_t s0 = h->s_now, l0 = h->launches, hb0 = h->h2d_bytes;
+    const size_t seis0 = h->seis_used;
+    std::vector<size_t> nrec(h->receivers.size());
+    for (size_t i = 0; i < nrec.size(); ++i) nrec[i] = h->receivers[i].t.size();
+    auto restore_host = [&] {
+      h->s_now = s0;
+      h->launches = l0;
+      h->h2d_bytes = hb0;
+      h->seis_used = seis0;
+      for (size_t i = 0; i < nrec.size(); ++i) {
+        h->receivers[i].t.resize(nrec[i]);
+        h->receivers[i].slot.resize(nrec[i]);
+      }
+    };
+    const bool prof = h->profiling;
+    h->profiling = false;
+    // candidates: engine x predict CTAs/SM x neighbour CTAs/SM (the occupancy maximum and
+    // one fewer)
+    std::vector<std::array<int, 3>> cand;
+    std::vector<int> engines{LTS_CONTRACT_FP32};
+    if (X.predict_tc) engines.push_back(LTS_CONTRACT_TF32X3);
+    if (X.predict_tc && allow_tf32) engines.push_back(LTS_CONTRACT_TF32);
+    for (int eng : engines) {
+      const int mp = std::max(1, eng == LTS_CONTRACT_FP32 ? X.blocks_predict : X.blocks_predict_tc);
+      const int mn = std::max(1, X.blocks_neighbour);
+      for (int cp = mp; cp >= std::max(1, mp - 1); --cp)
+        for (int cn = mn; cn >= std::max(1, mn - 1); --cn) cand.push_back({eng, cp, cn});
+    }
+    cudaEvent_t ev[2];
+    ck(cudaEventCreate(&ev[0]), "cudaEventCreate");
+    ck(cudaEventCreate(&ev[1]), "cudaEventCreate");
+    struct Ev {
+      cudaEvent_t* e;
+      ~Ev() {
+        cudaEventDestroy(e[0]);
+        cudaEventDestroy(e[1]);
+      }
+    } free_ev{ev};
+    copy_state(true);
+    const int64_t period = int64_t(1) << (h->nc - 1);
+    double best = 1e300;
+    int bi = 0;
+    // trial -1 warms caches and clocks with the first candidate and is not counted
+    for (int i = -1; i < (int)cand.size(); ++i) {
+      const auto& c = cand[std::max(i, 0)];
+      h->contraction = c[0];
+      h->ctas_predict = c[1];
+      h->ctas_neighbour = c[2];
+      ck(cudaEventRecord(ev[0], stream), "event record");
+      advance_steps(h, period, stream);
+      ck(cudaEventRecord(ev[1], stream), "event record");
+      ck(cudaEventSynchronize(ev[1]), "event sync");
+      float ms = 0.f;
+      ck(cudaEventElapsedTime(&ms, ev[0], ev[1]), "event time");
+      check_device_error(h);
+      copy_state(false);
+      restore_host();
+      if (i < 0) continue;
+      if (i < cap) {
+        table[4 * i + 0] = c[0];
+        table[4 * i + 1] = c[1];
+        table[4 * i + 2] = c[2];
+        table[4 * i + 3] = ms;
+      }
+      if (ms < best) {
+        best = ms;
+        bi = i;
+      }
+    }
+    ck(cudaStreamSynchronize(stream), "synchronize");
+    h->profiling = prof;
+    h->contraction = cand[bi][0];
+    h->ctas_predict = cand[bi][1];
+    h->ctas_neighbour = cand[bi][2];
+    if (chosen)
+      for (int i = 0; i < 3; ++i) chosen[i] = cand[bi][i];
+    if (best_ms) *best_ms = best;
+    if (n_out) *n_out = (int)cand.size();
   });
 }
 

@@ -121,3 +121,40 @@ def test_tensor_core_mode_availability():
     f.set_contraction("tf32x3")
     with pytest.raises(KeyError):
         f.set_contraction("bf16")
+
+
+def test_autotune_restores_state_and_keeps_accuracy():
+    """The autotuner's trial steps leave DOFs, time and receiver samples untouched; the run
+    continued with the chosen configuration matches the oracle."""
+    m, mat = _box()
+    gpu, ora, _ = make_pair(5, 3, m, mat)
+    xr = np.array([400.0, 500.0, -100.0])
+    gpu.setup_clusters(3, 0.5)
+    dt_rec = gpu.info()["finest_dt"] * 1.37
+    rg = gpu.add_receiver(xr, dt_rec)
+    ro = ora.add_receiver(xr, dt_rec)
+    cl, _, _ = gpu.setup_clusters(3, 0.5)
+    ora.setup_clusters(3, 0.5)
+    K = m["tet"].shape[0]
+    d0 = synth.random_dofs(K, 27, 35, seed=8)
+    gpu.set_dofs(d0)
+    ora.Q = d0.copy()
+    gpu.advance_steps(4)
+    ora.run_lts(4)
+    before = gpu.get_dofs()
+    t_before = gpu.info()["time"]
+    n_before = len(gpu.seismogram(rg)[0])
+    res = gpu.autotune(allow_tf32=False)
+    assert res["contraction"] in ("fp32", "tf32x3") and len(res["candidates"]) >= 2
+    assert all(c["ms"] > 0 for c in res["candidates"])
+    assert np.array_equal(gpu.get_dofs(), before)
+    assert gpu.info()["time"] == t_before and len(gpu.seismogram(rg)[0]) == n_before
+    gpu.advance_steps(8)
+    ora.run_lts(8)
+    err = rel_l2_groups(gpu.get_dofs(), ora.Q, 27)
+    for k, v in err.items():
+        assert v <= TOL, (res, err)
+    tg, vg = gpu.seismogram(rg)
+    to, vo = ora.seismogram(ro)
+    assert np.array_equal(tg, to)
+    assert np.sum((vg - vo) ** 2) <= 1e-8 * np.sum(vo ** 2)
