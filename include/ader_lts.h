@@ -201,6 +201,14 @@ int lts_transfer_bytes(lts_t* h, int64_t* h2d, int64_t* d2h);
 enum { LTS_CONTRACT_FP32 = 0, LTS_CONTRACT_TF32X3 = 1, LTS_CONTRACT_TF32 = 2 };
 int lts_set_contraction(lts_t* h, int mode);
 
+/* Bound of the tensor-core completion waits, in SM cycles (default 2e9, about one second).
+ * suppress_commit != 0 is the failure-path test: the kernels issue no tensor-core work, so
+ * every wait runs out at the bound, the kernel records the timeout, releases its tensor
+ * memory and returns; the next synchronising call returns LTS_ERR_TIMEOUT (and clears the
+ * report) while the handle stays usable. The DOFs are then undefined. Errors: LTS_ERR_ARG
+ * for cycles <= 0. */
+int lts_set_wait_limit(lts_t* h, int64_t cycles, int suppress_commit);
+
 /* Autotuner over launch configurations: contraction engine (FP32 CUDA cores, split-tf32
  * tensor cores, and plain tf32 only if allow_tf32) x resident CTAs per SM the predict and
  * neighbour grids are sized for (the occupancy maximum and one fewer). Each candidate

@@ -52,6 +52,7 @@ _SIGS = {
     "lts_set_contraction": (_I, [_P, _I]),
     "lts_launch_config": (_I, [_P, _P, _P]),
     "lts_autotune": (_I, [_P, _I, _P, _P, _P, _P, _I, _P]),
+    "lts_set_wait_limit": (_I, [_P, _L, _I]),
     "lts_energy_noalloc": (_I, [_I, _I, _P, _P, _L, _P, _P]),
     "lts_reference_operators": (_I, [_I, _P, _P, _P]),
     "lts_eval_basis": (_I, [_I, _L, _P, _P]),
@@ -314,6 +315,9 @@ class Solver:
                 for r in table[:min(n.value, 32)]]
         return dict(contraction=names[int(chosen[0])], ctas_predict=int(chosen[1]), ctas_neighbour=int(chosen[2]),
                     best_ms=best.value, candidates=rows)
+
+    def set_wait_limit(self, cycles=2000000000, suppress_commit=False):
+        self._check(lib().lts_set_wait_limit(self._h, int(cycles), 1 if suppress_commit else 0))
 
     def set_contraction(self, mode):
         """'fp32' (CUDA cores), 'tf32x3' (tensor cores, split tf32) or 'tf32' (tensor cores)."""

@@ -72,6 +72,8 @@ struct lts_solver {
   int nsim = 1;                             // fused simulations
   int contraction = LTS_CONTRACT_FP32;
   int ctas_predict = 0, ctas_neighbour = 0;  // resident CTAs per SM the grids are sized for (0: occupancy)
+  long long wait_cycles = ltsdev::TC_WAIT_CYCLES;   // bound of the tensor-core completion waits
+  int suppress_commit = 0;                          // failure-path test: waits run out
   std::string err;
   Launchers L{};
   lts::RefOps ops;
@@ -430,12 +432,15 @@ void ensure_capacity(void** ptr, size_t* cap, size_t need, size_t elem) {
 }
 
 // Raises LTS_ERR_TIMEOUT if a kernel reported a bounded wait that gave up (the device
-// must be synchronised).
+// must be synchronised); the report clears the word.
 void check_device_error(lts_solver* h) {
   if (!h->d_err) return;
   int v = 0;
   ck(cudaMemcpy(&v, h->d_err, sizeof(int), cudaMemcpyDeviceToHost), "read error word");
-  if (v != 0) fail(LTS_ERR_TIMEOUT, "a tensor-core completion wait gave up");
+  if (v != 0) {
+    ck(cudaMemset(h->d_err, 0, sizeof(int)), "clear error word");
+    fail(LTS_ERR_TIMEOUT, "a tensor-core completion wait gave up");
+  }
 }
 
 double ricker(double t, double f0, double t0) {
@@ -580,7 +585,8 @@ void advance_steps(lts_solver* h, int64_t n_finest, cudaStream_t stream) {
     if (ph.kind == 0)
       X.neighbour(h->dops, h->dst, pa, std::min(nb, grid_cap_n), stream);
     else if (use_tc)
-      X.predict_tc(h->dops, h->dst, pa, std::min(nb, grid_cap_p), passes, h->d_err, stream);
+      X.predict_tc(h->dops, h->dst, pa, std::min(nb, grid_cap_p), passes, h->d_err, h->wait_cycles,
+                   h->suppress_commit, stream);
     else
       X.predict(h->dops, h->dst, pa, std::min(nb, grid_cap_p), stream);
     ++h->launches;
@@ -1185,6 +1191,14 @@ int lts_autotune(lts_t* h, int allow_tf32, void* cuda_stream, int* chosen, doubl
       for (int i = 0; i < 3; ++i) chosen[i] = cand[bi][i];
     if (best_ms) *best_ms = best;
     if (n_out) *n_out = (int)cand.size();
+  });
+}
+
+int lts_set_wait_limit(lts_t* h, int64_t cycles, int suppress_commit) {
+  return run(h, [&] {
+    if (cycles <= 0) fail(LTS_ERR_ARG, "wait limit must be positive");
+    h->wait_cycles = cycles;
+    h->suppress_commit = suppress_commit != 0;
   });
 }
 

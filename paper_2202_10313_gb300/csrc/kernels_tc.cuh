@@ -56,12 +56,13 @@ struct TcCfg {
   static constexpr int SMEM_BYTES = (S_TOTAL * 4 > 80 * 1024) ? S_TOTAL * 4 : 80 * 1024;
 };
 
-// Bounded wait for one MMA chain: about one second at the maximum SM clock.
+// Default bound of the wait for one MMA chain: about one second at the maximum SM clock.
 constexpr long long TC_WAIT_CYCLES = 2000000000LL;
 
 template <int O, int M, int FG>
 __global__ void __launch_bounds__(Cfg<O, M, FG>::NT, 2)
-    k_predict_tc(DevOps ops, DevState st, PhaseArgs ph, int passes, int* err) {
+    k_predict_tc(DevOps ops, DevState st, PhaseArgs ph, int passes, int* err, long long wait_cycles,
+                 int suppress_commit) {
   using C = Cfg<O, M, FG>;
   using TC = TcCfg<O, M, FG>;
   static_assert(TC::SUPPORTED, "shape outside the tensor-core path");
@@ -156,7 +157,8 @@ __global__ void __launch_bounds__(Cfg<O, M, FG>::NT, 2)
     tc::fence_smem_to_async();
     tc::fence_before_sync();
     __syncthreads();
-    if (tid == 0) {
+    // suppress_commit (failure-path test): nothing is issued, so the wait below runs out
+    if (tid == 0 && !suppress_commit) {
       tc::fence_after_sync();
       constexpr uint32_t idesc = tc::idesc_tf32(128, NN);
       const uint32_t xh = tc::smem_u32(sXh), xl = tc::smem_u32(sXl);
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(Cfg<O, M, FG>::NT, 2)
   // (slot, r); the column map is resolved at compile time) and end with a barrier.
   // Returns false (in every thread) if the chain did not complete within the bounded wait.
   auto finish = [&]() -> bool {
-    bool ok = tc::mbar_wait(bar, phase, TC_WAIT_CYCLES);
+    bool ok = tc::mbar_wait(bar, phase, wait_cycles);
     ok = __all_sync(0xffffffffu, ok);
     phase ^= 1u;
     tc::fence_after_sync();

@@ -17,7 +17,8 @@ struct Launchers {
   void (*neighbour)(const DevOps&, const DevState&, const PhaseArgs&, int grid, cudaStream_t);
   // tensor-core predict + local kernel (nullptr where the shape has no tensor-core path);
   // passes 3: split-tf32 products, 1: tf32; err: device word set when a bounded wait gave up
-  void (*predict_tc)(const DevOps&, const DevState&, const PhaseArgs&, int grid, int passes, int* err, cudaStream_t);
+  void (*predict_tc)(const DevOps&, const DevState&, const PhaseArgs&, int grid, int passes, int* err,
+                     long long wait_cycles, int suppress_commit, cudaStream_t);
   size_t smem_predict_tc;
   int blocks_predict_tc;
   // fg: simulation group size of the layout (FG of the fused instantiation, 1 for one simulation)
@@ -68,9 +69,10 @@ struct Impl {
     k_neighbour<O, M, FG><<<grid, C::NTN, C::N_TOTAL * sizeof(float), st>>>(o, s, p);
   }
   static void predict_tc(const DevOps& o, const DevState& s, const PhaseArgs& p, int grid, int passes, int* err,
-                         cudaStream_t st) {
+                         long long wait_cycles, int suppress_commit, cudaStream_t st) {
     if constexpr (TcCfg<O, M, FG>::SUPPORTED)
-      k_predict_tc<O, M, FG><<<grid, C::NT, TcCfg<O, M, FG>::SMEM_BYTES, st>>>(o, s, p, passes, err);
+      k_predict_tc<O, M, FG><<<grid, C::NT, TcCfg<O, M, FG>::SMEM_BYTES, st>>>(o, s, p, passes, err, wait_cycles,
+                                                                               suppress_commit);
   }
   static void receivers(const DevOps& o, const float* Q, long long qs, int nsim, int fg, const float* ed,
                         const float* phi, const RecvItem* it, float* out, const float* om, int n, cudaStream_t st) {

@@ -158,3 +158,29 @@ def test_autotune_restores_state_and_keeps_accuracy():
     to, vo = ora.seismogram(ro)
     assert np.array_equal(tg, to)
     assert np.sum((vg - vo) ** 2) <= 1e-8 * np.sum(vo ** 2)
+
+
+def test_bounded_wait_runs_out_and_handle_recovers():
+    """Failure path without a GPU fault: with the tensor-core work suppressed, every
+    completion wait runs out at a short bound; the next synchronising call reports
+    LTS_ERR_TIMEOUT, and after restoring the defaults the same handle runs correctly."""
+    m, mat = _box()
+    gpu, ora, _ = make_pair(4, 0, m, mat)
+    gpu.set_contraction("tf32x3")
+    gpu.setup_clusters(1, 0.5)
+    K = m["tet"].shape[0]
+    d0 = synth.random_dofs(K, 9, 20, seed=12)
+    gpu.set_wait_limit(200000, suppress_commit=True)
+    gpu.set_dofs(d0)
+    gpu.advance_steps(2)
+    with pytest.raises(binding.LtsError) as ei:
+        gpu.get_dofs()
+    assert ei.value.code == binding.LTS_ERR_TIMEOUT
+    gpu.set_wait_limit()
+    gpu.set_dofs(d0)
+    ora.setup_clusters(1, 0.5)
+    ora.Q = d0.copy()
+    gpu.advance_steps(2)
+    ora.run_gts(ora.time_step_gts(0.5), 2)
+    err = rel_l2_groups(gpu.get_dofs(), ora.Q, 9)
+    assert err["all"] <= TOL, err
