@@ -197,10 +197,15 @@ def run_ours(args, rank, world, local_rank):
     dt_rec = 0.01
     for r in recs:
         s.add_receiver(r, dt_rec)
-    s.use_torch_memory(NCLUSTERS)
+    if args.partition <= 1:
+        s.use_torch_memory(NCLUSTERS)
     if args.contraction != "auto":
         s.set_contraction(args.contraction)
     _, lam, speedup = s.setup_clusters(NCLUSTERS, CFL)
+    pstats = None
+    if args.partition > 1:
+        part, pstats = s.partition(args.partition)
+        s.set_partition(part, args.partition)
     tuned = None
     if args.contraction == "auto":
         tuned = s.autotune(allow_tf32=False, stream=torch.cuda.current_stream())
@@ -215,6 +220,7 @@ def run_ours(args, rank, world, local_rank):
     clocks = ClockSampler(local_rank)
     s.set_profiling(True)
     launches0 = s.info()["launches"]
+    xb0 = s.exchange_bytes()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -230,6 +236,7 @@ def run_ours(args, rank, world, local_rank):
     ck = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     launches = s.info()["launches"] - launches0
+    xbytes = (s.exchange_bytes() - xb0) / args.steps
     kst = s.kernel_stats()
     s.set_profiling(False)
     # end to end through the public API: advance + seismogram read-back every step
@@ -305,6 +312,11 @@ def run_ours(args, rank, world, local_rank):
                 "h2d_bytes_per_step": (h2d1 - h2d0) / args.steps, "d2h_bytes_per_step": (d2h1 - d2h0) / args.steps},
         "clocks": ck,
     }
+    if pstats is not None:
+        B = ORDER * (ORDER + 1) * (ORDER + 2) // 6
+        line["partition"] = dict(parts=args.partition, face_local_bytes_per_step=xbytes,
+                                 whole_buffer_bytes_per_step=pstats["buffer_msgs_per_macro"] * 9 * B * 4,
+                                 **{k: v for k, v in pstats.items()})
     if not args.no_cpu_baseline and world == 1:
         per_m, times, Ks = oracle_sample(seconds_cap=20.0)
         v = per_m * len(times) / sum(times)
@@ -326,6 +338,8 @@ def main():
     ap.add_argument("--medium", action="store_true", help="262k-tet mesh (profiling captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fused", type=int, default=1, help="fused simulations (multiple of 4; 1 = single)")
+    ap.add_argument("--partition", type=int, default=1,
+                    help="emulated partitioned run: P weighted parts exchanging face-local messages")
     ap.add_argument("--contraction", default="auto", choices=["auto", "fp32", "tf32x3", "tf32"],
                     help="engine of the time/volume contractions: FP32 CUDA cores or tensor cores; auto runs "
                          "the autotuner over the FP32-accurate engines and the grid shapes")

@@ -201,6 +201,39 @@ int lts_transfer_bytes(lts_t* h, int64_t* h2d, int64_t* d2h);
 enum { LTS_CONTRACT_FP32 = 0, LTS_CONTRACT_TF32X3 = 1, LTS_CONTRACT_TF32 = 2 };
 int lts_set_contraction(lts_t* h, int mode);
 
+/* Weighted partitioning for distributed runs (Sec. V-C). Element weight 2^(N_c-1-l) (its
+ * updates per macro step, cluster l 0-based); face weight = messages per macro step over
+ * the face. Recursive coordinate bisection of the centroids at the weighted median, then a
+ * greedy boundary pass that lowers the face-weighted cut within a 3 % load tolerance.
+ * Needs clusters (lts_setup_clusters; host-only handles work). part_out[n_tet] in
+ * [0, n_parts); stats_out[6] = (largest part weight / mean, smallest / mean, total weight,
+ * cut faces counted per receiving side, face-local messages per macro step, whole-buffer
+ * messages per macro step of the uncompressed scheme: one 9 x B buffer per sending element,
+ * receiving part and receiver step). Either output may be NULL. Errors: LTS_ERR_STATE,
+ * LTS_ERR_ARG (n_parts < 1 or > n_tet). */
+int lts_partition(lts_t* h, int n_parts, int32_t* part_out, double* stats_out);
+
+/* The exchange plan of a partition: every face whose two elements lie in different parts,
+ * from the receiving side, in message order (receiving part, sending part, receiver
+ * cluster, receiver element, face). faces[cap][8] = (receiving element, its face i, sending
+ * element, its face j, orientation h, receiving part, sending part, receiver cluster), all
+ * original indices; the sender computes H = X F-_{j,h} (9 x F values) from its buffer X and
+ * the receiver applies the flux of face i to it. *n receives the count. */
+int lts_cut_faces(lts_t* h, const int32_t* part, int64_t cap, int64_t* faces, int64_t* n);
+
+/* Emulated partitioned run on one device (Sec. V-C): with n_parts > 1 every cut face takes
+ * its neighbour contribution from a face-local message instead of the neighbour's buffer —
+ * before each neighbour pass a pack kernel computes, on the sending side, H = X F-_{j,h}
+ * for the cut faces whose receivers are active, and the receiver's neighbour kernel reads
+ * it. The arithmetic is the one of the unpartitioned run, in the same order. One
+ * simulation only. If clusters are set up, re-creates the device state (time 0, DOFs
+ * zero). n_parts <= 1 (part may be NULL) switches it off. Errors: LTS_ERR_ARG, LTS_ERR_STATE. */
+int lts_set_partition(lts_t* h, int n_parts, const int32_t* part);
+
+/* Face-local message bytes the partitioned run has produced so far (9 x F FP32 values per
+ * active cut face and neighbour pass). */
+int lts_exchange_bytes(lts_t* h, int64_t* bytes);
+
 /* Bound of the tensor-core completion waits, in SM cycles (default 2e9, about one second).
  * suppress_commit != 0 is the failure-path test: the kernels issue no tensor-core work, so
  * every wait runs out at the bound, the kernel records the timeout, releases its tensor

@@ -100,6 +100,11 @@ class Solver:
         self.Q = np.zeros((K, self.nq, self.nb))
         self.sources = []
         self.receivers = []
+        # one part of a partitioned run (oracle.partitioned): the elements this solver
+        # updates (None: all) and the supplier of face-local messages for faces whose
+        # neighbour lies in another part (None: none)
+        self.owned = None
+        self.remote_h = None
 
     # ---------------------------------------------------------------- set-up
     def quadrature_points(self):
@@ -191,9 +196,11 @@ class Solver:
                 Sa += (self.Aam[idx, i] @ G) @ b.Fh[i]
         return self._surface_to_dofs(Se, Sa)
 
-    def neighbour_surface(self, idx, buffers):
+    def neighbour_surface(self, idx, buffers, given=None):
         """buffers[i]: (len(idx), 9, B) time-integrated neighbour DOFs for face i
-        (rows of boundary faces are ignored)."""
+        (rows of boundary faces are ignored). given[i], if not None: (mask over idx, H)
+        with H = X F-_{j,h} (9 x F) already formed by the neighbour's part for the masked
+        faces (Sec. V-C face-local messages); their buffer rows are not used."""
         b = self.basis
         mesh = self.mesh
         Se = np.zeros((len(idx), 9, self.nb))
@@ -208,9 +215,14 @@ class Solver:
             jj = mesh.nbr_face[sel, i]
             hh = mesh.nbr_orient[sel, i]
             X = buffers[i][has]
+            msg = np.zeros(len(sel), dtype=bool)
+            if given is not None and given[i] is not None:
+                gmask, gH = given[i]
+                msg = gmask[has]
+                H[msg] = gH[np.cumsum(gmask)[has][msg] - 1]
             for j in range(4):
                 for h in range(3):
-                    mk = (jj == j) & (hh == h)
+                    mk = (jj == j) & (hh == h) & ~msg
                     if np.any(mk):
                         H[mk] = X[mk] @ b.Fb[j][h]
             Se[has] += (self.Aep[sel, i] @ H) @ b.Fh[i]
@@ -322,6 +334,8 @@ class Solver:
 
     def _predict_local(self, l, n):
         idx = np.nonzero(self.clusters == l)[0]
+        if self.owned is not None:
+            idx = idx[self.owned[idx]]
         if len(idx) == 0:
             return
         dl = self.delta * 2.0 ** l
@@ -346,6 +360,10 @@ class Solver:
 
     def _neighbour(self, l, n):
         idx = np.nonzero(self.clusters == l)[0]
+        if self.owned is not None:
+            idx = idx[self.owned[idx]]
+        # the message exchange runs even when this part has no element of cluster l
+        given = self.remote_h(l, n, idx) if self.remote_h is not None else None
         if len(idx) == 0:
             return
         nbr = self.mesh.nbr
@@ -363,7 +381,7 @@ class Solver:
                 X[coa] = self.B1[nb[coa]] - self.B2[nb[coa]]
             X[nbr[idx, i] < 0] = 0.0
             bufs.append(X)
-        self.Q[idx] = self.Q[idx] + self.neighbour_surface(idx, bufs)
+        self.Q[idx] = self.Q[idx] + self.neighbour_surface(idx, bufs, given)
         s0 = n * 2 ** l
         self._apply_sources(idx, s0 * self.delta, (s0 + 2 ** l) * self.delta)
 

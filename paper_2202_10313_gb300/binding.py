@@ -53,6 +53,10 @@ _SIGS = {
     "lts_launch_config": (_I, [_P, _P, _P]),
     "lts_autotune": (_I, [_P, _I, _P, _P, _P, _P, _I, _P]),
     "lts_set_wait_limit": (_I, [_P, _L, _I]),
+    "lts_partition": (_I, [_P, _I, _P, _P]),
+    "lts_cut_faces": (_I, [_P, _P, _L, _P, _P]),
+    "lts_set_partition": (_I, [_P, _I, _P]),
+    "lts_exchange_bytes": (_I, [_P, _P]),
     "lts_energy_noalloc": (_I, [_I, _I, _P, _P, _L, _P, _P]),
     "lts_reference_operators": (_I, [_I, _P, _P, _P]),
     "lts_eval_basis": (_I, [_I, _L, _P, _P]),
@@ -315,6 +319,36 @@ class Solver:
                 for r in table[:min(n.value, 32)]]
         return dict(contraction=names[int(chosen[0])], ctas_predict=int(chosen[1]), ctas_neighbour=int(chosen[2]),
                     best_ms=best.value, candidates=rows)
+
+    def partition(self, n_parts):
+        """Weighted partition (part per element) and its statistics."""
+        part = np.zeros(self.K, dtype=np.int32)
+        st = np.zeros(6)
+        self._check(lib().lts_partition(self._h, int(n_parts), _ptr(part), _ptr(st)))
+        keys = ("max_load", "min_load", "total_weight", "cut_faces", "msgs_per_macro", "buffer_msgs_per_macro")
+        return part, dict(zip(keys, st.tolist()))
+
+    def cut_faces(self, part):
+        """Exchange plan: rows (recv elem, recv face, send elem, send face, orient, recv part,
+        send part, recv cluster) in message order."""
+        p = np.ascontiguousarray(part, dtype=np.int32)
+        n = ctypes.c_int64()
+        self._check(lib().lts_cut_faces(self._h, _ptr(p), 0, None, ctypes.byref(n)))
+        out = np.zeros((n.value, 8), dtype=np.int64)
+        self._check(lib().lts_cut_faces(self._h, _ptr(p), n.value, _ptr(out), ctypes.byref(n)))
+        return out
+
+    def set_partition(self, part=None, n_parts=None):
+        if part is None:
+            self._check(lib().lts_set_partition(self._h, 1, None))
+            return
+        p = np.ascontiguousarray(part, dtype=np.int32)
+        self._check(lib().lts_set_partition(self._h, int(n_parts if n_parts else p.max() + 1), _ptr(p)))
+
+    def exchange_bytes(self):
+        b = ctypes.c_int64()
+        self._check(lib().lts_exchange_bytes(self._h, ctypes.byref(b)))
+        return b.value
 
     def set_wait_limit(self, cycles=2000000000, suppress_commit=False):
         self._check(lib().lts_set_wait_limit(self._h, int(cycles), 1 if suppress_commit else 0))

@@ -11,6 +11,7 @@
 
 #include "../../include/ader_lts.h"
 #include "host.h"
+#include "host_partition.h"
 #include "launch.h"
 
 using ltsdev::DevOps;
@@ -74,6 +75,14 @@ struct lts_solver {
   int ctas_predict = 0, ctas_neighbour = 0;  // resident CTAs per SM the grids are sized for (0: occupancy)
   long long wait_cycles = ltsdev::TC_WAIT_CYCLES;   // bound of the tensor-core completion waits
   int suppress_commit = 0;                          // failure-path test: waits run out
+  // emulated partitioned run (Sec. V-C): cut faces receive face-local messages
+  int n_parts = 1;
+  std::vector<int32_t> part;
+  std::vector<int64_t> cut_beg;             // cut faces by receiver cluster (device order), nc+1
+  int64_t n_cut = 0;
+  int* d_cut = nullptr;                     // [3][n_cut]: sender element, code, receiver cluster
+  float* d_msg = nullptr;                   // [n_cut][9][F]
+  int64_t msg_bytes = 0;                    // face-local message bytes produced so far
   std::string err;
   Launchers L{};
   lts::RefOps ops;
@@ -144,7 +153,8 @@ int run(lts_t* h, const std::function<void()>& fn) {
 }
 
 struct Layout {
-  size_t Q, B1, B2, B3, edata, ndata, nbr, ncode, meta, emat, partial, err, K, Ft, Fh, Fb, rphi, sphi, total;
+  size_t Q, B1, B2, B3, edata, ndata, nbr, ncode, meta, emat, partial, err, K, Ft, Fh, Fb, rphi, sphi, cut, msg,
+      total;
 };
 
 // Element strides (floats) of Q and of the LTS buffers: [group][q][b][G] per element with
@@ -182,6 +192,16 @@ Layout layout_of(const lts_solver* h, int64_t K) {
   L.Fb = take(sizeof(float) * 12 * X.B * X.F);
   L.rphi = take(sizeof(float) * std::max<size_t>(1, h->receivers.size()) * X.B);
   L.sphi = take(sizeof(float) * std::max<size_t>(1, h->sources.size()) * X.B);
+  // cut faces of a partitioned run
+  int64_t ncut = 0;
+  if (h->n_parts > 1)
+    for (int64_t k = 0; k < K; ++k)
+      for (int f = 0; f < 4; ++f) {
+        const int64_t nb = h->mesh.nbr[4 * k + f];
+        if (nb >= 0 && h->part[nb] != h->part[k]) ++ncut;
+      }
+  L.cut = take(sizeof(int) * 3 * std::max<int64_t>(1, ncut));
+  L.msg = take(sizeof(float) * 9 * X.F * std::max<int64_t>(1, ncut));
   L.total = off;
   return L;
 }
@@ -331,6 +351,31 @@ void setup_device(lts_solver* h) {
   std::vector<float> sphi(std::max<size_t>(1, h->sources.size()) * B, 0.f);
   for (size_t s = 0; s < h->sources.size(); ++s)
     for (int b = 0; b < B; ++b) sphi[s * B + b] = (float)h->sources[s].phi[b];
+  // ---- partitioned run: cut faces in device order (receiver cluster, then message order)
+  std::vector<int> cut_host;
+  h->n_cut = 0;
+  h->cut_beg.assign(h->nc + 1, 0);
+  if (h->n_parts > 1) {
+    std::vector<lts::CutFace> cf;
+    lts::cut_faces(M, h->part, h->cluster, cf);
+    std::stable_sort(cf.begin(), cf.end(),
+                     [](const lts::CutFace& a, const lts::CutFace& b) { return a.recv_cluster < b.recv_cluster; });
+    h->n_cut = (int64_t)cf.size();
+    cut_host.resize(3 * cf.size());
+    for (size_t c = 0; c < cf.size(); ++c) {
+      const lts::CutFace& x = cf[c];
+      const int64_t nk = h->iperm[x.recv_elem];
+      const int dc = h->cluster[x.send_elem] - h->cluster[x.recv_elem];
+      const int rel = dc == 0 ? 0 : (dc < 0 ? 1 : 2);
+      cut_host[c] = (int)h->iperm[x.send_elem];
+      cut_host[cf.size() + c] = (x.send_face * 3 + x.orient) | (rel << 8);
+      cut_host[2 * cf.size() + c] = x.recv_cluster;
+      nbr[4 * nk + x.recv_face] = (int)c;
+      ncode[4 * nk + x.recv_face] |= ltsdev::FACE_REMOTE;
+      h->cut_beg[x.recv_cluster + 1]++;
+    }
+    for (int l = 0; l < h->nc; ++l) h->cut_beg[l + 1] += h->cut_beg[l];
+  }
   // ---- device block
   free_device(h);
   Layout Lo = layout_of(h, K);
@@ -366,6 +411,9 @@ void setup_device(lts_solver* h) {
   h->dops.Fb = reinterpret_cast<float*>(base + Lo.Fb);
   h->d_recv_phi = reinterpret_cast<float*>(base + Lo.rphi);
   h->d_src_phi = reinterpret_cast<float*>(base + Lo.sphi);
+  h->d_cut = reinterpret_cast<int*>(base + Lo.cut);
+  h->d_msg = reinterpret_cast<float*>(base + Lo.msg);
+  h->dst.msg = h->d_msg;
   auto up = [&](const void* dst, const void* src, size_t bytes) {
     ck(cudaMemcpy(const_cast<void*>(dst), src, bytes, cudaMemcpyHostToDevice), "upload");
   };
@@ -389,6 +437,7 @@ void setup_device(lts_solver* h) {
   up(h->dops.Fb, hFb.data(), sizeof(float) * hFb.size());
   up(h->d_recv_phi, rphi.data(), sizeof(float) * rphi.size());
   up(h->d_src_phi, sphi.data(), sizeof(float) * sphi.size());
+  if (!cut_host.empty()) up(h->d_cut, cut_host.data(), sizeof(int) * cut_host.size());
   for (auto& r : h->receivers) {
     r.t.clear();
     r.slot.clear();
@@ -581,6 +630,13 @@ void advance_steps(lts_solver* h, int64_t n_finest, cudaStream_t stream) {
                   h->d_seis, base.omega, ph.item_end - ph.item_beg, stream);
       ++h->launches;
     }
+    if (ph.kind == 0 && h->n_parts > 1 && h->cut_beg[ph.top + 1] > 0) {
+      // the neighbours' partitions compute the face-local messages of the active cut faces
+      const int nact = (int)h->cut_beg[ph.top + 1];
+      X.pack(h->dops, h->dst, pa, h->d_cut, h->d_cut + h->n_cut, h->d_cut + 2 * h->n_cut, nact, h->d_msg, stream);
+      ++h->launches;
+      h->msg_bytes += (int64_t)nact * 9 * X.F * (int64_t)sizeof(float);
+    }
     if (h->profiling) ck(cudaEventRecord(next_event(h), stream), "event record");
     if (ph.kind == 0)
       X.neighbour(h->dops, h->dst, pa, std::min(nb, grid_cap_n), stream);
@@ -675,6 +731,8 @@ int lts_set_mesh(lts_t* h, int64_t n_vert, const double* xyz, int64_t n_tet, con
     free_device(h);
     h->mesh = std::move(m);
     h->has_mesh = true;
+    h->part.clear();
+    h->n_parts = 1;
     h->has_mat = false;
     h->sources.clear();
     h->receivers.clear();
@@ -1191,6 +1249,71 @@ int lts_autotune(lts_t* h, int allow_tf32, void* cuda_stream, int* chosen, doubl
       for (int i = 0; i < 3; ++i) chosen[i] = cand[bi][i];
     if (best_ms) *best_ms = best;
     if (n_out) *n_out = (int)cand.size();
+  });
+}
+
+int lts_partition(lts_t* h, int n_parts, int32_t* part_out, double* stats_out) {
+  return run(h, [&] {
+    require_material(h);
+    if ((int64_t)h->cluster.size() != h->mesh.K) fail(LTS_ERR_STATE, "clusters not set up");
+    if (n_parts < 1 || n_parts > h->mesh.K) fail(LTS_ERR_ARG, "bad part count");
+    std::vector<int32_t> part;
+    lts::PartitionStats st;
+    lts::partition_elements(h->mesh, h->cluster, h->nc, n_parts, part, &st);
+    if (part_out) std::copy(part.begin(), part.end(), part_out);
+    if (stats_out) {
+      const double v[6] = {st.max_load, st.min_load, st.total_weight, st.cut_faces, st.msgs_per_macro,
+                           st.buffer_msgs_per_macro};
+      std::copy(v, v + 6, stats_out);
+    }
+  });
+}
+
+int lts_cut_faces(lts_t* h, const int32_t* part, int64_t cap, int64_t* faces, int64_t* n) {
+  return run(h, [&] {
+    require_material(h);
+    if ((int64_t)h->cluster.size() != h->mesh.K) fail(LTS_ERR_STATE, "clusters not set up");
+    if (!part || cap < 0 || (cap > 0 && !faces)) fail(LTS_ERR_ARG, "bad arguments");
+    std::vector<int32_t> p(part, part + h->mesh.K);
+    for (int32_t x : p)
+      if (x < 0) fail(LTS_ERR_ARG, "negative part index");
+    std::vector<lts::CutFace> cf;
+    lts::cut_faces(h->mesh, p, h->cluster, cf);
+    if (n) *n = (int64_t)cf.size();
+    for (int64_t c = 0; c < std::min<int64_t>(cap, (int64_t)cf.size()); ++c) {
+      const lts::CutFace& x = cf[c];
+      const int64_t v[8] = {x.recv_elem, x.recv_face, x.send_elem, x.send_face, x.orient, x.recv_part, x.send_part,
+                            x.recv_cluster};
+      std::copy(v, v + 8, faces + 8 * c);
+    }
+  });
+}
+
+int lts_set_partition(lts_t* h, int n_parts, const int32_t* part) {
+  return run(h, [&] {
+    require_material(h);
+    if (n_parts > 1) {
+      if (!part) fail(LTS_ERR_ARG, "null part array");
+      if (h->nsim != 1) fail(LTS_ERR_ARG, "partitioned runs take one simulation");
+      for (int64_t k = 0; k < h->mesh.K; ++k)
+        if (part[k] < 0 || part[k] >= n_parts) fail(LTS_ERR_ARG, "part index out of range");
+      h->part.assign(part, part + h->mesh.K);
+      h->n_parts = n_parts;
+    } else {
+      h->part.clear();
+      h->n_parts = 1;
+    }
+    if (h->device >= 0 && (int64_t)h->cluster.size() == h->mesh.K) {
+      ck(cudaSetDevice(h->device), "cudaSetDevice");
+      setup_device(h);
+    }
+  });
+}
+
+int lts_exchange_bytes(lts_t* h, int64_t* bytes) {
+  return run(h, [&] {
+    if (!bytes) fail(LTS_ERR_ARG, "null output");
+    *bytes = h->msg_bytes;
   });
 }
 

@@ -34,6 +34,9 @@ constexpr int MAXC = 8;  // max clusters
 constexpr int FUSED_GROUP = 4;   // simulations per CTA in fused mode
 constexpr int FLAG_FINER = 1 << 8;     // element has a finer neighbour: writes B2
 constexpr int FLAG_COARSER = 1 << 9;   // element has a coarser neighbour: writes B3
+// ncode bit of a face whose neighbour lies in another partition: nbr then holds the slot of
+// the face-local message H = X F-_{j,h} the neighbour's side computed (Sec. V-C)
+constexpr int FACE_REMOTE = 1 << 16;
 
 // FG = 1: a CTA slot is an element (single simulation). FG > 1: fused simulations, a CTA
 // owns one element and FG of its simulations, one slot per simulation.
@@ -110,6 +113,7 @@ struct DevState {
   const int* nbr;        // [K][4] neighbour (internal index) or -1
   const int* ncode;      // [K][4] (j*3+h) | (relation << 8): 0 same, 1 neighbour finer, 2 neighbour coarser
   const int* meta;       // [K] cluster | FLAG_*
+  const float* msg;      // [cut faces][9][F] face-local messages of a partitioned run (else unused)
 };
 
 struct PhaseArgs {
@@ -664,8 +668,8 @@ __global__ void __launch_bounds__(Cfg<O, M, FG>::NTN, Cfg<O, M, FG>::NMIN) k_nei
       float xv[4][9];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const int nb = valid ? ie[i] : -1;
-        const int rel = ie[4 + i] >> 8;
+        const int nb = (valid && !(ie[4 + i] & FACE_REMOTE)) ? ie[i] : -1;
+        const int rel = (ie[4 + i] >> 8) & 0xff;
         const float* src1 = (rel == 1) ? st.B3 : ((rel == 2 && par == 0) ? st.B2 : st.B1);
         const bool sub = (rel == 2 && par == 1);
         const size_t off = (size_t)(nb < 0 ? 0 : nb) * bs + (size_t)grp * (9 * B * FG) + b * FG + j;
@@ -691,17 +695,24 @@ __global__ void __launch_bounds__(Cfg<O, M, FG>::NTN, Cfg<O, M, FG>::NMIN) k_nei
       face_task_of<O, NE, (FG > 1)>(t, ee, i, f, pf);
       const int eel = (FG > 1) ? 0 : ee;
       const int code = sI[eel * 9 + 4 + i];
-      const int jh = (code >= 0) ? (code & 0xff) : 0;
+      const int jh = code & 0xff;
       float gq[9];
 #pragma unroll
       for (int r = 0; r < 9; ++r) gq[r] = 0.f;
-      const float* X = sX + (ee * 4 + i) * B * XR;
-      const float* Fm = sFb + jh * B * F + f;
-#pragma unroll 4
-      for (int k = nbasis(pf); k < B; ++k) {
-        const float w = Fm[k * F];
+      if (code & FACE_REMOTE) {
+        // computed by the neighbour's partition (k_pack_faces)
+        const float* h = st.msg + (size_t)sI[eel * 9 + i] * 9 * F + f;
 #pragma unroll
-        for (int r = 0; r < 9; ++r) gq[r] = fmaf(X[k * XR + r], w, gq[r]);
+        for (int r = 0; r < 9; ++r) gq[r] = h[r * F];
+      } else {
+        const float* X = sX + (ee * 4 + i) * B * XR;
+        const float* Fm = sFb + jh * B * F + f;
+#pragma unroll 4
+        for (int k = nbasis(pf); k < B; ++k) {
+          const float w = Fm[k * F];
+#pragma unroll
+          for (int r = 0; r < 9; ++r) gq[r] = fmaf(X[k * XR + r], w, gq[r]);
+        }
       }
       float w6[6];
       riemann_state(gq, sD + eel * ND + 4 + 11 * i, w6);
@@ -731,6 +742,46 @@ __global__ void __launch_bounds__(Cfg<O, M, FG>::NTN, Cfg<O, M, FG>::NMIN) k_nei
       }
     }
   }
+}
+
+// ------------------------------------------------------------------ face-local messages
+// Sender side of a partitioned run (Sec. V-C): for every cut face whose receiving element is
+// active in this phase, H = X F-_{j,h} (9 x F values) from the sending element's buffer X,
+// chosen by the cluster relation exactly as k_neighbour chooses it (B1, B3, B2 or B1 - B2 by
+// the receiver's step parity), with the same product order, so the receiver's flux sees the
+// values it would have computed itself. One thread per (cut face, face mode).
+template <int O, int M>
+__global__ void k_pack_faces(DevOps ops, DevState st, PhaseArgs ph, const int* send_elem, const int* send_code,
+                             const int* recv_cluster, int n, float* msg) {
+  using C = Cfg<O, M>;
+  constexpr int B = C::B, F = C::F, BUFS = C::BUFS;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * F) return;
+  const int c = t / F, f = t % F;
+  int pf = 0;
+  while (nface(pf + 1) <= f) ++pf;
+  const int code = send_code[c];
+  const int jh = code & 0xff, rel = (code >> 8) & 0xff;
+  const int par = ph.parity[recv_cluster[c]];
+  const float* src1 = (rel == 1) ? st.B3 : ((rel == 2 && par == 0) ? st.B2 : st.B1);
+  const bool sub = (rel == 2 && par == 1);
+  const size_t off = (size_t)send_elem[c] * BUFS;
+  const float* Fm = ops.Fb + jh * B * F + f;
+  float gq[9];
+#pragma unroll
+  for (int r = 0; r < 9; ++r) gq[r] = 0.f;
+#pragma unroll 4
+  for (int k = nbasis(pf); k < B; ++k) {
+    const float w = Fm[k * F];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+      float x = __ldg(src1 + off + r * B + k);
+      if (sub) x -= __ldg(st.B2 + off + r * B + k);
+      gq[r] = fmaf(x, w, gq[r]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 9; ++r) msg[((size_t)c * 9 + r) * F + f] = gq[r];
 }
 
 // ------------------------------------------------------------------ receivers

@@ -25,6 +25,9 @@ struct Launchers {
   void (*receivers)(const DevOps&, const float* Q, long long qs, int nsim, int fg, const float* edata,
                     const float* phi, const RecvItem* items, float* out, const float* omega, int n, cudaStream_t);
   void (*sources)(float* Q, long long qs, int fg, const float* phi, const SrcItem* items, int n, cudaStream_t);
+  // face-local messages of a partitioned run (one simulation)
+  void (*pack)(const DevOps&, const DevState&, const PhaseArgs&, const int* send_elem, const int* send_code,
+               const int* recv_cluster, int n, float* msg, cudaStream_t);
   void (*energy)(const float* Q, long long qs, int nsim, int fg, const double* emat, int K, double* partial,
                  int nblocks, cudaStream_t);
 };
@@ -81,6 +84,11 @@ struct Impl {
   static void sources(float* Q, long long qs, int fg, const float* phi, const SrcItem* it, int n, cudaStream_t st) {
     k_sources<O, M><<<1, 128, 0, st>>>(Q, qs, fg, phi, it, n);
   }
+  static void pack(const DevOps& o, const DevState& s, const PhaseArgs& p, const int* se, const int* sc,
+                   const int* rc, int n, float* msg, cudaStream_t st) {
+    const int threads = 128, nt = n * C::F;
+    k_pack_faces<O, M><<<(nt + threads - 1) / threads, threads, 0, st>>>(o, s, p, se, sc, rc, n, msg);
+  }
   static void energy(const float* Q, long long qs, int nsim, int fg, const double* emat, int K, double* partial,
                      int nblocks, cudaStream_t st) {
     k_energy<O, M><<<nblocks, 256, 0, st>>>(Q, qs, nsim, fg, emat, K, partial);
@@ -108,6 +116,7 @@ struct Impl {
     L.neighbour = &neighbour;
     L.receivers = &receivers;
     L.sources = &sources;
+    L.pack = &pack;
     L.energy = &energy;
     return L;
   }

@@ -1,0 +1,78 @@
+"""Emulated partitioned run on one GPU (Sec. V-C): cut faces take their neighbour
+contribution from face-local messages H = X F-_{j,h} computed on the sending side by a
+pack kernel. The arithmetic and its order are those of the unpartitioned run, so the DOFs
+must be bitwise equal to it, and within 1e-4 of the oracle."""
+import numpy as np
+import pytest
+
+from paper_2202_10313_gb300 import binding, build, synth
+from gpu_common import make_pair, rel_l2_groups
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+
+
+@pytest.mark.parametrize("order,n_mech,n_parts", [(5, 3, 2), (5, 3, 5), (4, 0, 3)])
+def test_partitioned_run_equals_unpartitioned_and_oracle(order, n_mech, n_parts):
+    m = synth.permute_vertex_order(synth.graded_box(6, 5, 3, 250.0, 125.0, seed=12), seed=2)
+    mat = synth.random_layers(m, n_layers=3, seed=5)
+    K = m["tet"].shape[0]
+    nq, nb = 9 + 6 * n_mech, order * (order + 1) * (order + 2) // 6
+    d0 = synth.random_dofs(K, nq, nb, seed=21)
+    xs, m6 = np.array([610.0, 640.0, -260.0]), np.array([0.2, -0.4, 0.2, 1.0, 0.1, -0.3])
+    runs = []
+    for parted in (False, True):
+        gpu, ora, _ = make_pair(order, n_mech, m, mat)
+        gpu.add_point_source(xs, m6, 8.0, 0.06, 1e12)
+        cl, _, _ = gpu.setup_clusters(3, 0.5)
+        if parted:
+            part, st = gpu.partition(n_parts)
+            gpu.set_partition(part, n_parts)
+        gpu.set_dofs(d0)
+        gpu.advance_steps(8)
+        runs.append(gpu.get_dofs())
+        if parted:
+            # 9 x F FP32 values per cut face and update of its receiving element
+            F = order * (order + 1) // 2
+            assert gpu.exchange_bytes() == 2 * st["msgs_per_macro"] * 9 * F * 4
+    assert np.array_equal(runs[0], runs[1])
+    ora.add_point_source(xs, m6, 8.0, 0.06, 1e12)
+    ora.setup_clusters(3, 0.5)
+    ora.Q = d0.copy()
+    ora.run_lts(8)
+    err = rel_l2_groups(runs[1], ora.Q, nq)
+    for k, v in err.items():
+        assert v <= 1e-4, err
+
+
+def test_partition_with_tensor_cores_and_switch_off():
+    m = synth.graded_box(5, 5, 3, 250.0, 125.0, seed=12)
+    mat = synth.random_layers(m, n_layers=3, seed=5)
+    K = m["tet"].shape[0]
+    d0 = synth.random_dofs(K, 27, 35, seed=4)
+    gpu, ora, _ = make_pair(5, 3, m, mat)
+    gpu.set_contraction("tf32x3")
+    gpu.setup_clusters(3, 0.5)
+    part, _ = gpu.partition(4)
+    gpu.set_partition(part, 4)
+    gpu.set_dofs(d0)
+    gpu.advance_steps(4)
+    a = gpu.get_dofs()
+    gpu.set_partition(None)
+    gpu.set_dofs(d0)
+    gpu.advance_steps(4)
+    assert np.array_equal(a, gpu.get_dofs())
+    f = binding.Solver(5, 3, device=0, n_fused=4)
+    f.set_mesh(m["xyz"], m["tet"], m["face_bc"])
+    f.set_material(mat["rho"], mat["vp"], mat["vs"], mat["qp"], mat["qs"], 0.1, 5.0)
+    f.setup_clusters(3, 0.5)
+    with pytest.raises(binding.LtsError) as ei:
+        f.set_partition(part, 4)
+    assert ei.value.code == binding.LTS_ERR_ARG

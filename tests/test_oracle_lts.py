@@ -116,7 +116,7 @@ def test_fig5_walkthrough_buffers_and_reads():
             recorded_D[s.s_clock] = [d[p].copy() for d in D]
         return D
 
-    def nbr_surface(idx, bufs):
+    def nbr_surface(idx, bufs, given=None):
         for p, e in enumerate(idx):
             for i in range(4):
                 if mesh.nbr[e, i] == 0:
