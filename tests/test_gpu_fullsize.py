@@ -35,7 +35,9 @@ def _ball(nbr, k, hops):
     return np.array(sorted(seen))
 
 
-def test_bench_configuration_sampled_parity():
+@pytest.mark.parametrize("contraction", ["fp32", "tf32x3"])
+def test_bench_configuration_sampled_parity(contraction):
+    """Both engines the autotuner may pick for the bench run."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -51,6 +53,7 @@ def test_bench_configuration_sampled_parity():
     for r in recs:
         g.add_receiver(r, 0.01)
     g.use_torch_memory(bench.NCLUSTERS)
+    g.set_contraction(contraction)
     cl_g, lam_g, sp_g = g.setup_clusters(bench.NCLUSTERS, bench.CFL)
     # ---- oracle clustering of the full mesh
     om = Mesh(mesh["xyz"], mesh["tet"], mesh["face_bc"])
@@ -92,3 +95,63 @@ def test_bench_configuration_sampled_parity():
         err = rel_l2_groups(got[s_i][None], want, 27)
         for name, v in err.items():
             assert v <= 1e-4, (k, int(cl[k]), err)
+
+
+def test_fused_configuration_sampled_parity():
+    """The fused workload of bench.py --fused 16 (983,040 tets, 16 simulations, one random
+    moment-tensor source each): one macro step, then the DOFs of sample elements in two
+    simulations of different CTA groups against the oracle on their 17-hop balls."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    F = 16
+    cfg = bench.FUSED_FULL
+    mesh, mat, src, recs = bench.make_workload(**cfg)
+    K = mesh["tet"].shape[0]
+    assert K == 983040
+    g = binding.Solver(bench.ORDER, bench.NMECH, device=0, n_fused=F)
+    g.set_mesh(mesh["xyz"], mesh["tet"], mesh["face_bc"])
+    g.set_material(mat["rho"], mat["vp"], mat["vs"], mat["qp"], mat["qs"], 0.1, 5.0)
+    lx, ly, depth = cfg["nx"] * cfg["h"], cfg["ny"] * cfg["h"], mesh["depth"]
+    pos, m6s, f0s = synth.random_sources(F, [0.1 * lx, 0.1 * ly, -0.6 * depth], [0.9 * lx, 0.9 * ly, -0.05 * depth],
+                                         f0_range=(1.0, 4.0), seed=7)
+    for f in range(F):
+        g.add_point_source(pos[f], m6s[f], f0s[f], 1.2 / f0s[f], src["m0"], fused_idx=f)
+    g.use_torch_memory(bench.NCLUSTERS)
+    cl_g, lam_g, _ = g.setup_clusters(bench.NCLUSTERS, bench.CFL)
+    om = Mesh(mesh["xyz"], mesh["tet"], mesh["face_bc"])
+    dt = olts.cfl_time_steps(om.dins, mat["vp"], bench.ORDER, bench.CFL)
+    lam, cl, _ = olts.search_lambda(dt, om.nbr, bench.NCLUSTERS)
+    assert lam == lam_g and np.array_equal(cl, cl_g)
+    delta = lam * dt.min()
+    rng = np.random.default_rng(19)
+    samples = [int(rng.choice(np.nonzero(cl == l)[0])) for l in range(bench.NCLUSTERS) if np.any(cl == l)][:3]
+    balls = [_ball(om.nbr, k, HOPS) for k in samples]
+    union = np.unique(np.concatenate(balls))
+    init = np.stack([synth.random_dofs(len(union), 27, 35, seed=60 + f) for f in range(F)])
+    g.set_dofs_subset(union, init)
+    row_of = {int(e): i for i, e in enumerate(union)}
+    g.advance_steps(2 ** (bench.NCLUSTERS - 1))
+    got = g.get_dofs_subset(np.array(samples))            # (F, n, 27, 35)
+    for f in (2, 13):
+        src_elem = om.locate(pos[f])
+        for s_i, (k, ball) in enumerate(zip(samples, balls)):
+            tet = mesh["tet"][ball]
+            uv, inv = np.unique(tet, return_inverse=True)
+            bc = mesh["face_bc"][ball].copy()
+            inside = np.isin(om.nbr[ball], ball)
+            bc[(om.nbr[ball] >= 0) & ~inside] = 1
+            sm = Mesh(mesh["xyz"][uv], inv.reshape(tet.shape), bc)
+            o = Oracle(bench.ORDER, bench.NMECH, sm, mat["rho"][ball], mat["vp"][ball], mat["vs"][ball],
+                       mat["qp"][ball], mat["qs"][ball], 0.1, 5.0)
+            o.setup_clusters(bench.NCLUSTERS, bench.CFL, lam=lam, clusters=cl[ball])
+            o.delta = delta
+            o.Q = init[f][[row_of[int(e)] for e in ball]].copy()
+            if src_elem in set(ball.tolist()):
+                o.add_point_source(pos[f], m6s[f], f0s[f], 1.2 / f0s[f], src["m0"])
+            o.run_lts(2 ** (bench.NCLUSTERS - 1))
+            want = o.Q[np.searchsorted(ball, k)][None]
+            err = rel_l2_groups(got[f, s_i][None], want, 27)
+            for name, v in err.items():
+                assert v <= 1e-4, (f, k, err)
