@@ -234,6 +234,14 @@ int lts_set_partition(lts_t* h, int n_parts, const int32_t* part);
  * active cut face and neighbour pass). */
 int lts_exchange_bytes(lts_t* h, int64_t* bytes);
 
+/* Macro steps run as CUDA graphs (default on): the launches of one macro step (Sec. V-B
+ * schedule) are captured once per parity of the macro-step index and replayed, with the
+ * step's source amplitudes and receiver sample times uploaded before each replay. A graph
+ * is re-captured when anything it captured changes (device state, engine, grid shape,
+ * buffers); with profiling enabled the launches are issued directly. enable = 0 issues
+ * every launch directly. */
+int lts_set_graphs(lts_t* h, int enable);
+
 /* Bound of the tensor-core completion waits, in SM cycles (default 2e9, about one second).
  * suppress_commit != 0 is the failure-path test: the kernels issue no tensor-core work, so
  * every wait runs out at the bound, the kernel records the timeout, releases its tensor

@@ -57,6 +57,7 @@ _SIGS = {
     "lts_cut_faces": (_I, [_P, _P, _L, _P, _P]),
     "lts_set_partition": (_I, [_P, _I, _P]),
     "lts_exchange_bytes": (_I, [_P, _P]),
+    "lts_set_graphs": (_I, [_P, _I]),
     "lts_energy_noalloc": (_I, [_I, _I, _P, _P, _L, _P, _P]),
     "lts_reference_operators": (_I, [_I, _P, _P, _P]),
     "lts_eval_basis": (_I, [_I, _L, _P, _P]),
@@ -349,6 +350,9 @@ class Solver:
         b = ctypes.c_int64()
         self._check(lib().lts_exchange_bytes(self._h, ctypes.byref(b)))
         return b.value
+
+    def set_graphs(self, enable=True):
+        self._check(lib().lts_set_graphs(self._h, 1 if enable else 0))
 
     def set_wait_limit(self, cycles=2000000000, suppress_commit=False):
         self._check(lib().lts_set_wait_limit(self._h, int(cycles), 1 if suppress_commit else 0))

@@ -68,6 +68,19 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 }  // namespace
 
+struct GraphKey {
+  const void *seis, *ritems, *sitems, *block;
+  int contraction, ctas_p, ctas_n, suppress, parts;
+  long long wait;
+  size_t n_r, n_s;
+};
+
+struct MacroGraph {
+  cudaGraphExec_t exec = nullptr;
+  GraphKey key{};
+  int launches = 0;
+};
+
 struct lts_solver {
   int order = 0, nmech = 0, device = 0;
   int nsim = 1;                             // fused simulations
@@ -83,6 +96,10 @@ struct lts_solver {
   int* d_cut = nullptr;                     // [3][n_cut]: sender element, code, receiver cluster
   float* d_msg = nullptr;                   // [n_cut][9][F]
   int64_t msg_bytes = 0;                    // face-local message bytes produced so far
+  // macro steps replayed from CUDA graphs (one per parity of the macro-step index)
+  bool use_graphs = true;
+  MacroGraph graphs[2];
+  cudaStream_t capture_stream = nullptr;
   std::string err;
   Launchers L{};
   lts::RefOps ops;
@@ -223,7 +240,16 @@ cudaEvent_t next_event(lts_solver* h) {
   return h->ev_pool[h->ev_used++];
 }
 
+void release_graphs(lts_solver* h) {
+  for (MacroGraph& g : h->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+    g.launches = 0;
+  }
+}
+
 void free_device(lts_solver* h) {
+  release_graphs(h);
   if (h->own_block && h->block) cudaFree(h->block);
   h->block = nullptr;
   h->own_block = false;
@@ -499,37 +525,32 @@ double ricker(double t, double f0, double t0) {
   return (1.0 - 2.0 * a) * std::exp(-a);
 }
 
-void advance_steps(lts_solver* h, int64_t n_finest, cudaStream_t stream) {
-  if (!h->ready) fail(LTS_ERR_STATE, "clusters not set up");
-  const int nc = h->nc;
-  const int64_t period = int64_t(1) << (nc - 1);
-  if (n_finest < 0 || n_finest % period != 0) fail(LTS_ERR_ARG, "n_finest must be a multiple of 2^(N_c-1)");
-  if (n_finest == 0) return;
-  const Launchers& X = h->L;
-  const int B = X.B;
-  const int64_t s0 = h->s_now, s1 = s0 + n_finest;
-  // Taylor coefficients per cluster
-  PhaseArgs base{};
-  for (int l = 0; l < nc; ++l) {
-    const double dl = h->delta * std::ldexp(1.0, l);
-    double fac = 1.0;
-    for (int d = 0; d < h->order; ++d) {
-      fac *= (d + 1);
-      base.coef[l][d] = (float)(std::pow(dl, d + 1) / fac);
-      base.hcoef[l][d] = (float)(std::pow(0.5 * dl, d + 1) / fac);
-    }
-  }
-  for (int l = 0; l < 3; ++l) base.omega[l] = l < (int)h->omega.size() ? (float)h->omega[l] : 0.f;
-  // ---- host plan: source and receiver items for the whole call
-  struct Phase {
-    int kind;          // 0 neighbour, 1 predict
-    int top;           // clusters 0..top
-    int64_t s;
-    int item_beg, item_end;
-  };
-  std::vector<Phase> plan;
+// One macro step (2^(N_c-1) finest steps from time level s_begin) as a fixed sequence of
+// phases: per finest level, the neighbour passes of the clusters ending there, then the
+// receivers and predict passes of the clusters starting there (Sec. V-B). The sequence, the
+// grids and the work-item counts are the same for every macro step; only the parity of the
+// coarsest cluster's step alternates (parity of the macro step) and the work-item values
+// (source amplitudes, receiver sample times) change.
+struct Phase {
+  int kind;          // 0 neighbour, 1 predict
+  int top;           // clusters 0..top
+  int64_t s;
+  int item_beg, item_end;
+};
+
+struct MacroPlan {
+  std::vector<Phase> phases;
   std::vector<SrcItem> sitems;
   std::vector<RecvItem> ritems;
+};
+
+void plan_macro(lts_solver* h, int64_t s_begin, size_t& seis_need, MacroPlan& mp) {
+  const int nc = h->nc;
+  const int B = h->L.B;
+  const int64_t s_end = s_begin + (int64_t(1) << (nc - 1));
+  mp.phases.clear();
+  mp.sitems.clear();
+  mp.ritems.clear();
   std::vector<double> gx, gw;
   lts::gauss_jacobi(h->order, 0.0, gx, gw);
   auto top_cluster = [&](int64_t s) {
@@ -537,10 +558,9 @@ void advance_steps(lts_solver* h, int64_t n_finest, cudaStream_t stream) {
     while (l + 1 < nc && s % (int64_t(1) << (l + 1)) == 0) ++l;
     return l;
   };
-  size_t seis_need = h->seis_used;
-  for (int64_t s = s0; s <= s1; ++s) {
-    if (s > s0) {
-      Phase ph{0, top_cluster(s), s, (int)sitems.size(), 0};
+  for (int64_t s = s_begin; s <= s_end; ++s) {
+    if (s > s_begin) {
+      Phase ph{0, top_cluster(s), s, (int)mp.sitems.size(), 0};
       for (size_t si = 0; si < h->sources.size(); ++si) {
         const Source& src = h->sources[si];
         const int l = h->cluster[src.elem];
@@ -555,13 +575,13 @@ void advance_steps(lts_solver* h, int64_t n_finest, cudaStream_t stream) {
         it.sim = src.sim;
         it.phi_off = (int)(si * B);
         for (int r = 0; r < 6; ++r) it.amp[r] = (float)(-src.m0 * src.m6[r] * integ / h->mesh.detJ[src.elem]);
-        sitems.push_back(it);
+        mp.sitems.push_back(it);
       }
-      ph.item_end = (int)sitems.size();
-      plan.push_back(ph);
+      ph.item_end = (int)mp.sitems.size();
+      mp.phases.push_back(ph);
     }
-    if (s < s1) {
-      Phase ph{1, top_cluster(s), s, (int)ritems.size(), 0};
+    if (s < s_end) {
+      Phase ph{1, top_cluster(s), s, (int)mp.ritems.size(), 0};
       for (size_t ri = 0; ri < h->receivers.size(); ++ri) {
         Receiver& rc = h->receivers[ri];
         const int l = h->cluster[rc.elem];
@@ -572,6 +592,7 @@ void advance_steps(lts_solver* h, int64_t n_finest, cudaStream_t stream) {
         it.sim = 0;
         it.phi_off = (int)(ri * B);
         it.n = 0;
+        it.out_off = 0;
         int64_t j = std::max<int64_t>((int64_t)std::floor(ta / rc.dt) - 1, 0);
         for (; j * rc.dt < tb; ++j) {
           const double tj = j * rc.dt;
@@ -584,35 +605,43 @@ void advance_steps(lts_solver* h, int64_t n_finest, cudaStream_t stream) {
           ++seis_need;
           ++it.n;
         }
-        // one item per simulation; sample slot j holds nsim x 9 values
-        for (int f = 0; it.n > 0 && f < h->nsim; ++f) {
+        // one item per simulation (also without samples: the item count of a phase is
+        // fixed); sample slot j holds nsim x 9 values
+        for (int f = 0; f < h->nsim; ++f) {
           it.sim = f;
-          ritems.push_back(it);
+          mp.ritems.push_back(it);
         }
       }
-      ph.item_end = (int)ritems.size();
-      plan.push_back(ph);
+      ph.item_end = (int)mp.ritems.size();
+      mp.phases.push_back(ph);
     }
   }
-  ensure_capacity(reinterpret_cast<void**>(&h->d_seis), &h->seis_cap, seis_need * 9 * h->nsim, sizeof(float));
-  ensure_capacity(reinterpret_cast<void**>(&h->d_ritems), &h->ritems_cap, ritems.size(), sizeof(RecvItem));
-  ensure_capacity(reinterpret_cast<void**>(&h->d_sitems), &h->sitems_cap, sitems.size(), sizeof(SrcItem));
-  if (!ritems.empty())
-    ck(cudaMemcpyAsync(h->d_ritems, ritems.data(), ritems.size() * sizeof(RecvItem), cudaMemcpyHostToDevice, stream),
-       "upload receiver items");
-  if (!sitems.empty())
-    ck(cudaMemcpyAsync(h->d_sitems, sitems.data(), sitems.size() * sizeof(SrcItem), cudaMemcpyHostToDevice, stream),
-       "upload source items");
-  h->h2d_bytes += (int64_t)(ritems.size() * sizeof(RecvItem) + sitems.size() * sizeof(SrcItem));
-  h->seis_used = seis_need;
-  // ---- launches
+}
+
+// Enqueues the launches of one macro step on `stream` (items at the start of the item
+// buffers); returns the number of kernels launched.
+int enqueue_macro(lts_solver* h, const MacroPlan& mp, cudaStream_t stream) {
+  const Launchers& X = h->L;
+  const int nc = h->nc;
+  PhaseArgs base{};
+  for (int l = 0; l < nc; ++l) {
+    const double dl = h->delta * std::ldexp(1.0, l);
+    double fac = 1.0;
+    for (int d = 0; d < h->order; ++d) {
+      fac *= (d + 1);
+      base.coef[l][d] = (float)(std::pow(dl, d + 1) / fac);
+      base.hcoef[l][d] = (float)(std::pow(0.5 * dl, d + 1) / fac);
+    }
+  }
+  for (int l = 0; l < 3; ++l) base.omega[l] = l < (int)h->omega.size() ? (float)h->omega[l] : 0.f;
   const bool use_tc = h->contraction != LTS_CONTRACT_FP32;
   const int passes = h->contraction == LTS_CONTRACT_TF32X3 ? 3 : 1;
   const int maxp = std::max(1, use_tc ? X.blocks_predict_tc : X.blocks_predict);
   const int maxn = std::max(1, X.blocks_neighbour);
   const int grid_cap_p = h->num_sms * (h->ctas_predict > 0 ? std::min(h->ctas_predict, maxp) : maxp);
   const int grid_cap_n = h->num_sms * (h->ctas_neighbour > 0 ? std::min(h->ctas_neighbour, maxn) : maxn);
-  for (const Phase& ph : plan) {
+  int launches = 0;
+  for (const Phase& ph : mp.phases) {
     PhaseArgs pa = base;
     pa.begin = 0;
     pa.end = (int)h->cbeg[ph.top + 1];
@@ -628,14 +657,13 @@ void advance_steps(lts_solver* h, int64_t n_finest, cudaStream_t stream) {
     if (ph.kind == 1 && ph.item_end > ph.item_beg) {
       X.receivers(h->dops, h->dst.Q, h->dst.qs, h->nsim, X.FG, h->dst.edata, h->d_recv_phi, h->d_ritems + ph.item_beg,
                   h->d_seis, base.omega, ph.item_end - ph.item_beg, stream);
-      ++h->launches;
+      ++launches;
     }
     if (ph.kind == 0 && h->n_parts > 1 && h->cut_beg[ph.top + 1] > 0) {
       // the neighbours' partitions compute the face-local messages of the active cut faces
       const int nact = (int)h->cut_beg[ph.top + 1];
       X.pack(h->dops, h->dst, pa, h->d_cut, h->d_cut + h->n_cut, h->d_cut + 2 * h->n_cut, nact, h->d_msg, stream);
-      ++h->launches;
-      h->msg_bytes += (int64_t)nact * 9 * X.F * (int64_t)sizeof(float);
+      ++launches;
     }
     if (h->profiling) ck(cudaEventRecord(next_event(h), stream), "event record");
     if (ph.kind == 0)
@@ -645,7 +673,7 @@ void advance_steps(lts_solver* h, int64_t n_finest, cudaStream_t stream) {
                    h->suppress_commit, stream);
     else
       X.predict(h->dops, h->dst, pa, std::min(nb, grid_cap_p), stream);
-    ++h->launches;
+    ++launches;
     if (h->profiling) {
       ck(cudaEventRecord(next_event(h), stream), "event record");
       h->ev_kind.push_back(ph.kind == 1 ? 0 : 1);
@@ -654,11 +682,98 @@ void advance_steps(lts_solver* h, int64_t n_finest, cudaStream_t stream) {
     if (ph.kind == 0 && ph.item_end > ph.item_beg) {
       X.sources(h->dst.Q, h->dst.qs, X.FG, h->d_src_phi, h->d_sitems + ph.item_beg, ph.item_end - ph.item_beg,
                 stream);
-      ++h->launches;
+      ++launches;
     }
   }
   ck(cudaGetLastError(), "kernel launch");
-  h->s_now = s1;
+  return launches;
+}
+
+// Face-local message bytes of one macro step of a partitioned run.
+int64_t macro_msg_bytes(const lts_solver* h, const MacroPlan& mp) {
+  int64_t b = 0;
+  if (h->n_parts <= 1) return 0;
+  for (const Phase& ph : mp.phases)
+    if (ph.kind == 0 && h->cbeg[ph.top + 1] > 0)
+      b += h->cut_beg[ph.top + 1] * 9 * (int64_t)h->L.F * (int64_t)sizeof(float);
+  return b;
+}
+
+void advance_steps(lts_solver* h, int64_t n_finest, cudaStream_t stream) {
+  if (!h->ready) fail(LTS_ERR_STATE, "clusters not set up");
+  const int nc = h->nc;
+  const int64_t period = int64_t(1) << (nc - 1);
+  if (n_finest < 0 || n_finest % period != 0) fail(LTS_ERR_ARG, "n_finest must be a multiple of 2^(N_c-1)");
+  if (n_finest == 0) return;
+  const int64_t s0 = h->s_now, nmac = n_finest / period;
+  // host plans of every macro step (receiver sample slots are assigned here)
+  std::vector<MacroPlan> plans(nmac);
+  size_t seis_need = h->seis_used;
+  for (int64_t m = 0; m < nmac; ++m) plan_macro(h, s0 + m * period, seis_need, plans[m]);
+  ensure_capacity(reinterpret_cast<void**>(&h->d_seis), &h->seis_cap, seis_need * 9 * h->nsim, sizeof(float));
+  ensure_capacity(reinterpret_cast<void**>(&h->d_ritems), &h->ritems_cap, plans[0].ritems.size(), sizeof(RecvItem));
+  ensure_capacity(reinterpret_cast<void**>(&h->d_sitems), &h->sitems_cap, plans[0].sitems.size(), sizeof(SrcItem));
+  h->seis_used = seis_need;
+  for (int64_t m = 0; m < nmac; ++m) {
+    const MacroPlan& mp = plans[m];
+    // this macro step's work items; stream-ordered after the previous macro step
+    if (!mp.ritems.empty())
+      ck(cudaMemcpyAsync(h->d_ritems, mp.ritems.data(), mp.ritems.size() * sizeof(RecvItem), cudaMemcpyHostToDevice,
+                         stream),
+         "upload receiver items");
+    if (!mp.sitems.empty())
+      ck(cudaMemcpyAsync(h->d_sitems, mp.sitems.data(), mp.sitems.size() * sizeof(SrcItem), cudaMemcpyHostToDevice,
+                         stream),
+         "upload source items");
+    h->h2d_bytes += (int64_t)(mp.ritems.size() * sizeof(RecvItem) + mp.sitems.size() * sizeof(SrcItem));
+    h->msg_bytes += macro_msg_bytes(h, mp);
+    if (!h->use_graphs || h->profiling) {
+      h->launches += enqueue_macro(h, mp, stream);
+      continue;
+    }
+    // CUDA graph of the macro step, one per parity of the macro-step index, rebuilt when
+    // anything its launches capture has changed
+    const int par = (int)(((s0 / period) + m) & 1);
+    GraphKey key{};
+    key.seis = h->d_seis;
+    key.ritems = h->d_ritems;
+    key.sitems = h->d_sitems;
+    key.block = h->block;
+    key.contraction = h->contraction;
+    key.ctas_p = h->ctas_predict;
+    key.ctas_n = h->ctas_neighbour;
+    key.wait = h->wait_cycles;
+    key.suppress = h->suppress_commit;
+    key.parts = h->n_parts;
+    key.n_r = mp.ritems.size();
+    key.n_s = mp.sitems.size();
+    MacroGraph& g = h->graphs[par];
+    if (!g.exec || std::memcmp(&g.key, &key, sizeof(GraphKey)) != 0) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      g.exec = nullptr;
+      if (!h->capture_stream) ck(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking), "capture stream");
+      ck(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+      int nl = 0;
+      try {
+        nl = enqueue_macro(h, mp, h->capture_stream);
+      } catch (...) {
+        cudaGraph_t tmp = nullptr;
+        cudaStreamEndCapture(h->capture_stream, &tmp);
+        if (tmp) cudaGraphDestroy(tmp);
+        throw;
+      }
+      cudaGraph_t graph = nullptr;
+      ck(cudaStreamEndCapture(h->capture_stream, &graph), "end capture");
+      cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
+      cudaGraphDestroy(graph);
+      ck(e, "graph instantiate");
+      g.key = key;
+      g.launches = nl;
+    }
+    ck(cudaGraphLaunch(g.exec, stream), "graph launch");
+    h->launches += g.launches;
+  }
+  h->s_now = s0 + n_finest;
 }
 
 }  // namespace
@@ -701,6 +816,7 @@ void lts_destroy(lts_t* h) {
   if (h->device >= 0) cudaSetDevice(h->device);
   free_device(h);
   release_events(h);
+  if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
   delete h;
 }
 
@@ -1314,6 +1430,13 @@ int lts_exchange_bytes(lts_t* h, int64_t* bytes) {
   return run(h, [&] {
     if (!bytes) fail(LTS_ERR_ARG, "null output");
     *bytes = h->msg_bytes;
+  });
+}
+
+int lts_set_graphs(lts_t* h, int enable) {
+  return run(h, [&] {
+    h->use_graphs = enable != 0;
+    if (!h->use_graphs) release_graphs(h);
   });
 }
 
