@@ -234,6 +234,32 @@ int lts_set_partition(lts_t* h, int n_parts, const int32_t* part);
  * active cut face and neighbour pass). */
 int lts_exchange_bytes(lts_t* h, int64_t* bytes);
 
+/* Overrides the finest time step (after cluster set-up) with dt seconds, e.g. to hold the
+ * step fixed while the material changes (the adjoint's finite-difference checks). The
+ * caller is responsible for stability. Errors: LTS_ERR_STATE, LTS_ERR_ARG (dt <= 0). */
+int lts_set_finest_dt(lts_t* h, double dt);
+
+/* Discrete adjoint of the global-time-stepping loop (the misfit objective of Sec. VII-B,
+ * summed): from the current state, advances n_steps steps of the elastic scheme (the same
+ * launches as lts_advance_steps, sources included) and evaluates
+ *   J = 1/2 sum_{n=0..N} sum_r sum_q (v_q(x_r, t_n) - data[n][r][q])^2,
+ * v the particle velocity (u, v, w) at receiver r (the handle's receivers, in order)
+ * sampled at the step boundaries t_n = t_0 + n dt. The reverse sweep applies the
+ * transposed time, volume, local and neighbour surface operators step by step,
+ * recomputing the forward states from checkpoints stored every `every` steps, and
+ * correlates the adjoint with the forward states; the correlations are contracted with
+ * the exact derivatives (forward-mode dual numbers) of the star matrices and the face
+ * flux solvers with respect to each element's rho, lambda, mu — the face terms also
+ * with respect to the neighbour's. Outputs (each may be NULL except data): *misfit J,
+ * grad[n_tet][3] = dJ/d(rho, lambda, mu) per element (original order), synth_out[N+1][n_rec][3]
+ * the samples, dq0[n_tet][9][B] = dJ/dQ at the start. The time step is held fixed. The
+ * state ends at t_N (as after lts_advance_steps). Needs one cluster (global time
+ * stepping), n_mech = 0, one simulation, no partition, at least one receiver. Device
+ * memory: (ceil(N/every) + min(every, N) + 1) copies of Q plus per-element operators.
+ * Errors: LTS_ERR_ARG, LTS_ERR_STATE, LTS_ERR_OOM, LTS_ERR_CUDA. */
+int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* data, double* misfit,
+                        double* grad, double* synth_out, double* dq0, void* cuda_stream);
+
 /* Macro steps run as CUDA graphs (default on): the launches of one macro step (Sec. V-B
  * schedule) are captured once per parity of the macro-step index and replayed, with the
  * step's source amplitudes and receiver sample times uploaded before each replay. A graph

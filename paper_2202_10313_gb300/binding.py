@@ -58,6 +58,8 @@ _SIGS = {
     "lts_set_partition": (_I, [_P, _I, _P]),
     "lts_exchange_bytes": (_I, [_P, _P]),
     "lts_set_graphs": (_I, [_P, _I]),
+    "lts_set_finest_dt": (_I, [_P, _D]),
+    "lts_misfit_gradient": (_I, [_P, _L, _L, _P, _P, _P, _P, _P, _P]),
     "lts_energy_noalloc": (_I, [_I, _I, _P, _P, _L, _P, _P]),
     "lts_reference_operators": (_I, [_I, _P, _P, _P]),
     "lts_eval_basis": (_I, [_I, _L, _P, _P]),
@@ -350,6 +352,22 @@ class Solver:
         b = ctypes.c_int64()
         self._check(lib().lts_exchange_bytes(self._h, ctypes.byref(b)))
         return b.value
+
+    def set_finest_dt(self, dt):
+        self._check(lib().lts_set_finest_dt(self._h, float(dt)))
+
+    def misfit_gradient(self, n_steps, data, every=100, stream=None, want_dq0=False):
+        """J, dJ/d(rho, lambda, mu) (K, 3), synthetic samples (N+1, n_rec, 3) and optionally
+        dJ/dQ at the start (K, 9, B), by the discrete adjoint of the GTS loop."""
+        data = _f64(data)
+        nrec = data.size // (3 * (int(n_steps) + 1))
+        J = ctypes.c_double()
+        grad = np.zeros((self.K, 3))
+        syn = np.zeros((int(n_steps) + 1, nrec, 3))
+        dq0 = np.zeros((self.K, 9, self.nb)) if want_dq0 else None
+        self._check(lib().lts_misfit_gradient(self._h, int(n_steps), int(every), _ptr(data), ctypes.byref(J),
+                                              _ptr(grad), _ptr(syn), _ptr(dq0), _stream_handle(stream)))
+        return (J.value, grad, syn, dq0) if want_dq0 else (J.value, grad, syn)
 
     def set_graphs(self, enable=True):
         self._check(lib().lts_set_graphs(self._h, 1 if enable else 0))

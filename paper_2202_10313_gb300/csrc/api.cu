@@ -1,6 +1,8 @@
 // C ABI of the solver: set-up tables, device state and the clustered-LTS schedule.
 #include <algorithm>
 #include <array>
+#include <thread>
+#include <type_traits>
 #include <cmath>
 #include <cstring>
 #include <functional>
@@ -11,9 +13,11 @@
 
 #include "../../include/ader_lts.h"
 #include "host.h"
+#include "host_flux.h"
 #include "host_partition.h"
 #include "launch.h"
 
+using ltsdev::AdjArgs;
 using ltsdev::DevOps;
 using ltsdev::DevState;
 using ltsdev::Launchers;
@@ -263,35 +267,6 @@ void free_device(lts_solver* h) {
   h->ready = false;
 }
 
-// Flux coefficients of one face: (n, a[4], b[4]) for the interior state and for the
-// exterior state, scaled by -2|S|/|det J|. Normal (P) and tangential (S) pairs:
-//   v* = (Z- v- + Z+ v+ + t+ - t-)/(Z- + Z+),  t* = (Z+ t- + Z- t+ + Z- Z+ (v+ - v-))/(Z- + Z+)
-// free surface: t* = 0, v* = v- - t-/Z-; absorbing: exterior state zero, Z+ = Z-.
-void face_coefficients(int bc, double zp_i, double zs_i, double zp_o, double zs_o, double scale, float* loc,
-                       float* nbc) {
-  double a[4], b[4], an[4], bn[4];
-  if (bc == LTS_BC_FREE_SURFACE) {
-    a[0] = 1.0; a[1] = -1.0 / zp_i; a[2] = 0.0; a[3] = 0.0;
-    b[0] = 1.0; b[1] = -1.0 / zs_i; b[2] = 0.0; b[3] = 0.0;
-    for (int i = 0; i < 4; ++i) an[i] = bn[i] = 0.0;
-  } else {
-    if (bc == LTS_BC_ABSORBING) { zp_o = zp_i; zs_o = zs_i; }
-    double sp = zp_i + zp_o, ss = zs_i + zs_o;
-    a[0] = zp_i / sp; a[1] = -1.0 / sp; a[2] = zp_o / sp; a[3] = -zp_i * zp_o / sp;
-    b[0] = zs_i / ss; b[1] = -1.0 / ss; b[2] = zs_o / ss; b[3] = -zs_i * zs_o / ss;
-    an[0] = zp_o / sp; an[1] = 1.0 / sp; an[2] = zp_i / sp; an[3] = zp_i * zp_o / sp;
-    bn[0] = zs_o / ss; bn[1] = 1.0 / ss; bn[2] = zs_i / ss; bn[3] = zs_i * zs_o / ss;
-    if (bc == LTS_BC_ABSORBING)
-      for (int i = 0; i < 4; ++i) an[i] = bn[i] = 0.0;
-  }
-  for (int i = 0; i < 4; ++i) {
-    loc[i] = (float)(scale * a[i]);
-    loc[4 + i] = (float)(scale * b[i]);
-    nbc[i] = (float)(scale * an[i]);
-    nbc[4 + i] = (float)(scale * bn[i]);
-  }
-}
-
 void setup_device(lts_solver* h) {
   const int64_t K = h->mesh.K;
   const Launchers& X = h->L;
@@ -346,7 +321,12 @@ void setup_device(lts_solver* h) {
       float* lf = ed + 20 + 11 * f;
       float* nf = nd + 4 + 11 * f;
       for (int d = 0; d < 3; ++d) lf[d] = nf[d] = (float)M.normal[12 * k + 3 * f + d];
-      face_coefficients(bc, zp, zs, zpo, zso, scale, lf + 3, nf + 3);
+      double cl[8], cn[8];
+      lts::face_coefficients_t<double>(bc, zp, zs, zpo, zso, scale, cl, cn);
+      for (int q = 0; q < 8; ++q) {
+        lf[3 + q] = (float)cl[q];
+        nf[3 + q] = (float)cn[q];
+      }
       if (nb >= 0) {
         nbr[4 * nk + f] = (int)h->iperm[nb];
         const int dc = h->cluster[nb] - h->cluster[k];
@@ -775,6 +755,61 @@ void advance_steps(lts_solver* h, int64_t n_finest, cudaStream_t stream) {
   }
   h->s_now = s0 + n_finest;
 }
+
+// ------------------------------------------------------------------ discrete adjoint
+// Explicit 9 x 9 operators of element k (original index) in FP64: star matrices S_c and, per
+// face, the flux solvers A- (interior state) and A+ (exterior state), from the closed forms
+// of the forward set-up. With T = lts::Dual, the seeded material parameter's derivative
+// rides along: param 0-2 the element's (rho, lambda, mu), 3-5 the face neighbour's of face
+// `face` (ignored for the star matrices and for boundary faces); -1 seeds nothing.
+template <typename T>
+void element_operators(const lts_solver* h, int64_t k, int face, int param, T S[3][81], T Am[81], T Ap[81]) {
+  const lts::Mesh& M = h->mesh;
+  auto mat = [&](int64_t e, int base) {
+    T rho(h->mat.rho[e]), lam(h->lam[e]), mu(h->mu[e]);
+    if constexpr (std::is_same<T, lts::Dual>::value) {
+      if (param == base + 0) rho.d = 1.0;
+      if (param == base + 1) lam.d = 1.0;
+      if (param == base + 2) mu.d = 1.0;
+    }
+    return std::array<T, 3>{rho, lam, mu};
+  };
+  const auto own = mat(k, 0);
+  const T rinv = T(1.0) / own[0];
+  if (S) lts::star_matrices_t<T>(&M.Jinv[9 * k], own[1], own[2], rinv, S);
+  if (face < 0) return;
+  const int bc = M.bc[4 * k + face];
+  const int64_t nb = M.nbr[4 * k + face];
+  const auto oth = nb >= 0 ? mat(nb, 3) : own;
+  const T zp = lts::sqrt_t((own[1] + T(2.0) * own[2]) * own[0]), zs = lts::sqrt_t(own[2] * own[0]);
+  const T zpo = nb >= 0 ? lts::sqrt_t((oth[1] + T(2.0) * oth[2]) * oth[0]) : zp;
+  const T zso = nb >= 0 ? lts::sqrt_t(oth[2] * oth[0]) : zs;
+  const T scale(-2.0 * M.area[4 * k + face] / M.detJ[k]);
+  T cl[8], cn[8];
+  lts::face_coefficients_t<T>(bc, zp, zs, zpo, zso, scale, cl, cn);
+  lts::face_flux_matrix<T>(&M.normal[12 * k + 3 * face], cl, own[1], own[2], rinv, Am);
+  lts::face_flux_matrix<T>(&M.normal[12 * k + 3 * face], cn, own[1], own[2], rinv, Ap);
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  template <typename T>
+  T* get() const {
+    return static_cast<T*>(p);
+  }
+  void alloc(size_t bytes) {
+    if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+      p = nullptr;
+      cudaGetLastError();
+      fail(LTS_ERR_OOM, "device allocation for the adjoint failed");
+    }
+  }
+};
 
 }  // namespace
 
@@ -1430,6 +1465,228 @@ int lts_exchange_bytes(lts_t* h, int64_t* bytes) {
   return run(h, [&] {
     if (!bytes) fail(LTS_ERR_ARG, "null output");
     *bytes = h->msg_bytes;
+  });
+}
+
+int lts_set_finest_dt(lts_t* h, double dt) {
+  return run(h, [&] {
+    if ((int64_t)h->cluster.size() != h->mesh.K) fail(LTS_ERR_STATE, "clusters not set up");
+    if (!(dt > 0.0)) fail(LTS_ERR_ARG, "time step must be positive");
+    h->delta = dt;
+    release_graphs(h);
+  });
+}
+
+int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* data, double* misfit, double* grad,
+                        double* synth_out, double* dq0, void* cuda_stream) {
+  return run(h, [&] {
+    if (!h->ready) fail(LTS_ERR_STATE, "clusters not set up");
+    const Launchers& X = h->L;
+    if (h->nc != 1 || h->nmech != 0 || h->nsim != 1 || h->n_parts > 1 || !X.adj_step)
+      fail(LTS_ERR_ARG, "the adjoint covers global time stepping, elastic, one simulation, no partition");
+    const int nrec = (int)h->receivers.size();
+    if (nrec < 1 || n_steps < 1 || every < 1 || !data) fail(LTS_ERR_ARG, "bad adjoint arguments");
+    ck(cudaSetDevice(h->device), "cudaSetDevice");
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    const int64_t K = h->mesh.K;
+    const int B = X.B, NB9 = 9 * B;
+    const int64_t qs = h->dst.qs;
+    // ---- explicit operators (internal order) and face links
+    std::vector<float> amat((size_t)K * ltsdev::AM_SIZE);
+    std::vector<int> fwd(8 * K, -1), back(8 * K, 0);
+    for (int64_t k = 0; k < K; ++k) {
+      const int64_t nk = h->iperm[k];
+      double S[3][81], Am[81], Ap[81];
+      element_operators<double>(h, k, -1, -1, S, nullptr, nullptr);
+      for (int c = 0; c < 3; ++c)
+        for (int q = 0; q < 81; ++q) amat[nk * ltsdev::AM_SIZE + ltsdev::AM_STAR + c * 81 + q] = (float)S[c][q];
+      for (int i = 0; i < 4; ++i) {
+        element_operators<double>(h, k, i, -1, nullptr, Am, Ap);
+        for (int q = 0; q < 81; ++q) {
+          amat[nk * ltsdev::AM_SIZE + ltsdev::AM_LOC + i * 81 + q] = (float)Am[q];
+          amat[nk * ltsdev::AM_SIZE + ltsdev::AM_NBR + i * 81 + q] = (float)Ap[q];
+        }
+        const int64_t nb = h->mesh.nbr[4 * k + i];
+        if (nb < 0) continue;
+        const int ip = h->mesh.nbr_face[4 * k + i];
+        fwd[8 * nk + 2 * i] = (int)h->iperm[nb];
+        fwd[8 * nk + 2 * i + 1] = ip * 3 + h->mesh.nbr_orient[4 * k + i];
+        back[8 * nk + 2 * i] = ip;
+        back[8 * nk + 2 * i + 1] = i * 3 + h->mesh.nbr_orient[4 * nb + ip];
+      }
+    }
+    std::vector<int> relem(nrec);
+    std::vector<float> rphi((size_t)nrec * B);
+    for (int r = 0; r < nrec; ++r) {
+      relem[r] = (int)h->iperm[h->receivers[r].elem];
+      for (int b = 0; b < B; ++b) rphi[(size_t)r * B + b] = (float)h->receivers[r].phi[b];
+    }
+    // ---- device buffers
+    const int64_t ncp = (n_steps + every - 1) / every;
+    const int64_t seg = std::min(every, n_steps);
+    DevBuf d_amat, d_fwd, d_back, d_relem, d_rphi, d_syn, d_res, d_t, d_la, d_lb, d_w, d_cp, d_seg, d_qn;
+    d_amat.alloc(sizeof(float) * amat.size());
+    d_fwd.alloc(sizeof(int) * fwd.size());
+    d_back.alloc(sizeof(int) * back.size());
+    d_relem.alloc(sizeof(int) * nrec);
+    d_rphi.alloc(sizeof(float) * rphi.size());
+    d_syn.alloc(sizeof(float) * (n_steps + 1) * nrec * 3);
+    d_res.alloc(sizeof(float) * (n_steps + 1) * nrec * 3);
+    d_t.alloc(sizeof(float) * K * NB9);
+    d_la.alloc(sizeof(float) * K * NB9);
+    d_lb.alloc(sizeof(float) * K * NB9);
+    d_w.alloc(sizeof(double) * K * ltsdev::AM_SIZE);
+    d_cp.alloc(sizeof(float) * ncp * K * qs);
+    d_seg.alloc(sizeof(float) * seg * K * qs);
+    d_qn.alloc(sizeof(float) * K * qs);
+    auto up = [&](void* dst, const void* src, size_t bytes) {
+      ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, stream), "adjoint upload");
+    };
+    up(d_amat.p, amat.data(), sizeof(float) * amat.size());
+    up(d_fwd.p, fwd.data(), sizeof(int) * fwd.size());
+    up(d_back.p, back.data(), sizeof(int) * back.size());
+    up(d_relem.p, relem.data(), sizeof(int) * nrec);
+    up(d_rphi.p, rphi.data(), sizeof(float) * rphi.size());
+    const size_t qbytes = sizeof(float) * K * qs;
+    auto dcopy = [&](void* dst, const void* src) {
+      ck(cudaMemcpyAsync(dst, src, qbytes, cudaMemcpyDeviceToDevice, stream), "adjoint copy");
+    };
+    float* cp = d_cp.get<float>();
+    float* sg = d_seg.get<float>();
+    // ---- forward sweep with checkpoints every `every` steps
+    const int64_t s0 = h->s_now;
+    const size_t seis0 = h->seis_used;
+    std::vector<size_t> nrec_t(nrec);
+    dcopy(cp, h->dst.Q);
+    X.adj_sample(h->dst.Q, qs, d_relem.get<int>(), d_rphi.get<float>(), nrec, d_syn.get<float>(), stream);
+    for (int64_t n = 0; n < n_steps; ++n) {
+      advance_steps(h, 1, stream);
+      X.adj_sample(h->dst.Q, qs, d_relem.get<int>(), d_rphi.get<float>(), nrec, d_syn.get<float>() + (n + 1) * nrec * 3,
+                   stream);
+      if ((n + 1) % every == 0 && n + 1 < n_steps) dcopy(cp + ((n + 1) / every) * K * qs, h->dst.Q);
+    }
+    for (int r = 0; r < nrec; ++r) nrec_t[r] = h->receivers[r].t.size();
+    const size_t seis_fwd = h->seis_used;
+    dcopy(d_qn.p, h->dst.Q);
+    std::vector<float> syn((size_t)(n_steps + 1) * nrec * 3);
+    ck(cudaMemcpyAsync(syn.data(), d_syn.p, sizeof(float) * syn.size(), cudaMemcpyDeviceToHost, stream), "samples");
+    ck(cudaStreamSynchronize(stream), "synchronize");
+    check_device_error(h);
+    std::vector<float> res(syn.size());
+    double J = 0.0;
+    for (size_t q = 0; q < syn.size(); ++q) {
+      const double r = (double)syn[q] - data[q];
+      res[q] = (float)r;
+      J += 0.5 * r * r;
+    }
+    up(d_res.p, res.data(), sizeof(float) * res.size());
+    // ---- reverse sweep
+    ck(cudaMemsetAsync(d_la.p, 0, sizeof(float) * K * NB9, stream), "memset");
+    ck(cudaMemsetAsync(d_w.p, 0, sizeof(double) * K * ltsdev::AM_SIZE, stream), "memset");
+    float* lam_a = d_la.get<float>();
+    float* lam_b = d_lb.get<float>();
+    X.adj_source(lam_a, d_relem.get<int>(), d_rphi.get<float>(), d_res.get<float>() + n_steps * nrec * 3, nrec,
+                 stream);
+    AdjArgs aa{};
+    aa.tbuf = d_t.get<float>();
+    aa.amat = d_amat.get<float>();
+    aa.fwd = d_fwd.get<int>();
+    aa.back = d_back.get<int>();
+    aa.W = d_w.get<double>();
+    aa.qs = qs;
+    {
+      double fac = 1.0;
+      for (int d = 0; d < h->order; ++d) {
+        fac *= (d + 1);
+        aa.cd[d] = (float)(std::pow(h->delta, d + 1) / fac);
+      }
+    }
+    for (int64_t sgi = ncp - 1; sgi >= 0; --sgi) {
+      const int64_t c0 = sgi * every, c1 = std::min(c0 + every, n_steps);
+      // recompute Q^c0 .. Q^(c1-1) from the checkpoint
+      dcopy(h->dst.Q, cp + sgi * K * qs);
+      h->s_now = s0 + c0;
+      dcopy(sg, h->dst.Q);
+      for (int64_t n = c0; n + 1 < c1; ++n) {
+        advance_steps(h, 1, stream);
+        dcopy(sg + (n + 1 - c0) * K * qs, h->dst.Q);
+      }
+      for (int64_t n = c1 - 1; n >= c0; --n) {
+        aa.Q = sg + (n - c0) * K * qs;
+        X.adj_T(h->dops, aa, d_t.get<float>(), (int)K, stream);
+        aa.lam_in = lam_a;
+        aa.lam_out = lam_b;
+        X.adj_step(h->dops, aa, (int)K, stream);
+        std::swap(lam_a, lam_b);
+        X.adj_source(lam_a, d_relem.get<int>(), d_rphi.get<float>(), d_res.get<float>() + n * nrec * 3, nrec, stream);
+      }
+      for (int r = 0; r < nrec; ++r) {
+        h->receivers[r].t.resize(nrec_t[r]);
+        h->receivers[r].slot.resize(nrec_t[r]);
+      }
+      h->seis_used = seis_fwd;
+    }
+    ck(cudaGetLastError(), "adjoint kernels");
+    // the state ends at t_N as after a plain advance
+    dcopy(h->dst.Q, d_qn.p);
+    h->s_now = s0 + n_steps;
+    (void)seis0;
+    std::vector<double> W((size_t)K * ltsdev::AM_SIZE);
+    ck(cudaMemcpyAsync(W.data(), d_w.p, sizeof(double) * W.size(), cudaMemcpyDeviceToHost, stream), "correlations");
+    std::vector<float> lq;
+    if (dq0) {
+      lq.resize((size_t)K * NB9);
+      ck(cudaMemcpyAsync(lq.data(), lam_a, sizeof(float) * lq.size(), cudaMemcpyDeviceToHost, stream), "adjoint state");
+    }
+    ck(cudaStreamSynchronize(stream), "synchronize");
+    check_device_error(h);
+    if (misfit) *misfit = J;
+    if (synth_out)
+      for (size_t q = 0; q < syn.size(); ++q) synth_out[q] = syn[q];
+    if (dq0)
+      for (int64_t k = 0; k < K; ++k)
+        for (int q = 0; q < NB9; ++q) dq0[k * NB9 + q] = lq[h->iperm[k] * NB9 + q];
+    // ---- gradient: correlations against the exact material derivatives of the operators
+    if (grad) {
+      auto work = [&](int64_t k0, int64_t k1) {
+        lts::Dual S[3][81], Am[81], Ap[81];
+        for (int64_t e = k0; e < k1; ++e) {
+          const double* We = &W[h->iperm[e] * ltsdev::AM_SIZE];
+          double g[3] = {0, 0, 0};
+          for (int p = 0; p < 3; ++p) {
+            element_operators<lts::Dual>(h, e, -1, p, S, nullptr, nullptr);
+            for (int c = 0; c < 3; ++c)
+              for (int q = 0; q < 81; ++q) g[p] += S[c][q].d * We[ltsdev::AM_STAR + c * 81 + q];
+          }
+          for (int i = 0; i < 4; ++i) {
+            for (int p = 0; p < 3; ++p) {
+              element_operators<lts::Dual>(h, e, i, p, nullptr, Am, Ap);
+              for (int q = 0; q < 81; ++q)
+                g[p] += Am[q].d * We[ltsdev::AM_LOC + i * 81 + q] + Ap[q].d * We[ltsdev::AM_NBR + i * 81 + q];
+            }
+            // the neighbour's face that looks at e: its operators depend on e's material
+            const int64_t nb = h->mesh.nbr[4 * e + i];
+            if (nb < 0) continue;
+            const int ip = h->mesh.nbr_face[4 * e + i];
+            const double* Wn = &W[h->iperm[nb] * ltsdev::AM_SIZE];
+            for (int p = 0; p < 3; ++p) {
+              element_operators<lts::Dual>(h, nb, ip, 3 + p, nullptr, Am, Ap);
+              for (int q = 0; q < 81; ++q)
+                g[p] += Am[q].d * Wn[ltsdev::AM_LOC + ip * 81 + q] + Ap[q].d * Wn[ltsdev::AM_NBR + ip * 81 + q];
+            }
+          }
+          for (int p = 0; p < 3; ++p) grad[3 * e + p] = g[p];
+        }
+      };
+      const int nth = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
+      std::vector<std::thread> pool;
+      const int64_t chunk = (K + nth - 1) / nth;
+      for (int t = 0; t < nth; ++t) {
+        const int64_t k0 = t * chunk, k1 = std::min(K, k0 + chunk);
+        if (k0 < k1) pool.emplace_back(work, k0, k1);
+      }
+      for (auto& th : pool) th.join();
+    }
   });
 }
 

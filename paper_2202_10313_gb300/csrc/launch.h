@@ -4,6 +4,7 @@
 
 #include "kernels.cuh"
 #include "kernels_tc.cuh"
+#include "kernels_adj.cuh"
 
 namespace ltsdev {
 
@@ -25,6 +26,12 @@ struct Launchers {
   void (*receivers)(const DevOps&, const float* Q, long long qs, int nsim, int fg, const float* edata,
                     const float* phi, const RecvItem* items, float* out, const float* omega, int n, cudaStream_t);
   void (*sources)(float* Q, long long qs, int fg, const float* phi, const SrcItem* items, int n, cudaStream_t);
+  // discrete adjoint of the elastic GTS loop (one simulation, no mechanisms; else nullptr)
+  void (*adj_T)(const DevOps&, const AdjArgs&, float* tbuf, int K, cudaStream_t);
+  void (*adj_step)(const DevOps&, const AdjArgs&, int K, cudaStream_t);
+  void (*adj_sample)(const float* Q, long long qs, const int* elem, const float* phi, int nrec, float* out,
+                     cudaStream_t);
+  void (*adj_source)(float* lam, const int* elem, const float* phi, const float* res, int nrec, cudaStream_t);
   // face-local messages of a partitioned run (one simulation)
   void (*pack)(const DevOps&, const DevState&, const PhaseArgs&, const int* send_elem, const int* send_code,
                const int* recv_cluster, int n, float* msg, cudaStream_t);
@@ -89,6 +96,19 @@ struct Impl {
     const int threads = 128, nt = n * C::F;
     k_pack_faces<O, M><<<(nt + threads - 1) / threads, threads, 0, st>>>(o, s, p, se, sc, rc, n, msg);
   }
+  static void adj_T(const DevOps& o, const AdjArgs& a, float* tbuf, int K, cudaStream_t st) {
+    k_adj_T<O><<<K, 64, 0, st>>>(o, a, tbuf);
+  }
+  static void adj_step(const DevOps& o, const AdjArgs& a, int K, cudaStream_t st) {
+    k_adj_step<O><<<K, 128, 0, st>>>(o, a);
+  }
+  static void adj_sample(const float* Q, long long qs, const int* elem, const float* phi, int nrec, float* out,
+                         cudaStream_t st) {
+    k_adj_sample<O><<<(3 * nrec + 127) / 128, 128, 0, st>>>(Q, qs, elem, phi, nrec, out);
+  }
+  static void adj_source(float* lam, const int* elem, const float* phi, const float* res, int nrec, cudaStream_t st) {
+    k_adj_source<O><<<1, 64, 0, st>>>(lam, elem, phi, res, nrec);
+  }
   static void energy(const float* Q, long long qs, int nsim, int fg, const double* emat, int K, double* partial,
                      int nblocks, cudaStream_t st) {
     k_energy<O, M><<<nblocks, 256, 0, st>>>(Q, qs, nsim, fg, emat, K, partial);
@@ -117,6 +137,12 @@ struct Impl {
     L.receivers = &receivers;
     L.sources = &sources;
     L.pack = &pack;
+    if constexpr (M == 0 && FG == 1) {
+      L.adj_T = &adj_T;
+      L.adj_step = &adj_step;
+      L.adj_sample = &adj_sample;
+      L.adj_source = &adj_source;
+    }
     L.energy = &energy;
     return L;
   }

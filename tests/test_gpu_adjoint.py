@@ -1,0 +1,144 @@
+"""Discrete adjoint on the GPU (global time stepping, elastic): misfit, samples, material
+gradient and dJ/dQ0 against the FP64 oracle's adjoint; invariance to the checkpoint
+spacing; central differences of the GPU's own misfit; the torch.autograd.Function."""
+import numpy as np
+import pytest
+
+from oracle.adjoint import misfit_gradient as oracle_misfit_gradient
+from oracle.mesh import Mesh
+from oracle.scheme import Solver as Oracle
+from paper_2202_10313_gb300 import binding, build, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+
+
+def _case(order, seed=6):
+    m = synth.permute_vertex_order(synth.graded_box(3, 3, 2, 200.0, 100.0, seed=seed), seed=5)
+    mat = synth.random_layers(m, n_layers=2, seed=3)
+    K = m["tet"].shape[0]
+    nb = order * (order + 1) * (order + 2) // 6
+    q0 = synth.random_dofs(K, 9, nb, seed=seed)
+    rec = [np.array([150.0, 200.0, -40.0]), np.array([420.0, 330.0, -90.0]), np.array([300.0, 480.0, -20.0])]
+    src = (np.array([310.0, 290.0, -120.0]), np.array([0.2, -0.4, 0.2, 1.0, 0.1, -0.3]), 10.0, 0.02, 1e12)
+    return m, mat, q0, rec, src
+
+
+def _rlm(mat):
+    rho = mat["rho"].astype(float)
+    mu = rho * mat["vs"] ** 2
+    lam = rho * mat["vp"] ** 2 - 2 * mu
+    return rho, lam, mu
+
+
+def _oracle(order, m, rho, lam, mu, q0, rec, src, data, dt, n):
+    om = Mesh(m["xyz"], m["tet"], m["face_bc"])
+    o = Oracle(order, 0, om, rho, np.sqrt((lam + 2 * mu) / rho), np.sqrt(mu / rho))
+    o.add_point_source(*src)
+    o.Q = q0.copy()
+    re = [om.locate(x) for x in rec]
+    rp = [o.basis.phi(om.xi_of(k, x)[None, :])[0] for k, x in zip(re, rec)]
+    return oracle_misfit_gradient(o, dt, n, re, rp, data), o
+
+
+def _gpu(order, m, rho, lam, mu, q0, rec, src, dt):
+    s = binding.Solver(order, 0, device=0)
+    s.set_mesh(m["xyz"], m["tet"], m["face_bc"])
+    s.set_material(rho, np.sqrt((lam + 2 * mu) / rho), np.sqrt(mu / rho))
+    s.add_point_source(*src)
+    for x in rec:
+        s.add_receiver(x, dt)
+    s.setup_clusters(1, 0.5)
+    s.set_finest_dt(dt)
+    s.set_dofs(q0)
+    return s
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("order", [3, 4])
+def test_gpu_adjoint_matches_oracle_adjoint(order):
+    m, mat, q0, rec, src = _case(order)
+    rho, lam, mu = _rlm(mat)
+    n = 8
+    om = Mesh(m["xyz"], m["tet"], m["face_bc"])
+    dt = Oracle(order, 0, om, rho, mat["vp"], mat["vs"]).time_step_gts(0.5)
+    # observed data: the oracle in a model with mu 2 % higher
+    (_, _, _, data), _ = _oracle(order, m, rho, lam, mu * 1.02, q0, rec, src, np.zeros((n + 1, 3, 3)), dt, n)
+    (J0, g0, dq0_o, syn0), _ = _oracle(order, m, rho, lam, mu, q0, rec, src, data, dt, n)
+    s = _gpu(order, m, rho, lam, mu, q0, rec, src, dt)
+    J, g, syn, dq0 = s.misfit_gradient(n, data, every=3, want_dq0=True)
+    assert _rel(syn, syn0) <= 1e-5
+    assert abs(J / J0 - 1) <= 1e-3
+    for p in range(3):
+        assert _rel(g[:, p], g0[:, p]) <= 2e-3, (p, _rel(g[:, p], g0[:, p]))
+    assert _rel(dq0, dq0_o) <= 2e-3
+    # the state ends at t_N
+    assert abs(s.info()["time"] - n * dt) <= 1e-12 * n * dt
+
+
+def test_checkpoint_spacing_does_not_change_the_result():
+    order, n = 4, 9
+    m, mat, q0, rec, src = _case(order, seed=8)
+    rho, lam, mu = _rlm(mat)
+    data = np.zeros((n + 1, 3, 3))
+    out = []
+    for every in (1, 4, n):
+        s = _gpu(order, m, rho, lam, mu, q0, rec, src, 2e-4)
+        out.append(s.misfit_gradient(n, data, every=every))
+        s.close()
+    for J, g, syn in out[1:]:
+        assert J == out[0][0] and np.array_equal(g, out[0][1]) and np.array_equal(syn, out[0][2])
+
+
+def test_gpu_gradient_against_central_differences_of_the_gpu_misfit():
+    order, n = 4, 8
+    m, mat, q0, rec, src = _case(order, seed=10)
+    rho, lam, mu = _rlm(mat)
+    dt = 2e-4
+    s = _gpu(order, m, rho, lam, mu, q0, rec, src, dt)
+    _, _, syn = s.misfit_gradient(n, np.zeros((n + 1, 3, 3)), every=4)
+    data = syn * 1.05
+    s = _gpu(order, m, rho, lam, mu, q0, rec, src, dt)
+    J, g, _ = s.misfit_gradient(n, data, every=4)
+    params = [rho, lam, mu]
+    rng = np.random.default_rng(2)
+    for p in range(3):
+        for k in np.argsort(-np.abs(g[:, p]))[:3].tolist() + [int(rng.integers(len(rho)))]:
+            h = 1e-3 * params[p][k]
+            vals = []
+            for sgn in (1, -1):
+                pp = [x.copy() for x in params]
+                pp[p][k] += sgn * h
+                t = _gpu(order, m, *pp, q0, rec, src, dt)
+                vals.append(t.misfit_gradient(n, data, every=n)[0])
+                t.close()
+            fd = (vals[0] - vals[1]) / (2 * h)
+            assert abs(fd - g[k, p]) <= 2e-2 * np.abs(g[:, p]).max(), (p, k, fd, g[k, p])
+
+
+def test_autograd_function():
+    torch = pytest.importorskip("torch")
+    from paper_2202_10313_gb300.adjoint import MisfitProblem, SeismogramMisfit
+    order, n = 3, 6
+    m, mat, q0, rec, src = _case(order, seed=12)
+    rho, lam, mu = _rlm(mat)
+    dt = 2e-4
+    data = np.zeros((n + 1, 3, 3))
+    prob = MisfitProblem(order, m, q0, rec, data, n, dt, sources=[src], every=2)
+    tr, tl, tm = (torch.tensor(x, dtype=torch.float64, requires_grad=True) for x in (rho, lam, mu))
+    J = SeismogramMisfit.apply(tr, tl, tm, prob)
+    J.backward()
+    s = _gpu(order, m, rho, lam, mu, q0, rec, src, dt)
+    J2, g, _ = s.misfit_gradient(n, data, every=2)
+    assert float(J.detach()) == J2
+    assert np.array_equal(tr.grad.numpy(), g[:, 0]) and np.array_equal(tm.grad.numpy(), g[:, 2])
