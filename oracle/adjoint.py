@@ -157,12 +157,152 @@ def misfit_gradient(solver, dt, n_steps, rec_elem, rec_phi, data):
         lam = lam + G[0]
         add_source(n)
     s.Q = Qs[-1].copy()
-    dAe, dAm, dAp = derivative_matrices(s)
+    return J, _contract(s, Wc, Wm, Wp), lam, synth
+
+
+def _contract(solver, Wc, Wm, Wp):
+    """dJ/d(rho, lambda, mu) from the per-element correlations."""
+    nbr = solver.mesh.nbr
+    dAe, dAm, dAp = derivative_matrices(solver)
     grad = np.einsum("kpcij,kcij->kp", dAe, Wc)
     grad += np.einsum("kipab,kiab->kp", dAm[:, :, :3], Wm) + np.einsum("kipab,kiab->kp", dAp[:, :, :3], Wp)
-    for k in range(K):
+    for k in range(solver.mesh.K):
         for i in range(4):
             kn = nbr[k, i]
             if kn >= 0:
                 grad[kn] += np.einsum("pab,ab->p", dAm[k, i, 3:], Wm[k, i]) + np.einsum("pab,ab->p", dAp[k, i, 3:], Wp[k, i])
-    return J, grad, lam, synth
+    return grad
+
+
+def misfit_gradient_lts(solver, n_macro, rec_elem, rec_phi, data):
+    """Clustered LTS (Sec. V-B): J = 1/2 sum_m sum_r |v_r(t_m) - d_r^m|^2 over the macro-step
+    boundaries t_m (every cluster has completed its steps there), m = 0..n_macro, from the
+    solver's current state with its clusters set up. The LTS state is (Q, B1, B2, B3); the
+    reverse sweep takes the phases backwards:
+    * a neighbour pass of cluster l (step n) added S_N(X_i) to Q_k with X_i the neighbour's
+      B1, B3, B2 or B1 - B2 (cluster relation, parity of n); its transpose adds
+      ((A~+^T lambda_Q_k) F^_i^T) F-_{j,h}^T to the adjoint of that buffer;
+    * a predict pass (step n) wrote B1 = T, B2 = T(dt/2) (finer neighbour), B3 = T or
+      B3 += T (coarser neighbour, even / odd n) and added V(T) + S_L(T) to Q; so
+      mu = dJ/dT = V^T + S_L^T + lambda_B1 (+ lambda_B3), mu_half = lambda_B2, the
+      buffer adjoints reset except lambda_B3 after an accumulation, and the transposed
+      time kernel G_d = c_d mu + c'_d mu_half + L^T(G_{d+1}) adds G_0 to lambda_Q.
+    Returns J, dJ/d(rho, lambda, mu) (K, 3), dJ/dQ at the start, samples (M+1, n_rec, 3)."""
+    s = solver
+    if s.m != 0:
+        raise ValueError("the oracle adjoint is written for the elastic equations")
+    mesh = s.mesh
+    b = s.basis
+    K, O = mesh.K, s.order
+    nc = s.n_clusters
+    period = 2 ** (nc - 1)
+    nbr, nbf, nbo = mesh.nbr, mesh.nbr_face, mesh.nbr_orient
+    Ae, Aem, Aep = s.Ae, s.Aem, s.Aep
+    K3 = b.K
+    records = [("S", 0)]
+    orig_p, orig_n = s._predict_local, s._neighbour
+
+    def rec_p(l, n):
+        idx = np.nonzero(s.clusters == l)[0]
+        if len(idx):
+            records.append(("P", l, n, idx, s.Q[idx].copy()))
+        orig_p(l, n)
+
+    def rec_n(l, n):
+        idx = np.nonzero(s.clusters == l)[0]
+        if len(idx):
+            X = np.zeros((len(idx), 4, 9, b.nb))
+            for p_, k in enumerate(idx):
+                for i in range(4):
+                    kn = nbr[k, i]
+                    if kn < 0:
+                        continue
+                    cn = s.clusters[kn]
+                    if cn == l - 1:
+                        X[p_, i] = s.B3[kn]
+                    elif cn == l + 1:
+                        X[p_, i] = s.B2[kn] if n % 2 == 0 else s.B1[kn] - s.B2[kn]
+                    else:
+                        X[p_, i] = s.B1[kn]
+            records.append(("N", l, n, idx, X))
+        orig_n(l, n)
+
+    s._predict_local, s._neighbour = rec_p, rec_n
+    samples = [_samples(s.Q, rec_elem, rec_phi)]
+    try:
+        for m in range(n_macro):
+            s.run_lts(period)
+            samples.append(_samples(s.Q, rec_elem, rec_phi))
+            records.append(("S", m + 1))
+    finally:
+        s._predict_local, s._neighbour = orig_p, orig_n
+    synth = np.stack(samples)
+    res = synth - data
+    J = 0.5 * float(np.sum(res ** 2))
+    lq = np.zeros((K, 9, b.nb))
+    lb1, lb2, lb3 = np.zeros_like(lq), np.zeros_like(lq), np.zeros_like(lq)
+    Wc = np.zeros((K, 3, 9, 9))
+    Wm = np.zeros((K, 4, 9, 9))
+    Wp = np.zeros((K, 4, 9, 9))
+    for rec in reversed(records):
+        if rec[0] == "S":
+            for r, (k, phi) in enumerate(zip(rec_elem, rec_phi)):
+                lq[k, 6:9, :] += np.outer(res[rec[1], r], phi)
+        elif rec[0] == "N":
+            _, l, n, idx, X = rec
+            for p_, k in enumerate(idx):
+                for i in range(4):
+                    kn = nbr[k, i]
+                    if kn < 0:
+                        continue
+                    Fb = b.Fb[nbf[k, i]][nbo[k, i]]
+                    Y = ((Aep[k, i].T @ lq[k]) @ b.Fh[i].T) @ Fb.T
+                    cn = s.clusters[kn]
+                    if cn == l - 1:
+                        lb3[kn] += Y
+                    elif cn == l + 1:
+                        lb2[kn] += Y if n % 2 == 0 else -Y
+                        if n % 2 == 1:
+                            lb1[kn] += Y
+                    else:
+                        lb1[kn] += Y
+                    Wp[k, i] += lq[k] @ ((X[p_, i] @ Fb) @ b.Fh[i]).T
+        else:
+            _, l, n, idx, Qb = rec
+            dl = s.delta * 2.0 ** l
+            cd = [dl ** (d + 1) / math.factorial(d + 1) for d in range(O)]
+            ch = [(0.5 * dl) ** (d + 1) / math.factorial(d + 1) for d in range(O)]
+            s_q = s.Q
+            s.Q = s.Q.copy()
+            s.Q[idx] = Qb
+            D = [d[:, :9, :] for d in s.derivatives(idx)]
+            s.Q = s_q
+            T = sum(cd[d] * D[d] for d in range(O))
+            lam = lq[idx]
+            mu = sum(np.transpose(Ae[idx, c], (0, 2, 1)) @ lam @ K3[c].T for c in range(3))
+            for i in range(4):
+                mu += ((np.transpose(Aem[idx, i], (0, 2, 1)) @ lam) @ b.Fh[i].T) @ b.Ft[i].T
+            mu += lb1[idx]
+            coa = s.has_coarser[idx]
+            fin = s.has_finer[idx]
+            mu[coa] += lb3[idx[coa]]
+            muh = np.zeros_like(mu)
+            muh[fin] = lb2[idx[fin]]
+            lb1[idx] = 0.0
+            lb2[idx[fin]] = 0.0
+            if n % 2 == 0:
+                lb3[idx[coa]] = 0.0
+            G = [None] * O
+            G[O - 1] = cd[O - 1] * mu + ch[O - 1] * muh
+            for d in range(O - 2, -1, -1):
+                G[d] = cd[d] * mu + ch[d] * muh - sum(np.transpose(Ae[idx, c], (0, 2, 1)) @ G[d + 1] @ K3[c]
+                                                      for c in range(3))
+            for c in range(3):
+                acc = lam @ np.transpose(T @ K3[c], (0, 2, 1))
+                for d in range(O - 1):
+                    acc -= G[d + 1] @ np.transpose(D[d] @ K3[c].T, (0, 2, 1))
+                Wc[idx, c] += acc
+            for i in range(4):
+                Wm[idx, i] += lam @ np.transpose((T @ b.Ft[i]) @ b.Fh[i], (0, 2, 1))
+            lq[idx] = lam + G[0]
+    return J, _contract(s, Wc, Wm, Wp), lq, synth
