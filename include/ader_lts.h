@@ -239,7 +239,7 @@ int lts_exchange_bytes(lts_t* h, int64_t* bytes);
  * caller is responsible for stability. Errors: LTS_ERR_STATE, LTS_ERR_ARG (dt <= 0). */
 int lts_set_finest_dt(lts_t* h, double dt);
 
-/* Discrete adjoint of the global-time-stepping loop (the misfit objective of Sec. VII-B,
+/* Discrete adjoint of the time-stepping loop (the misfit objective of Sec. VII-B,
  * summed): from the current state, advances n_steps steps of the elastic scheme (the same
  * launches as lts_advance_steps, sources included) and evaluates
  *   J = 1/2 sum_{n=0..N} sum_r sum_q (v_q(x_r, t_n) - data[n][r][q])^2,
@@ -253,9 +253,17 @@ int lts_set_finest_dt(lts_t* h, double dt);
  * with respect to the neighbour's. Outputs (each may be NULL except data): *misfit J,
  * grad[n_tet][3] = dJ/d(rho, lambda, mu) per element (original order), synth_out[N+1][n_rec][3]
  * the samples, dq0[n_tet][9][B] = dJ/dQ at the start. The time step is held fixed. The
- * state ends at t_N (as after lts_advance_steps). Needs one cluster (global time
- * stepping), n_mech = 0, one simulation, no partition, at least one receiver. Device
+ * state ends at t_N (as after lts_advance_steps). Needs n_mech = 0, one simulation, no
+ * partition, at least one receiver. With one cluster (global time stepping): Device
  * memory: (ceil(N/every) + min(every, N) + 1) copies of Q plus per-element operators.
+ * With clustered LTS (N_c > 1) the same holds per macro step: n_steps is a multiple of
+ * 2^(N_c-1), the samples are taken at the macro-step boundaries (data[M+1][n_rec][3],
+ * M = n_steps / 2^(N_c-1)), checkpoints every `every` macro steps, and the reverse
+ * sweep takes the LTS phases backwards over the state (Q, B1, B2, B3): a neighbour pass
+ * sends its transposed flux to the adjoint of the buffer it read (B1, B3, B2 or
+ * B1 - B2), a predict pass collects the adjoints of the buffers it wrote. Each macro step
+ * is recomputed phase by phase from its boundary state, keeping 2^(N_c-1) copies of Q
+ * and 3 x 2^(N_c-1) copies of the buffers.
  * Errors: LTS_ERR_ARG, LTS_ERR_STATE, LTS_ERR_OOM, LTS_ERR_CUDA. */
 int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* data, double* misfit,
                         double* grad, double* synth_out, double* dq0, void* cuda_stream);

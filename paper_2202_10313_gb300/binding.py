@@ -357,13 +357,13 @@ class Solver:
         self._check(lib().lts_set_finest_dt(self._h, float(dt)))
 
     def misfit_gradient(self, n_steps, data, every=100, stream=None, want_dq0=False):
-        """J, dJ/d(rho, lambda, mu) (K, 3), synthetic samples (N+1, n_rec, 3) and optionally
-        dJ/dQ at the start (K, 9, B), by the discrete adjoint of the GTS loop."""
-        data = _f64(data)
-        nrec = data.size // (3 * (int(n_steps) + 1))
+        """J, dJ/d(rho, lambda, mu) (K, 3), synthetic samples (shape of data: one row per
+        sample time, n_rec, 3) and optionally dJ/dQ at the start (K, 9, B), by the discrete
+        adjoint of the time loop (GTS: samples every step; LTS: every macro step)."""
+        data = np.ascontiguousarray(data, dtype=np.float64)
         J = ctypes.c_double()
         grad = np.zeros((self.K, 3))
-        syn = np.zeros((int(n_steps) + 1, nrec, 3))
+        syn = np.zeros(data.shape)
         dq0 = np.zeros((self.K, 9, self.nb)) if want_dq0 else None
         self._check(lib().lts_misfit_gradient(self._h, int(n_steps), int(every), _ptr(data), ctypes.byref(J),
                                               _ptr(grad), _ptr(syn), _ptr(dq0), _stream_handle(stream)))

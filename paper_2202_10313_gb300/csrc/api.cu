@@ -598,73 +598,82 @@ void plan_macro(lts_solver* h, int64_t s_begin, size_t& seis_need, MacroPlan& mp
   }
 }
 
-// Enqueues the launches of one macro step on `stream` (items at the start of the item
-// buffers); returns the number of kernels launched.
-int enqueue_macro(lts_solver* h, const MacroPlan& mp, cudaStream_t stream) {
-  const Launchers& X = h->L;
-  const int nc = h->nc;
-  PhaseArgs base{};
-  for (int l = 0; l < nc; ++l) {
+// Kernel arguments of one phase (Taylor coefficients per cluster, element range, step parities).
+PhaseArgs phase_args(const lts_solver* h, const Phase& ph) {
+  PhaseArgs pa{};
+  for (int l = 0; l < h->nc; ++l) {
     const double dl = h->delta * std::ldexp(1.0, l);
     double fac = 1.0;
     for (int d = 0; d < h->order; ++d) {
       fac *= (d + 1);
-      base.coef[l][d] = (float)(std::pow(dl, d + 1) / fac);
-      base.hcoef[l][d] = (float)(std::pow(0.5 * dl, d + 1) / fac);
+      pa.coef[l][d] = (float)(std::pow(dl, d + 1) / fac);
+      pa.hcoef[l][d] = (float)(std::pow(0.5 * dl, d + 1) / fac);
     }
   }
-  for (int l = 0; l < 3; ++l) base.omega[l] = l < (int)h->omega.size() ? (float)h->omega[l] : 0.f;
+  for (int l = 0; l < 3; ++l) pa.omega[l] = l < (int)h->omega.size() ? (float)h->omega[l] : 0.f;
+  pa.begin = 0;
+  pa.end = (int)h->cbeg[ph.top + 1];
+  for (int l = 0; l <= ph.top; ++l) {
+    const int64_t n = ph.kind == 0 ? (ph.s >> l) - 1 : (ph.s >> l);
+    pa.parity[l] = (int)(n & 1);
+  }
+  return pa;
+}
+
+// Enqueues the launches of one phase on `stream` (work items at the start of the item
+// buffers); returns the number of kernels launched. Receivers are skipped when
+// with_receivers is false (state-only replays).
+int enqueue_phase(lts_solver* h, const Phase& ph, cudaStream_t stream, bool with_receivers = true) {
+  const Launchers& X = h->L;
   const bool use_tc = h->contraction != LTS_CONTRACT_FP32;
   const int passes = h->contraction == LTS_CONTRACT_TF32X3 ? 3 : 1;
   const int maxp = std::max(1, use_tc ? X.blocks_predict_tc : X.blocks_predict);
   const int maxn = std::max(1, X.blocks_neighbour);
   const int grid_cap_p = h->num_sms * (h->ctas_predict > 0 ? std::min(h->ctas_predict, maxp) : maxp);
   const int grid_cap_n = h->num_sms * (h->ctas_neighbour > 0 ? std::min(h->ctas_neighbour, maxn) : maxn);
+  const PhaseArgs pa = phase_args(h, ph);
+  const int nelem = pa.end - pa.begin;
+  if (nelem <= 0) return 0;
   int launches = 0;
-  for (const Phase& ph : mp.phases) {
-    PhaseArgs pa = base;
-    pa.begin = 0;
-    pa.end = (int)h->cbeg[ph.top + 1];
-    for (int l = 0; l <= ph.top; ++l) {
-      const int64_t n = ph.kind == 0 ? (ph.s >> l) - 1 : (ph.s >> l);
-      pa.parity[l] = (int)(n & 1);
-    }
-    const int nelem = pa.end - pa.begin;
-    if (nelem <= 0) continue;
-    // CTA batches: NE elements (one simulation) or one element and FG of its simulations
-    const int nb = X.FG > 1 ? nelem * (h->nsim / X.FG)
-                            : (nelem + (ph.kind == 0 ? X.NEN : X.NE) - 1) / (ph.kind == 0 ? X.NEN : X.NE);
-    if (ph.kind == 1 && ph.item_end > ph.item_beg) {
-      X.receivers(h->dops, h->dst.Q, h->dst.qs, h->nsim, X.FG, h->dst.edata, h->d_recv_phi, h->d_ritems + ph.item_beg,
-                  h->d_seis, base.omega, ph.item_end - ph.item_beg, stream);
-      ++launches;
-    }
-    if (ph.kind == 0 && h->n_parts > 1 && h->cut_beg[ph.top + 1] > 0) {
-      // the neighbours' partitions compute the face-local messages of the active cut faces
-      const int nact = (int)h->cut_beg[ph.top + 1];
-      X.pack(h->dops, h->dst, pa, h->d_cut, h->d_cut + h->n_cut, h->d_cut + 2 * h->n_cut, nact, h->d_msg, stream);
-      ++launches;
-    }
-    if (h->profiling) ck(cudaEventRecord(next_event(h), stream), "event record");
-    if (ph.kind == 0)
-      X.neighbour(h->dops, h->dst, pa, std::min(nb, grid_cap_n), stream);
-    else if (use_tc)
-      X.predict_tc(h->dops, h->dst, pa, std::min(nb, grid_cap_p), passes, h->d_err, h->wait_cycles,
-                   h->suppress_commit, stream);
-    else
-      X.predict(h->dops, h->dst, pa, std::min(nb, grid_cap_p), stream);
+  // CTA batches: NE elements (one simulation) or one element and FG of its simulations
+  const int nb = X.FG > 1 ? nelem * (h->nsim / X.FG)
+                          : (nelem + (ph.kind == 0 ? X.NEN : X.NE) - 1) / (ph.kind == 0 ? X.NEN : X.NE);
+  if (with_receivers && ph.kind == 1 && ph.item_end > ph.item_beg) {
+    X.receivers(h->dops, h->dst.Q, h->dst.qs, h->nsim, X.FG, h->dst.edata, h->d_recv_phi, h->d_ritems + ph.item_beg,
+                h->d_seis, pa.omega, ph.item_end - ph.item_beg, stream);
     ++launches;
-    if (h->profiling) {
-      ck(cudaEventRecord(next_event(h), stream), "event record");
-      h->ev_kind.push_back(ph.kind == 1 ? 0 : 1);
-      h->ev_elems.push_back(nelem);
-    }
-    if (ph.kind == 0 && ph.item_end > ph.item_beg) {
-      X.sources(h->dst.Q, h->dst.qs, X.FG, h->d_src_phi, h->d_sitems + ph.item_beg, ph.item_end - ph.item_beg,
-                stream);
-      ++launches;
-    }
   }
+  if (ph.kind == 0 && h->n_parts > 1 && h->cut_beg[ph.top + 1] > 0) {
+    // the neighbours' partitions compute the face-local messages of the active cut faces
+    const int nact = (int)h->cut_beg[ph.top + 1];
+    X.pack(h->dops, h->dst, pa, h->d_cut, h->d_cut + h->n_cut, h->d_cut + 2 * h->n_cut, nact, h->d_msg, stream);
+    ++launches;
+  }
+  if (h->profiling) ck(cudaEventRecord(next_event(h), stream), "event record");
+  if (ph.kind == 0)
+    X.neighbour(h->dops, h->dst, pa, std::min(nb, grid_cap_n), stream);
+  else if (use_tc)
+    X.predict_tc(h->dops, h->dst, pa, std::min(nb, grid_cap_p), passes, h->d_err, h->wait_cycles, h->suppress_commit,
+                 stream);
+  else
+    X.predict(h->dops, h->dst, pa, std::min(nb, grid_cap_p), stream);
+  ++launches;
+  if (h->profiling) {
+    ck(cudaEventRecord(next_event(h), stream), "event record");
+    h->ev_kind.push_back(ph.kind == 1 ? 0 : 1);
+    h->ev_elems.push_back(nelem);
+  }
+  if (ph.kind == 0 && ph.item_end > ph.item_beg) {
+    X.sources(h->dst.Q, h->dst.qs, X.FG, h->d_src_phi, h->d_sitems + ph.item_beg, ph.item_end - ph.item_beg, stream);
+    ++launches;
+  }
+  return launches;
+}
+
+// Enqueues the launches of one macro step on `stream`; returns the number of kernels.
+int enqueue_macro(lts_solver* h, const MacroPlan& mp, cudaStream_t stream) {
+  int launches = 0;
+  for (const Phase& ph : mp.phases) launches += enqueue_phase(h, ph, stream);
   ck(cudaGetLastError(), "kernel launch");
   return launches;
 }
@@ -810,6 +819,208 @@ struct DevBuf {
     }
   }
 };
+
+void contract_gradient(const lts_solver* h, const std::vector<double>& W, double* grad) {
+  const int64_t K = h->mesh.K;
+  {
+      auto work = [&](int64_t k0, int64_t k1) {
+        lts::Dual S[3][81], Am[81], Ap[81];
+        for (int64_t e = k0; e < k1; ++e) {
+          const double* We = &W[h->iperm[e] * ltsdev::AM_SIZE];
+          double g[3] = {0, 0, 0};
+          for (int p = 0; p < 3; ++p) {
+            element_operators<lts::Dual>(h, e, -1, p, S, nullptr, nullptr);
+            for (int c = 0; c < 3; ++c)
+              for (int q = 0; q < 81; ++q) g[p] += S[c][q].d * We[ltsdev::AM_STAR + c * 81 + q];
+          }
+          for (int i = 0; i < 4; ++i) {
+            for (int p = 0; p < 3; ++p) {
+              element_operators<lts::Dual>(h, e, i, p, nullptr, Am, Ap);
+              for (int q = 0; q < 81; ++q)
+                g[p] += Am[q].d * We[ltsdev::AM_LOC + i * 81 + q] + Ap[q].d * We[ltsdev::AM_NBR + i * 81 + q];
+            }
+            // the neighbour's face that looks at e: its operators depend on e's material
+            const int64_t nb = h->mesh.nbr[4 * e + i];
+            if (nb < 0) continue;
+            const int ip = h->mesh.nbr_face[4 * e + i];
+            const double* Wn = &W[h->iperm[nb] * ltsdev::AM_SIZE];
+            for (int p = 0; p < 3; ++p) {
+              element_operators<lts::Dual>(h, nb, ip, 3 + p, nullptr, Am, Ap);
+              for (int q = 0; q < 81; ++q)
+                g[p] += Am[q].d * Wn[ltsdev::AM_LOC + ip * 81 + q] + Ap[q].d * Wn[ltsdev::AM_NBR + ip * 81 + q];
+            }
+          }
+          for (int p = 0; p < 3; ++p) grad[3 * e + p] = g[p];
+        }
+      };
+      const int nth = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
+      std::vector<std::thread> pool;
+      const int64_t chunk = (K + nth - 1) / nth;
+      for (int t = 0; t < nth; ++t) {
+        const int64_t k0 = t * chunk, k1 = std::min(K, k0 + chunk);
+        if (k0 < k1) pool.emplace_back(work, k0, k1);
+      }
+      for (auto& th : pool) th.join();
+  }
+}
+
+
+// Clustered-LTS branch of lts_misfit_gradient: samples at the macro-step boundaries, Q
+// checkpoints every `every` macro steps, and per macro step a phase-by-phase recompute
+// that keeps Q before each predict pass and the buffers before each neighbour pass for the
+// reverse sweep (k_adj_pred / k_adj_nbr, phases in reverse order).
+void adjoint_lts(lts_solver* h, int64_t n_macro, int64_t every, const double* data, double* misfit, double* grad,
+                 double* synth_out, double* dq0, cudaStream_t stream, const DevBuf& d_amat, const DevBuf& d_fwd,
+                 const DevBuf& d_back, const DevBuf& d_relem, const DevBuf& d_rphi, int nrec) {
+  const Launchers& X = h->L;
+  const int64_t K = h->mesh.K;
+  const int B = X.B, NB9 = 9 * B;
+  const int64_t qs = h->dst.qs, bs = h->dst.bs;
+  const int64_t period = int64_t(1) << (h->nc - 1);
+  const int64_t ncp = (n_macro + every - 1) / every;
+  const int64_t segm = std::min(every, n_macro);
+  DevBuf d_syn, d_res, d_lq, d_lb, d_w, d_cp, d_mac, d_qn, d_sq, d_sb;
+  d_syn.alloc(sizeof(float) * (n_macro + 1) * nrec * 3);
+  d_res.alloc(sizeof(float) * (n_macro + 1) * nrec * 3);
+  d_lq.alloc(sizeof(float) * K * NB9);
+  d_lb.alloc(sizeof(float) * 3 * K * NB9);
+  d_w.alloc(sizeof(double) * K * ltsdev::AM_SIZE);
+  d_cp.alloc(sizeof(float) * ncp * K * qs);
+  d_mac.alloc(sizeof(float) * segm * K * qs);
+  d_qn.alloc(sizeof(float) * K * qs);
+  d_sq.alloc(sizeof(float) * period * K * qs);
+  d_sb.alloc(sizeof(float) * 3 * period * K * bs);
+  const size_t qbytes = sizeof(float) * K * qs, bbytes = sizeof(float) * K * bs;
+  auto dcopy = [&](void* dst, const void* src, size_t bytes) {
+    ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, stream), "adjoint copy");
+  };
+  float* cp = d_cp.get<float>();
+  float* mac = d_mac.get<float>();
+  float* sq = d_sq.get<float>();
+  float* sb = d_sb.get<float>();
+  const int* relem = d_relem.get<int>();
+  const float* rphi = d_rphi.get<float>();
+  // ---- forward sweep: samples at the macro boundaries, checkpoints
+  const int64_t s0 = h->s_now;
+  std::vector<size_t> nrec_t(nrec);
+  X.adj_sample(h->dst.Q, qs, relem, rphi, nrec, d_syn.get<float>(), stream);
+  for (int64_t m = 0; m < n_macro; ++m) {
+    if (m % every == 0) dcopy(cp + (m / every) * K * qs, h->dst.Q, qbytes);
+    advance_steps(h, period, stream);
+    X.adj_sample(h->dst.Q, qs, relem, rphi, nrec, d_syn.get<float>() + (m + 1) * nrec * 3, stream);
+  }
+  for (int r = 0; r < nrec; ++r) nrec_t[r] = h->receivers[r].t.size();
+  const size_t seis_fwd = h->seis_used;
+  dcopy(d_qn.p, h->dst.Q, qbytes);
+  std::vector<float> syn((size_t)(n_macro + 1) * nrec * 3);
+  ck(cudaMemcpyAsync(syn.data(), d_syn.p, sizeof(float) * syn.size(), cudaMemcpyDeviceToHost, stream), "samples");
+  ck(cudaStreamSynchronize(stream), "synchronize");
+  check_device_error(h);
+  std::vector<float> res(syn.size());
+  double J = 0.0;
+  for (size_t q = 0; q < syn.size(); ++q) {
+    const double r = (double)syn[q] - data[q];
+    res[q] = (float)r;
+    J += 0.5 * r * r;
+  }
+  ck(cudaMemcpyAsync(d_res.p, res.data(), sizeof(float) * res.size(), cudaMemcpyHostToDevice, stream), "residuals");
+  // ---- reverse sweep
+  ck(cudaMemsetAsync(d_lq.p, 0, sizeof(float) * K * NB9, stream), "memset");
+  ck(cudaMemsetAsync(d_lb.p, 0, sizeof(float) * 3 * K * NB9, stream), "memset");
+  ck(cudaMemsetAsync(d_w.p, 0, sizeof(double) * K * ltsdev::AM_SIZE, stream), "memset");
+  X.adj_source(d_lq.get<float>(), relem, rphi, d_res.get<float>() + n_macro * nrec * 3, nrec, stream);
+  ltsdev::AdjLtsArgs aa{};
+  aa.lq = d_lq.get<float>();
+  aa.lb1 = d_lb.get<float>();
+  aa.lb2 = aa.lb1 + K * NB9;
+  aa.lb3 = aa.lb2 + K * NB9;
+  aa.amat = d_amat.get<float>();
+  aa.fwd = d_fwd.get<int>();
+  aa.back = d_back.get<int>();
+  aa.meta = h->dst.meta;
+  aa.W = d_w.get<double>();
+  aa.qs = qs;
+  aa.bufs = bs;
+  MacroPlan mp;
+  for (int64_t sgi = ncp - 1; sgi >= 0; --sgi) {
+    const int64_t m0 = sgi * every, m1 = std::min(m0 + every, n_macro);
+    // macro-boundary states of the segment
+    dcopy(h->dst.Q, cp + sgi * K * qs, qbytes);
+    h->s_now = s0 + m0 * period;
+    dcopy(mac, h->dst.Q, qbytes);
+    for (int64_t m = m0; m + 1 < m1; ++m) {
+      advance_steps(h, period, stream);
+      dcopy(mac + (m + 1 - m0) * K * qs, h->dst.Q, qbytes);
+    }
+    for (int64_t m = m1 - 1; m >= m0; --m) {
+      // recompute macro step m phase by phase, keeping the inputs of every phase
+      dcopy(h->dst.Q, mac + (m - m0) * K * qs, qbytes);
+      const int64_t sb0 = s0 + m * period;
+      h->s_now = sb0;
+      size_t seis_need = h->seis_used;
+      plan_macro(h, sb0, seis_need, mp);
+      ensure_capacity(reinterpret_cast<void**>(&h->d_sitems), &h->sitems_cap, mp.sitems.size(), sizeof(SrcItem));
+      if (!mp.sitems.empty())
+        ck(cudaMemcpyAsync(h->d_sitems, mp.sitems.data(), mp.sitems.size() * sizeof(SrcItem), cudaMemcpyHostToDevice,
+                           stream),
+           "upload source items");
+      for (const Phase& ph : mp.phases) {
+        const int64_t lvl = ph.s - sb0;
+        if (ph.kind == 1) {
+          dcopy(sq + lvl * K * qs, h->dst.Q, qbytes);
+        } else {
+          float* base = sb + 3 * (lvl - 1) * K * bs;
+          dcopy(base, h->dst.B1, bbytes);
+          dcopy(base + K * bs, h->dst.B2, bbytes);
+          dcopy(base + 2 * K * bs, h->dst.B3, bbytes);
+        }
+        enqueue_phase(h, ph, stream, false);
+      }
+      for (size_t pi = mp.phases.size(); pi-- > 0;) {
+        const Phase& ph = mp.phases[pi];
+        const PhaseArgs pa = phase_args(h, ph);
+        if (pa.end <= 0) continue;
+        const int64_t lvl = ph.s - sb0;
+        aa.end = pa.end;
+        if (ph.kind == 1) {
+          aa.Qs = sq + lvl * K * qs;
+          X.adj_pred(h->dops, aa, pa, pa.end, stream);
+        } else {
+          const float* base = sb + 3 * (lvl - 1) * K * bs;
+          aa.B1s = base;
+          aa.B2s = base + K * bs;
+          aa.B3s = base + 2 * K * bs;
+          X.adj_nbr(h->dops, aa, pa, (int)K, stream);
+        }
+      }
+      X.adj_source(d_lq.get<float>(), relem, rphi, d_res.get<float>() + m * nrec * 3, nrec, stream);
+      for (int r = 0; r < nrec; ++r) {
+        h->receivers[r].t.resize(nrec_t[r]);
+        h->receivers[r].slot.resize(nrec_t[r]);
+      }
+      h->seis_used = seis_fwd;
+    }
+  }
+  ck(cudaGetLastError(), "adjoint kernels");
+  dcopy(h->dst.Q, d_qn.p, qbytes);
+  h->s_now = s0 + n_macro * period;
+  std::vector<double> W((size_t)K * ltsdev::AM_SIZE);
+  ck(cudaMemcpyAsync(W.data(), d_w.p, sizeof(double) * W.size(), cudaMemcpyDeviceToHost, stream), "correlations");
+  std::vector<float> lq;
+  if (dq0) {
+    lq.resize((size_t)K * NB9);
+    ck(cudaMemcpyAsync(lq.data(), d_lq.p, sizeof(float) * lq.size(), cudaMemcpyDeviceToHost, stream), "adjoint state");
+  }
+  ck(cudaStreamSynchronize(stream), "synchronize");
+  check_device_error(h);
+  if (misfit) *misfit = J;
+  if (synth_out)
+    for (size_t q = 0; q < syn.size(); ++q) synth_out[q] = syn[q];
+  if (dq0)
+    for (int64_t k = 0; k < K; ++k)
+      for (int q = 0; q < NB9; ++q) dq0[k * NB9 + q] = lq[h->iperm[k] * NB9 + q];
+  if (grad) contract_gradient(h, W, grad);
+}
 
 }  // namespace
 
@@ -1482,8 +1693,10 @@ int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* 
   return run(h, [&] {
     if (!h->ready) fail(LTS_ERR_STATE, "clusters not set up");
     const Launchers& X = h->L;
-    if (h->nc != 1 || h->nmech != 0 || h->nsim != 1 || h->n_parts > 1 || !X.adj_step)
-      fail(LTS_ERR_ARG, "the adjoint covers global time stepping, elastic, one simulation, no partition");
+    if (h->nmech != 0 || h->nsim != 1 || h->n_parts > 1 || !X.adj_step)
+      fail(LTS_ERR_ARG, "the adjoint covers the elastic equations, one simulation, no partition");
+    const int64_t period = int64_t(1) << (h->nc - 1);
+    if (h->nc > 1 && n_steps % period != 0) fail(LTS_ERR_ARG, "n_steps must be a multiple of the macro step");
     const int nrec = (int)h->receivers.size();
     if (nrec < 1 || n_steps < 1 || every < 1 || !data) fail(LTS_ERR_ARG, "bad adjoint arguments");
     ck(cudaSetDevice(h->device), "cudaSetDevice");
@@ -1530,6 +1743,19 @@ int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* 
     d_back.alloc(sizeof(int) * back.size());
     d_relem.alloc(sizeof(int) * nrec);
     d_rphi.alloc(sizeof(float) * rphi.size());
+    auto up = [&](void* dst, const void* src, size_t bytes) {
+      ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, stream), "adjoint upload");
+    };
+    up(d_amat.p, amat.data(), sizeof(float) * amat.size());
+    up(d_fwd.p, fwd.data(), sizeof(int) * fwd.size());
+    up(d_back.p, back.data(), sizeof(int) * back.size());
+    up(d_relem.p, relem.data(), sizeof(int) * nrec);
+    up(d_rphi.p, rphi.data(), sizeof(float) * rphi.size());
+    if (h->nc > 1) {
+      adjoint_lts(h, n_steps / period, every, data, misfit, grad, synth_out, dq0, stream, d_amat, d_fwd, d_back,
+                  d_relem, d_rphi, nrec);
+      return;
+    }
     d_syn.alloc(sizeof(float) * (n_steps + 1) * nrec * 3);
     d_res.alloc(sizeof(float) * (n_steps + 1) * nrec * 3);
     d_t.alloc(sizeof(float) * K * NB9);
@@ -1539,14 +1765,6 @@ int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* 
     d_cp.alloc(sizeof(float) * ncp * K * qs);
     d_seg.alloc(sizeof(float) * seg * K * qs);
     d_qn.alloc(sizeof(float) * K * qs);
-    auto up = [&](void* dst, const void* src, size_t bytes) {
-      ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, stream), "adjoint upload");
-    };
-    up(d_amat.p, amat.data(), sizeof(float) * amat.size());
-    up(d_fwd.p, fwd.data(), sizeof(int) * fwd.size());
-    up(d_back.p, back.data(), sizeof(int) * back.size());
-    up(d_relem.p, relem.data(), sizeof(int) * nrec);
-    up(d_rphi.p, rphi.data(), sizeof(float) * rphi.size());
     const size_t qbytes = sizeof(float) * K * qs;
     auto dcopy = [&](void* dst, const void* src) {
       ck(cudaMemcpyAsync(dst, src, qbytes, cudaMemcpyDeviceToDevice, stream), "adjoint copy");
@@ -1647,46 +1865,7 @@ int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* 
       for (int64_t k = 0; k < K; ++k)
         for (int q = 0; q < NB9; ++q) dq0[k * NB9 + q] = lq[h->iperm[k] * NB9 + q];
     // ---- gradient: correlations against the exact material derivatives of the operators
-    if (grad) {
-      auto work = [&](int64_t k0, int64_t k1) {
-        lts::Dual S[3][81], Am[81], Ap[81];
-        for (int64_t e = k0; e < k1; ++e) {
-          const double* We = &W[h->iperm[e] * ltsdev::AM_SIZE];
-          double g[3] = {0, 0, 0};
-          for (int p = 0; p < 3; ++p) {
-            element_operators<lts::Dual>(h, e, -1, p, S, nullptr, nullptr);
-            for (int c = 0; c < 3; ++c)
-              for (int q = 0; q < 81; ++q) g[p] += S[c][q].d * We[ltsdev::AM_STAR + c * 81 + q];
-          }
-          for (int i = 0; i < 4; ++i) {
-            for (int p = 0; p < 3; ++p) {
-              element_operators<lts::Dual>(h, e, i, p, nullptr, Am, Ap);
-              for (int q = 0; q < 81; ++q)
-                g[p] += Am[q].d * We[ltsdev::AM_LOC + i * 81 + q] + Ap[q].d * We[ltsdev::AM_NBR + i * 81 + q];
-            }
-            // the neighbour's face that looks at e: its operators depend on e's material
-            const int64_t nb = h->mesh.nbr[4 * e + i];
-            if (nb < 0) continue;
-            const int ip = h->mesh.nbr_face[4 * e + i];
-            const double* Wn = &W[h->iperm[nb] * ltsdev::AM_SIZE];
-            for (int p = 0; p < 3; ++p) {
-              element_operators<lts::Dual>(h, nb, ip, 3 + p, nullptr, Am, Ap);
-              for (int q = 0; q < 81; ++q)
-                g[p] += Am[q].d * Wn[ltsdev::AM_LOC + ip * 81 + q] + Ap[q].d * Wn[ltsdev::AM_NBR + ip * 81 + q];
-            }
-          }
-          for (int p = 0; p < 3; ++p) grad[3 * e + p] = g[p];
-        }
-      };
-      const int nth = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
-      std::vector<std::thread> pool;
-      const int64_t chunk = (K + nth - 1) / nth;
-      for (int t = 0; t < nth; ++t) {
-        const int64_t k0 = t * chunk, k1 = std::min(K, k0 + chunk);
-        if (k0 < k1) pool.emplace_back(work, k0, k1);
-      }
-      for (auto& th : pool) th.join();
-    }
+    if (grad) contract_gradient(h, W, grad);
   });
 }
 

@@ -32,6 +32,8 @@ struct Launchers {
   void (*adj_sample)(const float* Q, long long qs, const int* elem, const float* phi, int nrec, float* out,
                      cudaStream_t);
   void (*adj_source)(float* lam, const int* elem, const float* phi, const float* res, int nrec, cudaStream_t);
+  void (*adj_pred)(const DevOps&, const AdjLtsArgs&, const PhaseArgs&, int nelem, cudaStream_t);
+  void (*adj_nbr)(const DevOps&, const AdjLtsArgs&, const PhaseArgs&, int K, cudaStream_t);
   // face-local messages of a partitioned run (one simulation)
   void (*pack)(const DevOps&, const DevState&, const PhaseArgs&, const int* send_elem, const int* send_code,
                const int* recv_cluster, int n, float* msg, cudaStream_t);
@@ -109,6 +111,12 @@ struct Impl {
   static void adj_source(float* lam, const int* elem, const float* phi, const float* res, int nrec, cudaStream_t st) {
     k_adj_source<O><<<1, 64, 0, st>>>(lam, elem, phi, res, nrec);
   }
+  static void adj_pred(const DevOps& o, const AdjLtsArgs& a, const PhaseArgs& p, int n, cudaStream_t st) {
+    k_adj_pred<O><<<n, 128, 0, st>>>(o, a, p);
+  }
+  static void adj_nbr(const DevOps& o, const AdjLtsArgs& a, const PhaseArgs& p, int K, cudaStream_t st) {
+    k_adj_nbr<O><<<K, 128, 0, st>>>(o, a, p);
+  }
   static void energy(const float* Q, long long qs, int nsim, int fg, const double* emat, int K, double* partial,
                      int nblocks, cudaStream_t st) {
     k_energy<O, M><<<nblocks, 256, 0, st>>>(Q, qs, nsim, fg, emat, K, partial);
@@ -142,6 +150,8 @@ struct Impl {
       L.adj_step = &adj_step;
       L.adj_sample = &adj_sample;
       L.adj_source = &adj_source;
+      L.adj_pred = &adj_pred;
+      L.adj_nbr = &adj_nbr;
     }
     L.energy = &energy;
     return L;

@@ -142,3 +142,73 @@ def test_autograd_function():
     J2, g, _ = s.misfit_gradient(n, data, every=2)
     assert float(J.detach()) == J2
     assert np.array_equal(tr.grad.numpy(), g[:, 0]) and np.array_equal(tm.grad.numpy(), g[:, 2])
+
+
+def _forced_clusters(m):
+    from oracle import lts as olts
+    om = Mesh(m["xyz"], m["tet"], m["face_bc"])
+    cx = om.centroid[:, 0]
+    return olts.normalise(np.digitize(cx, np.quantile(cx, [0.3, 0.65])), om.nbr)
+
+
+def _gpu_lts(order, m, rho, lam, mu, q0, rec, src, cl, dt):
+    s = binding.Solver(order, 0, device=0)
+    s.set_mesh(m["xyz"], m["tet"], m["face_bc"])
+    s.set_material(rho, np.sqrt((lam + 2 * mu) / rho), np.sqrt(mu / rho))
+    s.add_point_source(*src)
+    for x in rec:
+        s.add_receiver(x, dt)
+    s.force_clusters(cl, 3, 0.5, 1.0)
+    s.set_finest_dt(dt)
+    s.set_dofs(q0)
+    return s
+
+
+@pytest.mark.parametrize("order", [3, 4])
+def test_gpu_lts_adjoint_matches_oracle_lts_adjoint(order):
+    """Three forced clusters (all buffer relations), samples at the macro-step boundaries."""
+    from oracle.adjoint import misfit_gradient_lts
+    m, mat, q0, rec, src = _case(order, seed=14)
+    rho, lam, mu = _rlm(mat)
+    cl = _forced_clusters(m)
+    assert len(np.unique(cl)) == 3
+    dt, n_macro = 1.5e-4, 3
+    om = Mesh(m["xyz"], m["tet"], m["face_bc"])
+
+    def oracle(mu_):
+        o = Oracle(order, 0, om, rho, np.sqrt((lam + 2 * mu_) / rho), np.sqrt(mu_ / rho))
+        o.add_point_source(*src)
+        o.setup_clusters(3, 0.5, lam=1.0, clusters=cl)
+        o.delta = dt
+        o.Q = q0.copy()
+        re = [om.locate(x) for x in rec]
+        rp = [o.basis.phi(om.xi_of(k, x)[None, :])[0] for k, x in zip(re, rec)]
+        return o, re, rp
+
+    o, re, rp = oracle(mu * 1.02)
+    _, _, _, data = misfit_gradient_lts(o, n_macro, re, rp, np.zeros((n_macro + 1, 3, 3)))
+    o, re, rp = oracle(mu)
+    J0, g0, dq0_o, syn0 = misfit_gradient_lts(o, n_macro, re, rp, data)
+    s = _gpu_lts(order, m, rho, lam, mu, q0, rec, src, cl, dt)
+    J, g, syn, dq0 = s.misfit_gradient(4 * n_macro, data, every=2, want_dq0=True)
+    assert _rel(syn, syn0) <= 1e-5
+    assert abs(J / J0 - 1) <= 1e-3
+    for p in range(3):
+        assert _rel(g[:, p], g0[:, p]) <= 2e-3, (p, _rel(g[:, p], g0[:, p]))
+    assert _rel(dq0, dq0_o) <= 2e-3
+    assert abs(s.info()["time"] - 4 * n_macro * dt) <= 1e-12
+
+
+def test_lts_checkpoint_spacing_does_not_change_the_result():
+    order, n_macro = 4, 3
+    m, mat, q0, rec, src = _case(order, seed=16)
+    rho, lam, mu = _rlm(mat)
+    cl = _forced_clusters(m)
+    data = np.zeros((n_macro + 1, 3, 3))
+    out = []
+    for every in (1, 2, n_macro):
+        s = _gpu_lts(order, m, rho, lam, mu, q0, rec, src, cl, 1.5e-4)
+        out.append(s.misfit_gradient(4 * n_macro, data, every=every))
+        s.close()
+    for J, g, syn in out[1:]:
+        assert J == out[0][0] and np.array_equal(g, out[0][1]) and np.array_equal(syn, out[0][2])
