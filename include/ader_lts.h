@@ -264,6 +264,7 @@ int lts_set_finest_dt(lts_t* h, double dt);
  * B1 - B2), a predict pass collects the adjoints of the buffers it wrote. Each macro step
  * is recomputed phase by phase from its boundary state, keeping 2^(N_c-1) copies of Q
  * and 3 x 2^(N_c-1) copies of the buffers.
+ * With grad and dq0 both NULL only the forward sweep and the misfit run.
  * Errors: LTS_ERR_ARG, LTS_ERR_STATE, LTS_ERR_OOM, LTS_ERR_CUDA. */
 int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* data, double* misfit,
                         double* grad, double* synth_out, double* dq0, void* cuda_stream);

@@ -54,3 +54,96 @@ class SeismogramMisfit(torch.autograd.Function):
     def backward(ctx, gJ):
         gr, gl, gm = ctx.saved_tensors
         return gJ * gr, gJ * gl, gJ * gm, None
+
+
+def _config5(nx, ny, nz, order, n_clusters, n_rec, seed=11):
+    """Elastic layered box with a +1 % (rho, lambda, mu) blob for the observed data."""
+    from . import synth
+    mesh = synth.graded_box(nx, ny, nz, 250.0, 125.0)
+    mat = synth.random_layers(mesh)
+    rho = mat["rho"].astype(float)
+    mu = rho * mat["vs"] ** 2
+    lam = rho * mat["vp"] ** 2 - 2 * mu
+    cen = mesh["xyz"][mesh["tet"]].mean(axis=1)
+    c0 = np.array([0.45 * nx * 250.0, 0.5 * ny * 250.0, -600.0])
+    blob = 0.01 * np.exp(-np.sum((cen - c0) ** 2, axis=1) / (2 * 1000.0 ** 2))
+    rng = np.random.default_rng(seed)
+    rec = [np.array([x, y, -1.0]) for x, y in rng.uniform([0.1 * nx * 250.0, 0.1 * ny * 250.0],
+                                                           [0.9 * nx * 250.0, 0.9 * ny * 250.0], size=(n_rec, 2))]
+    src = (np.array([0.4 * nx * 250.0 + 7.0, 0.5 * ny * 250.0 - 3.0, -1000.0]),
+           np.array([0.0, 0.0, 0.0, 1.0, 0.0, 0.0]), 5.0, 0.24, 1e15)
+    return mesh, (rho, lam, mu), blob, rec, src
+
+
+def main():
+    """Gradient of the seismogram misfit on the adjoint workload: 40 x 40 x 21 hexes x 6 =
+    201,600 jittered graded tets, elastic order 4, 3 LTS clusters, 2,000 finest steps, 32
+    surface receivers, observed data from a run with rho, lambda, mu 1 % higher in a
+    Gaussian blob, checkpoints every 100 finest steps. Prints one JSON line."""
+    import argparse
+    import json
+    import time
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--nx", type=int, default=40)
+    ap.add_argument("--ny", type=int, default=40)
+    ap.add_argument("--nz", type=int, default=21)
+    ap.add_argument("--order", type=int, default=4)
+    ap.add_argument("--clusters", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--checkpoint", type=int, default=100, help="finest steps between checkpoints")
+    ap.add_argument("--receivers", type=int, default=32)
+    ap.add_argument("--fd", type=int, default=3, help="elements checked by central differences")
+    a = ap.parse_args()
+    mesh, (rho, lam, mu), blob, rec, src = _config5(a.nx, a.ny, a.nz, a.order, a.clusters, a.receivers)
+    K = mesh["tet"].shape[0]
+    period = 2 ** (a.clusters - 1)
+    n_macro = a.steps // period
+
+    def solver(r, l, m, cl=None, lam_c=None, dt=None):
+        s = binding.Solver(a.order, 0, device=0)
+        s.set_mesh(mesh["xyz"], mesh["tet"], mesh["face_bc"])
+        s.set_material(r, np.sqrt((l + 2 * m) / r), np.sqrt(m / r))
+        s.add_point_source(*src)
+        for x in rec:
+            s.add_receiver(x, 0.01)
+        if cl is None:
+            cl, lam_c, _ = s.setup_clusters(a.clusters, 0.5)
+            dt = s.info()["finest_dt"]
+        else:
+            s.force_clusters(cl, a.clusters, 0.5, lam_c)
+            s.set_finest_dt(dt)
+        return s, cl, lam_c, dt
+
+    base, cl, lam_c, dt = solver(rho, lam, mu)
+    data0 = np.zeros((n_macro + 1, len(rec), 3))
+    pert, _, _, _ = solver(rho * (1 + blob), lam * (1 + blob), mu * (1 + blob), cl, lam_c, dt)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, data = pert.misfit(a.steps, data0, every=a.checkpoint // period)
+    t_fwd = time.perf_counter() - t0
+    pert.close()
+    t0 = time.perf_counter()
+    J, grad, _ = base.misfit_gradient(a.steps, data, every=a.checkpoint // period)
+    t_grad = time.perf_counter() - t0
+    base.close()
+    fd = []
+    params = [rho, lam, mu]
+    for k in np.argsort(-np.abs(grad[:, 2]))[:a.fd]:
+        vals = []
+        for sgn in (1, -1):
+            pp = [x.copy() for x in params]
+            pp[2][k] *= 1 + sgn * 1e-3
+            s, _, _, _ = solver(*pp, cl, lam_c, dt)
+            vals.append(s.misfit(a.steps, data, every=a.checkpoint // period)[0])
+            s.close()
+        fd.append(dict(element=int(k), adjoint=float(grad[k, 2]),
+                       central_difference=float((vals[0] - vals[1]) / (2e-3 * mu[k]))))
+    out = dict(elements=int(K), order=a.order, clusters=a.clusters, cluster_elems=np.bincount(cl).tolist(),
+               finest_steps=a.steps, macro_steps=n_macro, checkpoint_finest_steps=a.checkpoint, receivers=len(rec),
+               misfit=J, forward_s=t_fwd, misfit_and_gradient_s=t_grad, gradient_over_forward=t_grad / t_fwd,
+               grad_norm=[float(np.linalg.norm(grad[:, p])) for p in range(3)], fd_check_mu=fd)
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -369,6 +369,15 @@ class Solver:
                                               _ptr(grad), _ptr(syn), _ptr(dq0), _stream_handle(stream)))
         return (J.value, grad, syn, dq0) if want_dq0 else (J.value, grad, syn)
 
+    def misfit(self, n_steps, data, every=100, stream=None):
+        """Forward sweep only: J and the samples."""
+        data = np.ascontiguousarray(data, dtype=np.float64)
+        J = ctypes.c_double()
+        syn = np.zeros(data.shape)
+        self._check(lib().lts_misfit_gradient(self._h, int(n_steps), int(every), _ptr(data), ctypes.byref(J), None,
+                                              _ptr(syn), None, _stream_handle(stream)))
+        return J.value, syn
+
     def set_graphs(self, enable=True):
         self._check(lib().lts_set_graphs(self._h, 1 if enable else 0))
 

@@ -923,6 +923,10 @@ void adjoint_lts(lts_solver* h, int64_t n_macro, int64_t every, const double* da
     res[q] = (float)r;
     J += 0.5 * r * r;
   }
+  if (misfit) *misfit = J;
+  if (synth_out)
+    for (size_t q = 0; q < syn.size(); ++q) synth_out[q] = syn[q];
+  if (!grad && !dq0) return;       // misfit only: no reverse sweep
   ck(cudaMemcpyAsync(d_res.p, res.data(), sizeof(float) * res.size(), cudaMemcpyHostToDevice, stream), "residuals");
   // ---- reverse sweep
   ck(cudaMemsetAsync(d_lq.p, 0, sizeof(float) * K * NB9, stream), "memset");
@@ -1796,6 +1800,12 @@ int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* 
       const double r = (double)syn[q] - data[q];
       res[q] = (float)r;
       J += 0.5 * r * r;
+    }
+    if (!grad && !dq0) {           // misfit only: no reverse sweep
+      if (misfit) *misfit = J;
+      if (synth_out)
+        for (size_t q = 0; q < syn.size(); ++q) synth_out[q] = syn[q];
+      return;
     }
     up(d_res.p, res.data(), sizeof(float) * res.size());
     // ---- reverse sweep
