@@ -46,7 +46,8 @@ enum {
     LTS_ERR_CUDA = -3,     /* a CUDA runtime call failed                                */
     LTS_ERR_OOM = -4,      /* host or device allocation failed / bound block too small  */
     LTS_ERR_STATE = -5,    /* call out of order (e.g. advance before cluster set-up)   */
-    LTS_ERR_TIMEOUT = -6   /* a bounded device-side wait gave up                       */
+    LTS_ERR_TIMEOUT = -6,  /* a bounded device-side wait gave up                       */
+    LTS_ERR_NONFINITE = -7 /* a reduction found NaN or Inf in the state                 */
 };
 
 /* Fused simulations (Sec. IV-A): n_fused is 1 or a multiple of LTS_FUSED_MULTIPLE up to
@@ -167,7 +168,10 @@ int lts_get_seismogram(lts_t* h, int id, int fused_idx, double* t_out, double* v
                        int64_t cap, int64_t* n);
 
 /* Discrete elastic energy sum_k |det J_k| sum_b (rho |v_b|^2/2 + sigma_b : C^-1 sigma_b / 2),
- * summed over the fused simulations, reduced in FP64 on the device. Synchronises. */
+ * summed over the fused simulations, reduced in FP64 on the device. Synchronises. The
+ * reduction is also the state's sentinel: a NaN or Inf anywhere in the stresses or
+ * velocities makes it non-finite, and the call then stores the value and returns
+ * LTS_ERR_NONFINITE. */
 int lts_energy(lts_t* h, double* e);
 
 /* Run information. n_clusters_out; per cluster (arrays of length >= 8, may be NULL):
@@ -304,6 +308,17 @@ int lts_autotune(lts_t* h, int allow_tf32, void* cuda_stream, int* chosen, doubl
  * threads[3] (threads per CTA), in the order predict+local (CUDA cores), neighbour,
  * predict+local (tensor cores). Either array may be NULL. */
 int lts_launch_config(lts_t* h, int* ctas_per_sm, int* threads);
+
+/* Checkpoint / resume at a macro-step boundary (every cluster has completed its steps and
+ * no LTS buffer holds data still to be read, so the DOFs are the whole state). save writes
+ * the DOFs of every simulation (FP32 as held on the device), the step counter, the finest
+ * step and every receiver's samples so far to `path`; load restores them into a handle
+ * set up the same way (mesh, material, sources, receivers, clusters, simulations), so that
+ * continuing reproduces the uninterrupted run bitwise. Both synchronise. Errors:
+ * LTS_ERR_STATE (no clusters, or not at a macro-step boundary), LTS_ERR_ARG (file not
+ * writable / readable, or written for a different set-up). */
+int lts_checkpoint_save(lts_t* h, const char* path);
+int lts_checkpoint_load(lts_t* h, const char* path);
 
 /* Energy of a caller-owned DOF array, for callers that cannot allocate device memory.
  * The paper has no counterpart: this is an integration aid. Some callers cannot call

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "libaderlts.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "ader_lts.h")
 
 LTS_OK, LTS_ERR_ARG, LTS_ERR_MESH, LTS_ERR_CUDA, LTS_ERR_OOM, LTS_ERR_STATE, LTS_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
+LTS_ERR_NONFINITE = -7
 BC_INTERIOR, BC_ABSORBING, BC_FREE_SURFACE, BC_PERIODIC = 0, 1, 2, 3
 
 _lib = None
@@ -58,6 +59,8 @@ _SIGS = {
     "lts_set_partition": (_I, [_P, _I, _P]),
     "lts_exchange_bytes": (_I, [_P, _P]),
     "lts_set_graphs": (_I, [_P, _I]),
+    "lts_checkpoint_save": (_I, [_P, ctypes.c_char_p]),
+    "lts_checkpoint_load": (_I, [_P, ctypes.c_char_p]),
     "lts_set_finest_dt": (_I, [_P, _D]),
     "lts_misfit_gradient": (_I, [_P, _L, _L, _P, _P, _P, _P, _P, _P]),
     "lts_energy_noalloc": (_I, [_I, _I, _P, _P, _L, _P, _P]),
@@ -377,6 +380,12 @@ class Solver:
         self._check(lib().lts_misfit_gradient(self._h, int(n_steps), int(every), _ptr(data), ctypes.byref(J), None,
                                               _ptr(syn), None, _stream_handle(stream)))
         return J.value, syn
+
+    def checkpoint_save(self, path):
+        self._check(lib().lts_checkpoint_save(self._h, str(path).encode()))
+
+    def checkpoint_load(self, path):
+        self._check(lib().lts_checkpoint_load(self._h, str(path).encode()))
 
     def set_graphs(self, enable=True):
         self._check(lib().lts_set_graphs(self._h, 1 if enable else 0))

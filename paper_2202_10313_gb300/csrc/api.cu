@@ -4,12 +4,15 @@
 #include <thread>
 #include <type_traits>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <functional>
 #include <new>
 #include <numeric>
 #include <string>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/ader_lts.h"
 #include "host.h"
@@ -635,6 +638,19 @@ int enqueue_phase(lts_solver* h, const Phase& ph, cudaStream_t stream, bool with
   const int nelem = pa.end - pa.begin;
   if (nelem <= 0) return 0;
   int launches = 0;
+  // NVTX range per phase while profiling (kind, finest level, clusters 0..top)
+  struct Range {
+    bool on;
+    ~Range() {
+      if (on) nvtxRangePop();
+    }
+  } range{h->profiling};
+  if (range.on) {
+    char name[64];
+    std::snprintf(name, sizeof(name), "%s s=%lld clusters<=%d", ph.kind == 0 ? "neighbour" : "predict",
+                  (long long)ph.s, ph.top);
+    nvtxRangePushA(name);
+  }
   // CTA batches: NE elements (one simulation) or one element and FG of its simulations
   const int nb = X.FG > 1 ? nelem * (h->nsim / X.FG)
                           : (nelem + (ph.kind == 0 ? X.NEN : X.NE) - 1) / (ph.kind == 0 ? X.NEN : X.NE);
@@ -690,6 +706,10 @@ int64_t macro_msg_bytes(const lts_solver* h, const MacroPlan& mp) {
 
 void advance_steps(lts_solver* h, int64_t n_finest, cudaStream_t stream) {
   if (!h->ready) fail(LTS_ERR_STATE, "clusters not set up");
+  struct Range {
+    Range() { nvtxRangePushA("lts_advance"); }
+    ~Range() { nvtxRangePop(); }
+  } range;
   const int nc = h->nc;
   const int64_t period = int64_t(1) << (nc - 1);
   if (n_finest < 0 || n_finest % period != 0) fail(LTS_ERR_ARG, "n_finest must be a multiple of 2^(N_c-1)");
@@ -1434,6 +1454,102 @@ int lts_energy(lts_t* h, double* e) {
     double s = 0.0;
     for (double v : part) s += v;
     *e = s;
+    if (!std::isfinite(s)) fail(LTS_ERR_NONFINITE, "non-finite energy: the state holds NaN or Inf");
+  });
+}
+
+int lts_checkpoint_save(lts_t* h, const char* path) {
+  return run(h, [&] {
+    if (!h->ready) fail(LTS_ERR_STATE, "clusters not set up");
+    const int64_t period = int64_t(1) << (h->nc - 1);
+    if (h->s_now % period != 0) fail(LTS_ERR_STATE, "not at a macro-step boundary");
+    if (!path) fail(LTS_ERR_ARG, "null path");
+    ck(cudaSetDevice(h->device), "cudaSetDevice");
+    ck(cudaDeviceSynchronize(), "synchronize");
+    check_device_error(h);
+    const int64_t K = h->mesh.K, qs = h->dst.qs;
+    std::vector<float> q((size_t)K * qs);
+    ck(cudaMemcpy(q.data(), h->dst.Q, q.size() * sizeof(float), cudaMemcpyDeviceToHost), "download Q");
+    std::vector<float> seis((size_t)h->seis_used * 9 * h->nsim);
+    if (!seis.empty())
+      ck(cudaMemcpy(seis.data(), h->d_seis, seis.size() * sizeof(float), cudaMemcpyDeviceToHost), "download samples");
+    FILE* f = std::fopen(path, "wb");
+    if (!f) fail(LTS_ERR_ARG, std::string("cannot write ") + path);
+    bool ok = true;
+    auto put = [&](const void* p, size_t bytes) { ok = ok && std::fwrite(p, 1, bytes, f) == bytes; };
+    const char magic[8] = {'L', 'T', 'S', 'C', 'K', 'P', 'T', '1'};
+    const int64_t hdr[9] = {h->order, h->nmech, h->nsim, K, h->nc, qs, (int64_t)h->receivers.size(),
+                            (int64_t)h->sources.size(), h->s_now};
+    put(magic, 8);
+    put(hdr, sizeof(hdr));
+    put(&h->delta, sizeof(double));
+    put(q.data(), q.size() * sizeof(float));
+    for (const Receiver& r : h->receivers) {
+      const int64_t n = (int64_t)r.t.size();
+      put(&n, sizeof(n));
+      put(r.t.data(), n * sizeof(double));
+      for (int64_t i = 0; i < n; ++i) put(&seis[(size_t)r.slot[i] * 9 * h->nsim], 9 * h->nsim * sizeof(float));
+    }
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) fail(LTS_ERR_ARG, std::string("write failed: ") + path);
+  });
+}
+
+int lts_checkpoint_load(lts_t* h, const char* path) {
+  return run(h, [&] {
+    if (!h->ready) fail(LTS_ERR_STATE, "clusters not set up");
+    if (!path) fail(LTS_ERR_ARG, "null path");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) fail(LTS_ERR_ARG, std::string("cannot read ") + path);
+    struct Close {
+      FILE* f;
+      ~Close() { std::fclose(f); }
+    } close_f{f};
+    auto get = [&](void* p, size_t bytes) {
+      if (std::fread(p, 1, bytes, f) != bytes) fail(LTS_ERR_ARG, "truncated checkpoint");
+    };
+    char magic[8];
+    get(magic, 8);
+    if (std::memcmp(magic, "LTSCKPT1", 8) != 0) fail(LTS_ERR_ARG, "not a checkpoint file");
+    int64_t hdr[9];
+    get(hdr, sizeof(hdr));
+    const int64_t K = h->mesh.K, qs = h->dst.qs;
+    const int64_t want[8] = {h->order, h->nmech, h->nsim, K, h->nc, qs, (int64_t)h->receivers.size(),
+                             (int64_t)h->sources.size()};
+    for (int i = 0; i < 8; ++i)
+      if (hdr[i] != want[i]) fail(LTS_ERR_ARG, "checkpoint written for a different set-up");
+    double delta = 0.0;
+    get(&delta, sizeof(double));
+    if (delta != h->delta) fail(LTS_ERR_ARG, "checkpoint written with a different time step");
+    std::vector<float> q((size_t)K * qs);
+    get(q.data(), q.size() * sizeof(float));
+    std::vector<std::vector<double>> ts(h->receivers.size());
+    std::vector<float> seis;
+    for (size_t r = 0; r < h->receivers.size(); ++r) {
+      int64_t n = 0;
+      get(&n, sizeof(n));
+      if (n < 0 || n > (int64_t(1) << 40)) fail(LTS_ERR_ARG, "corrupt checkpoint");
+      ts[r].resize(n);
+      get(ts[r].data(), n * sizeof(double));
+      const size_t off = seis.size();
+      seis.resize(off + (size_t)n * 9 * h->nsim);
+      get(seis.data() + off, (size_t)n * 9 * h->nsim * sizeof(float));
+    }
+    ck(cudaSetDevice(h->device), "cudaSetDevice");
+    ck(cudaDeviceSynchronize(), "synchronize");
+    ck(cudaMemcpy(h->dst.Q, q.data(), q.size() * sizeof(float), cudaMemcpyHostToDevice), "upload Q");
+    const size_t nsamp = seis.size() / (9 * h->nsim);
+    ensure_capacity(reinterpret_cast<void**>(&h->d_seis), &h->seis_cap, nsamp * 9 * h->nsim, sizeof(float));
+    if (!seis.empty())
+      ck(cudaMemcpy(h->d_seis, seis.data(), seis.size() * sizeof(float), cudaMemcpyHostToDevice), "upload samples");
+    int64_t slot = 0;
+    for (size_t r = 0; r < h->receivers.size(); ++r) {
+      h->receivers[r].t = ts[r];
+      h->receivers[r].slot.resize(ts[r].size());
+      for (size_t i = 0; i < ts[r].size(); ++i) h->receivers[r].slot[i] = slot++;
+    }
+    h->seis_used = nsamp;
+    h->s_now = hdr[8];
   });
 }
 

@@ -75,3 +75,34 @@ def bytes_neighbour(o, m, n_fused=1):
 def paper_flops_per_update():
     """Sec. VII-B: 529,110 flops per element update (O=5, m=3, one simulation, block-sparse)."""
     return 529110
+
+
+def operator_nonzeros(order, rel=1e-9):
+    """Nonzeros of the reference operators the kernels contract with (K_c, F~_i, F-_{j,h}),
+    counted from the library's own FP64 operators (host-side, no device); entries below
+    rel times the largest are the rounding of exact zeros."""
+    import numpy as np
+    from . import binding
+    K, Ft, Fb = binding.reference_operators(order)
+    nz = lambda a: int(np.sum(np.abs(a) > rel * np.abs(a).max()))
+    return dict(K=[nz(K[c]) for c in range(3)], Ft=[nz(Ft[i]) for i in range(4)],
+                Fb=[[nz(Fb[j, h]) for h in range(3)] for j in range(4)])
+
+
+def essential_flops(order, m):
+    """Flops of one element update if only the true nonzeros of K_c, F~ and F- were
+    multiplied (the kernels multiply whole degree blocks: flops_predict + flops_neighbour);
+    the star, flux and Taylor arithmetic is counted as in the block model."""
+    nzs = operator_nonzeros(order)
+    B, F, NQ = nbasis(order), nface(order), 9 + 6 * m
+    ck = 2 * 9 * sum(nzs["K"])                     # one derivative, 3 products of 9 rows
+    vol = ck
+    face_g = 2 * 9 * sum(nzs["Ft"])
+    face_h = 2 * 6 * sum(nzs["Ft"])                # F^ = F~^T
+    nbr_g = 2 * 9 * sum(nzs["Fb"][0]) / 3.0 * 4    # one F- per face
+    degs = _col_degrees(order)
+    star = 2 * 54 + 20
+    epi = (order - 1) * B * (star + m * 36 + 2 * (NQ + 9)) + B * (star + m * 36 + NQ)
+    flux = 2 * 4 * F * 50 + 2 * B * 4 * (30 + (18 if m else 0))
+    upd = 2 * B * (NQ + 12 * m)
+    return (order - 1) * ck + vol + face_g + face_h + nbr_g + face_h + epi + flux + upd
