@@ -35,6 +35,23 @@ UNIT = "element-updates/s"
 ORDER, NMECH, NCLUSTERS, CFL = 5, 3, 5, 0.5
 FULL = dict(nx=96, ny=96, nz=38, h=250.0, hz=125.0)
 FUSED_FULL = dict(nx=64, ny=64, nz=40, h=250.0, hz=125.0)
+# elastic order-5 workload: 64 x 64 x 32 hexes x 6 = 786,432 tets, three layers by depth
+ELASTIC_FULL = dict(nx=64, ny=64, nz=32, h=250.0, hz=125.0)
+ELASTIC_ORDER, ELASTIC_CLUSTERS = 5, 4
+
+
+def make_elastic_workload(nx, ny, nz, h, hz):
+    """Layers 0-1 km vs 1000, 1-3 km vs 2000, below vs 3500 m/s (vp = sqrt(3) vs, rho 2700),
+    a 2 Hz Ricker moment-tensor source at the centre 2 km deep (t0 = 1.2 / f0), 64 surface
+    receivers."""
+    from paper_2202_10313_gb300 import synth
+    mesh = synth.graded_box(nx, ny, nz, h, hz)
+    mat = synth.layered(mesh, [1000.0, 3000.0], [1000.0, 2000.0, 3500.0])
+    lx, ly, depth = nx * h, ny * h, mesh["depth"]
+    src = dict(x=np.array([0.5 * lx + 17.0, 0.5 * ly - 23.0, -2000.0 if depth > 2500 else -0.4 * depth]),
+               m6=np.array([0.0, 0.0, 0.0, 1.0, 0.0, 0.0]), f0=2.0, t0=0.6, m0=1e15)
+    recs = synth.surface_receiver_grid(8, 8, (0.0, lx), (0.0, ly), depth=1.0)
+    return mesh, mat, src, recs
 SAMPLE = dict(nx=12, ny=12, nz=5, h=250.0, hz=125.0)   # bounded CPU sample of the same generator
 
 
@@ -176,16 +193,17 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     F = max(1, args.fused)
-    cfg = FUSED_FULL if F > 1 else FULL
+    order, nmech, nclusters = (ELASTIC_ORDER, 0, ELASTIC_CLUSTERS) if args.elastic else (ORDER, NMECH, NCLUSTERS)
+    cfg = ELASTIC_FULL if args.elastic else (FUSED_FULL if F > 1 else FULL)
     if args.small:
         cfg = dict(nx=24, ny=24, nz=10, h=250.0, hz=125.0)
     elif args.medium:
         cfg = dict(nx=48, ny=48, nz=19, h=250.0, hz=125.0)
-    mesh, mat, src, recs = make_workload(**cfg)
+    mesh, mat, src, recs = (make_elastic_workload if args.elastic else make_workload)(**cfg)
     K = mesh["tet"].shape[0]
-    s = binding.Solver(ORDER, NMECH, device=local_rank, n_fused=F)
+    s = binding.Solver(order, nmech, device=local_rank, n_fused=F)
     s.set_mesh(mesh["xyz"], mesh["tet"], mesh["face_bc"])
-    s.set_material(mat["rho"], mat["vp"], mat["vs"], mat["qp"], mat["qs"], 0.1, 5.0)
+    s.set_material(mat["rho"], mat["vp"], mat["vs"], mat.get("qp"), mat.get("qs"), 0.1, 5.0)
     if F == 1:
         s.add_point_source(src["x"], src["m6"], src["f0"], src["t0"], src["m0"])
     else:
@@ -198,10 +216,10 @@ def run_ours(args, rank, world, local_rank):
     for r in recs:
         s.add_receiver(r, dt_rec)
     if args.partition <= 1:
-        s.use_torch_memory(NCLUSTERS)
+        s.use_torch_memory(nclusters)
     if args.contraction != "auto":
         s.set_contraction(args.contraction)
-    _, lam, speedup = s.setup_clusters(NCLUSTERS, CFL)
+    _, lam, speedup = s.setup_clusters(nclusters, CFL)
     pstats = None
     if args.partition > 1:
         part, pstats = s.partition(args.partition)
@@ -210,7 +228,7 @@ def run_ours(args, rank, world, local_rank):
     if args.contraction == "auto":
         tuned = s.autotune(allow_tf32=False, stream=torch.cuda.current_stream())
     info = s.info()
-    period = 2 ** (NCLUSTERS - 1)
+    period = 2 ** (nclusters - 1)
     per_macro = int(info["updates_per_macro"].sum()) * F      # simulation element updates
     stream = torch.cuda.current_stream()
     # warm-up
@@ -266,9 +284,9 @@ def run_ours(args, rank, world, local_rank):
     name = ["k_predict_local", "k_neighbour"][kind]
     avg_ms = kst["ms"][kind] / max(kst["launches"][kind], 1)
     elems_per_launch = kst["elems"][kind] * F / max(kst["launches"][kind], 1)    # simulation elements
-    fl = perfmodel.flops_predict(ORDER, NMECH) if kind == 0 else perfmodel.flops_neighbour(ORDER, NMECH)
-    by = (perfmodel.bytes_predict(ORDER, NMECH, n_fused=F) if kind == 0
-          else perfmodel.bytes_neighbour(ORDER, NMECH, n_fused=F))
+    fl = perfmodel.flops_predict(order, nmech) if kind == 0 else perfmodel.flops_neighbour(order, nmech)
+    by = (perfmodel.bytes_predict(order, nmech, n_fused=F) if kind == 0
+          else perfmodel.bytes_neighbour(order, nmech, n_fused=F))
     achieved_tf = fl * elems_per_launch / (avg_ms / 1000.0) / 1e12
     achieved_gbs = by * elems_per_launch / (avg_ms / 1000.0) / 1e9
     traffic = None
@@ -281,6 +299,8 @@ def run_ours(args, rank, world, local_rank):
         if ent and ent.get("kernel_hash") == kernel_hash():
             traffic = ent["dram_bytes_per_element"] * elems_per_launch
     metric, unit = METRIC, UNIT
+    if args.elastic:
+        metric = "element-updates/s, order-5 elastic LTS, 1 GB300"
     srcs = "1 moment-tensor source"
     if F > 1:
         metric = "simulation element-updates/s, order-5 anelastic LTS, %d fused sources, 1 GB300" % F
@@ -291,9 +311,10 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "contraction": tuned["contraction"] if tuned else args.contraction, "autotune": tuned,
-        "config": {"workload": "anelastic O5 m3 LTS, %d jittered graded tets, Nc=%d, lambda=%.2f, CFL %.1f, "
+        "config": {"workload": ("elastic O5" if args.elastic else "anelastic O5 m3") +
+                               " LTS, %d jittered graded tets, Nc=%d, lambda=%.2f, CFL %.1f, "
                                "%s, 64 receivers; step = 1 macro step (%d finest steps)"
-                               % (K, NCLUSTERS, lam, CFL, srcs, period),
+                               % (K, nclusters, lam, CFL, srcs, period),
                    "elements": K, "fused": F, "updates_per_step": per_macro,
                    "launch": s.launch_config(),
                    "cluster_elems": info["cluster_elems"].tolist(), "theoretical_lts_speedup": speedup,
@@ -313,7 +334,7 @@ def run_ours(args, rank, world, local_rank):
         "clocks": ck,
     }
     if pstats is not None:
-        B = ORDER * (ORDER + 1) * (ORDER + 2) // 6
+        B = order * (order + 1) * (order + 2) // 6
         line["partition"] = dict(parts=args.partition, face_local_bytes_per_step=xbytes,
                                  whole_buffer_bytes_per_step=pstats["buffer_msgs_per_macro"] * 9 * B * 4,
                                  **{k: v for k, v in pstats.items()})
@@ -338,6 +359,8 @@ def main():
     ap.add_argument("--medium", action="store_true", help="262k-tet mesh (profiling captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fused", type=int, default=1, help="fused simulations (multiple of 4; 1 = single)")
+    ap.add_argument("--elastic", action="store_true",
+                    help="elastic order-5 workload: 786,432 tets, 3 layers, 4 clusters (a parity config)")
     ap.add_argument("--partition", type=int, default=1,
                     help="emulated partitioned run: P weighted parts exchanging face-local messages")
     ap.add_argument("--contraction", default="auto", choices=["auto", "fp32", "tf32x3", "tf32"],

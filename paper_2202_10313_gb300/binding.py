@@ -359,7 +359,7 @@ class Solver:
     def set_finest_dt(self, dt):
         self._check(lib().lts_set_finest_dt(self._h, float(dt)))
 
-    def misfit_gradient(self, n_steps, data, every=100, stream=None, want_dq0=False):
+    def misfit_gradient(self, n_steps, data, every=100, stream=None, want_dq0=False, want_grad=True):
         """J, dJ/d(rho, lambda, mu) (K, 3), synthetic samples (shape of data: one row per
         sample time, n_rec, 3) and optionally dJ/dQ at the start (K, 9, B), by the discrete
         adjoint of the time loop (GTS: samples every step; LTS: every macro step)."""
@@ -369,7 +369,8 @@ class Solver:
         syn = np.zeros(data.shape)
         dq0 = np.zeros((self.K, 9, self.nb)) if want_dq0 else None
         self._check(lib().lts_misfit_gradient(self._h, int(n_steps), int(every), _ptr(data), ctypes.byref(J),
-                                              _ptr(grad), _ptr(syn), _ptr(dq0), _stream_handle(stream)))
+                                              _ptr(grad) if want_grad else None, _ptr(syn), _ptr(dq0),
+                                              _stream_handle(stream)))
         return (J.value, grad, syn, dq0) if want_dq0 else (J.value, grad, syn)
 
     def misfit(self, n_steps, data, every=100, stream=None):

@@ -1014,7 +1014,10 @@ void adjoint_lts(lts_solver* h, int64_t n_macro, int64_t every, const double* da
           aa.B1s = base;
           aa.B2s = base + K * bs;
           aa.B3s = base + 2 * K * bs;
-          X.adj_nbr(h->dops, aa, pa, (int)K, stream);
+          // a buffer owner differs by at most one cluster from the receivers it feeds, so
+          // the owners of this pass are the elements of clusters 0..top+1
+          const int owners = (int)h->cbeg[std::min(ph.top + 2, h->nc)];
+          X.adj_nbr(h->dops, aa, pa, owners, stream);
         }
       }
       X.adj_source(d_lq.get<float>(), relem, rphi, d_res.get<float>() + m * nrec * 3, nrec, stream);
@@ -1893,7 +1896,6 @@ int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* 
     float* sg = d_seg.get<float>();
     // ---- forward sweep with checkpoints every `every` steps
     const int64_t s0 = h->s_now;
-    const size_t seis0 = h->seis_used;
     std::vector<size_t> nrec_t(nrec);
     dcopy(cp, h->dst.Q);
     X.adj_sample(h->dst.Q, qs, d_relem.get<int>(), d_rphi.get<float>(), nrec, d_syn.get<float>(), stream);
@@ -1974,7 +1976,6 @@ int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* 
     // the state ends at t_N as after a plain advance
     dcopy(h->dst.Q, d_qn.p);
     h->s_now = s0 + n_steps;
-    (void)seis0;
     std::vector<double> W((size_t)K * ltsdev::AM_SIZE);
     ck(cudaMemcpyAsync(W.data(), d_w.p, sizeof(double) * W.size(), cudaMemcpyDeviceToHost, stream), "correlations");
     std::vector<float> lq;

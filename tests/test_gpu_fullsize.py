@@ -155,3 +155,104 @@ def test_fused_configuration_sampled_parity():
             err = rel_l2_groups(got[f, s_i][None], want, 27)
             for name, v in err.items():
                 assert v <= 1e-4, (f, k, err)
+
+
+def test_elastic_configuration_sampled_parity():
+    """The elastic order-5 workload of bench.py --elastic (786,432 tets, three layers, 4
+    clusters with the lambda search, 2 Hz Ricker source): one macro step (8 finest steps),
+    sample elements per cluster against the oracle on their 9-hop balls."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    hops = 9
+    mesh, mat, src, recs = bench.make_elastic_workload(**bench.ELASTIC_FULL)
+    K = mesh["tet"].shape[0]
+    assert K == 786432
+    nc, order = bench.ELASTIC_CLUSTERS, bench.ELASTIC_ORDER
+    g = binding.Solver(order, 0, device=0)
+    g.set_mesh(mesh["xyz"], mesh["tet"], mesh["face_bc"])
+    g.set_material(mat["rho"], mat["vp"], mat["vs"])
+    g.add_point_source(src["x"], src["m6"], src["f0"], src["t0"], src["m0"])
+    for r in recs:
+        g.add_receiver(r, 0.01)
+    g.use_torch_memory(nc)
+    cl_g, lam_g, _ = g.setup_clusters(nc, bench.CFL)
+    om = Mesh(mesh["xyz"], mesh["tet"], mesh["face_bc"])
+    dt = olts.cfl_time_steps(om.dins, mat["vp"], order, bench.CFL)
+    lam, cl, _ = olts.search_lambda(dt, om.nbr, nc)
+    assert lam == lam_g and np.array_equal(cl, cl_g)
+    delta = lam * dt.min()
+    rng = np.random.default_rng(29)
+    samples = [int(rng.choice(np.nonzero(cl == l)[0])) for l in range(nc) if np.any(cl == l)]
+    balls = [_ball(om.nbr, k, hops) for k in samples]
+    union = np.unique(np.concatenate(balls))
+    init = synth.random_dofs(len(union), 9, 35, seed=31)
+    g.set_dofs_subset(union, init)
+    row_of = {int(e): i for i, e in enumerate(union)}
+    src_elem = om.locate(src["x"])
+    g.advance_steps(2 ** (nc - 1))
+    got = g.get_dofs_subset(np.array(samples))
+    for s_i, (k, ball) in enumerate(zip(samples, balls)):
+        tet = mesh["tet"][ball]
+        uv, inv = np.unique(tet, return_inverse=True)
+        bc = mesh["face_bc"][ball].copy()
+        inside = np.isin(om.nbr[ball], ball)
+        bc[(om.nbr[ball] >= 0) & ~inside] = 1
+        sm = Mesh(mesh["xyz"][uv], inv.reshape(tet.shape), bc)
+        o = Oracle(order, 0, sm, mat["rho"][ball], mat["vp"][ball], mat["vs"][ball])
+        o.setup_clusters(nc, bench.CFL, lam=lam, clusters=cl[ball])
+        o.delta = delta
+        o.Q = init[[row_of[int(e)] for e in ball]].copy()
+        if src_elem in set(ball.tolist()):
+            o.add_point_source(src["x"], src["m6"], src["f0"], src["t0"], src["m0"])
+        o.run_lts(2 ** (nc - 1))
+        want = o.Q[np.searchsorted(ball, k)][None]
+        err = rel_l2_groups(got[s_i][None], want, 9)
+        for name, v in err.items():
+            assert v <= 1e-4, (k, int(cl[k]), err)
+
+
+def test_adjoint_configuration_gradient_against_central_differences():
+    """The adjoint workload (201,600 tets, elastic order 4, 3 LTS clusters, 2,000 finest
+    steps, 32 receivers, checkpoints every 100 finest steps): the gradient w.r.t. mu of the
+    two largest-gradient elements against central differences of the GPU misfit."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    from paper_2202_10313_gb300 import adjoint
+    mesh, (rho, lam, mu), blob, rec, src = adjoint._config5(40, 40, 21, 4, 3, 32)
+    assert mesh["tet"].shape[0] == 201600
+    steps, every = 2000, 25
+
+    def solver(r, l, m, fixed=None):
+        s = binding.Solver(4, 0, device=0)
+        s.set_mesh(mesh["xyz"], mesh["tet"], mesh["face_bc"])
+        s.set_material(r, np.sqrt((l + 2 * m) / r), np.sqrt(m / r))
+        s.add_point_source(*src)
+        for x in rec:
+            s.add_receiver(x, 0.01)
+        if fixed is None:
+            cl, lc, _ = s.setup_clusters(3, 0.5)
+            return s, (cl, lc, s.info()["finest_dt"])
+        s.force_clusters(fixed[0], 3, 0.5, fixed[1])
+        s.set_finest_dt(fixed[2])
+        return s, fixed
+
+    base, fixed = solver(rho, lam, mu)
+    pert, _ = solver(rho * (1 + blob), lam * (1 + blob), mu * (1 + blob), fixed)
+    _, data = pert.misfit(steps, np.zeros((steps // 4 + 1, len(rec), 3)), every=every)
+    pert.close()
+    J, grad, _ = base.misfit_gradient(steps, data, every=every)
+    assert J > 0
+    for k in np.argsort(-np.abs(grad[:, 2]))[:2]:
+        vals = []
+        for sgn in (1, -1):
+            m2 = mu.copy()
+            m2[k] *= 1 + sgn * 1e-3
+            s, _ = solver(rho, lam, m2, fixed)
+            vals.append(s.misfit(steps, data, every=every)[0])
+            s.close()
+        fd = (vals[0] - vals[1]) / (2e-3 * mu[k])
+        assert abs(fd - grad[k, 2]) <= 5e-3 * abs(fd), (int(k), fd, grad[k, 2])
