@@ -840,6 +840,49 @@ struct DevBuf {
   }
 };
 
+// Transposed copies of the operator tables for the adjoint kernels (their loops run over the
+// other index of K_c, F~_i, F^_i and F-_{j,h} than the forward kernels' do).
+struct AdjTables {
+  DevBuf buf;
+  const float *KT = nullptr, *FtT = nullptr, *FhT = nullptr, *FbT = nullptr;
+};
+
+void make_adj_tables(const lts_solver* h, AdjTables& T) {
+  const int B = h->L.B, F = h->L.F;
+  std::vector<float> K((size_t)3 * B * B), Ft((size_t)4 * B * F), Fh((size_t)4 * F * B), Fb((size_t)12 * B * F);
+  auto down = [&](std::vector<float>& v, const float* src) {
+    ck(cudaMemcpy(v.data(), src, sizeof(float) * v.size(), cudaMemcpyDeviceToHost), "download operators");
+  };
+  down(K, h->dops.K);
+  down(Ft, h->dops.Ft);
+  down(Fh, h->dops.Fh);
+  down(Fb, h->dops.Fb);
+  std::vector<float> all(K.size() + Ft.size() + Fh.size() + Fb.size());
+  float* kt = all.data();
+  float* ftt = kt + K.size();
+  float* fht = ftt + Ft.size();
+  float* fbt = fht + Fh.size();
+  for (int c = 0; c < 3; ++c)
+    for (int i = 0; i < B; ++i)
+      for (int j = 0; j < B; ++j) kt[(c * B + j) * B + i] = K[(c * B + i) * B + j];
+  for (int i = 0; i < 4; ++i)
+    for (int b = 0; b < B; ++b)
+      for (int f = 0; f < F; ++f) {
+        ftt[(i * F + f) * B + b] = Ft[(i * B + b) * F + f];
+        fht[(i * B + b) * F + f] = Fh[(i * F + f) * B + b];
+      }
+  for (int jh = 0; jh < 12; ++jh)
+    for (int b = 0; b < B; ++b)
+      for (int f = 0; f < F; ++f) fbt[(jh * F + f) * B + b] = Fb[(jh * B + b) * F + f];
+  T.buf.alloc(sizeof(float) * all.size());
+  ck(cudaMemcpy(T.buf.p, all.data(), sizeof(float) * all.size(), cudaMemcpyHostToDevice), "upload operators");
+  const float* base = T.buf.get<float>();
+  T.KT = base;
+  T.FtT = base + (ftt - kt);
+  T.FhT = base + (fht - kt);
+  T.FbT = base + (fbt - kt);
+}
+
 void contract_gradient(const lts_solver* h, const std::vector<double>& W, double* grad) {
   const int64_t K = h->mesh.K;
   {
@@ -891,7 +934,7 @@ void contract_gradient(const lts_solver* h, const std::vector<double>& W, double
 // reverse sweep (k_adj_pred / k_adj_nbr, phases in reverse order).
 void adjoint_lts(lts_solver* h, int64_t n_macro, int64_t every, const double* data, double* misfit, double* grad,
                  double* synth_out, double* dq0, cudaStream_t stream, const DevBuf& d_amat, const DevBuf& d_fwd,
-                 const DevBuf& d_back, const DevBuf& d_relem, const DevBuf& d_rphi, int nrec) {
+                 const DevBuf& d_back, const DevBuf& d_relem, const DevBuf& d_rphi, int nrec, const AdjTables& tabs) {
   const Launchers& X = h->L;
   const int64_t K = h->mesh.K;
   const int B = X.B, NB9 = 9 * B;
@@ -963,6 +1006,10 @@ void adjoint_lts(lts_solver* h, int64_t n_macro, int64_t every, const double* da
   aa.back = d_back.get<int>();
   aa.meta = h->dst.meta;
   aa.W = d_w.get<double>();
+  aa.KT = tabs.KT;
+  aa.FtT = tabs.FtT;
+  aa.FhT = tabs.FhT;
+  aa.FbT = tabs.FbT;
   aa.qs = qs;
   aa.bufs = bs;
   MacroPlan mp;
@@ -1874,9 +1921,11 @@ int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* 
     up(d_back.p, back.data(), sizeof(int) * back.size());
     up(d_relem.p, relem.data(), sizeof(int) * nrec);
     up(d_rphi.p, rphi.data(), sizeof(float) * rphi.size());
+    AdjTables tabs;
+    make_adj_tables(h, tabs);
     if (h->nc > 1) {
       adjoint_lts(h, n_steps / period, every, data, misfit, grad, synth_out, dq0, stream, d_amat, d_fwd, d_back,
-                  d_relem, d_rphi, nrec);
+                  d_relem, d_rphi, nrec, tabs);
       return;
     }
     d_syn.alloc(sizeof(float) * (n_steps + 1) * nrec * 3);
@@ -1939,6 +1988,10 @@ int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* 
     aa.fwd = d_fwd.get<int>();
     aa.back = d_back.get<int>();
     aa.W = d_w.get<double>();
+    aa.KT = tabs.KT;
+    aa.FtT = tabs.FtT;
+    aa.FhT = tabs.FhT;
+    aa.FbT = tabs.FbT;
     aa.qs = qs;
     {
       double fac = 1.0;

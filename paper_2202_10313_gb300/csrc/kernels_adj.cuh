@@ -24,6 +24,31 @@ constexpr int AM_LOC = 243;      // A-_i, i = 0..3
 constexpr int AM_NBR = 567;      // A+_i, i = 0..3
 constexpr int AM_SIZE = 891;     // floats per element (also the size of the correlations W)
 
+// Threads per element CTA: one warp up to order 4, two at order 5 (every phase needs at
+// least one thread per mode column; the 81 correlation entries are strided over the CTA).
+template <int O>
+struct AdjNT {
+  static constexpr int value = (nbasis(O) <= 32) ? 32 : 64;
+  static constexpr int WPT = (81 + value - 1) / value;   // correlation entries per thread
+};
+
+// Transposed copies of the operator tables, so that every loop over a table reads it with
+// consecutive threads on consecutive entries:
+//   KT[c][j][i] = K[c][i][j],  FtT[i][f][b] = F~_i[b][f],  FhT[i][b][f] = F^_i[f][b],
+//   FbT[jh][f][b] = F-_{jh}[b][f].
+// v[r] = sum_{j < N} src[r * LD + j] * tab[j * ts + t] for the 9 rows r: each table entry is
+// loaded once and the rows accumulate in registers.
+template <int N, int LD>
+__device__ __forceinline__ void rows9(const float* src, const float* __restrict__ tab, int ts, int t, float v[9]) {
+#pragma unroll
+  for (int r = 0; r < 9; ++r) v[r] = 0.f;
+  for (int j = 0; j < N; ++j) {
+    const float w = __ldg(tab + j * ts + t);
+#pragma unroll
+    for (int r = 0; r < 9; ++r) v[r] = fmaf(src[r * LD + j], w, v[r]);
+  }
+}
+
 struct AdjArgs {
   const float* Q;        // Q^n, element stride qs, rows of B
   const float* tbuf;     // [K][9B] T of step n
@@ -32,14 +57,15 @@ struct AdjArgs {
   const float* amat;     // [K][AM_SIZE]
   const int* fwd;        // [K][4][2]: neighbour (internal index, -1 none), j*3+h of F- for this face
   const int* back;       // [K][4][2]: the neighbour's face i' pointing here, i*3+h' of its F-
-  double* W;             // [K][AM_SIZE]
+  double* W;             // [K][AM_SIZE]: each step's sums are formed in FP32 and added here in FP64
+  const float *KT, *FtT, *FhT, *FbT;   // transposed operator tables (see AdjTables)
   long long qs;
   float cd[6];           // dt^(d+1)/(d+1)!
 };
 
 // T of every element from Q^n (the time kernel with the explicit star matrices).
 template <int O>
-__global__ void __launch_bounds__(64) k_adj_T(DevOps ops, AdjArgs a, float* tbuf) {
+__global__ void __launch_bounds__(AdjNT<O>::value) k_adj_T(DevOps ops, AdjArgs a, float* tbuf) {
   constexpr int B = nbasis(O), NB9 = 9 * B;
   __shared__ float sS[243];
   __shared__ float sX[2][NB9];
@@ -64,7 +90,7 @@ __global__ void __launch_bounds__(64) k_adj_T(DevOps ops, AdjArgs a, float* tbuf
       for (int kk = 0; kk < B; ++kk) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const float kc = ops.K[(c * B + t) * B + kk];
+          const float kc = a.KT[(c * B + kk) * B + t];
 #pragma unroll
           for (int s = 0; s < 9; ++s) Y[c][s] = fmaf(sX[cur][s * B + kk], kc, Y[c][s]);
         }
@@ -93,7 +119,8 @@ __global__ void __launch_bounds__(64) k_adj_T(DevOps ops, AdjArgs a, float* tbuf
 
 // One reverse step for every element (one CTA each): lambda^n and the correlations.
 template <int O>
-__global__ void __launch_bounds__(128) k_adj_step(DevOps ops, AdjArgs a) {
+__global__ void __launch_bounds__(AdjNT<O>::value) k_adj_step(DevOps ops, AdjArgs a) {
+  constexpr int WPT = AdjNT<O>::WPT;
   constexpr int B = nbasis(O), F = nface(O), NB9 = 9 * B;
   __shared__ float sM[AM_SIZE];
   __shared__ float sAb[4][81];
@@ -130,7 +157,7 @@ __global__ void __launch_bounds__(128) k_adj_step(DevOps ops, AdjArgs a) {
       for (int kk = 0; kk < B; ++kk)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const float kc = ops.K[(c * B + t) * B + kk];
+          const float kc = a.KT[(c * B + kk) * B + t];
 #pragma unroll
           for (int s = 0; s < 9; ++s) Y[c][s] = fmaf(sD[d][s * B + kk], kc, Y[c][s]);
         }
@@ -164,7 +191,7 @@ __global__ void __launch_bounds__(128) k_adj_step(DevOps ops, AdjArgs a) {
     for (int kk = 0; kk < B; ++kk)
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const float kc = ops.K[(c * B + t) * B + kk];
+        const float kc = a.KT[(c * B + kk) * B + t];
 #pragma unroll
         for (int r = 0; r < 9; ++r) mu[r] = fmaf(-sP[c][r * B + kk], kc, mu[r]);
       }
@@ -181,17 +208,16 @@ __global__ void __launch_bounds__(128) k_adj_step(DevOps ops, AdjArgs a) {
         sP[0][r * B + t] = v;
       }
     __syncthreads();
-    if (t < F)
+    if (t < F) {
+      float v[9];
+      rows9<B, B>(sP[0], a.FhT + i * B * F, F, t, v);
 #pragma unroll
-      for (int r = 0; r < 9; ++r) {
-        float v = 0.f;
-        for (int kk = 0; kk < B; ++kk) v = fmaf(sP[0][r * B + kk], ops.Fh[(i * F + t) * B + kk], v);
-        sU[r * F + t] = v;
-      }
+      for (int r = 0; r < 9; ++r) sU[r * F + t] = v[r];
+    }
     __syncthreads();
     if (t < B)
       for (int f = 0; f < F; ++f) {
-        const float w = ops.Ft[(i * B + t) * F + f];
+        const float w = a.FtT[(i * F + f) * B + t];
 #pragma unroll
         for (int r = 0; r < 9; ++r) mu[r] = fmaf(sU[r * F + f], w, mu[r]);
       }
@@ -213,17 +239,16 @@ __global__ void __launch_bounds__(128) k_adj_step(DevOps ops, AdjArgs a) {
       }
     __syncthreads();
     const int ip = sBk[2 * i], jh = sBk[2 * i + 1];
-    if (t < F)
+    if (t < F) {
+      float v[9];
+      rows9<B, B>(sP[0], a.FhT + ip * B * F, F, t, v);
 #pragma unroll
-      for (int r = 0; r < 9; ++r) {
-        float v = 0.f;
-        for (int kk = 0; kk < B; ++kk) v = fmaf(sP[0][r * B + kk], ops.Fh[(ip * F + t) * B + kk], v);
-        sU[r * F + t] = v;
-      }
+      for (int r = 0; r < 9; ++r) sU[r * F + t] = v[r];
+    }
     __syncthreads();
     if (t < B)
       for (int f = 0; f < F; ++f) {
-        const float w = ops.Fb[(jh * B + t) * F + f];
+        const float w = a.FbT[(jh * F + f) * B + t];
 #pragma unroll
         for (int r = 0; r < 9; ++r) mu[r] = fmaf(sU[r * F + f], w, mu[r]);
       }
@@ -264,58 +289,65 @@ __global__ void __launch_bounds__(128) k_adj_step(DevOps ops, AdjArgs a) {
   if (t < B)
 #pragma unroll
     for (int r = 0; r < 9; ++r) a.lam_out[(size_t)k * NB9 + r * B + t] = sL[r * B + t] + sG[0][r * B + t];
-  // ---- correlations (thread t < 81 owns entry (rr, ss))
-  const int rr = t / 9, ss = t % 9;
+  // ---- correlations (entry e = (e / 9, e % 9), strided over the CTA)
   double* Wk = a.W + (size_t)k * AM_SIZE;
   for (int c = 0; c < 3; ++c) {
-    double acc = 0.0;
-    if (t < B)
+    float acc[WPT];
 #pragma unroll
-      for (int s = 0; s < 9; ++s) {
-        float v = 0.f;
-        for (int kk = 0; kk < B; ++kk) v = fmaf(sT[s * B + kk], ops.K[(c * B + kk) * B + t], v);
-        sP[0][s * B + t] = v;
-      }
+    for (int j = 0; j < WPT; ++j) acc[j] = 0.f;
+    if (t < B) {
+      float v[9];
+      rows9<B, B>(sT, ops.K + c * B * B, B, t, v);
+#pragma unroll
+      for (int s = 0; s < 9; ++s) sP[0][s * B + t] = v[s];
+    }
     __syncthreads();
-    if (t < 81)
-      for (int b = 0; b < B; ++b) acc -= (double)sL[rr * B + b] * (double)sP[0][ss * B + b];
+#pragma unroll
+    for (int j = 0; j < WPT; ++j) {
+      const int e = t + j * nt;
+      if (e < 81)
+        for (int b = 0; b < B; ++b) acc[j] -= sL[(e / 9) * B + b] * sP[0][(e % 9) * B + b];
+    }
     __syncthreads();
     for (int d = 0; d < O - 1; ++d) {
-      if (t < B)
+      if (t < B) {
+        float v[9];
+        rows9<B, B>(sD[d], a.KT + c * B * B, B, t, v);
 #pragma unroll
-        for (int s = 0; s < 9; ++s) {
-          float v = 0.f;
-          for (int kk = 0; kk < B; ++kk) v = fmaf(sD[d][s * B + kk], ops.K[(c * B + t) * B + kk], v);
-          sP[0][s * B + t] = v;
-        }
+        for (int s = 0; s < 9; ++s) sP[0][s * B + t] = v[s];
+      }
       __syncthreads();
-      if (t < 81)
-        for (int b = 0; b < B; ++b) acc += (double)sG[d + 1][rr * B + b] * (double)sP[0][ss * B + b];
+#pragma unroll
+      for (int j = 0; j < WPT; ++j) {
+        const int e = t + j * nt;
+        if (e < 81)
+          for (int b = 0; b < B; ++b) acc[j] += sG[d + 1][(e / 9) * B + b] * sP[0][(e % 9) * B + b];
+      }
       __syncthreads();
     }
-    if (t < 81) Wk[AM_STAR + c * 81 + t] += acc;
+#pragma unroll
+    for (int j = 0; j < WPT; ++j)
+      if (t + j * nt < 81) Wk[AM_STAR + c * 81 + t + j * nt] += (double)acc[j];
   }
   for (int i = 0; i < 4; ++i) {
-    if (t < F)
+    if (t < F) {
+      float v[9];
+      rows9<B, B>(sT, ops.Ft + i * B * F, F, t, v);
 #pragma unroll
-      for (int s = 0; s < 9; ++s) {
-        float v = 0.f;
-        for (int kk = 0; kk < B; ++kk) v = fmaf(sT[s * B + kk], ops.Ft[(i * B + kk) * F + t], v);
-        sU[s * F + t] = v;
-      }
+      for (int s = 0; s < 9; ++s) sU[s * F + t] = v[s];
+    }
     __syncthreads();
-    if (t < B)
+    if (t < B) {
+      float v[9];
+      rows9<F, F>(sU, ops.Fh + i * F * B, B, t, v);
 #pragma unroll
-      for (int s = 0; s < 9; ++s) {
-        float v = 0.f;
-        for (int f = 0; f < F; ++f) v = fmaf(sU[s * F + f], ops.Fh[(i * F + f) * B + t], v);
-        sP[0][s * B + t] = v;
-      }
+      for (int s = 0; s < 9; ++s) sP[0][s * B + t] = v[s];
+    }
     __syncthreads();
-    if (t < 81) {
-      double acc = 0.0;
-      for (int b = 0; b < B; ++b) acc += (double)sL[rr * B + b] * (double)sP[0][ss * B + b];
-      Wk[AM_LOC + i * 81 + t] += acc;
+    for (int e = t; e < 81; e += nt) {
+      float acc = 0.f;
+      for (int b = 0; b < B; ++b) acc += sL[(e / 9) * B + b] * sP[0][(e % 9) * B + b];
+      Wk[AM_LOC + i * 81 + e] += (double)acc;
     }
     __syncthreads();
   }
@@ -325,26 +357,24 @@ __global__ void __launch_bounds__(128) k_adj_step(DevOps ops, AdjArgs a) {
     const int jh = sF[2 * i + 1];
     for (int q = t; q < NB9; q += nt) sP[1][q] = a.tbuf[(size_t)kn * NB9 + q];
     __syncthreads();
-    if (t < F)
+    if (t < F) {
+      float v[9];
+      rows9<B, B>(sP[1], ops.Fb + jh * B * F, F, t, v);
 #pragma unroll
-      for (int s = 0; s < 9; ++s) {
-        float v = 0.f;
-        for (int kk = 0; kk < B; ++kk) v = fmaf(sP[1][s * B + kk], ops.Fb[(jh * B + kk) * F + t], v);
-        sU[s * F + t] = v;
-      }
+      for (int s = 0; s < 9; ++s) sU[s * F + t] = v[s];
+    }
     __syncthreads();
-    if (t < B)
+    if (t < B) {
+      float v[9];
+      rows9<F, F>(sU, ops.Fh + i * F * B, B, t, v);
 #pragma unroll
-      for (int s = 0; s < 9; ++s) {
-        float v = 0.f;
-        for (int f = 0; f < F; ++f) v = fmaf(sU[s * F + f], ops.Fh[(i * F + f) * B + t], v);
-        sP[0][s * B + t] = v;
-      }
+      for (int s = 0; s < 9; ++s) sP[0][s * B + t] = v[s];
+    }
     __syncthreads();
-    if (t < 81) {
-      double acc = 0.0;
-      for (int b = 0; b < B; ++b) acc += (double)sL[rr * B + b] * (double)sP[0][ss * B + b];
-      Wk[AM_NBR + i * 81 + t] += acc;
+    for (int e = t; e < 81; e += nt) {
+      float acc = 0.f;
+      for (int b = 0; b < B; ++b) acc += sL[(e / 9) * B + b] * sP[0][(e % 9) * B + b];
+      Wk[AM_NBR + i * 81 + e] += (double)acc;
     }
     __syncthreads();
   }
@@ -393,20 +423,60 @@ struct AdjLtsArgs {
   const int* fwd;
   const int* back;
   const int* meta;
-  double* W;
+  double* W;                          // [K][AM_SIZE], per-pass sums in FP32 added in FP64
+  const float *KT, *FtT, *FhT, *FbT;  // transposed operator tables (see AdjTables)
   long long qs, bufs;
   int end;                            // active elements [0, end)
 };
 
+// y += S x (TR = false) or y += S^T x (TR = true) for an elastic star matrix S (row-major
+// [out][in]). It couples the six stresses only to the three velocities and the velocities
+// only to the stresses, so its other 45 entries are zero and skipped.
+template <bool TR>
+__device__ __forceinline__ void star_acc(const float* S, const float x[9], float y[9]) {
+#pragma unroll
+  for (int r = 0; r < 6; ++r)
+#pragma unroll
+    for (int s = 6; s < 9; ++s) y[r] = fmaf(TR ? S[s * 9 + r] : S[r * 9 + s], x[s], y[r]);
+#pragma unroll
+  for (int r = 6; r < 9; ++r)
+#pragma unroll
+    for (int s = 0; s < 6; ++s) y[r] = fmaf(TR ? S[s * 9 + r] : S[r * 9 + s], x[s], y[r]);
+}
+
+// acc[i][j] += sum_{j' < n} X[(r0 + i) * LD + j'] * Y[(s0 + j) * LD + j'] for a 3 x 3 tile.
+template <int LD>
+__device__ __forceinline__ void tile33(const float* X, const float* Y, int r0, int s0, int n, float acc[3][3]) {
+  for (int j = 0; j < n; ++j) {
+    float x[3], y[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      x[i] = X[(r0 + i) * LD + j];
+      y[i] = Y[(s0 + i) * LD + j];
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) acc[i][q] = fmaf(x[i], y[q], acc[i][q]);
+  }
+}
+
 // Reverse of a predict pass, one CTA per active element.
+//
+// Degree structure used throughout (exact): K_c[i][j] vanishes unless deg i < deg j, so
+// D_d is a polynomial of degree O-1-d and lives on the first nbasis(O-d) modes; only those
+// modes of its adjoint G_d matter. With Z_c = G_{d+1} K_c the reverse time kernel is
+// G_d = c_d mu + c'_d mu_half + sum_c S_c^T Z_c and the star correlation of level d is
+// Z_c D_d^T; with V_c = lambda K_c^T the volume term is mu = -sum_c S_c^T V_c and its
+// correlation -V_c T^T.
 template <int O>
-__global__ void __launch_bounds__(128) k_adj_pred(DevOps ops, AdjLtsArgs a, PhaseArgs ph) {
+__global__ void __launch_bounds__(AdjNT<O>::value) k_adj_pred(DevOps ops, AdjLtsArgs a, PhaseArgs ph) {
   constexpr int B = nbasis(O), F = nface(O), NB9 = 9 * B;
+  constexpr int NSCR = (3 * NB9 > 108 * F) ? 3 * NB9 : 108 * F;
   __shared__ float sM[AM_SIZE];
   __shared__ float sL[NB9], sT[NB9];
-  __shared__ float sD[O][NB9], sG[O][NB9];
-  __shared__ float sP[3][NB9];
-  __shared__ float sU[9 * F];
+  __shared__ float sD[O][NB9], sG[2][NB9];
+  __shared__ float sScr[NSCR];   // V_c, then the face products, then Z_c
   const int k = blockIdx.x, t = threadIdx.x, nt = blockDim.x;
   const int meta = a.meta[k];
   const int cl = meta & 0xff;
@@ -419,89 +489,132 @@ __global__ void __launch_bounds__(128) k_adj_pred(DevOps ops, AdjLtsArgs a, Phas
   }
   __syncthreads();
   const float* S = sM + AM_STAR;
+  // ---- forward time kernel: D_{d+1} = sum_c S_c D_d K_c^T on the support of D_{d+1}
   for (int d = 0; d < O - 1; ++d) {
+    const int nin = nbasis(O - d), nout = nbasis(O - 1 - d);
     if (t < B) {
       float Y[3][9];
 #pragma unroll
       for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int s = 0; s < 9; ++s) Y[c][s] = 0.f;
-      for (int kk = 0; kk < B; ++kk)
+      if (t < nout)
+        for (int kk = 0; kk < nin; ++kk)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const float kc = ops.K[(c * B + t) * B + kk];
+          for (int c = 0; c < 3; ++c) {
+            const float kc = __ldg(a.KT + (c * B + kk) * B + t);
 #pragma unroll
-          for (int s = 0; s < 9; ++s) Y[c][s] = fmaf(sD[d][s * B + kk], kc, Y[c][s]);
-        }
+            for (int s = 0; s < 9; ++s) Y[c][s] = fmaf(sD[d][s * B + kk], kc, Y[c][s]);
+          }
+      float v[9];
 #pragma unroll
-      for (int r = 0; r < 9; ++r) {
-        float v = 0.f;
+      for (int r = 0; r < 9; ++r) v[r] = 0.f;
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
+      for (int c = 0; c < 3; ++c) star_acc<false>(S + c * 81, Y[c], v);
 #pragma unroll
-          for (int s = 0; s < 9; ++s) v = fmaf(S[c * 81 + r * 9 + s], Y[c][s], v);
-        sD[d + 1][r * B + t] = v;
-      }
+      for (int r = 0; r < 9; ++r) sD[d + 1][r * B + t] = v[r];
     }
     __syncthreads();
   }
-  if (t < B)
+  float mu[9], muh[9];
+#pragma unroll
+  for (int r = 0; r < 9; ++r) mu[r] = muh[r] = 0.f;
+  float* sV = sScr;
+  if (t < B) {
 #pragma unroll
     for (int r = 0; r < 9; ++r) {
       float v = 0.f;
       for (int d = 0; d < O; ++d) v = fmaf(ph.coef[cl][d], sD[d][r * B + t], v);
       sT[r * B + t] = v;
     }
-  // mu: volume and local surface terms of this pass, then the buffers it wrote
-  float mu[9], muh[9];
+    // V_c = lambda K_c^T and the volume term
+    float V[3][9];
 #pragma unroll
-  for (int r = 0; r < 9; ++r) mu[r] = muh[r] = 0.f;
-  if (t < B)
     for (int c = 0; c < 3; ++c)
 #pragma unroll
-      for (int r = 0; r < 9; ++r) {
-        float v = 0.f;
-#pragma unroll
-        for (int s = 0; s < 9; ++s) v = fmaf(S[c * 81 + s * 9 + r], sL[s * B + t], v);
-        sP[c][r * B + t] = v;
-      }
-  __syncthreads();
-  if (t < B)
-    for (int kk = 0; kk < B; ++kk)
+      for (int s = 0; s < 9; ++s) V[c][s] = 0.f;
+    for (int b = 0; b < B; ++b)
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const float kc = ops.K[(c * B + t) * B + kk];
+        const float kc = __ldg(a.KT + (c * B + b) * B + t);
 #pragma unroll
-        for (int r = 0; r < 9; ++r) mu[r] = fmaf(-sP[c][r * B + kk], kc, mu[r]);
+        for (int s = 0; s < 9; ++s) V[c][s] = fmaf(sL[s * B + b], kc, V[c][s]);
       }
-  __syncthreads();
-  for (int i = 0; i < 4; ++i) {
-    const float* Am = sM + AM_LOC + i * 81;
-    if (t < B)
+    float w[9];
 #pragma unroll
-      for (int r = 0; r < 9; ++r) {
-        float v = 0.f;
+    for (int r = 0; r < 9; ++r) w[r] = 0.f;
 #pragma unroll
-        for (int s = 0; s < 9; ++s) v = fmaf(Am[s * 9 + r], sL[s * B + t], v);
-        sP[0][r * B + t] = v;
-      }
-    __syncthreads();
-    if (t < F)
+    for (int c = 0; c < 3; ++c) {
+      star_acc<true>(S + c * 81, V[c], w);
 #pragma unroll
-      for (int r = 0; r < 9; ++r) {
-        float v = 0.f;
-        for (int kk = 0; kk < B; ++kk) v = fmaf(sP[0][r * B + kk], ops.Fh[(i * F + t) * B + kk], v);
-        sU[r * F + t] = v;
-      }
-    __syncthreads();
-    if (t < B)
-      for (int f = 0; f < F; ++f) {
-        const float w = ops.Ft[(i * B + t) * F + f];
+      for (int s = 0; s < 9; ++s) sV[c * NB9 + s * B + t] = V[c][s];
+    }
 #pragma unroll
-        for (int r = 0; r < 9; ++r) mu[r] = fmaf(sU[r * F + f], w, mu[r]);
-      }
-    __syncthreads();
+    for (int r = 0; r < 9; ++r) mu[r] = -w[r];
   }
+  __syncthreads();
+  // star correlations, one 3 x 3 tile (c, row block, column block) per thread t < 27
+  const int tc = t / 9, trb = (t / 3) % 3, tsb = t % 3;
+  float wst[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) wst[i][q] = 0.f;
+  if (t < 27) {
+    tile33<B>(sV + tc * NB9, sT, 3 * trb, 3 * tsb, B, wst);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) wst[i][q] = -wst[i][q];
+  }
+  __syncthreads();
+  // local surface: LF_i = lambda F^_i^T, TF_i = T F~_i, U_i = A-_i^T LF_i, per (face, f)
+  float* sLF = sScr;
+  float* sTF = sScr + 36 * F;
+  float* sU = sScr + 72 * F;
+  for (int p = t; p < 4 * F; p += nt) {
+    const int i = p / F, f = p % F;
+    float lf[9], tf[9], u[9];
+    rows9<B, B>(sL, a.FhT + i * B * F, F, f, lf);
+    rows9<B, B>(sT, ops.Ft + i * B * F, F, f, tf);
+    const float* Am = sM + AM_LOC + i * 81;
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+      float v = 0.f;
+#pragma unroll
+      for (int s = 0; s < 9; ++s) v = fmaf(Am[s * 9 + r], lf[s], v);
+      u[r] = v;
+    }
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+      sLF[(i * 9 + r) * F + f] = lf[r];
+      sTF[(i * 9 + r) * F + f] = tf[r];
+      sU[(i * 9 + r) * F + f] = u[r];
+    }
+  }
+  __syncthreads();
+  if (t < B)
+    for (int i = 0; i < 4; ++i)
+      for (int f = 0; f < F; ++f) {
+        const float w = __ldg(a.FtT + (i * F + f) * B + t);
+#pragma unroll
+        for (int r = 0; r < 9; ++r) mu[r] = fmaf(sU[(i * 9 + r) * F + f], w, mu[r]);
+      }
+  double* Wk = a.W + (size_t)k * AM_SIZE;
+  for (int p = t; p < 36; p += nt) {
+    const int i = p / 9, rb = (p / 3) % 3, sb = p % 3;
+    float acc[3][3];
+#pragma unroll
+    for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) acc[ii][q] = 0.f;
+    tile33<F>(sLF + i * 9 * F, sTF + i * 9 * F, 3 * rb, 3 * sb, F, acc);
+#pragma unroll
+    for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) Wk[AM_LOC + i * 81 + (3 * rb + ii) * 9 + 3 * sb + q] += (double)acc[ii][q];
+  }
+  // the buffers this pass wrote
   if (t < B) {
     const size_t o = (size_t)k * NB9 + t;
 #pragma unroll
@@ -518,94 +631,53 @@ __global__ void __launch_bounds__(128) k_adj_pred(DevOps ops, AdjLtsArgs a, Phas
       }
     }
 #pragma unroll
-    for (int r = 0; r < 9; ++r) sG[O - 1][r * B + t] = ph.coef[cl][O - 1] * mu[r] + ph.hcoef[cl][O - 1] * muh[r];
+    for (int r = 0; r < 9; ++r)
+      sG[(O - 1) & 1][r * B + t] = ph.coef[cl][O - 1] * mu[r] + ph.hcoef[cl][O - 1] * muh[r];
   }
   __syncthreads();
+  // ---- reverse time kernel
+  float* sZ = sScr;
   for (int d = O - 2; d >= 0; --d) {
-    if (t < B)
+    const int nk = nbasis(O - 1 - d), nout = nbasis(O - d);
+    const float* Gn = sG[(d + 1) & 1];
+    if (t < B) {
+      float Z[3][9];
+#pragma unroll
       for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int r = 0; r < 9; ++r) {
-          float v = 0.f;
+        for (int r = 0; r < 9; ++r) Z[c][r] = 0.f;
+      if (t < nout)
+        for (int kk = 0; kk < nk; ++kk)
 #pragma unroll
-          for (int s = 0; s < 9; ++s) v = fmaf(S[c * 81 + s * 9 + r], sG[d + 1][s * B + t], v);
-          sP[c][r * B + t] = v;
-        }
-    __syncthreads();
-    if (t < B) {
+          for (int c = 0; c < 3; ++c) {
+            const float kc = __ldg(ops.K + (c * B + kk) * B + t);
+#pragma unroll
+            for (int r = 0; r < 9; ++r) Z[c][r] = fmaf(Gn[r * B + kk], kc, Z[c][r]);
+          }
       float g[9];
 #pragma unroll
       for (int r = 0; r < 9; ++r) g[r] = ph.coef[cl][d] * mu[r] + ph.hcoef[cl][d] * muh[r];
-      for (int kk = 0; kk < B; ++kk)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const float kc = ops.K[(c * B + kk) * B + t];
+      for (int c = 0; c < 3; ++c) {
+        star_acc<true>(S + c * 81, Z[c], g);
 #pragma unroll
-          for (int r = 0; r < 9; ++r) g[r] = fmaf(sP[c][r * B + kk], kc, g[r]);
-        }
+        for (int r = 0; r < 9; ++r) sZ[c * NB9 + r * B + t] = Z[c][r];
+      }
 #pragma unroll
-      for (int r = 0; r < 9; ++r) sG[d][r * B + t] = g[r];
+      for (int r = 0; r < 9; ++r) sG[d & 1][r * B + t] = g[r];
     }
+    __syncthreads();
+    if (t < 27) tile33<B>(sZ + tc * NB9, sD[d], 3 * trb, 3 * tsb, nout, wst);
     __syncthreads();
   }
   if (t < B)
 #pragma unroll
     for (int r = 0; r < 9; ++r) a.lq[(size_t)k * NB9 + r * B + t] = sL[r * B + t] + sG[0][r * B + t];
-  // correlations of the star matrices and of the local flux solvers
-  const int rr = t / 9, ss = t % 9;
-  double* Wk = a.W + (size_t)k * AM_SIZE;
-  for (int c = 0; c < 3; ++c) {
-    double acc = 0.0;
-    if (t < B)
+  if (t < 27)
 #pragma unroll
-      for (int s = 0; s < 9; ++s) {
-        float v = 0.f;
-        for (int kk = 0; kk < B; ++kk) v = fmaf(sT[s * B + kk], ops.K[(c * B + kk) * B + t], v);
-        sP[0][s * B + t] = v;
-      }
-    __syncthreads();
-    if (t < 81)
-      for (int b = 0; b < B; ++b) acc -= (double)sL[rr * B + b] * (double)sP[0][ss * B + b];
-    __syncthreads();
-    for (int d = 0; d < O - 1; ++d) {
-      if (t < B)
+    for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int s = 0; s < 9; ++s) {
-          float v = 0.f;
-          for (int kk = 0; kk < B; ++kk) v = fmaf(sD[d][s * B + kk], ops.K[(c * B + t) * B + kk], v);
-          sP[0][s * B + t] = v;
-        }
-      __syncthreads();
-      if (t < 81)
-        for (int b = 0; b < B; ++b) acc += (double)sG[d + 1][rr * B + b] * (double)sP[0][ss * B + b];
-      __syncthreads();
-    }
-    if (t < 81) Wk[AM_STAR + c * 81 + t] += acc;
-  }
-  for (int i = 0; i < 4; ++i) {
-    if (t < F)
-#pragma unroll
-      for (int s = 0; s < 9; ++s) {
-        float v = 0.f;
-        for (int kk = 0; kk < B; ++kk) v = fmaf(sT[s * B + kk], ops.Ft[(i * B + kk) * F + t], v);
-        sU[s * F + t] = v;
-      }
-    __syncthreads();
-    if (t < B)
-#pragma unroll
-      for (int s = 0; s < 9; ++s) {
-        float v = 0.f;
-        for (int f = 0; f < F; ++f) v = fmaf(sU[s * F + f], ops.Fh[(i * F + f) * B + t], v);
-        sP[0][s * B + t] = v;
-      }
-    __syncthreads();
-    if (t < 81) {
-      double acc = 0.0;
-      for (int b = 0; b < B; ++b) acc += (double)sL[rr * B + b] * (double)sP[0][ss * B + b];
-      Wk[AM_LOC + i * 81 + t] += acc;
-    }
-    __syncthreads();
-  }
+      for (int q = 0; q < 3; ++q) Wk[AM_STAR + tc * 81 + (3 * trb + i) * 9 + 3 * tsb + q] += (double)wst[i][q];
 }
 
 // Reverse of a neighbour pass, one CTA per buffer owner (every element): for each face
@@ -613,7 +685,7 @@ __global__ void __launch_bounds__(128) k_adj_pred(DevOps ops, AdjLtsArgs a, Phas
 // adjoint of the buffer it read, and the receiver's correlation with that buffer is
 // accumulated. Every (receiver, face) pair is visited by exactly one owner.
 template <int O>
-__global__ void __launch_bounds__(128) k_adj_nbr(DevOps ops, AdjLtsArgs a, PhaseArgs ph) {
+__global__ void __launch_bounds__(AdjNT<O>::value) k_adj_nbr(DevOps ops, AdjLtsArgs a, PhaseArgs ph) {
   constexpr int B = nbasis(O), F = nface(O), NB9 = 9 * B;
   __shared__ float sA[81];
   __shared__ float sLk[NB9], sX[NB9], sR[NB9];
@@ -652,20 +724,20 @@ __global__ void __launch_bounds__(128) k_adj_nbr(DevOps ops, AdjLtsArgs a, Phase
         sR[r * B + t] = v;
       }
     __syncthreads();
-    if (t < F)
+    if (t < F) {
+      float v[9];
+      rows9<B, B>(sR, a.FhT + ip * B * F, F, t, v);
 #pragma unroll
-      for (int r = 0; r < 9; ++r) {
-        float v = 0.f;
-        for (int kk = 0; kk < B; ++kk) v = fmaf(sR[r * B + kk], ops.Fh[(ip * F + t) * B + kk], v);
-        sU[r * F + t] = v;
-      }
+      for (int r = 0; r < 9; ++r) sU[r * F + t] = v[r];
+    }
     __syncthreads();
     if (t < B) {
       const size_t o = (size_t)kn * NB9 + t;
+      float yv[9];
+      rows9<F, F>(sU, a.FbT + jh * F * B, B, t, yv);
 #pragma unroll
       for (int r = 0; r < 9; ++r) {
-        float y = 0.f;
-        for (int f = 0; f < F; ++f) y = fmaf(sU[r * F + f], ops.Fb[(jh * B + t) * F + f], y);
+        const float y = yv[r];
         if (lo == lr - 1) {
           a.lb3[o + r * B] += y;
         } else if (lo == lr + 1) {
@@ -682,27 +754,24 @@ __global__ void __launch_bounds__(128) k_adj_nbr(DevOps ops, AdjLtsArgs a, Phase
     }
     __syncthreads();
     // correlation of the receiver's neighbour flux solver: lambda_Q_k (X F-_{jh} F^_ip)^T
-    if (t < F)
+    if (t < F) {
+      float v[9];
+      rows9<B, B>(sX, ops.Fb + jh * B * F, F, t, v);
 #pragma unroll
-      for (int s = 0; s < 9; ++s) {
-        float v = 0.f;
-        for (int kk = 0; kk < B; ++kk) v = fmaf(sX[s * B + kk], ops.Fb[(jh * B + kk) * F + t], v);
-        sU[s * F + t] = v;
-      }
+      for (int s = 0; s < 9; ++s) sU[s * F + t] = v[s];
+    }
     __syncthreads();
-    if (t < B)
+    if (t < B) {
+      float v[9];
+      rows9<F, F>(sU, ops.Fh + ip * F * B, B, t, v);
 #pragma unroll
-      for (int s = 0; s < 9; ++s) {
-        float v = 0.f;
-        for (int f = 0; f < F; ++f) v = fmaf(sU[s * F + f], ops.Fh[(ip * F + f) * B + t], v);
-        sR[s * B + t] = v;
-      }
+      for (int s = 0; s < 9; ++s) sR[s * B + t] = v[s];
+    }
     __syncthreads();
-    if (t < 81) {
-      const int rr = t / 9, ss = t % 9;
-      double acc = 0.0;
-      for (int b = 0; b < B; ++b) acc += (double)sLk[rr * B + b] * (double)sR[ss * B + b];
-      a.W[(size_t)k * AM_SIZE + AM_NBR + ip * 81 + t] += acc;
+    for (int e = t; e < 81; e += nt) {
+      float acc = 0.f;
+      for (int b = 0; b < B; ++b) acc += sLk[(e / 9) * B + b] * sR[(e % 9) * B + b];
+      a.W[(size_t)k * AM_SIZE + AM_NBR + ip * 81 + e] += (double)acc;
     }
     __syncthreads();
   }

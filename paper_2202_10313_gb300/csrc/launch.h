@@ -99,10 +99,10 @@ struct Impl {
     k_pack_faces<O, M><<<(nt + threads - 1) / threads, threads, 0, st>>>(o, s, p, se, sc, rc, n, msg);
   }
   static void adj_T(const DevOps& o, const AdjArgs& a, float* tbuf, int K, cudaStream_t st) {
-    k_adj_T<O><<<K, 64, 0, st>>>(o, a, tbuf);
+    k_adj_T<O><<<K, AdjNT<O>::value, 0, st>>>(o, a, tbuf);
   }
   static void adj_step(const DevOps& o, const AdjArgs& a, int K, cudaStream_t st) {
-    k_adj_step<O><<<K, 128, 0, st>>>(o, a);
+    k_adj_step<O><<<K, AdjNT<O>::value, 0, st>>>(o, a);
   }
   static void adj_sample(const float* Q, long long qs, const int* elem, const float* phi, int nrec, float* out,
                          cudaStream_t st) {
@@ -112,10 +112,10 @@ struct Impl {
     k_adj_source<O><<<1, 64, 0, st>>>(lam, elem, phi, res, nrec);
   }
   static void adj_pred(const DevOps& o, const AdjLtsArgs& a, const PhaseArgs& p, int n, cudaStream_t st) {
-    k_adj_pred<O><<<n, 128, 0, st>>>(o, a, p);
+    k_adj_pred<O><<<n, AdjNT<O>::value, 0, st>>>(o, a, p);
   }
   static void adj_nbr(const DevOps& o, const AdjLtsArgs& a, const PhaseArgs& p, int K, cudaStream_t st) {
-    k_adj_nbr<O><<<K, 128, 0, st>>>(o, a, p);
+    k_adj_nbr<O><<<K, AdjNT<O>::value, 0, st>>>(o, a, p);
   }
   static void energy(const float* Q, long long qs, int nsim, int fg, const double* emat, int K, double* partial,
                      int nblocks, cudaStream_t st) {
