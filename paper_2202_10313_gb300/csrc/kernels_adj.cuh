@@ -444,6 +444,20 @@ __device__ __forceinline__ void star_acc(const float* S, const float x[9], float
     for (int s = 0; s < 6; ++s) y[r] = fmaf(TR ? S[s * 9 + r] : S[r * 9 + s], x[s], y[r]);
 }
 
+// dst[q] = src[q] for q < N by a CTA of NT threads: every load is issued before the first
+// store, so the element's copies are in flight together.
+template <int N, int NT>
+__device__ __forceinline__ void stage(float* dst, const float* __restrict__ src, int t) {
+  constexpr int R = (N + NT - 1) / NT;
+  float v[R];
+#pragma unroll
+  for (int j = 0; j < R; ++j)
+    if (t + j * NT < N) v[j] = __ldg(src + t + j * NT);
+#pragma unroll
+  for (int j = 0; j < R; ++j)
+    if (t + j * NT < N) dst[t + j * NT] = v[j];
+}
+
 // acc[i][j] += sum_{j' < n} X[(r0 + i) * LD + j'] * Y[(s0 + j) * LD + j'] for a 3 x 3 tile.
 template <int LD>
 __device__ __forceinline__ void tile33(const float* X, const float* Y, int r0, int s0, int n, float acc[3][3]) {
@@ -482,11 +496,10 @@ __global__ void __launch_bounds__(AdjNT<O>::value) k_adj_pred(DevOps ops, AdjLts
   const int cl = meta & 0xff;
   const bool finer = meta & FLAG_FINER, coarser = meta & FLAG_COARSER;
   const bool even = ph.parity[cl] == 0;
-  for (int i = t; i < AM_SIZE; i += nt) sM[i] = a.amat[(size_t)k * AM_SIZE + i];
-  for (int i = t; i < NB9; i += nt) {
-    sL[i] = a.lq[(size_t)k * NB9 + i];
-    sD[0][i] = a.Qs[(size_t)k * a.qs + i];
-  }
+  constexpr int NT = AdjNT<O>::value;
+  stage<AM_SIZE, NT>(sM, a.amat + (size_t)k * AM_SIZE, t);
+  stage<NB9, NT>(sL, a.lq + (size_t)k * NB9, t);
+  stage<NB9, NT>(sD[0], a.Qs + (size_t)k * a.qs, t);
   __syncthreads();
   const float* S = sM + AM_STAR;
   // ---- forward time kernel: D_{d+1} = sum_c S_c D_d K_c^T on the support of D_{d+1}
@@ -683,13 +696,15 @@ __global__ void __launch_bounds__(AdjNT<O>::value) k_adj_pred(DevOps ops, AdjLts
 // Reverse of a neighbour pass, one CTA per buffer owner (every element): for each face
 // whose neighbour (the receiver) was active, the receiver's transposed flux goes to the
 // adjoint of the buffer it read, and the receiver's correlation with that buffer is
-// accumulated. Every (receiver, face) pair is visited by exactly one owner.
+// accumulated. Every (receiver, face) pair is visited by exactly one owner. The four faces
+// are handled together: with LF = lambda_k F^_ip^T and XF = X F-_jh (9 x F each), the
+// transposed flux is (A+^T LF) F-_jh^T and the correlation LF XF^T.
 template <int O>
 __global__ void __launch_bounds__(AdjNT<O>::value) k_adj_nbr(DevOps ops, AdjLtsArgs a, PhaseArgs ph) {
   constexpr int B = nbasis(O), F = nface(O), NB9 = 9 * B;
-  __shared__ float sA[81];
-  __shared__ float sLk[NB9], sX[NB9], sR[NB9];
-  __shared__ float sU[9 * F];
+  __shared__ float sA[4][81];
+  __shared__ float sLk[4][NB9], sX[4][NB9];
+  __shared__ float sLF[4][9 * F], sXF[4][9 * F], sU[4][9 * F];
   __shared__ int sF[8], sBk[8];
   const int kn = blockIdx.x, t = threadIdx.x, nt = blockDim.x;
   if (t < 8) {
@@ -697,83 +712,114 @@ __global__ void __launch_bounds__(AdjNT<O>::value) k_adj_nbr(DevOps ops, AdjLtsA
     sBk[t] = a.back[kn * 8 + t];
   }
   __syncthreads();
+  // buffer each active receiver read: 0 B1 (same cluster), 1 B3 (receiver coarser),
+  // 2 B2 / 3 B1 - B2 (receiver finer, first / second half); -1 receiver not active
   const int lo = a.meta[kn] & 0xff;
+  // modes packed 3 bits per face as mode + 1, so that a runtime face index needs no stack
+  int modes = 0;
+#pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int k = sF[2 * i];
     if (k < 0 || k >= a.end) continue;
     const int lr = a.meta[k] & 0xff;
-    const int par = ph.parity[lr];
-    const int ip = sBk[2 * i], jh = sBk[2 * i + 1];
-    for (int q = t; q < 81; q += nt) sA[q] = a.amat[(size_t)k * AM_SIZE + AM_NBR + ip * 81 + q];
-    for (int q = t; q < NB9; q += nt) {
-      sLk[q] = a.lq[(size_t)k * NB9 + q];
-      const size_t o = (size_t)kn * a.bufs + q;
-      float x;
-      if (lo == lr - 1) x = a.B3s[o];
-      else if (lo == lr + 1) x = (par == 0) ? a.B2s[o] : a.B1s[o] - a.B2s[o];
-      else x = a.B1s[o];
-      sX[q] = x;
-    }
-    __syncthreads();
-    if (t < B)
+    const int m = (lo == lr - 1) ? 1 : (lo == lr + 1) ? ((ph.parity[lr] == 0) ? 2 : 3) : 0;
+    modes |= (m + 1) << (3 * i);
+  }
+  if (modes == 0) return;   // the same for every thread of the CTA
+  auto mode = [modes](int i) { return ((modes >> (3 * i)) & 7) - 1; };
+  constexpr int NT = AdjNT<O>::value, R = (NB9 + NT - 1) / NT;
 #pragma unroll
-      for (int r = 0; r < 9; ++r) {
-        float v = 0.f;
+  for (int i = 0; i < 4; ++i) {
+    const int m = mode(i);
+    if (m < 0) continue;
+    const int k = sF[2 * i], ip = sBk[2 * i];
+    stage<81, NT>(sA[i], a.amat + (size_t)k * AM_SIZE + AM_NBR + ip * 81, t);
+    stage<NB9, NT>(sLk[i], a.lq + (size_t)k * NB9, t);
+    const float* b0 = (m == 1) ? a.B3s : (m == 2) ? a.B2s : a.B1s;
+    float x[R], x2[R];
 #pragma unroll
-        for (int s = 0; s < 9; ++s) v = fmaf(sA[s * 9 + r], sLk[s * B + t], v);
-        sR[r * B + t] = v;
+    for (int j = 0; j < R; ++j) {
+      const int q = t + j * NT;
+      x[j] = x2[j] = 0.f;
+      if (q < NB9) {
+        x[j] = __ldg(b0 + (size_t)kn * a.bufs + q);
+        if (m == 3) x2[j] = __ldg(a.B2s + (size_t)kn * a.bufs + q);
       }
-    __syncthreads();
-    if (t < F) {
-      float v[9];
-      rows9<B, B>(sR, a.FhT + ip * B * F, F, t, v);
-#pragma unroll
-      for (int r = 0; r < 9; ++r) sU[r * F + t] = v[r];
     }
-    __syncthreads();
-    if (t < B) {
-      const size_t o = (size_t)kn * NB9 + t;
-      float yv[9];
-      rows9<F, F>(sU, a.FbT + jh * F * B, B, t, yv);
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+      if (t + j * NT < NB9) sX[i][t + j * NT] = x[j] - x2[j];
+  }
+  __syncthreads();
+  for (int p = t; p < 4 * F; p += nt) {
+    const int i = p / F, f = p % F;
+    if (mode(i) < 0) continue;
+    const int ip = sBk[2 * i], jh = sBk[2 * i + 1];
+    float lf[9], xf[9];
+    rows9<B, B>(sLk[i], a.FhT + ip * B * F, F, f, lf);
+    rows9<B, B>(sX[i], ops.Fb + jh * B * F, F, f, xf);
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+      float u = 0.f;
+#pragma unroll
+      for (int s = 0; s < 9; ++s) u = fmaf(sA[i][s * 9 + r], lf[s], u);
+      sLF[i][r * F + f] = lf[r];
+      sXF[i][r * F + f] = xf[r];
+      sU[i][r * F + f] = u;
+    }
+  }
+  __syncthreads();
+  if (t < B) {
+    // the faces' contributions summed per buffer, then one update of each adjoint touched
+    float y1[9], y2[9], y3[9];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) y1[r] = y2[r] = y3[r] = 0.f;
+    bool u1 = false, u2 = false, u3 = false;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int m = mode(i);
+      if (m < 0) continue;
+      float y[9];
+      rows9<F, F>(sU[i], a.FbT + sBk[2 * i + 1] * F * B, B, t, y);
 #pragma unroll
       for (int r = 0; r < 9; ++r) {
-        const float y = yv[r];
-        if (lo == lr - 1) {
-          a.lb3[o + r * B] += y;
-        } else if (lo == lr + 1) {
-          if (par == 0) {
-            a.lb2[o + r * B] += y;
-          } else {
-            a.lb1[o + r * B] += y;
-            a.lb2[o + r * B] -= y;
-          }
+        if (m == 1) {
+          y3[r] += y[r];
+        } else if (m == 2) {
+          y2[r] += y[r];
+        } else if (m == 3) {
+          y1[r] += y[r];
+          y2[r] -= y[r];
         } else {
-          a.lb1[o + r * B] += y;
+          y1[r] += y[r];
         }
       }
+      u1 |= (m == 0 || m == 3);
+      u2 |= (m == 2 || m == 3);
+      u3 |= (m == 1);
     }
-    __syncthreads();
-    // correlation of the receiver's neighbour flux solver: lambda_Q_k (X F-_{jh} F^_ip)^T
-    if (t < F) {
-      float v[9];
-      rows9<B, B>(sX, ops.Fb + jh * B * F, F, t, v);
+    const size_t o = (size_t)kn * NB9 + t;
 #pragma unroll
-      for (int s = 0; s < 9; ++s) sU[s * F + t] = v[s];
+    for (int r = 0; r < 9; ++r) {
+      if (u1) a.lb1[o + r * B] += y1[r];
+      if (u2) a.lb2[o + r * B] += y2[r];
+      if (u3) a.lb3[o + r * B] += y3[r];
     }
-    __syncthreads();
-    if (t < B) {
-      float v[9];
-      rows9<F, F>(sU, ops.Fh + ip * F * B, B, t, v);
+  }
+  for (int p = t; p < 36; p += nt) {
+    const int i = p / 9, rb = (p / 3) % 3, sb = p % 3;
+    if (mode(i) < 0) continue;
+    float acc[3][3];
 #pragma unroll
-      for (int s = 0; s < 9; ++s) sR[s * B + t] = v[s];
-    }
-    __syncthreads();
-    for (int e = t; e < 81; e += nt) {
-      float acc = 0.f;
-      for (int b = 0; b < B; ++b) acc += sLk[(e / 9) * B + b] * sR[(e % 9) * B + b];
-      a.W[(size_t)k * AM_SIZE + AM_NBR + ip * 81 + e] += (double)acc;
-    }
-    __syncthreads();
+    for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) acc[ii][q] = 0.f;
+    tile33<F>(sLF[i], sXF[i], 3 * rb, 3 * sb, F, acc);
+    double* Wk = a.W + (size_t)sF[2 * i] * AM_SIZE + AM_NBR + sBk[2 * i] * 81;
+#pragma unroll
+    for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) Wk[(3 * rb + ii) * 9 + 3 * sb + q] += (double)acc[ii][q];
   }
 }
 
