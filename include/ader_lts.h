@@ -265,13 +265,23 @@ int lts_set_finest_dt(lts_t* h, double dt);
  * M = n_steps / 2^(N_c-1)), checkpoints every `every` macro steps, and the reverse
  * sweep takes the LTS phases backwards over the state (Q, B1, B2, B3): a neighbour pass
  * sends its transposed flux to the adjoint of the buffer it read (B1, B3, B2 or
- * B1 - B2), a predict pass collects the adjoints of the buffers it wrote. Each macro step
- * is recomputed phase by phase from its boundary state, keeping 2^(N_c-1) copies of Q
- * and 3 x 2^(N_c-1) copies of the buffers.
+ * B1 - B2), a predict pass collects the adjoints of the buffers it wrote. The reverse
+ * of a phase reads the phase's inputs: Q of its active elements (predict) or B1, B2, B3
+ * of the buffer owners (neighbour), kept while the segment from its checkpoint is
+ * replayed. When one segment's worth (every x the bytes of one macro step's phase inputs)
+ * fits the adjoint memory budget (lts_set_adjoint_memory; default half the free device
+ * memory) the segment is replayed once; otherwise its macro-boundary states are kept and
+ * each macro step is replayed once more just before its reverse, keeping one macro step's
+ * phase inputs. Both orders give bitwise the same results.
  * With grad and dq0 both NULL only the forward sweep and the misfit run.
  * Errors: LTS_ERR_ARG, LTS_ERR_STATE, LTS_ERR_OOM, LTS_ERR_CUDA. */
 int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* data, double* misfit,
                         double* grad, double* synth_out, double* dq0, void* cuda_stream);
+
+/* Device-memory budget in bytes for the phase inputs the LTS adjoint keeps per segment
+ * (see lts_misfit_gradient); 0 restores the default (half the free device memory at the
+ * call). Errors: none. */
+int lts_set_adjoint_memory(lts_t* h, uint64_t bytes);
 
 /* Macro steps run as CUDA graphs (default on): the launches of one macro step (Sec. V-B
  * schedule) are captured once per parity of the macro-step index and replayed, with the

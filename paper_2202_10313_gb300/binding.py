@@ -54,6 +54,7 @@ _SIGS = {
     "lts_launch_config": (_I, [_P, _P, _P]),
     "lts_autotune": (_I, [_P, _I, _P, _P, _P, _P, _I, _P]),
     "lts_set_wait_limit": (_I, [_P, _L, _I]),
+    "lts_set_adjoint_memory": (_I, [_P, ctypes.c_uint64]),
     "lts_partition": (_I, [_P, _I, _P, _P]),
     "lts_cut_faces": (_I, [_P, _P, _L, _P, _P]),
     "lts_set_partition": (_I, [_P, _I, _P]),
@@ -390,6 +391,11 @@ class Solver:
 
     def set_graphs(self, enable=True):
         self._check(lib().lts_set_graphs(self._h, 1 if enable else 0))
+
+    def set_adjoint_memory(self, nbytes=0):
+        """Budget for the phase inputs the LTS adjoint keeps per checkpoint segment (0: half
+        the free device memory)."""
+        self._check(lib().lts_set_adjoint_memory(self._h, int(nbytes)))
 
     def set_wait_limit(self, cycles=2000000000, suppress_commit=False):
         self._check(lib().lts_set_wait_limit(self._h, int(cycles), 1 if suppress_commit else 0))

@@ -148,6 +148,7 @@ struct lts_solver {
   SrcItem* d_sitems = nullptr;
   size_t sitems_cap = 0;
   int num_sms = 0;
+  uint64_t adj_budget = 0;   // bytes for the LTS adjoint's phase inputs (0: half the free memory)
   // profiling: event pairs around each predict / neighbour launch, read lazily
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -942,25 +943,19 @@ void adjoint_lts(lts_solver* h, int64_t n_macro, int64_t every, const double* da
   const int64_t period = int64_t(1) << (h->nc - 1);
   const int64_t ncp = (n_macro + every - 1) / every;
   const int64_t segm = std::min(every, n_macro);
-  DevBuf d_syn, d_res, d_lq, d_lb, d_w, d_cp, d_mac, d_qn, d_sq, d_sb;
+  DevBuf d_syn, d_res, d_lq, d_lb, d_w, d_cp, d_mac, d_qn;
   d_syn.alloc(sizeof(float) * (n_macro + 1) * nrec * 3);
   d_res.alloc(sizeof(float) * (n_macro + 1) * nrec * 3);
   d_lq.alloc(sizeof(float) * K * NB9);
   d_lb.alloc(sizeof(float) * 3 * K * NB9);
   d_w.alloc(sizeof(double) * K * ltsdev::AM_SIZE);
   d_cp.alloc(sizeof(float) * ncp * K * qs);
-  d_mac.alloc(sizeof(float) * segm * K * qs);
   d_qn.alloc(sizeof(float) * K * qs);
-  d_sq.alloc(sizeof(float) * period * K * qs);
-  d_sb.alloc(sizeof(float) * 3 * period * K * bs);
-  const size_t qbytes = sizeof(float) * K * qs, bbytes = sizeof(float) * K * bs;
+  const size_t qbytes = sizeof(float) * K * qs;
   auto dcopy = [&](void* dst, const void* src, size_t bytes) {
     ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, stream), "adjoint copy");
   };
   float* cp = d_cp.get<float>();
-  float* mac = d_mac.get<float>();
-  float* sq = d_sq.get<float>();
-  float* sb = d_sb.get<float>();
   const int* relem = d_relem.get<int>();
   const float* rphi = d_rphi.get<float>();
   // ---- forward sweep: samples at the macro boundaries, checkpoints
@@ -1013,66 +1008,122 @@ void adjoint_lts(lts_solver* h, int64_t n_macro, int64_t every, const double* da
   aa.qs = qs;
   aa.bufs = bs;
   MacroPlan mp;
+  // Phase layout of a macro step (the same for every macro step; the step indices are
+  // relative) and the bytes each phase's reverse reads: Q of the active elements before a
+  // predict pass, B1, B2, B3 of the buffer owners before a neighbour pass. Elements are in
+  // cluster order, so both are prefixes.
+  std::vector<Phase> lay;
+  std::vector<size_t> snap_off, snap_len;
+  size_t per_macro = 0;
+  {
+    size_t seis_need = h->seis_used;
+    plan_macro(h, s0, seis_need, mp);
+    for (int r = 0; r < nrec; ++r) {
+      h->receivers[r].t.resize(nrec_t[r]);
+      h->receivers[r].slot.resize(nrec_t[r]);
+    }
+    for (const Phase& ph : mp.phases) {
+      Phase q = ph;
+      q.s -= s0;
+      lay.push_back(q);
+      const int64_t n = ph.kind == 1 ? h->cbeg[ph.top + 1] : h->cbeg[std::min(ph.top + 2, h->nc)];
+      const size_t len = ph.kind == 1 ? sizeof(float) * n * qs : 3 * sizeof(float) * n * bs;
+      snap_off.push_back(per_macro);
+      snap_len.push_back(len);
+      per_macro += (len + 255) / 256 * 256;
+    }
+  }
+  auto phase_at = [&](size_t pi, int64_t sb0) {
+    Phase q = lay[pi];
+    q.s += sb0;
+    return q;
+  };
+  // reverse of one macro step from the phase inputs kept in `snap` (layout above)
+  auto reverse_macro = [&](int64_t m, const char* snap) {
+    const int64_t sb0 = s0 + m * period;
+    for (size_t pi = lay.size(); pi-- > 0;) {
+      const Phase ph = phase_at(pi, sb0);
+      const PhaseArgs pa = phase_args(h, ph);
+      if (pa.end <= 0) continue;
+      aa.end = pa.end;
+      const float* base = reinterpret_cast<const float*>(snap + snap_off[pi]);
+      if (ph.kind == 1) {
+        aa.Qs = base;
+        X.adj_pred(h->dops, aa, pa, pa.end, stream);
+      } else {
+        // a buffer owner differs by at most one cluster from the receivers it feeds, so
+        // the owners of this pass are the elements of clusters 0..top+1
+        const int owners = (int)h->cbeg[std::min(ph.top + 2, h->nc)];
+        aa.B1s = base;
+        aa.B2s = base + (size_t)owners * bs;
+        aa.B3s = base + 2 * (size_t)owners * bs;
+        aa.bufs = bs;
+        X.adj_nbr(h->dops, aa, pa, owners, stream);
+      }
+    }
+    X.adj_source(d_lq.get<float>(), relem, rphi, d_res.get<float>() + m * nrec * 3, nrec, stream);
+  };
+  // forward replay of macro step m, keeping every phase's inputs in `snap`
+  auto replay_macro = [&](int64_t m, char* snap) {
+    const int64_t sb0 = s0 + m * period;
+    h->s_now = sb0;
+    size_t seis_need = h->seis_used;
+    plan_macro(h, sb0, seis_need, mp);
+    ensure_capacity(reinterpret_cast<void**>(&h->d_sitems), &h->sitems_cap, mp.sitems.size(), sizeof(SrcItem));
+    if (!mp.sitems.empty())
+      ck(cudaMemcpyAsync(h->d_sitems, mp.sitems.data(), mp.sitems.size() * sizeof(SrcItem), cudaMemcpyHostToDevice,
+                         stream),
+         "upload source items");
+    for (size_t pi = 0; pi < mp.phases.size(); ++pi) {
+      const Phase& ph = mp.phases[pi];
+      char* dst = snap + snap_off[pi];
+      if (ph.kind == 1) {
+        dcopy(dst, h->dst.Q, snap_len[pi]);
+      } else {
+        const size_t one = snap_len[pi] / 3;
+        dcopy(dst, h->dst.B1, one);
+        dcopy(dst + one, h->dst.B2, one);
+        dcopy(dst + 2 * one, h->dst.B3, one);
+      }
+      enqueue_phase(h, ph, stream, false);
+    }
+    for (int r = 0; r < nrec; ++r) {
+      h->receivers[r].t.resize(nrec_t[r]);
+      h->receivers[r].slot.resize(nrec_t[r]);
+    }
+    h->seis_used = seis_fwd;
+  };
+  // The inputs of a whole segment's phases are kept when they fit in half the free device
+  // memory: one forward replay per segment. Otherwise the segment's macro-boundary states are
+  // kept and each macro step is replayed once more just before its reverse.
+  size_t free_b = 0, total_b = 0;
+  ck(cudaMemGetInfo(&free_b, &total_b), "memory info");
+  const double budget = h->adj_budget ? (double)h->adj_budget : 0.5 * (double)free_b;
+  const bool whole_segment = (double)segm * (double)per_macro <= budget;
+  DevBuf d_snap;
+  d_snap.alloc(whole_segment ? segm * per_macro : per_macro);
+  char* snap = d_snap.get<char>();
+  if (!whole_segment) d_mac.alloc(sizeof(float) * segm * K * qs);
+  float* mac = d_mac.get<float>();
   for (int64_t sgi = ncp - 1; sgi >= 0; --sgi) {
     const int64_t m0 = sgi * every, m1 = std::min(m0 + every, n_macro);
-    // macro-boundary states of the segment
     dcopy(h->dst.Q, cp + sgi * K * qs, qbytes);
     h->s_now = s0 + m0 * period;
+    if (whole_segment) {
+      for (int64_t m = m0; m < m1; ++m) replay_macro(m, snap + (m - m0) * per_macro);
+      for (int64_t m = m1 - 1; m >= m0; --m) reverse_macro(m, snap + (m - m0) * per_macro);
+      continue;
+    }
+    // macro-boundary states of the segment
     dcopy(mac, h->dst.Q, qbytes);
     for (int64_t m = m0; m + 1 < m1; ++m) {
       advance_steps(h, period, stream);
       dcopy(mac + (m + 1 - m0) * K * qs, h->dst.Q, qbytes);
     }
     for (int64_t m = m1 - 1; m >= m0; --m) {
-      // recompute macro step m phase by phase, keeping the inputs of every phase
       dcopy(h->dst.Q, mac + (m - m0) * K * qs, qbytes);
-      const int64_t sb0 = s0 + m * period;
-      h->s_now = sb0;
-      size_t seis_need = h->seis_used;
-      plan_macro(h, sb0, seis_need, mp);
-      ensure_capacity(reinterpret_cast<void**>(&h->d_sitems), &h->sitems_cap, mp.sitems.size(), sizeof(SrcItem));
-      if (!mp.sitems.empty())
-        ck(cudaMemcpyAsync(h->d_sitems, mp.sitems.data(), mp.sitems.size() * sizeof(SrcItem), cudaMemcpyHostToDevice,
-                           stream),
-           "upload source items");
-      for (const Phase& ph : mp.phases) {
-        const int64_t lvl = ph.s - sb0;
-        if (ph.kind == 1) {
-          dcopy(sq + lvl * K * qs, h->dst.Q, qbytes);
-        } else {
-          float* base = sb + 3 * (lvl - 1) * K * bs;
-          dcopy(base, h->dst.B1, bbytes);
-          dcopy(base + K * bs, h->dst.B2, bbytes);
-          dcopy(base + 2 * K * bs, h->dst.B3, bbytes);
-        }
-        enqueue_phase(h, ph, stream, false);
-      }
-      for (size_t pi = mp.phases.size(); pi-- > 0;) {
-        const Phase& ph = mp.phases[pi];
-        const PhaseArgs pa = phase_args(h, ph);
-        if (pa.end <= 0) continue;
-        const int64_t lvl = ph.s - sb0;
-        aa.end = pa.end;
-        if (ph.kind == 1) {
-          aa.Qs = sq + lvl * K * qs;
-          X.adj_pred(h->dops, aa, pa, pa.end, stream);
-        } else {
-          const float* base = sb + 3 * (lvl - 1) * K * bs;
-          aa.B1s = base;
-          aa.B2s = base + K * bs;
-          aa.B3s = base + 2 * K * bs;
-          // a buffer owner differs by at most one cluster from the receivers it feeds, so
-          // the owners of this pass are the elements of clusters 0..top+1
-          const int owners = (int)h->cbeg[std::min(ph.top + 2, h->nc)];
-          X.adj_nbr(h->dops, aa, pa, owners, stream);
-        }
-      }
-      X.adj_source(d_lq.get<float>(), relem, rphi, d_res.get<float>() + m * nrec * 3, nrec, stream);
-      for (int r = 0; r < nrec; ++r) {
-        h->receivers[r].t.resize(nrec_t[r]);
-        h->receivers[r].slot.resize(nrec_t[r]);
-      }
-      h->seis_used = seis_fwd;
+      replay_macro(m, snap);
+      reverse_macro(m, snap);
     }
   }
   ck(cudaGetLastError(), "adjoint kernels");
@@ -2054,6 +2105,10 @@ int lts_set_graphs(lts_t* h, int enable) {
     h->use_graphs = enable != 0;
     if (!h->use_graphs) release_graphs(h);
   });
+}
+
+int lts_set_adjoint_memory(lts_t* h, uint64_t bytes) {
+  return run(h, [&] { h->adj_budget = bytes; });
 }
 
 int lts_set_wait_limit(lts_t* h, int64_t cycles, int suppress_commit) {

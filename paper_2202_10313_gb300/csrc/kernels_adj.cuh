@@ -42,6 +42,7 @@ template <int N, int LD>
 __device__ __forceinline__ void rows9(const float* src, const float* __restrict__ tab, int ts, int t, float v[9]) {
 #pragma unroll
   for (int r = 0; r < 9; ++r) v[r] = 0.f;
+#pragma unroll 4
   for (int j = 0; j < N; ++j) {
     const float w = __ldg(tab + j * ts + t);
 #pragma unroll
@@ -475,7 +476,49 @@ __device__ __forceinline__ void tile33(const float* X, const float* Y, int r0, i
   }
 }
 
-// Reverse of a predict pass, one CTA per active element.
+// Shared-memory plan of k_adj_pred, a persistent kernel: the operator tables (K_c^T, K_c,
+// F~_i, F^_i^T, F~_i^T) once per CTA, then one region per element group. A group is one warp
+// (orders 3-4) or two (order 5) and takes the CTA's elements in turn; G groups fill the
+// shared memory (at most 128 registers a thread, 15 named barriers for two-warp groups).
+template <int O>
+struct AdjPredCfg {
+  static constexpr int B = nbasis(O), F = nface(O), NB9 = 9 * B, NT = AdjNT<O>::value;
+  static constexpr int NSCR = (3 * NB9 > 108 * F) ? 3 * NB9 : 108 * F;
+  static constexpr int ELEM = rup(AM_SIZE + (4 + O) * NB9 + NSCR, 4);   // sM, sL, sT, sG[2], sD[O], scratch
+  static constexpr int TAB = rup(6 * B * B + 12 * B * F, 4);
+  static constexpr int G_SMEM = (227 * 1024 / 4 - TAB) / ELEM;
+  static constexpr int G_REG = 65536 / (128 * NT);
+  static constexpr int G_BAR = (NT == 32) ? 32 : 15;
+  static constexpr int G0 = G_SMEM < G_REG ? G_SMEM : G_REG;
+  static constexpr int G = G0 < G_BAR ? G0 : G_BAR;
+  static constexpr int THREADS = G * NT;
+  static constexpr int SMEM_BYTES = 4 * (TAB + G * ELEM);
+  static_assert(G >= 1 && SMEM_BYTES <= 227 * 1024, "k_adj_pred shared-memory plan");
+};
+
+// Barrier of one element group: the warp itself, or a named barrier over its two warps.
+template <int NT>
+__device__ __forceinline__ void gsync(int g) {
+  if constexpr (NT == 32)
+    __syncwarp();
+  else
+    asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "n"(NT) : "memory");
+}
+
+// rows9 with the table in shared memory.
+template <int N, int LD>
+__device__ __forceinline__ void rows9s(const float* src, const float* tab, int ts, int t, float v[9]) {
+#pragma unroll
+  for (int r = 0; r < 9; ++r) v[r] = 0.f;
+#pragma unroll 4
+  for (int j = 0; j < N; ++j) {
+    const float w = tab[j * ts + t];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) v[r] = fmaf(src[r * LD + j], w, v[r]);
+  }
+}
+
+// Reverse of a predict pass over the active elements [0, end).
 //
 // Degree structure used throughout (exact): K_c[i][j] vanishes unless deg i < deg j, so
 // D_d is a polynomial of degree O-1-d and lives on the first nbasis(O-d) modes; only those
@@ -484,213 +527,240 @@ __device__ __forceinline__ void tile33(const float* X, const float* Y, int r0, i
 // Z_c D_d^T; with V_c = lambda K_c^T the volume term is mu = -sum_c S_c^T V_c and its
 // correlation -V_c T^T.
 template <int O>
-__global__ void __launch_bounds__(AdjNT<O>::value) k_adj_pred(DevOps ops, AdjLtsArgs a, PhaseArgs ph) {
-  constexpr int B = nbasis(O), F = nface(O), NB9 = 9 * B;
-  constexpr int NSCR = (3 * NB9 > 108 * F) ? 3 * NB9 : 108 * F;
-  __shared__ float sM[AM_SIZE];
-  __shared__ float sL[NB9], sT[NB9];
-  __shared__ float sD[O][NB9], sG[2][NB9];
-  __shared__ float sScr[NSCR];   // V_c, then the face products, then Z_c
-  const int k = blockIdx.x, t = threadIdx.x, nt = blockDim.x;
-  const int meta = a.meta[k];
-  const int cl = meta & 0xff;
-  const bool finer = meta & FLAG_FINER, coarser = meta & FLAG_COARSER;
-  const bool even = ph.parity[cl] == 0;
-  constexpr int NT = AdjNT<O>::value;
-  stage<AM_SIZE, NT>(sM, a.amat + (size_t)k * AM_SIZE, t);
-  stage<NB9, NT>(sL, a.lq + (size_t)k * NB9, t);
-  stage<NB9, NT>(sD[0], a.Qs + (size_t)k * a.qs, t);
+__global__ void __launch_bounds__(AdjPredCfg<O>::THREADS, 1) k_adj_pred(DevOps ops, AdjLtsArgs a, PhaseArgs ph) {
+  using C = AdjPredCfg<O>;
+  constexpr int B = C::B, F = C::F, NB9 = C::NB9, NT = C::NT, NSCR = C::NSCR;
+  extern __shared__ __align__(16) float smem[];
+  float* tKT = smem;
+  float* tK = tKT + 3 * B * B;
+  float* tFt = tK + 3 * B * B;
+  float* tFhT = tFt + 4 * B * F;
+  float* tFtT = tFhT + 4 * B * F;
+  for (int i = threadIdx.x; i < 3 * B * B; i += C::THREADS) {
+    tKT[i] = a.KT[i];
+    tK[i] = ops.K[i];
+  }
+  for (int i = threadIdx.x; i < 4 * B * F; i += C::THREADS) {
+    tFt[i] = ops.Ft[i];
+    tFhT[i] = a.FhT[i];
+    tFtT[i] = a.FtT[i];
+  }
   __syncthreads();
-  const float* S = sM + AM_STAR;
-  // ---- forward time kernel: D_{d+1} = sum_c S_c D_d K_c^T on the support of D_{d+1}
-  for (int d = 0; d < O - 1; ++d) {
-    const int nin = nbasis(O - d), nout = nbasis(O - 1 - d);
+  const int g = threadIdx.x / NT, t = threadIdx.x % NT;
+  float* sM = smem + C::TAB + g * C::ELEM;
+  float* sL = sM + AM_SIZE;
+  float* sT = sL + NB9;
+  float* sG0 = sT + NB9;          // G ping-pong [2][9B]
+  float* sDb = sG0 + 2 * NB9;     // D_0 .. D_{O-1} [O][9B]
+  float* sScr = sDb + O * NB9;    // V_c, then the face products, then Z_c
+  (void)NSCR;
+  for (int k = blockIdx.x * C::G + g; k < a.end; k += gridDim.x * C::G) {
+    const int meta = a.meta[k];
+    const int cl = meta & 0xff;
+    const bool finer = meta & FLAG_FINER, coarser = meta & FLAG_COARSER;
+    const bool even = ph.parity[cl] == 0;
+    stage<AM_SIZE, NT>(sM, a.amat + (size_t)k * AM_SIZE, t);
+    stage<NB9, NT>(sL, a.lq + (size_t)k * NB9, t);
+    stage<NB9, NT>(sDb, a.Qs + (size_t)k * a.qs, t);
+    gsync<NT>(g);
+    const float* S = sM + AM_STAR;
+    // ---- forward time kernel: D_{d+1} = sum_c S_c D_d K_c^T on the support of D_{d+1}
+#pragma unroll
+    for (int d = 0; d < O - 1; ++d) {
+      const int nin = nbasis(O - d), nout = nbasis(O - 1 - d);
+      if (t < B) {
+        float Y[3][9];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int s = 0; s < 9; ++s) Y[c][s] = 0.f;
+        if (t < nout)
+#pragma unroll 4
+          for (int kk = 0; kk < nin; ++kk)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              const float kc = tKT[(c * B + kk) * B + t];
+#pragma unroll
+              for (int s = 0; s < 9; ++s) Y[c][s] = fmaf(sDb[(d) * NB9 + s * B + kk], kc, Y[c][s]);
+            }
+        float v[9];
+#pragma unroll
+        for (int r = 0; r < 9; ++r) v[r] = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) star_acc<false>(S + c * 81, Y[c], v);
+#pragma unroll
+        for (int r = 0; r < 9; ++r) sDb[(d + 1) * NB9 + r * B + t] = v[r];
+      }
+      gsync<NT>(g);
+    }
+    float mu[9], muh[9];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) mu[r] = muh[r] = 0.f;
+    float* sV = sScr;
     if (t < B) {
-      float Y[3][9];
+#pragma unroll
+      for (int r = 0; r < 9; ++r) {
+        float v = 0.f;
+        for (int d = 0; d < O; ++d) v = fmaf(ph.coef[cl][d], sDb[(d) * NB9 + r * B + t], v);
+        sT[r * B + t] = v;
+      }
+      // V_c = lambda K_c^T and the volume term
+      float V[3][9];
 #pragma unroll
       for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int s = 0; s < 9; ++s) Y[c][s] = 0.f;
-      if (t < nout)
-        for (int kk = 0; kk < nin; ++kk)
+        for (int s = 0; s < 9; ++s) V[c][s] = 0.f;
+#pragma unroll 4
+      for (int b = 0; b < B; ++b)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const float kc = __ldg(a.KT + (c * B + kk) * B + t);
+        for (int c = 0; c < 3; ++c) {
+          const float kc = tKT[(c * B + b) * B + t];
 #pragma unroll
-            for (int s = 0; s < 9; ++s) Y[c][s] = fmaf(sD[d][s * B + kk], kc, Y[c][s]);
-          }
-      float v[9];
+          for (int s = 0; s < 9; ++s) V[c][s] = fmaf(sL[s * B + b], kc, V[c][s]);
+        }
+      float w[9];
 #pragma unroll
-      for (int r = 0; r < 9; ++r) v[r] = 0.f;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) star_acc<false>(S + c * 81, Y[c], v);
-#pragma unroll
-      for (int r = 0; r < 9; ++r) sD[d + 1][r * B + t] = v[r];
-    }
-    __syncthreads();
-  }
-  float mu[9], muh[9];
-#pragma unroll
-  for (int r = 0; r < 9; ++r) mu[r] = muh[r] = 0.f;
-  float* sV = sScr;
-  if (t < B) {
-#pragma unroll
-    for (int r = 0; r < 9; ++r) {
-      float v = 0.f;
-      for (int d = 0; d < O; ++d) v = fmaf(ph.coef[cl][d], sD[d][r * B + t], v);
-      sT[r * B + t] = v;
-    }
-    // V_c = lambda K_c^T and the volume term
-    float V[3][9];
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int s = 0; s < 9; ++s) V[c][s] = 0.f;
-    for (int b = 0; b < B; ++b)
+      for (int r = 0; r < 9; ++r) w[r] = 0.f;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const float kc = __ldg(a.KT + (c * B + b) * B + t);
+        star_acc<true>(S + c * 81, V[c], w);
 #pragma unroll
-        for (int s = 0; s < 9; ++s) V[c][s] = fmaf(sL[s * B + b], kc, V[c][s]);
+        for (int s = 0; s < 9; ++s) sV[c * NB9 + s * B + t] = V[c][s];
       }
-    float w[9];
 #pragma unroll
-    for (int r = 0; r < 9; ++r) w[r] = 0.f;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      star_acc<true>(S + c * 81, V[c], w);
-#pragma unroll
-      for (int s = 0; s < 9; ++s) sV[c * NB9 + s * B + t] = V[c][s];
+      for (int r = 0; r < 9; ++r) mu[r] = -w[r];
     }
-#pragma unroll
-    for (int r = 0; r < 9; ++r) mu[r] = -w[r];
-  }
-  __syncthreads();
-  // star correlations, one 3 x 3 tile (c, row block, column block) per thread t < 27
-  const int tc = t / 9, trb = (t / 3) % 3, tsb = t % 3;
-  float wst[3][3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int q = 0; q < 3; ++q) wst[i][q] = 0.f;
-  if (t < 27) {
-    tile33<B>(sV + tc * NB9, sT, 3 * trb, 3 * tsb, B, wst);
+    gsync<NT>(g);
+    // star correlations, one 3 x 3 tile (c, row block, column block) per thread t < 27
+    const int tc = t / 9, trb = (t / 3) % 3, tsb = t % 3;
+    float wst[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int q = 0; q < 3; ++q) wst[i][q] = -wst[i][q];
-  }
-  __syncthreads();
-  // local surface: LF_i = lambda F^_i^T, TF_i = T F~_i, U_i = A-_i^T LF_i, per (face, f)
-  float* sLF = sScr;
-  float* sTF = sScr + 36 * F;
-  float* sU = sScr + 72 * F;
-  for (int p = t; p < 4 * F; p += nt) {
-    const int i = p / F, f = p % F;
-    float lf[9], tf[9], u[9];
-    rows9<B, B>(sL, a.FhT + i * B * F, F, f, lf);
-    rows9<B, B>(sT, ops.Ft + i * B * F, F, f, tf);
-    const float* Am = sM + AM_LOC + i * 81;
+      for (int q = 0; q < 3; ++q) wst[i][q] = 0.f;
+    if (t < 27) {
+      tile33<B>(sV + tc * NB9, sT, 3 * trb, 3 * tsb, B, wst);
 #pragma unroll
-    for (int r = 0; r < 9; ++r) {
-      float v = 0.f;
+      for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int s = 0; s < 9; ++s) v = fmaf(Am[s * 9 + r], lf[s], v);
-      u[r] = v;
+        for (int q = 0; q < 3; ++q) wst[i][q] = -wst[i][q];
     }
+    gsync<NT>(g);
+    // local surface: LF_i = lambda F^_i^T, TF_i = T F~_i, U_i = A-_i^T LF_i, per (face, f)
+    float* sLF = sScr;
+    float* sTF = sScr + 36 * F;
+    float* sU = sScr + 72 * F;
+    for (int p = t; p < 4 * F; p += NT) {
+      const int i = p / F, f = p % F;
+      float lf[9], tf[9], u[9];
+      rows9s<B, B>(sL, tFhT + i * B * F, F, f, lf);
+      rows9s<B, B>(sT, tFt + i * B * F, F, f, tf);
+      const float* Am = sM + AM_LOC + i * 81;
 #pragma unroll
-    for (int r = 0; r < 9; ++r) {
-      sLF[(i * 9 + r) * F + f] = lf[r];
-      sTF[(i * 9 + r) * F + f] = tf[r];
-      sU[(i * 9 + r) * F + f] = u[r];
-    }
-  }
-  __syncthreads();
-  if (t < B)
-    for (int i = 0; i < 4; ++i)
-      for (int f = 0; f < F; ++f) {
-        const float w = __ldg(a.FtT + (i * F + f) * B + t);
+      for (int r = 0; r < 9; ++r) {
+        float v = 0.f;
 #pragma unroll
-        for (int r = 0; r < 9; ++r) mu[r] = fmaf(sU[(i * 9 + r) * F + f], w, mu[r]);
+        for (int s = 0; s < 9; ++s) v = fmaf(Am[s * 9 + r], lf[s], v);
+        u[r] = v;
       }
-  double* Wk = a.W + (size_t)k * AM_SIZE;
-  for (int p = t; p < 36; p += nt) {
-    const int i = p / 9, rb = (p / 3) % 3, sb = p % 3;
-    float acc[3][3];
 #pragma unroll
-    for (int ii = 0; ii < 3; ++ii)
-#pragma unroll
-      for (int q = 0; q < 3; ++q) acc[ii][q] = 0.f;
-    tile33<F>(sLF + i * 9 * F, sTF + i * 9 * F, 3 * rb, 3 * sb, F, acc);
-#pragma unroll
-    for (int ii = 0; ii < 3; ++ii)
-#pragma unroll
-      for (int q = 0; q < 3; ++q) Wk[AM_LOC + i * 81 + (3 * rb + ii) * 9 + 3 * sb + q] += (double)acc[ii][q];
-  }
-  // the buffers this pass wrote
-  if (t < B) {
-    const size_t o = (size_t)k * NB9 + t;
-#pragma unroll
-    for (int r = 0; r < 9; ++r) {
-      mu[r] += a.lb1[o + r * B];
-      a.lb1[o + r * B] = 0.f;
-      if (coarser) {
-        mu[r] += a.lb3[o + r * B];
-        if (even) a.lb3[o + r * B] = 0.f;
-      }
-      if (finer) {
-        muh[r] = a.lb2[o + r * B];
-        a.lb2[o + r * B] = 0.f;
+      for (int r = 0; r < 9; ++r) {
+        sLF[(i * 9 + r) * F + f] = lf[r];
+        sTF[(i * 9 + r) * F + f] = tf[r];
+        sU[(i * 9 + r) * F + f] = u[r];
       }
     }
+    gsync<NT>(g);
+    if (t < B)
+      for (int i = 0; i < 4; ++i)
+#pragma unroll 5
+        for (int f = 0; f < F; ++f) {
+          const float w = tFtT[(i * F + f) * B + t];
 #pragma unroll
-    for (int r = 0; r < 9; ++r)
-      sG[(O - 1) & 1][r * B + t] = ph.coef[cl][O - 1] * mu[r] + ph.hcoef[cl][O - 1] * muh[r];
-  }
-  __syncthreads();
-  // ---- reverse time kernel
-  float* sZ = sScr;
-  for (int d = O - 2; d >= 0; --d) {
-    const int nk = nbasis(O - 1 - d), nout = nbasis(O - d);
-    const float* Gn = sG[(d + 1) & 1];
+          for (int r = 0; r < 9; ++r) mu[r] = fmaf(sU[(i * 9 + r) * F + f], w, mu[r]);
+        }
+    double* Wk = a.W + (size_t)k * AM_SIZE;
+    for (int p = t; p < 36; p += NT) {
+      const int i = p / 9, rb = (p / 3) % 3, sb = p % 3;
+      float acc[3][3];
+#pragma unroll
+      for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) acc[ii][q] = 0.f;
+      tile33<F>(sLF + i * 9 * F, sTF + i * 9 * F, 3 * rb, 3 * sb, F, acc);
+#pragma unroll
+      for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) Wk[AM_LOC + i * 81 + (3 * rb + ii) * 9 + 3 * sb + q] += (double)acc[ii][q];
+    }
+    // the buffers this pass wrote
     if (t < B) {
-      float Z[3][9];
+      const size_t o = (size_t)k * NB9 + t;
 #pragma unroll
-      for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int r = 0; r < 9; ++r) Z[c][r] = 0.f;
-      if (t < nout)
-        for (int kk = 0; kk < nk; ++kk)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const float kc = __ldg(ops.K + (c * B + kk) * B + t);
-#pragma unroll
-            for (int r = 0; r < 9; ++r) Z[c][r] = fmaf(Gn[r * B + kk], kc, Z[c][r]);
-          }
-      float g[9];
-#pragma unroll
-      for (int r = 0; r < 9; ++r) g[r] = ph.coef[cl][d] * mu[r] + ph.hcoef[cl][d] * muh[r];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        star_acc<true>(S + c * 81, Z[c], g);
-#pragma unroll
-        for (int r = 0; r < 9; ++r) sZ[c * NB9 + r * B + t] = Z[c][r];
+      for (int r = 0; r < 9; ++r) {
+        mu[r] += a.lb1[o + r * B];
+        a.lb1[o + r * B] = 0.f;
+        if (coarser) {
+          mu[r] += a.lb3[o + r * B];
+          if (even) a.lb3[o + r * B] = 0.f;
+        }
+        if (finer) {
+          muh[r] = a.lb2[o + r * B];
+          a.lb2[o + r * B] = 0.f;
+        }
       }
 #pragma unroll
-      for (int r = 0; r < 9; ++r) sG[d & 1][r * B + t] = g[r];
+      for (int r = 0; r < 9; ++r)
+        sG0[((O - 1) & 1) * NB9 + r * B + t] = ph.coef[cl][O - 1] * mu[r] + ph.hcoef[cl][O - 1] * muh[r];
     }
-    __syncthreads();
-    if (t < 27) tile33<B>(sZ + tc * NB9, sD[d], 3 * trb, 3 * tsb, nout, wst);
-    __syncthreads();
+    gsync<NT>(g);
+    // ---- reverse time kernel
+    float* sZ = sScr;
+#pragma unroll
+    for (int d = O - 2; d >= 0; --d) {
+      const int nk = nbasis(O - 1 - d), nout = nbasis(O - d);
+      const float* Gn = (sG0 + ((d + 1) & 1) * NB9);
+      if (t < B) {
+        float Z[3][9];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int r = 0; r < 9; ++r) Z[c][r] = 0.f;
+        if (t < nout)
+#pragma unroll 4
+          for (int kk = 0; kk < nk; ++kk)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              const float kc = tK[(c * B + kk) * B + t];
+#pragma unroll
+              for (int r = 0; r < 9; ++r) Z[c][r] = fmaf(Gn[r * B + kk], kc, Z[c][r]);
+            }
+        float g[9];
+#pragma unroll
+        for (int r = 0; r < 9; ++r) g[r] = ph.coef[cl][d] * mu[r] + ph.hcoef[cl][d] * muh[r];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          star_acc<true>(S + c * 81, Z[c], g);
+#pragma unroll
+          for (int r = 0; r < 9; ++r) sZ[c * NB9 + r * B + t] = Z[c][r];
+        }
+#pragma unroll
+        for (int r = 0; r < 9; ++r) sG0[(d & 1) * NB9 + r * B + t] = g[r];
+      }
+      gsync<NT>(g);
+      if (t < 27) tile33<B>(sZ + tc * NB9, (sDb + (d) * NB9), 3 * trb, 3 * tsb, nout, wst);
+      gsync<NT>(g);
+    }
+    if (t < B)
+#pragma unroll
+      for (int r = 0; r < 9; ++r) a.lq[(size_t)k * NB9 + r * B + t] = sL[r * B + t] + sG0[(0) * NB9 + r * B + t];
+    if (t < 27)
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) Wk[AM_STAR + tc * 81 + (3 * trb + i) * 9 + 3 * tsb + q] += (double)wst[i][q];
+    gsync<NT>(g);   // the group's region is refilled for its next element
   }
-  if (t < B)
-#pragma unroll
-    for (int r = 0; r < 9; ++r) a.lq[(size_t)k * NB9 + r * B + t] = sL[r * B + t] + sG[0][r * B + t];
-  if (t < 27)
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int q = 0; q < 3; ++q) Wk[AM_STAR + tc * 81 + (3 * trb + i) * 9 + 3 * tsb + q] += (double)wst[i][q];
 }
 
 // Reverse of a neighbour pass, one CTA per buffer owner (every element): for each face

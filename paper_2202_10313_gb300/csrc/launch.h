@@ -71,6 +71,10 @@ struct Impl {
       // two fit the 512 tensor-memory columns)
       L->blocks_predict_tc = 2;
     }
+    if constexpr (M == 0 && FG == 1) {
+      e = cudaFuncSetAttribute(k_adj_pred<O>, cudaFuncAttributeMaxDynamicSharedMemorySize, AdjPredCfg<O>::SMEM_BYTES);
+      if (e != cudaSuccess) return e;
+    }
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L->blocks_neighbour, k_neighbour<O, M, FG>, C::NTN,
                                                          L->smem_neighbour);
   }
@@ -111,8 +115,15 @@ struct Impl {
   static void adj_source(float* lam, const int* elem, const float* phi, const float* res, int nrec, cudaStream_t st) {
     k_adj_source<O><<<1, 64, 0, st>>>(lam, elem, phi, res, nrec);
   }
+  // persistent: at most one CTA per SM, each CTA's element groups take elements in turn
   static void adj_pred(const DevOps& o, const AdjLtsArgs& a, const PhaseArgs& p, int n, cudaStream_t st) {
-    k_adj_pred<O><<<n, AdjNT<O>::value, 0, st>>>(o, a, p);
+    using A = AdjPredCfg<O>;
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int ctas = (n + A::G - 1) / A::G;
+    const int grid = ctas < nsm ? ctas : nsm;
+    if (grid > 0) k_adj_pred<O><<<grid, A::THREADS, A::SMEM_BYTES, st>>>(o, a, p);
   }
   static void adj_nbr(const DevOps& o, const AdjLtsArgs& a, const PhaseArgs& p, int K, cudaStream_t st) {
     k_adj_nbr<O><<<K, AdjNT<O>::value, 0, st>>>(o, a, p);

@@ -212,3 +212,24 @@ def test_lts_checkpoint_spacing_does_not_change_the_result():
         s.close()
     for J, g, syn in out[1:]:
         assert J == out[0][0] and np.array_equal(g, out[0][1]) and np.array_equal(syn, out[0][2])
+
+
+def test_lts_adjoint_memory_budget_does_not_change_the_result():
+    """A segment replayed once with every phase input kept, and (a 1-byte budget) replayed
+    macro step by macro step: the same reverse sweep, bitwise."""
+    order, n_macro = 4, 4
+    m, mat, q0, rec, src = _case(order, seed=18)
+    rho, lam, mu = _rlm(mat)
+    cl = _forced_clusters(m)
+    s = _gpu_lts(order, m, rho, lam, mu, q0, rec, src, cl, 1.5e-4)
+    _, _, syn = s.misfit_gradient(4 * n_macro, np.zeros((n_macro + 1, 3, 3)), every=n_macro)
+    s.close()
+    data = syn * 1.03
+    out = []
+    for budget in (0, 1):
+        s = _gpu_lts(order, m, rho, lam, mu, q0, rec, src, cl, 1.5e-4)
+        s.set_adjoint_memory(budget)
+        out.append(s.misfit_gradient(4 * n_macro, data, every=3, want_dq0=True))
+        s.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(np.asarray(a), np.asarray(b))
