@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(AdjNT<O>::value) k_adj_step(DevOps ops, AdjArg
     }
 #pragma unroll
     for (int j = 0; j < WPT; ++j)
-      if (t + j * nt < 81) Wk[AM_STAR + c * 81 + t + j * nt] += (double)acc[j];
+      if (t + j * nt < 81) atomicAdd(Wk + AM_STAR + c * 81 + t + j * nt, (double)acc[j]);
   }
   for (int i = 0; i < 4; ++i) {
     if (t < F) {
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(AdjNT<O>::value) k_adj_step(DevOps ops, AdjArg
     for (int e = t; e < 81; e += nt) {
       float acc = 0.f;
       for (int b = 0; b < B; ++b) acc += sL[(e / 9) * B + b] * sP[0][(e % 9) * B + b];
-      Wk[AM_LOC + i * 81 + e] += (double)acc;
+      atomicAdd(Wk + AM_LOC + i * 81 + e, (double)acc);
     }
     __syncthreads();
   }
@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(AdjNT<O>::value) k_adj_step(DevOps ops, AdjArg
     for (int e = t; e < 81; e += nt) {
       float acc = 0.f;
       for (int b = 0; b < B; ++b) acc += sL[(e / 9) * B + b] * sP[0][(e % 9) * B + b];
-      Wk[AM_NBR + i * 81 + e] += (double)acc;
+      atomicAdd(Wk + AM_NBR + i * 81 + e, (double)acc);
     }
     __syncthreads();
   }
@@ -562,6 +562,34 @@ __global__ void __launch_bounds__(AdjPredCfg<O>::THREADS, 1) k_adj_pred(DevOps o
     stage<AM_SIZE, NT>(sM, a.amat + (size_t)k * AM_SIZE, t);
     stage<NB9, NT>(sL, a.lq + (size_t)k * NB9, t);
     stage<NB9, NT>(sDb, a.Qs + (size_t)k * a.qs, t);
+    {
+      // the adjoints of the buffers this pass wrote: lambda_B1 (+ lambda_B3) into sG0[0],
+      // lambda_B2 into sG0[1]; reset here (lambda_B3 survives an accumulation)
+      constexpr int R = (NB9 + NT - 1) / NT;
+      const size_t o = (size_t)k * NB9;
+      float v1[R], v2[R], v3[R];
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const int q = t + j * NT;
+        v1[j] = v2[j] = v3[j] = 0.f;
+        if (q < NB9) {
+          v1[j] = a.lb1[o + q];
+          if (coarser) v3[j] = a.lb3[o + q];
+          if (finer) v2[j] = a.lb2[o + q];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const int q = t + j * NT;
+        if (q < NB9) {
+          sG0[q] = v1[j] + v3[j];
+          sG0[NB9 + q] = v2[j];
+          a.lb1[o + q] = 0.f;
+          if (coarser && even) a.lb3[o + q] = 0.f;
+          if (finer) a.lb2[o + q] = 0.f;
+        }
+      }
+    }
     gsync<NT>(g);
     const float* S = sM + AM_STAR;
     // ---- forward time kernel: D_{d+1} = sum_c S_c D_d K_c^T on the support of D_{d+1}
@@ -691,23 +719,14 @@ __global__ void __launch_bounds__(AdjPredCfg<O>::THREADS, 1) k_adj_pred(DevOps o
 #pragma unroll
       for (int ii = 0; ii < 3; ++ii)
 #pragma unroll
-        for (int q = 0; q < 3; ++q) Wk[AM_LOC + i * 81 + (3 * rb + ii) * 9 + 3 * sb + q] += (double)acc[ii][q];
+        for (int q = 0; q < 3; ++q) atomicAdd(Wk + AM_LOC + i * 81 + (3 * rb + ii) * 9 + 3 * sb + q, (double)acc[ii][q]);
     }
     // the buffers this pass wrote
     if (t < B) {
-      const size_t o = (size_t)k * NB9 + t;
 #pragma unroll
       for (int r = 0; r < 9; ++r) {
-        mu[r] += a.lb1[o + r * B];
-        a.lb1[o + r * B] = 0.f;
-        if (coarser) {
-          mu[r] += a.lb3[o + r * B];
-          if (even) a.lb3[o + r * B] = 0.f;
-        }
-        if (finer) {
-          muh[r] = a.lb2[o + r * B];
-          a.lb2[o + r * B] = 0.f;
-        }
+        mu[r] += sG0[r * B + t];
+        muh[r] = sG0[NB9 + r * B + t];
       }
 #pragma unroll
       for (int r = 0; r < 9; ++r)
@@ -758,7 +777,7 @@ __global__ void __launch_bounds__(AdjPredCfg<O>::THREADS, 1) k_adj_pred(DevOps o
 #pragma unroll
       for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int q = 0; q < 3; ++q) Wk[AM_STAR + tc * 81 + (3 * trb + i) * 9 + 3 * tsb + q] += (double)wst[i][q];
+        for (int q = 0; q < 3; ++q) atomicAdd(Wk + AM_STAR + tc * 81 + (3 * trb + i) * 9 + 3 * tsb + q, (double)wst[i][q]);
     gsync<NT>(g);   // the group's region is refilled for its next element
   }
 }
@@ -871,9 +890,9 @@ __global__ void __launch_bounds__(AdjNT<O>::value) k_adj_nbr(DevOps ops, AdjLtsA
     const size_t o = (size_t)kn * NB9 + t;
 #pragma unroll
     for (int r = 0; r < 9; ++r) {
-      if (u1) a.lb1[o + r * B] += y1[r];
-      if (u2) a.lb2[o + r * B] += y2[r];
-      if (u3) a.lb3[o + r * B] += y3[r];
+      if (u1) atomicAdd(a.lb1 + o + r * B, y1[r]);
+      if (u2) atomicAdd(a.lb2 + o + r * B, y2[r]);
+      if (u3) atomicAdd(a.lb3 + o + r * B, y3[r]);
     }
   }
   for (int p = t; p < 36; p += nt) {
@@ -889,7 +908,7 @@ __global__ void __launch_bounds__(AdjNT<O>::value) k_adj_nbr(DevOps ops, AdjLtsA
 #pragma unroll
     for (int ii = 0; ii < 3; ++ii)
 #pragma unroll
-      for (int q = 0; q < 3; ++q) Wk[(3 * rb + ii) * 9 + 3 * sb + q] += (double)acc[ii][q];
+      for (int q = 0; q < 3; ++q) atomicAdd(Wk + (3 * rb + ii) * 9 + 3 * sb + q, (double)acc[ii][q]);
   }
 }
 
