@@ -125,6 +125,16 @@ struct PhaseArgs {
 };
 
 // ------------------------------------------------------------------ helpers
+// L2 prefetch of the DOFs a CTA's next batch reads: elements [e0, e0 + n) x qs floats
+// (one simulation), or one simulation group's NQ x B x FG block of element e0 (fused);
+// one 128-byte line per thread and step, every address inside the block.
+template <int NQ, int B, int FG, int NT>
+__device__ __forceinline__ void prefetch_batch_q(const float* Q, long long qs, int e0, int grp, int n, int tid) {
+  const float* p = Q + (size_t)e0 * qs + ((FG > 1) ? (size_t)grp * (NQ * B * FG) : 0);
+  const long long len = (FG > 1) ? (long long)NQ * B * FG : (long long)n * qs;
+  for (long long off = 32LL * tid; off < len; off += 32LL * NT) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + off));
+}
+
 // Tasks ordered by the degree of the mode column, highest first; within a degree the mode
 // varies fastest (SF = false) or the slot does (SF = true: fused simulations, so that
 // neighbouring threads touch neighbouring simulations of one DOF).
@@ -609,6 +619,13 @@ __global__ void __launch_bounds__(Cfg<O, M, FG>::NT, Cfg<O, M, FG>::PMIN) k_pred
           for (int r = 0; r < 6; ++r) q[(9 + 6 * l + r) * rs] = acc[9 + 6 * l + r] + ph.omega[l] * S[NS - 6 + r];
       }
     }
+    {
+      const int bn = batch + gridDim.x;                    // this CTA's next batch
+      if (bn < nbatch) {
+        const int en = (FG > 1) ? ph.begin + bn / nsg : ph.begin + bn * NE;
+        prefetch_batch_q<NQ, B, FG, NT>(st.Q, qs, en, (FG > 1) ? bn % nsg : 0, min(NE, ph.end - en), tid);
+      }
+    }
   }
 }
 
@@ -640,19 +657,45 @@ __global__ void __launch_bounds__(Cfg<O, M, FG>::NTN, Cfg<O, M, FG>::NMIN) k_nei
   const int nbatch = (FG > 1) ? nelem * nsg : (nelem + NE - 1) / NE;
   constexpr int rs = B * FG;
 
+  // per-element tables (face data; neighbours, codes, meta) of a batch, fetched into
+  // registers one batch ahead so that the gathers need not wait for them
+  constexpr int RD = (NEL * ND + NT - 1) / NT, RI = (NEL * 9 + NT - 1) / NT;
+  float pd[RD];
+  int pi[RI];
+  auto fetch = [&](int bt) {
+    const int f0 = (FG > 1) ? ph.begin + bt / nsg : ph.begin + bt * NE;
+#pragma unroll
+    for (int u = 0; u < RD; ++u) {
+      const int i = tid + u * NT, gg = f0 + i / ND;
+      pd[u] = (i < NEL * ND && bt < nbatch && gg < ph.end) ? __ldg(st.ndata + (size_t)gg * ND + (i % ND)) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < RI; ++u) {
+      const int i = tid + u * NT, c = i % 9, gg = f0 + i / 9;
+      int v = -1;
+      if (i < NEL * 9 && bt < nbatch && gg < ph.end)
+        v = (c < 4) ? __ldg(st.nbr + (size_t)gg * 4 + c) : (c < 8 ? __ldg(st.ncode + (size_t)gg * 4 + c - 4) : __ldg(st.meta + gg));
+      pi[u] = v;
+    }
+  };
+  fetch(blockIdx.x);
   for (int batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
     const int e0 = (FG > 1) ? ph.begin + batch / nsg : ph.begin + batch * NE;
     const int grp = (FG > 1) ? batch % nsg : 0;
     __syncthreads();
-    for (int i = tid; i < NEL * ND; i += NT) {
-      const int ee = i / ND, gg = e0 + ee;
-      sD[i] = (gg < ph.end) ? st.ndata[(size_t)gg * ND + (i % ND)] : 0.f;
-    }
-    for (int i = tid; i < NEL * 9; i += NT) {
-      const int ee = i / 9, c = i % 9, gg = e0 + ee;
-      int v = -1;
-      if (gg < ph.end) v = (c < 4) ? st.nbr[(size_t)gg * 4 + c] : (c < 8 ? st.ncode[(size_t)gg * 4 + c - 4] : st.meta[gg]);
-      sI[i] = v;
+#pragma unroll
+    for (int u = 0; u < RD; ++u)
+      if (tid + u * NT < NEL * ND) sD[tid + u * NT] = pd[u];
+#pragma unroll
+    for (int u = 0; u < RI; ++u)
+      if (tid + u * NT < NEL * 9) sI[tid + u * NT] = pi[u];
+    fetch(batch + gridDim.x);
+    {
+      const int bn = batch + gridDim.x;
+      if (bn < nbatch) {
+        const int en = (FG > 1) ? ph.begin + bn / nsg : ph.begin + bn * NE;
+        prefetch_batch_q<C::NQ, B, FG, NT>(st.Q, qs, en, (FG > 1) ? bn % nsg : 0, min(NE, ph.end - en), tid);
+      }
     }
     __syncthreads();
     const int g = e0 + ((FG > 1) ? 0 : e);
