@@ -275,6 +275,11 @@ def run_ours(args, rank, world, local_rank):
     ms, e2e_ms = float(ms_t[0]), float(ms_t[1])
     if rank != 0:
         return
+    # FP32 and tf32 throughput probes of this GPU (after the timed region)
+    try:
+        pk = s.measure_peaks()
+    except Exception as exc:   # reported, not fatal: the derived peak stays the denominator
+        pk = {"error": str(exc)}
     total_updates = per_macro * args.steps * world
     value = total_updates / (ms / 1000.0)
     hbm_gbs, sm_max, peak_src = peaks()
@@ -323,7 +328,10 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "alu", "kernel": name, "achieved": achieved_tf, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved_tf / fp32_peak, "traffic": traffic,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (derived)" % sm_max,
-                     "flops_per_element": fl, "elements_per_launch": elems_per_launch, "avg_launch_ms": avg_ms},
+                     "flops_per_element": fl, "elements_per_launch": elems_per_launch, "avg_launch_ms": avg_ms,
+                     "measured_peak": pk.get("fp32_tflops"),
+                     "frac_of_measured": (achieved_tf / pk["fp32_tflops"]) if pk.get("fp32_tflops") else None},
+        "peaks_measured": pk,
         "hbm": {"kernel": name, "achieved": achieved_gbs, "peak": hbm_gbs, "unit": "GB/s",
                 "frac": achieved_gbs / hbm_gbs, "peak_source": peak_src, "bytes_per_element": by},
         "kernel_ms": {"k_predict_local": kst["ms"][0], "k_neighbour": kst["ms"][1],

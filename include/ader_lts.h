@@ -278,6 +278,16 @@ int lts_set_finest_dt(lts_t* h, double dt);
 int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* data, double* misfit,
                         double* grad, double* synth_out, double* dq0, void* cuda_stream);
 
+/* Throughput probes of the GPU the handle runs on, for roofline denominators: FP32 FMA on
+ * the CUDA cores (8 independent FMA chains per thread, 8 CTAs of 256 threads per SM) and
+ * tcgen05 MMA of kind tf32 (M = 128, N = 256, K = 8, FP32 accumulation in tensor memory,
+ * one CTA per SM issuing back-to-back products). Each is timed with CUDA events on
+ * `cuda_stream` after one warm-up launch. out[4] = FP32 TFLOP/s, tf32 TFLOP/s, and the two
+ * timed durations in ms. Synchronises the stream. Errors: LTS_ERR_ARG (out NULL),
+ * LTS_ERR_TIMEOUT (a tensor-core wait ran out; its tensor memory is released),
+ * LTS_ERR_CUDA. */
+int lts_measure_peaks(lts_t* h, void* cuda_stream, double* out);
+
 /* Device-memory budget in bytes for the phase inputs the LTS adjoint keeps per segment
  * (see lts_misfit_gradient); 0 restores the default (half the free device memory at the
  * call). Errors: none. */

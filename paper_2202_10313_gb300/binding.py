@@ -55,6 +55,7 @@ _SIGS = {
     "lts_autotune": (_I, [_P, _I, _P, _P, _P, _P, _I, _P]),
     "lts_set_wait_limit": (_I, [_P, _L, _I]),
     "lts_set_adjoint_memory": (_I, [_P, ctypes.c_uint64]),
+    "lts_measure_peaks": (_I, [_P, _P, _P]),
     "lts_partition": (_I, [_P, _I, _P, _P]),
     "lts_cut_faces": (_I, [_P, _P, _L, _P, _P]),
     "lts_set_partition": (_I, [_P, _I, _P]),
@@ -391,6 +392,12 @@ class Solver:
 
     def set_graphs(self, enable=True):
         self._check(lib().lts_set_graphs(self._h, 1 if enable else 0))
+
+    def measure_peaks(self, stream=None):
+        """Throughput probes: dict(fp32_tflops, tf32_tflops, fp32_ms, tf32_ms)."""
+        out = (ctypes.c_double * 4)()
+        self._check(lib().lts_measure_peaks(self._h, _stream_handle(stream), out))
+        return dict(fp32_tflops=out[0], tf32_tflops=out[1], fp32_ms=out[2], tf32_ms=out[3])
 
     def set_adjoint_memory(self, nbytes=0):
         """Budget for the phase inputs the LTS adjoint keeps per checkpoint segment (0: half

@@ -15,7 +15,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libaderlts.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 HOST_SOURCES = ["host_basis.cpp", "host_mesh.cpp", "host_setup.cpp", "host_partition.cpp"]
-CUDA_SOURCES = ["api.cu", "kernels_o3.cu", "kernels_o4.cu", "kernels_o5.cu", "energy_noalloc.cu"]
+CUDA_SOURCES = ["api.cu", "kernels_o3.cu", "kernels_o4.cu", "kernels_o5.cu", "energy_noalloc.cu", "peaks.cu"]
 
 
 def _nvcc():

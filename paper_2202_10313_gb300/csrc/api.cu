@@ -1149,6 +1149,10 @@ void adjoint_lts(lts_solver* h, int64_t n_macro, int64_t every, const double* da
 
 }  // namespace
 
+namespace ltsdev {
+cudaError_t measure_peaks(cudaStream_t stream, double* out);   // peaks.cu
+}
+
 extern "C" {
 
 int lts_create(int order, int n_mech, int n_fused, int device, lts_t** out) {
@@ -2104,6 +2108,15 @@ int lts_set_graphs(lts_t* h, int enable) {
   return run(h, [&] {
     h->use_graphs = enable != 0;
     if (!h->use_graphs) release_graphs(h);
+  });
+}
+
+int lts_measure_peaks(lts_t* h, void* cuda_stream, double* out) {
+  return run(h, [&] {
+    if (!out) fail(LTS_ERR_ARG, "out is NULL");
+    const cudaError_t e = ltsdev::measure_peaks(static_cast<cudaStream_t>(cuda_stream), out);
+    if (e == cudaErrorTimeout) fail(LTS_ERR_TIMEOUT, "tensor-core peak probe did not complete within its bound");
+    if (e != cudaSuccess) fail(LTS_ERR_CUDA, std::string("peak probes: ") + cudaGetErrorString(e));
   });
 }
 
