@@ -329,6 +329,9 @@ def run_ours(args, rank, world, local_rank):
                      "frac": achieved_tf / fp32_peak, "traffic": traffic,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (derived)" % sm_max,
                      "flops_per_element": fl, "elements_per_launch": elems_per_launch, "avg_launch_ms": avg_ms,
+                     # roofline time of one launch, max(bytes / HBM, flops / FP32 peak), over its duration
+                     "roofline_time_attained": max(by * elems_per_launch / (hbm_gbs * 1e9),
+                                                   fl * elems_per_launch / (fp32_peak * 1e12)) / (avg_ms / 1000.0),
                      "measured_peak": pk.get("fp32_tflops"),
                      "frac_of_measured": (achieved_tf / pk["fp32_tflops"]) if pk.get("fp32_tflops") else None},
         "peaks_measured": pk,
