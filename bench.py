@@ -143,31 +143,33 @@ def oracle_sample(seconds_cap=25.0, steps=None):
     o.add_point_source(src["x"], src["m6"], src["f0"], src["t0"], src["m0"])
     period = 2 ** (NCLUSTERS - 1)
     per_macro = o.element_updates(period)
-    times = []
+    times, cpu = [], []
     t_all = time.time()
     n = steps if steps is not None else 10 ** 9
     for _ in range(n):
-        t0 = time.perf_counter()
+        t0, c0 = time.perf_counter(), time.process_time()
         o.run_lts(period)
         times.append(time.perf_counter() - t0)
+        cpu.append(time.process_time() - c0)
         if steps is None and time.time() - t_all > seconds_cap:
             break
-    return per_macro, times, om.K
+    return per_macro, times, om.K, cpu
 
 
-def threads_used():
-    try:
-        from threadpoolctl import threadpool_info
-        return max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
-    except Exception:
-        return os.cpu_count() or 1
+def threads_used(times, cpu):
+    """Cores the oracle actually kept busy: process CPU time over wall time of the timed
+    steps (the oracle's small products leave most of a BLAS thread pool idle)."""
+    wall = sum(times)
+    ratio = sum(cpu) / wall if wall > 0 else 1.0
+    return max(1, int(round(ratio))), ratio
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    per_macro, times, K = oracle_sample(steps=args.warmup + args.steps)
+    per_macro, times, K, cpu = oracle_sample(steps=args.warmup + args.steps)
     timed = times[args.warmup:]
+    cores, busy = threads_used(timed, cpu[args.warmup:])
     total = sum(timed)
     value = per_macro * len(timed) / total
     line = {
@@ -176,7 +178,8 @@ def run_reference(args, rank, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "anelastic O5 m3 LTS Nc=5, bounded sample %d tets of the same generator" % K,
                    "elements": K, "order": ORDER, "n_mech": NMECH, "clusters": NCLUSTERS},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads_used(), "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "cpu_time_over_wall": busy,
+                         "host_cores": os.cpu_count(), "kind": "oracle",
                          "sample": "%d-tet mesh (12x12x5 hexes) of the same generator, one macro step per step" % K},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -350,9 +353,11 @@ def run_ours(args, rank, world, local_rank):
                                  whole_buffer_bytes_per_step=pstats["buffer_msgs_per_macro"] * 9 * B * 4,
                                  **{k: v for k, v in pstats.items()})
     if not args.no_cpu_baseline and world == 1:
-        per_m, times, Ks = oracle_sample(seconds_cap=20.0)
+        per_m, times, Ks, cpu = oracle_sample(seconds_cap=20.0)
         v = per_m * len(times) / sum(times)
-        line["cpu_baseline"] = {"value": v, "unit": unit, "cores": threads_used(), "kind": "oracle",
+        cores, busy = threads_used(times, cpu)
+        line["cpu_baseline"] = {"value": v, "unit": unit, "cores": cores, "cpu_time_over_wall": busy,
+                                "host_cores": os.cpu_count(), "kind": "oracle",
                                 "sample": "%d macro steps of a %d-tet mesh (12x12x5 hexes) of the same generator"
                                           % (len(times), Ks)}
     print(json.dumps(line), flush=True)
