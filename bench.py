@@ -304,7 +304,9 @@ def run_ours(args, rank, world, local_rank):
         ent = t.get(name)
         if F > 1:
             ent = t.get(name + "_fused%d" % F)
-        if ent and ent.get("kernel_hash") == kernel_hash():
+        # only for the kernel instantiation the counters were taken on
+        if (ent and ent.get("kernel_hash") == kernel_hash() and ent.get("order") == order
+                and ent.get("n_mech") == nmech):
             traffic = ent["dram_bytes_per_element"] * elems_per_launch
     metric, unit = METRIC, UNIT
     if args.elastic:
