@@ -134,3 +134,28 @@ def test_fused_subset_access_and_projection_broadcast():
     assert np.allclose(back, sub.astype(np.float32), rtol=0, atol=0)
     full = g.get_dofs()
     assert np.array_equal(full[:, elems], back)
+
+
+def test_maximum_fused_count():
+    """LTS_MAX_FUSED (64) simulations in one run (16 CTA groups per element): simulations at
+    both ends and in the middle match their single-simulation GPU runs."""
+    m, mat = _case(seed=37)
+    F, order, n_mech = 64, 3, 3
+    pos, m6, f0, d0 = _inputs(m, F, 27, 10, seed=91)
+    g = _fused_solver(order, n_mech, m, mat, F)
+    for f in range(F):
+        g.add_point_source(pos[f], m6[f], f0[f], 0.1, 1e12, fused_idx=f)
+    g.setup_clusters(2, 0.5)
+    g.set_dofs(d0)
+    g.advance_steps(4)
+    got = g.get_dofs()
+    assert np.all(np.isfinite(got))
+    for f in (0, 1, 31, 62, 63):
+        s, _, _ = make_pair(order, n_mech, m, mat)
+        s.add_point_source(pos[f], m6[f], f0[f], 0.1, 1e12)
+        s.setup_clusters(2, 0.5)
+        s.set_dofs(d0[f])
+        s.advance_steps(4)
+        one = s.get_dofs()
+        s.close()
+        assert np.sqrt(np.sum((got[f] - one) ** 2)) / np.sqrt(np.sum(one ** 2)) <= 1e-6, f
