@@ -41,3 +41,10 @@ def initial_field(nq, center, width, plane=None):
         return v
 
     return fn
+
+
+def report_parity(case, errors):
+    """One line per parity case (run pytest with -s to see them): the worst relative L2
+    error against the FP64 oracle per quantity group."""
+    import json
+    print("PARITY " + json.dumps({"case": case, **{k: float(v) for k, v in errors.items()}}))

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from paper_2202_10313_gb300 import binding, build, synth
-from gpu_common import initial_field, make_pair, rel_l2_groups
+from gpu_common import initial_field, make_pair, rel_l2_groups, report_parity
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-4
@@ -47,7 +47,7 @@ def test_periodic_cube_order3_gts_plane_wave_50_steps():
     assert abs(info["finest_dt"] / dt - 1) < 1e-12
     gpu.advance_steps(50)
     ora.run_gts(dt, 50)
-    _check(gpu, ora)
+    report_parity("periodic cube, 3,072 tets, O3 elastic, P plane wave, GTS, 50 steps", _check(gpu, ora))
     assert abs(gpu.energy() / ora.energy() - 1) < 1e-5
 
 
@@ -69,7 +69,8 @@ def test_graded_box_lts_auto_clusters(order, n_mech):
     n = 2 * 2 ** (nc - 1)
     gpu.advance_steps(n)
     ora.run_lts(n)
-    _check(gpu, ora)
+    report_parity("graded box, %d tets, O%d, %d mechanisms, 3 clusters, 2 macro steps" % (m["tet"].shape[0], order, n_mech),
+                  _check(gpu, ora))
 
 
 def test_forced_clusters_with_all_relations():
