@@ -233,3 +233,47 @@ def test_lts_adjoint_memory_budget_does_not_change_the_result():
         s.close()
     for a, b in zip(out[0], out[1]):
         assert np.array_equal(np.asarray(a), np.asarray(b))
+
+
+def test_gpu_adjoint_periodic_cube_matches_oracle_adjoint():
+    """Periodic faces (every face has a neighbour, some across the box) and a heterogeneous
+    material: the GTS adjoint's misfit, gradients and dJ/dQ0 against the oracle's adjoint."""
+    order, n = 3, 6
+    m = synth.permute_vertex_order(synth.periodic_cube(3, 1000.0), seed=3)
+    K = m["tet"].shape[0]
+    rng = np.random.default_rng(4)
+    rho = 2700.0 * (1.0 + 0.1 * rng.uniform(-1.0, 1.0, K))
+    vs = 3464.0 * (1.0 + 0.05 * rng.uniform(-1.0, 1.0, K))
+    vp = 6000.0 * (1.0 + 0.05 * rng.uniform(-1.0, 1.0, K))
+    mu = rho * vs ** 2
+    lam = rho * vp ** 2 - 2 * mu
+    nb = order * (order + 1) * (order + 2) // 6
+    q0 = synth.random_dofs(K, 9, nb, seed=6)
+    rec = [np.array([250.0, 400.0, 600.0]), np.array([700.0, 300.0, 200.0])]
+    om = Mesh(m["xyz"], m["tet"], m["face_bc"], m["period"])
+
+    def oracle(mu_):
+        o = Oracle(order, 0, om, rho, np.sqrt((lam + 2 * mu_) / rho), np.sqrt(mu_ / rho))
+        o.Q = q0.copy()
+        return o
+
+    dt = oracle(mu).time_step_gts(0.5)
+    re = [om.locate(x) for x in rec]
+    o = oracle(mu * 1.02)
+    rp = [o.basis.phi(om.xi_of(k, x)[None, :])[0] for k, x in zip(re, rec)]
+    _, _, _, data = oracle_misfit_gradient(o, dt, n, re, rp, np.zeros((n + 1, 2, 3)))
+    J0, g0, dq0_o, syn0 = oracle_misfit_gradient(oracle(mu), dt, n, re, rp, data)
+    s = binding.Solver(order, 0, device=0)
+    s.set_mesh(m["xyz"], m["tet"], m["face_bc"], m["period"])
+    s.set_material(rho, np.sqrt((lam + 2 * mu) / rho), np.sqrt(mu / rho))
+    for x in rec:
+        s.add_receiver(x, dt)
+    s.setup_clusters(1, 0.5)
+    s.set_finest_dt(dt)
+    s.set_dofs(q0)
+    J, g, syn, dq0 = s.misfit_gradient(n, data, every=2, want_dq0=True)
+    assert _rel(syn, syn0) <= 1e-5
+    assert abs(J / J0 - 1) <= 1e-3
+    for p in range(3):
+        assert _rel(g[:, p], g0[:, p]) <= 2e-3, (p, _rel(g[:, p], g0[:, p]))
+    assert _rel(dq0, dq0_o) <= 2e-3
