@@ -257,8 +257,12 @@ int lts_set_finest_dt(lts_t* h, double dt);
  * with respect to the neighbour's. Outputs (each may be NULL except data): *misfit J,
  * grad[n_tet][3] = dJ/d(rho, lambda, mu) per element (original order), synth_out[N+1][n_rec][3]
  * the samples, dq0[n_tet][9][B] = dJ/dQ at the start. The time step is held fixed. The
- * state ends at t_N (as after lts_advance_steps). Needs n_mech = 0, one simulation, no
- * partition, at least one receiver. With one cluster (global time stepping): Device
+ * state ends at t_N (as after lts_advance_steps). Needs n_mech = 0, no partition, at least
+ * one receiver. Fused simulations (n_fused = F > 1: each its own sources and initial state,
+ * the material shared): data and synth_out [..][F][n_rec][3] (simulation before receiver),
+ * dq0[F][n_tet][9][B], and J and grad summed over the simulations — the gradient of the
+ * summed misfit, as for several sources of one inversion; fused runs take the clustered
+ * (phase-level) sweep below for any cluster count. With one cluster (global time stepping): Device
  * memory: (ceil(N/every) + min(every, N) + 1) copies of Q plus per-element operators.
  * With clustered LTS (N_c > 1) the same holds per macro step: n_steps is a multiple of
  * 2^(N_c-1), the samples are taken at the macro-step boundaries (data[M+1][n_rec][3],

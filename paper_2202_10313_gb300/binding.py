@@ -363,13 +363,16 @@ class Solver:
 
     def misfit_gradient(self, n_steps, data, every=100, stream=None, want_dq0=False, want_grad=True):
         """J, dJ/d(rho, lambda, mu) (K, 3), synthetic samples (shape of data: one row per
-        sample time, n_rec, 3) and optionally dJ/dQ at the start (K, 9, B), by the discrete
-        adjoint of the time loop (GTS: samples every step; LTS: every macro step)."""
+        sample time, then n_rec, 3; fused: sample time, F, n_rec, 3) and optionally dJ/dQ at the
+        start ((K, 9, B); fused (F, K, 9, B)), by the discrete adjoint of the time loop (GTS:
+        samples every step; LTS: every macro step). Fused runs give J and the gradient summed
+        over the simulations."""
         data = np.ascontiguousarray(data, dtype=np.float64)
         J = ctypes.c_double()
         grad = np.zeros((self.K, 3))
         syn = np.zeros(data.shape)
-        dq0 = np.zeros((self.K, 9, self.nb)) if want_dq0 else None
+        shape = (self.K, 9, self.nb) if self.n_fused == 1 else (self.n_fused, self.K, 9, self.nb)
+        dq0 = np.zeros(shape) if want_dq0 else None
         self._check(lib().lts_misfit_gradient(self._h, int(n_steps), int(every), _ptr(data), ctypes.byref(J),
                                               _ptr(grad) if want_grad else None, _ptr(syn), _ptr(dq0),
                                               _stream_handle(stream)))

@@ -943,11 +943,15 @@ void adjoint_lts(lts_solver* h, int64_t n_macro, int64_t every, const double* da
   const int64_t period = int64_t(1) << (h->nc - 1);
   const int64_t ncp = (n_macro + every - 1) / every;
   const int64_t segm = std::min(every, n_macro);
+  // fused runs: nsim simulations in groups of G; samples [time][sim][receiver][3], adjoints
+  // [element][sim][9][B]
+  const int nsim = h->nsim, G = nsim > 1 ? X.FG : 1;
+  const int64_t ns = (int64_t)nsim * nrec * 3;   // sample values per sample time
   DevBuf d_syn, d_res, d_lq, d_lb, d_w, d_cp, d_mac, d_qn;
-  d_syn.alloc(sizeof(float) * (n_macro + 1) * nrec * 3);
-  d_res.alloc(sizeof(float) * (n_macro + 1) * nrec * 3);
-  d_lq.alloc(sizeof(float) * K * NB9);
-  d_lb.alloc(sizeof(float) * 3 * K * NB9);
+  d_syn.alloc(sizeof(float) * (n_macro + 1) * ns);
+  d_res.alloc(sizeof(float) * (n_macro + 1) * ns);
+  d_lq.alloc(sizeof(float) * K * nsim * NB9);
+  d_lb.alloc(sizeof(float) * 3 * K * nsim * NB9);
   d_w.alloc(sizeof(double) * K * ltsdev::AM_SIZE);
   d_cp.alloc(sizeof(float) * ncp * K * qs);
   d_qn.alloc(sizeof(float) * K * qs);
@@ -961,16 +965,16 @@ void adjoint_lts(lts_solver* h, int64_t n_macro, int64_t every, const double* da
   // ---- forward sweep: samples at the macro boundaries, checkpoints
   const int64_t s0 = h->s_now;
   std::vector<size_t> nrec_t(nrec);
-  X.adj_sample(h->dst.Q, qs, relem, rphi, nrec, d_syn.get<float>(), stream);
+  X.adj_sample(h->dst.Q, qs, nsim, G, relem, rphi, nrec, d_syn.get<float>(), stream);
   for (int64_t m = 0; m < n_macro; ++m) {
     if (m % every == 0) dcopy(cp + (m / every) * K * qs, h->dst.Q, qbytes);
     advance_steps(h, period, stream);
-    X.adj_sample(h->dst.Q, qs, relem, rphi, nrec, d_syn.get<float>() + (m + 1) * nrec * 3, stream);
+    X.adj_sample(h->dst.Q, qs, nsim, G, relem, rphi, nrec, d_syn.get<float>() + (m + 1) * ns, stream);
   }
   for (int r = 0; r < nrec; ++r) nrec_t[r] = h->receivers[r].t.size();
   const size_t seis_fwd = h->seis_used;
   dcopy(d_qn.p, h->dst.Q, qbytes);
-  std::vector<float> syn((size_t)(n_macro + 1) * nrec * 3);
+  std::vector<float> syn((size_t)(n_macro + 1) * ns);
   ck(cudaMemcpyAsync(syn.data(), d_syn.p, sizeof(float) * syn.size(), cudaMemcpyDeviceToHost, stream), "samples");
   ck(cudaStreamSynchronize(stream), "synchronize");
   check_device_error(h);
@@ -987,15 +991,17 @@ void adjoint_lts(lts_solver* h, int64_t n_macro, int64_t every, const double* da
   if (!grad && !dq0) return;       // misfit only: no reverse sweep
   ck(cudaMemcpyAsync(d_res.p, res.data(), sizeof(float) * res.size(), cudaMemcpyHostToDevice, stream), "residuals");
   // ---- reverse sweep
-  ck(cudaMemsetAsync(d_lq.p, 0, sizeof(float) * K * NB9, stream), "memset");
-  ck(cudaMemsetAsync(d_lb.p, 0, sizeof(float) * 3 * K * NB9, stream), "memset");
+  ck(cudaMemsetAsync(d_lq.p, 0, sizeof(float) * K * nsim * NB9, stream), "memset");
+  ck(cudaMemsetAsync(d_lb.p, 0, sizeof(float) * 3 * K * nsim * NB9, stream), "memset");
   ck(cudaMemsetAsync(d_w.p, 0, sizeof(double) * K * ltsdev::AM_SIZE, stream), "memset");
-  X.adj_source(d_lq.get<float>(), relem, rphi, d_res.get<float>() + n_macro * nrec * 3, nrec, stream);
+  X.adj_source(d_lq.get<float>(), nsim, relem, rphi, d_res.get<float>() + n_macro * ns, nrec, stream);
   ltsdev::AdjLtsArgs aa{};
   aa.lq = d_lq.get<float>();
   aa.lb1 = d_lb.get<float>();
-  aa.lb2 = aa.lb1 + K * NB9;
-  aa.lb3 = aa.lb2 + K * NB9;
+  aa.lb2 = aa.lb1 + K * nsim * NB9;
+  aa.lb3 = aa.lb2 + K * nsim * NB9;
+  aa.nsim = nsim;
+  aa.G = G;
   aa.amat = d_amat.get<float>();
   aa.fwd = d_fwd.get<int>();
   aa.back = d_back.get<int>();
@@ -1061,7 +1067,7 @@ void adjoint_lts(lts_solver* h, int64_t n_macro, int64_t every, const double* da
         X.adj_nbr(h->dops, aa, pa, owners, stream);
       }
     }
-    X.adj_source(d_lq.get<float>(), relem, rphi, d_res.get<float>() + m * nrec * 3, nrec, stream);
+    X.adj_source(d_lq.get<float>(), nsim, relem, rphi, d_res.get<float>() + m * ns, nrec, stream);
   };
   // forward replay of macro step m, keeping every phase's inputs in `snap`
   auto replay_macro = [&](int64_t m, char* snap) {
@@ -1133,7 +1139,7 @@ void adjoint_lts(lts_solver* h, int64_t n_macro, int64_t every, const double* da
   ck(cudaMemcpyAsync(W.data(), d_w.p, sizeof(double) * W.size(), cudaMemcpyDeviceToHost, stream), "correlations");
   std::vector<float> lq;
   if (dq0) {
-    lq.resize((size_t)K * NB9);
+    lq.resize((size_t)K * nsim * NB9);
     ck(cudaMemcpyAsync(lq.data(), d_lq.p, sizeof(float) * lq.size(), cudaMemcpyDeviceToHost, stream), "adjoint state");
   }
   ck(cudaStreamSynchronize(stream), "synchronize");
@@ -1141,9 +1147,11 @@ void adjoint_lts(lts_solver* h, int64_t n_macro, int64_t every, const double* da
   if (misfit) *misfit = J;
   if (synth_out)
     for (size_t q = 0; q < syn.size(); ++q) synth_out[q] = syn[q];
-  if (dq0)
-    for (int64_t k = 0; k < K; ++k)
-      for (int q = 0; q < NB9; ++q) dq0[k * NB9 + q] = lq[h->iperm[k] * NB9 + q];
+  if (dq0)   // [sim][element (original order)][9][B]
+    for (int f = 0; f < nsim; ++f)
+      for (int64_t k = 0; k < K; ++k)
+        for (int q = 0; q < NB9; ++q)
+          dq0[((size_t)f * K + k) * NB9 + q] = lq[((size_t)h->iperm[k] * nsim + f) * NB9 + q];
   if (grad) contract_gradient(h, W, grad);
 }
 
@@ -1918,8 +1926,8 @@ int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* 
   return run(h, [&] {
     if (!h->ready) fail(LTS_ERR_STATE, "clusters not set up");
     const Launchers& X = h->L;
-    if (h->nmech != 0 || h->nsim != 1 || h->n_parts > 1 || !X.adj_step)
-      fail(LTS_ERR_ARG, "the adjoint covers the elastic equations, one simulation, no partition");
+    if (h->nmech != 0 || h->n_parts > 1 || !X.adj_pred)
+      fail(LTS_ERR_ARG, "the adjoint covers the elastic equations without a partition");
     const int64_t period = int64_t(1) << (h->nc - 1);
     if (h->nc > 1 && n_steps % period != 0) fail(LTS_ERR_ARG, "n_steps must be a multiple of the macro step");
     const int nrec = (int)h->receivers.size();
@@ -1978,7 +1986,9 @@ int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* 
     up(d_rphi.p, rphi.data(), sizeof(float) * rphi.size());
     AdjTables tabs;
     make_adj_tables(h, tabs);
-    if (h->nc > 1) {
+    // clustered runs, and fused runs with any cluster count (one cluster: a macro step is
+    // one step), take the phase-level sweep; one simulation with one cluster the step-level one
+    if (h->nc > 1 || h->nsim > 1) {
       adjoint_lts(h, n_steps / period, every, data, misfit, grad, synth_out, dq0, stream, d_amat, d_fwd, d_back,
                   d_relem, d_rphi, nrec, tabs);
       return;
@@ -2002,11 +2012,11 @@ int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* 
     const int64_t s0 = h->s_now;
     std::vector<size_t> nrec_t(nrec);
     dcopy(cp, h->dst.Q);
-    X.adj_sample(h->dst.Q, qs, d_relem.get<int>(), d_rphi.get<float>(), nrec, d_syn.get<float>(), stream);
+    X.adj_sample(h->dst.Q, qs, 1, 1, d_relem.get<int>(), d_rphi.get<float>(), nrec, d_syn.get<float>(), stream);
     for (int64_t n = 0; n < n_steps; ++n) {
       advance_steps(h, 1, stream);
-      X.adj_sample(h->dst.Q, qs, d_relem.get<int>(), d_rphi.get<float>(), nrec, d_syn.get<float>() + (n + 1) * nrec * 3,
-                   stream);
+      X.adj_sample(h->dst.Q, qs, 1, 1, d_relem.get<int>(), d_rphi.get<float>(), nrec,
+                   d_syn.get<float>() + (n + 1) * nrec * 3, stream);
       if ((n + 1) % every == 0 && n + 1 < n_steps) dcopy(cp + ((n + 1) / every) * K * qs, h->dst.Q);
     }
     for (int r = 0; r < nrec; ++r) nrec_t[r] = h->receivers[r].t.size();
@@ -2035,7 +2045,7 @@ int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* 
     ck(cudaMemsetAsync(d_w.p, 0, sizeof(double) * K * ltsdev::AM_SIZE, stream), "memset");
     float* lam_a = d_la.get<float>();
     float* lam_b = d_lb.get<float>();
-    X.adj_source(lam_a, d_relem.get<int>(), d_rphi.get<float>(), d_res.get<float>() + n_steps * nrec * 3, nrec,
+    X.adj_source(lam_a, 1, d_relem.get<int>(), d_rphi.get<float>(), d_res.get<float>() + n_steps * nrec * 3, nrec,
                  stream);
     AdjArgs aa{};
     aa.tbuf = d_t.get<float>();
@@ -2072,7 +2082,7 @@ int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* 
         aa.lam_out = lam_b;
         X.adj_step(h->dops, aa, (int)K, stream);
         std::swap(lam_a, lam_b);
-        X.adj_source(lam_a, d_relem.get<int>(), d_rphi.get<float>(), d_res.get<float>() + n * nrec * 3, nrec, stream);
+        X.adj_source(lam_a, 1, d_relem.get<int>(), d_rphi.get<float>(), d_res.get<float>() + n * nrec * 3, nrec, stream);
       }
       for (int r = 0; r < nrec; ++r) {
         h->receivers[r].t.resize(nrec_t[r]);

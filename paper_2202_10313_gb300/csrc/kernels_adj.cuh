@@ -381,28 +381,34 @@ __global__ void __launch_bounds__(AdjNT<O>::value) k_adj_step(DevOps ops, AdjArg
   }
 }
 
-// Velocity at the receivers from Q^n: out[r][q] = sum_b Q[elem_r][6+q][b] phi_r[b].
+// Velocity at the receivers from Q^n: out[f][r][q] = sum_b Q_f[elem_r][6+q][b] phi_r[b] for
+// the nsim simulations of an (elastic) state in groups of G (simulation f of element k, row
+// q, mode b at k qs + (f / G) 9 B G + (q B + b) G + f % G; G = 1 for one simulation).
 template <int O>
-__global__ void k_adj_sample(const float* Q, long long qs, const int* elem, const float* phi, int nrec, float* out) {
+__global__ void k_adj_sample(const float* Q, long long qs, int nsim, int G, const int* elem, const float* phi,
+                             int nrec, float* out) {
   constexpr int B = nbasis(O);
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 3 * nrec) return;
-  const int r = t / 3, q = t % 3;
-  const float* row = Q + (size_t)elem[r] * qs + (6 + q) * B;
+  if (t >= 3 * nrec * nsim) return;
+  const int f = t / (3 * nrec), r = (t / 3) % nrec, q = t % 3;
+  const float* row = Q + (size_t)elem[r] * qs + (size_t)(f / G) * (9 * B * G) + f % G + (size_t)(6 + q) * B * G;
   float v = 0.f;
-  for (int b = 0; b < B; ++b) v = fmaf(row[b], phi[r * B + b], v);
+  for (int b = 0; b < B; ++b) v = fmaf(row[(size_t)b * G], phi[r * B + b], v);
   out[t] = v;
 }
 
-// The misfit's source: lambda[elem_r][6+q][b] += res[r][q] phi_r[b] (receivers in order, so
-// receivers that share an element add in a fixed order).
+// The misfit's source: lambda_f[elem_r][6+q][b] += res[f][r][q] phi_r[b], lambda laid out
+// [element][simulation][9][B] (receivers in order, so receivers that share an element add
+// in a fixed order).
 template <int O>
-__global__ void k_adj_source(float* lam, const int* elem, const float* phi, const float* res, int nrec) {
+__global__ void k_adj_source(float* lam, int nsim, const int* elem, const float* phi, const float* res, int nrec) {
   constexpr int B = nbasis(O);
   const int b = threadIdx.x;
   if (b >= B) return;
-  for (int r = 0; r < nrec; ++r)
-    for (int q = 0; q < 3; ++q) lam[(size_t)elem[r] * 9 * B + (6 + q) * B + b] += res[r * 3 + q] * phi[r * B + b];
+  for (int f = 0; f < nsim; ++f)
+    for (int r = 0; r < nrec; ++r)
+      for (int q = 0; q < 3; ++q)
+        lam[((size_t)elem[r] * nsim + f) * 9 * B + (6 + q) * B + b] += res[(f * nrec + r) * 3 + q] * phi[r * B + b];
 }
 
 
@@ -428,6 +434,11 @@ struct AdjLtsArgs {
   const float *KT, *FtT, *FhT, *FbT;  // transposed operator tables (see AdjTables)
   long long qs, bufs;
   int end;                            // active elements [0, end)
+  // simulations of a fused run, in groups of G in the state and buffer snapshots (element k,
+  // simulation f, row r, mode b at k qs + (f / G) 9 B G + (r B + b) G + f % G; one
+  // simulation: nsim = G = 1); the adjoints are [element][simulation][9][B] and W sums the
+  // simulations' correlations
+  int nsim, G;
 };
 
 // y += S x (TR = false) or y += S^T x (TR = true) for an elastic star matrix S (row-major
@@ -454,6 +465,19 @@ __device__ __forceinline__ void stage(float* dst, const float* __restrict__ src,
 #pragma unroll
   for (int j = 0; j < R; ++j)
     if (t + j * NT < N) v[j] = __ldg(src + t + j * NT);
+#pragma unroll
+  for (int j = 0; j < R; ++j)
+    if (t + j * NT < N) dst[t + j * NT] = v[j];
+}
+
+// dst[q] = src[q G] for q < N (one simulation of a fused block), loads issued first.
+template <int N, int NT>
+__device__ __forceinline__ void stage_strided(float* dst, const float* __restrict__ src, int G, int t) {
+  constexpr int R = (N + NT - 1) / NT;
+  float v[R];
+#pragma unroll
+  for (int j = 0; j < R; ++j)
+    if (t + j * NT < N) v[j] = __ldg(src + (size_t)(t + j * NT) * G);
 #pragma unroll
   for (int j = 0; j < R; ++j)
     if (t + j * NT < N) dst[t + j * NT] = v[j];
@@ -560,225 +584,234 @@ __global__ void __launch_bounds__(AdjPredCfg<O>::THREADS, 1) k_adj_pred(DevOps o
     const bool finer = meta & FLAG_FINER, coarser = meta & FLAG_COARSER;
     const bool even = ph.parity[cl] == 0;
     stage<AM_SIZE, NT>(sM, a.amat + (size_t)k * AM_SIZE, t);
-    stage<NB9, NT>(sL, a.lq + (size_t)k * NB9, t);
-    stage<NB9, NT>(sDb, a.Qs + (size_t)k * a.qs, t);
-    {
-      // the adjoints of the buffers this pass wrote: lambda_B1 (+ lambda_B3) into sG0[0],
-      // lambda_B2 into sG0[1]; reset here (lambda_B3 survives an accumulation)
-      constexpr int R = (NB9 + NT - 1) / NT;
-      const size_t o = (size_t)k * NB9;
-      float v1[R], v2[R], v3[R];
-#pragma unroll
-      for (int j = 0; j < R; ++j) {
-        const int q = t + j * NT;
-        v1[j] = v2[j] = v3[j] = 0.f;
-        if (q < NB9) {
-          v1[j] = a.lb1[o + q];
-          if (coarser) v3[j] = a.lb3[o + q];
-          if (finer) v2[j] = a.lb2[o + q];
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < R; ++j) {
-        const int q = t + j * NT;
-        if (q < NB9) {
-          sG0[q] = v1[j] + v3[j];
-          sG0[NB9 + q] = v2[j];
-          a.lb1[o + q] = 0.f;
-          if (coarser && even) a.lb3[o + q] = 0.f;
-          if (finer) a.lb2[o + q] = 0.f;
-        }
-      }
-    }
-    gsync<NT>(g);
-    const float* S = sM + AM_STAR;
-    // ---- forward time kernel: D_{d+1} = sum_c S_c D_d K_c^T on the support of D_{d+1}
-#pragma unroll
-    for (int d = 0; d < O - 1; ++d) {
-      const int nin = nbasis(O - d), nout = nbasis(O - 1 - d);
-      if (t < B) {
-        float Y[3][9];
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-          for (int s = 0; s < 9; ++s) Y[c][s] = 0.f;
-        if (t < nout)
-#pragma unroll 4
-          for (int kk = 0; kk < nin; ++kk)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              const float kc = tKT[(c * B + kk) * B + t];
-#pragma unroll
-              for (int s = 0; s < 9; ++s) Y[c][s] = fmaf(sDb[(d) * NB9 + s * B + kk], kc, Y[c][s]);
-            }
-        float v[9];
-#pragma unroll
-        for (int r = 0; r < 9; ++r) v[r] = 0.f;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) star_acc<false>(S + c * 81, Y[c], v);
-#pragma unroll
-        for (int r = 0; r < 9; ++r) sDb[(d + 1) * NB9 + r * B + t] = v[r];
-      }
-      gsync<NT>(g);
-    }
-    float mu[9], muh[9];
-#pragma unroll
-    for (int r = 0; r < 9; ++r) mu[r] = muh[r] = 0.f;
-    float* sV = sScr;
-    if (t < B) {
-#pragma unroll
-      for (int r = 0; r < 9; ++r) {
-        float v = 0.f;
-        for (int d = 0; d < O; ++d) v = fmaf(ph.coef[cl][d], sDb[(d) * NB9 + r * B + t], v);
-        sT[r * B + t] = v;
-      }
-      // V_c = lambda K_c^T and the volume term
-      float V[3][9];
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int s = 0; s < 9; ++s) V[c][s] = 0.f;
-#pragma unroll 4
-      for (int b = 0; b < B; ++b)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const float kc = tKT[(c * B + b) * B + t];
-#pragma unroll
-          for (int s = 0; s < 9; ++s) V[c][s] = fmaf(sL[s * B + b], kc, V[c][s]);
-        }
-      float w[9];
-#pragma unroll
-      for (int r = 0; r < 9; ++r) w[r] = 0.f;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        star_acc<true>(S + c * 81, V[c], w);
-#pragma unroll
-        for (int s = 0; s < 9; ++s) sV[c * NB9 + s * B + t] = V[c][s];
-      }
-#pragma unroll
-      for (int r = 0; r < 9; ++r) mu[r] = -w[r];
-    }
-    gsync<NT>(g);
-    // star correlations, one 3 x 3 tile (c, row block, column block) per thread t < 27
+    double* Wk = a.W + (size_t)k * AM_SIZE;
+    // star correlations summed over the simulations, one 3 x 3 tile (c, row block, column
+    // block) per thread t < 27
     const int tc = t / 9, trb = (t / 3) % 3, tsb = t % 3;
     float wst[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int q = 0; q < 3; ++q) wst[i][q] = 0.f;
-    if (t < 27) {
-      tile33<B>(sV + tc * NB9, sT, 3 * trb, 3 * tsb, B, wst);
+    for (int sim = 0; sim < a.nsim; ++sim) {
+      const size_t kf = (size_t)k * a.nsim + sim;
+      stage<NB9, NT>(sL, a.lq + kf * NB9, t);
+      stage_strided<NB9, NT>(sDb, a.Qs + (size_t)k * a.qs + (size_t)(sim / a.G) * (NB9 * a.G) + sim % a.G, a.G, t);
+      {
+        // the adjoints of the buffers this pass wrote: lambda_B1 (+ lambda_B3) into sG0[0],
+        // lambda_B2 into sG0[1]; reset here (lambda_B3 survives an accumulation)
+        constexpr int R = (NB9 + NT - 1) / NT;
+        const size_t o = kf * NB9;
+        float v1[R], v2[R], v3[R];
 #pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) wst[i][q] = -wst[i][q];
-    }
-    gsync<NT>(g);
-    // local surface: LF_i = lambda F^_i^T, TF_i = T F~_i, U_i = A-_i^T LF_i, per (face, f)
-    float* sLF = sScr;
-    float* sTF = sScr + 36 * F;
-    float* sU = sScr + 72 * F;
-    for (int p = t; p < 4 * F; p += NT) {
-      const int i = p / F, f = p % F;
-      float lf[9], tf[9], u[9];
-      rows9s<B, B>(sL, tFhT + i * B * F, F, f, lf);
-      rows9s<B, B>(sT, tFt + i * B * F, F, f, tf);
-      const float* Am = sM + AM_LOC + i * 81;
-#pragma unroll
-      for (int r = 0; r < 9; ++r) {
-        float v = 0.f;
-#pragma unroll
-        for (int s = 0; s < 9; ++s) v = fmaf(Am[s * 9 + r], lf[s], v);
-        u[r] = v;
-      }
-#pragma unroll
-      for (int r = 0; r < 9; ++r) {
-        sLF[(i * 9 + r) * F + f] = lf[r];
-        sTF[(i * 9 + r) * F + f] = tf[r];
-        sU[(i * 9 + r) * F + f] = u[r];
-      }
-    }
-    gsync<NT>(g);
-    if (t < B)
-      for (int i = 0; i < 4; ++i)
-#pragma unroll 5
-        for (int f = 0; f < F; ++f) {
-          const float w = tFtT[(i * F + f) * B + t];
-#pragma unroll
-          for (int r = 0; r < 9; ++r) mu[r] = fmaf(sU[(i * 9 + r) * F + f], w, mu[r]);
+        for (int j = 0; j < R; ++j) {
+          const int q = t + j * NT;
+          v1[j] = v2[j] = v3[j] = 0.f;
+          if (q < NB9) {
+            v1[j] = a.lb1[o + q];
+            if (coarser) v3[j] = a.lb3[o + q];
+            if (finer) v2[j] = a.lb2[o + q];
+          }
         }
-    double* Wk = a.W + (size_t)k * AM_SIZE;
-    for (int p = t; p < 36; p += NT) {
-      const int i = p / 9, rb = (p / 3) % 3, sb = p % 3;
-      float acc[3][3];
 #pragma unroll
-      for (int ii = 0; ii < 3; ++ii)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) acc[ii][q] = 0.f;
-      tile33<F>(sLF + i * 9 * F, sTF + i * 9 * F, 3 * rb, 3 * sb, F, acc);
-#pragma unroll
-      for (int ii = 0; ii < 3; ++ii)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) atomicAdd(Wk + AM_LOC + i * 81 + (3 * rb + ii) * 9 + 3 * sb + q, (double)acc[ii][q]);
-    }
-    // the buffers this pass wrote
-    if (t < B) {
-#pragma unroll
-      for (int r = 0; r < 9; ++r) {
-        mu[r] += sG0[r * B + t];
-        muh[r] = sG0[NB9 + r * B + t];
+        for (int j = 0; j < R; ++j) {
+          const int q = t + j * NT;
+          if (q < NB9) {
+            sG0[q] = v1[j] + v3[j];
+            sG0[NB9 + q] = v2[j];
+            a.lb1[o + q] = 0.f;
+            if (coarser && even) a.lb3[o + q] = 0.f;
+            if (finer) a.lb2[o + q] = 0.f;
+          }
+        }
       }
+      gsync<NT>(g);
+      const float* S = sM + AM_STAR;
+      // ---- forward time kernel: D_{d+1} = sum_c S_c D_d K_c^T on the support of D_{d+1}
 #pragma unroll
-      for (int r = 0; r < 9; ++r)
-        sG0[((O - 1) & 1) * NB9 + r * B + t] = ph.coef[cl][O - 1] * mu[r] + ph.hcoef[cl][O - 1] * muh[r];
-    }
-    gsync<NT>(g);
-    // ---- reverse time kernel
-    float* sZ = sScr;
+      for (int d = 0; d < O - 1; ++d) {
+        const int nin = nbasis(O - d), nout = nbasis(O - 1 - d);
+        if (t < B) {
+          float Y[3][9];
 #pragma unroll
-    for (int d = O - 2; d >= 0; --d) {
-      const int nk = nbasis(O - 1 - d), nout = nbasis(O - d);
-      const float* Gn = (sG0 + ((d + 1) & 1) * NB9);
+          for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int s = 0; s < 9; ++s) Y[c][s] = 0.f;
+          if (t < nout)
+#pragma unroll 4
+            for (int kk = 0; kk < nin; ++kk)
+#pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                const float kc = tKT[(c * B + kk) * B + t];
+#pragma unroll
+                for (int s = 0; s < 9; ++s) Y[c][s] = fmaf(sDb[(d) * NB9 + s * B + kk], kc, Y[c][s]);
+              }
+          float v[9];
+#pragma unroll
+          for (int r = 0; r < 9; ++r) v[r] = 0.f;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) star_acc<false>(S + c * 81, Y[c], v);
+#pragma unroll
+          for (int r = 0; r < 9; ++r) sDb[(d + 1) * NB9 + r * B + t] = v[r];
+        }
+        gsync<NT>(g);
+      }
+      float mu[9], muh[9];
+#pragma unroll
+      for (int r = 0; r < 9; ++r) mu[r] = muh[r] = 0.f;
+      float* sV = sScr;
       if (t < B) {
-        float Z[3][9];
+#pragma unroll
+        for (int r = 0; r < 9; ++r) {
+          float v = 0.f;
+          for (int d = 0; d < O; ++d) v = fmaf(ph.coef[cl][d], sDb[(d) * NB9 + r * B + t], v);
+          sT[r * B + t] = v;
+        }
+        // V_c = lambda K_c^T and the volume term
+        float V[3][9];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
-          for (int r = 0; r < 9; ++r) Z[c][r] = 0.f;
-        if (t < nout)
+          for (int s = 0; s < 9; ++s) V[c][s] = 0.f;
 #pragma unroll 4
-          for (int kk = 0; kk < nk; ++kk)
+        for (int b = 0; b < B; ++b)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              const float kc = tK[(c * B + kk) * B + t];
+          for (int c = 0; c < 3; ++c) {
+            const float kc = tKT[(c * B + b) * B + t];
 #pragma unroll
-              for (int r = 0; r < 9; ++r) Z[c][r] = fmaf(Gn[r * B + kk], kc, Z[c][r]);
-            }
-        float g[9];
+            for (int s = 0; s < 9; ++s) V[c][s] = fmaf(sL[s * B + b], kc, V[c][s]);
+          }
+        float w[9];
 #pragma unroll
-        for (int r = 0; r < 9; ++r) g[r] = ph.coef[cl][d] * mu[r] + ph.hcoef[cl][d] * muh[r];
+        for (int r = 0; r < 9; ++r) w[r] = 0.f;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          star_acc<true>(S + c * 81, Z[c], g);
+          star_acc<true>(S + c * 81, V[c], w);
 #pragma unroll
-          for (int r = 0; r < 9; ++r) sZ[c * NB9 + r * B + t] = Z[c][r];
+          for (int s = 0; s < 9; ++s) sV[c * NB9 + s * B + t] = V[c][s];
         }
 #pragma unroll
-        for (int r = 0; r < 9; ++r) sG0[(d & 1) * NB9 + r * B + t] = g[r];
+        for (int r = 0; r < 9; ++r) mu[r] = -w[r];
       }
       gsync<NT>(g);
-      if (t < 27) tile33<B>(sZ + tc * NB9, (sDb + (d) * NB9), 3 * trb, 3 * tsb, nout, wst);
-      gsync<NT>(g);
-    }
-    if (t < B)
+      if (t < 27) {
+        float tv[3][3];
 #pragma unroll
-      for (int r = 0; r < 9; ++r) a.lq[(size_t)k * NB9 + r * B + t] = sL[r * B + t] + sG0[(0) * NB9 + r * B + t];
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int q = 0; q < 3; ++q) tv[i][q] = 0.f;
+        tile33<B>(sV + tc * NB9, sT, 3 * trb, 3 * tsb, B, tv);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int q = 0; q < 3; ++q) wst[i][q] -= tv[i][q];
+      }
+      gsync<NT>(g);
+      // local surface: LF_i = lambda F^_i^T, TF_i = T F~_i, U_i = A-_i^T LF_i, per (face, f)
+      float* sLF = sScr;
+      float* sTF = sScr + 36 * F;
+      float* sU = sScr + 72 * F;
+      for (int p = t; p < 4 * F; p += NT) {
+        const int i = p / F, f = p % F;
+        float lf[9], tf[9], u[9];
+        rows9s<B, B>(sL, tFhT + i * B * F, F, f, lf);
+        rows9s<B, B>(sT, tFt + i * B * F, F, f, tf);
+        const float* Am = sM + AM_LOC + i * 81;
+#pragma unroll
+        for (int r = 0; r < 9; ++r) {
+          float v = 0.f;
+#pragma unroll
+          for (int s = 0; s < 9; ++s) v = fmaf(Am[s * 9 + r], lf[s], v);
+          u[r] = v;
+        }
+#pragma unroll
+        for (int r = 0; r < 9; ++r) {
+          sLF[(i * 9 + r) * F + f] = lf[r];
+          sTF[(i * 9 + r) * F + f] = tf[r];
+          sU[(i * 9 + r) * F + f] = u[r];
+        }
+      }
+      gsync<NT>(g);
+      if (t < B)
+        for (int i = 0; i < 4; ++i)
+#pragma unroll 5
+          for (int f = 0; f < F; ++f) {
+            const float w = tFtT[(i * F + f) * B + t];
+#pragma unroll
+            for (int r = 0; r < 9; ++r) mu[r] = fmaf(sU[(i * 9 + r) * F + f], w, mu[r]);
+          }
+      for (int p = t; p < 36; p += NT) {
+        const int i = p / 9, rb = (p / 3) % 3, sb = p % 3;
+        float acc[3][3];
+#pragma unroll
+        for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+          for (int q = 0; q < 3; ++q) acc[ii][q] = 0.f;
+        tile33<F>(sLF + i * 9 * F, sTF + i * 9 * F, 3 * rb, 3 * sb, F, acc);
+#pragma unroll
+        for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+          for (int q = 0; q < 3; ++q) atomicAdd(Wk + AM_LOC + i * 81 + (3 * rb + ii) * 9 + 3 * sb + q, (double)acc[ii][q]);
+      }
+      // the buffers this pass wrote
+      if (t < B) {
+#pragma unroll
+        for (int r = 0; r < 9; ++r) {
+          mu[r] += sG0[r * B + t];
+          muh[r] = sG0[NB9 + r * B + t];
+        }
+#pragma unroll
+        for (int r = 0; r < 9; ++r)
+          sG0[((O - 1) & 1) * NB9 + r * B + t] = ph.coef[cl][O - 1] * mu[r] + ph.hcoef[cl][O - 1] * muh[r];
+      }
+      gsync<NT>(g);
+      // ---- reverse time kernel
+      float* sZ = sScr;
+#pragma unroll
+      for (int d = O - 2; d >= 0; --d) {
+        const int nk = nbasis(O - 1 - d), nout = nbasis(O - d);
+        const float* Gn = (sG0 + ((d + 1) & 1) * NB9);
+        if (t < B) {
+          float Z[3][9];
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int r = 0; r < 9; ++r) Z[c][r] = 0.f;
+          if (t < nout)
+#pragma unroll 4
+            for (int kk = 0; kk < nk; ++kk)
+#pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                const float kc = tK[(c * B + kk) * B + t];
+#pragma unroll
+                for (int r = 0; r < 9; ++r) Z[c][r] = fmaf(Gn[r * B + kk], kc, Z[c][r]);
+              }
+          float g[9];
+#pragma unroll
+          for (int r = 0; r < 9; ++r) g[r] = ph.coef[cl][d] * mu[r] + ph.hcoef[cl][d] * muh[r];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            star_acc<true>(S + c * 81, Z[c], g);
+#pragma unroll
+            for (int r = 0; r < 9; ++r) sZ[c * NB9 + r * B + t] = Z[c][r];
+          }
+#pragma unroll
+          for (int r = 0; r < 9; ++r) sG0[(d & 1) * NB9 + r * B + t] = g[r];
+        }
+        gsync<NT>(g);
+        if (t < 27) tile33<B>(sZ + tc * NB9, (sDb + (d) * NB9), 3 * trb, 3 * tsb, nout, wst);
+        gsync<NT>(g);
+      }
+      if (t < B)
+#pragma unroll
+        for (int r = 0; r < 9; ++r) a.lq[kf * NB9 + r * B + t] = sL[r * B + t] + sG0[(0) * NB9 + r * B + t];
+      gsync<NT>(g);   // the group's region is refilled for the next simulation or element
+    }
     if (t < 27)
 #pragma unroll
       for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int q = 0; q < 3; ++q) atomicAdd(Wk + AM_STAR + tc * 81 + (3 * trb + i) * 9 + 3 * tsb + q, (double)wst[i][q]);
-    gsync<NT>(g);   // the group's region is refilled for its next element
   }
 }
 
@@ -818,97 +851,104 @@ __global__ void __launch_bounds__(AdjNT<O>::value) k_adj_nbr(DevOps ops, AdjLtsA
   auto mode = [modes](int i) { return ((modes >> (3 * i)) & 7) - 1; };
   constexpr int NT = AdjNT<O>::value, R = (NB9 + NT - 1) / NT;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int m = mode(i);
-    if (m < 0) continue;
-    const int k = sF[2 * i], ip = sBk[2 * i];
-    stage<81, NT>(sA[i], a.amat + (size_t)k * AM_SIZE + AM_NBR + ip * 81, t);
-    stage<NB9, NT>(sLk[i], a.lq + (size_t)k * NB9, t);
-    const float* b0 = (m == 1) ? a.B3s : (m == 2) ? a.B2s : a.B1s;
-    float x[R], x2[R];
-#pragma unroll
-    for (int j = 0; j < R; ++j) {
-      const int q = t + j * NT;
-      x[j] = x2[j] = 0.f;
-      if (q < NB9) {
-        x[j] = __ldg(b0 + (size_t)kn * a.bufs + q);
-        if (m == 3) x2[j] = __ldg(a.B2s + (size_t)kn * a.bufs + q);
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < R; ++j)
-      if (t + j * NT < NB9) sX[i][t + j * NT] = x[j] - x2[j];
-  }
-  __syncthreads();
-  for (int p = t; p < 4 * F; p += nt) {
-    const int i = p / F, f = p % F;
-    if (mode(i) < 0) continue;
-    const int ip = sBk[2 * i], jh = sBk[2 * i + 1];
-    float lf[9], xf[9];
-    rows9<B, B>(sLk[i], a.FhT + ip * B * F, F, f, lf);
-    rows9<B, B>(sX[i], ops.Fb + jh * B * F, F, f, xf);
-#pragma unroll
-    for (int r = 0; r < 9; ++r) {
-      float u = 0.f;
-#pragma unroll
-      for (int s = 0; s < 9; ++s) u = fmaf(sA[i][s * 9 + r], lf[s], u);
-      sLF[i][r * F + f] = lf[r];
-      sXF[i][r * F + f] = xf[r];
-      sU[i][r * F + f] = u;
-    }
-  }
-  __syncthreads();
-  if (t < B) {
-    // the faces' contributions summed per buffer, then one update of each adjoint touched
-    float y1[9], y2[9], y3[9];
-#pragma unroll
-    for (int r = 0; r < 9; ++r) y1[r] = y2[r] = y3[r] = 0.f;
-    bool u1 = false, u2 = false, u3 = false;
+  for (int i = 0; i < 4; ++i)
+    if (mode(i) >= 0) stage<81, NT>(sA[i], a.amat + (size_t)sF[2 * i] * AM_SIZE + AM_NBR + sBk[2 * i] * 81, t);
+  for (int sim = 0; sim < a.nsim; ++sim) {
+    // this simulation's block of the owner's buffers (stride G between modes)
+    const size_t xo = (size_t)kn * a.bufs + (size_t)(sim / a.G) * (NB9 * a.G) + sim % a.G;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int m = mode(i);
       if (m < 0) continue;
-      float y[9];
-      rows9<F, F>(sU[i], a.FbT + sBk[2 * i + 1] * F * B, B, t, y);
+      const int k = sF[2 * i];
+      stage<NB9, NT>(sLk[i], a.lq + ((size_t)k * a.nsim + sim) * NB9, t);
+      const float* b0 = (m == 1) ? a.B3s : (m == 2) ? a.B2s : a.B1s;
+      float x[R], x2[R];
 #pragma unroll
-      for (int r = 0; r < 9; ++r) {
-        if (m == 1) {
-          y3[r] += y[r];
-        } else if (m == 2) {
-          y2[r] += y[r];
-        } else if (m == 3) {
-          y1[r] += y[r];
-          y2[r] -= y[r];
-        } else {
-          y1[r] += y[r];
+      for (int j = 0; j < R; ++j) {
+        const int q = t + j * NT;
+        x[j] = x2[j] = 0.f;
+        if (q < NB9) {
+          x[j] = __ldg(b0 + xo + (size_t)q * a.G);
+          if (m == 3) x2[j] = __ldg(a.B2s + xo + (size_t)q * a.G);
         }
       }
-      u1 |= (m == 0 || m == 3);
-      u2 |= (m == 2 || m == 3);
-      u3 |= (m == 1);
+#pragma unroll
+      for (int j = 0; j < R; ++j)
+        if (t + j * NT < NB9) sX[i][t + j * NT] = x[j] - x2[j];
     }
-    const size_t o = (size_t)kn * NB9 + t;
+    __syncthreads();
+    for (int p = t; p < 4 * F; p += nt) {
+      const int i = p / F, f = p % F;
+      if (mode(i) < 0) continue;
+      const int ip = sBk[2 * i], jh = sBk[2 * i + 1];
+      float lf[9], xf[9];
+      rows9<B, B>(sLk[i], a.FhT + ip * B * F, F, f, lf);
+      rows9<B, B>(sX[i], ops.Fb + jh * B * F, F, f, xf);
 #pragma unroll
-    for (int r = 0; r < 9; ++r) {
-      if (u1) atomicAdd(a.lb1 + o + r * B, y1[r]);
-      if (u2) atomicAdd(a.lb2 + o + r * B, y2[r]);
-      if (u3) atomicAdd(a.lb3 + o + r * B, y3[r]);
+      for (int r = 0; r < 9; ++r) {
+        float u = 0.f;
+#pragma unroll
+        for (int s = 0; s < 9; ++s) u = fmaf(sA[i][s * 9 + r], lf[s], u);
+        sLF[i][r * F + f] = lf[r];
+        sXF[i][r * F + f] = xf[r];
+        sU[i][r * F + f] = u;
+      }
     }
-  }
-  for (int p = t; p < 36; p += nt) {
-    const int i = p / 9, rb = (p / 3) % 3, sb = p % 3;
-    if (mode(i) < 0) continue;
-    float acc[3][3];
+    __syncthreads();
+    if (t < B) {
+      // the faces' contributions summed per buffer, then one update of each adjoint touched
+      float y1[9], y2[9], y3[9];
 #pragma unroll
-    for (int ii = 0; ii < 3; ++ii)
+      for (int r = 0; r < 9; ++r) y1[r] = y2[r] = y3[r] = 0.f;
+      bool u1 = false, u2 = false, u3 = false;
 #pragma unroll
-      for (int q = 0; q < 3; ++q) acc[ii][q] = 0.f;
-    tile33<F>(sLF[i], sXF[i], 3 * rb, 3 * sb, F, acc);
-    double* Wk = a.W + (size_t)sF[2 * i] * AM_SIZE + AM_NBR + sBk[2 * i] * 81;
+      for (int i = 0; i < 4; ++i) {
+        const int m = mode(i);
+        if (m < 0) continue;
+        float y[9];
+        rows9<F, F>(sU[i], a.FbT + sBk[2 * i + 1] * F * B, B, t, y);
 #pragma unroll
-    for (int ii = 0; ii < 3; ++ii)
+        for (int r = 0; r < 9; ++r) {
+          if (m == 1) {
+            y3[r] += y[r];
+          } else if (m == 2) {
+            y2[r] += y[r];
+          } else if (m == 3) {
+            y1[r] += y[r];
+            y2[r] -= y[r];
+          } else {
+            y1[r] += y[r];
+          }
+        }
+        u1 |= (m == 0 || m == 3);
+        u2 |= (m == 2 || m == 3);
+        u3 |= (m == 1);
+      }
+      const size_t o = ((size_t)kn * a.nsim + sim) * NB9 + t;
 #pragma unroll
-      for (int q = 0; q < 3; ++q) atomicAdd(Wk + (3 * rb + ii) * 9 + 3 * sb + q, (double)acc[ii][q]);
+      for (int r = 0; r < 9; ++r) {
+        if (u1) atomicAdd(a.lb1 + o + r * B, y1[r]);
+        if (u2) atomicAdd(a.lb2 + o + r * B, y2[r]);
+        if (u3) atomicAdd(a.lb3 + o + r * B, y3[r]);
+      }
+    }
+    for (int p = t; p < 36; p += nt) {
+      const int i = p / 9, rb = (p / 3) % 3, sb = p % 3;
+      if (mode(i) < 0) continue;
+      float acc[3][3];
+#pragma unroll
+      for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) acc[ii][q] = 0.f;
+      tile33<F>(sLF[i], sXF[i], 3 * rb, 3 * sb, F, acc);
+      double* Wk = a.W + (size_t)sF[2 * i] * AM_SIZE + AM_NBR + sBk[2 * i] * 81;
+#pragma unroll
+      for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) atomicAdd(Wk + (3 * rb + ii) * 9 + 3 * sb + q, (double)acc[ii][q]);
+    }
+    __syncthreads();   // the staged blocks are refilled for the next simulation
   }
 }
 

@@ -29,9 +29,10 @@ struct Launchers {
   // discrete adjoint of the elastic GTS loop (one simulation, no mechanisms; else nullptr)
   void (*adj_T)(const DevOps&, const AdjArgs&, float* tbuf, int K, cudaStream_t);
   void (*adj_step)(const DevOps&, const AdjArgs&, int K, cudaStream_t);
-  void (*adj_sample)(const float* Q, long long qs, const int* elem, const float* phi, int nrec, float* out,
+  void (*adj_sample)(const float* Q, long long qs, int nsim, int G, const int* elem, const float* phi, int nrec,
+                     float* out, cudaStream_t);
+  void (*adj_source)(float* lam, int nsim, const int* elem, const float* phi, const float* res, int nrec,
                      cudaStream_t);
-  void (*adj_source)(float* lam, const int* elem, const float* phi, const float* res, int nrec, cudaStream_t);
   void (*adj_pred)(const DevOps&, const AdjLtsArgs&, const PhaseArgs&, int nelem, cudaStream_t);
   void (*adj_nbr)(const DevOps&, const AdjLtsArgs&, const PhaseArgs&, int K, cudaStream_t);
   // face-local messages of a partitioned run (one simulation)
@@ -71,7 +72,7 @@ struct Impl {
       // two fit the 512 tensor-memory columns)
       L->blocks_predict_tc = 2;
     }
-    if constexpr (M == 0 && FG == 1) {
+    if constexpr (M == 0) {
       e = cudaFuncSetAttribute(k_adj_pred<O>, cudaFuncAttributeMaxDynamicSharedMemorySize, AdjPredCfg<O>::SMEM_BYTES);
       if (e != cudaSuccess) return e;
     }
@@ -108,12 +109,13 @@ struct Impl {
   static void adj_step(const DevOps& o, const AdjArgs& a, int K, cudaStream_t st) {
     k_adj_step<O><<<K, AdjNT<O>::value, 0, st>>>(o, a);
   }
-  static void adj_sample(const float* Q, long long qs, const int* elem, const float* phi, int nrec, float* out,
-                         cudaStream_t st) {
-    k_adj_sample<O><<<(3 * nrec + 127) / 128, 128, 0, st>>>(Q, qs, elem, phi, nrec, out);
+  static void adj_sample(const float* Q, long long qs, int nsim, int G, const int* elem, const float* phi, int nrec,
+                         float* out, cudaStream_t st) {
+    k_adj_sample<O><<<(3 * nrec * nsim + 127) / 128, 128, 0, st>>>(Q, qs, nsim, G, elem, phi, nrec, out);
   }
-  static void adj_source(float* lam, const int* elem, const float* phi, const float* res, int nrec, cudaStream_t st) {
-    k_adj_source<O><<<1, 64, 0, st>>>(lam, elem, phi, res, nrec);
+  static void adj_source(float* lam, int nsim, const int* elem, const float* phi, const float* res, int nrec,
+                         cudaStream_t st) {
+    k_adj_source<O><<<1, 64, 0, st>>>(lam, nsim, elem, phi, res, nrec);
   }
   // persistent: at most one CTA per SM, each CTA's element groups take elements in turn
   static void adj_pred(const DevOps& o, const AdjLtsArgs& a, const PhaseArgs& p, int n, cudaStream_t st) {
@@ -156,9 +158,13 @@ struct Impl {
     L.receivers = &receivers;
     L.sources = &sources;
     L.pack = &pack;
+    // the adjoint covers the elastic equations; its global-time-stepping kernels one
+    // simulation, the clustered ones also fused simulations
     if constexpr (M == 0 && FG == 1) {
       L.adj_T = &adj_T;
       L.adj_step = &adj_step;
+    }
+    if constexpr (M == 0) {
       L.adj_sample = &adj_sample;
       L.adj_source = &adj_source;
       L.adj_pred = &adj_pred;

@@ -277,3 +277,68 @@ def test_gpu_adjoint_periodic_cube_matches_oracle_adjoint():
     for p in range(3):
         assert _rel(g[:, p], g0[:, p]) <= 2e-3, (p, _rel(g[:, p], g0[:, p]))
     assert _rel(dq0, dq0_o) <= 2e-3
+
+
+def _fused_inputs(m, order, F, seed):
+    K = m["tet"].shape[0]
+    nb = order * (order + 1) * (order + 2) // 6
+    rng = np.random.default_rng(seed)
+    q0s = np.stack([synth.random_dofs(K, 9, nb, seed=seed + f) for f in range(F)])
+    srcs = [(np.array([200.0, 200.0, -60.0]) + rng.uniform(0.0, 250.0, 3) * np.array([1.0, 1.0, -0.3]),
+             rng.normal(size=6), 10.0, 0.02, 1e12) for _ in range(F)]
+    return q0s, srcs
+
+
+def _fused_lts(order, m, rho, lam, mu, q0s, rec, srcs, cl, dt, F):
+    s = binding.Solver(order, 0, device=0, n_fused=F)
+    s.set_mesh(m["xyz"], m["tet"], m["face_bc"])
+    s.set_material(rho, np.sqrt((lam + 2 * mu) / rho), np.sqrt(mu / rho))
+    for f, src in enumerate(srcs):
+        s.add_point_source(*src, fused_idx=f)
+    for x in rec:
+        s.add_receiver(x, dt)
+    if cl is None:
+        s.setup_clusters(1, 0.5)
+    else:
+        s.force_clusters(cl, 3, 0.5, 1.0)
+    s.set_finest_dt(dt)
+    s.set_dofs(q0s)
+    return s
+
+
+@pytest.mark.parametrize("F,clustered", [(4, True), (8, True), (4, False)])
+def test_fused_adjoint_equals_the_sum_of_single_simulation_adjoints(F, clustered):
+    """F simulations (own sources, initial states and data; shared material) in one adjoint
+    sweep: J and the material gradient are the sums of the single-simulation values, the
+    samples and dJ/dQ0 those of each simulation (three forced clusters, or one cluster,
+    where the fused run takes the phase-level sweep and the single ones the step-level one)."""
+    order = 4
+    m, mat, _, rec, _ = _case(order, seed=20)
+    rho, lam, mu = _rlm(mat)
+    cl = _forced_clusters(m) if clustered else None
+    dt = 1.5e-4
+    n = 8 if clustered else 6
+    q0s, srcs = _fused_inputs(m, order, F, seed=40)
+    s = _fused_lts(order, m, rho, lam, mu, q0s, rec, srcs, cl, dt, F)
+    rows = n // 4 + 1 if clustered else n + 1
+    _, syn = s.misfit(n, np.zeros((rows, F, 3, 3)), every=1)
+    s.close()
+    data = syn * 1.04 + 1e-9
+    s = _fused_lts(order, m, rho, lam, mu, q0s, rec, srcs, cl, dt, F)
+    J, g, syn_f, dq0 = s.misfit_gradient(n, data, every=1, want_dq0=True)
+    s.close()
+    J1, g1 = 0.0, np.zeros_like(g)
+    for f in range(F):
+        if clustered:
+            t = _gpu_lts(order, m, rho, lam, mu, q0s[f], rec, srcs[f], cl, dt)
+        else:
+            t = _gpu(order, m, rho, lam, mu, q0s[f], rec, srcs[f], dt)
+        Jf, gf, synf, dqf = t.misfit_gradient(n, data[:, f], every=1, want_dq0=True)
+        t.close()
+        J1 += Jf
+        g1 += gf
+        assert _rel(syn_f[:, f], synf) <= 1e-5, f
+        assert _rel(dq0[f], dqf) <= 1e-4, (f, _rel(dq0[f], dqf))
+    assert abs(J / J1 - 1) <= 1e-5
+    for p in range(3):
+        assert _rel(g[:, p], g1[:, p]) <= 1e-4, (p, _rel(g[:, p], g1[:, p]))
