@@ -79,7 +79,9 @@ def main():
     """Gradient of the seismogram misfit on the adjoint workload: 40 x 40 x 21 hexes x 6 =
     201,600 jittered graded tets, elastic order 4, 3 LTS clusters, 2,000 finest steps, 32
     surface receivers, observed data from a run with rho, lambda, mu 1 % higher in a
-    Gaussian blob, checkpoints every 100 finest steps. Prints one JSON line."""
+    Gaussian blob, checkpoints every 100 finest steps. With --fused F, F sources (the first
+    one and F - 1 at seeded positions) run fused: the gradient of the summed misfit, timed
+    beside one single-source gradient. Prints one JSON line."""
     import argparse
     import json
     import time
@@ -93,17 +95,28 @@ def main():
     ap.add_argument("--checkpoint", type=int, default=100, help="finest steps between checkpoints")
     ap.add_argument("--receivers", type=int, default=32)
     ap.add_argument("--fd", type=int, default=3, help="elements checked by central differences")
+    ap.add_argument("--fused", type=int, default=1,
+                    help="F > 1: F sources in one fused run (gradient of the summed misfit), timed "
+                         "against one single-source gradient")
     a = ap.parse_args()
     mesh, (rho, lam, mu), blob, rec, src = _config5(a.nx, a.ny, a.nz, a.order, a.clusters, a.receivers)
+    F = a.fused
+    srcs = [src]
+    if F > 1:   # further sources at seeded positions and orientations, 1 km deep
+        rng = np.random.default_rng(7)
+        for _ in range(F - 1):
+            x = np.array([rng.uniform(0.2, 0.8) * a.nx * 250.0, rng.uniform(0.2, 0.8) * a.ny * 250.0, -1000.0])
+            srcs.append((x, rng.normal(size=6), src[2], src[3], src[4]))
     K = mesh["tet"].shape[0]
     period = 2 ** (a.clusters - 1)
     n_macro = a.steps // period
 
-    def solver(r, l, m, cl=None, lam_c=None, dt=None):
-        s = binding.Solver(a.order, 0, device=0)
+    def solver(r, l, m, cl=None, lam_c=None, dt=None, nf=F):
+        s = binding.Solver(a.order, 0, device=0, n_fused=nf)
         s.set_mesh(mesh["xyz"], mesh["tet"], mesh["face_bc"])
         s.set_material(r, np.sqrt((l + 2 * m) / r), np.sqrt(m / r))
-        s.add_point_source(*src)
+        for f in range(nf):
+            s.add_point_source(*srcs[f], fused_idx=f)
         for x in rec:
             s.add_receiver(x, 0.01)
         if cl is None:
@@ -115,7 +128,7 @@ def main():
         return s, cl, lam_c, dt
 
     base, cl, lam_c, dt = solver(rho, lam, mu)
-    data0 = np.zeros((n_macro + 1, len(rec), 3))
+    data0 = np.zeros((n_macro + 1, len(rec), 3) if F == 1 else (n_macro + 1, F, len(rec), 3))
     pert, _, _, _ = solver(rho * (1 + blob), lam * (1 + blob), mu * (1 + blob), cl, lam_c, dt)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -126,6 +139,13 @@ def main():
     J, grad, _ = base.misfit_gradient(a.steps, data, every=a.checkpoint // period)
     t_grad = time.perf_counter() - t0
     base.close()
+    single = None
+    if F > 1:   # one source alone, same material and data of that source
+        one, _, _, _ = solver(rho, lam, mu, cl, lam_c, dt, nf=1)
+        t0 = time.perf_counter()
+        one.misfit_gradient(a.steps, np.ascontiguousarray(data[:, 0]), every=a.checkpoint // period)
+        single = time.perf_counter() - t0
+        one.close()
     fd = []
     params = [rho, lam, mu]
     for k in np.argsort(-np.abs(grad[:, 2]))[:a.fd]:
@@ -140,6 +160,7 @@ def main():
                        central_difference=float((vals[0] - vals[1]) / (2e-3 * mu[k]))))
     out = dict(elements=int(K), order=a.order, clusters=a.clusters, cluster_elems=np.bincount(cl).tolist(),
                finest_steps=a.steps, macro_steps=n_macro, checkpoint_finest_steps=a.checkpoint, receivers=len(rec),
+               fused_sources=F, single_source_gradient_s=single,
                misfit=J, forward_s=t_fwd, misfit_and_gradient_s=t_grad, gradient_over_forward=t_grad / t_fwd,
                grad_norm=[float(np.linalg.norm(grad[:, p])) for p in range(3)], fd_check_mu=fd)
     print(json.dumps(out))
