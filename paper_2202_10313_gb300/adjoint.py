@@ -15,22 +15,27 @@ from . import binding
 
 class MisfitProblem:
     """Everything but the material: mesh, order, initial DOFs, sources, receivers,
-    observed data (N+1, n_rec, 3), step count, fixed time step and checkpoint spacing."""
+    observed data (N+1, n_rec, 3), step count, fixed time step and checkpoint spacing.
+    n_fused = F > 1: F simulations in one run, source f in simulation f, initial DOFs
+    (F, K, 9, B), data (N+1, F, n_rec, 3); the misfit is summed over the simulations."""
 
-    def __init__(self, order, mesh, q0, receivers, data, n_steps, dt, sources=(), every=100, device=0):
+    def __init__(self, order, mesh, q0, receivers, data, n_steps, dt, sources=(), every=100, device=0, n_fused=1):
         self.order, self.mesh, self.q0 = order, mesh, np.asarray(q0, dtype=np.float64)
         self.receivers, self.data = list(receivers), np.asarray(data, dtype=np.float64)
         self.n_steps, self.dt, self.sources, self.every, self.device = n_steps, dt, list(sources), every, device
+        self.n_fused = n_fused
+        if n_fused > 1 and len(self.sources) != n_fused:
+            raise ValueError("a fused problem takes one source per simulation")
 
     def solver(self, rho, lam, mu):
-        s = binding.Solver(self.order, 0, device=self.device)
+        s = binding.Solver(self.order, 0, device=self.device, n_fused=self.n_fused)
         m = self.mesh
         s.set_mesh(m["xyz"], m["tet"], m["face_bc"], m.get("period"))
         vp = np.sqrt((lam + 2.0 * mu) / rho)
         vs = np.sqrt(mu / rho)
         s.set_material(rho, vp, vs)
-        for src in self.sources:
-            s.add_point_source(*src)
+        for f, src in enumerate(self.sources):
+            s.add_point_source(*src, fused_idx=f if self.n_fused > 1 else 0)
         for x in self.receivers:
             s.add_receiver(x, self.dt)
         s.setup_clusters(1, 0.5)

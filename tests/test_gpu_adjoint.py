@@ -342,3 +342,22 @@ def test_fused_adjoint_equals_the_sum_of_single_simulation_adjoints(F, clustered
     assert abs(J / J1 - 1) <= 1e-5
     for p in range(3):
         assert _rel(g[:, p], g1[:, p]) <= 1e-4, (p, _rel(g[:, p], g1[:, p]))
+
+
+def test_autograd_function_fused():
+    torch = pytest.importorskip("torch")
+    from paper_2202_10313_gb300.adjoint import MisfitProblem, SeismogramMisfit
+    order, n, F = 3, 6, 4
+    m, mat, _, rec, _ = _case(order, seed=22)
+    rho, lam, mu = _rlm(mat)
+    q0s, srcs = _fused_inputs(m, order, F, seed=50)
+    dt = 2e-4
+    data = np.full((n + 1, F, 3, 3), 1e-9)
+    prob = MisfitProblem(order, m, q0s, rec, data, n, dt, sources=srcs, every=2, n_fused=F)
+    tr, tl, tm = (torch.tensor(x, dtype=torch.float64, requires_grad=True) for x in (rho, lam, mu))
+    J = SeismogramMisfit.apply(tr, tl, tm, prob)
+    J.backward()
+    s = _fused_lts(order, m, rho, lam, mu, q0s, rec, srcs, None, dt, F)
+    J2, g, _ = s.misfit_gradient(n, data, every=2)
+    assert float(J.detach()) == J2
+    assert np.array_equal(tl.grad.numpy(), g[:, 1]) and np.array_equal(tm.grad.numpy(), g[:, 2])
