@@ -246,27 +246,28 @@ int lts_set_finest_dt(lts_t* h, double dt);
 /* Discrete adjoint of the time-stepping loop (the misfit objective of Sec. VII-B,
  * summed): from the current state, advances n_steps steps of the elastic scheme (the same
  * launches as lts_advance_steps, sources included) and evaluates
- *   J = 1/2 sum_{n=0..N} sum_r sum_q (v_q(x_r, t_n) - data[n][r][q])^2,
+ *   J = 1/2 sum_{m=0..M} sum_r sum_q (v_q(x_r, t_m) - data[m][r][q])^2,
  * v the particle velocity (u, v, w) at receiver r (the handle's receivers, in order)
- * sampled at the step boundaries t_n = t_0 + n dt. The reverse sweep applies the
- * transposed time, volume, local and neighbour surface operators step by step,
- * recomputing the forward states from checkpoints stored every `every` steps, and
+ * sampled at the macro-step boundaries t_m (every step with one cluster). The reverse
+ * sweep applies the transposed time, volume, local and neighbour surface operators phase
+ * by phase, recomputing the forward states from checkpoints stored every `every` macro
+ * steps, and
  * correlates the adjoint with the forward states; the correlations are contracted with
  * the exact derivatives (forward-mode dual numbers) of the star matrices and the face
  * flux solvers with respect to each element's rho, lambda, mu — the face terms also
  * with respect to the neighbour's. Outputs (each may be NULL except data): *misfit J,
- * grad[n_tet][3] = dJ/d(rho, lambda, mu) per element (original order), synth_out[N+1][n_rec][3]
+ * grad[n_tet][3] = dJ/d(rho, lambda, mu) per element (original order), synth_out[M+1][n_rec][3]
  * the samples, dq0[n_tet][9][B] = dJ/dQ at the start. The time step is held fixed. The
  * state ends at t_N (as after lts_advance_steps). Needs n_mech = 0, no partition, at least
  * one receiver. Fused simulations (n_fused = F > 1: each its own sources and initial state,
  * the material shared): data and synth_out [..][F][n_rec][3] (simulation before receiver),
  * dq0[F][n_tet][9][B], and J and grad summed over the simulations — the gradient of the
- * summed misfit, as for several sources of one inversion; fused runs take the clustered
- * (phase-level) sweep below for any cluster count. With one cluster (global time stepping): Device
- * memory: (ceil(N/every) + min(every, N) + 1) copies of Q plus per-element operators.
- * With clustered LTS (N_c > 1) the same holds per macro step: n_steps is a multiple of
- * 2^(N_c-1), the samples are taken at the macro-step boundaries (data[M+1][n_rec][3],
- * M = n_steps / 2^(N_c-1)), checkpoints every `every` macro steps, and the reverse
+ * summed misfit, as for several sources of one inversion. The sweep is the phase-level
+ * one of clustered LTS for every cluster count. Time is counted in macro steps of 2^(N_c-1) finest steps
+ * (one cluster, global time stepping: every step): n_steps is a multiple of the macro
+ * step, the samples are taken at the macro-step boundaries (data[M+1][n_rec][3],
+ * M = n_steps / 2^(N_c-1)), Q is checkpointed every `every` macro steps
+ * (ceil(M/every) + 1 copies of Q plus the per-element operators), and the reverse
  * sweep takes the LTS phases backwards over the state (Q, B1, B2, B3): a neighbour pass
  * sends its transposed flux to the adjoint of the buffer it read (B1, B3, B2 or
  * B1 - B2), a predict pass collects the adjoints of the buffers it wrote. The reverse

@@ -20,7 +20,6 @@
 #include "host_partition.h"
 #include "launch.h"
 
-using ltsdev::AdjArgs;
 using ltsdev::DevOps;
 using ltsdev::DevState;
 using ltsdev::Launchers;
@@ -1935,8 +1934,7 @@ int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* 
     ck(cudaSetDevice(h->device), "cudaSetDevice");
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
     const int64_t K = h->mesh.K;
-    const int B = X.B, NB9 = 9 * B;
-    const int64_t qs = h->dst.qs;
+    const int B = X.B;
     // ---- explicit operators (internal order) and face links
     std::vector<float> amat((size_t)K * ltsdev::AM_SIZE);
     std::vector<int> fwd(8 * K, -1), back(8 * K, 0);
@@ -1968,9 +1966,7 @@ int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* 
       for (int b = 0; b < B; ++b) rphi[(size_t)r * B + b] = (float)h->receivers[r].phi[b];
     }
     // ---- device buffers
-    const int64_t ncp = (n_steps + every - 1) / every;
-    const int64_t seg = std::min(every, n_steps);
-    DevBuf d_amat, d_fwd, d_back, d_relem, d_rphi, d_syn, d_res, d_t, d_la, d_lb, d_w, d_cp, d_seg, d_qn;
+    DevBuf d_amat, d_fwd, d_back, d_relem, d_rphi;
     d_amat.alloc(sizeof(float) * amat.size());
     d_fwd.alloc(sizeof(int) * fwd.size());
     d_back.alloc(sizeof(int) * back.size());
@@ -1986,131 +1982,9 @@ int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* 
     up(d_rphi.p, rphi.data(), sizeof(float) * rphi.size());
     AdjTables tabs;
     make_adj_tables(h, tabs);
-    // clustered runs, and fused runs with any cluster count (one cluster: a macro step is
-    // one step), take the phase-level sweep; one simulation with one cluster the step-level one
-    if (h->nc > 1 || h->nsim > 1) {
-      adjoint_lts(h, n_steps / period, every, data, misfit, grad, synth_out, dq0, stream, d_amat, d_fwd, d_back,
-                  d_relem, d_rphi, nrec, tabs);
-      return;
-    }
-    d_syn.alloc(sizeof(float) * (n_steps + 1) * nrec * 3);
-    d_res.alloc(sizeof(float) * (n_steps + 1) * nrec * 3);
-    d_t.alloc(sizeof(float) * K * NB9);
-    d_la.alloc(sizeof(float) * K * NB9);
-    d_lb.alloc(sizeof(float) * K * NB9);
-    d_w.alloc(sizeof(double) * K * ltsdev::AM_SIZE);
-    d_cp.alloc(sizeof(float) * ncp * K * qs);
-    d_seg.alloc(sizeof(float) * seg * K * qs);
-    d_qn.alloc(sizeof(float) * K * qs);
-    const size_t qbytes = sizeof(float) * K * qs;
-    auto dcopy = [&](void* dst, const void* src) {
-      ck(cudaMemcpyAsync(dst, src, qbytes, cudaMemcpyDeviceToDevice, stream), "adjoint copy");
-    };
-    float* cp = d_cp.get<float>();
-    float* sg = d_seg.get<float>();
-    // ---- forward sweep with checkpoints every `every` steps
-    const int64_t s0 = h->s_now;
-    std::vector<size_t> nrec_t(nrec);
-    dcopy(cp, h->dst.Q);
-    X.adj_sample(h->dst.Q, qs, 1, 1, d_relem.get<int>(), d_rphi.get<float>(), nrec, d_syn.get<float>(), stream);
-    for (int64_t n = 0; n < n_steps; ++n) {
-      advance_steps(h, 1, stream);
-      X.adj_sample(h->dst.Q, qs, 1, 1, d_relem.get<int>(), d_rphi.get<float>(), nrec,
-                   d_syn.get<float>() + (n + 1) * nrec * 3, stream);
-      if ((n + 1) % every == 0 && n + 1 < n_steps) dcopy(cp + ((n + 1) / every) * K * qs, h->dst.Q);
-    }
-    for (int r = 0; r < nrec; ++r) nrec_t[r] = h->receivers[r].t.size();
-    const size_t seis_fwd = h->seis_used;
-    dcopy(d_qn.p, h->dst.Q);
-    std::vector<float> syn((size_t)(n_steps + 1) * nrec * 3);
-    ck(cudaMemcpyAsync(syn.data(), d_syn.p, sizeof(float) * syn.size(), cudaMemcpyDeviceToHost, stream), "samples");
-    ck(cudaStreamSynchronize(stream), "synchronize");
-    check_device_error(h);
-    std::vector<float> res(syn.size());
-    double J = 0.0;
-    for (size_t q = 0; q < syn.size(); ++q) {
-      const double r = (double)syn[q] - data[q];
-      res[q] = (float)r;
-      J += 0.5 * r * r;
-    }
-    if (!grad && !dq0) {           // misfit only: no reverse sweep
-      if (misfit) *misfit = J;
-      if (synth_out)
-        for (size_t q = 0; q < syn.size(); ++q) synth_out[q] = syn[q];
-      return;
-    }
-    up(d_res.p, res.data(), sizeof(float) * res.size());
-    // ---- reverse sweep
-    ck(cudaMemsetAsync(d_la.p, 0, sizeof(float) * K * NB9, stream), "memset");
-    ck(cudaMemsetAsync(d_w.p, 0, sizeof(double) * K * ltsdev::AM_SIZE, stream), "memset");
-    float* lam_a = d_la.get<float>();
-    float* lam_b = d_lb.get<float>();
-    X.adj_source(lam_a, 1, d_relem.get<int>(), d_rphi.get<float>(), d_res.get<float>() + n_steps * nrec * 3, nrec,
-                 stream);
-    AdjArgs aa{};
-    aa.tbuf = d_t.get<float>();
-    aa.amat = d_amat.get<float>();
-    aa.fwd = d_fwd.get<int>();
-    aa.back = d_back.get<int>();
-    aa.W = d_w.get<double>();
-    aa.KT = tabs.KT;
-    aa.FtT = tabs.FtT;
-    aa.FhT = tabs.FhT;
-    aa.FbT = tabs.FbT;
-    aa.qs = qs;
-    {
-      double fac = 1.0;
-      for (int d = 0; d < h->order; ++d) {
-        fac *= (d + 1);
-        aa.cd[d] = (float)(std::pow(h->delta, d + 1) / fac);
-      }
-    }
-    for (int64_t sgi = ncp - 1; sgi >= 0; --sgi) {
-      const int64_t c0 = sgi * every, c1 = std::min(c0 + every, n_steps);
-      // recompute Q^c0 .. Q^(c1-1) from the checkpoint
-      dcopy(h->dst.Q, cp + sgi * K * qs);
-      h->s_now = s0 + c0;
-      dcopy(sg, h->dst.Q);
-      for (int64_t n = c0; n + 1 < c1; ++n) {
-        advance_steps(h, 1, stream);
-        dcopy(sg + (n + 1 - c0) * K * qs, h->dst.Q);
-      }
-      for (int64_t n = c1 - 1; n >= c0; --n) {
-        aa.Q = sg + (n - c0) * K * qs;
-        X.adj_T(h->dops, aa, d_t.get<float>(), (int)K, stream);
-        aa.lam_in = lam_a;
-        aa.lam_out = lam_b;
-        X.adj_step(h->dops, aa, (int)K, stream);
-        std::swap(lam_a, lam_b);
-        X.adj_source(lam_a, 1, d_relem.get<int>(), d_rphi.get<float>(), d_res.get<float>() + n * nrec * 3, nrec, stream);
-      }
-      for (int r = 0; r < nrec; ++r) {
-        h->receivers[r].t.resize(nrec_t[r]);
-        h->receivers[r].slot.resize(nrec_t[r]);
-      }
-      h->seis_used = seis_fwd;
-    }
-    ck(cudaGetLastError(), "adjoint kernels");
-    // the state ends at t_N as after a plain advance
-    dcopy(h->dst.Q, d_qn.p);
-    h->s_now = s0 + n_steps;
-    std::vector<double> W((size_t)K * ltsdev::AM_SIZE);
-    ck(cudaMemcpyAsync(W.data(), d_w.p, sizeof(double) * W.size(), cudaMemcpyDeviceToHost, stream), "correlations");
-    std::vector<float> lq;
-    if (dq0) {
-      lq.resize((size_t)K * NB9);
-      ck(cudaMemcpyAsync(lq.data(), lam_a, sizeof(float) * lq.size(), cudaMemcpyDeviceToHost, stream), "adjoint state");
-    }
-    ck(cudaStreamSynchronize(stream), "synchronize");
-    check_device_error(h);
-    if (misfit) *misfit = J;
-    if (synth_out)
-      for (size_t q = 0; q < syn.size(); ++q) synth_out[q] = syn[q];
-    if (dq0)
-      for (int64_t k = 0; k < K; ++k)
-        for (int q = 0; q < NB9; ++q) dq0[k * NB9 + q] = lq[h->iperm[k] * NB9 + q];
-    // ---- gradient: correlations against the exact material derivatives of the operators
-    if (grad) contract_gradient(h, W, grad);
+    // the phase-level sweep for every cluster count (one cluster: a macro step is one step)
+    adjoint_lts(h, n_steps / period, every, data, misfit, grad, synth_out, dq0, stream, d_amat, d_fwd, d_back,
+                d_relem, d_rphi, nrec, tabs);
   });
 }
 

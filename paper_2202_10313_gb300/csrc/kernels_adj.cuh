@@ -1,19 +1,22 @@
-// Discrete adjoint of the global-time-stepping loop, elastic equations (one simulation).
+// Discrete adjoint of the clustered-LTS time loop, elastic equations, one or fused
+// simulations (one cluster is the global-time-stepping case: a macro step is one step).
 //
-// One forward step maps Q to Q' = Q + V(T) + S_L(T) + S_N(T of the face neighbours), with
-// D_0 = Q, D_{d+1} = sum_c S_c D_d K_c^T (S_c the star matrices of the time kernel),
+// One step of an element maps Q to Q' = Q + V(T) + S_L(T) + S_N(X of the face neighbours),
+// with D_0 = Q, D_{d+1} = sum_c S_c D_d K_c^T (S_c the star matrices of the time kernel),
 // T = sum_d c_d D_d, V = -sum_c S_c T K_c, S_L = sum_i A-_i (T F~_i) F^_i and
-// S_N = sum_i A+_i (T_{k_i} F-_{j,h}) F^_i (A-_i, A+_i the 9 x 9 flux solvers of face i).
-// For the adjoint lambda = dJ/dQ' of one step this file's kernels compute, per element,
+// S_N = sum_i A+_i (X_i F-_{j,h}) F^_i (A-_i, A+_i the 9 x 9 flux solvers of face i, X_i the
+// neighbour's buffer that the cluster relation selects). For the adjoint lambda = dJ/dQ'
+// the reverse passes below compute, per element,
 //   mu = dJ/dT = -sum_c S_c^T lambda K_c^T + sum_i ((A-_i^T lambda) F^_i^T) F~_i^T
-//        + sum over the neighbours k' of ((A+_{k',i'}^T lambda_k') F^_{i'}^T) F-_{i,h'}^T,
+//        + the adjoints of the buffers the step wrote,
 //   G_{O-1} = c_{O-1} mu, G_d = c_d mu + sum_c S_c^T G_{d+1} K_c,   dJ/dQ = lambda + G_0,
-// and the per-element correlations that the material derivatives of S_c, A-_i, A+_i
-// are contracted with once the loop is done:
+// the transposed neighbour fluxes into the adjoints of the buffers they read, and the
+// per-element correlations that the material derivatives of S_c, A-_i, A+_i are contracted
+// with once the loop is done:
 //   W_c  += sum_{d<O-1} G_{d+1} (D_d K_c^T)^T - lambda (T K_c)^T,
-//   W-_i += lambda (T F~_i F^_i)^T,   W+_i += lambda (T_{k_i} F-_{j,h} F^_i)^T.
+//   W-_i += lambda (T F~_i F^_i)^T,   W+_i += lambda_k (X F-_{j,h} F^_i)^T.
 // The matrices are explicit (FP32, built on the host from the same closed forms as the
-// forward kernels' star and flux code); one CTA per element, plain CUDA cores.
+// forward kernels' star and flux code); CUDA cores.
 #pragma once
 #include "kernels.cuh"
 
@@ -24,12 +27,11 @@ constexpr int AM_LOC = 243;      // A-_i, i = 0..3
 constexpr int AM_NBR = 567;      // A+_i, i = 0..3
 constexpr int AM_SIZE = 891;     // floats per element (also the size of the correlations W)
 
-// Threads per element CTA: one warp up to order 4, two at order 5 (every phase needs at
-// least one thread per mode column; the 81 correlation entries are strided over the CTA).
+// Threads per element group: one warp up to order 4, two at order 5 (every phase needs at
+// least one thread per mode column).
 template <int O>
 struct AdjNT {
   static constexpr int value = (nbasis(O) <= 32) ? 32 : 64;
-  static constexpr int WPT = (81 + value - 1) / value;   // correlation entries per thread
 };
 
 // Transposed copies of the operator tables, so that every loop over a table reads it with
@@ -47,337 +49,6 @@ __device__ __forceinline__ void rows9(const float* src, const float* __restrict_
     const float w = __ldg(tab + j * ts + t);
 #pragma unroll
     for (int r = 0; r < 9; ++r) v[r] = fmaf(src[r * LD + j], w, v[r]);
-  }
-}
-
-struct AdjArgs {
-  const float* Q;        // Q^n, element stride qs, rows of B
-  const float* tbuf;     // [K][9B] T of step n
-  const float* lam_in;   // [K][9B] lambda^{n+1}
-  float* lam_out;        // [K][9B] lambda^n without the misfit's source
-  const float* amat;     // [K][AM_SIZE]
-  const int* fwd;        // [K][4][2]: neighbour (internal index, -1 none), j*3+h of F- for this face
-  const int* back;       // [K][4][2]: the neighbour's face i' pointing here, i*3+h' of its F-
-  double* W;             // [K][AM_SIZE]: each step's sums are formed in FP32 and added here in FP64
-  const float *KT, *FtT, *FhT, *FbT;   // transposed operator tables (see AdjTables)
-  long long qs;
-  float cd[6];           // dt^(d+1)/(d+1)!
-};
-
-// T of every element from Q^n (the time kernel with the explicit star matrices).
-template <int O>
-__global__ void __launch_bounds__(AdjNT<O>::value) k_adj_T(DevOps ops, AdjArgs a, float* tbuf) {
-  constexpr int B = nbasis(O), NB9 = 9 * B;
-  __shared__ float sS[243];
-  __shared__ float sX[2][NB9];
-  const int k = blockIdx.x, t = threadIdx.x;
-  for (int i = t; i < 243; i += blockDim.x) sS[i] = a.amat[(size_t)k * AM_SIZE + AM_STAR + i];
-  for (int i = t; i < NB9; i += blockDim.x) sX[0][i] = a.Q[(size_t)k * a.qs + i];
-  __syncthreads();
-  float T[9];
-#pragma unroll
-  for (int r = 0; r < 9; ++r) T[r] = (t < B) ? a.cd[0] * sX[0][r * B + t] : 0.f;
-  int cur = 0;
-  for (int d = 0; d < O - 1; ++d) {
-    float nxt[9];
-#pragma unroll
-    for (int r = 0; r < 9; ++r) nxt[r] = 0.f;
-    if (t < B) {
-      float Y[3][9];
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int s = 0; s < 9; ++s) Y[c][s] = 0.f;
-      for (int kk = 0; kk < B; ++kk) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const float kc = a.KT[(c * B + kk) * B + t];
-#pragma unroll
-          for (int s = 0; s < 9; ++s) Y[c][s] = fmaf(sX[cur][s * B + kk], kc, Y[c][s]);
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < 9; ++r) {
-        float v = 0.f;
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-          for (int s = 0; s < 9; ++s) v = fmaf(sS[c * 81 + r * 9 + s], Y[c][s], v);
-        nxt[r] = v;
-        T[r] = fmaf(a.cd[d + 1], v, T[r]);
-      }
-    }
-    if (t < B)
-#pragma unroll
-      for (int r = 0; r < 9; ++r) sX[cur ^ 1][r * B + t] = nxt[r];
-    __syncthreads();
-    cur ^= 1;
-  }
-  if (t < B)
-#pragma unroll
-    for (int r = 0; r < 9; ++r) tbuf[(size_t)k * NB9 + r * B + t] = T[r];
-}
-
-// One reverse step for every element (one CTA each): lambda^n and the correlations.
-template <int O>
-__global__ void __launch_bounds__(AdjNT<O>::value) k_adj_step(DevOps ops, AdjArgs a) {
-  constexpr int WPT = AdjNT<O>::WPT;
-  constexpr int B = nbasis(O), F = nface(O), NB9 = 9 * B;
-  __shared__ float sM[AM_SIZE];
-  __shared__ float sAb[4][81];
-  __shared__ float sL[NB9], sT[NB9];
-  __shared__ float sD[O][NB9], sG[O][NB9];
-  __shared__ float sP[3][NB9];
-  __shared__ float sU[9 * F];
-  __shared__ int sF[8], sBk[8];
-  const int k = blockIdx.x, t = threadIdx.x, nt = blockDim.x;
-  for (int i = t; i < AM_SIZE; i += nt) sM[i] = a.amat[(size_t)k * AM_SIZE + i];
-  if (t < 8) {
-    sF[t] = a.fwd[k * 8 + t];
-    sBk[t] = a.back[k * 8 + t];
-  }
-  for (int i = t; i < NB9; i += nt) {
-    sL[i] = a.lam_in[(size_t)k * NB9 + i];
-    sT[i] = a.tbuf[(size_t)k * NB9 + i];
-    sD[0][i] = a.Q[(size_t)k * a.qs + i];
-  }
-  __syncthreads();
-  for (int i = t; i < 4 * 81; i += nt) {
-    const int f = i / 81, kn = sF[2 * f];
-    sAb[f][i % 81] = (kn >= 0) ? a.amat[(size_t)kn * AM_SIZE + AM_NBR + sBk[2 * f] * 81 + i % 81] : 0.f;
-  }
-  const float* S = sM + AM_STAR;
-  // ---- forward derivatives D_1 .. D_{O-1}
-  for (int d = 0; d < O - 1; ++d) {
-    if (t < B) {
-      float Y[3][9];
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int s = 0; s < 9; ++s) Y[c][s] = 0.f;
-      for (int kk = 0; kk < B; ++kk)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const float kc = a.KT[(c * B + kk) * B + t];
-#pragma unroll
-          for (int s = 0; s < 9; ++s) Y[c][s] = fmaf(sD[d][s * B + kk], kc, Y[c][s]);
-        }
-#pragma unroll
-      for (int r = 0; r < 9; ++r) {
-        float v = 0.f;
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-          for (int s = 0; s < 9; ++s) v = fmaf(S[c * 81 + r * 9 + s], Y[c][s], v);
-        sD[d + 1][r * B + t] = v;
-      }
-    }
-    __syncthreads();
-  }
-  // ---- mu = dJ/dT: volume term
-  float mu[9];
-#pragma unroll
-  for (int r = 0; r < 9; ++r) mu[r] = 0.f;
-  if (t < B)
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int r = 0; r < 9; ++r) {
-        float v = 0.f;
-#pragma unroll
-        for (int s = 0; s < 9; ++s) v = fmaf(S[c * 81 + s * 9 + r], sL[s * B + t], v);
-        sP[c][r * B + t] = v;
-      }
-  __syncthreads();
-  if (t < B)
-    for (int kk = 0; kk < B; ++kk)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const float kc = a.KT[(c * B + kk) * B + t];
-#pragma unroll
-        for (int r = 0; r < 9; ++r) mu[r] = fmaf(-sP[c][r * B + kk], kc, mu[r]);
-      }
-  __syncthreads();
-  // local surface term, face by face
-  for (int i = 0; i < 4; ++i) {
-    const float* Am = sM + AM_LOC + i * 81;
-    if (t < B)
-#pragma unroll
-      for (int r = 0; r < 9; ++r) {
-        float v = 0.f;
-#pragma unroll
-        for (int s = 0; s < 9; ++s) v = fmaf(Am[s * 9 + r], sL[s * B + t], v);
-        sP[0][r * B + t] = v;
-      }
-    __syncthreads();
-    if (t < F) {
-      float v[9];
-      rows9<B, B>(sP[0], a.FhT + i * B * F, F, t, v);
-#pragma unroll
-      for (int r = 0; r < 9; ++r) sU[r * F + t] = v[r];
-    }
-    __syncthreads();
-    if (t < B)
-      for (int f = 0; f < F; ++f) {
-        const float w = a.FtT[(i * F + f) * B + t];
-#pragma unroll
-        for (int r = 0; r < 9; ++r) mu[r] = fmaf(sU[r * F + f], w, mu[r]);
-      }
-    __syncthreads();
-  }
-  // neighbour surface term: the faces of the neighbours that read this element's T
-  for (int i = 0; i < 4; ++i) {
-    const int kn = sF[2 * i];
-    if (kn < 0) continue;
-    for (int q = t; q < NB9; q += nt) sP[1][q] = a.lam_in[(size_t)kn * NB9 + q];
-    __syncthreads();
-    if (t < B)
-#pragma unroll
-      for (int r = 0; r < 9; ++r) {
-        float v = 0.f;
-#pragma unroll
-        for (int s = 0; s < 9; ++s) v = fmaf(sAb[i][s * 9 + r], sP[1][s * B + t], v);
-        sP[0][r * B + t] = v;
-      }
-    __syncthreads();
-    const int ip = sBk[2 * i], jh = sBk[2 * i + 1];
-    if (t < F) {
-      float v[9];
-      rows9<B, B>(sP[0], a.FhT + ip * B * F, F, t, v);
-#pragma unroll
-      for (int r = 0; r < 9; ++r) sU[r * F + t] = v[r];
-    }
-    __syncthreads();
-    if (t < B)
-      for (int f = 0; f < F; ++f) {
-        const float w = a.FbT[(jh * F + f) * B + t];
-#pragma unroll
-        for (int r = 0; r < 9; ++r) mu[r] = fmaf(sU[r * F + f], w, mu[r]);
-      }
-    __syncthreads();
-  }
-  // ---- reverse time kernel: G_{O-1} = c mu, G_d = c_d mu + sum_c S_c^T G_{d+1} K_c
-  if (t < B)
-#pragma unroll
-    for (int r = 0; r < 9; ++r) sG[O - 1][r * B + t] = a.cd[O - 1] * mu[r];
-  __syncthreads();
-  for (int d = O - 2; d >= 0; --d) {
-    if (t < B)
-      for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int r = 0; r < 9; ++r) {
-          float v = 0.f;
-#pragma unroll
-          for (int s = 0; s < 9; ++s) v = fmaf(S[c * 81 + s * 9 + r], sG[d + 1][s * B + t], v);
-          sP[c][r * B + t] = v;
-        }
-    __syncthreads();
-    if (t < B) {
-      float g[9];
-#pragma unroll
-      for (int r = 0; r < 9; ++r) g[r] = a.cd[d] * mu[r];
-      for (int kk = 0; kk < B; ++kk)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const float kc = ops.K[(c * B + kk) * B + t];
-#pragma unroll
-          for (int r = 0; r < 9; ++r) g[r] = fmaf(sP[c][r * B + kk], kc, g[r]);
-        }
-#pragma unroll
-      for (int r = 0; r < 9; ++r) sG[d][r * B + t] = g[r];
-    }
-    __syncthreads();
-  }
-  if (t < B)
-#pragma unroll
-    for (int r = 0; r < 9; ++r) a.lam_out[(size_t)k * NB9 + r * B + t] = sL[r * B + t] + sG[0][r * B + t];
-  // ---- correlations (entry e = (e / 9, e % 9), strided over the CTA)
-  double* Wk = a.W + (size_t)k * AM_SIZE;
-  for (int c = 0; c < 3; ++c) {
-    float acc[WPT];
-#pragma unroll
-    for (int j = 0; j < WPT; ++j) acc[j] = 0.f;
-    if (t < B) {
-      float v[9];
-      rows9<B, B>(sT, ops.K + c * B * B, B, t, v);
-#pragma unroll
-      for (int s = 0; s < 9; ++s) sP[0][s * B + t] = v[s];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < WPT; ++j) {
-      const int e = t + j * nt;
-      if (e < 81)
-        for (int b = 0; b < B; ++b) acc[j] -= sL[(e / 9) * B + b] * sP[0][(e % 9) * B + b];
-    }
-    __syncthreads();
-    for (int d = 0; d < O - 1; ++d) {
-      if (t < B) {
-        float v[9];
-        rows9<B, B>(sD[d], a.KT + c * B * B, B, t, v);
-#pragma unroll
-        for (int s = 0; s < 9; ++s) sP[0][s * B + t] = v[s];
-      }
-      __syncthreads();
-#pragma unroll
-      for (int j = 0; j < WPT; ++j) {
-        const int e = t + j * nt;
-        if (e < 81)
-          for (int b = 0; b < B; ++b) acc[j] += sG[d + 1][(e / 9) * B + b] * sP[0][(e % 9) * B + b];
-      }
-      __syncthreads();
-    }
-#pragma unroll
-    for (int j = 0; j < WPT; ++j)
-      if (t + j * nt < 81) atomicAdd(Wk + AM_STAR + c * 81 + t + j * nt, (double)acc[j]);
-  }
-  for (int i = 0; i < 4; ++i) {
-    if (t < F) {
-      float v[9];
-      rows9<B, B>(sT, ops.Ft + i * B * F, F, t, v);
-#pragma unroll
-      for (int s = 0; s < 9; ++s) sU[s * F + t] = v[s];
-    }
-    __syncthreads();
-    if (t < B) {
-      float v[9];
-      rows9<F, F>(sU, ops.Fh + i * F * B, B, t, v);
-#pragma unroll
-      for (int s = 0; s < 9; ++s) sP[0][s * B + t] = v[s];
-    }
-    __syncthreads();
-    for (int e = t; e < 81; e += nt) {
-      float acc = 0.f;
-      for (int b = 0; b < B; ++b) acc += sL[(e / 9) * B + b] * sP[0][(e % 9) * B + b];
-      atomicAdd(Wk + AM_LOC + i * 81 + e, (double)acc);
-    }
-    __syncthreads();
-  }
-  for (int i = 0; i < 4; ++i) {
-    const int kn = sF[2 * i];
-    if (kn < 0) continue;
-    const int jh = sF[2 * i + 1];
-    for (int q = t; q < NB9; q += nt) sP[1][q] = a.tbuf[(size_t)kn * NB9 + q];
-    __syncthreads();
-    if (t < F) {
-      float v[9];
-      rows9<B, B>(sP[1], ops.Fb + jh * B * F, F, t, v);
-#pragma unroll
-      for (int s = 0; s < 9; ++s) sU[s * F + t] = v[s];
-    }
-    __syncthreads();
-    if (t < B) {
-      float v[9];
-      rows9<F, F>(sU, ops.Fh + i * F * B, B, t, v);
-#pragma unroll
-      for (int s = 0; s < 9; ++s) sP[0][s * B + t] = v[s];
-    }
-    __syncthreads();
-    for (int e = t; e < 81; e += nt) {
-      float acc = 0.f;
-      for (int b = 0; b < B; ++b) acc += sL[(e / 9) * B + b] * sP[0][(e % 9) * B + b];
-      atomicAdd(Wk + AM_NBR + i * 81 + e, (double)acc);
-    }
-    __syncthreads();
   }
 }
 

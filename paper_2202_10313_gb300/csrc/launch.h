@@ -27,8 +27,6 @@ struct Launchers {
                     const float* phi, const RecvItem* items, float* out, const float* omega, int n, cudaStream_t);
   void (*sources)(float* Q, long long qs, int fg, const float* phi, const SrcItem* items, int n, cudaStream_t);
   // discrete adjoint of the elastic GTS loop (one simulation, no mechanisms; else nullptr)
-  void (*adj_T)(const DevOps&, const AdjArgs&, float* tbuf, int K, cudaStream_t);
-  void (*adj_step)(const DevOps&, const AdjArgs&, int K, cudaStream_t);
   void (*adj_sample)(const float* Q, long long qs, int nsim, int G, const int* elem, const float* phi, int nrec,
                      float* out, cudaStream_t);
   void (*adj_source)(float* lam, int nsim, const int* elem, const float* phi, const float* res, int nrec,
@@ -103,12 +101,6 @@ struct Impl {
     const int threads = 128, nt = n * C::F;
     k_pack_faces<O, M><<<(nt + threads - 1) / threads, threads, 0, st>>>(o, s, p, se, sc, rc, n, msg);
   }
-  static void adj_T(const DevOps& o, const AdjArgs& a, float* tbuf, int K, cudaStream_t st) {
-    k_adj_T<O><<<K, AdjNT<O>::value, 0, st>>>(o, a, tbuf);
-  }
-  static void adj_step(const DevOps& o, const AdjArgs& a, int K, cudaStream_t st) {
-    k_adj_step<O><<<K, AdjNT<O>::value, 0, st>>>(o, a);
-  }
   static void adj_sample(const float* Q, long long qs, int nsim, int G, const int* elem, const float* phi, int nrec,
                          float* out, cudaStream_t st) {
     k_adj_sample<O><<<(3 * nrec * nsim + 127) / 128, 128, 0, st>>>(Q, qs, nsim, G, elem, phi, nrec, out);
@@ -158,12 +150,7 @@ struct Impl {
     L.receivers = &receivers;
     L.sources = &sources;
     L.pack = &pack;
-    // the adjoint covers the elastic equations; its global-time-stepping kernels one
-    // simulation, the clustered ones also fused simulations
-    if constexpr (M == 0 && FG == 1) {
-      L.adj_T = &adj_T;
-      L.adj_step = &adj_step;
-    }
+    // the adjoint covers the elastic equations (one or fused simulations)
     if constexpr (M == 0) {
       L.adj_sample = &adj_sample;
       L.adj_source = &adj_source;

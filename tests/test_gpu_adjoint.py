@@ -310,8 +310,7 @@ def _fused_lts(order, m, rho, lam, mu, q0s, rec, srcs, cl, dt, F):
 def test_fused_adjoint_equals_the_sum_of_single_simulation_adjoints(F, clustered):
     """F simulations (own sources, initial states and data; shared material) in one adjoint
     sweep: J and the material gradient are the sums of the single-simulation values, the
-    samples and dJ/dQ0 those of each simulation (three forced clusters, or one cluster,
-    where the fused run takes the phase-level sweep and the single ones the step-level one)."""
+    samples and dJ/dQ0 those of each simulation (three forced clusters, or one cluster)."""
     order = 4
     m, mat, _, rec, _ = _case(order, seed=20)
     rho, lam, mu = _rlm(mat)
