@@ -214,20 +214,29 @@ def test_lts_checkpoint_spacing_does_not_change_the_result():
         assert J == out[0][0] and np.array_equal(g, out[0][1]) and np.array_equal(syn, out[0][2])
 
 
-def test_lts_adjoint_memory_budget_does_not_change_the_result():
+@pytest.mark.parametrize("F", [1, 4])
+def test_lts_adjoint_memory_budget_does_not_change_the_result(F):
     """A segment replayed once with every phase input kept, and (a 1-byte budget) replayed
-    macro step by macro step: the same reverse sweep, bitwise."""
+    macro step by macro step: the same reverse sweep, bitwise (one and fused simulations)."""
     order, n_macro = 4, 4
     m, mat, q0, rec, src = _case(order, seed=18)
     rho, lam, mu = _rlm(mat)
     cl = _forced_clusters(m)
-    s = _gpu_lts(order, m, rho, lam, mu, q0, rec, src, cl, 1.5e-4)
-    _, _, syn = s.misfit_gradient(4 * n_macro, np.zeros((n_macro + 1, 3, 3)), every=n_macro)
+
+    def make():
+        if F == 1:
+            return _gpu_lts(order, m, rho, lam, mu, q0, rec, src, cl, 1.5e-4)
+        q0s, srcs = _fused_inputs(m, order, F, seed=60)
+        return _fused_lts(order, m, rho, lam, mu, q0s, rec, srcs, cl, 1.5e-4, F)
+
+    shape = (n_macro + 1, 3, 3) if F == 1 else (n_macro + 1, F, 3, 3)
+    s = make()
+    _, _, syn = s.misfit_gradient(4 * n_macro, np.zeros(shape), every=n_macro)
     s.close()
     data = syn * 1.03
     out = []
     for budget in (0, 1):
-        s = _gpu_lts(order, m, rho, lam, mu, q0, rec, src, cl, 1.5e-4)
+        s = make()
         s.set_adjoint_memory(budget)
         out.append(s.misfit_gradient(4 * n_macro, data, every=3, want_dq0=True))
         s.close()
