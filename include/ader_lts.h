@@ -258,8 +258,8 @@ int lts_set_finest_dt(lts_t* h, double dt);
  * with respect to the neighbour's. Outputs (each may be NULL except data): *misfit J,
  * grad[n_tet][3] = dJ/d(rho, lambda, mu) per element (original order), synth_out[M+1][n_rec][3]
  * the samples, dq0[n_tet][9][B] = dJ/dQ at the start. The time step is held fixed. The
- * state ends at t_N (as after lts_advance_steps). Needs n_mech = 0, no partition, at least
- * one receiver. Fused simulations (n_fused = F > 1: each its own sources and initial state,
+ * state ends at t_N (as after lts_advance_steps). Needs n_mech = 0 and at least one
+ * receiver; a partitioned run (lts_set_partition) gives bitwise the unpartitioned result. Fused simulations (n_fused = F > 1: each its own sources and initial state,
  * the material shared): data and synth_out [..][F][n_rec][3] (simulation before receiver),
  * dq0[F][n_tet][9][B], and J and grad summed over the simulations — the gradient of the
  * summed misfit, as for several sources of one inversion. The sweep is the phase-level

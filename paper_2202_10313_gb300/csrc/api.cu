@@ -1925,8 +1925,10 @@ int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* 
   return run(h, [&] {
     if (!h->ready) fail(LTS_ERR_STATE, "clusters not set up");
     const Launchers& X = h->L;
-    if (h->nmech != 0 || h->n_parts > 1 || !X.adj_pred)
-      fail(LTS_ERR_ARG, "the adjoint covers the elastic equations without a partition");
+    // a partitioned run on one GPU is bitwise the unpartitioned one; its reverse sweep reads
+    // the owners' buffer snapshots directly (a multi-GPU build would send the transposed face
+    // messages back over the cut)
+    if (h->nmech != 0 || !X.adj_pred) fail(LTS_ERR_ARG, "the adjoint covers the elastic equations");
     const int64_t period = int64_t(1) << (h->nc - 1);
     if (h->nc > 1 && n_steps % period != 0) fail(LTS_ERR_ARG, "n_steps must be a multiple of the macro step");
     const int nrec = (int)h->receivers.size();

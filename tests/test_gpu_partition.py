@@ -76,3 +76,31 @@ def test_partition_with_tensor_cores_and_switch_off():
     with pytest.raises(binding.LtsError) as ei:
         f.set_partition(part, 4)
     assert ei.value.code == binding.LTS_ERR_ARG
+
+
+def test_adjoint_of_a_partitioned_run_equals_the_unpartitioned_adjoint():
+    """The partitioned forward run is bitwise the unpartitioned one, and so is its adjoint:
+    misfit, gradient, samples and dJ/dQ0 (three clusters, elastic)."""
+    order = 4
+    m = synth.permute_vertex_order(synth.graded_box(6, 5, 3, 250.0, 125.0, seed=12), seed=2)
+    mat = synth.random_layers(m, n_layers=3, seed=5)
+    K = m["tet"].shape[0]
+    d0 = synth.random_dofs(K, 9, 20, seed=23)
+    rec = [np.array([400.0, 500.0, -20.0]), np.array([900.0, 700.0, -60.0])]
+    out = []
+    for parted in (False, True):
+        gpu, _, _ = make_pair(order, 0, m, mat)
+        gpu.add_point_source(np.array([610.0, 640.0, -260.0]), np.array([0.2, -0.4, 0.2, 1.0, 0.1, -0.3]), 8.0, 0.06,
+                             1e12)
+        for x in rec:
+            gpu.add_receiver(x, 1e-3)
+        gpu.setup_clusters(3, 0.5)
+        if parted:
+            part, _ = gpu.partition(3)
+            gpu.set_partition(part, 3)
+        gpu.set_dofs(d0)
+        data = np.full((3, 2, 3), 1e-7)
+        out.append(gpu.misfit_gradient(8, data, every=1, want_dq0=True))
+        gpu.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(np.asarray(a), np.asarray(b))
