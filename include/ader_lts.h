@@ -283,6 +283,15 @@ int lts_set_finest_dt(lts_t* h, double dt);
 int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* data, double* misfit,
                         double* grad, double* synth_out, double* dq0, void* cuda_stream);
 
+/* Moment-tensor gradient from the last lts_misfit_gradient call that ran the reverse sweep
+ * (grad or dq0 requested): out[n_src][6] = dJ/dm6 of every point source (registration order,
+ * the six components as given to lts_add_point_source; the source time function and m0
+ * held fixed). Each neighbour pass that added a source contributes
+ * -m0 (int s dt) / |det J| sum_b lambda_Q[elem][r][b] phi_b(xi_s), lambda_Q the adjoint of Q
+ * after the pass. Errors: LTS_ERR_ARG (out NULL), LTS_ERR_STATE (no such sweep since the
+ * sources last changed). */
+int lts_adjoint_source_gradient(lts_t* h, double* out);
+
 /* Throughput probes of the GPU the handle runs on, for roofline denominators: FP32 FMA on
  * the CUDA cores (8 independent FMA chains per thread, 8 CTAs of 256 threads per SM) and
  * tcgen05 MMA of kind tf32 (M = 128, N = 256, K = 8, FP32 accumulation in tensor memory,

@@ -56,6 +56,7 @@ _SIGS = {
     "lts_set_wait_limit": (_I, [_P, _L, _I]),
     "lts_set_adjoint_memory": (_I, [_P, ctypes.c_uint64]),
     "lts_measure_peaks": (_I, [_P, _P, _P]),
+    "lts_adjoint_source_gradient": (_I, [_P, _P]),
     "lts_partition": (_I, [_P, _I, _P, _P]),
     "lts_cut_faces": (_I, [_P, _P, _L, _P, _P]),
     "lts_set_partition": (_I, [_P, _I, _P]),
@@ -161,6 +162,7 @@ class Solver:
         """n_fused > 1: fused simulations; DOF arrays then carry a leading simulation axis
         (n_fused, K, n_q, B) and sources / seismograms take a simulation index."""
         self.order, self.n_mech, self.device, self.n_fused = order, n_mech, device, n_fused
+        self.n_sources = 0
         self.nq = 9 + 6 * n_mech
         self.nb = order * (order + 1) * (order + 2) // 6
         self._h = ctypes.c_void_p()
@@ -194,6 +196,7 @@ class Solver:
         self.K = tet.shape[0]
         per = None if period is None else _f64(period, 3)
         self._check(lib().lts_set_mesh(self._h, xyz.shape[0], _ptr(xyz), self.K, _ptr(tet), _ptr(bc), _ptr(per)))
+        self.n_sources = 0   # a new mesh drops the sources
 
     def set_material(self, rho, vp, vs, qp=None, qs=None, f_min=0.1, f_max=5.0):
         K = self.K
@@ -205,6 +208,7 @@ class Solver:
     def add_point_source(self, x, m6, f0, t0, m0=1.0, fused_idx=0):
         self._check(lib().lts_add_point_source(self._h, fused_idx, _ptr(_f64(x, 3)), _ptr(_f64(m6, 6)),
                                                float(f0), float(t0), float(m0)))
+        self.n_sources += 1
 
     def add_receiver(self, x, dt_sample):
         rid = ctypes.c_int()
@@ -395,6 +399,12 @@ class Solver:
 
     def set_graphs(self, enable=True):
         self._check(lib().lts_set_graphs(self._h, 1 if enable else 0))
+
+    def source_gradient(self):
+        """dJ/dm6 (n_sources, 6) of the point sources from the last misfit_gradient call."""
+        out = np.zeros((self.n_sources, 6))
+        self._check(lib().lts_adjoint_source_gradient(self._h, _ptr(out)))
+        return out
 
     def measure_peaks(self, stream=None):
         """Throughput probes: dict(fp32_tflops, tf32_tflops, fp32_ms, tf32_ms)."""

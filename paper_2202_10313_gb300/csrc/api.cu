@@ -148,6 +148,7 @@ struct lts_solver {
   size_t sitems_cap = 0;
   int num_sms = 0;
   uint64_t adj_budget = 0;   // bytes for the LTS adjoint's phase inputs (0: half the free memory)
+  std::vector<double> adj_src_grad;   // dJ/dm6 per source from the last adjoint sweep
   // profiling: event pairs around each predict / neighbour launch, read lazily
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -524,6 +525,7 @@ struct Phase {
 struct MacroPlan {
   std::vector<Phase> phases;
   std::vector<SrcItem> sitems;
+  std::vector<double> sscale;   // per source item: -m0 (int s dt) / |det J| (amp = sscale m6)
   std::vector<RecvItem> ritems;
 };
 
@@ -533,6 +535,7 @@ void plan_macro(lts_solver* h, int64_t s_begin, size_t& seis_need, MacroPlan& mp
   const int64_t s_end = s_begin + (int64_t(1) << (nc - 1));
   mp.phases.clear();
   mp.sitems.clear();
+  mp.sscale.clear();
   mp.ritems.clear();
   std::vector<double> gx, gw;
   lts::gauss_jacobi(h->order, 0.0, gx, gw);
@@ -559,6 +562,7 @@ void plan_macro(lts_solver* h, int64_t s_begin, size_t& seis_need, MacroPlan& mp
         it.phi_off = (int)(si * B);
         for (int r = 0; r < 6; ++r) it.amp[r] = (float)(-src.m0 * src.m6[r] * integ / h->mesh.detJ[src.elem]);
         mp.sitems.push_back(it);
+        mp.sscale.push_back(-src.m0 * integ / h->mesh.detJ[src.elem]);
       }
       ph.item_end = (int)mp.sitems.size();
       mp.phases.push_back(ph);
@@ -945,6 +949,7 @@ void adjoint_lts(lts_solver* h, int64_t n_macro, int64_t every, const double* da
   // fused runs: nsim simulations in groups of G; samples [time][sim][receiver][3], adjoints
   // [element][sim][9][B]
   const int nsim = h->nsim, G = nsim > 1 ? X.FG : 1;
+  h->adj_src_grad.clear();   // set again only by a completed reverse sweep
   const int64_t ns = (int64_t)nsim * nrec * 3;   // sample values per sample time
   DevBuf d_syn, d_res, d_lq, d_lb, d_w, d_cp, d_mac, d_qn;
   d_syn.alloc(sizeof(float) * (n_macro + 1) * ns);
@@ -954,6 +959,12 @@ void adjoint_lts(lts_solver* h, int64_t n_macro, int64_t every, const double* da
   d_w.alloc(sizeof(double) * K * ltsdev::AM_SIZE);
   d_cp.alloc(sizeof(float) * ncp * K * qs);
   d_qn.alloc(sizeof(float) * K * qs);
+  // moment-tensor gradient: [source][6] and one pass's source items with their scales
+  const int nsrc = (int)h->sources.size();
+  DevBuf d_sg, d_sgi, d_sgc;
+  d_sg.alloc(sizeof(double) * std::max(nsrc, 1) * 6);
+  d_sgi.alloc(sizeof(SrcItem) * std::max(nsrc, 1));
+  d_sgc.alloc(sizeof(double) * std::max(nsrc, 1));
   const size_t qbytes = sizeof(float) * K * qs;
   auto dcopy = [&](void* dst, const void* src, size_t bytes) {
     ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, stream), "adjoint copy");
@@ -993,6 +1004,7 @@ void adjoint_lts(lts_solver* h, int64_t n_macro, int64_t every, const double* da
   ck(cudaMemsetAsync(d_lq.p, 0, sizeof(float) * K * nsim * NB9, stream), "memset");
   ck(cudaMemsetAsync(d_lb.p, 0, sizeof(float) * 3 * K * nsim * NB9, stream), "memset");
   ck(cudaMemsetAsync(d_w.p, 0, sizeof(double) * K * ltsdev::AM_SIZE, stream), "memset");
+  ck(cudaMemsetAsync(d_sg.p, 0, sizeof(double) * std::max(nsrc, 1) * 6, stream), "memset");
   X.adj_source(d_lq.get<float>(), nsim, relem, rphi, d_res.get<float>() + n_macro * ns, nrec, stream);
   ltsdev::AdjLtsArgs aa{};
   aa.lq = d_lq.get<float>();
@@ -1044,10 +1056,34 @@ void adjoint_lts(lts_solver* h, int64_t n_macro, int64_t every, const double* da
     return q;
   };
   // reverse of one macro step from the phase inputs kept in `snap` (layout above)
+  MacroPlan smp;   // the reversed macro step's source items
   auto reverse_macro = [&](int64_t m, const char* snap) {
     const int64_t sb0 = s0 + m * period;
+    if (nsrc > 0) {
+      size_t seis_need = h->seis_used;
+      plan_macro(h, sb0, seis_need, smp);
+      for (int r = 0; r < nrec; ++r) {
+        h->receivers[r].t.resize(nrec_t[r]);
+        h->receivers[r].slot.resize(nrec_t[r]);
+      }
+    }
     for (size_t pi = lay.size(); pi-- > 0;) {
       const Phase ph = phase_at(pi, sb0);
+      if (nsrc > 0 && ph.kind == 0) {
+        // the sources this neighbour pass added: lambda_Q is now the adjoint of Q after it
+        const Phase& sp = smp.phases[pi];
+        const int n = sp.item_end - sp.item_beg;
+        if (n > 0) {
+          ck(cudaMemcpyAsync(d_sgi.p, smp.sitems.data() + sp.item_beg, sizeof(SrcItem) * n, cudaMemcpyHostToDevice,
+                             stream),
+             "source items");
+          ck(cudaMemcpyAsync(d_sgc.p, smp.sscale.data() + sp.item_beg, sizeof(double) * n, cudaMemcpyHostToDevice,
+                             stream),
+             "source scales");
+          X.adj_src_grad(d_lq.get<float>(), nsim, d_sgi.get<SrcItem>(), d_sgc.get<double>(), n, h->d_src_phi,
+                         d_sg.get<double>(), stream);
+        }
+      }
       const PhaseArgs pa = phase_args(h, ph);
       if (pa.end <= 0) continue;
       aa.end = pa.end;
@@ -1136,6 +1172,10 @@ void adjoint_lts(lts_solver* h, int64_t n_macro, int64_t every, const double* da
   h->s_now = s0 + n_macro * period;
   std::vector<double> W((size_t)K * ltsdev::AM_SIZE);
   ck(cudaMemcpyAsync(W.data(), d_w.p, sizeof(double) * W.size(), cudaMemcpyDeviceToHost, stream), "correlations");
+  h->adj_src_grad.assign((size_t)nsrc * 6, 0.0);
+  if (nsrc > 0)
+    ck(cudaMemcpyAsync(h->adj_src_grad.data(), d_sg.p, sizeof(double) * nsrc * 6, cudaMemcpyDeviceToHost, stream),
+       "source gradient");
   std::vector<float> lq;
   if (dq0) {
     lq.resize((size_t)K * nsim * NB9);
@@ -1994,6 +2034,15 @@ int lts_set_graphs(lts_t* h, int enable) {
   return run(h, [&] {
     h->use_graphs = enable != 0;
     if (!h->use_graphs) release_graphs(h);
+  });
+}
+
+int lts_adjoint_source_gradient(lts_t* h, double* out) {
+  return run(h, [&] {
+    if (!out) fail(LTS_ERR_ARG, "out is NULL");
+    if (h->adj_src_grad.size() != h->sources.size() * 6)
+      fail(LTS_ERR_STATE, "no adjoint sweep with the current sources");
+    std::copy(h->adj_src_grad.begin(), h->adj_src_grad.end(), out);
   });
 }
 

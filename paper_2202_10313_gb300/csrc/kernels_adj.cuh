@@ -83,6 +83,25 @@ __global__ void k_adj_source(float* lam, int nsim, const int* elem, const float*
 }
 
 
+// Moment-tensor gradient of the point sources one neighbour pass added:
+// g[src][r] += c_s sum_b lambda_f[elem][r][b] phi_src[b], with c_s = -m0 (int s dt) / |det J|
+// of item s and lambda the adjoint of Q after the pass ([element][simulation][9][B]). One
+// thread per (item, stress component); a pass holds at most one item per source, so every
+// entry has one writer.
+template <int O>
+__global__ void k_adj_src_grad(const float* lam, int nsim, const SrcItem* items, const double* c, int n,
+                               const float* phi, double* g) {
+  constexpr int B = nbasis(O);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 6 * n) return;
+  const int s = t / 6, r = t % 6;
+  const SrcItem it = items[s];
+  const float* row = lam + ((size_t)it.elem * nsim + it.sim) * 9 * B + (size_t)r * B;
+  float v = 0.f;
+  for (int b = 0; b < B; ++b) v = fmaf(row[b], phi[it.phi_off + b], v);
+  g[(size_t)(it.phi_off / B) * 6 + r] += c[s] * (double)v;
+}
+
 // ------------------------------------------------------------------ clustered LTS adjoint
 // The LTS state is (Q, B1, B2, B3). Taken backwards, a neighbour pass of cluster l (step n)
 // that added S_N(X_i) to Q_k sends ((A+_i^T lambda_Q_k) F^_i^T) F-_{j,h}^T to the adjoint

@@ -31,6 +31,8 @@ struct Launchers {
                      float* out, cudaStream_t);
   void (*adj_source)(float* lam, int nsim, const int* elem, const float* phi, const float* res, int nrec,
                      cudaStream_t);
+  void (*adj_src_grad)(const float* lam, int nsim, const SrcItem* items, const double* c, int n, const float* phi,
+                       double* g, cudaStream_t);
   void (*adj_pred)(const DevOps&, const AdjLtsArgs&, const PhaseArgs&, int nelem, cudaStream_t);
   void (*adj_nbr)(const DevOps&, const AdjLtsArgs&, const PhaseArgs&, int K, cudaStream_t);
   // face-local messages of a partitioned run (one simulation)
@@ -109,6 +111,10 @@ struct Impl {
                          cudaStream_t st) {
     k_adj_source<O><<<1, 64, 0, st>>>(lam, nsim, elem, phi, res, nrec);
   }
+  static void adj_src_grad(const float* lam, int nsim, const SrcItem* items, const double* c, int n,
+                           const float* phi, double* g, cudaStream_t st) {
+    if (n > 0) k_adj_src_grad<O><<<(6 * n + 127) / 128, 128, 0, st>>>(lam, nsim, items, c, n, phi, g);
+  }
   // persistent: at most one CTA per SM, each CTA's element groups take elements in turn
   static void adj_pred(const DevOps& o, const AdjLtsArgs& a, const PhaseArgs& p, int n, cudaStream_t st) {
     using A = AdjPredCfg<O>;
@@ -154,6 +160,7 @@ struct Impl {
     if constexpr (M == 0) {
       L.adj_sample = &adj_sample;
       L.adj_source = &adj_source;
+      L.adj_src_grad = &adj_src_grad;
       L.adj_pred = &adj_pred;
       L.adj_nbr = &adj_nbr;
     }

@@ -334,6 +334,7 @@ def test_fused_adjoint_equals_the_sum_of_single_simulation_adjoints(F, clustered
     data = syn * 1.04 + 1e-9
     s = _fused_lts(order, m, rho, lam, mu, q0s, rec, srcs, cl, dt, F)
     J, g, syn_f, dq0 = s.misfit_gradient(n, data, every=1, want_dq0=True)
+    gsrc = s.source_gradient()   # source f drives simulation f only
     s.close()
     J1, g1 = 0.0, np.zeros_like(g)
     for f in range(F):
@@ -342,6 +343,8 @@ def test_fused_adjoint_equals_the_sum_of_single_simulation_adjoints(F, clustered
         else:
             t = _gpu(order, m, rho, lam, mu, q0s[f], rec, srcs[f], dt)
         Jf, gf, synf, dqf = t.misfit_gradient(n, data[:, f], every=1, want_dq0=True)
+        # a source beyond the adjoint's reach in n steps has a zero gradient in both runs
+        assert np.allclose(gsrc[f], t.source_gradient()[0], rtol=1e-4, atol=1e-6 * np.abs(gsrc).max()), f
         t.close()
         J1 += Jf
         g1 += gf
@@ -369,3 +372,54 @@ def test_autograd_function_fused():
     J2, g, _ = s.misfit_gradient(n, data, every=2)
     assert float(J.detach()) == J2
     assert np.array_equal(tl.grad.numpy(), g[:, 1]) and np.array_equal(tm.grad.numpy(), g[:, 2])
+
+
+@pytest.mark.parametrize("clustered", [True, False])
+def test_moment_tensor_gradient_against_central_differences(clustered):
+    """dJ/dm6 of two point sources (LTS with three forced clusters, and one cluster): J is
+    quadratic in m6, so central differences of the GPU misfit are exact up to FP32 rounding."""
+    order, n = 4, 8
+    m, mat, q0, rec, src = _case(order, seed=24)
+    rho, lam, mu = _rlm(mat)
+    cl = _forced_clusters(m)
+    src2 = (np.array([420.0, 260.0, -90.0]), np.array([-0.3, 0.5, 0.1, -0.2, 0.7, 0.4]), 12.0, 0.015, 8e11)
+    dt = 1.5e-4
+
+    def make(m6a, m6b):
+        s = binding.Solver(order, 0, device=0)
+        s.set_mesh(m["xyz"], m["tet"], m["face_bc"])
+        s.set_material(rho, np.sqrt((lam + 2 * mu) / rho), np.sqrt(mu / rho))
+        s.add_point_source(src[0], m6a, *src[2:])
+        s.add_point_source(src2[0], m6b, *src2[2:])
+        for x in rec:
+            s.add_receiver(x, dt)
+        if clustered:
+            s.force_clusters(cl, 3, 0.5, 1.0)
+        else:
+            s.setup_clusters(1, 0.5)
+        s.set_finest_dt(dt)
+        s.set_dofs(np.zeros_like(q0))   # the samples come from the sources alone
+        return s
+
+    rows = n // 4 + 1 if clustered else n + 1
+    s = make(src[1], src2[1])
+    _, syn = s.misfit(n, np.zeros((rows, 3, 3)), every=1)
+    s.close()
+    data = syn * 0.7 + 1e-10
+    s = make(src[1], src2[1])
+    s.misfit_gradient(n, data, every=1)
+    g = s.source_gradient()
+    s.close()
+    assert g.shape == (2, 6) and np.abs(g).max() > 0
+    for i, (m6, other) in enumerate([(src[1], src2[1]), (src2[1], src[1])]):
+        for r in range(6):
+            h = 0.5
+            vals = []
+            for sgn in (1, -1):
+                mm = m6.copy()
+                mm[r] += sgn * h
+                t = make(mm, other) if i == 0 else make(other, mm)
+                vals.append(t.misfit(n, data, every=1)[0])
+                t.close()
+            fd = (vals[0] - vals[1]) / (2 * h)
+            assert abs(fd - g[i, r]) <= 2e-3 * np.abs(g).max(), (i, r, fd, g[i, r])
