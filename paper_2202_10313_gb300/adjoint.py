@@ -143,6 +143,7 @@ def main():
     t0 = time.perf_counter()
     J, grad, _ = base.misfit_gradient(a.steps, data, every=a.checkpoint // period)
     t_grad = time.perf_counter() - t0
+    g_m6 = base.source_gradient()
     base.close()
     single = None
     if F > 1:   # one source alone, same material and data of that source
@@ -167,7 +168,8 @@ def main():
                finest_steps=a.steps, macro_steps=n_macro, checkpoint_finest_steps=a.checkpoint, receivers=len(rec),
                fused_sources=F, single_source_gradient_s=single,
                misfit=J, forward_s=t_fwd, misfit_and_gradient_s=t_grad, gradient_over_forward=t_grad / t_fwd,
-               grad_norm=[float(np.linalg.norm(grad[:, p])) for p in range(3)], fd_check_mu=fd)
+               grad_norm=[float(np.linalg.norm(grad[:, p])) for p in range(3)],
+               moment_tensor_gradient=g_m6.tolist(), fd_check_mu=fd)
     print(json.dumps(out))
 
 
