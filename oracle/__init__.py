@@ -21,6 +21,12 @@ It is a plain, slow, obviously-correct restatement of the method of
                  local/neighbour surface kernels, update (Eq. update), the LTS
                  buffers B1/B2/B3 and their use (Sec. V-B), global time stepping,
                  point source, receivers and the discrete energy.
+* ``partitioned`` -- a run split into parts that exchange the face-local messages
+                 H = X F-_{j,h} (Sec. V-C); pinned against the unpartitioned oracle.
+* ``adjoint`` -- discrete adjoint of the global-time-stepping and clustered-LTS loops for
+                 the seismogram misfit (Sec. VII-B) and the material derivatives of the
+                 star matrices and flux solvers; pinned by central differences of the
+                 oracle's own misfit.
 
 Parity status of each function is stated in its docstring; every function is
 pinned by a ``-m "not gpu"`` test except where the docstring says
