@@ -737,6 +737,7 @@ __global__ void __launch_bounds__(Cfg<O, M, FG>::NTN, Cfg<O, M, FG>::NMIN) k_nei
       int ee, i, f, pf;
       face_task_of<O, NE, (FG > 1)>(t, ee, i, f, pf);
       const int eel = (FG > 1) ? 0 : ee;
+      if (sI[eel * 9 + 8] < 0) continue;   // slot past the end of the phase: no face data
       const int code = sI[eel * 9 + 4 + i];
       const int jh = code & 0xff;
       float gq[9];
