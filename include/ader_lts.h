@@ -229,13 +229,13 @@ int lts_cut_faces(lts_t* h, const int32_t* part, int64_t cap, int64_t* faces, in
  * its neighbour contribution from a face-local message instead of the neighbour's buffer —
  * before each neighbour pass a pack kernel computes, on the sending side, H = X F-_{j,h}
  * for the cut faces whose receivers are active, and the receiver's neighbour kernel reads
- * it. The arithmetic is the one of the unpartitioned run, in the same order. One
- * simulation only. If clusters are set up, re-creates the device state (time 0, DOFs
- * zero). n_parts <= 1 (part may be NULL) switches it off. Errors: LTS_ERR_ARG, LTS_ERR_STATE. */
+ * it. The arithmetic is the one of the unpartitioned run, in the same order. Fused runs
+ * send one message per simulation. If clusters are set up, re-creates the device state
+ * (time 0, DOFs zero). n_parts <= 1 (part may be NULL) switches it off. Errors: LTS_ERR_ARG, LTS_ERR_STATE. */
 int lts_set_partition(lts_t* h, int n_parts, const int32_t* part);
 
 /* Face-local message bytes the partitioned run has produced so far (9 x F FP32 values per
- * active cut face and neighbour pass). */
+ * active cut face, simulation and neighbour pass). */
 int lts_exchange_bytes(lts_t* h, int64_t* bytes);
 
 /* Overrides the finest time step (after cluster set-up) with dt seconds, e.g. to hold the

@@ -100,7 +100,7 @@ struct lts_solver {
   std::vector<int64_t> cut_beg;             // cut faces by receiver cluster (device order), nc+1
   int64_t n_cut = 0;
   int* d_cut = nullptr;                     // [3][n_cut]: sender element, code, receiver cluster
-  float* d_msg = nullptr;                   // [n_cut][9][F]
+  float* d_msg = nullptr;                   // [n_cut][nsim][9][F]
   int64_t msg_bytes = 0;                    // face-local message bytes produced so far
   // macro steps replayed from CUDA graphs (one per parity of the macro-step index)
   bool use_graphs = true;
@@ -226,7 +226,7 @@ Layout layout_of(const lts_solver* h, int64_t K) {
         if (nb >= 0 && h->part[nb] != h->part[k]) ++ncut;
       }
   L.cut = take(sizeof(int) * 3 * std::max<int64_t>(1, ncut));
-  L.msg = take(sizeof(float) * 9 * X.F * std::max<int64_t>(1, ncut));
+  L.msg = take(sizeof(float) * 9 * X.F * h->nsim * std::max<int64_t>(1, ncut));
   L.total = off;
   return L;
 }
@@ -704,7 +704,7 @@ int64_t macro_msg_bytes(const lts_solver* h, const MacroPlan& mp) {
   if (h->n_parts <= 1) return 0;
   for (const Phase& ph : mp.phases)
     if (ph.kind == 0 && h->cbeg[ph.top + 1] > 0)
-      b += h->cut_beg[ph.top + 1] * 9 * (int64_t)h->L.F * (int64_t)sizeof(float);
+      b += h->cut_beg[ph.top + 1] * h->nsim * 9 * (int64_t)h->L.F * (int64_t)sizeof(float);
   return b;
 }
 
@@ -1928,7 +1928,6 @@ int lts_set_partition(lts_t* h, int n_parts, const int32_t* part) {
     require_material(h);
     if (n_parts > 1) {
       if (!part) fail(LTS_ERR_ARG, "null part array");
-      if (h->nsim != 1) fail(LTS_ERR_ARG, "partitioned runs take one simulation");
       for (int64_t k = 0; k < h->mesh.K; ++k)
         if (part[k] < 0 || part[k] >= n_parts) fail(LTS_ERR_ARG, "part index out of range");
       h->part.assign(part, part + h->mesh.K);

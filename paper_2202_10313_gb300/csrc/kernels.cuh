@@ -113,7 +113,7 @@ struct DevState {
   const int* nbr;        // [K][4] neighbour (internal index) or -1
   const int* ncode;      // [K][4] (j*3+h) | (relation << 8): 0 same, 1 neighbour finer, 2 neighbour coarser
   const int* meta;       // [K] cluster | FLAG_*
-  const float* msg;      // [cut faces][9][F] face-local messages of a partitioned run (else unused)
+  const float* msg;      // [cut faces][nsim][9][F] face-local messages of a partitioned run (else unused)
 };
 
 struct PhaseArgs {
@@ -744,8 +744,9 @@ __global__ void __launch_bounds__(Cfg<O, M, FG>::NTN, Cfg<O, M, FG>::NMIN) k_nei
 #pragma unroll
       for (int r = 0; r < 9; ++r) gq[r] = 0.f;
       if (code & FACE_REMOTE) {
-        // computed by the neighbour's partition (k_pack_faces)
-        const float* h = st.msg + (size_t)sI[eel * 9 + i] * 9 * F + f;
+        // computed by the neighbour's partition (k_pack_faces), one message per simulation
+        const int sim = (FG > 1) ? grp * FG + ee : 0;
+        const float* h = st.msg + ((size_t)sI[eel * 9 + i] * nsim + sim) * 9 * F + f;
 #pragma unroll
         for (int r = 0; r < 9; ++r) gq[r] = h[r * F];
       } else {
@@ -796,12 +797,13 @@ __global__ void __launch_bounds__(Cfg<O, M, FG>::NTN, Cfg<O, M, FG>::NMIN) k_nei
 // values it would have computed itself. One thread per (cut face, face mode).
 template <int O, int M>
 __global__ void k_pack_faces(DevOps ops, DevState st, PhaseArgs ph, const int* send_elem, const int* send_code,
-                             const int* recv_cluster, int n, float* msg) {
+                             const int* recv_cluster, int n, int fg, float* msg) {
   using C = Cfg<O, M>;
-  constexpr int B = C::B, F = C::F, BUFS = C::BUFS;
+  constexpr int B = C::B, F = C::F;
+  const int nsim = st.nsim;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n * F) return;
-  const int c = t / F, f = t % F;
+  if (t >= n * nsim * F) return;
+  const int c = t / (nsim * F), sim = (t / F) % nsim, f = t % F;
   int pf = 0;
   while (nface(pf + 1) <= f) ++pf;
   const int code = send_code[c];
@@ -809,7 +811,8 @@ __global__ void k_pack_faces(DevOps ops, DevState st, PhaseArgs ph, const int* s
   const int par = ph.parity[recv_cluster[c]];
   const float* src1 = (rel == 1) ? st.B3 : ((rel == 2 && par == 0) ? st.B2 : st.B1);
   const bool sub = (rel == 2 && par == 1);
-  const size_t off = (size_t)send_elem[c] * BUFS;
+  // simulation sim's rows in the sender's buffer (groups of fg simulations, innermost)
+  const size_t off = (size_t)send_elem[c] * st.bs + (size_t)(sim / fg) * (9 * B * fg) + sim % fg;
   const float* Fm = ops.Fb + jh * B * F + f;
   float gq[9];
 #pragma unroll
@@ -819,13 +822,13 @@ __global__ void k_pack_faces(DevOps ops, DevState st, PhaseArgs ph, const int* s
     const float w = Fm[k * F];
 #pragma unroll
     for (int r = 0; r < 9; ++r) {
-      float x = __ldg(src1 + off + r * B + k);
-      if (sub) x -= __ldg(st.B2 + off + r * B + k);
+      float x = __ldg(src1 + off + (size_t)(r * B + k) * fg);
+      if (sub) x -= __ldg(st.B2 + off + (size_t)(r * B + k) * fg);
       gq[r] = fmaf(x, w, gq[r]);
     }
   }
 #pragma unroll
-  for (int r = 0; r < 9; ++r) msg[((size_t)c * 9 + r) * F + f] = gq[r];
+  for (int r = 0; r < 9; ++r) msg[(((size_t)c * nsim + sim) * 9 + r) * F + f] = gq[r];
 }
 
 // ------------------------------------------------------------------ receivers

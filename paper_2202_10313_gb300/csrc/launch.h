@@ -100,8 +100,8 @@ struct Impl {
   }
   static void pack(const DevOps& o, const DevState& s, const PhaseArgs& p, const int* se, const int* sc,
                    const int* rc, int n, float* msg, cudaStream_t st) {
-    const int threads = 128, nt = n * C::F;
-    k_pack_faces<O, M><<<(nt + threads - 1) / threads, threads, 0, st>>>(o, s, p, se, sc, rc, n, msg);
+    const int threads = 128, nt = n * s.nsim * C::F;   // one thread per (cut face, simulation, face mode)
+    k_pack_faces<O, M><<<(nt + threads - 1) / threads, threads, 0, st>>>(o, s, p, se, sc, rc, n, FG, msg);
   }
   static void adj_sample(const float* Q, long long qs, int nsim, int G, const int* elem, const float* phi, int nrec,
                          float* out, cudaStream_t st) {

@@ -69,13 +69,6 @@ def test_partition_with_tensor_cores_and_switch_off():
     gpu.set_dofs(d0)
     gpu.advance_steps(4)
     assert np.array_equal(a, gpu.get_dofs())
-    f = binding.Solver(5, 3, device=0, n_fused=4)
-    f.set_mesh(m["xyz"], m["tet"], m["face_bc"])
-    f.set_material(mat["rho"], mat["vp"], mat["vs"], mat["qp"], mat["qs"], 0.1, 5.0)
-    f.setup_clusters(3, 0.5)
-    with pytest.raises(binding.LtsError) as ei:
-        f.set_partition(part, 4)
-    assert ei.value.code == binding.LTS_ERR_ARG
 
 
 def test_adjoint_of_a_partitioned_run_equals_the_unpartitioned_adjoint():
@@ -104,3 +97,47 @@ def test_adjoint_of_a_partitioned_run_equals_the_unpartitioned_adjoint():
         gpu.close()
     for a, b in zip(out[0], out[1]):
         assert np.array_equal(np.asarray(a), np.asarray(b))
+
+
+@pytest.mark.parametrize("F", [4, 8])
+def test_fused_partitioned_run_equals_fused_unpartitioned(F):
+    """Fused simulations in a partitioned run: one face-local message per simulation and cut
+    face; every simulation bitwise equal to the fused unpartitioned run, message bytes F times
+    those of one simulation."""
+    order, n_mech = 5, 3
+    m = synth.permute_vertex_order(synth.graded_box(6, 5, 3, 250.0, 125.0, seed=12), seed=2)
+    mat = synth.random_layers(m, n_layers=3, seed=5)
+    K = m["tet"].shape[0]
+    nq, nb = 27, 35
+    d0 = np.stack([synth.random_dofs(K, nq, nb, seed=30 + f) for f in range(F)])
+    lo, hi = m["xyz"].min(axis=0), m["xyz"].max(axis=0)
+    pos, m6, f0 = synth.random_sources(F, lo + 0.2 * (hi - lo), hi - 0.2 * (hi - lo), f0_range=(4.0, 8.0), seed=3)
+    runs, xbytes = [], []
+    for parted in (False, True):
+        g = binding.Solver(order, n_mech, device=0, n_fused=F)
+        g.set_mesh(m["xyz"], m["tet"], m["face_bc"])
+        g.set_material(mat["rho"], mat["vp"], mat["vs"], mat["qp"], mat["qs"], 0.1, 5.0)
+        for f in range(F):
+            g.add_point_source(pos[f], m6[f], f0[f], 0.1, 1e12, fused_idx=f)
+        g.setup_clusters(3, 0.5)
+        if parted:
+            part, _ = g.partition(3)
+            g.set_partition(part, 3)
+        g.set_dofs(d0)
+        g.advance_steps(8)
+        runs.append(g.get_dofs())
+        xbytes.append(g.exchange_bytes())
+        g.close()
+    assert np.array_equal(runs[0], runs[1])
+    assert xbytes[0] == 0 and xbytes[1] > 0
+    # one simulation: the same cut, 1/F of the bytes
+    s = binding.Solver(order, n_mech, device=0)
+    s.set_mesh(m["xyz"], m["tet"], m["face_bc"])
+    s.set_material(mat["rho"], mat["vp"], mat["vs"], mat["qp"], mat["qs"], 0.1, 5.0)
+    s.setup_clusters(3, 0.5)
+    part, _ = s.partition(3)
+    s.set_partition(part, 3)
+    s.set_dofs(d0[0])
+    s.advance_steps(8)
+    assert xbytes[1] == F * s.exchange_bytes()
+    s.close()
