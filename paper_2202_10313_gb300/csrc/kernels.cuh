@@ -59,7 +59,14 @@ struct Cfg {
   // staged Riemann states (v*, t*: 6 values) per face mode: a stride of 12 floats keeps the
   // 16-byte stores of 8 consecutive tasks on 8 distinct 4-bank groups
   static constexpr int FR = 12;
-  static constexpr int XR = 9;                       // gathered neighbour rows (odd stride)
+  // gathered neighbour rows: a stride of 10 floats gives 8-byte row loads and keeps the
+  // 8-byte stores of 16 consecutive modes on distinct bank pairs
+  static constexpr int XR = 10;
+  // k_neighbour's staged Riemann states: 8 floats per face mode, and a slot stride of 4 banks
+  // mod 32 so that the 16-byte reads of neighbouring slots do not collide
+  static constexpr int FRN = 8;
+  static constexpr int FLSN = 4 * F * FRN + 4;
+  static constexpr int NPAIR = (F + 1) / 2;           // face-mode pairs of the neighbour product
   // time kernel load balance: columns of degree <= O-3 split their k-range with a
   // helper thread that owns a degree O-1 column (which has no time-kernel product)
   static constexpr int NSPLIT = nbasis(O - 2);
@@ -85,7 +92,7 @@ struct Cfg {
   static constexpr int N_FH = rup(N_FB + 12 * B * F, 4);
   static constexpr int N_X = rup(N_FH + 4 * F * B, 4);
   static constexpr int N_FL = rup(N_X + NEN * 4 * B * XR, 4);
-  static constexpr int N_D = rup(N_FL + NEN * FLS, 4);
+  static constexpr int N_D = rup(N_FL + NEN * FLSN, 4);
   static constexpr int N_I = rup(N_D + NELN * ND, 4);      // ints: nbr[4], code[4], meta per element
   static constexpr int N_TOTAL = rup(N_I + NELN * 9, 4);
 };
@@ -173,6 +180,35 @@ __device__ __forceinline__ void face_task_of(int t, int& ee, int& i, int& f, int
     }
     off += n;
   }
+}
+
+// Polynomial degree of face mode f (modes are ordered by degree).
+__device__ __forceinline__ int face_degree(int f) {
+  int q = 0;
+  while (nface(q + 1) <= f) ++q;
+  return q;
+}
+
+// Face-mode pair tasks of the neighbour product: pair a holds modes F-1-2a and F-2-2a (the
+// second absent when F is odd and a is the last pair), i.e. modes of equal or neighbouring
+// degree, so that the pair's k-range (that of its lower-degree mode) adds few zero terms.
+// Pairs vary fastest, so the threads of one face share its staged rows (SF = false), or
+// the slot does (SF = true: fused simulations).
+template <int NE, int NPAIR, bool SF = false>
+__device__ __forceinline__ void face_pair_of(int t, int& ee, int& i, int& a) {
+  if (SF) {
+    ee = t % NE;
+    a = (t / NE) % NPAIR;
+    i = t / (NE * NPAIR);
+  } else {
+    ee = t / (4 * NPAIR);
+    i = (t / NPAIR) % 4;
+    a = t % NPAIR;
+  }
+}
+
+__device__ __forceinline__ void st2(float* p, float a, float b) {
+  *reinterpret_cast<float2*>(p) = make_float2(a, b);
 }
 
 __device__ __forceinline__ void st4(float* p, float a, float b, float c, float d) {
@@ -633,7 +669,8 @@ __global__ void __launch_bounds__(Cfg<O, M, FG>::NT, Cfg<O, M, FG>::PMIN) k_pred
 template <int O, int M, int FG>
 __global__ void __launch_bounds__(Cfg<O, M, FG>::NTN, Cfg<O, M, FG>::NMIN) k_neighbour(DevOps ops, DevState st, PhaseArgs ph) {
   using C = Cfg<O, M, FG>;
-  constexpr int B = C::B, F = C::F, NE = C::NEN, NEL = C::NELN, NT = C::NTN, FR = C::FR, XR = C::XR;
+  constexpr int B = C::B, F = C::F, NE = C::NEN, NEL = C::NELN, NT = C::NTN, FR = C::FRN, XR = C::XR;
+  constexpr int NPAIR = C::NPAIR;
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
   float* sFb = smem + C::N_FB;
@@ -643,7 +680,14 @@ __global__ void __launch_bounds__(Cfg<O, M, FG>::NTN, Cfg<O, M, FG>::NMIN) k_nei
   float* sD = smem + C::N_D;
   int* sI = reinterpret_cast<int*>(smem + C::N_I);   // per element: nbr[4], code[4], meta
   const int tid = threadIdx.x;
-  for (int i = tid; i < 12 * B * F; i += NT) sFb[i] = ops.Fb[i];
+  // F-_{j,h}[k][f] vanishes for deg k < deg f (the trace of a lower-degree polynomial is
+  // orthogonal to face mode f); those entries are staged as exact zeros, so that a face-mode
+  // pair may run over the k-range of its lower-degree mode and the other mode's extra terms
+  // add nothing
+  for (int i = tid; i < 12 * B * F; i += NT) {
+    const int f = i % F, k = (i / F) % B;
+    sFb[i] = (k < nbasis(face_degree(f))) ? 0.f : ops.Fb[i];
+  }
   for (int i = tid; i < 4 * F * B; i += NT) sFh[i] = ops.Fh[i];
 
   int e = -1, b = 0, p = 0;
@@ -726,42 +770,65 @@ __global__ void __launch_bounds__(Cfg<O, M, FG>::NTN, Cfg<O, M, FG>::NMIN) k_nei
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         float* x = sX + ((e * 4 + i) * B + b) * XR;
-#pragma unroll
-        for (int r = 0; r < 9; ++r) x[r] = xv[i][r];
+        st2(x, xv[i][0], xv[i][1]);
+        st2(x + 2, xv[i][2], xv[i][3]);
+        st2(x + 4, xv[i][4], xv[i][5]);
+        st2(x + 6, xv[i][6], xv[i][7]);
+        x[8] = xv[i][8];
       }
     }
     __syncthreads();
-    // ---- H_i = X F-_{j,h}, closed-form interface states with the neighbour's coefficients
+    // ---- H_i = X F-_{j,h} for two face modes per task (they share the staged rows),
+    // closed-form interface states with the neighbour's coefficients
 #pragma unroll 1
-    for (int t = tid; t < NE * 4 * F; t += NT) {
-      int ee, i, f, pf;
-      face_task_of<O, NE, (FG > 1)>(t, ee, i, f, pf);
+    for (int t = tid; t < NE * 4 * NPAIR; t += NT) {
+      int ee, i, a;
+      face_pair_of<NE, NPAIR, (FG > 1)>(t, ee, i, a);
       const int eel = (FG > 1) ? 0 : ee;
       if (sI[eel * 9 + 8] < 0) continue;   // slot past the end of the phase: no face data
+      const int f1 = F - 1 - 2 * a, f2 = f1 - 1;     // f2 < 0: f1 alone
+      const int f2r = (f2 >= 0) ? f2 : f1;
       const int code = sI[eel * 9 + 4 + i];
       const int jh = code & 0xff;
-      float gq[9];
+      float g1[9], g2[9];
 #pragma unroll
-      for (int r = 0; r < 9; ++r) gq[r] = 0.f;
+      for (int r = 0; r < 9; ++r) g1[r] = g2[r] = 0.f;
       if (code & FACE_REMOTE) {
         // computed by the neighbour's partition (k_pack_faces), one message per simulation
         const int sim = (FG > 1) ? grp * FG + ee : 0;
-        const float* h = st.msg + ((size_t)sI[eel * 9 + i] * nsim + sim) * 9 * F + f;
+        const float* h = st.msg + ((size_t)sI[eel * 9 + i] * nsim + sim) * 9 * F;
 #pragma unroll
-        for (int r = 0; r < 9; ++r) gq[r] = h[r * F];
+        for (int r = 0; r < 9; ++r) {
+          g1[r] = h[r * F + f1];
+          g2[r] = h[r * F + f2r];
+        }
       } else {
         const float* X = sX + (ee * 4 + i) * B * XR;
-        const float* Fm = sFb + jh * B * F + f;
+        const float* Fm = sFb + jh * B * F;
 #pragma unroll 4
-        for (int k = nbasis(pf); k < B; ++k) {
-          const float w = Fm[k * F];
+        for (int k = nbasis(face_degree(f2r)); k < B; ++k) {
+          const float2 x01 = *reinterpret_cast<const float2*>(X + k * XR);
+          const float2 x23 = *reinterpret_cast<const float2*>(X + k * XR + 2);
+          const float2 x45 = *reinterpret_cast<const float2*>(X + k * XR + 4);
+          const float2 x67 = *reinterpret_cast<const float2*>(X + k * XR + 6);
+          const float xs[9] = {x01.x, x01.y, x23.x, x23.y, x45.x, x45.y, x67.x, x67.y, X[k * XR + 8]};
+          const float w1 = Fm[k * F + f1], w2 = Fm[k * F + f2r];
 #pragma unroll
-          for (int r = 0; r < 9; ++r) gq[r] = fmaf(X[k * XR + r], w, gq[r]);
+          for (int r = 0; r < 9; ++r) {
+            g1[r] = fmaf(xs[r], w1, g1[r]);
+            g2[r] = fmaf(xs[r], w2, g2[r]);
+          }
         }
       }
+      const float* fd = sD + eel * ND + 4 + 11 * i;
+      float* fl = sFl + ee * C::FLSN + i * F * FR;
       float w6[6];
-      riemann_state(gq, sD + eel * ND + 4 + 11 * i, w6);
-      store_state(sFl + ee * C::FLS + (i * F + f) * FR, w6);
+      riemann_state(g1, fd, w6);
+      store_state(fl + f1 * FR, w6);
+      if (f2 >= 0) {
+        riemann_state(g2, fd, w6);
+        store_state(fl + f2 * FR, w6);
+      }
     }
     __syncthreads();
     if (valid) {
@@ -776,7 +843,7 @@ __global__ void __launch_bounds__(Cfg<O, M, FG>::NTN, Cfg<O, M, FG>::NMIN) k_nei
 #pragma unroll
       for (int r = 0; r < NS; ++r) S[r] = 0.f;
       const float* nd = sD + eb * ND;
-      project_faces<NS, F, B, FR>(sFl + e * C::FLS, sFh, nd + 4, 11, nd[0], nd[1], nd[2], fmax, b, S);
+      project_faces<NS, F, B, FR>(sFl + e * C::FLSN, sFh, nd + 4, 11, nd[0], nd[1], nd[2], fmax, b, S);
 #pragma unroll
       for (int r = 0; r < 9; ++r) q[r * rs] = qv[r] + S[r];
       if constexpr (M > 0) {
