@@ -378,16 +378,19 @@ __global__ void __launch_bounds__(Cfg<O, M, FG>::NT, Cfg<O, M, FG>::PMIN) k_pred
   task_of<O, NE, (FG > 1)>(tid, e, b, p);
   const bool act = e >= 0;
   const int es = act ? e : 0;
-  // time-kernel product of this thread: column ck_col over k in [ck_k0, ck_k1)
+  // time-kernel product of this thread: column ck_col over a k-range set per derivative
   const int hj = b - nbasis(O - 1);                    // index among the degree O-1 columns
   const bool helper = act && p == O - 1 && hj < NSPLIT;
   const bool split_owner = act && b < NSPLIT;
+  // (k-range of the first derivative; a split owner takes the first half of its column's
+  // range, the helper the second)
   auto kmid = [](int col, int pd) { return (nbasis(pd + 1) + B + 1) / 2; };
-  int ck_col = b, ck_k0 = nbasis(p + 1), ck_k1 = B;
+  int ck_col = b, ck_p = p, ck_k0 = nbasis(p + 1), ck_k1 = B;
   if (helper) {
     int ph_ = 0;
     while (nbasis(ph_ + 1) <= hj) ++ph_;
     ck_col = hj;
+    ck_p = ph_;
     ck_k0 = kmid(hj, ph_);
     ck_k1 = B;
   } else if (split_owner) {
@@ -465,10 +468,20 @@ __global__ void __launch_bounds__(Cfg<O, M, FG>::NT, Cfg<O, M, FG>::PMIN) k_pred
 #pragma unroll
         for (int r = 0; r < 9; ++r) Y[c][r] = 0.f;
       {
+        // X = d^d Q: column ck_col needs the modes k of degree > deg ck_col. Elastic: d^d Q
+        // has degree <= O-1-d (each derivative is one spatial derivative), so only the first
+        // nbasis(O-d) modes are nonzero; the anelastic coupling keeps every degree
+        int k0 = ck_k0, k1 = ck_k1;
+        if constexpr (M == 0) {
+          const int kend = nbasis(O - d);
+          const int kb = nbasis(ck_p + 1), km = max(kb, (kb + kend + 1) / 2);
+          k0 = act ? (helper ? km : kb) : 0;
+          k1 = act ? (split_owner ? km : kend) : 0;
+        }
         const float* Ab = sA + ((buf * NE + es) * B) * AR;
         const float* K0 = sK + ck_col * BS * 4;
 #pragma unroll 4
-        for (int k = ck_k0; k < ck_k1; ++k) {
+        for (int k = k0; k < k1; ++k) {
           const float4 x0 = *reinterpret_cast<const float4*>(Ab + k * AR);
           const float4 x1 = *reinterpret_cast<const float4*>(Ab + k * AR + 4);
           const float x8 = Ab[k * AR + 8];

@@ -27,14 +27,17 @@ def flops_predict(o, m):
     B, F, NQ = nbasis(o), nface(o), 9 + 6 * m
     degs = _col_degrees(o)
     fdeg = [p for p in range(o) for _ in range(p + 1)]
-    ck_gemm = 27 * sum(B - nbasis(p + 1) for p in degs)
+    # time kernel, summed over the derivatives d = 0 .. o-2: column b takes the modes k of
+    # degree > deg b of d^d Q; elastic: d^d Q has degree <= o-1-d, so k < nbasis(o-d)
+    kend = [nbasis(o - d) if m == 0 else B for d in range(o - 1)]
+    ck_gemm = 27 * sum(max(0, ke - nbasis(p + 1)) for ke in kend for p in degs)
     vol_gemm = 27 * sum(nbasis(p) for p in degs)
     star = 2 * 54 + 20                              # W_d combinations + Hooke / momentum
     ck_epi = star + m * 24 + m * 12 + 2 * (NQ + 9)  # coupling, relaxation, Taylor sums
     vol_epi = star + m * 24 + m * 12 + NQ
     surf_g, flux, surf_h = _surface(o, m)
     upd = B * (NQ + 2 * 6 * m)
-    return (o - 1) * (2 * ck_gemm + B * ck_epi) + 2 * vol_gemm + B * vol_epi + surf_g + flux + surf_h + upd
+    return 2 * ck_gemm + (o - 1) * B * ck_epi + 2 * vol_gemm + B * vol_epi + surf_g + flux + surf_h + upd
 
 
 def _surface(o, m):
@@ -93,10 +96,16 @@ def essential_flops(order, m):
     """Flops of one element update if only the true nonzeros of K_c, F~ and F- were
     multiplied (the kernels multiply whole degree blocks: flops_predict + flops_neighbour);
     the star, flux and Taylor arithmetic is counted as in the block model."""
+    import numpy as np
+    from . import binding
     nzs = operator_nonzeros(order)
     B, F, NQ = nbasis(order), nface(order), 9 + 6 * m
-    ck = 2 * 9 * sum(nzs["K"])                     # one derivative, 3 products of 9 rows
-    vol = ck
+    K = binding.reference_operators(order)[0]
+    nzk = lambda a: int(np.sum(np.abs(a) > 1e-9 * np.abs(K).max()))
+    # one derivative: 3 products of 9 rows; elastic: only the modes k < nbasis(order-d) of d^d Q
+    ck = sum(2 * 9 * sum(nzk(K[c][:, :(nbasis(order - d) if m == 0 else B)]) for c in range(3))
+             for d in range(order - 1))
+    vol = 2 * 9 * sum(nzs["K"])
     face_g = 2 * 9 * sum(nzs["Ft"])
     face_h = 2 * 6 * sum(nzs["Ft"])                # F^ = F~^T
     nbr_g = 2 * 9 * sum(nzs["Fb"][0]) / 3.0 * 4    # one F- per face
@@ -105,4 +114,4 @@ def essential_flops(order, m):
     epi = (order - 1) * B * (star + m * 36 + 2 * (NQ + 9)) + B * (star + m * 36 + NQ)
     flux = 2 * 4 * F * 50 + 2 * B * 4 * (30 + (18 if m else 0))
     upd = 2 * B * (NQ + 12 * m)
-    return (order - 1) * ck + vol + face_g + face_h + nbr_g + face_h + epi + flux + upd
+    return ck + vol + face_g + face_h + nbr_g + face_h + epi + flux + upd
