@@ -189,22 +189,19 @@ __device__ __forceinline__ int face_degree(int f) {
   return q;
 }
 
-// Face-mode pair tasks of the neighbour product: pair a holds modes F-1-2a and F-2-2a (the
+// Face-mode pair tasks of the face products: pair a holds modes F-1-2a and F-2-2a (the
 // second absent when F is odd and a is the last pair), i.e. modes of equal or neighbouring
 // degree, so that the pair's k-range (that of its lower-degree mode) adds few zero terms.
-// Pairs vary fastest, so the threads of one face share its staged rows (SF = false), or
-// the slot does (SF = true: fused simulations).
-template <int NE, int NPAIR, bool SF = false>
+// The pair index varies slowest: the threads of a warp then walk the same k together, and
+// a staged row read is one broadcast per slot instead of one address per pair (shared
+// memory serves a 16-byte load in quarter-warp phases, a 4-byte broadcast in one). Within
+// a pair the slot varies fastest for fused simulations (SF), else the face.
+template <int NE, bool SF = false>
 __device__ __forceinline__ void face_pair_of(int t, int& ee, int& i, int& a) {
-  if (SF) {
-    ee = t % NE;
-    a = (t / NE) % NPAIR;
-    i = t / (NE * NPAIR);
-  } else {
-    ee = t / (4 * NPAIR);
-    i = (t / NPAIR) % 4;
-    a = t % NPAIR;
-  }
+  a = t / (4 * NE);
+  const int r = t % (4 * NE);
+  ee = SF ? r % NE : r / 4;
+  i = SF ? r / NE : r % 4;
 }
 
 __device__ __forceinline__ void st2(float* p, float a, float b) {
@@ -371,7 +368,11 @@ __global__ void __launch_bounds__(Cfg<O, M, FG>::NT, Cfg<O, M, FG>::PMIN) k_pred
     const int c = i % 4, rc = i / 4, r = rc / BS, col = rc % BS;
     sK[i] = (c < 3 && col < B) ? ops.K[(c * B + r) * B + col] : 0.f;
   }
-  for (int i = tid; i < 4 * B * F; i += NT) sFt[i] = ops.Ft[i];
+  // F~_i[k][f] vanishes for deg k < deg f; staged as exact zeros (see the neighbour kernel)
+  for (int i = tid; i < 4 * B * F; i += NT) {
+    const int f = i % F, k = (i / F) % B;
+    sFt[i] = (k < nbasis(face_degree(f))) ? 0.f : ops.Ft[i];
+  }
   for (int i = tid; i < 4 * F * B; i += NT) sFh[i] = ops.Fh[i];
 
   int e = -1, b = 0, p = 0;
@@ -399,7 +400,6 @@ __global__ void __launch_bounds__(Cfg<O, M, FG>::NT, Cfg<O, M, FG>::PMIN) k_pred
   if (!act) ck_k0 = ck_k1 = 0;
   const int ke_vol = nbasis(p);         // K_c[k][b] != 0 needs deg k < deg b
   const int fmax = nface(p + 1);        // face modes of degree <= deg b
-  int fe = -1, fi = 0, ff = 0, fpf = 0;  // first face task of this thread (second one below)
   const int nelem = ph.end - ph.begin;
   // element strides and simulation count: compile-time constants for one simulation
   const long long qs = (FG > 1) ? st.qs : C::QS, bs = (FG > 1) ? st.bs : C::BUFS;
@@ -622,34 +622,40 @@ __global__ void __launch_bounds__(Cfg<O, M, FG>::NT, Cfg<O, M, FG>::PMIN) k_pred
             acc[9 + 6 * l + r] = q[(9 + 6 * l + r) * rs] + ph.omega[l] * (-eps[r] - T[9 + 6 * l + r]);
       }
     }
-    // ---- local surface kernel: G_i = T^e F~_i, flux, staged for F^
+    // ---- local surface kernel: G_i = T^e F~_i for two face modes per task (as in the
+    // neighbour kernel), flux, staged for F^
 #pragma unroll 1
-    for (int t = tid; t < NE * 4 * F; t += NT) {
-      face_task_of<O, NE, (FG > 1)>(t, fe, fi, ff, fpf);
-      float gq[9];
+    for (int t = tid; t < NE * 4 * C::NPAIR; t += NT) {
+      int fe, fi, a;
+      face_pair_of<NE, (FG > 1)>(t, fe, fi, a);
+      const int f1 = F - 1 - 2 * a, f2 = f1 - 1;     // f2 < 0: f1 alone
+      const int f2r = (f2 >= 0) ? f2 : f1;
+      float g1[9], g2[9];
 #pragma unroll
-      for (int r = 0; r < 9; ++r) gq[r] = 0.f;
+      for (int r = 0; r < 9; ++r) g1[r] = g2[r] = 0.f;
       const float* Ab = sA + ((buf * NE + fe) * B) * AR;
-      const float* Fi = sFt + fi * B * F + ff;
+      const float* Fi = sFt + fi * B * F;
 #pragma unroll 4
-      for (int k = nbasis(fpf); k < B; ++k) {
+      for (int k = nbasis(face_degree(f2r)); k < B; ++k) {
         const float4 x0 = *reinterpret_cast<const float4*>(Ab + k * AR);
         const float4 x1 = *reinterpret_cast<const float4*>(Ab + k * AR + 4);
-        const float x8 = Ab[k * AR + 8];
-        const float w = Fi[k * F];
-        gq[0] = fmaf(x0.x, w, gq[0]);
-        gq[1] = fmaf(x0.y, w, gq[1]);
-        gq[2] = fmaf(x0.z, w, gq[2]);
-        gq[3] = fmaf(x0.w, w, gq[3]);
-        gq[4] = fmaf(x1.x, w, gq[4]);
-        gq[5] = fmaf(x1.y, w, gq[5]);
-        gq[6] = fmaf(x1.z, w, gq[6]);
-        gq[7] = fmaf(x1.w, w, gq[7]);
-        gq[8] = fmaf(x8, w, gq[8]);
+        const float xs[9] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w, Ab[k * AR + 8]};
+        const float w1 = Fi[k * F + f1], w2 = Fi[k * F + f2r];
+#pragma unroll
+        for (int r = 0; r < 9; ++r) {
+          g1[r] = fmaf(xs[r], w1, g1[r]);
+          g2[r] = fmaf(xs[r], w2, g2[r]);
+        }
       }
+      const float* fd = sE + ((FG > 1) ? 0 : fe) * ED + 20 + 11 * fi;
+      float* fl = sFl + fe * C::FLS + fi * F * FR;
       float w6[6];
-      riemann_state(gq, sE + ((FG > 1) ? 0 : fe) * ED + 20 + 11 * fi, w6);
-      store_state(sFl + fe * C::FLS + (fi * F + ff) * FR, w6);
+      riemann_state(g1, fd, w6);
+      store_state(fl + f1 * FR, w6);
+      if (f2 >= 0) {
+        riemann_state(g2, fd, w6);
+        store_state(fl + f2 * FR, w6);
+      }
     }
     __syncthreads();
     if (valid) {
@@ -796,7 +802,7 @@ __global__ void __launch_bounds__(Cfg<O, M, FG>::NTN, Cfg<O, M, FG>::NMIN) k_nei
 #pragma unroll 1
     for (int t = tid; t < NE * 4 * NPAIR; t += NT) {
       int ee, i, a;
-      face_pair_of<NE, NPAIR, (FG > 1)>(t, ee, i, a);
+      face_pair_of<NE, (FG > 1)>(t, ee, i, a);
       const int eel = (FG > 1) ? 0 : ee;
       if (sI[eel * 9 + 8] < 0) continue;   // slot past the end of the phase: no face data
       const int f1 = F - 1 - 2 * a, f2 = f1 - 1;     // f2 < 0: f1 alone
