@@ -44,6 +44,10 @@ template <int O, int M, int FG = 1>
 struct Cfg {
   static constexpr int B = nbasis(O), F = nface(O), NQ = 9 + 6 * M, NA = 6 * M;
   static constexpr int BS = (B % 2) ? B : B + 1;     // odd row stride: conflict-free rows and columns
+  // staged K_c: three planes [c][row][col], odd row stride KS, read as 4-byte loads (a thread
+  // reads its own column: three distinct-bank loads per k instead of one padded 16-byte load
+  // that shared memory serves in four quarter-warp phases)
+  static constexpr int KS = BS + 2;
   static constexpr int QS = rup(NQ * B, 4);          // element stride of Q
   static constexpr int BUFS = rup(9 * B, 4);         // element stride of B1/B2/B3
   // elements per CTA: 7 x 35 columns = 8 warps at order 5, so two CTAs fit with up to
@@ -73,7 +77,7 @@ struct Cfg {
   static constexpr int SPR = 28;                     // floats per staged partial (27 + pad)
   // shared memory (floats) of k_predict_local
   static constexpr int P_K = 0;                      // K_c[row][col] at ((row * BS + col) * 4 + c)
-  static constexpr int P_FT = rup(P_K + 4 * B * BS, 4);
+  static constexpr int P_FT = rup(P_K + 3 * B * KS, 4);
   static constexpr int P_FH = rup(P_FT + 4 * B * F, 4);
   static constexpr int P_A = rup(P_FH + 4 * F * B, 4);
   static constexpr int P_FL = rup(P_A + 2 * NE * B * AR, 4);
@@ -350,7 +354,7 @@ __device__ __forceinline__ void project_faces(const float* Fl, const float* sFh,
 template <int O, int M, int FG>
 __global__ void __launch_bounds__(Cfg<O, M, FG>::NT, Cfg<O, M, FG>::PMIN) k_predict_local(DevOps ops, DevState st, PhaseArgs ph) {
   using C = Cfg<O, M, FG>;
-  constexpr int B = C::B, F = C::F, NE = C::NE, NEL = C::NEL, NT = C::NT, BS = C::BS, AR = C::AR, FR = C::FR;
+  constexpr int B = C::B, F = C::F, NE = C::NE, NEL = C::NEL, NT = C::NT, KS = C::KS, AR = C::AR, FR = C::FR;
   constexpr int NQ = C::NQ, NA = C::NA, NSPLIT = C::NSPLIT, SPR = C::SPR;
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
@@ -364,9 +368,9 @@ __global__ void __launch_bounds__(Cfg<O, M, FG>::NT, Cfg<O, M, FG>::PMIN) k_pred
   int* sMeta = reinterpret_cast<int*>(smem + C::P_META);
   const int tid = threadIdx.x;
 
-  for (int i = tid; i < 4 * B * BS; i += NT) {
-    const int c = i % 4, rc = i / 4, r = rc / BS, col = rc % BS;
-    sK[i] = (c < 3 && col < B) ? ops.K[(c * B + r) * B + col] : 0.f;
+  for (int i = tid; i < 3 * B * KS; i += NT) {
+    const int c = i / (B * KS), r = (i / KS) % B, col = i % KS;
+    sK[i] = (col < B) ? ops.K[(c * B + r) * B + col] : 0.f;
   }
   // F~_i[k][f] vanishes for deg k < deg f; staged as exact zeros (see the neighbour kernel)
   for (int i = tid; i < 4 * B * F; i += NT) {
@@ -479,15 +483,14 @@ __global__ void __launch_bounds__(Cfg<O, M, FG>::NT, Cfg<O, M, FG>::PMIN) k_pred
           k1 = act ? (split_owner ? km : kend) : 0;
         }
         const float* Ab = sA + ((buf * NE + es) * B) * AR;
-        const float* K0 = sK + ck_col * BS * 4;
+        const float* K0 = sK + ck_col * KS;
 #pragma unroll 4
         for (int k = k0; k < k1; ++k) {
           const float4 x0 = *reinterpret_cast<const float4*>(Ab + k * AR);
           const float4 x1 = *reinterpret_cast<const float4*>(Ab + k * AR + 4);
           const float x8 = Ab[k * AR + 8];
-          const float4 k4 = *reinterpret_cast<const float4*>(K0 + 4 * k);
           const float xs[9] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w, x8};
-          const float kc[3] = {k4.x, k4.y, k4.z};
+          const float kc[3] = {K0[k], K0[B * KS + k], K0[2 * B * KS + k]};
 #pragma unroll
           for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -595,9 +598,9 @@ __global__ void __launch_bounds__(Cfg<O, M, FG>::NT, Cfg<O, M, FG>::PMIN) k_pred
           const float4 x0 = *reinterpret_cast<const float4*>(Ab + k * AR);
           const float4 x1 = *reinterpret_cast<const float4*>(Ab + k * AR + 4);
           const float x8 = Ab[k * AR + 8];
-          const float4 k4 = *reinterpret_cast<const float4*>(sK + (k * BS + b) * 4);
+          const float* Kk = sK + k * KS + b;
           const float xs[9] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w, x8};
-          const float kc[3] = {k4.x, k4.y, k4.z};
+          const float kc[3] = {Kk[0], Kk[B * KS], Kk[2 * B * KS]};
 #pragma unroll
           for (int c = 0; c < 3; ++c)
 #pragma unroll
