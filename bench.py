@@ -326,7 +326,8 @@ def run_ours(args, rank, world, local_rank):
                    "elements": K, "fused": F, "updates_per_step": per_macro,
                    "launch": s.launch_config(),
                    "cluster_elems": info["cluster_elems"].tolist(), "theoretical_lts_speedup": speedup,
-                   "l2": "inputs larger than L2 (DOFs %.1f GB)" % (K * 945 * 4 * F / 1e9),
+                   "l2": "inputs larger than L2 (DOFs %.1f GB)"
+                         % (K * (9 + 6 * nmech) * perfmodel.nbasis(order) * 4 * F / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "kernel": name, "achieved": achieved_tf, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved_tf / fp32_peak, "traffic": traffic,
