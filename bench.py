@@ -314,6 +314,7 @@ def run_ours(args, rank, world, local_rank):
         metric = "simulation element-updates/s, order-5 anelastic LTS, %d fused sources, 1 GB300" % F
         unit = "sim-element-updates/s"
         srcs = "%d fused simulations, one random moment-tensor source each" % F
+    dof_bytes = K * (9 + 6 * nmech) * perfmodel.nbasis(order) * 4 * F
     line = {
         "metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -326,8 +327,8 @@ def run_ours(args, rank, world, local_rank):
                    "elements": K, "fused": F, "updates_per_step": per_macro,
                    "launch": s.launch_config(),
                    "cluster_elems": info["cluster_elems"].tolist(), "theoretical_lts_speedup": speedup,
-                   "l2": "inputs larger than L2 (DOFs %.1f GB)"
-                         % (K * (9 + 6 * nmech) * perfmodel.nbasis(order) * 4 * F / 1e9),
+                   "l2": ("inputs larger than L2 (DOFs %.1f GB)" if dof_bytes > 129e6 else
+                          "inputs within L2 (DOFs %.2f GB): a quick-check size, not a timing case") % (dof_bytes / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "kernel": name, "achieved": achieved_tf, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved_tf / fp32_peak, "traffic": traffic,
