@@ -206,3 +206,26 @@ def test_source_injection_matches_closed_form_time_integral():
     others = np.delete(np.arange(mesh.K), k)
     assert np.all(s.Q[others] == 0)
     assert abs(ricker(t0, f0, t0) - 1.0) < 1e-15
+
+
+@pytest.mark.parametrize("order", [3, 4, 5])
+def test_elastic_time_derivatives_lose_one_degree_each(order):
+    """Cauchy-Kowalevski (Sec. III-A): every time derivative of the elastic state is one
+    spatial derivative, so d^d Q has degree <= O-1-d and its modes beyond the first
+    nbasis(O-d) vanish (the truncation the elastic time kernel uses). The anelastic coupling
+    E theta carries the memory variables' full degree into every derivative."""
+    a, mesh = _cube_solver(3, order)
+    b, _ = _cube_solver(3, order, m=3, qs=40.0)
+    rng = np.random.default_rng(order)
+    B = order * (order + 1) * (order + 2) // 6
+    a.Q = rng.standard_normal((mesh.K, 9, B))
+    b.Q = rng.standard_normal((mesh.K, 27, B))
+    idx = np.arange(mesh.K)
+    Da, Db = a.derivatives(idx), b.derivatives(idx)
+    for d in range(1, order):
+        keep = (order - d) * (order - d + 1) * (order - d + 2) // 6
+        scale = np.abs(Da[d]).max()
+        assert scale > 0
+        assert np.abs(Da[d][:, :, keep:]).max() <= 1e-12 * scale, d
+        # anelastic: far above rounding (the coupling is weaker than the stiffness terms)
+        assert np.abs(Db[d][:, :9, keep:]).max() > 1e-8 * np.abs(Db[d][:, :9]).max(), d
