@@ -47,6 +47,28 @@ def test_plane_wave_convergence(order):
     assert rate > order - 0.6, (errs, rate)
 
 
+@pytest.mark.parametrize("order", [3, 4, 5])
+def test_s_plane_wave_convergence(order):
+    """S plane wave (velocity along (1, -1, 0), k = 2 pi (1, 1, 1)) on the periodic cube:
+    the L2 error of the velocities and of the stresses drops at rate ~O (3x3x3 -> 6x6x6)."""
+    sw = synth.s_plane_wave(RHO, VS, KVEC, [1.0, -1.0, 0.0])
+    tend = 0.25 / (VS * np.linalg.norm(KVEC) / (2 * np.pi))
+    errs_v, errs_s = [], []
+    for n in (3, 6):
+        s, mesh = _cube_solver(n, order)
+        s.project(lambda x: sw(x, 0.0))
+        dt = s.time_step_gts(0.5)
+        nst = int(math.ceil(tend / dt))
+        s.run_gts(tend / nst, nst)
+        ex, _ = _cube_solver(n, order)
+        ex.project(lambda x: sw(x, tend))
+        errs_v.append(_rel_err(s.Q, ex.Q, slice(6, 9)))
+        errs_s.append(_rel_err(s.Q, ex.Q, slice(0, 6)))
+    for errs in (errs_v, errs_s):
+        rate = math.log2(errs[0] / errs[1])
+        assert rate > order - 0.6, (errs, rate)
+
+
 def test_lts_single_cluster_equals_gts_bitwise():
     pw = synth.p_plane_wave(RHO, VP, VS, KVEC)
     a, _ = _cube_solver(3, 3)
