@@ -367,7 +367,10 @@ int lts_checkpoint_load(lts_t* h, const char* path);
  * sum_k |det J_k| sum_b (rho |v_b|^2/2 + sigma_b : C^-1 sigma_b / 2), the quantity of
  * lts_energy. Runs asynchronously on cuda_stream (NULL = legacy default stream).
  * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture. Every call
+ * (cudaGetSymbolAddress); make that first call before any stream capture. The address is
+ * kept per device for the life of the process: after a cudaDeviceReset (or any other end of
+ * the device's primary context) the kept address is stale, so this entry point must not be
+ * called on that device again in the same process. Every call
  * shares the one scratch array, so calls that overlap on the GPU (on different streams)
  * race; the array is fully rewritten for the first n_elem entries by each call, so
  * nothing needs clearing. Errors: LTS_ERR_ARG for a bad order or mechanism count, a NULL

@@ -3,9 +3,10 @@
 `SeismogramMisfit.apply(rho, lam, mu, problem)` runs the problem's forward simulation on
 the GPU with per-element density and Lame parameters taken from the three tensors and
 returns the misfit J (a 0-d tensor); `backward` hands out dJ/d(rho, lambda, mu) from the
-library's discrete adjoint of the global-time-stepping loop (checkpointed recomputation,
-exact derivatives of the star matrices and flux solvers). The time step is the problem's
-and stays fixed when the material changes.
+library's discrete adjoint of the time loop (checkpointed recomputation, exact derivatives
+of the star matrices and flux solvers): global time stepping, or the clustered LTS loop
+when the problem carries a cluster assignment. The time step (the finest one under LTS) and
+the clusters are the problem's and stay fixed when the material changes.
 """
 import numpy as np
 import torch
@@ -15,17 +16,29 @@ from . import binding
 
 class MisfitProblem:
     """Everything but the material: mesh, order, initial DOFs, sources, receivers,
-    observed data (N+1, n_rec, 3), step count, fixed time step and checkpoint spacing.
-    n_fused = F > 1: F simulations in one run, source f in simulation f, initial DOFs
-    (F, K, 9, B), data (N+1, F, n_rec, 3); the misfit is summed over the simulations."""
+    observed data, step count, fixed time step and checkpoint spacing.
 
-    def __init__(self, order, mesh, q0, receivers, data, n_steps, dt, sources=(), every=100, device=0, n_fused=1):
+    Global time stepping (clusters=None): data (N+1, n_rec, 3), one row per step, n_steps
+    steps of dt. Clustered LTS (clusters = per-element cluster index 0..n_clusters-1, a
+    normalised assignment, with its lambda): dt is the finest time step, n_steps counts finest
+    steps (a multiple of the macro step 2^(n_clusters-1)), data holds one row per macro-step
+    boundary (n_steps / 2^(n_clusters-1) + 1 rows) and `every` counts macro steps.
+    n_fused = F > 1: F simulations in one run, source f in simulation f, initial DOFs
+    (F, K, 9, B), data (rows, F, n_rec, 3); the misfit is summed over the simulations."""
+
+    def __init__(self, order, mesh, q0, receivers, data, n_steps, dt, sources=(), every=100, device=0, n_fused=1,
+                 clusters=None, n_clusters=None, lam=1.0):
         self.order, self.mesh, self.q0 = order, mesh, np.asarray(q0, dtype=np.float64)
         self.receivers, self.data = list(receivers), np.asarray(data, dtype=np.float64)
         self.n_steps, self.dt, self.sources, self.every, self.device = n_steps, dt, list(sources), every, device
         self.n_fused = n_fused
         if n_fused > 1 and len(self.sources) != n_fused:
             raise ValueError("a fused problem takes one source per simulation")
+        self.clusters = None if clusters is None else np.ascontiguousarray(clusters, dtype=np.int32)
+        self.n_clusters = 1 if clusters is None else int(n_clusters if n_clusters is not None else self.clusters.max() + 1)
+        self.lam = float(lam)
+        if n_steps % (2 ** (self.n_clusters - 1)):
+            raise ValueError("n_steps must be a whole number of macro steps")
 
     def solver(self, rho, lam, mu):
         s = binding.Solver(self.order, 0, device=self.device, n_fused=self.n_fused)
@@ -38,7 +51,10 @@ class MisfitProblem:
             s.add_point_source(*src, fused_idx=f if self.n_fused > 1 else 0)
         for x in self.receivers:
             s.add_receiver(x, self.dt)
-        s.setup_clusters(1, 0.5)
+        if self.clusters is None:
+            s.setup_clusters(1, 0.5)
+        else:
+            s.force_clusters(self.clusters, self.n_clusters, 0.5, self.lam)
         s.set_finest_dt(self.dt)
         s.set_dofs(self.q0)
         return s
