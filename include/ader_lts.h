@@ -193,16 +193,19 @@ int lts_kernel_stats(lts_t* h, double* ms_out2, int64_t* launches_out2, int64_t*
 int lts_transfer_bytes(lts_t* h, int64_t* h2d, int64_t* d2h);
 
 /* Contraction engine of the time and volume kernels (Sec. IV: the products of the DOFs
- * with the stiffness matrices K_c). LTS_CONTRACT_FP32: FP32 CUDA cores (default).
+ * with the stiffness matrices K_c). LTS_CONTRACT_FP32: FP32 CUDA cores, dense degree
+ * blocks (the paper's block sparsity; default).
  * LTS_CONTRACT_TF32X3: 5th-generation tensor cores, every operand split into two tf32
  * parts and the three leading products accumulated in FP32 (FP32-level accuracy).
  * LTS_CONTRACT_TF32: tensor cores on the rounded tf32 parts only (about 1e-3 relative
- * error per product). The surface kernels always run on CUDA cores. Takes effect at the
- * next lts_advance. Errors: LTS_ERR_ARG for an unknown mode or a tensor-core mode the
- * handle's shape has no kernel for (order 3 with one simulation). A tensor-core wait that
- * gives up (bounded, about one second) makes the next synchronising call return
- * LTS_ERR_TIMEOUT. */
-enum { LTS_CONTRACT_FP32 = 0, LTS_CONTRACT_TF32X3 = 1, LTS_CONTRACT_TF32 = 2 };
+ * error per product). LTS_CONTRACT_SPARSE: FP32 CUDA cores with the products of K_c and of
+ * the local face matrices F~_i generated at build time from the nonzero entries only (Sec.
+ * IV-A "all sparsity"; one simulation only). The other surface products always run on CUDA
+ * cores. Takes effect at the next lts_advance. Errors: LTS_ERR_ARG for an unknown mode or a
+ * mode the handle's shape has no kernel for (tensor cores: order 3 with one simulation;
+ * sparse: fused simulations). A tensor-core wait that gives up (bounded, about one second)
+ * makes the next synchronising call return LTS_ERR_TIMEOUT. */
+enum { LTS_CONTRACT_FP32 = 0, LTS_CONTRACT_TF32X3 = 1, LTS_CONTRACT_TF32 = 2, LTS_CONTRACT_SPARSE = 3 };
 int lts_set_contraction(lts_t* h, int mode);
 
 /* Weighted partitioning for distributed runs (Sec. V-C). Element weight 2^(N_c-1-l) (its

@@ -326,7 +326,7 @@ class Solver:
         n = ctypes.c_int()
         self._check(lib().lts_autotune(self._h, 1 if allow_tf32 else 0, _stream_handle(stream), _ptr(chosen),
                                        ctypes.byref(best), _ptr(table), 32, ctypes.byref(n)))
-        names = {0: "fp32", 1: "tf32x3", 2: "tf32"}
+        names = {0: "fp32", 1: "tf32x3", 2: "tf32", 3: "sparse"}
         rows = [dict(contraction=names[int(r[0])], ctas_predict=int(r[1]), ctas_neighbour=int(r[2]), ms=float(r[3]))
                 for r in table[:min(n.value, 32)]]
         return dict(contraction=names[int(chosen[0])], ctas_predict=int(chosen[1]), ctas_neighbour=int(chosen[2]),
@@ -421,8 +421,9 @@ class Solver:
         self._check(lib().lts_set_wait_limit(self._h, int(cycles), 1 if suppress_commit else 0))
 
     def set_contraction(self, mode):
-        """'fp32' (CUDA cores), 'tf32x3' (tensor cores, split tf32) or 'tf32' (tensor cores)."""
-        code = {"fp32": 0, "tf32x3": 1, "tf32": 2}[mode]
+        """'fp32' (CUDA cores), 'sparse' (CUDA cores, generated sparse products), 'tf32x3'
+        (tensor cores, split tf32) or 'tf32' (tensor cores)."""
+        code = {"fp32": 0, "tf32x3": 1, "tf32": 2, "sparse": 3}[mode]
         self._check(lib().lts_set_contraction(self._h, code))
 
     def set_profiling(self, on=True):

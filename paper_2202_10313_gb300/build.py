@@ -1,7 +1,9 @@
 """Builds the solver's shared library in-tree: paper_2202_10313_gb300/libaderlts.so.
 
 Host set-up (C++17, g++) and CUDA kernels (nvcc, sm_103a only) are compiled as separate
-translation units in parallel and linked with nvcc. Usage: ``python -m
+translation units in parallel and linked with nvcc. Before them, a small host program
+(gen_sparse.cpp, built with the library's host basis code) writes the sparse operator
+products of the predict kernel into _build/sparse_ops.cuh. Usage: ``python -m
 paper_2202_10313_gb300.build`` or ``build()``.
 """
 import concurrent.futures
@@ -37,10 +39,25 @@ def _stale(obj, srcs):
     return any(os.path.getmtime(s) > t for s in srcs)
 
 
+def _generate_sparse_ops():
+    """Builds and runs the generator of the sparse operator products (gen_sparse.cpp with the
+    library's own host basis code) -> _build/sparse_ops.cuh, when its inputs changed."""
+    gen_src = [os.path.join(SRC, f) for f in ("gen_sparse.cpp", "host_basis.cpp", "host.h")]
+    exe = os.path.join(OUT_DIR, "gen_sparse")
+    out = os.path.join(OUT_DIR, "sparse_ops.cuh")
+    if _stale(exe, gen_src):
+        _run(["g++", "-std=c++17", "-O2", "-Wall", gen_src[0], gen_src[1], "-o", exe])
+    if _stale(out, [exe]):
+        _run([exe, out + ".tmp"])
+        os.replace(out + ".tmp", out)
+    return out
+
+
 def build(verbose=False, ptxas_info=False):
     os.makedirs(OUT_DIR, exist_ok=True)
     headers = [os.path.join(SRC, f) for f in os.listdir(SRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(HERE, "..", "include", "ader_lts.h"))
+    headers.append(_generate_sparse_ops())
     jobs = []
     objs = []
     for f in HOST_SOURCES:
@@ -54,7 +71,7 @@ def build(verbose=False, ptxas_info=False):
         obj = os.path.join(OUT_DIR, f + ".o")
         objs.append(obj)
         if _stale(obj, [src] + headers):
-            cmd = [_nvcc(), "-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC",
+            cmd = [_nvcc(), "-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", OUT_DIR,
                    "-c", src, "-o", obj] + ARCH
             if ptxas_info:
                 cmd.insert(1, "-Xptxas=-v")

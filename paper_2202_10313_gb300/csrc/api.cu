@@ -632,9 +632,10 @@ PhaseArgs phase_args(const lts_solver* h, const Phase& ph) {
 // with_receivers is false (state-only replays).
 int enqueue_phase(lts_solver* h, const Phase& ph, cudaStream_t stream, bool with_receivers = true) {
   const Launchers& X = h->L;
-  const bool use_tc = h->contraction != LTS_CONTRACT_FP32;
+  const bool use_sp = h->contraction == LTS_CONTRACT_SPARSE;
+  const bool use_tc = h->contraction == LTS_CONTRACT_TF32X3 || h->contraction == LTS_CONTRACT_TF32;
   const int passes = h->contraction == LTS_CONTRACT_TF32X3 ? 3 : 1;
-  const int maxp = std::max(1, use_tc ? X.blocks_predict_tc : X.blocks_predict);
+  const int maxp = std::max(1, use_tc ? X.blocks_predict_tc : (use_sp ? X.blocks_predict_sp : X.blocks_predict));
   const int maxn = std::max(1, X.blocks_neighbour);
   const int grid_cap_p = h->num_sms * (h->ctas_predict > 0 ? std::min(h->ctas_predict, maxp) : maxp);
   const int grid_cap_n = h->num_sms * (h->ctas_neighbour > 0 ? std::min(h->ctas_neighbour, maxn) : maxn);
@@ -656,8 +657,8 @@ int enqueue_phase(lts_solver* h, const Phase& ph, cudaStream_t stream, bool with
     nvtxRangePushA(name);
   }
   // CTA batches: NE elements (one simulation) or one element and FG of its simulations
-  const int nb = X.FG > 1 ? nelem * (h->nsim / X.FG)
-                          : (nelem + (ph.kind == 0 ? X.NEN : X.NE) - 1) / (ph.kind == 0 ? X.NEN : X.NE);
+  const int ne_batch = ph.kind == 0 ? X.NEN : (use_sp ? X.NE_SP : X.NE);
+  const int nb = X.FG > 1 ? nelem * (h->nsim / X.FG) : (nelem + ne_batch - 1) / ne_batch;
   if (with_receivers && ph.kind == 1 && ph.item_end > ph.item_beg) {
     X.receivers(h->dops, h->dst.Q, h->dst.qs, h->nsim, X.FG, h->dst.edata, h->d_recv_phi, h->d_ritems + ph.item_beg,
                 h->d_seis, pa.omega, ph.item_end - ph.item_beg, stream);
@@ -675,6 +676,8 @@ int enqueue_phase(lts_solver* h, const Phase& ph, cudaStream_t stream, bool with
   else if (use_tc)
     X.predict_tc(h->dops, h->dst, pa, std::min(nb, grid_cap_p), passes, h->d_err, h->wait_cycles, h->suppress_commit,
                  stream);
+  else if (use_sp)
+    X.predict_sp(h->dops, h->dst, pa, std::min(nb, grid_cap_p), stream);
   else
     X.predict(h->dops, h->dst, pa, std::min(nb, grid_cap_p), stream);
   ++launches;
@@ -1825,10 +1828,13 @@ int lts_autotune(lts_t* h, int allow_tf32, void* cuda_stream, int* chosen, doubl
     // one fewer)
     std::vector<std::array<int, 3>> cand;
     std::vector<int> engines{LTS_CONTRACT_FP32};
+    if (X.predict_sp) engines.push_back(LTS_CONTRACT_SPARSE);
     if (X.predict_tc) engines.push_back(LTS_CONTRACT_TF32X3);
     if (X.predict_tc && allow_tf32) engines.push_back(LTS_CONTRACT_TF32);
     for (int eng : engines) {
-      const int mp = std::max(1, eng == LTS_CONTRACT_FP32 ? X.blocks_predict : X.blocks_predict_tc);
+      const int mp = std::max(1, eng == LTS_CONTRACT_FP32     ? X.blocks_predict
+                                 : eng == LTS_CONTRACT_SPARSE ? X.blocks_predict_sp
+                                                              : X.blocks_predict_tc);
       const int mn = std::max(1, X.blocks_neighbour);
       for (int cp = mp; cp >= std::max(1, mp - 1); --cp)
         for (int cn = mn; cn >= std::max(1, mn - 1); --cn) cand.push_back({eng, cp, cn});
@@ -2068,9 +2074,12 @@ int lts_set_wait_limit(lts_t* h, int64_t cycles, int suppress_commit) {
 
 int lts_set_contraction(lts_t* h, int mode) {
   return run(h, [&] {
-    if (mode != LTS_CONTRACT_FP32 && mode != LTS_CONTRACT_TF32X3 && mode != LTS_CONTRACT_TF32)
+    if (mode != LTS_CONTRACT_FP32 && mode != LTS_CONTRACT_TF32X3 && mode != LTS_CONTRACT_TF32 &&
+        mode != LTS_CONTRACT_SPARSE)
       fail(LTS_ERR_ARG, "unknown contraction mode");
-    if (mode != LTS_CONTRACT_FP32 && !h->L.predict_tc) fail(LTS_ERR_ARG, "no tensor-core kernel for this shape");
+    if ((mode == LTS_CONTRACT_TF32X3 || mode == LTS_CONTRACT_TF32) && !h->L.predict_tc)
+      fail(LTS_ERR_ARG, "no tensor-core kernel for this shape");
+    if (mode == LTS_CONTRACT_SPARSE && !h->L.predict_sp) fail(LTS_ERR_ARG, "no sparse kernel for fused simulations");
     h->contraction = mode;
   });
 }

@@ -1013,8 +1013,9 @@ __global__ void k_receivers(DevOps ops, const float* Q, long long qs, int nsim, 
       if (lane == 0) sRed[s][r][warp] = v;
     }
   __syncthreads();
-  if ((int)threadIdx.x < 9 * it.n) {
-    const int s = threadIdx.x / 9, r = threadIdx.x % 9;
+  // 9 n values (up to 72) written by a block of 32 or 64 threads
+  for (int i = threadIdx.x; i < 9 * it.n; i += blockDim.x) {
+    const int s = i / 9, r = i % 9;
     float v = sRed[s][r][0];
     if (blockDim.x > 32) v += sRed[s][r][1];
     out[((size_t)(it.out_off + s) * nsim + it.sim) * 9 + r] = v;

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include "kernels.cuh"
+#include "kernels_sp.cuh"
 #include "kernels_tc.cuh"
 #include "kernels_adj.cuh"
 
@@ -22,6 +23,10 @@ struct Launchers {
                      long long wait_cycles, int suppress_commit, cudaStream_t);
   size_t smem_predict_tc;
   int blocks_predict_tc;
+  // predict + local kernel with generated sparse products (one simulation; else nullptr)
+  void (*predict_sp)(const DevOps&, const DevState&, const PhaseArgs&, int grid, cudaStream_t);
+  size_t smem_predict_sp;
+  int blocks_predict_sp, NE_SP, NT_SP;
   // fg: simulation group size of the layout (FG of the fused instantiation, 1 for one simulation)
   void (*receivers)(const DevOps&, const float* Q, long long qs, int nsim, int fg, const float* edata,
                     const float* phi, const RecvItem* items, float* out, const float* omega, int n, cudaStream_t);
@@ -72,6 +77,13 @@ struct Impl {
       // two fit the 512 tensor-memory columns)
       L->blocks_predict_tc = 2;
     }
+    if constexpr (FG == 1) {
+      e = smem_attrs(k_predict_sp<O, M>, L->smem_predict_sp, true);
+      if (e != cudaSuccess) return e;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L->blocks_predict_sp, k_predict_sp<O, M>, SpCfg<O, M>::NT,
+                                                        L->smem_predict_sp);
+      if (e != cudaSuccess) return e;
+    }
     if constexpr (M == 0) {
       e = cudaFuncSetAttribute(k_adj_pred<O>, cudaFuncAttributeMaxDynamicSharedMemorySize, AdjPredCfg<O>::SMEM_BYTES);
       if (e != cudaSuccess) return e;
@@ -84,6 +96,10 @@ struct Impl {
   }
   static void neighbour(const DevOps& o, const DevState& s, const PhaseArgs& p, int grid, cudaStream_t st) {
     k_neighbour<O, M, FG><<<grid, C::NTN, C::N_TOTAL * sizeof(float), st>>>(o, s, p);
+  }
+  static void predict_sp(const DevOps& o, const DevState& s, const PhaseArgs& p, int grid, cudaStream_t st) {
+    if constexpr (FG == 1)
+      k_predict_sp<O, M><<<grid, SpCfg<O, M>::NT, SpCfg<O, M>::TOTAL * sizeof(float), st>>>(o, s, p);
   }
   static void predict_tc(const DevOps& o, const DevState& s, const PhaseArgs& p, int grid, int passes, int* err,
                          long long wait_cycles, int suppress_commit, cudaStream_t st) {
@@ -151,6 +167,12 @@ struct Impl {
     if constexpr (TcCfg<O, M, FG>::SUPPORTED) {
       L.predict_tc = &predict_tc;
       L.smem_predict_tc = TcCfg<O, M, FG>::SMEM_BYTES;
+    }
+    if constexpr (FG == 1) {
+      L.predict_sp = &predict_sp;
+      L.smem_predict_sp = SpCfg<O, M>::TOTAL * sizeof(float);
+      L.NE_SP = SpCfg<O, M>::NE;
+      L.NT_SP = SpCfg<O, M>::NT;
     }
     L.neighbour = &neighbour;
     L.receivers = &receivers;

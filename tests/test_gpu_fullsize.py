@@ -70,9 +70,9 @@ def _ball(nbr, k, hops):
     return np.array(sorted(seen))
 
 
-@pytest.mark.parametrize("contraction", ["fp32", "tf32x3"])
+@pytest.mark.parametrize("contraction", ["fp32", "sparse", "tf32x3"])
 def test_bench_configuration_sampled_parity(contraction):
-    """Both engines the autotuner may pick for the bench run."""
+    """Every engine the autotuner may pick for the bench run."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")

@@ -132,6 +132,40 @@ def test_source_and_receivers_lts():
                 assert np.sum((vg[:, q] - ref) ** 2) / den <= 1e-8
 
 
+@pytest.mark.parametrize("order,engine", [(3, "fp32"), (4, "fp32"), (5, "fp32"), (5, "sparse")])
+def test_receivers_with_eight_samples_per_step(order, engine):
+    """Receivers in every cluster sampled at 0.52 finest steps: a coarsest-cluster step (4
+    finest steps) holds 7 or 8 samples, i.e. up to 72 values per receiver item, more than
+    the 32 or 64 threads of the receiver kernel's block. Every trace matches the oracle."""
+    m = synth.graded_box(5, 5, 3, 250.0, 125.0, seed=21)
+    mat = synth.random_layers(m, n_layers=3, seed=8)
+    gpu, ora, om = make_pair(order, 3, m, mat)
+    if engine != "fp32":
+        gpu.set_contraction(engine)
+    cl, _, _ = gpu.setup_clusters(3, 0.5)
+    ora.setup_clusters(3, 0.5)
+    assert np.array_equal(cl, ora.clusters) and len(np.unique(cl)) == 3
+    rng = np.random.default_rng(4)
+    recs = [om.centroid[int(rng.choice(np.nonzero(cl == l)[0]))] for l in range(3) for _ in range(2)]
+    dt_rec = gpu.info()["finest_dt"] * 0.52
+    rid_g = [gpu.add_receiver(r, dt_rec) for r in recs]
+    rid_o = [ora.add_receiver(r, dt_rec) for r in recs]
+    gpu.setup_clusters(3, 0.5)
+    ora.setup_clusters(3, 0.5)
+    _seed_same(gpu, ora, initial_field(ora.nq, [600.0, 700.0, -300.0], 400.0))
+    gpu.advance_steps(8)
+    ora.run_lts(8)
+    _check(gpu, ora)
+    for a, b in zip(rid_g, rid_o):
+        tg, vg = gpu.seismogram(a)
+        to, vo = ora.seismogram(b)
+        assert np.array_equal(tg, to) and len(tg) >= 15
+        for q in range(9):
+            den = np.sum(vo[:, q] ** 2)
+            assert den > 0
+            assert np.sum((vg[:, q] - vo[:, q]) ** 2) / den <= 1e-8, (a, q)
+
+
 def test_advance_to_time_and_torch_memory():
     import torch
     m = synth.graded_box(4, 4, 3, 200.0, 100.0, seed=5)
