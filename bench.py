@@ -125,7 +125,8 @@ def kernel_hash():
     """Hash of the forward kernels' source (the DRAM counters in profiles/traffic.json are valid
     only for the code they were taken on)."""
     h = hashlib.sha256()
-    h.update(open(os.path.join(ROOT, "paper_2202_10313_gb300", "csrc", "kernels.cuh"), "rb").read())
+    for f in ("kernels.cuh", "kernels_sp.cuh", "gen_sparse.cpp"):
+        h.update(open(os.path.join(ROOT, "paper_2202_10313_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -323,10 +324,19 @@ def run_ours(args, rank, world, local_rank):
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12     # TFLOP/s at the maximum SM clock
     # dominant kernel by device time
     kind = int(np.argmax(kst["ms"]))
-    name = ["k_predict_local", "k_neighbour"][kind]
+    engine = tuned["contraction"] if tuned else args.contraction
+    predict_name = "k_predict_sp" if engine == "sparse" else ("k_predict_tc" if engine.startswith("tf32")
+                                                               else "k_predict_local")
+    name = [predict_name, "k_neighbour_sp" if (engine == "sparse" and args.partition <= 1) else "k_neighbour"][kind]
     avg_ms = kst["ms"][kind] / max(kst["launches"][kind], 1)
     elems_per_launch = kst["elems"][kind] * F / max(kst["launches"][kind], 1)    # simulation elements
-    fl = perfmodel.flops_predict(order, nmech) if kind == 0 else perfmodel.flops_neighbour(order, nmech)
+    # flops the dominant kernel's formulation needs per element: the sparse engine multiplies
+    # only the operators' nonzero entries (its count is lower than the block count of the
+    # dense kernels, given beside it)
+    fl_block = perfmodel.flops_predict(order, nmech) if kind == 0 else perfmodel.flops_neighbour(order, nmech)
+    fl = fl_block
+    if engine == "sparse" and F == 1:
+        fl = perfmodel.flops_predict_sparse(order, nmech) if kind == 0 else perfmodel.flops_neighbour_sparse(order, nmech)
     by = (perfmodel.bytes_predict(order, nmech, n_fused=F) if kind == 0
           else perfmodel.bytes_neighbour(order, nmech, n_fused=F))
     achieved_tf = fl * elems_per_launch / (avg_ms / 1000.0) / 1e12
@@ -361,7 +371,7 @@ def run_ours(args, rank, world, local_rank):
                                "%s, 64 receivers; step = 1 macro step (%d finest steps)"
                                % (K, nclusters, lam, CFL, srcs, period),
                    "elements": K, "fused": F, "updates_per_step": per_macro,
-                   "launch": s.launch_config(),
+                   "launch": dict(s.launch_config(), engine=engine, tile=(tuned["tile"] if tuned else 0)),
                    "cluster_elems": info["cluster_elems"].tolist(), "theoretical_lts_speedup": speedup,
                    "l2": ("inputs larger than L2 (DOFs %.1f GB)" if dof_bytes > 129e6 else
                           "inputs within L2 (DOFs %.2f GB): a quick-check size, not a timing case") % (dof_bytes / 1e9),
@@ -370,6 +380,8 @@ def run_ours(args, rank, world, local_rank):
                      "frac": achieved_tf / fp32_peak, "traffic": traffic,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (derived)" % sm_max,
                      "flops_per_element": fl, "elements_per_launch": elems_per_launch, "avg_launch_ms": avg_ms,
+                     "flops_per_element_block": fl_block,
+                     "frac_block": fl_block * elems_per_launch / (avg_ms / 1000.0) / 1e12 / fp32_peak,
                      # roofline time of one launch, max(bytes / HBM, flops / FP32 peak), over its duration
                      "roofline_time_attained": max(by * elems_per_launch / (hbm_gbs * 1e9),
                                                    fl * elems_per_launch / (fp32_peak * 1e12)) / (avg_ms / 1000.0),
@@ -379,7 +391,7 @@ def run_ours(args, rank, world, local_rank):
         "hbm": {"kernel": name, "achieved": achieved_gbs, "peak": hbm_gbs, "unit": "GB/s",
                 "frac": achieved_gbs / hbm_gbs, "peak_source": peak_src, "bytes_per_element": by},
         "kernel_ms": {"k_predict_local": kst["ms"][0], "k_neighbour": kst["ms"][1],
-                      "launches": kst["launches"].tolist()},
+                      "launches": kst["launches"].tolist(), "predict_kernel": predict_name},
         "gpu_launches": int(launches),
         "e2e": {"value": total_updates / (e2e_ms / 1000.0), "unit": unit,
                 "h2d_bytes_per_step": (h2d1 - h2d0) / args.steps, "d2h_bytes_per_step": (d2h1 - d2h0) / args.steps},

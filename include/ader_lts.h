@@ -194,19 +194,28 @@ int lts_transfer_bytes(lts_t* h, int64_t* h2d, int64_t* d2h);
 
 /* Contraction engine of the time and volume kernels (Sec. IV: the products of the DOFs
  * with the stiffness matrices K_c). LTS_CONTRACT_FP32: FP32 CUDA cores, dense degree
- * blocks (the paper's block sparsity; default).
+ * blocks (the paper's block sparsity; default for fused simulations).
  * LTS_CONTRACT_TF32X3: 5th-generation tensor cores, every operand split into two tf32
  * parts and the three leading products accumulated in FP32 (FP32-level accuracy).
  * LTS_CONTRACT_TF32: tensor cores on the rounded tf32 parts only (about 1e-3 relative
- * error per product). LTS_CONTRACT_SPARSE: FP32 CUDA cores with the products of K_c and of
- * the local face matrices F~_i generated at build time from the nonzero entries only (Sec.
- * IV-A "all sparsity"; one simulation only). The other surface products always run on CUDA
- * cores. Takes effect at the next lts_advance. Errors: LTS_ERR_ARG for an unknown mode or a
+ * error per product). LTS_CONTRACT_SPARSE (default for one simulation): FP32 CUDA cores with
+ * the products of K_c, of the face matrices F~_i and of their transposes generated at build
+ * time from the nonzero entries only (Sec. IV-A "all sparsity"), in the predict kernel and
+ * in a neighbour kernel that forms X F-_{j,h} as (X F~_j) R_h (R_h the face-basis map of the
+ * orientation); one simulation only, and a partitioned run keeps the other engines'
+ * neighbour kernel. The tensor-core engines' surface products run on CUDA cores. Takes effect at the next lts_advance. Errors: LTS_ERR_ARG for an unknown mode or a
  * mode the handle's shape has no kernel for (tensor cores: order 3 with one simulation;
  * sparse: fused simulations). A tensor-core wait that gives up (bounded, about one second)
  * makes the next synchronising call return LTS_ERR_TIMEOUT. */
 enum { LTS_CONTRACT_FP32 = 0, LTS_CONTRACT_TF32X3 = 1, LTS_CONTRACT_TF32 = 2, LTS_CONTRACT_SPARSE = 3 };
 int lts_set_contraction(lts_t* h, int mode);
+
+/* Tile variant of the sparse engine's neighbour kernel (Sec. III-A neighbour surface
+ * kernel): 0 = 8 elements per CTA (two CTAs per SM), 1 = 4 elements per CTA (four CTAs per
+ * SM). The arithmetic per element is the same, so the results are bitwise identical; only
+ * the grouping of elements into CTAs changes. Set by lts_autotune; ignored by the other
+ * engines. Errors: LTS_ERR_ARG for another value. */
+int lts_set_tile(lts_t* h, int tile);
 
 /* Weighted partitioning for distributed runs (Sec. V-C). Element weight 2^(N_c-1-l) (its
  * updates per macro step, cluster l 0-based); face weight = messages per macro step over
@@ -326,17 +335,18 @@ int lts_set_graphs(lts_t* h, int enable);
  * for cycles <= 0. */
 int lts_set_wait_limit(lts_t* h, int64_t cycles, int suppress_commit);
 
-/* Autotuner over launch configurations: contraction engine (FP32 CUDA cores, split-tf32
- * tensor cores, and plain tf32 only if allow_tf32) x resident CTAs per SM the predict and
- * neighbour grids are sized for (the occupancy maximum and one fewer). Each candidate
- * advances one macro step from a device-side snapshot of the state, timed with CUDA
- * events on `cuda_stream` after one untimed warm-up step; the state (DOFs, LTS buffers,
- * time, receiver samples) is restored exactly after every trial, so the simulation is
- * unchanged. The fastest candidate becomes the handle's configuration. Outputs (each may
- * be NULL): chosen[3] = (engine, predict CTAs/SM, neighbour CTAs/SM), best_ms, and for
- * the first `cap` candidates table[cap][4] = (engine, CTAs/SM, CTAs/SM, ms); *n_out the
- * number of candidates. Needs device memory for one copy of the state (else
- * LTS_ERR_OOM); synchronises the stream. */
+/* Autotuner over launch configurations: contraction engine (FP32 CUDA cores, sparse
+ * products, split-tf32 tensor cores, and plain tf32 only if allow_tf32) x resident CTAs per
+ * SM the predict and neighbour grids are sized for (the occupancy maximum and one fewer) x
+ * tile variant (sparse engine: the neighbour kernel's 8 or 4 elements per CTA; other
+ * engines: 0). Each candidate advances one macro step from a device-side snapshot of the
+ * state, timed with CUDA events on `cuda_stream` after one untimed warm-up step; the state
+ * (DOFs, LTS buffers, time, receiver samples) is restored exactly after every trial, so the
+ * simulation is unchanged. The fastest candidate becomes the handle's configuration.
+ * Outputs (each may be NULL): chosen[4] = (engine, predict CTAs/SM, neighbour CTAs/SM,
+ * tile), best_ms, and for the first `cap` candidates table[cap][5] = (engine, CTAs/SM,
+ * CTAs/SM, tile, ms); *n_out the number of candidates. Needs device memory for one copy of
+ * the state (else LTS_ERR_OOM); synchronises the stream. */
 int lts_autotune(lts_t* h, int allow_tf32, void* cuda_stream, int* chosen, double* best_ms, double* table,
                  int cap, int* n_out);
 

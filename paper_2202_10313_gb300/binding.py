@@ -51,6 +51,7 @@ _SIGS = {
     "lts_kernel_stats": (_I, [_P, _P, _P, _P]),
     "lts_transfer_bytes": (_I, [_P, _P, _P]),
     "lts_set_contraction": (_I, [_P, _I]),
+    "lts_set_tile": (_I, [_P, _I]),
     "lts_launch_config": (_I, [_P, _P, _P]),
     "lts_autotune": (_I, [_P, _I, _P, _P, _P, _P, _I, _P]),
     "lts_set_wait_limit": (_I, [_P, _L, _I]),
@@ -320,17 +321,17 @@ class Solver:
     def autotune(self, allow_tf32=False, stream=None):
         """Time the candidate launch configurations on a snapshot of the state and keep the
         fastest; returns the choice and every candidate's milliseconds per macro step."""
-        chosen = np.zeros(3, dtype=np.int32)
+        chosen = np.zeros(4, dtype=np.int32)
         best = ctypes.c_double()
-        table = np.zeros((32, 4))
+        table = np.zeros((32, 5))
         n = ctypes.c_int()
         self._check(lib().lts_autotune(self._h, 1 if allow_tf32 else 0, _stream_handle(stream), _ptr(chosen),
                                        ctypes.byref(best), _ptr(table), 32, ctypes.byref(n)))
         names = {0: "fp32", 1: "tf32x3", 2: "tf32", 3: "sparse"}
-        rows = [dict(contraction=names[int(r[0])], ctas_predict=int(r[1]), ctas_neighbour=int(r[2]), ms=float(r[3]))
-                for r in table[:min(n.value, 32)]]
+        rows = [dict(contraction=names[int(r[0])], ctas_predict=int(r[1]), ctas_neighbour=int(r[2]), tile=int(r[3]),
+                     ms=float(r[4])) for r in table[:min(n.value, 32)]]
         return dict(contraction=names[int(chosen[0])], ctas_predict=int(chosen[1]), ctas_neighbour=int(chosen[2]),
-                    best_ms=best.value, candidates=rows)
+                    tile=int(chosen[3]), best_ms=best.value, candidates=rows)
 
     def partition(self, n_parts):
         """Weighted partition (part per element) and its statistics."""
@@ -425,6 +426,10 @@ class Solver:
         (tensor cores, split tf32) or 'tf32' (tensor cores)."""
         code = {"fp32": 0, "tf32x3": 1, "tf32": 2, "sparse": 3}[mode]
         self._check(lib().lts_set_contraction(self._h, code))
+
+    def set_tile(self, tile):
+        """Tile variant of the sparse engine's neighbour kernel: 0 (8 elements per CTA) or 1 (4)."""
+        self._check(lib().lts_set_tile(self._h, int(tile)))
 
     def set_profiling(self, on=True):
         self._check(lib().lts_set_profiling(self._h, 1 if on else 0))

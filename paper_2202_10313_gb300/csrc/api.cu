@@ -76,7 +76,7 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 struct GraphKey {
   const void *seis, *ritems, *sitems, *block;
-  int contraction, ctas_p, ctas_n, suppress, parts;
+  int contraction, ctas_p, ctas_n, suppress, parts, tile;
   long long wait;
   size_t n_r, n_s;
 };
@@ -92,6 +92,7 @@ struct lts_solver {
   int nsim = 1;                             // fused simulations
   int contraction = LTS_CONTRACT_FP32;
   int ctas_predict = 0, ctas_neighbour = 0;  // resident CTAs per SM the grids are sized for (0: occupancy)
+  int tile = 0;                              // tile variant of the sparse engine's neighbour kernel
   long long wait_cycles = ltsdev::TC_WAIT_CYCLES;   // bound of the tensor-core completion waits
   int suppress_commit = 0;                          // failure-path test: waits run out
   // emulated partitioned run (Sec. V-C): cut faces receive face-local messages
@@ -177,8 +178,67 @@ int run(lts_t* h, const std::function<void()>& fn) {
   }
 }
 
+// Face-basis maps of the three orientations h: the neighbour matrices factor as F-_{j,h} =
+// F~_j R_h, R_h[f'][f] = int psi_f(chi) psi_f'(chi'(chi, h)) (the trace on the neighbour's face
+// j, re-expanded in the local face parametrisation; an affine map of the triangle keeps
+// polynomial degree, so R_h is block diagonal by degree and orthogonal). Solved here from the
+// normal equations of F~_0 R_h = F-_{0,h} in FP64 and checked on every face j.
+void face_orientation_maps(const lts::RefOps& ops, std::vector<float>& out) {
+  const int B = ops.B, F = ops.F;
+  std::vector<double> A(F * F), rhs(F * F);
+  for (int h = 0; h < 3; ++h) {
+    for (int p = 0; p < F; ++p)
+      for (int q = 0; q < F; ++q) {
+        double a = 0.0, r = 0.0;
+        for (int k = 0; k < B; ++k) {
+          a += ops.Ft[0][k * F + p] * ops.Ft[0][k * F + q];
+          r += ops.Ft[0][k * F + p] * ops.Fb[h][k * F + q];
+        }
+        A[p * F + q] = a;
+        rhs[p * F + q] = r;
+      }
+    // Gauss-Jordan with partial pivoting on [A | rhs] (A is symmetric positive definite)
+    std::vector<double> M = A, R = rhs;
+    for (int c = 0; c < F; ++c) {
+      int piv = c;
+      for (int r = c + 1; r < F; ++r)
+        if (std::fabs(M[r * F + c]) > std::fabs(M[piv * F + c])) piv = r;
+      for (int q = 0; q < F; ++q) {
+        std::swap(M[c * F + q], M[piv * F + q]);
+        std::swap(R[c * F + q], R[piv * F + q]);
+      }
+      const double d = M[c * F + c];
+      if (std::fabs(d) < 1e-300) fail(LTS_ERR_ARG, "singular face trace matrix");
+      for (int q = 0; q < F; ++q) {
+        M[c * F + q] /= d;
+        R[c * F + q] /= d;
+      }
+      for (int r = 0; r < F; ++r) {
+        if (r == c) continue;
+        const double f = M[r * F + c];
+        if (f == 0.0) continue;
+        for (int q = 0; q < F; ++q) {
+          M[r * F + q] -= f * M[c * F + q];
+          R[r * F + q] -= f * R[c * F + q];
+        }
+      }
+    }
+    double scale = 0.0, err = 0.0;
+    for (int j = 0; j < 4; ++j)
+      for (int k = 0; k < B; ++k)
+        for (int q = 0; q < F; ++q) {
+          double v = 0.0;
+          for (int p = 0; p < F; ++p) v += ops.Ft[j][k * F + p] * R[p * F + q];
+          scale = std::max(scale, std::fabs(ops.Fb[j * 3 + h][k * F + q]));
+          err = std::max(err, std::fabs(v - ops.Fb[j * 3 + h][k * F + q]));
+        }
+    if (err > 1e-8 * scale) fail(LTS_ERR_ARG, "neighbour matrices do not factor through the face traces");
+    for (int i = 0; i < F * F; ++i) out[h * F * F + i] = (float)R[i];
+  }
+}
+
 struct Layout {
-  size_t Q, B1, B2, B3, edata, ndata, nbr, ncode, meta, emat, partial, err, K, Ft, Fh, Fb, rphi, sphi, cut, msg,
+  size_t Q, B1, B2, B3, edata, ndata, nbr, ncode, meta, emat, partial, err, K, Ft, Fh, Fb, Rh, rphi, sphi, cut, msg,
       total;
 };
 
@@ -215,6 +275,7 @@ Layout layout_of(const lts_solver* h, int64_t K) {
   L.Ft = take(sizeof(float) * 4 * X.B * X.F);
   L.Fh = take(sizeof(float) * 4 * X.F * X.B);
   L.Fb = take(sizeof(float) * 12 * X.B * X.F);
+  L.Rh = take(sizeof(float) * 3 * X.F * X.F);
   L.rphi = take(sizeof(float) * std::max<size_t>(1, h->receivers.size()) * X.B);
   L.sphi = take(sizeof(float) * std::max<size_t>(1, h->sources.size()) * X.B);
   // cut faces of a partitioned run
@@ -355,6 +416,8 @@ void setup_device(lts_solver* h) {
       }
   for (int jh = 0; jh < 12; ++jh)
     for (int i = 0; i < B * F; ++i) hFb[jh * B * F + i] = (float)h->ops.Fb[jh][i];
+  std::vector<float> hRh(3 * F * F);
+  face_orientation_maps(h->ops, hRh);
   std::vector<float> rphi(std::max<size_t>(1, h->receivers.size()) * B, 0.f);
   for (size_t r = 0; r < h->receivers.size(); ++r)
     for (int b = 0; b < B; ++b) rphi[r * B + b] = (float)h->receivers[r].phi[b];
@@ -419,6 +482,7 @@ void setup_device(lts_solver* h) {
   h->dops.Ft = reinterpret_cast<float*>(base + Lo.Ft);
   h->dops.Fh = reinterpret_cast<float*>(base + Lo.Fh);
   h->dops.Fb = reinterpret_cast<float*>(base + Lo.Fb);
+  h->dops.Rh = reinterpret_cast<float*>(base + Lo.Rh);
   h->d_recv_phi = reinterpret_cast<float*>(base + Lo.rphi);
   h->d_src_phi = reinterpret_cast<float*>(base + Lo.sphi);
   h->d_cut = reinterpret_cast<int*>(base + Lo.cut);
@@ -445,6 +509,7 @@ void setup_device(lts_solver* h) {
   up(h->dops.Ft, hFt.data(), sizeof(float) * hFt.size());
   up(h->dops.Fh, hFh.data(), sizeof(float) * hFh.size());
   up(h->dops.Fb, hFb.data(), sizeof(float) * hFb.size());
+  up(h->dops.Rh, hRh.data(), sizeof(float) * hRh.size());
   up(h->d_recv_phi, rphi.data(), sizeof(float) * rphi.size());
   up(h->d_src_phi, sphi.data(), sizeof(float) * sphi.size());
   if (!cut_host.empty()) up(h->d_cut, cut_host.data(), sizeof(int) * cut_host.size());
@@ -636,7 +701,11 @@ int enqueue_phase(lts_solver* h, const Phase& ph, cudaStream_t stream, bool with
   const bool use_tc = h->contraction == LTS_CONTRACT_TF32X3 || h->contraction == LTS_CONTRACT_TF32;
   const int passes = h->contraction == LTS_CONTRACT_TF32X3 ? 3 : 1;
   const int maxp = std::max(1, use_tc ? X.blocks_predict_tc : (use_sp ? X.blocks_predict_sp : X.blocks_predict));
-  const int maxn = std::max(1, X.blocks_neighbour);
+  // the sparse engine's neighbour kernel reads every neighbour from local buffers: partitioned
+  // runs (face-local messages) keep the gather-and-product neighbour kernel
+  const bool use_nsp = use_sp && X.neighbour_sp[0] && h->n_parts <= 1;
+  const int tv = h->tile & 1;
+  const int maxn = std::max(1, use_nsp ? X.blocks_neighbour_sp[tv] : X.blocks_neighbour);
   const int grid_cap_p = h->num_sms * (h->ctas_predict > 0 ? std::min(h->ctas_predict, maxp) : maxp);
   const int grid_cap_n = h->num_sms * (h->ctas_neighbour > 0 ? std::min(h->ctas_neighbour, maxn) : maxn);
   const PhaseArgs pa = phase_args(h, ph);
@@ -657,7 +726,7 @@ int enqueue_phase(lts_solver* h, const Phase& ph, cudaStream_t stream, bool with
     nvtxRangePushA(name);
   }
   // CTA batches: NE elements (one simulation) or one element and FG of its simulations
-  const int ne_batch = ph.kind == 0 ? X.NEN : (use_sp ? X.NE_SP : X.NE);
+  const int ne_batch = ph.kind == 0 ? (use_nsp ? X.NEN_SP[tv] : X.NEN) : (use_sp ? X.NE_SP : X.NE);
   const int nb = X.FG > 1 ? nelem * (h->nsim / X.FG) : (nelem + ne_batch - 1) / ne_batch;
   if (with_receivers && ph.kind == 1 && ph.item_end > ph.item_beg) {
     X.receivers(h->dops, h->dst.Q, h->dst.qs, h->nsim, X.FG, h->dst.edata, h->d_recv_phi, h->d_ritems + ph.item_beg,
@@ -671,7 +740,9 @@ int enqueue_phase(lts_solver* h, const Phase& ph, cudaStream_t stream, bool with
     ++launches;
   }
   if (h->profiling) ck(cudaEventRecord(next_event(h), stream), "event record");
-  if (ph.kind == 0)
+  if (ph.kind == 0 && use_nsp)
+    X.neighbour_sp[tv](h->dops, h->dst, pa, std::min(nb, grid_cap_n), stream);
+  else if (ph.kind == 0)
     X.neighbour(h->dops, h->dst, pa, std::min(nb, grid_cap_n), stream);
   else if (use_tc)
     X.predict_tc(h->dops, h->dst, pa, std::min(nb, grid_cap_p), passes, h->d_err, h->wait_cycles, h->suppress_commit,
@@ -758,6 +829,7 @@ void advance_steps(lts_solver* h, int64_t n_finest, cudaStream_t stream) {
     key.contraction = h->contraction;
     key.ctas_p = h->ctas_predict;
     key.ctas_n = h->ctas_neighbour;
+    key.tile = h->tile;
     key.wait = h->wait_cycles;
     key.suppress = h->suppress_commit;
     key.parts = h->n_parts;
@@ -1221,6 +1293,8 @@ int lts_create(int order, int n_mech, int n_fused, int device, lts_t** out) {
     h->nsim = n_fused;
     if (!ltsdev::get_launchers(order, n_mech, n_fused > 1, &h->L)) fail(LTS_ERR_ARG, "unsupported order / mechanisms");
     if (n_fused > 1 && n_fused % h->L.FG != 0) fail(LTS_ERR_ARG, "fused count not a multiple of the CTA group");
+    // one simulation: the sparse-product kernels by default (the fastest FP32 engine)
+    if (h->L.predict_sp) h->contraction = LTS_CONTRACT_SPARSE;
     if (device >= 0) {
       ck(cudaSetDevice(device), "cudaSetDevice");
       ck(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device), "device attribute");
@@ -1826,7 +1900,7 @@ int lts_autotune(lts_t* h, int allow_tf32, void* cuda_stream, int* chosen, doubl
     h->profiling = false;
     // candidates: engine x predict CTAs/SM x neighbour CTAs/SM (the occupancy maximum and
     // one fewer)
-    std::vector<std::array<int, 3>> cand;
+    std::vector<std::array<int, 4>> cand;
     std::vector<int> engines{LTS_CONTRACT_FP32};
     if (X.predict_sp) engines.push_back(LTS_CONTRACT_SPARSE);
     if (X.predict_tc) engines.push_back(LTS_CONTRACT_TF32X3);
@@ -1835,9 +1909,12 @@ int lts_autotune(lts_t* h, int allow_tf32, void* cuda_stream, int* chosen, doubl
       const int mp = std::max(1, eng == LTS_CONTRACT_FP32     ? X.blocks_predict
                                  : eng == LTS_CONTRACT_SPARSE ? X.blocks_predict_sp
                                                               : X.blocks_predict_tc);
-      const int mn = std::max(1, X.blocks_neighbour);
-      for (int cp = mp; cp >= std::max(1, mp - 1); --cp)
-        for (int cn = mn; cn >= std::max(1, mn - 1); --cn) cand.push_back({eng, cp, cn});
+      const bool nsp = eng == LTS_CONTRACT_SPARSE && X.neighbour_sp[0] && h->n_parts <= 1;
+      for (int tv = 0; tv < (nsp ? 2 : 1); ++tv) {
+        const int mn = std::max(1, nsp ? X.blocks_neighbour_sp[tv] : X.blocks_neighbour);
+        for (int cp = mp; cp >= std::max(1, mp - 1); --cp)
+          for (int cn = mn; cn >= std::max(1, mn - 1); --cn) cand.push_back({eng, cp, cn, tv});
+      }
     }
     cudaEvent_t ev[2];
     ck(cudaEventCreate(&ev[0]), "cudaEventCreate");
@@ -1859,6 +1936,7 @@ int lts_autotune(lts_t* h, int allow_tf32, void* cuda_stream, int* chosen, doubl
       h->contraction = c[0];
       h->ctas_predict = c[1];
       h->ctas_neighbour = c[2];
+      h->tile = c[3];
       ck(cudaEventRecord(ev[0], stream), "event record");
       advance_steps(h, period, stream);
       ck(cudaEventRecord(ev[1], stream), "event record");
@@ -1870,10 +1948,11 @@ int lts_autotune(lts_t* h, int allow_tf32, void* cuda_stream, int* chosen, doubl
       restore_host();
       if (i < 0) continue;
       if (i < cap) {
-        table[4 * i + 0] = c[0];
-        table[4 * i + 1] = c[1];
-        table[4 * i + 2] = c[2];
-        table[4 * i + 3] = ms;
+        table[5 * i + 0] = c[0];
+        table[5 * i + 1] = c[1];
+        table[5 * i + 2] = c[2];
+        table[5 * i + 3] = c[3];
+        table[5 * i + 4] = ms;
       }
       if (ms < best) {
         best = ms;
@@ -1885,8 +1964,9 @@ int lts_autotune(lts_t* h, int allow_tf32, void* cuda_stream, int* chosen, doubl
     h->contraction = cand[bi][0];
     h->ctas_predict = cand[bi][1];
     h->ctas_neighbour = cand[bi][2];
+    h->tile = cand[bi][3];
     if (chosen)
-      for (int i = 0; i < 3; ++i) chosen[i] = cand[bi][i];
+      for (int i = 0; i < 4; ++i) chosen[i] = cand[bi][i];
     if (best_ms) *best_ms = best;
     if (n_out) *n_out = (int)cand.size();
   });
@@ -2069,6 +2149,13 @@ int lts_set_wait_limit(lts_t* h, int64_t cycles, int suppress_commit) {
     if (cycles <= 0) fail(LTS_ERR_ARG, "wait limit must be positive");
     h->wait_cycles = cycles;
     h->suppress_commit = suppress_commit != 0;
+  });
+}
+
+int lts_set_tile(lts_t* h, int tile) {
+  return run(h, [&] {
+    if (tile != 0 && tile != 1) fail(LTS_ERR_ARG, "tile variant must be 0 or 1");
+    h->tile = tile;
   });
 }
 

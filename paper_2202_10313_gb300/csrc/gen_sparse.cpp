@@ -11,7 +11,9 @@
 // thread holds one row (one quantity of one element) of the operand in registers and
 // forms all products of that row; the products are split into NPART parts of nearly equal
 // multiply-add count, and a warp executes one part, so every thread of a warp runs the same
-// straight-line code (no divergence) and no operator entry is read from memory.
+// straight-line code (no divergence) and no operator entry is read from memory. A part is a
+// contiguous run of the outputs ordered by mode, so its outputs share most of their inputs
+// and a thread loads only the inputs its part uses.
 //
 // Emitted, per order O and part count P (O = 3, 4, 5 with P = 1, 2, 4):
 //   sp_time_o{O}(part, variant, x, y): Y_c[b] = sum_k x[k] K_c[b][k]        (time kernel,
@@ -20,12 +22,21 @@
 //       kernel's degree truncation at derivative v; v = 0 is the full product).
 //   sp_vol_o{O}(part, x, y, g): Z_c[b] = sum_k x[k] K_c[k][b] (volume kernel) and
 //       G_i[f] = sum_k x[k] F~_i[k][f] (local face traces), from the same row.
-// x[k * XP] is the thread's row, y[(c B + b) XP], g[(i F + f) XP] the outputs (XP the pair
-// stride of the staging arrays, a template parameter so that every address is an
-// immediate offset). Every output the kernel reads is written (identically zero ones as
-// 0); Z_c[0], which vanishes for every c, is not.
+//   sp_proj_o{O}(part, x, y): P_i[b] = sum_f x[i F + f] F^_i[f][b] (projection of one row of
+//       the four faces' interface states, F^_i = F~_i^T in the orthonormal face basis).
+//   sp_ntrace_o{O}(j, x, y): G_j[f] = sum_k x[k] F~_j[k][f] of one row of a neighbour's
+//       buffer on the face j that each thread asks for (neighbour kernel).
+// x[k * XP] is the thread's row, y[(c B + b) XP] (or y[(i B + b) XP]) and g[(i F + f) XP]
+// the outputs (XP the pair stride of the staging arrays, a template parameter so that
+// every address is an immediate offset). Every output the kernel reads is written
+// (identically zero ones as 0); Z_c[0], which vanishes for every c, is not.
 //
-// Usage: gen_sparse <out.cuh>
+// Usage: gen_sparse <out.cuh>      writes the header
+//        gen_sparse --list <order> lists every product term, one line each:
+//        "<kind> <part> <output> <input> <value>", kind t (time kernel, output c B + b, full
+//        variant), v (volume, output c B + b), g (face trace, output i F + f), p (face
+//        projection, output i B + b, input i F + f) or n (neighbour face trace, output j F + f);
+//        for checks against other operators.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -40,8 +51,131 @@
 namespace {
 
 struct Out {
-  std::string dst;                       // store expression (relative to y or g)
-  std::vector<std::pair<int, float>> t;  // (k, value), ascending k
+  char kind;                             // t, v, g, p, n
+  int id;                                // output index within its kind
+  std::string dst;                       // store expression
+  std::vector<std::pair<int, float>> t;  // (input index, value), ascending input
+};
+
+using Parts = std::vector<std::vector<int>>;
+
+// Parts of nearly equal multiply-add count (a store counts as one), each a contiguous run
+// of the outputs in the given order.
+Parts partition(const std::vector<Out>& outs, int nparts, const std::vector<int>& order) {
+  size_t total = 0;
+  for (int o : order) total += outs[o].t.size() + 1;
+  Parts parts(nparts);
+  size_t acc = 0;
+  int p = 0;
+  for (int o : order) {
+    const size_t w = outs[o].t.size() + 1;
+    // move on when this output would take the part further past its share than short of it
+    if (p + 1 < nparts && acc + w / 2 > (size_t)(p + 1) * total / nparts) ++p;
+    parts[p].push_back(o);
+    acc += w;
+  }
+  return parts;
+}
+
+int nb(int o) { return o * (o + 1) * (o + 2) / 6; }
+
+// All products of one order: time-kernel variants, volume + face traces, face projection.
+struct Products {
+  int O = 0, B = 0, F = 0, nparts = 1;
+  std::vector<std::vector<Out>> time;    // per variant
+  std::vector<Parts> time_parts;
+  std::vector<Out> vol;                  // Z_c (b >= 1) then G_i
+  Parts vol_parts;
+  std::vector<Out> proj;
+  Parts proj_parts;
+  std::vector<std::vector<Out>> ntrace;  // per face j: the F outputs G_j[f]
+  size_t time_terms = 0, vol_terms = 0, face_terms = 0;
+
+  void build(int order, int np) {
+    O = order;
+    nparts = np;
+    lts::RefOps ops;
+    ops.build(O);
+    B = ops.B;
+    F = ops.F;
+    double kmax = 0.0, fmax = 0.0;
+    for (int c = 0; c < 3; ++c)
+      for (double v : ops.K[c]) kmax = std::max(kmax, std::fabs(v));
+    for (int i = 0; i < 4; ++i)
+      for (double v : ops.Ft[i]) fmax = std::max(fmax, std::fabs(v));
+    auto nzk = [&](double v) { return std::fabs(v) > 1e-7 * kmax; };
+    auto nzf = [&](double v) { return std::fabs(v) > 1e-7 * fmax; };
+    auto dst = [](const char* arr, int idx) {
+      char d[64];
+      std::snprintf(d, sizeof d, "%s[%d * XP]", arr, idx);
+      return std::string(d);
+    };
+    // time kernel variants; outputs (c, b) ordered by mode b, then c
+    for (int v = 0; v <= O - 2; ++v) {
+      const int kend = nb(O - v), bend = nb(O - 1 - v);
+      std::vector<Out> outs;
+      std::vector<int> ord;
+      for (int b = 0; b < bend; ++b)
+        for (int c = 0; c < 3; ++c) {
+          Out u{'t', c * B + b, dst("y", c * B + b), {}};
+          for (int k = 0; k < kend; ++k)
+            if (nzk(ops.K[c][b * B + k])) u.t.push_back({k, (float)ops.K[c][b * B + k]});
+          if (v == 0) time_terms += u.t.size();
+          ord.push_back((int)outs.size());
+          outs.push_back(u);
+        }
+      time_parts.push_back(partition(outs, nparts, ord));
+      time.push_back(outs);
+    }
+    // volume (by mode b, then c) and face traces (by face mode f, then face i)
+    std::vector<int> ord;
+    for (int b = 0; b < B; ++b)
+      for (int c = 0; c < 3; ++c) {
+        Out u{'v', c * B + b, dst("y", c * B + b), {}};
+        for (int k = 0; k < B; ++k)
+          if (nzk(ops.K[c][k * B + b])) u.t.push_back({k, (float)ops.K[c][k * B + b]});
+        vol_terms += u.t.size();
+        if (b == 0) {   // the constant mode has no derivative: Z_c[0] = 0, not read
+          if (!u.t.empty()) throw std::runtime_error("K_c[k][0] must vanish");
+          continue;
+        }
+        ord.push_back((int)vol.size());
+        vol.push_back(u);
+      }
+    for (int m = 0; m < F; ++m)
+      for (int i = 0; i < 4; ++i) {
+        Out u{'g', i * F + m, dst("g", i * F + m), {}};
+        for (int k = 0; k < B; ++k)
+          if (nzf(ops.Ft[i][k * F + m])) u.t.push_back({k, (float)ops.Ft[i][k * F + m]});
+        face_terms += u.t.size();
+        ord.push_back((int)vol.size());
+        vol.push_back(u);
+      }
+    vol_parts = partition(vol, nparts, ord);
+    // face projection, outputs (i, b) by face, then mode: F^_i[f][b] = F~_i[b][f]
+    ord.clear();
+    for (int i = 0; i < 4; ++i)
+      for (int b = 0; b < B; ++b) {
+        Out u{'p', i * B + b, dst("y", i * B + b), {}};
+        for (int m = 0; m < F; ++m)
+          if (nzf(ops.Ft[i][b * F + m])) u.t.push_back({i * F + m, (float)ops.Ft[i][b * F + m]});
+        ord.push_back((int)proj.size());
+        proj.push_back(u);
+      }
+    proj_parts = partition(proj, nparts, ord);
+    // face traces of a neighbour's buffer on its face j (one face per thread, chosen at run
+    // time): G_j[f] = sum_k x[k] F~_j[k][f]
+    for (int j = 0; j < 4; ++j) {
+      std::vector<Out> outs;
+      for (int m = 0; m < F; ++m) {
+        Out u{'n', j * F + m, dst("y", m), {}};
+        for (int k = 0; k < B; ++k)
+          if (nzf(ops.Ft[j][k * F + m])) u.t.push_back({k, (float)ops.Ft[j][k * F + m]});
+        outs.push_back(u);
+      }
+      ntrace.push_back(outs);
+    }
+  }
 };
 
 std::string flt(float v) {
@@ -50,26 +184,8 @@ std::string flt(float v) {
   return std::string(b) + "f";
 }
 
-// Greedy balance: outputs in descending term count, each to the part with the fewest terms.
-std::vector<std::vector<int>> partition(const std::vector<Out>& outs, int nparts) {
-  std::vector<int> order(outs.size());
-  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return outs[a].t.size() > outs[b].t.size(); });
-  std::vector<std::vector<int>> parts(nparts);
-  std::vector<size_t> load(nparts, 0);
-  for (int o : order) {
-    int best = 0;
-    for (int p = 1; p < nparts; ++p)
-      if (load[p] < load[best]) best = p;
-    parts[best].push_back(o);
-    load[best] += outs[o].t.size();
-  }
-  for (auto& p : parts) std::sort(p.begin(), p.end());
-  return parts;
-}
-
-// Straight-line body of one part: loads of the needed row entries, then one fma chain per
-// output (terms in ascending k, the order of the dense kernels), then its store.
+// Straight-line body of one part: loads of the needed inputs, then one fma chain per
+// output (terms in ascending input index, the order of the dense kernels), then its store.
 void emit_part(FILE* f, const std::vector<Out>& outs, const std::vector<int>& part) {
   std::vector<int> need;
   for (int o : part)
@@ -91,8 +207,8 @@ void emit_part(FILE* f, const std::vector<Out>& outs, const std::vector<int>& pa
 }
 
 void emit_dispatch(FILE* f, const char* name, const char* args, const char* call_args,
-                   const std::vector<std::vector<std::vector<int>>>& parts_of_variant,
-                   const std::vector<std::vector<Out>>& outs_of_variant, bool has_variant) {
+                   const std::vector<Parts>& parts_of_variant, const std::vector<std::vector<Out>>& outs_of_variant,
+                   bool has_variant) {
   const int nv = (int)parts_of_variant.size();
   for (int v = 0; v < nv; ++v) {
     const auto& parts = parts_of_variant[v];
@@ -115,146 +231,88 @@ void emit_dispatch(FILE* f, const char* name, const char* args, const char* call
   std::fprintf(f, "}\n");
 }
 
-void emit_order(FILE* f, int O, int nparts) {
-  lts::RefOps ops;
-  ops.build(O);
-  const int B = ops.B, F = ops.F;
-  double kmax = 0.0, fmax = 0.0;
-  for (int c = 0; c < 3; ++c)
-    for (double v : ops.K[c]) kmax = std::max(kmax, std::fabs(v));
-  for (int i = 0; i < 4; ++i)
-    for (double v : ops.Ft[i]) fmax = std::max(fmax, std::fabs(v));
-  auto nzk = [&](double v) { return std::fabs(v) > 1e-7 * kmax; };
-  auto nzf = [&](double v) { return std::fabs(v) > 1e-7 * fmax; };
-  auto nb = [](int o) { return o * (o + 1) * (o + 2) / 6; };
-  std::fprintf(f, "// ---- order %d (B = %d, F = %d), %d parts\n", O, B, F, nparts);
-  // time kernel variants
-  std::vector<std::vector<Out>> tv;
-  std::vector<std::vector<std::vector<int>>> tp;
-  size_t terms0 = 0;
-  for (int v = 0; v <= O - 2; ++v) {
-    const int kend = nb(O - v), bend = nb(O - 1 - v);
-    std::vector<Out> outs;
-    for (int c = 0; c < 3; ++c)
-      for (int b = 0; b < bend; ++b) {
-        Out u;
-        char d[64];
-        std::snprintf(d, sizeof d, "y[%d * XP]", c * B + b);
-        u.dst = d;
-        for (int k = 0; k < kend; ++k) {
-          const double val = ops.K[c][b * B + k];
-          if (nzk(val)) u.t.push_back({k, (float)val});
-        }
-        outs.push_back(u);
-      }
-    if (v == 0)
-      for (auto& u : outs) terms0 += u.t.size();
-    tp.push_back(partition(outs, nparts));
-    tv.push_back(outs);
-  }
-  // volume + face traces
-  std::vector<Out> vo;
-  size_t vterms = 0, gterms = 0;
-  for (int c = 0; c < 3; ++c)
-    for (int b = 0; b < B; ++b) {
-      Out u;
-      char d[64];
-      std::snprintf(d, sizeof d, "y[%d * XP]", c * B + b);
-      u.dst = d;
-      for (int k = 0; k < B; ++k) {
-        const double val = ops.K[c][k * B + b];
-        if (nzk(val)) u.t.push_back({k, (float)val});
-      }
-      vterms += u.t.size();
-      if (b == 0) {   // the constant mode has no derivative: Z_c[0] = 0, not read
-        if (!u.t.empty()) throw std::runtime_error("K_c[k][0] must vanish");
+// sp_ntrace_o{O}(j, x, y): G_j[f] = sum_k x[k] F~_j[k][f] for the face j the thread asks for
+// (j < 0: none). A warp computes the faces that any of its lanes asks for (warp-uniform
+// branches; every lane of the warp must call it) and each lane stores its own face's F
+// outputs y[f * XP].
+void emit_ntrace(FILE* f, int O, const Products& P) {
+  std::fprintf(f, "template <int XP>\n__device__ __forceinline__ void sp_ntrace_o%d(int j, const float* __restrict__ x, "
+               "float* __restrict__ y) {\n", O);
+  std::vector<int> need;
+  for (auto& outs : P.ntrace)
+    for (auto& u : outs)
+      for (auto& t : u.t) need.push_back(t.first);
+  std::sort(need.begin(), need.end());
+  need.erase(std::unique(need.begin(), need.end()), need.end());
+  for (int k : need) std::fprintf(f, "  const float x%d = x[%d * XP];\n", k, k);
+  for (int j = 0; j < 4; ++j) {
+    std::fprintf(f, "  if (__any_sync(0xffffffffu, j == %d)) {\n", j);
+    const auto& outs = P.ntrace[j];
+    for (size_t m = 0; m < outs.size(); ++m) {
+      const Out& u = outs[m];
+      if (u.t.empty()) {
+        std::fprintf(f, "    const float a%zu = 0.f;\n", m);
         continue;
       }
-      vo.push_back(u);
+      std::fprintf(f, "    float a%zu = x%d * %s;\n", m, u.t[0].first, flt(u.t[0].second).c_str());
+      for (size_t i = 1; i < u.t.size(); ++i)
+        std::fprintf(f, "    a%zu = fmaf(x%d, %s, a%zu);\n", m, u.t[i].first, flt(u.t[i].second).c_str(), m);
     }
-  for (int i = 0; i < 4; ++i)
-    for (int m = 0; m < F; ++m) {
-      Out u;
-      char d[64];
-      std::snprintf(d, sizeof d, "g[%d * XP]", i * F + m);
-      u.dst = d;
-      for (int k = 0; k < B; ++k) {
-        const double val = ops.Ft[i][k * F + m];
-        if (nzf(val)) u.t.push_back({k, (float)val});
-      }
-      gterms += u.t.size();
-      vo.push_back(u);
-    }
-  std::fprintf(f, "// time-kernel product: %zu multiply-adds per row (full variant); volume %zu, face traces %zu\n",
-               terms0, vterms, gterms);
-  std::fprintf(f, "constexpr int kSpTimeTerms_o%d = %zu, kSpVolTerms_o%d = %zu, kSpFaceTerms_o%d = %zu;\n", O,
-               terms0, O, vterms, O, gterms);
-  char nm[64];
-  std::snprintf(nm, sizeof nm, "sp_time_o%d", O);
-  emit_dispatch(f, nm, "const float* __restrict__ x, float* __restrict__ y", "x, y", tp, tv, true);
-  std::vector<std::vector<std::vector<int>>> vp{partition(vo, nparts)};
-  std::vector<std::vector<Out>> vv{vo};
-  std::snprintf(nm, sizeof nm, "sp_vol_o%d", O);
-  emit_dispatch(f, nm, "const float* __restrict__ x, float* __restrict__ y, float* __restrict__ g", "x, y, g", vp, vv,
-                false);
+    std::fprintf(f, "    if (j == %d) {\n", j);
+    for (size_t m = 0; m < outs.size(); ++m) std::fprintf(f, "      %s = a%zu;\n", outs[m].dst.c_str(), m);
+    std::fprintf(f, "    }\n  }\n");
+  }
+  std::fprintf(f, "}\n");
 }
 
-}  // namespace
+void emit_order(FILE* f, int O, int nparts) {
+  Products P;
+  P.build(O, nparts);
+  std::fprintf(f, "// ---- order %d (B = %d, F = %d), %d parts\n", O, P.B, P.F, nparts);
+  std::fprintf(f, "// multiply-adds per row: time kernel %zu (full variant), volume %zu, face traces %zu\n",
+               P.time_terms, P.vol_terms, P.face_terms);
+  std::fprintf(f, "constexpr int kSpTimeTerms_o%d = %zu, kSpVolTerms_o%d = %zu, kSpFaceTerms_o%d = %zu;\n", O,
+               P.time_terms, O, P.vol_terms, O, P.face_terms);
+  char nm[64];
+  std::snprintf(nm, sizeof nm, "sp_time_o%d", O);
+  emit_dispatch(f, nm, "const float* __restrict__ x, float* __restrict__ y", "x, y", P.time_parts, P.time, true);
+  std::snprintf(nm, sizeof nm, "sp_vol_o%d", O);
+  emit_dispatch(f, nm, "const float* __restrict__ x, float* __restrict__ y, float* __restrict__ g", "x, y, g",
+                {P.vol_parts}, {P.vol}, false);
+  std::snprintf(nm, sizeof nm, "sp_proj_o%d", O);
+  emit_dispatch(f, nm, "const float* __restrict__ x, float* __restrict__ y", "x, y", {P.proj_parts}, {P.proj}, false);
+  emit_ntrace(f, O, P);
+}
 
-// gen_sparse --list O: one line per product term, "<kind> <part> <output> <k> <value>" with
-// kind t (time kernel, output c*B + b, full variant), v (volume, output c*B + b) or g (face
-// trace, output i*F + f), for checking the generated products against other operators.
-int list_terms(int O, int nparts) {
-  lts::RefOps ops;
-  ops.build(O);
-  const int B = ops.B, F = ops.F;
-  double kmax = 0.0, fmax = 0.0;
-  for (int c = 0; c < 3; ++c)
-    for (double v : ops.K[c]) kmax = std::max(kmax, std::fabs(v));
-  for (int i = 0; i < 4; ++i)
-    for (double v : ops.Ft[i]) fmax = std::max(fmax, std::fabs(v));
-  std::vector<Out> t, v;
-  std::vector<int> tid, vid;
-  for (int c = 0; c < 3; ++c)
-    for (int b = 0; b < B; ++b) {
-      Out u, w;
-      for (int k = 0; k < B; ++k) {
-        if (std::fabs(ops.K[c][b * B + k]) > 1e-7 * kmax) u.t.push_back({k, (float)ops.K[c][b * B + k]});
-        if (std::fabs(ops.K[c][k * B + b]) > 1e-7 * kmax) w.t.push_back({k, (float)ops.K[c][k * B + b]});
-      }
-      if (b < (O - 1) * O * (O + 1) / 6) {   // outputs of the full time variant: deg b <= O-2
-        t.push_back(u);
-        tid.push_back(c * B + b);
-      }
-      if (b > 0) {
-        v.push_back(w);
-        vid.push_back(c * B + b);
-      }
-    }
-  const size_t nv = v.size();
-  for (int i = 0; i < 4; ++i)
-    for (int m = 0; m < F; ++m) {
-      Out u;
-      for (int k = 0; k < B; ++k)
-        if (std::fabs(ops.Ft[i][k * F + m]) > 1e-7 * fmax) u.t.push_back({k, (float)ops.Ft[i][k * F + m]});
-      v.push_back(u);
-      vid.push_back(i * F + m);
-    }
-  const auto tp = partition(t, nparts), vp = partition(v, nparts);
-  for (int p = 0; p < nparts; ++p) {
-    for (int o : tp[p])
-      for (auto& x : t[o].t) std::printf("t %d %d %d %.9e\n", p, tid[o], x.first, (double)x.second);
-    for (int o : vp[p])
-      for (auto& x : v[o].t) std::printf("%c %d %d %d %.9e\n", (size_t)o < nv ? 'v' : 'g', p, vid[o], x.first, (double)x.second);
+int parts_of(int O) { return O == 5 ? 4 : (O == 4 ? 2 : 1); }
+
+int list_terms(int O) {
+  Products P;
+  P.build(O, parts_of(O));
+  auto list = [](const std::vector<Out>& outs, const Parts& parts) {
+    for (size_t p = 0; p < parts.size(); ++p)
+      for (int o : parts[p])
+        for (auto& x : outs[o].t)
+          std::printf("%c %zu %d %d %.9e\n", outs[o].kind, p, outs[o].id, x.first, (double)x.second);
+  };
+  list(P.time[0], P.time_parts[0]);
+  list(P.vol, P.vol_parts);
+  list(P.proj, P.proj_parts);
+  for (auto& outs : P.ntrace) {
+    std::vector<int> all(outs.size());
+    for (size_t i = 0; i < all.size(); ++i) all[i] = (int)i;
+    list(outs, Parts{all});
   }
   return 0;
 }
+
+}  // namespace
 
 int main(int argc, char** argv) {
   if (argc == 3 && std::strcmp(argv[1], "--list") == 0) {
     const int O = std::atoi(argv[2]);
     if (O < 3 || O > 5) return 2;
-    return list_terms(O, O == 5 ? 4 : (O == 4 ? 2 : 1));
+    return list_terms(O);
   }
   if (argc != 2) {
     std::fprintf(stderr, "usage: gen_sparse <out.cuh> | gen_sparse --list <order>\n");
@@ -267,9 +325,7 @@ int main(int argc, char** argv) {
   }
   std::fprintf(f, "// Generated at build time by gen_sparse.cpp from the reference operators: do not edit.\n");
   std::fprintf(f, "#pragma once\nnamespace ltssp {\n");
-  emit_order(f, 3, 1);
-  emit_order(f, 4, 2);
-  emit_order(f, 5, 4);
+  for (int O = 3; O <= 5; ++O) emit_order(f, O, parts_of(O));
   std::fprintf(f, "}  // namespace ltssp\n");
   return std::fclose(f) == 0 ? 0 : 1;
 }

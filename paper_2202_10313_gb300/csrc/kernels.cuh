@@ -106,6 +106,7 @@ struct DevOps {
   const float* Ft;   // [4][B][F]   F~_i
   const float* Fh;   // [4F][B]     F^ stacked: row i*F+f = F^_i[f][:]
   const float* Fb;   // [12][B][F]  F-_{j,h}, index j*3+h
+  const float* Rh;   // [3][F][F]   face-basis map of orientation h: F-_{j,h} = F~_j R_h
 };
 
 struct DevState {

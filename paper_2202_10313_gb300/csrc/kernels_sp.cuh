@@ -12,15 +12,17 @@
 //                 K_c[k][b] and G_i[r][f] = sum_k T[r][k] F~_i[k][f] for the volume and local
 //                 face kernels. No operator entry is read from memory and the structural zeros
 //                 of K_c and F~_i (Sec. IV-A "all sparsity") are not multiplied.
-//   column phase: thread = (element e, mode b) as in k_predict_local: it reads the 27
-//                 products of its column, applies the star matrices (physical form), the
+//   column phase: thread = (element e, mode b), modes fastest: it reads the 27 products of
+//                 its column, applies the star matrices (physical form), the
 //                 anelastic coupling and relaxation, adds the Taylor terms and writes the
 //                 next derivative's column back for the next row phase.
 // Shared-memory arrays are [mode or output][pair] with a pair stride XP = 1 mod 32, so the
 // row phase's loads and stores (consecutive pairs) and the column phase's accesses
 // (consecutive modes) fall on distinct banks.
-// The local surface kernel's Riemann states and F^ projection, the receivers, sources and
-// neighbour kernel are those of kernels.cuh.
+// The local surface kernel's interface states (closed-form Riemann solver of kernels.cuh) are
+// projected the same way (row phase with the generated F^_i products), and the column phase
+// forms the flux rows per face. Receivers, sources and the neighbour kernel are those of
+// kernels.cuh.
 #pragma once
 #include "kernels.cuh"
 #include "sparse_ops.cuh"
@@ -54,15 +56,16 @@ struct SpCfg {
   static constexpr int NT = RT * NPART;
   static_assert(NE * B <= NT, "column phase needs one thread per (element, mode)");
   static constexpr int XP = RT + 1;                    // pair stride (1 mod 32)
-  static constexpr int FR = C::FR;                     // floats per staged Riemann state
-  static constexpr int FLS = 4 * F * FR;               // staged Riemann states per element
-  static constexpr int S_X = 0;                        // [B][XP]        row operand
-  static constexpr int S_Y = rup(S_X + B * XP, 4);     // [3 B][XP]      products Y_c / Z_c
-  static constexpr int S_G = rup(S_Y + 3 * B * XP, 4); // [4 F][XP]      face traces G_i
-  static constexpr int S_FH = rup(S_G + 4 * F * XP, 4);// [4 F][B]       F^
-  static constexpr int S_FL = rup(S_FH + 4 * F * B, 4);
-  static constexpr int S_E = rup(S_FL + NE * FLS, 4);
-  static constexpr int S_META = rup(S_E + NE * ED, 4);
+  static constexpr int EDP = ED + 1;                   // staged element data stride (odd: elements
+                                                       // of one warp on distinct banks)
+  static constexpr int S_X = 0;                        // [B][XP]          row operand
+  static constexpr int S_Y = rup(S_X + B * XP, 4);     // [3 B][XP]        products Y_c / Z_c
+  static constexpr int S_G = rup(S_Y + 3 * B * XP, 4); // [4 F][XP]        face traces G_i
+  static constexpr int S_P = S_Y;                      // [4 B][XP]        projected states P_i
+  static_assert(S_P + 4 * B * XP <= S_G + 4 * F * XP, "P_i overlays Y and G");
+  static constexpr int S_W = rup(S_G + 4 * F * XP, 4); // [4 F][XP]        interface states, 6 rows
+  static constexpr int S_E = rup(S_W + 4 * F * XP, 4);
+  static constexpr int S_META = rup(S_E + NE * EDP, 4);
   static constexpr int TOTAL = rup(S_META + NE, 4);
 };
 
@@ -79,38 +82,43 @@ __device__ __forceinline__ void sp_vol(int part, const float* x, float* y, float
   if constexpr (O == 4) ltssp::sp_vol_o4<XP>(part, x, y, g);
   if constexpr (O == 3) ltssp::sp_vol_o3<XP>(part, x, y, g);
 }
+template <int O, int XP>
+__device__ __forceinline__ void sp_proj(int part, const float* x, float* y) {
+  if constexpr (O == 5) ltssp::sp_proj_o5<XP>(part, x, y);
+  if constexpr (O == 4) ltssp::sp_proj_o4<XP>(part, x, y);
+  if constexpr (O == 3) ltssp::sp_proj_o3<XP>(part, x, y);
+}
 
 template <int O, int M>
 __global__ void __launch_bounds__(SpCfg<O, M>::NT, 2) k_predict_sp(DevOps ops, DevState st, PhaseArgs ph) {
   using S = SpCfg<O, M>;
   using C = typename S::C;
-  constexpr int B = S::B, F = S::F, NE = S::NE, NT = S::NT, XP = S::XP, FR = S::FR, NQ = S::NQ, NA = S::NA;
+  constexpr int B = S::B, F = S::F, NE = S::NE, NT = S::NT, XP = S::XP, NQ = S::NQ, NA = S::NA, EDP = S::EDP;
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
   float* sX = smem + S::S_X;
   float* sY = smem + S::S_Y;
   float* sG = smem + S::S_G;
-  float* sFh = smem + S::S_FH;
-  float* sFl = smem + S::S_FL;
+  float* sP = smem + S::S_P;
+  float* sW = smem + S::S_W;
   float* sE = smem + S::S_E;
   int* sMeta = reinterpret_cast<int*>(smem + S::S_META);
   const int tid = threadIdx.x;
 
-  for (int i = tid; i < 4 * F * B; i += NT) sFh[i] = ops.Fh[i];
-
-  // column task (element, mode), modes of the highest degree first
-  int e = -1, b = 0, p = 0;
-  task_of<O, NE>(tid, e, b, p);
-  const bool act = e >= 0;
-  const int es = act ? e : 0;
-  const int fmax = nface(p + 1);                // face modes of degree <= deg b
-  // row task (part, pair)
-  const int part = tid / S::RT, pair = tid % S::RT;
-  const bool ract = pair < S::NPAIR;
+  // column task (element, mode), modes fastest: a warp spans at most two elements
+  const bool act = tid < NE * B;
+  const int es = act ? tid / B : 0;
+  const int b = act ? tid % B : 0;
+  // row task (part, pair): warp w takes part w mod NPART, so that the warps an SM
+  // sub-partition runs (w mod 4) all execute the same part's straight-line code and its
+  // instruction cache holds one part only
+  const int part = (tid >> 5) % S::NPART, pair = ((tid >> 5) / S::NPART) * 32 + (tid & 31);
+  const bool ract = pair < S::NPAIR;          // (element, quantity) rows of the 9 elastic rows
+  const bool pact = pair < 6 * NE;            // (element, interface-state) rows of the projection
   const int nelem = ph.end - ph.begin;
   const int nbatch = (nelem + NE - 1) / NE;
   constexpr long long qs = C::QS, bs = C::BUFS;
-  const int col = es * 9;                       // this column's pair offset
+  const int col = es * 9;                     // this column's pair offset
 
   for (int batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
     const int e0 = ph.begin + batch * NE;
@@ -134,8 +142,8 @@ __global__ void __launch_bounds__(SpCfg<O, M>::NT, 2) k_predict_sp(DevOps ops, D
       for (int r = 0; r < NA; ++r) Da[r] = 0.f;
     }
     for (int i = tid; i < NE * ED; i += NT) {
-      const int gg = e0 + i / ED;
-      sE[i] = (gg < ph.end) ? st.edata[(size_t)gg * ED + (i % ED)] : 0.f;
+      const int ee = i / ED, gg = e0 + ee;
+      sE[ee * EDP + i % ED] = (gg < ph.end) ? st.edata[(size_t)gg * ED + (i % ED)] : 0.f;
     }
     if (tid < NE) sMeta[tid] = (e0 + tid < ph.end) ? st.meta[e0 + tid] : 0;
     if (act) {
@@ -143,7 +151,7 @@ __global__ void __launch_bounds__(SpCfg<O, M>::NT, 2) k_predict_sp(DevOps ops, D
       for (int r = 0; r < 9; ++r) sX[b * XP + col + r] = v[r];
     }
     __syncthreads();
-    const float* ed = sE + es * ED;
+    const float* ed = sE + es * EDP;
     const int meta = act ? sMeta[es] : 0;
     const int cl = meta & 0xff;
 #pragma unroll
@@ -250,8 +258,8 @@ __global__ void __launch_bounds__(SpCfg<O, M>::NT, 2) k_predict_sp(DevOps ops, D
             acc[9 + 6 * l + r] = q[(9 + 6 * l + r) * B] + ph.omega[l] * (-eps[r] - T[9 + 6 * l + r]);
       }
     }
-    // ---- local surface kernel: interface states of the face traces G_i (one task per
-    // element, face and face mode, face modes fastest), staged for the F^ projection
+    // ---- local surface kernel: interface states (v*, t*) of the face traces G_i, one task
+    // per element, face and face mode (face modes fastest), as rows of the projection
 #pragma unroll 1
     for (int t = tid; t < NE * 4 * F; t += NT) {
       const int fe = t / (4 * F), fi = (t / F) % 4, f = t % F;
@@ -260,16 +268,28 @@ __global__ void __launch_bounds__(SpCfg<O, M>::NT, 2) k_predict_sp(DevOps ops, D
 #pragma unroll
       for (int r = 0; r < 9; ++r) gv[r] = gp[r];
       float w6[6];
-      riemann_state(gv, sE + fe * ED + 20 + 11 * fi, w6);
-      store_state(sFl + fe * S::FLS + (fi * F + f) * FR, w6);
+      riemann_state(gv, sE + fe * EDP + 20 + 11 * fi, w6);
+      float* wp = sW + (fi * F + f) * XP + fe * 6;
+#pragma unroll
+      for (int r = 0; r < 6; ++r) wp[r] = w6[r];
     }
+    __syncthreads();
+    // ---- projection P_i[r'][b] = sum_f W_i[r'][f] F^_i[f][b] (row phase, over Y and G)
+    if (pact) sp_proj<O, XP>(part, sW + pair, sP + pair);
     __syncthreads();
     if (valid) {
       constexpr int NS = (M > 0) ? 15 : 9;
       float Sv[NS];
 #pragma unroll
       for (int r = 0; r < NS; ++r) Sv[r] = 0.f;
-      project_faces<NS, F, B, FR>(sFl + es * S::FLS, sFh, ed + 20, 11, ed[9], ed[10], ed[11], fmax, b, Sv);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float* pp = sP + (i * B + b) * XP + es * 6;
+        float W[6];
+#pragma unroll
+        for (int r = 0; r < 6; ++r) W[r] = pp[r];
+        flux_rows_add<NS>(W, ed + 20 + 11 * i, ed[9], ed[10], ed[11], Sv);
+      }
       float* q = st.Q + qoff;
 #pragma unroll
       for (int r = 0; r < 9; ++r) q[r * B] = acc[r] + Sv[r];
@@ -285,6 +305,220 @@ __global__ void __launch_bounds__(SpCfg<O, M>::NT, 2) k_predict_sp(DevOps ops, D
       if (bn < nbatch) {
         const int en = ph.begin + bn * NE;
         prefetch_batch_q<NQ, B, 1, NT>(st.Q, qs, en, 0, min(NE, ph.end - en), tid);
+      }
+    }
+  }
+}
+
+
+// ------------------------------------------------------------------ neighbour kernel
+// k_neighbour_sp: the neighbour surface kernel (Sec. III-A, with the buffer chosen by the
+// clusters' time-stepping relation, Sec. V-B), one simulation, no partition. The neighbour
+// matrices factor as F-_{j,h} = F~_j R_h (trace on the neighbour's face j, then the face-basis
+// map R_h of the orientation, block diagonal by degree), so H = X F-_{j,h} is formed as
+// (X F~_j) R_h:
+//   gather:      thread = (element, mode): the four neighbours' buffer columns (B1, B2, B3 or
+//                B1 - B2) into shared memory, rows (element, face, quantity) as pairs;
+//   trace phase: thread = (element, face, quantity): the generated sparse product X F~_j for
+//                the face j its neighbour touches (a warp computes the faces its lanes need);
+//   states:      thread = (element, face, face mode): H = G R_h (degree block), closed-form
+//                interface state with the neighbour coefficients;
+//   projection:  row phase with the generated F^_i products, as in k_predict_sp;
+//   update:      thread = (element, mode): flux rows per face, Q <- Q + S^N.
+template <int O, int M, int NE_>
+struct SpnCfg {
+  using C = Cfg<O, M, 1>;
+  static constexpr int B = C::B, F = C::F, NQ = C::NQ;
+  static constexpr int NE = NE_;                        // elements per CTA (tile variant: 8 or 4)
+  static constexpr int NROW = NE * 4 * 9;               // (element, face, quantity) rows
+  static constexpr int NT = rup(NROW > NE * B ? NROW : NE * B, 32);
+  static constexpr int XN = NROW + 1;                   // row stride of gathered columns and traces
+  static constexpr int NPART = SpShape<O>::NPART;       // parts of the projection
+  static constexpr int RT6 = rup(6 * NE, 32);
+  static_assert(NPART * RT6 <= NT, "projection rows");
+  static constexpr int XP6 = RT6 + 1;                   // stride of interface states / projections
+  static constexpr int NDP = ND + 1;
+  static constexpr int S_X = 0;                                                      // [B][XN]
+  static constexpr int S_P = 0;                                                      // [4B][XP6] over X
+  static constexpr int S_G = rup((B * XN > 4 * B * XP6) ? B * XN : 4 * B * XP6, 4);  // [F][XN]
+  static constexpr int S_W = rup(S_G + F * XN, 4);                                   // [4F][XP6]
+  static constexpr int S_R = rup(S_W + 4 * F * XP6, 4);                              // [3][F][F]
+  static constexpr int S_D = rup(S_R + 3 * F * F, 4);                                // [NE][NDP]
+  static constexpr int S_I = rup(S_D + NE * NDP, 4);                                 // [NE][9] ints
+  static constexpr int S_PERM = rup(S_I + NE * 9, 4);                                // [4 NE] ints
+  static constexpr int TOTAL = rup(S_PERM + 4 * NE, 4);
+  static_assert(4 * NE <= 32, "one warp sorts the face slots of a batch");
+};
+
+template <int O, int XP>
+__device__ __forceinline__ void sp_ntrace(int j, const float* x, float* y) {
+  if constexpr (O == 5) ltssp::sp_ntrace_o5<XP>(j, x, y);
+  if constexpr (O == 4) ltssp::sp_ntrace_o4<XP>(j, x, y);
+  if constexpr (O == 3) ltssp::sp_ntrace_o3<XP>(j, x, y);
+}
+
+template <int O, int M, int NE_>
+__global__ void __launch_bounds__(SpnCfg<O, M, NE_>::NT, (NE_ == 8 ? 2 : 4))
+    k_neighbour_sp(DevOps ops, DevState st, PhaseArgs ph) {
+  using S = SpnCfg<O, M, NE_>;
+  using C = typename S::C;
+  constexpr int B = S::B, F = S::F, NE = S::NE, NT = S::NT, XN = S::XN, XP6 = S::XP6, NQ = S::NQ, NDP = S::NDP;
+  extern __shared__ float4 smem4[];
+  float* smem = reinterpret_cast<float*>(smem4);
+  float* sX = smem + S::S_X;
+  float* sP = smem + S::S_P;
+  float* sG = smem + S::S_G;
+  float* sW = smem + S::S_W;
+  float* sR = smem + S::S_R;
+  float* sD = smem + S::S_D;
+  int* sI = reinterpret_cast<int*>(smem + S::S_I);      // per element: nbr[4], code[4], meta
+  int* sPerm = reinterpret_cast<int*>(smem + S::S_PERM); // face slots ordered by the neighbour's face j
+  const int tid = threadIdx.x;
+  for (int i = tid; i < 3 * F * F; i += NT) sR[i] = ops.Rh[i];
+
+  const bool act = tid < NE * B;                         // column task (element, mode)
+  const int es = act ? tid / B : 0;
+  const int b = act ? tid % B : 0;
+
+  const int part = (tid >> 5) % S::NPART;                // projection row: as in k_predict_sp
+  const int pair6 = ((tid >> 5) / S::NPART) * 32 + (tid & 31);
+  const bool pact = pair6 < 6 * NE;
+  const int nelem = ph.end - ph.begin;
+  const int nbatch = (nelem + NE - 1) / NE;
+  constexpr long long qs = C::QS, bs = C::BUFS;
+
+  for (int batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
+    const int e0 = ph.begin + batch * NE;
+    __syncthreads();
+    for (int i = tid; i < NE * ND; i += NT) {
+      const int ee = i / ND, gg = e0 + ee;
+      sD[ee * NDP + i % ND] = (gg < ph.end) ? __ldg(st.ndata + (size_t)gg * ND + (i % ND)) : 0.f;
+    }
+    for (int i = tid; i < NE * 9; i += NT) {
+      const int c = i % 9, gg = e0 + i / 9;
+      int v = -1;
+      if (gg < ph.end)
+        v = (c < 4) ? __ldg(st.nbr + (size_t)gg * 4 + c) : (c < 8 ? __ldg(st.ncode + (size_t)gg * 4 + c - 4) : __ldg(st.meta + gg));
+      sI[i] = v;
+    }
+    {
+      const int bn = batch + gridDim.x;
+      if (bn < nbatch) {
+        const int en = ph.begin + bn * NE;
+        prefetch_batch_q<NQ, B, 1, NT>(st.Q, qs, en, 0, min(NE, ph.end - en), tid);
+      }
+    }
+    __syncthreads();
+    // face slots (element, face) sorted by the neighbour's face j (faces without one last), so
+    // that the rows of a warp mostly ask for one face in the trace phase
+    if (tid < 32) {
+      const int fe = tid / 4, fi = tid % 4;
+      int key = 5;                                      // lanes past the batch's face slots
+      if (tid < 4 * NE) key = (e0 + fe < ph.end && sI[fe * 9 + fi] >= 0) ? (sI[fe * 9 + 4 + fi] & 0xff) / 3 : 4;
+      const unsigned lt = (1u << tid) - 1u;
+      int base = 0, rank = 0;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        const unsigned m = __ballot_sync(0xffffffffu, key == k);
+        if (key == k) rank = base + __popc(m & lt);
+        base += __popc(m);
+      }
+      if (tid < 4 * NE) sPerm[rank] = tid;
+    }
+    const int g = e0 + es;
+    const bool valid = act && g < ph.end;
+    // ---- gather the neighbours' time-integrated DOFs by cluster relation (Sec. V-B)
+    if (act) {
+      const int* ie = sI + es * 9;
+      const int cl = ie[8] & 0xff;
+      const int par = valid ? ph.parity[cl] : 0;
+      float xv[4][9];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int nb = valid ? ie[i] : -1;
+        const int rel = (ie[4 + i] >> 8) & 0xff;
+        const float* src1 = (rel == 1) ? st.B3 : ((rel == 2 && par == 0) ? st.B2 : st.B1);
+        const bool sub = (rel == 2 && par == 1);
+        const size_t off = (size_t)(nb < 0 ? 0 : nb) * bs + b;
+#pragma unroll
+        for (int r = 0; r < 9; ++r) xv[i][r] = (nb < 0) ? 0.f : __ldg(src1 + off + r * B);
+        if (sub) {
+#pragma unroll
+          for (int r = 0; r < 9; ++r) xv[i][r] -= __ldg(st.B2 + off + r * B);
+        }
+      }
+      float* xo = sX + b * XN + es * 36;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int r = 0; r < 9; ++r) xo[i * 9 + r] = xv[i][r];
+    }
+    __syncthreads();
+    // ---- traces on the neighbour's face j (every thread calls: warp-uniform face branches)
+    {
+      int j = -1, row = 0;
+      if (tid < S::NROW) {
+        const int slot = sPerm[tid / 9], fe = slot / 4, fi = slot % 4;
+        row = slot * 9 + tid % 9;
+        if (e0 + fe < ph.end && sI[fe * 9 + fi] >= 0) j = (sI[fe * 9 + 4 + fi] & 0xff) / 3;
+      }
+      sp_ntrace<O, XN>(j, sX + row, sG + row);
+    }
+    __syncthreads();
+    // ---- H = G R_h per face mode (degree block), interface states with the neighbour
+    // coefficients; faces without a neighbour contribute nothing
+#pragma unroll 1
+    for (int t = tid; t < NE * 4 * F; t += NT) {
+      const int fe = t / (4 * F), fi = (t / F) % 4, f = t % F;
+      float w6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (e0 + fe < ph.end && sI[fe * 9 + fi] >= 0) {
+        const int h = (sI[fe * 9 + 4 + fi] & 0xff) % 3;
+        const int pf = face_degree(f), f0 = nface(pf), f1 = nface(pf + 1);
+        const float* gp = sG + (fe * 4 + fi) * 9;
+        const float* R = sR + h * F * F + f;
+        float hv[9];
+#pragma unroll
+        for (int r = 0; r < 9; ++r) hv[r] = 0.f;
+        for (int q = f0; q < f1; ++q) {
+          const float w = R[q * F];
+#pragma unroll
+          for (int r = 0; r < 9; ++r) hv[r] = fmaf(gp[q * XN + r], w, hv[r]);
+        }
+        riemann_state(hv, sD + fe * NDP + 4 + 11 * fi, w6);
+      }
+      float* wp = sW + (fi * F + f) * XP6 + fe * 6;
+#pragma unroll
+      for (int r = 0; r < 6; ++r) wp[r] = w6[r];
+    }
+    __syncthreads();
+    // ---- projection P_i[r'][b] = sum_f W_i[r'][f] F^_i[f][b] (row phase, over the gathers)
+    if (pact) sp_proj<O, XP6>(part, sW + pair6, sP + pair6);
+    __syncthreads();
+    if (valid) {
+      constexpr int NS = (M > 0) ? 15 : 9;
+      float* q = st.Q + (size_t)g * qs + b;
+      float qv[NQ];
+#pragma unroll
+      for (int r = 0; r < NQ; ++r) qv[r] = q[r * B];
+      float Sv[NS];
+#pragma unroll
+      for (int r = 0; r < NS; ++r) Sv[r] = 0.f;
+      const float* nd = sD + es * NDP;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float* pp = sP + (i * B + b) * XP6 + es * 6;
+        float W[6];
+#pragma unroll
+        for (int r = 0; r < 6; ++r) W[r] = pp[r];
+        flux_rows_add<NS>(W, nd + 4 + 11 * i, nd[0], nd[1], nd[2], Sv);
+      }
+#pragma unroll
+      for (int r = 0; r < 9; ++r) q[r * B] = qv[r] + Sv[r];
+      if constexpr (M > 0) {
+#pragma unroll
+        for (int l = 0; l < M; ++l)
+#pragma unroll
+          for (int r = 0; r < 6; ++r) q[(9 + 6 * l + r) * B] = qv[9 + 6 * l + r] + ph.omega[l] * Sv[NS - 6 + r];
       }
     }
   }

@@ -27,6 +27,11 @@ struct Launchers {
   void (*predict_sp)(const DevOps&, const DevState&, const PhaseArgs&, int grid, cudaStream_t);
   size_t smem_predict_sp;
   int blocks_predict_sp, NE_SP, NT_SP;
+  // neighbour kernel of the same engine (face traces and orientation maps; no partition), in
+  // two tile variants: 8 elements per CTA (two CTAs per SM) or 4 (four CTAs per SM)
+  void (*neighbour_sp[2])(const DevOps&, const DevState&, const PhaseArgs&, int grid, cudaStream_t);
+  size_t smem_neighbour_sp[2];
+  int blocks_neighbour_sp[2], NEN_SP[2];
   // fg: simulation group size of the layout (FG of the fused instantiation, 1 for one simulation)
   void (*receivers)(const DevOps&, const float* Q, long long qs, int nsim, int fg, const float* edata,
                     const float* phi, const RecvItem* items, float* out, const float* omega, int n, cudaStream_t);
@@ -83,6 +88,16 @@ struct Impl {
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L->blocks_predict_sp, k_predict_sp<O, M>, SpCfg<O, M>::NT,
                                                         L->smem_predict_sp);
       if (e != cudaSuccess) return e;
+      e = smem_attrs(k_neighbour_sp<O, M, 8>, L->smem_neighbour_sp[0], true);
+      if (e != cudaSuccess) return e;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L->blocks_neighbour_sp[0], k_neighbour_sp<O, M, 8>,
+                                                        SpnCfg<O, M, 8>::NT, L->smem_neighbour_sp[0]);
+      if (e != cudaSuccess) return e;
+      e = smem_attrs(k_neighbour_sp<O, M, 4>, L->smem_neighbour_sp[1], true);
+      if (e != cudaSuccess) return e;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L->blocks_neighbour_sp[1], k_neighbour_sp<O, M, 4>,
+                                                        SpnCfg<O, M, 4>::NT, L->smem_neighbour_sp[1]);
+      if (e != cudaSuccess) return e;
     }
     if constexpr (M == 0) {
       e = cudaFuncSetAttribute(k_adj_pred<O>, cudaFuncAttributeMaxDynamicSharedMemorySize, AdjPredCfg<O>::SMEM_BYTES);
@@ -100,6 +115,11 @@ struct Impl {
   static void predict_sp(const DevOps& o, const DevState& s, const PhaseArgs& p, int grid, cudaStream_t st) {
     if constexpr (FG == 1)
       k_predict_sp<O, M><<<grid, SpCfg<O, M>::NT, SpCfg<O, M>::TOTAL * sizeof(float), st>>>(o, s, p);
+  }
+  template <int NE>
+  static void neighbour_sp(const DevOps& o, const DevState& s, const PhaseArgs& p, int grid, cudaStream_t st) {
+    if constexpr (FG == 1)
+      k_neighbour_sp<O, M, NE><<<grid, SpnCfg<O, M, NE>::NT, SpnCfg<O, M, NE>::TOTAL * sizeof(float), st>>>(o, s, p);
   }
   static void predict_tc(const DevOps& o, const DevState& s, const PhaseArgs& p, int grid, int passes, int* err,
                          long long wait_cycles, int suppress_commit, cudaStream_t st) {
@@ -173,6 +193,12 @@ struct Impl {
       L.smem_predict_sp = SpCfg<O, M>::TOTAL * sizeof(float);
       L.NE_SP = SpCfg<O, M>::NE;
       L.NT_SP = SpCfg<O, M>::NT;
+      L.neighbour_sp[0] = &neighbour_sp<8>;
+      L.neighbour_sp[1] = &neighbour_sp<4>;
+      L.smem_neighbour_sp[0] = SpnCfg<O, M, 8>::TOTAL * sizeof(float);
+      L.smem_neighbour_sp[1] = SpnCfg<O, M, 4>::TOTAL * sizeof(float);
+      L.NEN_SP[0] = 8;
+      L.NEN_SP[1] = 4;
     }
     L.neighbour = &neighbour;
     L.receivers = &receivers;

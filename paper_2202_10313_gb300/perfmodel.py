@@ -92,6 +92,50 @@ def operator_nonzeros(order, rel=1e-9):
                 Fb=[[nz(Fb[j, h]) for h in range(3)] for j in range(4)])
 
 
+def sparse_terms(order):
+    """Multiply-adds per row of the generated sparse products (the nonzero entries of the
+    library's FP64 operators, entries below 1e-7 of the largest being rounding of exact
+    zeros): time kernel per derivative variant v (elastic truncation; v = 0 full), volume,
+    face traces (= face projection, F^_i = F~_i^T)."""
+    import numpy as np
+    from . import binding
+    K, Ft, _ = binding.reference_operators(order)
+    kz = np.abs(K) > 1e-7 * np.abs(K).max()
+    fz = np.abs(Ft) > 1e-7 * np.abs(Ft).max()
+    time = [int(sum(kz[c][:nbasis(order - 1 - v), :nbasis(order - v)].sum() for c in range(3)))
+            for v in range(order - 1)]
+    return dict(time=time, vol=int(kz.sum()), face=int(fz.sum()))
+
+
+def flops_predict_sparse(o, m):
+    """Flops of k_predict_sp per element: the generated sparse products (time kernel, volume,
+    face traces and face projection: nonzero operator entries only, Sec. IV-A "all
+    sparsity"), the star / relaxation / Taylor arithmetic of the column phase, the
+    interface states and flux rows, and the update."""
+    B, F, NQ = nbasis(o), nface(o), 9 + 6 * m
+    t = sparse_terms(o)
+    time = sum(2 * 9 * t["time"][d if m == 0 else 0] for d in range(o - 1))
+    star = 2 * 54 + 20
+    ck_epi = star + m * 24 + m * 12 + 2 * (NQ + 9)
+    vol_epi = star + m * 24 + m * 12 + NQ
+    rows = 30 + (18 if m else 0)
+    return (time + (o - 1) * B * ck_epi + 2 * 9 * t["vol"] + B * vol_epi + 2 * 9 * t["face"] + 4 * F * 50
+            + 2 * 6 * t["face"] + B * 4 * rows + B * (NQ + 2 * 6 * m))
+
+
+def flops_neighbour_sparse(o, m):
+    """Flops of k_neighbour_sp per element: the traces X F~_j of the four neighbours' buffers on
+    their faces j (nonzero entries; each face of the reference element equally likely, so the
+    four faces together cost the nonzeros of all four F~), the orientation maps R_h (degree
+    blocks), the interface states, the generated F^ projection, flux rows and update."""
+    B, F, NQ = nbasis(o), nface(o), 9 + 6 * m
+    t = sparse_terms(o)
+    rh = sum((p + 1) ** 2 for p in range(o))          # terms of one R_h per face row
+    rows = 30 + (18 if m else 0)
+    return (2 * 9 * t["face"] + 2 * 9 * 4 * rh + 4 * F * 50 + 2 * 6 * t["face"] + B * 4 * rows
+            + B * (NQ + 2 * 6 * m))
+
+
 def essential_flops(order, m):
     """Flops of one element update if only the true nonzeros of K_c, F~ and F- were
     multiplied (the kernels multiply whole degree blocks: flops_predict + flops_neighbour);

@@ -65,13 +65,15 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def _central_difference(make, params, p, k, misfit, J, h_rel):
-    """Central difference of the GPU misfit w.r.t. parameter p of element k with the step
-    h = h_rel params[p][k], and the rounding floor it carries: J is a sum of squares of FP32
-    samples, so each evaluation is good to about 1e-6 J (ten times the FP32 epsilon), which
-    the difference quotient turns into 1e-6 J / h. Per element, the adjoint must agree within
-    a relative tolerance plus that floor."""
-    h = h_rel * params[p][k]
+def _central_difference(make, params, p, k, misfit, J, g, noise):
+    """Central difference of the GPU misfit w.r.t. parameter p of element k, with the floor
+    it can resolve. The relative step is h = min(0.1, 5e-3 J / |g p|), so that J moves by about
+    1 % (J is a sum of squares of FP32 samples, smooth in the parameter, but strongly
+    non-linear for the few elements next to the source). Each evaluation of J carries FP32
+    rounding of about `noise` J; the quotient turns that into noise J / h. Per element and
+    parameter the adjoint must agree within 2e-2 |g| + noise J / h."""
+    pk = params[p][k]
+    h = min(0.1, 5e-3 * J / max(abs(g * pk), 1e-300)) * pk
     vals = []
     for sgn in (1, -1):
         pp = [x.copy() for x in params]
@@ -79,7 +81,8 @@ def _central_difference(make, params, p, k, misfit, J, h_rel):
         t = make(pp)
         vals.append(misfit(t))
         t.close()
-    return (vals[0] - vals[1]) / (2 * h), 1e-6 * J / h
+    fd = (vals[0] - vals[1]) / (2 * h)
+    return fd, abs(fd - g) <= 2e-2 * abs(g) + noise * J / h, noise * J / h
 
 
 @pytest.mark.parametrize("order", [3, 4])
@@ -137,13 +140,14 @@ def test_gpu_gradient_against_central_differences_of_the_gpu_misfit():
     bad, worst = [], 0.0
     for p in range(3):
         for k in top + rest:
-            fd, tol = _central_difference(lambda pp: _gpu(order, m, *pp, q0, rec, src, dt), params, p, k,
-                                          lambda t: t.misfit_gradient(n, data, every=n)[0], J, 1e-2)
-            err = abs(fd - g[k, p])
-            if err > 1e-2 * abs(g[k, p]) + tol:
+            fd, ok, floor = _central_difference(lambda pp: _gpu(order, m, *pp, q0, rec, src, dt), params, p, k,
+                                                lambda t: t.misfit_gradient(n, data, every=n)[0], J, g[k, p], 1e-5)
+            if not ok:
                 bad.append((p, k, fd, g[k, p]))
-            if abs(g[k, p]) > 10 * tol:
-                worst = max(worst, err / abs(g[k, p]))
+            if abs(g[k, p]) > 10 * floor:
+                worst = max(worst, abs(fd - g[k, p]) / abs(g[k, p]))
+    for r in bad:
+        print("FD MISMATCH parameter %d element %d: central difference %.6e adjoint %.6e" % r)
     assert not bad, bad
     print("FD per-element worst relative error (gradients above the rounding floor): %.2e" % worst)
 

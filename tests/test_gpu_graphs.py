@@ -35,8 +35,11 @@ def _run(graphs, switch_engine=False):
     for step in range(5):                                 # five macro steps of 4 finest steps
         if switch_engine and step == 2:
             gpu.set_contraction("tf32x3")
-        if switch_engine and step == 4:
+        if switch_engine and step == 3:
             gpu.set_contraction("fp32")
+        if switch_engine and step == 4:
+            gpu.set_contraction("sparse")
+            gpu.set_tile(1)
         gpu.advance_steps(4)
     traces = [gpu.seismogram(r) for r in rids]
     return gpu.get_dofs(), traces, gpu.info()["launches"]

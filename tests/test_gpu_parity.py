@@ -140,8 +140,7 @@ def test_receivers_with_eight_samples_per_step(order, engine):
     m = synth.graded_box(5, 5, 3, 250.0, 125.0, seed=21)
     mat = synth.random_layers(m, n_layers=3, seed=8)
     gpu, ora, om = make_pair(order, 3, m, mat)
-    if engine != "fp32":
-        gpu.set_contraction(engine)
+    gpu.set_contraction(engine)
     cl, _, _ = gpu.setup_clusters(3, 0.5)
     ora.setup_clusters(3, 0.5)
     assert np.array_equal(cl, ora.clusters) and len(np.unique(cl)) == 3

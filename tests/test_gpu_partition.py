@@ -1,7 +1,9 @@
 """Emulated partitioned run on one GPU (Sec. V-C): cut faces take their neighbour
 contribution from face-local messages H = X F-_{j,h} computed on the sending side by a
-pack kernel. The arithmetic and its order are those of the unpartitioned run, so the DOFs
-must be bitwise equal to it, and within 1e-4 of the oracle."""
+pack kernel. The arithmetic and its order are those of the unpartitioned run with the same
+(gather-and-product) neighbour kernel, so the DOFs must be bitwise equal to it, and within
+1e-4 of the oracle. These runs use the FP32 dense-block engine, whose neighbour kernel is the
+one partitioned runs use."""
 import numpy as np
 import pytest
 
@@ -30,6 +32,7 @@ def test_partitioned_run_equals_unpartitioned_and_oracle(order, n_mech, n_parts)
     runs = []
     for parted in (False, True):
         gpu, ora, _ = make_pair(order, n_mech, m, mat)
+        gpu.set_contraction("fp32")
         gpu.add_point_source(xs, m6, 8.0, 0.06, 1e12)
         cl, _, _ = gpu.setup_clusters(3, 0.5)
         if parted:
@@ -83,6 +86,7 @@ def test_adjoint_of_a_partitioned_run_equals_the_unpartitioned_adjoint():
     out = []
     for parted in (False, True):
         gpu, _, _ = make_pair(order, 0, m, mat)
+        gpu.set_contraction("fp32")
         gpu.add_point_source(np.array([610.0, 640.0, -260.0]), np.array([0.2, -0.4, 0.2, 1.0, 0.1, -0.3]), 8.0, 0.06,
                              1e12)
         for x in rec:

@@ -137,3 +137,22 @@ def test_fused_handle_rejects_sparse_engine():
     g.set_mesh(m["xyz"], m["tet"], m["face_bc"])
     with pytest.raises(RuntimeError):
         g.set_contraction("sparse")
+
+
+def test_neighbour_tile_variants_bitwise_equal():
+    """The sparse engine's neighbour kernel with 8 and with 4 elements per CTA: the same
+    arithmetic per element, so bitwise equal results (order 5 and 4, 3 mechanisms)."""
+    m = synth.permute_vertex_order(synth.graded_box(5, 5, 3, 250.0, 125.0, seed=12), seed=2)
+    mat = synth.random_layers(m, n_layers=3, seed=5)
+    for order in (4, 5):
+        outs = []
+        for tile in (0, 1):
+            gpu, ora, _ = make_pair(order, 3, m, mat)
+            gpu.set_contraction("sparse")
+            gpu.set_tile(tile)
+            gpu.setup_clusters(3, 0.5)
+            ora.project(initial_field(ora.nq, [600.0, 700.0, -300.0], 400.0))
+            gpu.set_dofs(ora.Q)
+            gpu.advance_steps(8)
+            outs.append(gpu.get_dofs())
+        assert np.array_equal(outs[0], outs[1])

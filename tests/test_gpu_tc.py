@@ -145,7 +145,9 @@ def test_autotune_restores_state_and_keeps_accuracy():
     t_before = gpu.info()["time"]
     n_before = len(gpu.seismogram(rg)[0])
     res = gpu.autotune(allow_tf32=False)
-    assert res["contraction"] in ("fp32", "tf32x3") and len(res["candidates"]) >= 2
+    assert res["contraction"] in ("fp32", "sparse", "tf32x3") and len(res["candidates"]) >= 2
+    # engines x grid shapes x the sparse engine's two neighbour tile variants
+    assert {c["tile"] for c in res["candidates"] if c["contraction"] == "sparse"} == {0, 1}
     assert all(c["ms"] > 0 for c in res["candidates"])
     assert np.array_equal(gpu.get_dofs(), before)
     assert gpu.info()["time"] == t_before and len(gpu.seismogram(rg)[0]) == n_before

@@ -1,7 +1,7 @@
 """The generated sparse products of the predict kernel (contraction engine 'sparse') take
 exactly the nonzero entries of the stiffness matrices K_c and of the face matrices F~_i
-(Sec. III-A), with values equal to the oracle's independently built operators to FP32
-rounding, and no term the oracle has is dropped. The generator lists every product term
+and of their transposes F^_i (Sec. III-A), with values equal to the oracle's independently
+built operators to FP32 rounding, and no term the oracle has is dropped. The generator lists every product term
 (kind, part, output, k, value) it writes into the kernel."""
 import os
 import subprocess
@@ -34,13 +34,19 @@ def test_generated_terms_are_the_oracle_operators_nonzeros(order):
     want = {"t": np.stack([ob.K[c] for c in range(3)]).reshape(3 * B, B),
             "v": np.stack([ob.K[c].T for c in range(3)]).reshape(3 * B, B),
             "g": np.stack([ob.Ft[i].T for i in range(4)]).reshape(4 * F, B)}
-    scale = {"t": kmax, "v": kmax, "g": fmax}
+    # face projection: out (i, b) from the inputs (i, f), F^_i[f][b] = int psi_f phi_b = F~_i[b][f]
+    proj = np.zeros((4 * B, 4 * F))
+    for i in range(4):
+        proj[i * B:(i + 1) * B, i * F:(i + 1) * F] = ob.Fh[i].T
+    want["p"] = proj
+    want["n"] = np.stack([ob.Ft[j].T for j in range(4)]).reshape(4 * F, B)
+    scale = {"t": kmax, "v": kmax, "g": fmax, "p": fmax, "n": fmax}
     got = {k: np.zeros_like(v) for k, v in want.items()}
     part_of = {}
     for kind, part, o, k, val in terms:
         assert got[kind][o, k] == 0.0, "term listed twice"
         got[kind][o, k] = val
-        assert part_of.setdefault((kind if kind == "t" else "vg", o, kind), part) == part, "output split over parts"
+        assert part_of.setdefault((kind, o), part) == part, "output split over parts"
     for kind in want:
         w, g = want[kind], got[kind]
         if kind == "t":       # the kernel's full time variant writes outputs of degree <= O-2
