@@ -257,6 +257,7 @@ def run_ours(args, rank, world, local_rank):
         s.use_torch_memory(nclusters)
     if args.contraction != "auto":
         s.set_contraction(args.contraction)
+        s.set_tile(args.tile)
     _, lam, speedup = s.setup_clusters(nclusters, CFL)
     pstats = None
     if args.partition > 1:
@@ -371,7 +372,7 @@ def run_ours(args, rank, world, local_rank):
                                "%s, 64 receivers; step = 1 macro step (%d finest steps)"
                                % (K, nclusters, lam, CFL, srcs, period),
                    "elements": K, "fused": F, "updates_per_step": per_macro,
-                   "launch": dict(s.launch_config(), engine=engine, tile=(tuned["tile"] if tuned else 0)),
+                   "launch": dict(s.launch_config(), engine=engine, tile=(tuned["tile"] if tuned else args.tile)),
                    "cluster_elems": info["cluster_elems"].tolist(), "theoretical_lts_speedup": speedup,
                    "l2": ("inputs larger than L2 (DOFs %.1f GB)" if dof_bytes > 129e6 else
                           "inputs within L2 (DOFs %.2f GB): a quick-check size, not a timing case") % (dof_bytes / 1e9),
@@ -434,6 +435,8 @@ def main():
                     help="elastic order-5 workload: 786,432 tets, 3 layers, 4 clusters (a parity config)")
     ap.add_argument("--partition", type=int, default=1,
                     help="emulated partitioned run: P weighted parts exchanging face-local messages")
+    ap.add_argument("--tile", type=int, default=0, choices=[0, 1],
+                    help="with an explicit --contraction sparse: the neighbour kernel's 8 (0) or 4 (1) elements per CTA")
     ap.add_argument("--contraction", default="auto", choices=["auto", "fp32", "sparse", "tf32x3", "tf32"],
                     help="engine of the time/volume contractions: FP32 CUDA cores or tensor cores; auto runs "
                          "the autotuner over the FP32-accurate engines and the grid shapes")

@@ -962,48 +962,116 @@ void make_adj_tables(const lts_solver* h, AdjTables& T) {
   T.FbT = base + (fbt - kt);
 }
 
-void contract_gradient(const lts_solver* h, const std::vector<double>& W, double* grad) {
-  const int64_t K = h->mesh.K;
-  {
-      auto work = [&](int64_t k0, int64_t k1) {
-        lts::Dual S[3][81], Am[81], Ap[81];
-        for (int64_t e = k0; e < k1; ++e) {
-          const double* We = &W[h->iperm[e] * ltsdev::AM_SIZE];
-          double g[3] = {0, 0, 0};
-          for (int p = 0; p < 3; ++p) {
-            element_operators<lts::Dual>(h, e, -1, p, S, nullptr, nullptr);
-            for (int c = 0; c < 3; ++c)
-              for (int q = 0; q < 81; ++q) g[p] += S[c][q].d * We[ltsdev::AM_STAR + c * 81 + q];
-          }
-          for (int i = 0; i < 4; ++i) {
-            for (int p = 0; p < 3; ++p) {
-              element_operators<lts::Dual>(h, e, i, p, nullptr, Am, Ap);
-              for (int q = 0; q < 81; ++q)
-                g[p] += Am[q].d * We[ltsdev::AM_LOC + i * 81 + q] + Ap[q].d * We[ltsdev::AM_NBR + i * 81 + q];
-            }
-            // the neighbour's face that looks at e: its operators depend on e's material
-            const int64_t nb = h->mesh.nbr[4 * e + i];
-            if (nb < 0) continue;
-            const int ip = h->mesh.nbr_face[4 * e + i];
-            const double* Wn = &W[h->iperm[nb] * ltsdev::AM_SIZE];
-            for (int p = 0; p < 3; ++p) {
-              element_operators<lts::Dual>(h, nb, ip, 3 + p, nullptr, Am, Ap);
-              for (int q = 0; q < 81; ++q)
-                g[p] += Am[q].d * Wn[ltsdev::AM_LOC + ip * 81 + q] + Ap[q].d * Wn[ltsdev::AM_NBR + ip * 81 + q];
-            }
-          }
-          for (int p = 0; p < 3; ++p) grad[3 * e + p] = g[p];
-        }
-      };
-      const int nth = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
-      std::vector<std::thread> pool;
-      const int64_t chunk = (K + nth - 1) / nth;
-      for (int t = 0; t < nth; ++t) {
-        const int64_t k0 = t * chunk, k1 = std::min(K, k0 + chunk);
-        if (k0 < k1) pool.emplace_back(work, k0, k1);
-      }
-      for (auto& th : pool) th.join();
+// Material gradient from the correlations W (device, [internal element][AM_SIZE]): dJ/dp =
+// sum <dM/dp, W> over the element's star matrices and face operators and over the operators
+// of the neighbours' faces that look at it (they depend on this element's material through
+// the Riemann state). One thread per element (original order); the derivatives are exact,
+// by forward-mode dual numbers through the same closed forms the forward set-up evaluates
+// (host_flux.h), contracted with W without forming the 9 x 9 matrices.
+struct GradGeom {
+  const double *jinv, *normal, *area, *detJ, *rho, *lam, *mu, *W;
+  const int *bc, *nbr, *nbr_face;
+  const long long* iperm;
+  long long K;
+};
+
+__device__ lts::Dual grad_face_dot(const GradGeom& g, long long k, int face, int param) {
+  using lts::Dual;
+  auto mat = [&](long long e, int base, Dual* m) {
+    m[0] = Dual(g.rho[e], param == base ? 1.0 : 0.0);
+    m[1] = Dual(g.lam[e], param == base + 1 ? 1.0 : 0.0);
+    m[2] = Dual(g.mu[e], param == base + 2 ? 1.0 : 0.0);
+  };
+  Dual own[3], oth[3];
+  mat(k, 0, own);
+  const Dual rinv = Dual(1.0) / own[0];
+  const int bc = g.bc[4 * k + face];
+  const long long nb = g.nbr[4 * k + face];
+  if (nb >= 0)
+    mat(nb, 3, oth);
+  else
+    for (int q = 0; q < 3; ++q) oth[q] = own[q];
+  const Dual zp = lts::sqrt_t((own[1] + Dual(2.0) * own[2]) * own[0]), zs = lts::sqrt_t(own[2] * own[0]);
+  const Dual zpo = nb >= 0 ? lts::sqrt_t((oth[1] + Dual(2.0) * oth[2]) * oth[0]) : zp;
+  const Dual zso = nb >= 0 ? lts::sqrt_t(oth[2] * oth[0]) : zs;
+  const Dual scale(-2.0 * g.area[4 * k + face] / g.detJ[k]);
+  Dual cl[8], cn[8];
+  lts::face_coefficients_t<Dual>(bc, zp, zs, zpo, zso, scale, cl, cn);
+  const double* Wk = g.W + (size_t)g.iperm[k] * ltsdev::AM_SIZE;
+  const double* n = g.normal + 12 * k + 3 * face;
+  return lts::face_flux_dot<Dual>(n, cl, own[1], own[2], rinv, Wk + ltsdev::AM_LOC + face * 81) +
+         lts::face_flux_dot<Dual>(n, cn, own[1], own[2], rinv, Wk + ltsdev::AM_NBR + face * 81);
+}
+
+__global__ void k_grad_contract(GradGeom g, double* grad) {
+  using lts::Dual;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= g.K) return;
+  const double* We = g.W + (size_t)g.iperm[e] * ltsdev::AM_SIZE;
+  for (int p = 0; p < 3; ++p) {
+    const Dual rho(g.rho[e], p == 0 ? 1.0 : 0.0), lam(g.lam[e], p == 1 ? 1.0 : 0.0), mu(g.mu[e], p == 2 ? 1.0 : 0.0);
+    double acc = lts::star_dot<Dual>(g.jinv + 9 * e, lam, mu, Dual(1.0) / rho, We + ltsdev::AM_STAR).d;
+    for (int i = 0; i < 4; ++i) {
+      acc += grad_face_dot(g, e, i, p).d;
+      const long long nb = g.nbr[4 * e + i];
+      if (nb >= 0) acc += grad_face_dot(g, nb, g.nbr_face[4 * e + i], 3 + p).d;
+    }
+    grad[3 * e + p] = acc;
   }
+}
+
+void contract_gradient(const lts_solver* h, const double* d_w, double* grad, cudaStream_t stream) {
+  const lts::Mesh& M = h->mesh;
+  const int64_t K = M.K;
+  std::vector<int> bc(4 * K), nbr(4 * K), nface(4 * K);
+  std::vector<long long> iperm(K);
+  for (int64_t i = 0; i < 4 * K; ++i) {
+    bc[i] = M.bc[i];
+    nbr[i] = (int)M.nbr[i];
+    nface[i] = M.nbr_face[i];
+  }
+  for (int64_t k = 0; k < K; ++k) iperm[k] = (long long)h->iperm[k];
+  DevBuf d_geo, d_int, d_perm, d_grad;
+  const size_t nd = (size_t)K * (9 + 12 + 4 + 1 + 3);
+  d_geo.alloc(sizeof(double) * nd);
+  d_int.alloc(sizeof(int) * 12 * K);
+  d_perm.alloc(sizeof(long long) * K);
+  d_grad.alloc(sizeof(double) * 3 * K);
+  double* geo = d_geo.get<double>();
+  int* in = d_int.get<int>();
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, stream), "gradient geometry");
+  };
+  GradGeom g{};
+  g.jinv = geo;
+  g.normal = geo + 9 * K;
+  g.area = geo + 21 * K;
+  g.detJ = geo + 25 * K;
+  g.rho = geo + 26 * K;
+  g.lam = geo + 27 * K;
+  g.mu = geo + 28 * K;
+  g.W = d_w;
+  g.bc = in;
+  g.nbr = in + 4 * K;
+  g.nbr_face = in + 8 * K;
+  g.iperm = d_perm.get<long long>();
+  g.K = K;
+  up(const_cast<double*>(g.jinv), M.Jinv.data(), sizeof(double) * 9 * K);
+  up(const_cast<double*>(g.normal), M.normal.data(), sizeof(double) * 12 * K);
+  up(const_cast<double*>(g.area), M.area.data(), sizeof(double) * 4 * K);
+  up(const_cast<double*>(g.detJ), M.detJ.data(), sizeof(double) * K);
+  up(const_cast<double*>(g.rho), h->mat.rho.data(), sizeof(double) * K);
+  up(const_cast<double*>(g.lam), h->lam.data(), sizeof(double) * K);
+  up(const_cast<double*>(g.mu), h->mu.data(), sizeof(double) * K);
+  up(in, bc.data(), sizeof(int) * 4 * K);
+  up(in + 4 * K, nbr.data(), sizeof(int) * 4 * K);
+  up(in + 8 * K, nface.data(), sizeof(int) * 4 * K);
+  up(d_perm.p, iperm.data(), sizeof(long long) * K);
+  const int threads = 128;
+  k_grad_contract<<<(unsigned)((K + threads - 1) / threads), threads, 0, stream>>>(g, d_grad.get<double>());
+  ck(cudaGetLastError(), "gradient contraction");
+  ck(cudaMemcpyAsync(grad, d_grad.p, sizeof(double) * 3 * K, cudaMemcpyDeviceToHost, stream), "download gradient");
+  ck(cudaStreamSynchronize(stream), "synchronize");
 }
 
 
@@ -1245,8 +1313,6 @@ void adjoint_lts(lts_solver* h, int64_t n_macro, int64_t every, const double* da
   ck(cudaGetLastError(), "adjoint kernels");
   dcopy(h->dst.Q, d_qn.p, qbytes);
   h->s_now = s0 + n_macro * period;
-  std::vector<double> W((size_t)K * ltsdev::AM_SIZE);
-  ck(cudaMemcpyAsync(W.data(), d_w.p, sizeof(double) * W.size(), cudaMemcpyDeviceToHost, stream), "correlations");
   h->adj_src_grad.assign((size_t)nsrc * 6, 0.0);
   if (nsrc > 0)
     ck(cudaMemcpyAsync(h->adj_src_grad.data(), d_sg.p, sizeof(double) * nsrc * 6, cudaMemcpyDeviceToHost, stream),
@@ -1266,7 +1332,7 @@ void adjoint_lts(lts_solver* h, int64_t n_macro, int64_t every, const double* da
       for (int64_t k = 0; k < K; ++k)
         for (int q = 0; q < NB9; ++q)
           dq0[((size_t)f * K + k) * NB9 + q] = lq[((size_t)h->iperm[k] * nsim + f) * NB9 + q];
-  if (grad) contract_gradient(h, W, grad);
+  if (grad) contract_gradient(h, d_w.get<double>(), grad, stream);
 }
 
 }  // namespace
@@ -1836,14 +1902,18 @@ int lts_launch_config(lts_t* h, int* ctas_per_sm, int* threads) {
   return run(h, [&] {
     const Launchers& X = h->L;
     const bool tc = X.predict_tc != nullptr;
+    // the predict and neighbour kernels of the handle's engine (sparse: with its tile variant)
+    const bool sp = h->contraction == LTS_CONTRACT_SPARSE && X.predict_sp;
+    const bool nsp = sp && X.neighbour_sp[0] && h->n_parts <= 1;
+    const int tv = h->tile & 1;
     if (ctas_per_sm) {
-      ctas_per_sm[0] = X.blocks_predict;
-      ctas_per_sm[1] = X.blocks_neighbour;
+      ctas_per_sm[0] = sp ? X.blocks_predict_sp : X.blocks_predict;
+      ctas_per_sm[1] = nsp ? X.blocks_neighbour_sp[tv] : X.blocks_neighbour;
       ctas_per_sm[2] = tc ? X.blocks_predict_tc : 0;
     }
     if (threads) {
-      threads[0] = X.NT;
-      threads[1] = X.NTN;
+      threads[0] = sp ? X.NT_SP : X.NT;
+      threads[1] = nsp ? X.NTN_SP[tv] : X.NTN;
       threads[2] = tc ? X.NT : 0;
     }
   });

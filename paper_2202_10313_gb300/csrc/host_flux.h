@@ -12,10 +12,17 @@
 
 #include "../../include/ader_lts.h"
 
+// host and device (the adjoint's material-gradient contraction runs on the GPU)
+#ifdef __CUDACC__
+#define LTS_HD __host__ __device__
+#else
+#define LTS_HD
+#endif
+
 namespace lts {
 
 template <typename T>
-void face_coefficients_t(int bc, T zp_i, T zs_i, T zp_o, T zs_o, T scale, T* loc, T* nbc) {
+LTS_HD void face_coefficients_t(int bc, T zp_i, T zs_i, T zp_o, T zs_o, T scale, T* loc, T* nbc) {
   T a[4], b[4], an[4], bn[4];
   if (bc == LTS_BC_FREE_SURFACE) {
     a[0] = T(1.0); a[1] = T(-1.0) / zp_i; a[2] = T(0.0); a[3] = T(0.0);
@@ -46,7 +53,7 @@ void face_coefficients_t(int bc, T zp_i, T zs_i, T zp_o, T zs_o, T scale, T* loc
 // side, then the flux rows it adds: S -= flux(w) with the interior element's lam, mu,
 // 1/rho (the forward kernels' riemann_state and flux_rows_add).
 template <typename T>
-void face_flux_apply(const T g[9], const double n[3], const T c[8], T lam, T mu, T rinv, T S[9]) {
+LTS_HD void face_flux_apply(const T g[9], const double n[3], const T c[8], T lam, T mu, T rinv, T S[9]) {
   const double nx = n[0], ny = n[1], nz = n[2];
   const T tx = g[0] * nx + g[3] * ny + g[5] * nz;
   const T ty = g[3] * nx + g[1] * ny + g[4] * nz;
@@ -81,7 +88,7 @@ void face_flux_apply(const T g[9], const double n[3], const T c[8], T lam, T mu,
 
 // 9 x 9 matrix of the face map g -> S (row-major [out][in]).
 template <typename T>
-void face_flux_matrix(const double n[3], const T c[8], T lam, T mu, T rinv, T M[81]) {
+LTS_HD void face_flux_matrix(const double n[3], const T c[8], T lam, T mu, T rinv, T M[81]) {
   for (int j = 0; j < 9; ++j) {
     T g[9], S[9];
     for (int q = 0; q < 9; ++q) {
@@ -93,15 +100,31 @@ void face_flux_matrix(const double n[3], const T c[8], T lam, T mu, T rinv, T M[
   }
 }
 
-// Star matrices S_c (row-major [out][in]) of the time kernel's map D_{d+1} = sum_c S_c Y_c,
-// Y_c = D_d K_c^T (the forward kernels' star_apply: physical velocity gradient W_d =
-// sum_c dxi_c/dx_d Y_c, Hooke's law on the stress rows, stress divergence / rho on the
-// velocity rows). jinv[c*3+d] = dxi_c/dx_d.
+// sum_{q,j} M[q][j] W[q*9 + j] of that matrix, column by column (no 9 x 9 storage).
 template <typename T>
-void star_matrices_t(const double jinv[9], T lam, T mu, T rinv, T S[3][81]) {
-  static const int SIG[3][3] = {{0, 3, 5}, {3, 1, 4}, {5, 4, 2}};
-  for (int c = 0; c < 3; ++c)
-    for (int q = 0; q < 81; ++q) S[c][q] = T(0.0);
+LTS_HD T face_flux_dot(const double n[3], const T c[8], T lam, T mu, T rinv, const double* W) {
+  T acc(0.0);
+  for (int j = 0; j < 9; ++j) {
+    T g[9], S[9];
+    for (int q = 0; q < 9; ++q) {
+      g[q] = T(q == j ? 1.0 : 0.0);
+      S[q] = T(0.0);
+    }
+    face_flux_apply(g, n, c, lam, mu, rinv, S);
+    for (int q = 0; q < 9; ++q) acc = acc + S[q] * W[q * 9 + j];
+  }
+  return acc;
+}
+
+// Voigt index of the stress component (i, d).
+LTS_HD inline int voigt(int i, int d) {
+  return i == d ? i : ((i + d == 1) ? 3 : ((i + d == 3) ? 4 : 5));
+}
+
+// The terms of the star matrices (below), each handed to add(c, out * 9 + in, term); an
+// entry may receive several terms.
+template <typename T, typename Add>
+LTS_HD void star_terms_t(const double jinv[9], T lam, T mu, T rinv, Add&& add) {
   for (int c = 0; c < 3; ++c) {
     // stress rows from the velocity gradient g[d][j] = sum_c jinv[c][d] Y_c[6+j]
     for (int d = 0; d < 3; ++d)
@@ -110,40 +133,61 @@ void star_matrices_t(const double jinv[9], T lam, T mu, T rinv, T S[3][81]) {
         const int col = 6 + j;
         // tr = g00 + g11 + g22
         if (d == j) {
-          for (int a = 0; a < 3; ++a) S[c][a * 9 + col] = S[c][a * 9 + col] + lam * w;
-          S[c][d * 9 + col] = S[c][d * 9 + col] + T(2.0) * mu * w;
+          for (int a = 0; a < 3; ++a) add(c, a * 9 + col, lam * w);
+          add(c, d * 9 + col, T(2.0) * mu * w);
         } else {
           // out[3] = mu (g01 + g10), out[4] = mu (g12 + g21), out[5] = mu (g02 + g20)
-          const int lo = d < j ? d : j, hi = d < j ? j : d;
-          const int row = (lo == 0 && hi == 1) ? 3 : ((lo == 1 && hi == 2) ? 4 : 5);
-          S[c][row * 9 + col] = S[c][row * 9 + col] + mu * w;
+          add(c, voigt(d, j) * 9 + col, mu * w);
         }
       }
     // velocity rows: rinv * sum_d jinv[c][d] Y_c[SIG[i][d]]
     for (int i = 0; i < 3; ++i)
-      for (int d = 0; d < 3; ++d) {
-        const int col = SIG[i][d];
-        S[c][(6 + i) * 9 + col] = S[c][(6 + i) * 9 + col] + rinv * jinv[c * 3 + d];
-      }
+      for (int d = 0; d < 3; ++d) add(c, (6 + i) * 9 + voigt(i, d), rinv * jinv[c * 3 + d]);
   }
+}
+
+// Star matrices S_c (row-major [out][in]) of the time kernel's map D_{d+1} = sum_c S_c Y_c,
+// Y_c = D_d K_c^T (the forward kernels' star_apply: physical velocity gradient W_d =
+// sum_c dxi_c/dx_d Y_c, Hooke's law on the stress rows, stress divergence / rho on the
+// velocity rows). jinv[c*3+d] = dxi_c/dx_d.
+template <typename T>
+LTS_HD void star_matrices_t(const double jinv[9], T lam, T mu, T rinv, T S[3][81]) {
+  for (int c = 0; c < 3; ++c)
+    for (int q = 0; q < 81; ++q) S[c][q] = T(0.0);
+  star_terms_t<T>(jinv, lam, mu, rinv, [&](int c, int q, T v) { S[c][q] = S[c][q] + v; });
+}
+
+// sum_c sum_q S_c[q] W[c*81 + q] of the star matrices.
+template <typename T>
+LTS_HD T star_dot(const double jinv[9], T lam, T mu, T rinv, const double* W) {
+  T acc(0.0);
+  star_terms_t<T>(jinv, lam, mu, rinv, [&](int c, int q, T v) { acc = acc + v * W[c * 81 + q]; });
+  return acc;
 }
 
 // Forward-mode dual number with one derivative component.
 struct Dual {
   double v, d;
-  Dual(double x = 0.0, double dx = 0.0) : v(x), d(dx) {}
+  LTS_HD Dual(double x = 0.0, double dx = 0.0) : v(x), d(dx) {}
 };
-inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
-inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
-inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
-inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
-inline Dual operator/(Dual a, Dual b) { return Dual(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)); }
-inline Dual operator*(Dual a, double b) { return Dual(a.v * b, a.d * b); }
-inline Dual operator*(double a, Dual b) { return Dual(a * b.v, a * b.d); }
-inline Dual sqrt_t(Dual a) {
-  const double s = std::sqrt(a.v);
+LTS_HD inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+LTS_HD inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+LTS_HD inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+LTS_HD inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+LTS_HD inline Dual operator/(Dual a, Dual b) { return Dual(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)); }
+LTS_HD inline Dual operator*(Dual a, double b) { return Dual(a.v * b, a.d * b); }
+LTS_HD inline Dual operator*(double a, Dual b) { return Dual(a * b.v, a * b.d); }
+LTS_HD inline double sqrt_d(double a) {
+#ifdef __CUDA_ARCH__
+  return ::sqrt(a);
+#else
+  return std::sqrt(a);
+#endif
+}
+LTS_HD inline Dual sqrt_t(Dual a) {
+  const double s = sqrt_d(a.v);
   return Dual(s, a.d / (2.0 * s));
 }
-inline double sqrt_t(double a) { return std::sqrt(a); }
+LTS_HD inline double sqrt_t(double a) { return sqrt_d(a); }
 
 }  // namespace lts

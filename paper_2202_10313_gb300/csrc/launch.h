@@ -31,7 +31,7 @@ struct Launchers {
   // two tile variants: 8 elements per CTA (two CTAs per SM) or 4 (four CTAs per SM)
   void (*neighbour_sp[2])(const DevOps&, const DevState&, const PhaseArgs&, int grid, cudaStream_t);
   size_t smem_neighbour_sp[2];
-  int blocks_neighbour_sp[2], NEN_SP[2];
+  int blocks_neighbour_sp[2], NEN_SP[2], NTN_SP[2];
   // fg: simulation group size of the layout (FG of the fused instantiation, 1 for one simulation)
   void (*receivers)(const DevOps&, const float* Q, long long qs, int nsim, int fg, const float* edata,
                     const float* phi, const RecvItem* items, float* out, const float* omega, int n, cudaStream_t);
@@ -199,6 +199,8 @@ struct Impl {
       L.smem_neighbour_sp[1] = SpnCfg<O, M, 4>::TOTAL * sizeof(float);
       L.NEN_SP[0] = 8;
       L.NEN_SP[1] = 4;
+      L.NTN_SP[0] = SpnCfg<O, M, 8>::NT;
+      L.NTN_SP[1] = SpnCfg<O, M, 4>::NT;
     }
     L.neighbour = &neighbour;
     L.receivers = &receivers;

@@ -105,6 +105,7 @@ def test_fused_equals_single_simulation_runs_and_energy_sums():
     e_sum = 0.0
     for f in range(F):
         s, _, _ = make_pair(order, n_mech, m, mat)
+        s.set_contraction("fp32")     # the kernels a fused handle runs
         s.add_point_source(pos[f], m6[f], f0[f], 0.1, 1e12)
         s.setup_clusters(2, 0.5)
         s.set_dofs(d0[f])
@@ -152,6 +153,7 @@ def test_maximum_fused_count():
     assert np.all(np.isfinite(got))
     for f in (0, 1, 31, 62, 63):
         s, _, _ = make_pair(order, n_mech, m, mat)
+        s.set_contraction("fp32")     # the kernels a fused handle runs
         s.add_point_source(pos[f], m6[f], f0[f], 0.1, 1e12)
         s.setup_clusters(2, 0.5)
         s.set_dofs(d0[f])
