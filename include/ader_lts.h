@@ -202,10 +202,11 @@ int lts_transfer_bytes(lts_t* h, int64_t* h2d, int64_t* d2h);
  * the products of K_c, of the face matrices F~_i and of their transposes generated at build
  * time from the nonzero entries only (Sec. IV-A "all sparsity"), in the predict kernel and
  * in a neighbour kernel that forms X F-_{j,h} as (X F~_j) R_h (R_h the face-basis map of the
- * orientation); one simulation only, and a partitioned run keeps the other engines'
- * neighbour kernel. The tensor-core engines' surface products run on CUDA cores. Takes effect at the next lts_advance. Errors: LTS_ERR_ARG for an unknown mode or a
- * mode the handle's shape has no kernel for (tensor cores: order 3 with one simulation;
- * sparse: fused simulations). A tensor-core wait that gives up (bounded, about one second)
+ * orientation); with fused simulations it runs (element, simulation) slots, and a
+ * partitioned run keeps the other engines' neighbour kernel. The tensor-core engines'
+ * surface products run on CUDA cores. Takes effect at the next lts_advance. Errors: LTS_ERR_ARG for an unknown mode or a
+ * mode the handle's shape has no kernel for (tensor cores: order 3 with one simulation).
+ * A tensor-core wait that gives up (bounded, about one second)
  * makes the next synchronising call return LTS_ERR_TIMEOUT. */
 enum { LTS_CONTRACT_FP32 = 0, LTS_CONTRACT_TF32X3 = 1, LTS_CONTRACT_TF32 = 2, LTS_CONTRACT_SPARSE = 3 };
 int lts_set_contraction(lts_t* h, int mode);

@@ -727,7 +727,10 @@ int enqueue_phase(lts_solver* h, const Phase& ph, cudaStream_t stream, bool with
   }
   // CTA batches: NE elements (one simulation) or one element and FG of its simulations
   const int ne_batch = ph.kind == 0 ? (use_nsp ? X.NEN_SP[tv] : X.NEN) : (use_sp ? X.NE_SP : X.NE);
-  const int nb = X.FG > 1 ? nelem * (h->nsim / X.FG) : (nelem + ne_batch - 1) / ne_batch;
+  // sparse engine: batches of ne_batch slots (elements, or (element, simulation) pairs)
+  const bool slots = ph.kind == 0 ? use_nsp : use_sp;
+  const int nb = slots ? (int)(((int64_t)nelem * h->nsim + ne_batch - 1) / ne_batch)
+                       : (X.FG > 1 ? nelem * (h->nsim / X.FG) : (nelem + ne_batch - 1) / ne_batch);
   if (with_receivers && ph.kind == 1 && ph.item_end > ph.item_beg) {
     X.receivers(h->dops, h->dst.Q, h->dst.qs, h->nsim, X.FG, h->dst.edata, h->d_recv_phi, h->d_ritems + ph.item_beg,
                 h->d_seis, pa.omega, ph.item_end - ph.item_beg, stream);
@@ -1359,8 +1362,10 @@ int lts_create(int order, int n_mech, int n_fused, int device, lts_t** out) {
     h->nsim = n_fused;
     if (!ltsdev::get_launchers(order, n_mech, n_fused > 1, &h->L)) fail(LTS_ERR_ARG, "unsupported order / mechanisms");
     if (n_fused > 1 && n_fused % h->L.FG != 0) fail(LTS_ERR_ARG, "fused count not a multiple of the CTA group");
-    // one simulation: the sparse-product kernels by default (the fastest FP32 engine)
-    if (h->L.predict_sp) h->contraction = LTS_CONTRACT_SPARSE;
+    // one simulation: the sparse-product kernels by default (the fastest FP32 engine there;
+    // with fused simulations the dense-block kernels, whose slots keep the simulations of an
+    // element in the innermost 16 bytes, are faster)
+    if (h->L.predict_sp && n_fused == 1) h->contraction = LTS_CONTRACT_SPARSE;
     if (device >= 0) {
       ck(cudaSetDevice(device), "cudaSetDevice");
       ck(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device), "device attribute");
@@ -2236,7 +2241,7 @@ int lts_set_contraction(lts_t* h, int mode) {
       fail(LTS_ERR_ARG, "unknown contraction mode");
     if ((mode == LTS_CONTRACT_TF32X3 || mode == LTS_CONTRACT_TF32) && !h->L.predict_tc)
       fail(LTS_ERR_ARG, "no tensor-core kernel for this shape");
-    if (mode == LTS_CONTRACT_SPARSE && !h->L.predict_sp) fail(LTS_ERR_ARG, "no sparse kernel for fused simulations");
+    if (mode == LTS_CONTRACT_SPARSE && !h->L.predict_sp) fail(LTS_ERR_ARG, "no sparse kernel for this shape");
     h->contraction = mode;
   });
 }

@@ -89,7 +89,26 @@ __device__ __forceinline__ void sp_proj(int part, const float* x, float* y) {
   if constexpr (O == 3) ltssp::sp_proj_o3<XP>(part, x, y);
 }
 
-template <int O, int M>
+// Slots of a phase: one simulation (FUSED false): slot = element; fused simulations: slot =
+// (element, simulation), the simulations of an element consecutive, simulation f of element
+// k at k * (element stride) + (f / G) * (rows x B x G) + (row x B + mode) x G + f mod G in the
+// simulation-blocked layout (G = FUSED_GROUP). The per-slot arithmetic is the same either way.
+template <bool FUSED>
+struct Slots {
+  int nsim;
+  long long n;                                  // slots in the phase
+  __device__ Slots(const DevState& st, const PhaseArgs& ph)
+      : nsim(FUSED ? st.nsim : 1), n((long long)(ph.end - ph.begin) * (FUSED ? st.nsim : 1)) {}
+  __device__ int elem(const PhaseArgs& ph, long long t) const { return ph.begin + (int)(t / nsim); }
+  // offset of (slot t, row 0, mode 0) from its element's start in an array of `rows` rows
+  __device__ size_t sub(long long t, int rows, int B) const {
+    if (!FUSED) return 0;
+    const int f = (int)(t % nsim);
+    return (size_t)(f / FUSED_GROUP) * rows * B * FUSED_GROUP + f % FUSED_GROUP;
+  }
+};
+
+template <int O, int M, bool FUSED>
 __global__ void __launch_bounds__(SpCfg<O, M>::NT, 2) k_predict_sp(DevOps ops, DevState st, PhaseArgs ph) {
   using S = SpCfg<O, M>;
   using C = typename S::C;
@@ -115,18 +134,21 @@ __global__ void __launch_bounds__(SpCfg<O, M>::NT, 2) k_predict_sp(DevOps ops, D
   const int part = (tid >> 5) % S::NPART, pair = ((tid >> 5) / S::NPART) * 32 + (tid & 31);
   const bool ract = pair < S::NPAIR;          // (element, quantity) rows of the 9 elastic rows
   const bool pact = pair < 6 * NE;            // (element, interface-state) rows of the projection
-  const int nelem = ph.end - ph.begin;
-  const int nbatch = (nelem + NE - 1) / NE;
-  constexpr long long qs = C::QS, bs = C::BUFS;
+  const Slots<FUSED> sl(st, ph);
+  const int nbatch = (int)((sl.n + NE - 1) / NE);
+  const long long qs = FUSED ? st.qs : C::QS, bs = FUSED ? st.bs : C::BUFS;
+  constexpr int RS = FUSED ? B * FUSED_GROUP : B;   // row stride of Q and the buffers
+  constexpr int CS = FUSED ? FUSED_GROUP : 1;       // mode stride
   const int col = es * 9;                     // this column's pair offset
 
   for (int batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
-    const int e0 = ph.begin + batch * NE;
+    const long long t0 = (long long)batch * NE;
     __syncthreads();
-    const int g = e0 + es;
-    const bool valid = act && g < ph.end;
-    const size_t qoff = (size_t)g * qs + b;
-    const size_t boff = (size_t)g * bs + b;
+    const long long ts = t0 + es;
+    const bool valid = act && ts < sl.n;
+    const int g = valid ? sl.elem(ph, ts) : ph.begin;
+    const size_t qoff = (size_t)g * qs + (valid ? sl.sub(ts, NQ, B) : 0) + (size_t)b * CS;
+    const size_t boff = (size_t)g * bs + (valid ? sl.sub(ts, 9, B) : 0) + (size_t)b * CS;
     float T[NQ], Th[9], Da[NA > 0 ? NA : 1];
     float v[9];
 #pragma unroll
@@ -134,18 +156,19 @@ __global__ void __launch_bounds__(SpCfg<O, M>::NT, 2) k_predict_sp(DevOps ops, D
     if (valid) {
       const float* q = st.Q + qoff;
 #pragma unroll
-      for (int r = 0; r < 9; ++r) v[r] = q[r * B];
+      for (int r = 0; r < 9; ++r) v[r] = q[r * RS];
 #pragma unroll
-      for (int r = 0; r < NA; ++r) Da[r] = q[(9 + r) * B];
+      for (int r = 0; r < NA; ++r) Da[r] = q[(9 + r) * RS];
     } else {
 #pragma unroll
       for (int r = 0; r < NA; ++r) Da[r] = 0.f;
     }
     for (int i = tid; i < NE * ED; i += NT) {
-      const int ee = i / ED, gg = e0 + ee;
-      sE[ee * EDP + i % ED] = (gg < ph.end) ? st.edata[(size_t)gg * ED + (i % ED)] : 0.f;
+      const int ee = i / ED;
+      const bool in = t0 + ee < sl.n;
+      sE[ee * EDP + i % ED] = in ? st.edata[(size_t)sl.elem(ph, t0 + ee) * ED + (i % ED)] : 0.f;
     }
-    if (tid < NE) sMeta[tid] = (e0 + tid < ph.end) ? st.meta[e0 + tid] : 0;
+    if (tid < NE) sMeta[tid] = (t0 + tid < sl.n) ? st.meta[sl.elem(ph, t0 + tid)] : 0;
     if (act) {
 #pragma unroll
       for (int r = 0; r < 9; ++r) sX[b * XP + col + r] = v[r];
@@ -211,20 +234,20 @@ __global__ void __launch_bounds__(SpCfg<O, M>::NT, 2) k_predict_sp(DevOps ops, D
     if (valid) {
       float* b1 = st.B1 + boff;
 #pragma unroll
-      for (int r = 0; r < 9; ++r) b1[r * B] = T[r];
+      for (int r = 0; r < 9; ++r) b1[r * RS] = T[r];
       if (meta & FLAG_FINER) {
         float* b2 = st.B2 + boff;
 #pragma unroll
-        for (int r = 0; r < 9; ++r) b2[r * B] = Th[r];
+        for (int r = 0; r < 9; ++r) b2[r * RS] = Th[r];
       }
       if (meta & FLAG_COARSER) {
         float* b3 = st.B3 + boff;
         if (ph.parity[cl] == 0) {
 #pragma unroll
-          for (int r = 0; r < 9; ++r) b3[r * B] = T[r];
+          for (int r = 0; r < 9; ++r) b3[r * RS] = T[r];
         } else {
 #pragma unroll
-          for (int r = 0; r < 9; ++r) b3[r * B] += T[r];
+          for (int r = 0; r < 9; ++r) b3[r * RS] += T[r];
         }
       }
     }
@@ -250,12 +273,12 @@ __global__ void __launch_bounds__(SpCfg<O, M>::NT, 2) k_predict_sp(DevOps ops, D
         for (int l = 0; l < M; ++l) coupling_add(V, T + 9 + 6 * l, ed[12 + 2 * l], ed[13 + 2 * l]);
         const float* q = st.Q + qoff;
 #pragma unroll
-        for (int r = 0; r < 9; ++r) acc[r] = q[r * B] + V[r];
+        for (int r = 0; r < 9; ++r) acc[r] = q[r * RS] + V[r];
 #pragma unroll
         for (int l = 0; l < M; ++l)
 #pragma unroll
           for (int r = 0; r < 6; ++r)
-            acc[9 + 6 * l + r] = q[(9 + 6 * l + r) * B] + ph.omega[l] * (-eps[r] - T[9 + 6 * l + r]);
+            acc[9 + 6 * l + r] = q[(9 + 6 * l + r) * RS] + ph.omega[l] * (-eps[r] - T[9 + 6 * l + r]);
       }
     }
     // ---- local surface kernel: interface states (v*, t*) of the face traces G_i, one task
@@ -292,15 +315,15 @@ __global__ void __launch_bounds__(SpCfg<O, M>::NT, 2) k_predict_sp(DevOps ops, D
       }
       float* q = st.Q + qoff;
 #pragma unroll
-      for (int r = 0; r < 9; ++r) q[r * B] = acc[r] + Sv[r];
+      for (int r = 0; r < 9; ++r) q[r * RS] = acc[r] + Sv[r];
       if constexpr (M > 0) {
 #pragma unroll
         for (int l = 0; l < M; ++l)
 #pragma unroll
-          for (int r = 0; r < 6; ++r) q[(9 + 6 * l + r) * B] = acc[9 + 6 * l + r] + ph.omega[l] * Sv[NS - 6 + r];
+          for (int r = 0; r < 6; ++r) q[(9 + 6 * l + r) * RS] = acc[9 + 6 * l + r] + ph.omega[l] * Sv[NS - 6 + r];
       }
     }
-    {
+    if constexpr (!FUSED) {
       const int bn = batch + gridDim.x;                    // this CTA's next batch
       if (bn < nbatch) {
         const int en = ph.begin + bn * NE;
@@ -357,7 +380,7 @@ __device__ __forceinline__ void sp_ntrace(int j, const float* x, float* y) {
   if constexpr (O == 3) ltssp::sp_ntrace_o3<XP>(j, x, y);
 }
 
-template <int O, int M, int NE_>
+template <int O, int M, int NE_, bool FUSED>
 __global__ void __launch_bounds__(SpnCfg<O, M, NE_>::NT, (NE_ == 8 ? 2 : 4))
     k_neighbour_sp(DevOps ops, DevState st, PhaseArgs ph) {
   using S = SpnCfg<O, M, NE_>;
@@ -383,25 +406,29 @@ __global__ void __launch_bounds__(SpnCfg<O, M, NE_>::NT, (NE_ == 8 ? 2 : 4))
   const int part = (tid >> 5) % S::NPART;                // projection row: as in k_predict_sp
   const int pair6 = ((tid >> 5) / S::NPART) * 32 + (tid & 31);
   const bool pact = pair6 < 6 * NE;
-  const int nelem = ph.end - ph.begin;
-  const int nbatch = (nelem + NE - 1) / NE;
-  constexpr long long qs = C::QS, bs = C::BUFS;
+  const Slots<FUSED> sl(st, ph);
+  const int nbatch = (int)((sl.n + NE - 1) / NE);
+  const long long qs = FUSED ? st.qs : C::QS, bs = FUSED ? st.bs : C::BUFS;
+  constexpr int RS = FUSED ? B * FUSED_GROUP : B;   // row stride of Q and the buffers
+  constexpr int CS = FUSED ? FUSED_GROUP : 1;       // mode stride
 
   for (int batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
-    const int e0 = ph.begin + batch * NE;
+    const long long t0 = (long long)batch * NE;
     __syncthreads();
     for (int i = tid; i < NE * ND; i += NT) {
-      const int ee = i / ND, gg = e0 + ee;
-      sD[ee * NDP + i % ND] = (gg < ph.end) ? __ldg(st.ndata + (size_t)gg * ND + (i % ND)) : 0.f;
+      const int ee = i / ND;
+      sD[ee * NDP + i % ND] = (t0 + ee < sl.n) ? __ldg(st.ndata + (size_t)sl.elem(ph, t0 + ee) * ND + (i % ND)) : 0.f;
     }
     for (int i = tid; i < NE * 9; i += NT) {
-      const int c = i % 9, gg = e0 + i / 9;
+      const int c = i % 9;
       int v = -1;
-      if (gg < ph.end)
+      if (t0 + i / 9 < sl.n) {
+        const int gg = sl.elem(ph, t0 + i / 9);
         v = (c < 4) ? __ldg(st.nbr + (size_t)gg * 4 + c) : (c < 8 ? __ldg(st.ncode + (size_t)gg * 4 + c - 4) : __ldg(st.meta + gg));
+      }
       sI[i] = v;
     }
-    {
+    if constexpr (!FUSED) {
       const int bn = batch + gridDim.x;
       if (bn < nbatch) {
         const int en = ph.begin + bn * NE;
@@ -414,7 +441,7 @@ __global__ void __launch_bounds__(SpnCfg<O, M, NE_>::NT, (NE_ == 8 ? 2 : 4))
     if (tid < 32) {
       const int fe = tid / 4, fi = tid % 4;
       int key = 5;                                      // lanes past the batch's face slots
-      if (tid < 4 * NE) key = (e0 + fe < ph.end && sI[fe * 9 + fi] >= 0) ? (sI[fe * 9 + 4 + fi] & 0xff) / 3 : 4;
+      if (tid < 4 * NE) key = (t0 + fe < sl.n && sI[fe * 9 + fi] >= 0) ? (sI[fe * 9 + 4 + fi] & 0xff) / 3 : 4;
       const unsigned lt = (1u << tid) - 1u;
       int base = 0, rank = 0;
 #pragma unroll
@@ -425,8 +452,10 @@ __global__ void __launch_bounds__(SpnCfg<O, M, NE_>::NT, (NE_ == 8 ? 2 : 4))
       }
       if (tid < 4 * NE) sPerm[rank] = tid;
     }
-    const int g = e0 + es;
-    const bool valid = act && g < ph.end;
+    const long long ts = t0 + es;
+    const bool valid = act && ts < sl.n;
+    const int g = valid ? sl.elem(ph, ts) : ph.begin;
+    const size_t bsub = valid ? sl.sub(ts, 9, B) : 0;    // this slot's simulation in the buffers
     // ---- gather the neighbours' time-integrated DOFs by cluster relation (Sec. V-B)
     if (act) {
       const int* ie = sI + es * 9;
@@ -439,12 +468,12 @@ __global__ void __launch_bounds__(SpnCfg<O, M, NE_>::NT, (NE_ == 8 ? 2 : 4))
         const int rel = (ie[4 + i] >> 8) & 0xff;
         const float* src1 = (rel == 1) ? st.B3 : ((rel == 2 && par == 0) ? st.B2 : st.B1);
         const bool sub = (rel == 2 && par == 1);
-        const size_t off = (size_t)(nb < 0 ? 0 : nb) * bs + b;
+        const size_t off = (size_t)(nb < 0 ? 0 : nb) * bs + bsub + (size_t)b * CS;
 #pragma unroll
-        for (int r = 0; r < 9; ++r) xv[i][r] = (nb < 0) ? 0.f : __ldg(src1 + off + r * B);
+        for (int r = 0; r < 9; ++r) xv[i][r] = (nb < 0) ? 0.f : __ldg(src1 + off + r * RS);
         if (sub) {
 #pragma unroll
-          for (int r = 0; r < 9; ++r) xv[i][r] -= __ldg(st.B2 + off + r * B);
+          for (int r = 0; r < 9; ++r) xv[i][r] -= __ldg(st.B2 + off + r * RS);
         }
       }
       float* xo = sX + b * XN + es * 36;
@@ -460,7 +489,7 @@ __global__ void __launch_bounds__(SpnCfg<O, M, NE_>::NT, (NE_ == 8 ? 2 : 4))
       if (tid < S::NROW) {
         const int slot = sPerm[tid / 9], fe = slot / 4, fi = slot % 4;
         row = slot * 9 + tid % 9;
-        if (e0 + fe < ph.end && sI[fe * 9 + fi] >= 0) j = (sI[fe * 9 + 4 + fi] & 0xff) / 3;
+        if (t0 + fe < sl.n && sI[fe * 9 + fi] >= 0) j = (sI[fe * 9 + 4 + fi] & 0xff) / 3;
       }
       sp_ntrace<O, XN>(j, sX + row, sG + row);
     }
@@ -471,7 +500,7 @@ __global__ void __launch_bounds__(SpnCfg<O, M, NE_>::NT, (NE_ == 8 ? 2 : 4))
     for (int t = tid; t < NE * 4 * F; t += NT) {
       const int fe = t / (4 * F), fi = (t / F) % 4, f = t % F;
       float w6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      if (e0 + fe < ph.end && sI[fe * 9 + fi] >= 0) {
+      if (t0 + fe < sl.n && sI[fe * 9 + fi] >= 0) {
         const int h = (sI[fe * 9 + 4 + fi] & 0xff) % 3;
         const int pf = face_degree(f), f0 = nface(pf), f1 = nface(pf + 1);
         const float* gp = sG + (fe * 4 + fi) * 9;
@@ -496,10 +525,10 @@ __global__ void __launch_bounds__(SpnCfg<O, M, NE_>::NT, (NE_ == 8 ? 2 : 4))
     __syncthreads();
     if (valid) {
       constexpr int NS = (M > 0) ? 15 : 9;
-      float* q = st.Q + (size_t)g * qs + b;
+      float* q = st.Q + (size_t)g * qs + sl.sub(ts, NQ, B) + (size_t)b * CS;
       float qv[NQ];
 #pragma unroll
-      for (int r = 0; r < NQ; ++r) qv[r] = q[r * B];
+      for (int r = 0; r < NQ; ++r) qv[r] = q[r * RS];
       float Sv[NS];
 #pragma unroll
       for (int r = 0; r < NS; ++r) Sv[r] = 0.f;
@@ -513,12 +542,12 @@ __global__ void __launch_bounds__(SpnCfg<O, M, NE_>::NT, (NE_ == 8 ? 2 : 4))
         flux_rows_add<NS>(W, nd + 4 + 11 * i, nd[0], nd[1], nd[2], Sv);
       }
 #pragma unroll
-      for (int r = 0; r < 9; ++r) q[r * B] = qv[r] + Sv[r];
+      for (int r = 0; r < 9; ++r) q[r * RS] = qv[r] + Sv[r];
       if constexpr (M > 0) {
 #pragma unroll
         for (int l = 0; l < M; ++l)
 #pragma unroll
-          for (int r = 0; r < 6; ++r) q[(9 + 6 * l + r) * B] = qv[9 + 6 * l + r] + ph.omega[l] * Sv[NS - 6 + r];
+          for (int r = 0; r < 6; ++r) q[(9 + 6 * l + r) * RS] = qv[9 + 6 * l + r] + ph.omega[l] * Sv[NS - 6 + r];
       }
     }
   }

@@ -23,7 +23,8 @@ struct Launchers {
                      long long wait_cycles, int suppress_commit, cudaStream_t);
   size_t smem_predict_tc;
   int blocks_predict_tc;
-  // predict + local kernel with generated sparse products (one simulation; else nullptr)
+  // predict + local kernel with generated sparse products (slots: elements, or (element,
+  // simulation) pairs of fused simulations)
   void (*predict_sp)(const DevOps&, const DevState&, const PhaseArgs&, int grid, cudaStream_t);
   size_t smem_predict_sp;
   int blocks_predict_sp, NE_SP, NT_SP;
@@ -82,20 +83,21 @@ struct Impl {
       // two fit the 512 tensor-memory columns)
       L->blocks_predict_tc = 2;
     }
-    if constexpr (FG == 1) {
-      e = smem_attrs(k_predict_sp<O, M>, L->smem_predict_sp, true);
+    {
+      constexpr bool FU = FG > 1;
+      e = smem_attrs(k_predict_sp<O, M, FU>, L->smem_predict_sp, true);
       if (e != cudaSuccess) return e;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L->blocks_predict_sp, k_predict_sp<O, M>, SpCfg<O, M>::NT,
-                                                        L->smem_predict_sp);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L->blocks_predict_sp, k_predict_sp<O, M, FU>,
+                                                        SpCfg<O, M>::NT, L->smem_predict_sp);
       if (e != cudaSuccess) return e;
-      e = smem_attrs(k_neighbour_sp<O, M, 8>, L->smem_neighbour_sp[0], true);
+      e = smem_attrs(k_neighbour_sp<O, M, 8, FU>, L->smem_neighbour_sp[0], true);
       if (e != cudaSuccess) return e;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L->blocks_neighbour_sp[0], k_neighbour_sp<O, M, 8>,
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L->blocks_neighbour_sp[0], k_neighbour_sp<O, M, 8, FU>,
                                                         SpnCfg<O, M, 8>::NT, L->smem_neighbour_sp[0]);
       if (e != cudaSuccess) return e;
-      e = smem_attrs(k_neighbour_sp<O, M, 4>, L->smem_neighbour_sp[1], true);
+      e = smem_attrs(k_neighbour_sp<O, M, 4, FU>, L->smem_neighbour_sp[1], true);
       if (e != cudaSuccess) return e;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L->blocks_neighbour_sp[1], k_neighbour_sp<O, M, 4>,
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L->blocks_neighbour_sp[1], k_neighbour_sp<O, M, 4, FU>,
                                                         SpnCfg<O, M, 4>::NT, L->smem_neighbour_sp[1]);
       if (e != cudaSuccess) return e;
     }
@@ -113,13 +115,12 @@ struct Impl {
     k_neighbour<O, M, FG><<<grid, C::NTN, C::N_TOTAL * sizeof(float), st>>>(o, s, p);
   }
   static void predict_sp(const DevOps& o, const DevState& s, const PhaseArgs& p, int grid, cudaStream_t st) {
-    if constexpr (FG == 1)
-      k_predict_sp<O, M><<<grid, SpCfg<O, M>::NT, SpCfg<O, M>::TOTAL * sizeof(float), st>>>(o, s, p);
+    k_predict_sp<O, M, (FG > 1)><<<grid, SpCfg<O, M>::NT, SpCfg<O, M>::TOTAL * sizeof(float), st>>>(o, s, p);
   }
   template <int NE>
   static void neighbour_sp(const DevOps& o, const DevState& s, const PhaseArgs& p, int grid, cudaStream_t st) {
-    if constexpr (FG == 1)
-      k_neighbour_sp<O, M, NE><<<grid, SpnCfg<O, M, NE>::NT, SpnCfg<O, M, NE>::TOTAL * sizeof(float), st>>>(o, s, p);
+    k_neighbour_sp<O, M, NE, (FG > 1)>
+        <<<grid, SpnCfg<O, M, NE>::NT, SpnCfg<O, M, NE>::TOTAL * sizeof(float), st>>>(o, s, p);
   }
   static void predict_tc(const DevOps& o, const DevState& s, const PhaseArgs& p, int grid, int passes, int* err,
                          long long wait_cycles, int suppress_commit, cudaStream_t st) {
@@ -188,7 +189,7 @@ struct Impl {
       L.predict_tc = &predict_tc;
       L.smem_predict_tc = TcCfg<O, M, FG>::SMEM_BYTES;
     }
-    if constexpr (FG == 1) {
+    {
       L.predict_sp = &predict_sp;
       L.smem_predict_sp = SpCfg<O, M>::TOTAL * sizeof(float);
       L.NE_SP = SpCfg<O, M>::NE;

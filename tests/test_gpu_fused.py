@@ -87,14 +87,17 @@ def test_fused_lts_matches_oracle_per_simulation(order, n_mech, F):
                     assert np.sum((vg[:, q] - vo[:, q]) ** 2) / den <= 1e-8, (f, q)
 
 
-def test_fused_equals_single_simulation_runs_and_energy_sums():
-    """The fused run against F single-simulation GPU runs with the same inputs: same
-    arithmetic per simulation, so agreement to FP32 rounding; energies add up."""
+@pytest.mark.parametrize("engine", ["sparse", "fp32"])
+def test_fused_equals_single_simulation_runs_and_energy_sums(engine):
+    """The fused run against F single-simulation GPU runs with the same inputs and engine:
+    same arithmetic per simulation, so agreement to FP32 rounding (the sparse engine's
+    kernels take (element, simulation) slots and are bitwise equal); energies add up."""
     m, mat = _case(seed=33)
     F, order, n_mech = 8, 5, 3
     K = m["tet"].shape[0]
     pos, m6, f0, d0 = _inputs(m, F, 27, 35, seed=90)
     g = _fused_solver(order, n_mech, m, mat, F)
+    g.set_contraction(engine)
     for f in range(F):
         g.add_point_source(pos[f], m6[f], f0[f], 0.1, 1e12, fused_idx=f)
     g.setup_clusters(2, 0.5)
@@ -105,7 +108,7 @@ def test_fused_equals_single_simulation_runs_and_energy_sums():
     e_sum = 0.0
     for f in range(F):
         s, _, _ = make_pair(order, n_mech, m, mat)
-        s.set_contraction("fp32")     # the kernels a fused handle runs
+        s.set_contraction(engine)
         s.add_point_source(pos[f], m6[f], f0[f], 0.1, 1e12)
         s.setup_clusters(2, 0.5)
         s.set_dofs(d0[f])
@@ -114,6 +117,8 @@ def test_fused_equals_single_simulation_runs_and_energy_sums():
         e_sum += s.energy()
         den = np.sqrt(np.sum(one ** 2))
         assert np.sqrt(np.sum((got[f] - one) ** 2)) / den <= 1e-6, f
+        if engine == "sparse":
+            assert np.array_equal(got[f], one), f
         s.close()
     assert abs(e_fused / e_sum - 1.0) < 1e-9
 
@@ -153,7 +158,6 @@ def test_maximum_fused_count():
     assert np.all(np.isfinite(got))
     for f in (0, 1, 31, 62, 63):
         s, _, _ = make_pair(order, n_mech, m, mat)
-        s.set_contraction("fp32")     # the kernels a fused handle runs
         s.add_point_source(pos[f], m6[f], f0[f], 0.1, 1e12)
         s.setup_clusters(2, 0.5)
         s.set_dofs(d0[f])

@@ -119,6 +119,7 @@ def test_fused_partitioned_run_equals_fused_unpartitioned(F):
     runs, xbytes = [], []
     for parted in (False, True):
         g = binding.Solver(order, n_mech, device=0, n_fused=F)
+        g.set_contraction("fp32")
         g.set_mesh(m["xyz"], m["tet"], m["face_bc"])
         g.set_material(mat["rho"], mat["vp"], mat["vs"], mat["qp"], mat["qs"], 0.1, 5.0)
         for f in range(F):

@@ -130,13 +130,38 @@ def test_sparse_engine_repeatable_bitwise():
     assert np.array_equal(outs[0], outs[1])
 
 
-def test_fused_handle_rejects_sparse_engine():
+def test_fused_sparse_engine_matches_oracle_per_simulation():
+    """Four and eight fused simulations on the sparse engine ((element, simulation) slots),
+    each with its own source and initial state, against its own oracle run (3 clusters)."""
+    m = synth.graded_box(4, 4, 3, 250.0, 125.0, seed=33)
+    mat = synth.random_layers(m, n_layers=3, seed=6)
+    K = m["tet"].shape[0]
     from paper_2202_10313_gb300 import binding
-    m = synth.graded_box(2, 2, 2, 200.0, 100.0, seed=1)
-    g = binding.Solver(5, 3, device=0, n_fused=4)
-    g.set_mesh(m["xyz"], m["tet"], m["face_bc"])
-    with pytest.raises(RuntimeError):
+    for order, F in ((5, 4), (4, 8)):
+        nb = order * (order + 1) * (order + 2) // 6
+        d0 = np.stack([synth.random_dofs(K, 27, nb, seed=70 + f) for f in range(F)])
+        lo, hi = m["xyz"].min(axis=0), m["xyz"].max(axis=0)
+        pos, m6, f0 = synth.random_sources(F, lo + 0.2 * (hi - lo), hi - 0.2 * (hi - lo), f0_range=(4.0, 8.0), seed=5)
+        g = binding.Solver(order, 3, device=0, n_fused=F)
+        g.set_mesh(m["xyz"], m["tet"], m["face_bc"])
+        g.set_material(mat["rho"], mat["vp"], mat["vs"], mat["qp"], mat["qs"], 0.1, 5.0)
         g.set_contraction("sparse")
+        for f in range(F):
+            g.add_point_source(pos[f], m6[f], f0[f], 0.1, 1e12, fused_idx=f)
+        cl, _, _ = g.setup_clusters(3, 0.5)
+        g.set_dofs(d0)
+        g.advance_steps(8)
+        got = g.get_dofs()
+        for f in (0, F - 1):
+            _, ora, _ = make_pair(order, 3, m, mat)
+            ora.add_point_source(pos[f], m6[f], f0[f], 0.1, 1e12)
+            ora.setup_clusters(3, 0.5)
+            assert np.array_equal(cl, ora.clusters)
+            ora.Q = d0[f].copy()
+            ora.run_lts(8)
+            report_parity("sparse engine, fused %d, O%d, simulation %d" % (F, order, f),
+                          check_parity(got[f], ora.Q, 27, TOL))
+        g.close()
 
 
 def test_neighbour_tile_variants_bitwise_equal():
