@@ -124,10 +124,13 @@ __global__ void __launch_bounds__(SpCfg<O, M>::NT, 2) k_predict_sp(DevOps ops, D
   int* sMeta = reinterpret_cast<int*>(smem + S::S_META);
   const int tid = threadIdx.x;
 
-  // column task (element, mode), modes fastest: a warp spans at most two elements
+  // column task (slot, mode). One simulation: modes fastest (a warp spans at most two
+  // elements, and reads a row's consecutive modes). Fused simulations: slots fastest, so that
+  // the simulations of an element, innermost in the simulation-blocked layout, are in
+  // neighbouring lanes and the DOF accesses coalesce.
   const bool act = tid < NE * B;
-  const int es = act ? tid / B : 0;
-  const int b = act ? tid % B : 0;
+  const int es = act ? (FUSED ? tid % NE : tid / B) : 0;
+  const int b = act ? (FUSED ? tid / NE : tid % B) : 0;
   // row task (part, pair): warp w takes part w mod NPART, so that the warps an SM
   // sub-partition runs (w mod 4) all execute the same part's straight-line code and its
   // instruction cache holds one part only
@@ -399,9 +402,9 @@ __global__ void __launch_bounds__(SpnCfg<O, M, NE_>::NT, (NE_ == 8 ? 2 : 4))
   const int tid = threadIdx.x;
   for (int i = tid; i < 3 * F * F; i += NT) sR[i] = ops.Rh[i];
 
-  const bool act = tid < NE * B;                         // column task (element, mode)
-  const int es = act ? tid / B : 0;
-  const int b = act ? tid % B : 0;
+  const bool act = tid < NE * B;                         // column task (slot, mode), as in k_predict_sp
+  const int es = act ? (FUSED ? tid % NE : tid / B) : 0;
+  const int b = act ? (FUSED ? tid / NE : tid % B) : 0;
 
   const int part = (tid >> 5) % S::NPART;                // projection row: as in k_predict_sp
   const int pair6 = ((tid >> 5) / S::NPART) * 32 + (tid & 31);
