@@ -14,7 +14,7 @@ tetrahedra of the same generator, F simulations (a multiple of 4), each driven b
 moment-tensor Ricker source (seeded random positions and orientations, f0 in [1, 4] Hz);
 the metric is then simulation element updates per second.
 
---impl reference times the FP64 CPU oracle (the only reference there is) on the box's
+--impl reference times the FP64 CPU oracle (the only reference there is) on the machine's
 host cores on a bounded sample of the same workload.
 """
 import argparse

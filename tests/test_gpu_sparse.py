@@ -181,3 +181,35 @@ def test_neighbour_tile_variants_bitwise_equal():
             gpu.advance_steps(8)
             outs.append(gpu.get_dofs())
         assert np.array_equal(outs[0], outs[1])
+
+
+def test_sparse_engine_empty_clusters_and_periodic_gts():
+    """Degenerate schedules on the sparse engine: a homogeneous mesh with 4 clusters requested
+    (the lambda search leaves some empty, so some phases have no element), and global time
+    stepping on a periodic cube (every face has a neighbour, some across the box)."""
+    m = synth.graded_box(3, 3, 2, 200.0, 200.0, grade=1.0, jitter=0.0, seed=1)
+    K = m["tet"].shape[0]
+    gpu, ora, _ = make_pair(4, 3, m, dict(synth.homogeneous(K), qp=np.full(K, 80.0), qs=np.full(K, 40.0)))
+    gpu.set_contraction("sparse")
+    cl, _, _ = gpu.setup_clusters(4, 0.5)
+    ora.setup_clusters(4, 0.5)
+    assert np.array_equal(cl, ora.clusters) and len(np.unique(cl)) < 4
+    d = synth.random_dofs(K, 27, 20, seed=4)
+    gpu.set_dofs(d)
+    ora.Q = d.copy()
+    gpu.advance_steps(8)
+    ora.run_lts(8)
+    check_parity(gpu.get_dofs(), ora.Q, 27, TOL)
+    m = synth.permute_vertex_order(synth.periodic_cube(4), seed=7)
+    K = m["tet"].shape[0]
+    gpu, ora, _ = make_pair(5, 3, m, dict(synth.homogeneous(K), qp=np.full(K, 80.0), qs=np.full(K, 40.0)),
+                            500.0, 20000.0)
+    gpu.set_contraction("sparse")
+    gpu.setup_clusters(1, 0.5)
+    d = synth.random_dofs(K, 27, 35, seed=3)
+    gpu.set_dofs(d)
+    ora.Q = d.copy()
+    gpu.advance_steps(20)
+    ora.run_gts(ora.time_step_gts(0.5), 20)
+    report_parity("sparse engine: periodic cube, O5, 3 mechanisms, GTS, 20 steps",
+                  check_parity(gpu.get_dofs(), ora.Q, 27, TOL))
