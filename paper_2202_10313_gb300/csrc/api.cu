@@ -1397,6 +1397,7 @@ int lts_set_mesh(lts_t* h, int64_t n_vert, const double* xyz, int64_t n_tet, con
   return run(h, [&] {
     if (n_vert <= 0 || n_tet <= 0 || !xyz || !tet || !face_bc) fail(LTS_ERR_ARG, "bad mesh arguments");
     if (n_tet > (int64_t(1) << 30)) fail(LTS_ERR_ARG, "too many elements");
+    if (n_tet * h->nsim > INT32_MAX) fail(LTS_ERR_ARG, "too many (element, simulation) slots");
     lts::Mesh m;
     m.nv = n_vert;
     m.K = n_tet;

@@ -65,8 +65,8 @@ struct SpCfg {
   static_assert(S_P + 4 * B * XP <= S_G + 4 * F * XP, "P_i overlays Y and G");
   static constexpr int S_W = rup(S_G + 4 * F * XP, 4); // [4 F][XP]        interface states, 6 rows
   static constexpr int S_E = rup(S_W + 4 * F * XP, 4);
-  static constexpr int S_META = rup(S_E + NE * EDP, 4);
-  static constexpr int TOTAL = rup(S_META + NE, 4);
+  static constexpr int S_META = rup(S_E + NE * EDP, 4);  // [3][NE] ints: meta, element, simulation
+  static constexpr int TOTAL = rup(S_META + 3 * NE, 4);
 };
 
 // the generated products of order O
@@ -93,18 +93,28 @@ __device__ __forceinline__ void sp_proj(int part, const float* x, float* y) {
 // (element, simulation), the simulations of an element consecutive, simulation f of element
 // k at k * (element stride) + (f / G) * (rows x B x G) + (row x B + mode) x G + f mod G in the
 // simulation-blocked layout (G = FUSED_GROUP). The per-slot arithmetic is the same either way.
+// Slot counts fit 32 bits (checked when the mesh is set). Fused kernels decode a batch's
+// slots once (one division each, by the first NE threads) into shared memory.
 template <bool FUSED>
 struct Slots {
   int nsim;
-  long long n;                                  // slots in the phase
+  int n;                                        // slots in the phase
   __device__ Slots(const DevState& st, const PhaseArgs& ph)
-      : nsim(FUSED ? st.nsim : 1), n((long long)(ph.end - ph.begin) * (FUSED ? st.nsim : 1)) {}
-  __device__ int elem(const PhaseArgs& ph, long long t) const { return ph.begin + (int)(t / nsim); }
-  // offset of (slot t, row 0, mode 0) from its element's start in an array of `rows` rows
-  __device__ size_t sub(long long t, int rows, int B) const {
+      : nsim(FUSED ? st.nsim : 1), n((ph.end - ph.begin) * (FUSED ? st.nsim : 1)) {}
+  // element (offset from the phase's first) and simulation of slot t < n
+  __device__ void decode(int t, int& e, int& f) const {
+    if (!FUSED) {
+      e = t;
+      f = 0;
+    } else {
+      e = (int)((unsigned)t / (unsigned)nsim);
+      f = t - e * nsim;
+    }
+  }
+  // offset of (simulation f, row 0, mode 0) from its element's start in an array of `rows` rows
+  __device__ static int sub(int f, int rows, int B) {
     if (!FUSED) return 0;
-    const int f = (int)(t % nsim);
-    return (size_t)(f / FUSED_GROUP) * rows * B * FUSED_GROUP + f % FUSED_GROUP;
+    return (int)((unsigned)f / FUSED_GROUP) * rows * B * FUSED_GROUP + (int)((unsigned)f % FUSED_GROUP);
   }
 };
 
@@ -122,6 +132,7 @@ __global__ void __launch_bounds__(SpCfg<O, M>::NT, 2) k_predict_sp(DevOps ops, D
   float* sW = smem + S::S_W;
   float* sE = smem + S::S_E;
   int* sMeta = reinterpret_cast<int*>(smem + S::S_META);
+  int* sSlot = sMeta + NE;                    // fused: [2][NE] element, simulation of the batch's slots
   const int tid = threadIdx.x;
 
   // column task (slot, mode). One simulation: modes fastest (a warp spans at most two
@@ -138,20 +149,30 @@ __global__ void __launch_bounds__(SpCfg<O, M>::NT, 2) k_predict_sp(DevOps ops, D
   const bool ract = pair < S::NPAIR;          // (element, quantity) rows of the 9 elastic rows
   const bool pact = pair < 6 * NE;            // (element, interface-state) rows of the projection
   const Slots<FUSED> sl(st, ph);
-  const int nbatch = (int)((sl.n + NE - 1) / NE);
+  const int nbatch = (sl.n + NE - 1) / NE;
   const long long qs = FUSED ? st.qs : C::QS, bs = FUSED ? st.bs : C::BUFS;
   constexpr int RS = FUSED ? B * FUSED_GROUP : B;   // row stride of Q and the buffers
   constexpr int CS = FUSED ? FUSED_GROUP : 1;       // mode stride
   const int col = es * 9;                     // this column's pair offset
 
   for (int batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
-    const long long t0 = (long long)batch * NE;
+    const int t0 = batch * NE;
+    // element of the batch's slot k (fused: decoded below; every read of sSlot comes before
+    // the batch's second barrier, every write before its first)
+    auto elem_of = [&](int k) { return FUSED ? sSlot[k] : ph.begin + t0 + k; };
+    if (FUSED && tid < NE) {
+      int e = 0, f = 0;
+      if (t0 + tid < sl.n) sl.decode(t0 + tid, e, f);
+      sSlot[tid] = ph.begin + e;
+      sSlot[NE + tid] = f;
+    }
     __syncthreads();
-    const long long ts = t0 + es;
+    const int ts = t0 + es;
     const bool valid = act && ts < sl.n;
-    const int g = valid ? sl.elem(ph, ts) : ph.begin;
-    const size_t qoff = (size_t)g * qs + (valid ? sl.sub(ts, NQ, B) : 0) + (size_t)b * CS;
-    const size_t boff = (size_t)g * bs + (valid ? sl.sub(ts, 9, B) : 0) + (size_t)b * CS;
+    const int g = valid ? elem_of(es) : ph.begin;
+    const int fs = (FUSED && valid) ? sSlot[NE + es] : 0;
+    const size_t qoff = (size_t)g * qs + Slots<FUSED>::sub(fs, NQ, B) + (size_t)b * CS;
+    const size_t boff = (size_t)g * bs + Slots<FUSED>::sub(fs, 9, B) + (size_t)b * CS;
     float T[NQ], Th[9], Da[NA > 0 ? NA : 1];
     float v[9];
 #pragma unroll
@@ -169,9 +190,9 @@ __global__ void __launch_bounds__(SpCfg<O, M>::NT, 2) k_predict_sp(DevOps ops, D
     for (int i = tid; i < NE * ED; i += NT) {
       const int ee = i / ED;
       const bool in = t0 + ee < sl.n;
-      sE[ee * EDP + i % ED] = in ? st.edata[(size_t)sl.elem(ph, t0 + ee) * ED + (i % ED)] : 0.f;
+      sE[ee * EDP + i % ED] = in ? st.edata[(size_t)elem_of(ee) * ED + (i % ED)] : 0.f;
     }
-    if (tid < NE) sMeta[tid] = (t0 + tid < sl.n) ? st.meta[sl.elem(ph, t0 + tid)] : 0;
+    if (tid < NE) sMeta[tid] = (t0 + tid < sl.n) ? st.meta[elem_of(tid)] : 0;
     if (act) {
 #pragma unroll
       for (int r = 0; r < 9; ++r) sX[b * XP + col + r] = v[r];
@@ -372,7 +393,8 @@ struct SpnCfg {
   static constexpr int S_D = rup(S_R + 3 * F * F, 4);                                // [NE][NDP]
   static constexpr int S_I = rup(S_D + NE * NDP, 4);                                 // [NE][9] ints
   static constexpr int S_PERM = rup(S_I + NE * 9, 4);                                // [4 NE] ints
-  static constexpr int TOTAL = rup(S_PERM + 4 * NE, 4);
+  static constexpr int S_SLOT = rup(S_PERM + 4 * NE, 4);                             // [2][NE] ints
+  static constexpr int TOTAL = rup(S_SLOT + 2 * NE, 4);
   static_assert(4 * NE <= 32, "one warp sorts the face slots of a batch");
 };
 
@@ -399,6 +421,7 @@ __global__ void __launch_bounds__(SpnCfg<O, M, NE_>::NT, (NE_ == 8 ? 2 : 4))
   float* sD = smem + S::S_D;
   int* sI = reinterpret_cast<int*>(smem + S::S_I);      // per element: nbr[4], code[4], meta
   int* sPerm = reinterpret_cast<int*>(smem + S::S_PERM); // face slots ordered by the neighbour's face j
+  int* sSlot = reinterpret_cast<int*>(smem + S::S_SLOT); // fused: element, simulation of the batch's slots
   const int tid = threadIdx.x;
   for (int i = tid; i < 3 * F * F; i += NT) sR[i] = ops.Rh[i];
 
@@ -410,23 +433,31 @@ __global__ void __launch_bounds__(SpnCfg<O, M, NE_>::NT, (NE_ == 8 ? 2 : 4))
   const int pair6 = ((tid >> 5) / S::NPART) * 32 + (tid & 31);
   const bool pact = pair6 < 6 * NE;
   const Slots<FUSED> sl(st, ph);
-  const int nbatch = (int)((sl.n + NE - 1) / NE);
+  const int nbatch = (sl.n + NE - 1) / NE;
   const long long qs = FUSED ? st.qs : C::QS, bs = FUSED ? st.bs : C::BUFS;
   constexpr int RS = FUSED ? B * FUSED_GROUP : B;   // row stride of Q and the buffers
   constexpr int CS = FUSED ? FUSED_GROUP : 1;       // mode stride
 
   for (int batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
-    const long long t0 = (long long)batch * NE;
+    const int t0 = batch * NE;
+    // element of the batch's slot k, as in k_predict_sp
+    auto elem_of = [&](int k) { return FUSED ? sSlot[k] : ph.begin + t0 + k; };
+    if (FUSED && tid < NE) {
+      int e = 0, f = 0;
+      if (t0 + tid < sl.n) sl.decode(t0 + tid, e, f);
+      sSlot[tid] = ph.begin + e;
+      sSlot[NE + tid] = f;
+    }
     __syncthreads();
     for (int i = tid; i < NE * ND; i += NT) {
       const int ee = i / ND;
-      sD[ee * NDP + i % ND] = (t0 + ee < sl.n) ? __ldg(st.ndata + (size_t)sl.elem(ph, t0 + ee) * ND + (i % ND)) : 0.f;
+      sD[ee * NDP + i % ND] = (t0 + ee < sl.n) ? __ldg(st.ndata + (size_t)elem_of(ee) * ND + (i % ND)) : 0.f;
     }
     for (int i = tid; i < NE * 9; i += NT) {
       const int c = i % 9;
       int v = -1;
       if (t0 + i / 9 < sl.n) {
-        const int gg = sl.elem(ph, t0 + i / 9);
+        const int gg = elem_of(i / 9);
         v = (c < 4) ? __ldg(st.nbr + (size_t)gg * 4 + c) : (c < 8 ? __ldg(st.ncode + (size_t)gg * 4 + c - 4) : __ldg(st.meta + gg));
       }
       sI[i] = v;
@@ -455,10 +486,11 @@ __global__ void __launch_bounds__(SpnCfg<O, M, NE_>::NT, (NE_ == 8 ? 2 : 4))
       }
       if (tid < 4 * NE) sPerm[rank] = tid;
     }
-    const long long ts = t0 + es;
+    const int ts = t0 + es;
     const bool valid = act && ts < sl.n;
-    const int g = valid ? sl.elem(ph, ts) : ph.begin;
-    const size_t bsub = valid ? sl.sub(ts, 9, B) : 0;    // this slot's simulation in the buffers
+    const int g = valid ? elem_of(es) : ph.begin;
+    const int fs = (FUSED && valid) ? sSlot[NE + es] : 0;
+    const size_t bsub = Slots<FUSED>::sub(fs, 9, B);    // this slot's simulation in the buffers
     // ---- gather the neighbours' time-integrated DOFs by cluster relation (Sec. V-B)
     if (act) {
       const int* ie = sI + es * 9;
@@ -528,7 +560,7 @@ __global__ void __launch_bounds__(SpnCfg<O, M, NE_>::NT, (NE_ == 8 ? 2 : 4))
     __syncthreads();
     if (valid) {
       constexpr int NS = (M > 0) ? 15 : 9;
-      float* q = st.Q + (size_t)g * qs + sl.sub(ts, NQ, B) + (size_t)b * CS;
+      float* q = st.Q + (size_t)g * qs + Slots<FUSED>::sub(fs, NQ, B) + (size_t)b * CS;
       float qv[NQ];
 #pragma unroll
       for (int r = 0; r < NQ; ++r) qv[r] = q[r * RS];
