@@ -131,21 +131,6 @@ struct AdjLtsArgs {
   int nsim, G;
 };
 
-// y += S x (TR = false) or y += S^T x (TR = true) for an elastic star matrix S (row-major
-// [out][in]). It couples the six stresses only to the three velocities and the velocities
-// only to the stresses, so its other 45 entries are zero and skipped.
-template <bool TR>
-__device__ __forceinline__ void star_acc(const float* S, const float x[9], float y[9]) {
-#pragma unroll
-  for (int r = 0; r < 6; ++r)
-#pragma unroll
-    for (int s = 6; s < 9; ++s) y[r] = fmaf(TR ? S[s * 9 + r] : S[r * 9 + s], x[s], y[r]);
-#pragma unroll
-  for (int r = 6; r < 9; ++r)
-#pragma unroll
-    for (int s = 0; s < 6; ++s) y[r] = fmaf(TR ? S[s * 9 + r] : S[r * 9 + s], x[s], y[r]);
-}
-
 // dst[q] = src[q] for q < N by a CTA of NT threads: every load is issued before the first
 // store, so the element's copies are in flight together.
 template <int N, int NT>
@@ -155,19 +140,6 @@ __device__ __forceinline__ void stage(float* dst, const float* __restrict__ src,
 #pragma unroll
   for (int j = 0; j < R; ++j)
     if (t + j * NT < N) v[j] = __ldg(src + t + j * NT);
-#pragma unroll
-  for (int j = 0; j < R; ++j)
-    if (t + j * NT < N) dst[t + j * NT] = v[j];
-}
-
-// dst[q] = src[q G] for q < N (one simulation of a fused block), loads issued first.
-template <int N, int NT>
-__device__ __forceinline__ void stage_strided(float* dst, const float* __restrict__ src, int G, int t) {
-  constexpr int R = (N + NT - 1) / NT;
-  float v[R];
-#pragma unroll
-  for (int j = 0; j < R; ++j)
-    if (t + j * NT < N) v[j] = __ldg(src + (size_t)(t + j * NT) * G);
 #pragma unroll
   for (int j = 0; j < R; ++j)
     if (t + j * NT < N) dst[t + j * NT] = v[j];
@@ -190,16 +162,120 @@ __device__ __forceinline__ void tile33(const float* X, const float* Y, int r0, i
   }
 }
 
+// acc[i][q] += sum_{j < n} X[(r0 + i) * LD + j] * Y[(s0 + q) * LD + j] for a 3 x 3 tile, four
+// j at a time (LD and n multiples of 4, X and Y 16-byte aligned; entries j >= the true length
+// are zero on one side at least).
+template <int LD>
+__device__ __forceinline__ void tile33v(const float* X, const float* Y, int r0, int s0, int n, float acc[3][3]) {
+#pragma unroll 1
+  for (int j = 0; j < n; j += 4) {
+    float4 x[3], y[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      x[i] = *reinterpret_cast<const float4*>(X + (r0 + i) * LD + j);
+      y[i] = *reinterpret_cast<const float4*>(Y + (s0 + i) * LD + j);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        acc[i][q] = fmaf(x[i].x, y[q].x, acc[i][q]);
+        acc[i][q] = fmaf(x[i].y, y[q].y, acc[i][q]);
+        acc[i][q] = fmaf(x[i].z, y[q].z, acc[i][q]);
+        acc[i][q] = fmaf(x[i].w, y[q].w, acc[i][q]);
+      }
+  }
+}
+
+// The nine rows of a [9][LD] block, entries j .. j + 3 (16-byte aligned; the same address in
+// every lane, so each load is one broadcast).
+template <int LD>
+__device__ __forceinline__ void load_cols4(const float* src, int j, float4 x[9]) {
+#pragma unroll
+  for (int r = 0; r < 9; ++r) x[r] = *reinterpret_cast<const float4*>(src + r * LD + j);
+}
+__device__ __forceinline__ float lane4(const float4& v, int u) { return u == 0 ? v.x : u == 1 ? v.y : u == 2 ? v.z : v.w; }
+
+// v[r] = sum_{j < N} src[r * LD + j] * tab[j * ts + t] for the 9 rows r, the broadcast
+// operand four entries at a time (N, LD multiples of 4; pad entries zero on one side).
+template <int N, int LD>
+__device__ __forceinline__ void rows9v(const float* src, const float* tab, int ts, int t, float v[9]) {
+#pragma unroll
+  for (int r = 0; r < 9; ++r) v[r] = 0.f;
+#pragma unroll 1
+  for (int j = 0; j < N; j += 4) {
+    float4 x[9];
+    load_cols4<LD>(src, j, x);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float w = tab[(j + u) * ts + t];
+#pragma unroll
+      for (int r = 0; r < 9; ++r) v[r] = fmaf(lane4(x[r], u), w, v[r]);
+    }
+  }
+}
+
+// Elastic star matrix S_c (row-major [out][in]) in compact form: it couples the six stresses
+// only to the three velocities and back, so only the 6 x 3 block S[r][6 + s] (row-major, 18
+// entries) and the 3 x 6 block S[6 + r][s] (18 entries) are kept, 36 floats per c.
+__device__ __forceinline__ int star_compact_index(int x) {
+  return x < 18 ? (x / 3) * 9 + 6 + x % 3 : (6 + (x - 18) / 6) * 9 + (x - 18) % 6;
+}
+// y += S x (TR = false) or y += S^T x (TR = true), S in compact form (16-byte aligned).
+template <bool TR>
+__device__ __forceinline__ void star_acc(const float* Sc, const float x[9], float y[9]) {
+  float e[36];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const float4 v = reinterpret_cast<const float4*>(Sc)[i];
+    e[4 * i] = v.x;
+    e[4 * i + 1] = v.y;
+    e[4 * i + 2] = v.z;
+    e[4 * i + 3] = v.w;
+  }
+  if (!TR) {
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+      for (int s = 0; s < 3; ++s) y[r] = fmaf(e[r * 3 + s], x[6 + s], y[r]);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int s = 0; s < 6; ++s) y[6 + r] = fmaf(e[18 + r * 6 + s], x[s], y[6 + r]);
+  } else {
+#pragma unroll
+    for (int s = 0; s < 3; ++s)
+#pragma unroll
+      for (int r = 0; r < 6; ++r) y[6 + s] = fmaf(e[r * 3 + s], x[r], y[6 + s]);
+#pragma unroll
+    for (int s = 0; s < 6; ++s)
+#pragma unroll
+      for (int r = 0; r < 3; ++r) y[s] = fmaf(e[18 + r * 6 + s], x[6 + r], y[s]);
+  }
+}
+
+// Polynomial degree of volume mode j (modes are ordered by degree).
+__device__ __forceinline__ int mode_degree(int j) {
+  int p = 0;
+  while (nbasis(p + 1) <= j) ++p;
+  return p;
+}
+
 // Shared-memory plan of k_adj_pred, a persistent kernel: the operator tables (K_c^T, K_c,
 // F~_i, F^_i^T, F~_i^T) once per CTA, then one region per element group. A group is one warp
 // (orders 3-4) or two (order 5) and takes the CTA's elements in turn; G groups fill the
 // shared memory (at most 128 registers a thread, 15 named barriers for two-warp groups).
+// Mode rows are padded to BP = rup(B, 4) and face-mode rows to FP = rup(F, 4), the pad entries
+// zero (table rows past B or F zero as well), so that every contraction reads its broadcast
+// operand four entries at a time.
 template <int O>
 struct AdjPredCfg {
-  static constexpr int B = nbasis(O), F = nface(O), NB9 = 9 * B, NT = AdjNT<O>::value;
-  static constexpr int NSCR = (3 * NB9 > 108 * F) ? 3 * NB9 : 108 * F;
-  static constexpr int ELEM = rup(AM_SIZE + (4 + O) * NB9 + NSCR, 4);   // sM, sL, sT, sG[2], sD[O], scratch
-  static constexpr int TAB = rup(6 * B * B + 12 * B * F, 4);
+  static constexpr int B = nbasis(O), F = nface(O), NT = AdjNT<O>::value;
+  static constexpr int BP = rup(B, 4), FP = rup(F, 4), NB9 = 9 * BP;
+  static constexpr int NSTAR = 3 * 36, NALOC = 4 * 9 * 12;       // compact S_c; A-_i rows padded to 12
+  static constexpr int NSCR = (3 * NB9 > 27 * 4 * FP) ? 3 * NB9 : 27 * 4 * FP;
+  static constexpr int ELEM = NSTAR + NALOC + (4 + O) * NB9 + NSCR;   // sS, sA, sL, sT, sG[2], sD[O], scratch
+  static constexpr int TAB = 6 * BP * B + 8 * BP * F + 4 * FP * B;
   static constexpr int G_SMEM = (227 * 1024 / 4 - TAB) / ELEM;
   static constexpr int G_REG = 65536 / (128 * NT);
   static constexpr int G_BAR = (NT == 32) ? 32 : 15;
@@ -208,6 +284,7 @@ struct AdjPredCfg {
   static constexpr int THREADS = G * NT;
   static constexpr int SMEM_BYTES = 4 * (TAB + G * ELEM);
   static_assert(G >= 1 && SMEM_BYTES <= 227 * 1024, "k_adj_pred shared-memory plan");
+  static_assert(TAB % 4 == 0 && ELEM % 4 == 0 && NB9 % 4 == 0, "16-byte aligned regions");
 };
 
 // Barrier of one element group: the warp itself, or a named barrier over its two warps.
@@ -219,16 +296,19 @@ __device__ __forceinline__ void gsync(int g) {
     asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "n"(NT) : "memory");
 }
 
-// rows9 with the table in shared memory.
-template <int N, int LD>
-__device__ __forceinline__ void rows9s(const float* src, const float* tab, int ts, int t, float v[9]) {
+// dst[(q / B) BP + q % B] = src[q G] for q < 9 B: a [9][B] block (stride G between entries)
+// into the padded [9][BP] layout, every load issued before the first store.
+template <int B, int BP, int NT>
+__device__ __forceinline__ void stage_pad(float* dst, const float* __restrict__ src, int G, int t) {
+  constexpr int N = 9 * B, R = (N + NT - 1) / NT;
+  float v[R];
 #pragma unroll
-  for (int r = 0; r < 9; ++r) v[r] = 0.f;
-#pragma unroll 4
-  for (int j = 0; j < N; ++j) {
-    const float w = tab[j * ts + t];
+  for (int j = 0; j < R; ++j)
+    if (t + j * NT < N) v[j] = __ldg(src + (size_t)(t + j * NT) * G);
 #pragma unroll
-    for (int r = 0; r < 9; ++r) v[r] = fmaf(src[r * LD + j], w, v[r]);
+  for (int j = 0; j < R; ++j) {
+    const int q = t + j * NT;
+    if (q < N) dst[(q / B) * BP + q % B] = v[j];
   }
 }
 
@@ -239,41 +319,58 @@ __device__ __forceinline__ void rows9s(const float* src, const float* tab, int t
 // modes of its adjoint G_d matter. With Z_c = G_{d+1} K_c the reverse time kernel is
 // G_d = c_d mu + c'_d mu_half + sum_c S_c^T Z_c and the star correlation of level d is
 // Z_c D_d^T; with V_c = lambda K_c^T the volume term is mu = -sum_c S_c^T V_c and its
-// correlation -V_c T^T.
+// correlation -V_c T^T. The contractions run over a multiple of four entries; the extra
+// entries multiply structural zeros of K_c or zero pads, so the sums are those of the
+// unpadded loops, term for term.
 template <int O>
 __global__ void __launch_bounds__(AdjPredCfg<O>::THREADS, 1) k_adj_pred(DevOps ops, AdjLtsArgs a, PhaseArgs ph) {
   using C = AdjPredCfg<O>;
-  constexpr int B = C::B, F = C::F, NB9 = C::NB9, NT = C::NT, NSCR = C::NSCR;
+  constexpr int B = C::B, F = C::F, BP = C::BP, FP = C::FP, NB9 = C::NB9, NT = C::NT;
   extern __shared__ __align__(16) float smem[];
-  float* tKT = smem;
-  float* tK = tKT + 3 * B * B;
-  float* tFt = tK + 3 * B * B;
-  float* tFhT = tFt + 4 * B * F;
-  float* tFtT = tFhT + 4 * B * F;
-  for (int i = threadIdx.x; i < 3 * B * B; i += C::THREADS) {
-    tKT[i] = a.KT[i];
-    tK[i] = ops.K[i];
+  float* tKT = smem;                  // [3][BP][B]   K_c^T[j][i] at (c BP + j) B + i
+  float* tK = tKT + 3 * BP * B;       // [3][BP][B]   K_c[j][i]
+  float* tFt = tK + 3 * BP * B;       // [4][BP][F]   F~_i[b][f] at (i BP + b) F + f
+  float* tFhT = tFt + 4 * BP * F;     // [4][BP][F]   F^_i[f][b] at (i BP + b) F + f
+  float* tFtT = tFhT + 4 * BP * F;    // [4][FP][B]   F~_i[b][f] at (i FP + f) B + b
+  // K_c[i][j] vanishes unless deg i < deg j (phi_i is orthogonal to the derivative of phi_j
+  // otherwise); those entries are set to exact zeros, so that the padded loops below add
+  // exact zeros only
+  for (int i = threadIdx.x; i < 3 * BP * B; i += C::THREADS) {
+    const int c = i / (BP * B), j = (i / B) % BP, x = i % B;
+    const bool in = j < B;
+    tKT[i] = (in && mode_degree(x) < mode_degree(j)) ? a.KT[(c * B + j) * B + x] : 0.f;
+    tK[i] = (in && mode_degree(j) < mode_degree(x)) ? ops.K[(c * B + j) * B + x] : 0.f;
   }
-  for (int i = threadIdx.x; i < 4 * B * F; i += C::THREADS) {
-    tFt[i] = ops.Ft[i];
-    tFhT[i] = a.FhT[i];
-    tFtT[i] = a.FtT[i];
+  for (int i = threadIdx.x; i < 4 * BP * F; i += C::THREADS) {
+    const int fi = i / (BP * F), j = (i / F) % BP, f = i % F;
+    tFt[i] = (j < B) ? ops.Ft[(fi * B + j) * F + f] : 0.f;
+    tFhT[i] = (j < B) ? a.FhT[(fi * B + j) * F + f] : 0.f;
   }
+  for (int i = threadIdx.x; i < 4 * FP * B; i += C::THREADS) {
+    const int fi = i / (FP * B), f = (i / B) % FP, x = i % B;
+    tFtT[i] = (f < F) ? a.FtT[(fi * F + f) * B + x] : 0.f;
+  }
+  // every group region starts zero: the pad entries are never written afterwards
+  for (int i = threadIdx.x; i < C::G * C::ELEM; i += C::THREADS) smem[C::TAB + i] = 0.f;
   __syncthreads();
   const int g = threadIdx.x / NT, t = threadIdx.x % NT;
-  float* sM = smem + C::TAB + g * C::ELEM;
-  float* sL = sM + AM_SIZE;
+  float* sS = smem + C::TAB + g * C::ELEM;   // compact S_c [3][36]
+  float* sA = sS + C::NSTAR;      // A-_i [4][9][12]: row s of face i at (i 9 + s) 12
+  float* sL = sA + C::NALOC;      // [9][BP] lambda
   float* sT = sL + NB9;
-  float* sG0 = sT + NB9;          // G ping-pong [2][9B]
-  float* sDb = sG0 + 2 * NB9;     // D_0 .. D_{O-1} [O][9B]
+  float* sG0 = sT + NB9;          // G ping-pong [2][9][BP]
+  float* sDb = sG0 + 2 * NB9;     // D_0 .. D_{O-1} [O][9][BP]
   float* sScr = sDb + O * NB9;    // V_c, then the face products, then Z_c
-  (void)NSCR;
   for (int k = blockIdx.x * C::G + g; k < a.end; k += gridDim.x * C::G) {
     const int meta = a.meta[k];
     const int cl = meta & 0xff;
     const bool finer = meta & FLAG_FINER, coarser = meta & FLAG_COARSER;
     const bool even = ph.parity[cl] == 0;
-    stage<AM_SIZE, NT>(sM, a.amat + (size_t)k * AM_SIZE, t);
+    {
+      const float* am = a.amat + (size_t)k * AM_SIZE;
+      for (int q = t; q < C::NSTAR; q += NT) sS[q] = __ldg(am + AM_STAR + (q / 36) * 81 + star_compact_index(q % 36));
+      for (int q = t; q < 4 * 81; q += NT) sA[(q / 9) * 12 + q % 9] = __ldg(am + AM_LOC + q);
+    }
     double* Wk = a.W + (size_t)k * AM_SIZE;
     // star correlations summed over the simulations, one 3 x 3 tile (c, row block, column
     // block) per thread t < 27
@@ -285,19 +382,19 @@ __global__ void __launch_bounds__(AdjPredCfg<O>::THREADS, 1) k_adj_pred(DevOps o
       for (int q = 0; q < 3; ++q) wst[i][q] = 0.f;
     for (int sim = 0; sim < a.nsim; ++sim) {
       const size_t kf = (size_t)k * a.nsim + sim;
-      stage<NB9, NT>(sL, a.lq + kf * NB9, t);
-      stage_strided<NB9, NT>(sDb, a.Qs + (size_t)k * a.qs + (size_t)(sim / a.G) * (NB9 * a.G) + sim % a.G, a.G, t);
+      stage_pad<B, BP, NT>(sL, a.lq + kf * (9 * B), 1, t);
+      stage_pad<B, BP, NT>(sDb, a.Qs + (size_t)k * a.qs + (size_t)(sim / a.G) * (9 * B * a.G) + sim % a.G, a.G, t);
       {
         // the adjoints of the buffers this pass wrote: lambda_B1 (+ lambda_B3) into sG0[0],
         // lambda_B2 into sG0[1]; reset here (lambda_B3 survives an accumulation)
-        constexpr int R = (NB9 + NT - 1) / NT;
-        const size_t o = kf * NB9;
+        constexpr int N = 9 * B, R = (N + NT - 1) / NT;
+        const size_t o = kf * N;
         float v1[R], v2[R], v3[R];
 #pragma unroll
         for (int j = 0; j < R; ++j) {
           const int q = t + j * NT;
           v1[j] = v2[j] = v3[j] = 0.f;
-          if (q < NB9) {
+          if (q < N) {
             v1[j] = a.lb1[o + q];
             if (coarser) v3[j] = a.lb3[o + q];
             if (finer) v2[j] = a.lb2[o + q];
@@ -306,9 +403,10 @@ __global__ void __launch_bounds__(AdjPredCfg<O>::THREADS, 1) k_adj_pred(DevOps o
 #pragma unroll
         for (int j = 0; j < R; ++j) {
           const int q = t + j * NT;
-          if (q < NB9) {
-            sG0[q] = v1[j] + v3[j];
-            sG0[NB9 + q] = v2[j];
+          if (q < N) {
+            const int qp = (q / B) * BP + q % B;
+            sG0[qp] = v1[j] + v3[j];
+            sG0[NB9 + qp] = v2[j];
             a.lb1[o + q] = 0.f;
             if (coarser && even) a.lb3[o + q] = 0.f;
             if (finer) a.lb2[o + q] = 0.f;
@@ -316,7 +414,6 @@ __global__ void __launch_bounds__(AdjPredCfg<O>::THREADS, 1) k_adj_pred(DevOps o
         }
       }
       gsync<NT>(g);
-      const float* S = sM + AM_STAR;
       // ---- forward time kernel: D_{d+1} = sum_c S_c D_d K_c^T on the support of D_{d+1}
 #pragma unroll
       for (int d = 0; d < O - 1; ++d) {
@@ -328,21 +425,26 @@ __global__ void __launch_bounds__(AdjPredCfg<O>::THREADS, 1) k_adj_pred(DevOps o
 #pragma unroll
             for (int s = 0; s < 9; ++s) Y[c][s] = 0.f;
           if (t < nout)
-#pragma unroll 4
-            for (int kk = 0; kk < nin; ++kk)
+#pragma unroll 1
+            for (int kk = 0; kk < nin; kk += 4) {
+              float4 x[9];
+              load_cols4<BP>(sDb + d * NB9, kk, x);
 #pragma unroll
-              for (int c = 0; c < 3; ++c) {
-                const float kc = tKT[(c * B + kk) * B + t];
+              for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int s = 0; s < 9; ++s) Y[c][s] = fmaf(sDb[(d) * NB9 + s * B + kk], kc, Y[c][s]);
-              }
+                for (int c = 0; c < 3; ++c) {
+                  const float kc = tKT[(c * BP + kk + u) * B + t];
+#pragma unroll
+                  for (int s = 0; s < 9; ++s) Y[c][s] = fmaf(lane4(x[s], u), kc, Y[c][s]);
+                }
+            }
           float v[9];
 #pragma unroll
           for (int r = 0; r < 9; ++r) v[r] = 0.f;
 #pragma unroll
-          for (int c = 0; c < 3; ++c) star_acc<false>(S + c * 81, Y[c], v);
+          for (int c = 0; c < 3; ++c) star_acc<false>(sS + c * 36, Y[c], v);
 #pragma unroll
-          for (int r = 0; r < 9; ++r) sDb[(d + 1) * NB9 + r * B + t] = v[r];
+          for (int r = 0; r < 9; ++r) sDb[(d + 1) * NB9 + r * BP + t] = v[r];
         }
         gsync<NT>(g);
       }
@@ -354,8 +456,8 @@ __global__ void __launch_bounds__(AdjPredCfg<O>::THREADS, 1) k_adj_pred(DevOps o
 #pragma unroll
         for (int r = 0; r < 9; ++r) {
           float v = 0.f;
-          for (int d = 0; d < O; ++d) v = fmaf(ph.coef[cl][d], sDb[(d) * NB9 + r * B + t], v);
-          sT[r * B + t] = v;
+          for (int d = 0; d < O; ++d) v = fmaf(ph.coef[cl][d], sDb[d * NB9 + r * BP + t], v);
+          sT[r * BP + t] = v;
         }
         // V_c = lambda K_c^T and the volume term
         float V[3][9];
@@ -363,22 +465,27 @@ __global__ void __launch_bounds__(AdjPredCfg<O>::THREADS, 1) k_adj_pred(DevOps o
         for (int c = 0; c < 3; ++c)
 #pragma unroll
           for (int s = 0; s < 9; ++s) V[c][s] = 0.f;
-#pragma unroll 4
-        for (int b = 0; b < B; ++b)
+#pragma unroll 1
+        for (int b = 0; b < BP; b += 4) {
+          float4 x[9];
+          load_cols4<BP>(sL, b, x);
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const float kc = tKT[(c * B + b) * B + t];
+          for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int s = 0; s < 9; ++s) V[c][s] = fmaf(sL[s * B + b], kc, V[c][s]);
-          }
+            for (int c = 0; c < 3; ++c) {
+              const float kc = tKT[(c * BP + b + u) * B + t];
+#pragma unroll
+              for (int s = 0; s < 9; ++s) V[c][s] = fmaf(lane4(x[s], u), kc, V[c][s]);
+            }
+        }
         float w[9];
 #pragma unroll
         for (int r = 0; r < 9; ++r) w[r] = 0.f;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          star_acc<true>(S + c * 81, V[c], w);
+          star_acc<true>(sS + c * 36, V[c], w);
 #pragma unroll
-          for (int s = 0; s < 9; ++s) sV[c * NB9 + s * B + t] = V[c][s];
+          for (int s = 0; s < 9; ++s) sV[c * NB9 + s * BP + t] = V[c][s];
         }
 #pragma unroll
         for (int r = 0; r < 9; ++r) mu[r] = -w[r];
@@ -390,45 +497,67 @@ __global__ void __launch_bounds__(AdjPredCfg<O>::THREADS, 1) k_adj_pred(DevOps o
         for (int i = 0; i < 3; ++i)
 #pragma unroll
           for (int q = 0; q < 3; ++q) tv[i][q] = 0.f;
-        tile33<B>(sV + tc * NB9, sT, 3 * trb, 3 * tsb, B, tv);
+        tile33v<BP>(sV + tc * NB9, sT, 3 * trb, 3 * tsb, BP, tv);
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
           for (int q = 0; q < 3; ++q) wst[i][q] -= tv[i][q];
       }
       gsync<NT>(g);
-      // local surface: LF_i = lambda F^_i^T, TF_i = T F~_i, U_i = A-_i^T LF_i, per (face, f)
-      float* sLF = sScr;
-      float* sTF = sScr + 36 * F;
-      float* sU = sScr + 72 * F;
-      for (int p = t; p < 4 * F; p += NT) {
-        const int i = p / F, f = p % F;
+      // local surface: LF_i = lambda F^_i^T, TF_i = T F~_i, U_i = A-_i^T LF_i, per (face, f);
+      // the pad columns f >= F are written zero
+      float* sLF = sScr;              // [4][9][FP]
+      float* sTF = sScr + 36 * FP;
+      float* sU = sScr + 72 * FP;
+      for (int p = t; p < 4 * FP; p += NT) {
+        const int i = p / FP, f = p % FP;
         float lf[9], tf[9], u[9];
-        rows9s<B, B>(sL, tFhT + i * B * F, F, f, lf);
-        rows9s<B, B>(sT, tFt + i * B * F, F, f, tf);
-        const float* Am = sM + AM_LOC + i * 81;
+        if (f < F) {
+          rows9v<BP, BP>(sL, tFhT + i * BP * F, F, f, lf);
+          rows9v<BP, BP>(sT, tFt + i * BP * F, F, f, tf);
 #pragma unroll
-        for (int r = 0; r < 9; ++r) {
-          float v = 0.f;
+          for (int r = 0; r < 9; ++r) u[r] = 0.f;
+          const float* Am = sA + i * 108;
 #pragma unroll
-          for (int s = 0; s < 9; ++s) v = fmaf(Am[s * 9 + r], lf[s], v);
-          u[r] = v;
+          for (int s = 0; s < 9; ++s) {
+            const float4 a0 = *reinterpret_cast<const float4*>(Am + s * 12);
+            const float4 a1 = *reinterpret_cast<const float4*>(Am + s * 12 + 4);
+            const float a8 = Am[s * 12 + 8];
+            u[0] = fmaf(a0.x, lf[s], u[0]);
+            u[1] = fmaf(a0.y, lf[s], u[1]);
+            u[2] = fmaf(a0.z, lf[s], u[2]);
+            u[3] = fmaf(a0.w, lf[s], u[3]);
+            u[4] = fmaf(a1.x, lf[s], u[4]);
+            u[5] = fmaf(a1.y, lf[s], u[5]);
+            u[6] = fmaf(a1.z, lf[s], u[6]);
+            u[7] = fmaf(a1.w, lf[s], u[7]);
+            u[8] = fmaf(a8, lf[s], u[8]);
+          }
+        } else {
+#pragma unroll
+          for (int r = 0; r < 9; ++r) lf[r] = tf[r] = u[r] = 0.f;
         }
 #pragma unroll
         for (int r = 0; r < 9; ++r) {
-          sLF[(i * 9 + r) * F + f] = lf[r];
-          sTF[(i * 9 + r) * F + f] = tf[r];
-          sU[(i * 9 + r) * F + f] = u[r];
+          sLF[(i * 9 + r) * FP + f] = lf[r];
+          sTF[(i * 9 + r) * FP + f] = tf[r];
+          sU[(i * 9 + r) * FP + f] = u[r];
         }
       }
       gsync<NT>(g);
       if (t < B)
+#pragma unroll 1
         for (int i = 0; i < 4; ++i)
-#pragma unroll 5
-          for (int f = 0; f < F; ++f) {
-            const float w = tFtT[(i * F + f) * B + t];
 #pragma unroll
-            for (int r = 0; r < 9; ++r) mu[r] = fmaf(sU[(i * 9 + r) * F + f], w, mu[r]);
+          for (int f = 0; f < FP; f += 4) {
+            float4 x[9];
+            load_cols4<FP>(sU + i * 9 * FP, f, x);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const float w = tFtT[(i * FP + f + u) * B + t];
+#pragma unroll
+              for (int r = 0; r < 9; ++r) mu[r] = fmaf(lane4(x[r], u), w, mu[r]);
+            }
           }
       for (int p = t; p < 36; p += NT) {
         const int i = p / 9, rb = (p / 3) % 3, sb = p % 3;
@@ -437,7 +566,7 @@ __global__ void __launch_bounds__(AdjPredCfg<O>::THREADS, 1) k_adj_pred(DevOps o
         for (int ii = 0; ii < 3; ++ii)
 #pragma unroll
           for (int q = 0; q < 3; ++q) acc[ii][q] = 0.f;
-        tile33<F>(sLF + i * 9 * F, sTF + i * 9 * F, 3 * rb, 3 * sb, F, acc);
+        tile33v<FP>(sLF + i * 9 * FP, sTF + i * 9 * FP, 3 * rb, 3 * sb, FP, acc);
 #pragma unroll
         for (int ii = 0; ii < 3; ++ii)
 #pragma unroll
@@ -447,12 +576,12 @@ __global__ void __launch_bounds__(AdjPredCfg<O>::THREADS, 1) k_adj_pred(DevOps o
       if (t < B) {
 #pragma unroll
         for (int r = 0; r < 9; ++r) {
-          mu[r] += sG0[r * B + t];
-          muh[r] = sG0[NB9 + r * B + t];
+          mu[r] += sG0[r * BP + t];
+          muh[r] = sG0[NB9 + r * BP + t];
         }
 #pragma unroll
         for (int r = 0; r < 9; ++r)
-          sG0[((O - 1) & 1) * NB9 + r * B + t] = ph.coef[cl][O - 1] * mu[r] + ph.hcoef[cl][O - 1] * muh[r];
+          sG0[((O - 1) & 1) * NB9 + r * BP + t] = ph.coef[cl][O - 1] * mu[r] + ph.hcoef[cl][O - 1] * muh[r];
       }
       gsync<NT>(g);
       // ---- reverse time kernel
@@ -467,34 +596,40 @@ __global__ void __launch_bounds__(AdjPredCfg<O>::THREADS, 1) k_adj_pred(DevOps o
           for (int c = 0; c < 3; ++c)
 #pragma unroll
             for (int r = 0; r < 9; ++r) Z[c][r] = 0.f;
+          // entries kk >= nk of G_{d+1} meet K_c[kk][t] = 0 for t < nout (degree structure)
           if (t < nout)
-#pragma unroll 4
-            for (int kk = 0; kk < nk; ++kk)
+#pragma unroll 1
+            for (int kk = 0; kk < nk; kk += 4) {
+              float4 x[9];
+              load_cols4<BP>(Gn, kk, x);
 #pragma unroll
-              for (int c = 0; c < 3; ++c) {
-                const float kc = tK[(c * B + kk) * B + t];
+              for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int r = 0; r < 9; ++r) Z[c][r] = fmaf(Gn[r * B + kk], kc, Z[c][r]);
-              }
-          float g[9];
+                for (int c = 0; c < 3; ++c) {
+                  const float kc = tK[(c * BP + kk + u) * B + t];
 #pragma unroll
-          for (int r = 0; r < 9; ++r) g[r] = ph.coef[cl][d] * mu[r] + ph.hcoef[cl][d] * muh[r];
+                  for (int r = 0; r < 9; ++r) Z[c][r] = fmaf(lane4(x[r], u), kc, Z[c][r]);
+                }
+            }
+          float gv[9];
+#pragma unroll
+          for (int r = 0; r < 9; ++r) gv[r] = ph.coef[cl][d] * mu[r] + ph.hcoef[cl][d] * muh[r];
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            star_acc<true>(S + c * 81, Z[c], g);
+            star_acc<true>(sS + c * 36, Z[c], gv);
 #pragma unroll
-            for (int r = 0; r < 9; ++r) sZ[c * NB9 + r * B + t] = Z[c][r];
+            for (int r = 0; r < 9; ++r) sZ[c * NB9 + r * BP + t] = Z[c][r];
           }
 #pragma unroll
-          for (int r = 0; r < 9; ++r) sG0[(d & 1) * NB9 + r * B + t] = g[r];
+          for (int r = 0; r < 9; ++r) sG0[(d & 1) * NB9 + r * BP + t] = gv[r];
         }
         gsync<NT>(g);
-        if (t < 27) tile33<B>(sZ + tc * NB9, (sDb + (d) * NB9), 3 * trb, 3 * tsb, nout, wst);
+        if (t < 27) tile33v<BP>(sZ + tc * NB9, sDb + d * NB9, 3 * trb, 3 * tsb, rup(nout, 4), wst);
         gsync<NT>(g);
       }
       if (t < B)
 #pragma unroll
-        for (int r = 0; r < 9; ++r) a.lq[kf * NB9 + r * B + t] = sL[r * B + t] + sG0[(0) * NB9 + r * B + t];
+        for (int r = 0; r < 9; ++r) a.lq[kf * (9 * B) + r * B + t] = sL[r * BP + t] + sG0[r * BP + t];
       gsync<NT>(g);   // the group's region is refilled for the next simulation or element
     }
     if (t < 27)

@@ -12,7 +12,8 @@
 //                 K_c[k][b] and G_i[r][f] = sum_k T[r][k] F~_i[k][f] for the volume and local
 //                 face kernels. No operator entry is read from memory and the structural zeros
 //                 of K_c and F~_i (Sec. IV-A "all sparsity") are not multiplied.
-//   column phase: thread = (element e, mode b), modes fastest: it reads the 27 products of
+//   column phase: thread = (element e, mode b), modes fastest (fused simulations: the
+//                 simulations of an element fastest): it reads the 27 products of
 //                 its column, applies the star matrices (physical form), the
 //                 anelastic coupling and relaxation, adds the Taylor terms and writes the
 //                 next derivative's column back for the next row phase.
@@ -136,12 +137,10 @@ __global__ void __launch_bounds__(SpCfg<O, M>::NT, 2) k_predict_sp(DevOps ops, D
   const int tid = threadIdx.x;
 
   // column task (slot, mode). One simulation: modes fastest (a warp spans at most two
-  // elements, and reads a row's consecutive modes). Fused simulations: slots fastest, so that
-  // the simulations of an element, innermost in the simulation-blocked layout, are in
-  // neighbouring lanes and the DOF accesses coalesce.
+  // elements, and reads a row's consecutive modes). Fused simulations: set per batch below.
   const bool act = tid < NE * B;
-  const int es = act ? (FUSED ? tid % NE : tid / B) : 0;
-  const int b = act ? (FUSED ? tid / NE : tid % B) : 0;
+  int es = act ? tid / B : 0;
+  int b = act ? tid % B : 0;
   // row task (part, pair): warp w takes part w mod NPART, so that the warps an SM
   // sub-partition runs (w mod 4) all execute the same part's straight-line code and its
   // instruction cache holds one part only
@@ -153,7 +152,7 @@ __global__ void __launch_bounds__(SpCfg<O, M>::NT, 2) k_predict_sp(DevOps ops, D
   const long long qs = FUSED ? st.qs : C::QS, bs = FUSED ? st.bs : C::BUFS;
   constexpr int RS = FUSED ? B * FUSED_GROUP : B;   // row stride of Q and the buffers
   constexpr int CS = FUSED ? FUSED_GROUP : 1;       // mode stride
-  const int col = es * 9;                     // this column's pair offset
+  int col = es * 9;                           // this column's pair offset
 
   for (int batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
     const int t0 = batch * NE;
@@ -167,6 +166,25 @@ __global__ void __launch_bounds__(SpCfg<O, M>::NT, 2) k_predict_sp(DevOps ops, D
       sSlot[NE + tid] = f;
     }
     __syncthreads();
+    if (FUSED && act) {
+      // fused column tasks ordered by (element, mode, simulation): the slots of the batch that
+      // share an element form a segment [s0, s1), and its B (s1 - s0) tasks take the modes in
+      // turn with the segment's simulations fastest, so that a warp's lanes read consecutive
+      // floats of the simulation-blocked layout (tasks of slot m lie in segment of slot m)
+      const int m = tid / B;
+      const int nval = min(NE, sl.n - t0);
+      if (m < nval) {
+        const int fm = sSlot[NE + m];
+        const int s0 = max(0, m - fm), s1 = min(nval, m - fm + sl.nsim);
+        const int local = tid - B * s0, nf = s1 - s0;
+        b = local / nf;
+        es = s0 + local % nf;
+      } else {
+        es = m;
+        b = tid % B;
+      }
+      col = es * 9;
+    }
     const int ts = t0 + es;
     const bool valid = act && ts < sl.n;
     const int g = valid ? elem_of(es) : ph.begin;
@@ -347,11 +365,20 @@ __global__ void __launch_bounds__(SpCfg<O, M>::NT, 2) k_predict_sp(DevOps ops, D
           for (int r = 0; r < 6; ++r) q[(9 + 6 * l + r) * RS] = acc[9 + 6 * l + r] + ph.omega[l] * Sv[NS - 6 + r];
       }
     }
-    if constexpr (!FUSED) {
-      const int bn = batch + gridDim.x;                    // this CTA's next batch
-      if (bn < nbatch) {
+    const int bn = batch + gridDim.x;                      // this CTA's next batch: its DOFs into L2
+    if (bn < nbatch) {
+      if constexpr (!FUSED) {
         const int en = ph.begin + bn * NE;
         prefetch_batch_q<NQ, B, 1, NT>(st.Q, qs, en, 0, min(NE, ph.end - en), tid);
+      } else {
+        // the simulation groups from the batch's first slot to its last are contiguous
+        int e0, f0, e1, f1;
+        sl.decode(bn * NE, e0, f0);
+        sl.decode(min(sl.n, bn * NE + NE) - 1, e1, f1);
+        constexpr int GB = NQ * B * FUSED_GROUP;
+        const float* p = st.Q + (size_t)(ph.begin + e0) * qs + (size_t)(f0 / FUSED_GROUP) * GB;
+        const long long len = (long long)(e1 - e0) * qs + (long long)(f1 / FUSED_GROUP - f0 / FUSED_GROUP + 1) * GB;
+        for (long long off = 32LL * tid; off < len; off += 32LL * NT) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + off));
       }
     }
   }
