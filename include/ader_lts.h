@@ -203,8 +203,10 @@ int lts_transfer_bytes(lts_t* h, int64_t* h2d, int64_t* d2h);
  * time from the nonzero entries only (Sec. IV-A "all sparsity"), in the predict kernel and
  * in a neighbour kernel that forms X F-_{j,h} as (X F~_j) R_h (R_h the face-basis map of the
  * orientation); with fused simulations it runs (element, simulation) slots, and a
- * partitioned run keeps the other engines' neighbour kernel. The tensor-core engines'
- * surface products run on CUDA cores. Takes effect at the next lts_advance. Errors: LTS_ERR_ARG for an unknown mode or a
+ * partitioned run keeps the other engines' neighbour kernel. With one simulation the
+ * adjoint's reverse predict pass (lts_misfit_gradient) uses the same generated products
+ * (their transposed forms); every other engine, and fused runs, take its dense-block
+ * kernel. The tensor-core engines' surface products run on CUDA cores. Takes effect at the next lts_advance. Errors: LTS_ERR_ARG for an unknown mode or a
  * mode the handle's shape has no kernel for (tensor cores: order 3 with one simulation).
  * A tensor-core wait that gives up (bounded, about one second)
  * makes the next synchronising call return LTS_ERR_TIMEOUT. */

@@ -1236,7 +1236,12 @@ void adjoint_lts(lts_solver* h, int64_t n_macro, int64_t every, const double* da
       const float* base = reinterpret_cast<const float*>(snap + snap_off[pi]);
       if (ph.kind == 1) {
         aa.Qs = base;
-        X.adj_pred(h->dops, aa, pa, pa.end, stream);
+        // the sparse engine's reverse predict serves one simulation; fused runs and the
+        // other engines take the dense-block kernel
+        if (nsim == 1 && h->contraction == LTS_CONTRACT_SPARSE && X.adj_pred_sp)
+          X.adj_pred_sp(aa, pa, pa.end, stream);
+        else
+          X.adj_pred(h->dops, aa, pa, pa.end, stream);
       } else {
         // a buffer owner differs by at most one cluster from the receivers it feeds, so
         // the owners of this pass are the elements of clusters 0..top+1

@@ -26,6 +26,13 @@
 //       the four faces' interface states, F^_i = F~_i^T in the orthonormal face basis).
 //   sp_ntrace_o{O}(j, x, y): G_j[f] = sum_k x[k] F~_j[k][f] of one row of a neighbour's
 //       buffer on the face j that each thread asks for (neighbour kernel).
+// and for the reverse predict pass of the discrete adjoint (k_adj_pred_sp):
+//   sp_trace_o{O}(part, x, g): G_i[f] = sum_k x[k] F~_i[k][f] alone (the traces of sp_vol).
+//   sp_tproj_o{O}(part, x, y): y[b] = sum_i sum_f x[i F + f] F~_i[b][f] (the transposed face
+//       traces of the four faces, summed).
+//   sp_kvol_o{O}(part, variant, x, y): Z_c[b] = sum_k x[k] K_c[k][b] for 1 <= b < nbasis(O - v)
+//       (the reverse time kernel at level v; K_c[k][b] != 0 only for deg k < deg b, so the
+//       inputs are k < nbasis(O - 1 - v)).
 // x[k * XP] is the thread's row, y[(c B + b) XP] (or y[(i B + b) XP]) and g[(i F + f) XP]
 // the outputs (XP the pair stride of the staging arrays, a template parameter so that
 // every address is an immediate offset). Every output the kernel reads is written
@@ -35,8 +42,9 @@
 //        gen_sparse --list <order> lists every product term, one line each:
 //        "<kind> <part> <output> <input> <value>", kind t (time kernel, output c B + b, full
 //        variant), v (volume, output c B + b), g (face trace, output i F + f), p (face
-//        projection, output i B + b, input i F + f) or n (neighbour face trace, output j F + f);
-//        for checks against other operators.
+//        projection, output i B + b, input i F + f), n (neighbour face trace, output j F + f),
+//        s (summed transposed traces, output b, input i F + f) or k (reverse time kernel,
+//        output c B + b, full variant); for checks against other operators.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -89,6 +97,12 @@ struct Products {
   std::vector<Out> proj;
   Parts proj_parts;
   std::vector<std::vector<Out>> ntrace;  // per face j: the F outputs G_j[f]
+  std::vector<Out> trace;                // G_i alone
+  Parts trace_parts;
+  std::vector<Out> tproj;                // sum over faces of the transposed traces
+  Parts tproj_parts;
+  std::vector<std::vector<Out>> kvol;    // reverse time kernel, per level
+  std::vector<Parts> kvol_parts;
   size_t time_terms = 0, vol_terms = 0, face_terms = 0;
 
   void build(int order, int np) {
@@ -174,6 +188,43 @@ struct Products {
         outs.push_back(u);
       }
       ntrace.push_back(outs);
+    }
+    // adjoint products: the face traces alone (as in vol, by face mode then face)
+    ord.clear();
+    for (const Out& u : vol)
+      if (u.kind == 'g') {
+        ord.push_back((int)trace.size());
+        trace.push_back(u);
+      }
+    trace_parts = partition(trace, nparts, ord);
+    // y[b] = sum_{i, f} x[i F + f] F~_i[b][f], by mode
+    ord.clear();
+    for (int b = 0; b < B; ++b) {
+      Out u{'s', b, dst("y", b), {}};
+      for (int i = 0; i < 4; ++i)
+        for (int m = 0; m < F; ++m)
+          if (nzf(ops.Ft[i][b * F + m])) u.t.push_back({i * F + m, (float)ops.Ft[i][b * F + m]});
+      ord.push_back((int)tproj.size());
+      tproj.push_back(u);
+    }
+    tproj_parts = partition(tproj, nparts, ord);
+    // Z_c[b] = sum_k x[k] K_c[k][b], 1 <= b < nbasis(O - v), by mode then c
+    for (int v = 0; v <= O - 2; ++v) {
+      std::vector<Out> outs;
+      std::vector<int> o2;
+      for (int b = 1; b < nb(O - v); ++b)
+        for (int c = 0; c < 3; ++c) {
+          Out u{'k', c * B + b, dst("y", c * B + b), {}};
+          for (int k = 0; k < B; ++k)
+            if (nzk(ops.K[c][k * B + b])) {
+              if (k >= nb(O - 1 - v)) throw std::runtime_error("K_c[k][b] must vanish for deg k >= deg b");
+              u.t.push_back({k, (float)ops.K[c][k * B + b]});
+            }
+          o2.push_back((int)outs.size());
+          outs.push_back(u);
+        }
+      kvol_parts.push_back(partition(outs, nparts, o2));
+      kvol.push_back(outs);
     }
   }
 };
@@ -282,6 +333,14 @@ void emit_order(FILE* f, int O, int nparts) {
   std::snprintf(nm, sizeof nm, "sp_proj_o%d", O);
   emit_dispatch(f, nm, "const float* __restrict__ x, float* __restrict__ y", "x, y", {P.proj_parts}, {P.proj}, false);
   emit_ntrace(f, O, P);
+  std::snprintf(nm, sizeof nm, "sp_trace_o%d", O);
+  emit_dispatch(f, nm, "const float* __restrict__ x, float* __restrict__ g", "x, g", {P.trace_parts}, {P.trace},
+                false);
+  std::snprintf(nm, sizeof nm, "sp_tproj_o%d", O);
+  emit_dispatch(f, nm, "const float* __restrict__ x, float* __restrict__ y", "x, y", {P.tproj_parts}, {P.tproj},
+                false);
+  std::snprintf(nm, sizeof nm, "sp_kvol_o%d", O);
+  emit_dispatch(f, nm, "const float* __restrict__ x, float* __restrict__ y", "x, y", P.kvol_parts, P.kvol, true);
 }
 
 int parts_of(int O) { return O == 5 ? 4 : (O == 4 ? 2 : 1); }
@@ -303,6 +362,8 @@ int list_terms(int O) {
     for (size_t i = 0; i < all.size(); ++i) all[i] = (int)i;
     list(outs, Parts{all});
   }
+  list(P.tproj, P.tproj_parts);
+  list(P.kvol[0], P.kvol_parts[0]);
   return 0;
 }
 

@@ -6,6 +6,7 @@
 #include "kernels_sp.cuh"
 #include "kernels_tc.cuh"
 #include "kernels_adj.cuh"
+#include "kernels_adj_sp.cuh"
 
 namespace ltsdev {
 
@@ -45,6 +46,8 @@ struct Launchers {
   void (*adj_src_grad)(const float* lam, int nsim, const SrcItem* items, const double* c, int n, const float* phi,
                        double* g, cudaStream_t);
   void (*adj_pred)(const DevOps&, const AdjLtsArgs&, const PhaseArgs&, int nelem, cudaStream_t);
+  // the same with generated sparse products (one simulation; nullptr for fused instantiations)
+  void (*adj_pred_sp)(const AdjLtsArgs&, const PhaseArgs&, int nelem, cudaStream_t);
   void (*adj_nbr)(const DevOps&, const AdjLtsArgs&, const PhaseArgs&, int K, cudaStream_t);
   // face-local messages of a partitioned run (one simulation)
   void (*pack)(const DevOps&, const DevState&, const PhaseArgs&, const int* send_elem, const int* send_code,
@@ -104,6 +107,10 @@ struct Impl {
     if constexpr (M == 0) {
       e = cudaFuncSetAttribute(k_adj_pred<O>, cudaFuncAttributeMaxDynamicSharedMemorySize, AdjPredCfg<O>::SMEM_BYTES);
       if (e != cudaSuccess) return e;
+      if constexpr (FG == 1) {
+        e = smem_attrs(k_adj_pred_sp<O>, AdjSpCfg<O>::TOTAL * sizeof(float), true);
+        if (e != cudaSuccess) return e;
+      }
     }
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L->blocks_neighbour, k_neighbour<O, M, FG>, C::NTN,
                                                          L->smem_neighbour);
@@ -162,6 +169,16 @@ struct Impl {
     const int grid = ctas < nsm ? ctas : nsm;
     if (grid > 0) k_adj_pred<O><<<grid, A::THREADS, A::SMEM_BYTES, st>>>(o, a, p);
   }
+  // two CTAs per SM, each taking batches of NE elements in turn
+  static void adj_pred_sp(const AdjLtsArgs& a, const PhaseArgs& p, int n, cudaStream_t st) {
+    using A = AdjSpCfg<O>;
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int nb = (n + A::NE - 1) / A::NE;
+    const int grid = nb < 2 * nsm ? nb : 2 * nsm;
+    if (grid > 0) k_adj_pred_sp<O><<<grid, A::NT, A::TOTAL * sizeof(float), st>>>(a, p);
+  }
   static void adj_nbr(const DevOps& o, const AdjLtsArgs& a, const PhaseArgs& p, int K, cudaStream_t st) {
     k_adj_nbr<O><<<K, AdjNT<O>::value, 0, st>>>(o, a, p);
   }
@@ -213,6 +230,7 @@ struct Impl {
       L.adj_source = &adj_source;
       L.adj_src_grad = &adj_src_grad;
       L.adj_pred = &adj_pred;
+      if constexpr (FG == 1) L.adj_pred_sp = &adj_pred_sp;
       L.adj_nbr = &adj_nbr;
     }
     L.energy = &energy;

@@ -48,8 +48,9 @@ def _oracle(order, m, rho, lam, mu, q0, rec, src, data, dt, n):
     return oracle_misfit_gradient(o, dt, n, re, rp, data), o
 
 
-def _gpu(order, m, rho, lam, mu, q0, rec, src, dt):
+def _gpu(order, m, rho, lam, mu, q0, rec, src, dt, engine="sparse"):
     s = binding.Solver(order, 0, device=0)
+    s.set_contraction(engine)
     s.set_mesh(m["xyz"], m["tet"], m["face_bc"])
     s.set_material(rho, np.sqrt((lam + 2 * mu) / rho), np.sqrt(mu / rho))
     s.add_point_source(*src)
@@ -85,8 +86,11 @@ def _central_difference(make, params, p, k, misfit, J, g, noise):
     return fd, abs(fd - g) <= 2e-2 * abs(g) + noise * J / h, noise * J / h
 
 
+@pytest.mark.parametrize("engine", ["sparse", "fp32"])
 @pytest.mark.parametrize("order", [3, 4])
-def test_gpu_adjoint_matches_oracle_adjoint(order):
+def test_gpu_adjoint_matches_oracle_adjoint(order, engine):
+    """Both reverse predict kernels: generated sparse products (engine 'sparse', the default
+    for one simulation) and dense degree blocks ('fp32')."""
     m, mat, q0, rec, src = _case(order)
     rho, lam, mu = _rlm(mat)
     n = 8
@@ -95,7 +99,7 @@ def test_gpu_adjoint_matches_oracle_adjoint(order):
     # observed data: the oracle in a model with mu 2 % higher
     (_, _, _, data), _ = _oracle(order, m, rho, lam, mu * 1.02, q0, rec, src, np.zeros((n + 1, 3, 3)), dt, n)
     (J0, g0, dq0_o, syn0), _ = _oracle(order, m, rho, lam, mu, q0, rec, src, data, dt, n)
-    s = _gpu(order, m, rho, lam, mu, q0, rec, src, dt)
+    s = _gpu(order, m, rho, lam, mu, q0, rec, src, dt, engine)
     J, g, syn, dq0 = s.misfit_gradient(n, data, every=3, want_dq0=True)
     assert _rel(syn, syn0) <= 1e-5
     assert abs(J / J0 - 1) <= 1e-3
@@ -203,8 +207,9 @@ def _forced_clusters(m):
     return olts.normalise(np.digitize(cx, np.quantile(cx, [0.3, 0.65])), om.nbr)
 
 
-def _gpu_lts(order, m, rho, lam, mu, q0, rec, src, cl, dt):
+def _gpu_lts(order, m, rho, lam, mu, q0, rec, src, cl, dt, engine="sparse"):
     s = binding.Solver(order, 0, device=0)
+    s.set_contraction(engine)
     s.set_mesh(m["xyz"], m["tet"], m["face_bc"])
     s.set_material(rho, np.sqrt((lam + 2 * mu) / rho), np.sqrt(mu / rho))
     s.add_point_source(*src)
@@ -216,9 +221,11 @@ def _gpu_lts(order, m, rho, lam, mu, q0, rec, src, cl, dt):
     return s
 
 
-@pytest.mark.parametrize("order", [3, 4])
-def test_gpu_lts_adjoint_matches_oracle_lts_adjoint(order):
-    """Three forced clusters (all buffer relations), samples at the macro-step boundaries."""
+@pytest.mark.parametrize("engine", ["sparse", "fp32"])
+@pytest.mark.parametrize("order", [3, 4, 5])
+def test_gpu_lts_adjoint_matches_oracle_lts_adjoint(order, engine):
+    """Three forced clusters (all buffer relations), samples at the macro-step boundaries;
+    both reverse predict kernels."""
     from oracle.adjoint import misfit_gradient_lts
     m, mat, q0, rec, src = _case(order, seed=14)
     rho, lam, mu = _rlm(mat)
@@ -241,7 +248,7 @@ def test_gpu_lts_adjoint_matches_oracle_lts_adjoint(order):
     _, _, _, data = misfit_gradient_lts(o, n_macro, re, rp, np.zeros((n_macro + 1, 3, 3)))
     o, re, rp = oracle(mu)
     J0, g0, dq0_o, syn0 = misfit_gradient_lts(o, n_macro, re, rp, data)
-    s = _gpu_lts(order, m, rho, lam, mu, q0, rec, src, cl, dt)
+    s = _gpu_lts(order, m, rho, lam, mu, q0, rec, src, cl, dt, engine)
     J, g, syn, dq0 = s.misfit_gradient(4 * n_macro, data, every=2, want_dq0=True)
     assert _rel(syn, syn0) <= 1e-5
     assert abs(J / J0 - 1) <= 1e-3

@@ -1,6 +1,7 @@
 """The generated sparse products of the predict kernel (contraction engine 'sparse') take
 exactly the nonzero entries of the stiffness matrices K_c and of the face matrices F~_i
-and of their transposes F^_i (Sec. III-A), with values equal to the oracle's independently
+and of their transposes F^_i (Sec. III-A), and so do the products of the adjoint's reverse
+predict pass, with values equal to the oracle's independently
 built operators to FP32 rounding, and no term the oracle has is dropped. The generator lists every product term
 (kind, part, output, k, value) it writes into the kernel."""
 import os
@@ -40,7 +41,11 @@ def test_generated_terms_are_the_oracle_operators_nonzeros(order):
         proj[i * B:(i + 1) * B, i * F:(i + 1) * F] = ob.Fh[i].T
     want["p"] = proj
     want["n"] = np.stack([ob.Ft[j].T for j in range(4)]).reshape(4 * F, B)
-    scale = {"t": kmax, "v": kmax, "g": fmax, "p": fmax, "n": fmax}
+    # adjoint products: the four faces' transposed traces summed, out b from the inputs
+    # (i, f), F~_i[b][f]; the reverse time kernel X K_c (as the volume kernel)
+    want["s"] = np.concatenate([ob.Ft[i] for i in range(4)], axis=1)
+    want["k"] = want["v"]
+    scale = {"t": kmax, "v": kmax, "g": fmax, "p": fmax, "n": fmax, "s": fmax, "k": kmax}
     got = {k: np.zeros_like(v) for k, v in want.items()}
     part_of = {}
     for kind, part, o, k, val in terms:
@@ -63,3 +68,4 @@ def test_generated_terms_are_the_oracle_operators_nonzeros(order):
     nk = sum(int(np.sum(np.abs(ob.K[c]) > 1e-9 * kmax)) for c in range(3))
     assert sum(1 for t in terms if t[0] == "t") == nk
     assert sum(1 for t in terms if t[0] == "v") == nk
+    assert sum(1 for t in terms if t[0] == "k") == nk
