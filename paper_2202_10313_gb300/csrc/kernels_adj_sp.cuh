@@ -191,6 +191,25 @@ __global__ void __launch_bounds__(AdjSpCfg<O>::NT, 2) k_adj_pred_sp(AdjLtsArgs a
       }
     }
     __syncthreads();
+    {
+      // the next batch's inputs into L2 while this batch computes: operator matrices, Q,
+      // lambda and lambda_B1 (128-byte lines)
+      const int kn = k0 + gridDim.x * NE;
+      if (kn < a.end) {
+        const int nn = min(NE, a.end - kn);
+        const long long la = (long long)nn * AM_SIZE, lqn = (long long)nn * 9 * B, lQ = (long long)nn * a.qs;
+        const float* pa = a.amat + (size_t)kn * AM_SIZE;
+        const float* pq = a.Qs + (size_t)kn * a.qs;
+        const float* pl = a.lq + (size_t)kn * 9 * B;
+        const float* pb = a.lb1 + (size_t)kn * 9 * B;
+        for (long long off = 32LL * tid; off < la; off += 32LL * NT) asm volatile("prefetch.global.L2 [%0];" ::"l"(pa + off));
+        for (long long off = 32LL * tid; off < lQ; off += 32LL * NT) asm volatile("prefetch.global.L2 [%0];" ::"l"(pq + off));
+        for (long long off = 32LL * tid; off < lqn; off += 32LL * NT) {
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(pl + off));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(pb + off));
+        }
+      }
+    }
     const float* Sk = sStar + es * 108;
     // ---- forward time kernel: D_{d+1} = sum_c S_c D_d K_c^T (variant d: D_d on nbasis(O - d)
     // modes, D_{d+1} on nbasis(O - 1 - d))
