@@ -215,9 +215,9 @@ int lts_set_contraction(lts_t* h, int mode);
 
 /* Tile variant of the sparse engine's neighbour kernel (Sec. III-A neighbour surface
  * kernel): 0 = 8 elements per CTA (two CTAs per SM), 1 = 4 elements per CTA (four CTAs per
- * SM). The arithmetic per element is the same, so the results are bitwise identical; only
- * the grouping of elements into CTAs changes. Set by lts_autotune; ignored by the other
- * engines. Errors: LTS_ERR_ARG for another value. */
+ * SM; the default). The arithmetic per element is the same, so the results are bitwise
+ * identical; only the grouping of elements into CTAs changes. Set by lts_autotune; ignored
+ * by the other engines. Errors: LTS_ERR_ARG for another value. */
 int lts_set_tile(lts_t* h, int tile);
 
 /* Weighted partitioning for distributed runs (Sec. V-C). Element weight 2^(N_c-1-l) (its

@@ -116,6 +116,8 @@ def main():
     ap.add_argument("--checkpoint", type=int, default=100, help="finest steps between checkpoints")
     ap.add_argument("--receivers", type=int, default=32)
     ap.add_argument("--fd", type=int, default=3, help="elements checked by central differences")
+    ap.add_argument("--tile", type=int, default=None,
+                    help="tile variant of the sparse engine's neighbour kernel (0: 8 elements per CTA, 1: 4)")
     ap.add_argument("--fused", type=int, default=1,
                     help="F > 1: F sources in one fused run (gradient of the summed misfit), timed "
                          "against one single-source gradient")
@@ -134,6 +136,8 @@ def main():
 
     def solver(r, l, m, cl=None, lam_c=None, dt=None, nf=F):
         s = binding.Solver(a.order, 0, device=0, n_fused=nf)
+        if a.tile is not None:
+            s.set_tile(a.tile)
         s.set_mesh(mesh["xyz"], mesh["tet"], mesh["face_bc"])
         s.set_material(r, np.sqrt((l + 2 * m) / r), np.sqrt(m / r))
         for f in range(nf):

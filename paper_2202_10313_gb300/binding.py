@@ -428,7 +428,8 @@ class Solver:
         self._check(lib().lts_set_contraction(self._h, code))
 
     def set_tile(self, tile):
-        """Tile variant of the sparse engine's neighbour kernel: 0 (8 elements per CTA) or 1 (4)."""
+        """Tile variant of the sparse engine's neighbour kernel: 0 (8 elements per CTA) or 1 (4, the
+        default)."""
         self._check(lib().lts_set_tile(self._h, int(tile)))
 
     def set_profiling(self, on=True):

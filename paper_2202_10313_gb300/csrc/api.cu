@@ -92,7 +92,7 @@ struct lts_solver {
   int nsim = 1;                             // fused simulations
   int contraction = LTS_CONTRACT_FP32;
   int ctas_predict = 0, ctas_neighbour = 0;  // resident CTAs per SM the grids are sized for (0: occupancy)
-  int tile = 0;                              // tile variant of the sparse engine's neighbour kernel
+  int tile = 1;                              // tile variant of the sparse engine's neighbour kernel
   long long wait_cycles = ltsdev::TC_WAIT_CYCLES;   // bound of the tensor-core completion waits
   int suppress_commit = 0;                          // failure-path test: waits run out
   // emulated partitioned run (Sec. V-C): cut faces receive face-local messages
@@ -868,40 +868,6 @@ void advance_steps(lts_solver* h, int64_t n_finest, cudaStream_t stream) {
 }
 
 // ------------------------------------------------------------------ discrete adjoint
-// Explicit 9 x 9 operators of element k (original index) in FP64: star matrices S_c and, per
-// face, the flux solvers A- (interior state) and A+ (exterior state), from the closed forms
-// of the forward set-up. With T = lts::Dual, the seeded material parameter's derivative
-// rides along: param 0-2 the element's (rho, lambda, mu), 3-5 the face neighbour's of face
-// `face` (ignored for the star matrices and for boundary faces); -1 seeds nothing.
-template <typename T>
-void element_operators(const lts_solver* h, int64_t k, int face, int param, T S[3][81], T Am[81], T Ap[81]) {
-  const lts::Mesh& M = h->mesh;
-  auto mat = [&](int64_t e, int base) {
-    T rho(h->mat.rho[e]), lam(h->lam[e]), mu(h->mu[e]);
-    if constexpr (std::is_same<T, lts::Dual>::value) {
-      if (param == base + 0) rho.d = 1.0;
-      if (param == base + 1) lam.d = 1.0;
-      if (param == base + 2) mu.d = 1.0;
-    }
-    return std::array<T, 3>{rho, lam, mu};
-  };
-  const auto own = mat(k, 0);
-  const T rinv = T(1.0) / own[0];
-  if (S) lts::star_matrices_t<T>(&M.Jinv[9 * k], own[1], own[2], rinv, S);
-  if (face < 0) return;
-  const int bc = M.bc[4 * k + face];
-  const int64_t nb = M.nbr[4 * k + face];
-  const auto oth = nb >= 0 ? mat(nb, 3) : own;
-  const T zp = lts::sqrt_t((own[1] + T(2.0) * own[2]) * own[0]), zs = lts::sqrt_t(own[2] * own[0]);
-  const T zpo = nb >= 0 ? lts::sqrt_t((oth[1] + T(2.0) * oth[2]) * oth[0]) : zp;
-  const T zso = nb >= 0 ? lts::sqrt_t(oth[2] * oth[0]) : zs;
-  const T scale(-2.0 * M.area[4 * k + face] / M.detJ[k]);
-  T cl[8], cn[8];
-  lts::face_coefficients_t<T>(bc, zp, zs, zpo, zso, scale, cl, cn);
-  lts::face_flux_matrix<T>(&M.normal[12 * k + 3 * face], cl, own[1], own[2], rinv, Am);
-  lts::face_flux_matrix<T>(&M.normal[12 * k + 3 * face], cn, own[1], own[2], rinv, Ap);
-}
-
 struct DevBuf {
   void* p = nullptr;
   DevBuf() = default;
@@ -1023,7 +989,45 @@ __global__ void k_grad_contract(GradGeom g, double* grad) {
   }
 }
 
-void contract_gradient(const lts_solver* h, const double* d_w, double* grad, cudaStream_t stream) {
+// Explicit 9 x 9 operators of every element in FP32 (internal order): the star matrices S_c
+// and, per face, the flux solvers A- (interior state) and A+ (exterior state), from the
+// closed forms of the forward set-up (host_flux.h) evaluated in FP64. One thread per
+// (element, task): task 0 the star matrices, task 1 + i face i.
+__global__ void k_build_amat(GradGeom g, float* amat) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 5 * g.K) return;
+  const long long k = t / 5;
+  const int task = (int)(t % 5);
+  float* out = amat + (size_t)g.iperm[k] * ltsdev::AM_SIZE;
+  const double rho = g.rho[k], lam = g.lam[k], mu = g.mu[k], rinv = 1.0 / rho;
+  if (task == 0) {
+    double S[3][81];
+    lts::star_matrices_t<double>(g.jinv + 9 * k, lam, mu, rinv, S);
+    for (int c = 0; c < 3; ++c)
+      for (int q = 0; q < 81; ++q) out[ltsdev::AM_STAR + c * 81 + q] = (float)S[c][q];
+    return;
+  }
+  const int i = task - 1;
+  const int bc = g.bc[4 * k + i];
+  const long long nb = g.nbr[4 * k + i];
+  const double zp = lts::sqrt_t((lam + 2.0 * mu) * rho), zs = lts::sqrt_t(mu * rho);
+  const double zpo = nb >= 0 ? lts::sqrt_t((g.lam[nb] + 2.0 * g.mu[nb]) * g.rho[nb]) : zp;
+  const double zso = nb >= 0 ? lts::sqrt_t(g.mu[nb] * g.rho[nb]) : zs;
+  const double scale = -2.0 * g.area[4 * k + i] / g.detJ[k];
+  double cl[8], cn[8], M[81];
+  lts::face_coefficients_t<double>(bc, zp, zs, zpo, zso, scale, cl, cn);
+  lts::face_flux_matrix<double>(g.normal + 12 * k + 3 * i, cl, lam, mu, rinv, M);
+  for (int q = 0; q < 81; ++q) out[ltsdev::AM_LOC + i * 81 + q] = (float)M[q];
+  lts::face_flux_matrix<double>(g.normal + 12 * k + 3 * i, cn, lam, mu, rinv, M);
+  for (int q = 0; q < 81; ++q) out[ltsdev::AM_NBR + i * 81 + q] = (float)M[q];
+}
+
+// Geometry and material of every element on the device (original element order), for the
+// operator build and the gradient contraction; the buffers live as long as `bufs`.
+struct GeoBufs {
+  DevBuf dbl, ints, perm;
+};
+GradGeom upload_geometry(const lts_solver* h, GeoBufs& bufs, cudaStream_t stream) {
   const lts::Mesh& M = h->mesh;
   const int64_t K = M.K;
   std::vector<int> bc(4 * K), nbr(4 * K), nface(4 * K);
@@ -1034,16 +1038,14 @@ void contract_gradient(const lts_solver* h, const double* d_w, double* grad, cud
     nface[i] = M.nbr_face[i];
   }
   for (int64_t k = 0; k < K; ++k) iperm[k] = (long long)h->iperm[k];
-  DevBuf d_geo, d_int, d_perm, d_grad;
   const size_t nd = (size_t)K * (9 + 12 + 4 + 1 + 3);
-  d_geo.alloc(sizeof(double) * nd);
-  d_int.alloc(sizeof(int) * 12 * K);
-  d_perm.alloc(sizeof(long long) * K);
-  d_grad.alloc(sizeof(double) * 3 * K);
-  double* geo = d_geo.get<double>();
-  int* in = d_int.get<int>();
+  bufs.dbl.alloc(sizeof(double) * nd);
+  bufs.ints.alloc(sizeof(int) * 12 * K);
+  bufs.perm.alloc(sizeof(long long) * K);
+  double* geo = bufs.dbl.get<double>();
+  int* in = bufs.ints.get<int>();
   auto up = [&](void* dst, const void* src, size_t bytes) {
-    ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, stream), "gradient geometry");
+    ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, stream), "adjoint geometry");
   };
   GradGeom g{};
   g.jinv = geo;
@@ -1053,11 +1055,10 @@ void contract_gradient(const lts_solver* h, const double* d_w, double* grad, cud
   g.rho = geo + 26 * K;
   g.lam = geo + 27 * K;
   g.mu = geo + 28 * K;
-  g.W = d_w;
   g.bc = in;
   g.nbr = in + 4 * K;
   g.nbr_face = in + 8 * K;
-  g.iperm = d_perm.get<long long>();
+  g.iperm = bufs.perm.get<long long>();
   g.K = K;
   up(const_cast<double*>(g.jinv), M.Jinv.data(), sizeof(double) * 9 * K);
   up(const_cast<double*>(g.normal), M.normal.data(), sizeof(double) * 12 * K);
@@ -1069,11 +1070,20 @@ void contract_gradient(const lts_solver* h, const double* d_w, double* grad, cud
   up(in, bc.data(), sizeof(int) * 4 * K);
   up(in + 4 * K, nbr.data(), sizeof(int) * 4 * K);
   up(in + 8 * K, nface.data(), sizeof(int) * 4 * K);
-  up(d_perm.p, iperm.data(), sizeof(long long) * K);
+  up(bufs.perm.p, iperm.data(), sizeof(long long) * K);
+  // the host vectors must outlive the copies: the stream is synchronised before they go
+  ck(cudaStreamSynchronize(stream), "synchronize");
+  return g;
+}
+
+void contract_gradient(GradGeom g, const double* d_w, double* grad, cudaStream_t stream) {
+  g.W = d_w;
+  DevBuf d_grad;
+  d_grad.alloc(sizeof(double) * 3 * g.K);
   const int threads = 128;
-  k_grad_contract<<<(unsigned)((K + threads - 1) / threads), threads, 0, stream>>>(g, d_grad.get<double>());
+  k_grad_contract<<<(unsigned)((g.K + threads - 1) / threads), threads, 0, stream>>>(g, d_grad.get<double>());
   ck(cudaGetLastError(), "gradient contraction");
-  ck(cudaMemcpyAsync(grad, d_grad.p, sizeof(double) * 3 * K, cudaMemcpyDeviceToHost, stream), "download gradient");
+  ck(cudaMemcpyAsync(grad, d_grad.p, sizeof(double) * 3 * g.K, cudaMemcpyDeviceToHost, stream), "download gradient");
   ck(cudaStreamSynchronize(stream), "synchronize");
 }
 
@@ -1084,7 +1094,8 @@ void contract_gradient(const lts_solver* h, const double* d_w, double* grad, cud
 // reverse sweep (k_adj_pred / k_adj_nbr, phases in reverse order).
 void adjoint_lts(lts_solver* h, int64_t n_macro, int64_t every, const double* data, double* misfit, double* grad,
                  double* synth_out, double* dq0, cudaStream_t stream, const DevBuf& d_amat, const DevBuf& d_fwd,
-                 const DevBuf& d_back, const DevBuf& d_relem, const DevBuf& d_rphi, int nrec, const AdjTables& tabs) {
+                 const DevBuf& d_back, const DevBuf& d_relem, const DevBuf& d_rphi, int nrec, const AdjTables& tabs,
+                 const GradGeom& geo) {
   const Launchers& X = h->L;
   const int64_t K = h->mesh.K;
   const int B = X.B, NB9 = 9 * B;
@@ -1097,14 +1108,18 @@ void adjoint_lts(lts_solver* h, int64_t n_macro, int64_t every, const double* da
   const int nsim = h->nsim, G = nsim > 1 ? X.FG : 1;
   h->adj_src_grad.clear();   // set again only by a completed reverse sweep
   const int64_t ns = (int64_t)nsim * nrec * 3;   // sample values per sample time
+  // the reverse sweep's state (adjoints, correlations, checkpoints) only when it runs
+  const bool reverse = grad || dq0;
   DevBuf d_syn, d_res, d_lq, d_lb, d_w, d_cp, d_mac, d_qn;
   d_syn.alloc(sizeof(float) * (n_macro + 1) * ns);
-  d_res.alloc(sizeof(float) * (n_macro + 1) * ns);
-  d_lq.alloc(sizeof(float) * K * nsim * NB9);
-  d_lb.alloc(sizeof(float) * 3 * K * nsim * NB9);
-  d_w.alloc(sizeof(double) * K * ltsdev::AM_SIZE);
-  d_cp.alloc(sizeof(float) * ncp * K * qs);
-  d_qn.alloc(sizeof(float) * K * qs);
+  if (reverse) {
+    d_res.alloc(sizeof(float) * (n_macro + 1) * ns);
+    d_lq.alloc(sizeof(float) * K * nsim * NB9);
+    d_lb.alloc(sizeof(float) * 3 * K * nsim * NB9);
+    d_w.alloc(sizeof(double) * K * ltsdev::AM_SIZE);
+    d_cp.alloc(sizeof(float) * ncp * K * qs);
+    d_qn.alloc(sizeof(float) * K * qs);
+  }
   // moment-tensor gradient: [source][6] and one pass's source items with their scales
   const int nsrc = (int)h->sources.size();
   DevBuf d_sg, d_sgi, d_sgc;
@@ -1123,13 +1138,13 @@ void adjoint_lts(lts_solver* h, int64_t n_macro, int64_t every, const double* da
   std::vector<size_t> nrec_t(nrec);
   X.adj_sample(h->dst.Q, qs, nsim, G, relem, rphi, nrec, d_syn.get<float>(), stream);
   for (int64_t m = 0; m < n_macro; ++m) {
-    if (m % every == 0) dcopy(cp + (m / every) * K * qs, h->dst.Q, qbytes);
+    if (reverse && m % every == 0) dcopy(cp + (m / every) * K * qs, h->dst.Q, qbytes);
     advance_steps(h, period, stream);
     X.adj_sample(h->dst.Q, qs, nsim, G, relem, rphi, nrec, d_syn.get<float>() + (m + 1) * ns, stream);
   }
   for (int r = 0; r < nrec; ++r) nrec_t[r] = h->receivers[r].t.size();
   const size_t seis_fwd = h->seis_used;
-  dcopy(d_qn.p, h->dst.Q, qbytes);
+  if (reverse) dcopy(d_qn.p, h->dst.Q, qbytes);
   std::vector<float> syn((size_t)(n_macro + 1) * ns);
   ck(cudaMemcpyAsync(syn.data(), d_syn.p, sizeof(float) * syn.size(), cudaMemcpyDeviceToHost, stream), "samples");
   ck(cudaStreamSynchronize(stream), "synchronize");
@@ -1340,7 +1355,7 @@ void adjoint_lts(lts_solver* h, int64_t n_macro, int64_t every, const double* da
       for (int64_t k = 0; k < K; ++k)
         for (int q = 0; q < NB9; ++q)
           dq0[((size_t)f * K + k) * NB9 + q] = lq[((size_t)h->iperm[k] * nsim + f) * NB9 + q];
-  if (grad) contract_gradient(h, d_w.get<double>(), grad, stream);
+  if (grad) contract_gradient(geo, d_w.get<double>(), grad, stream);
 }
 
 }  // namespace
@@ -2143,21 +2158,11 @@ int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* 
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
     const int64_t K = h->mesh.K;
     const int B = X.B;
-    // ---- explicit operators (internal order) and face links
-    std::vector<float> amat((size_t)K * ltsdev::AM_SIZE);
+    // ---- face links (internal order)
     std::vector<int> fwd(8 * K, -1), back(8 * K, 0);
     for (int64_t k = 0; k < K; ++k) {
       const int64_t nk = h->iperm[k];
-      double S[3][81], Am[81], Ap[81];
-      element_operators<double>(h, k, -1, -1, S, nullptr, nullptr);
-      for (int c = 0; c < 3; ++c)
-        for (int q = 0; q < 81; ++q) amat[nk * ltsdev::AM_SIZE + ltsdev::AM_STAR + c * 81 + q] = (float)S[c][q];
       for (int i = 0; i < 4; ++i) {
-        element_operators<double>(h, k, i, -1, nullptr, Am, Ap);
-        for (int q = 0; q < 81; ++q) {
-          amat[nk * ltsdev::AM_SIZE + ltsdev::AM_LOC + i * 81 + q] = (float)Am[q];
-          amat[nk * ltsdev::AM_SIZE + ltsdev::AM_NBR + i * 81 + q] = (float)Ap[q];
-        }
         const int64_t nb = h->mesh.nbr[4 * k + i];
         if (nb < 0) continue;
         const int ip = h->mesh.nbr_face[4 * k + i];
@@ -2173,9 +2178,17 @@ int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* 
       relem[r] = (int)h->iperm[h->receivers[r].elem];
       for (int b = 0; b < B; ++b) rphi[(size_t)r * B + b] = (float)h->receivers[r].phi[b];
     }
-    // ---- device buffers
+    // ---- device buffers; the explicit operators (reverse sweep only) are built on the device
     DevBuf d_amat, d_fwd, d_back, d_relem, d_rphi;
-    d_amat.alloc(sizeof(float) * amat.size());
+    GeoBufs geo_bufs;
+    GradGeom geo{};
+    if (grad || dq0) {
+      geo = upload_geometry(h, geo_bufs, stream);
+      d_amat.alloc(sizeof(float) * K * ltsdev::AM_SIZE);
+      const long long nt = 5 * K;
+      k_build_amat<<<(unsigned)((nt + 127) / 128), 128, 0, stream>>>(geo, d_amat.get<float>());
+      ck(cudaGetLastError(), "operator build");
+    }
     d_fwd.alloc(sizeof(int) * fwd.size());
     d_back.alloc(sizeof(int) * back.size());
     d_relem.alloc(sizeof(int) * nrec);
@@ -2183,7 +2196,6 @@ int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* 
     auto up = [&](void* dst, const void* src, size_t bytes) {
       ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, stream), "adjoint upload");
     };
-    up(d_amat.p, amat.data(), sizeof(float) * amat.size());
     up(d_fwd.p, fwd.data(), sizeof(int) * fwd.size());
     up(d_back.p, back.data(), sizeof(int) * back.size());
     up(d_relem.p, relem.data(), sizeof(int) * nrec);
@@ -2192,7 +2204,7 @@ int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* 
     make_adj_tables(h, tabs);
     // the phase-level sweep for every cluster count (one cluster: a macro step is one step)
     adjoint_lts(h, n_steps / period, every, data, misfit, grad, synth_out, dq0, stream, d_amat, d_fwd, d_back,
-                d_relem, d_rphi, nrec, tabs);
+                d_relem, d_rphi, nrec, tabs, geo);
   });
 }
 

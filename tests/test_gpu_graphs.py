@@ -39,7 +39,7 @@ def _run(graphs, switch_engine=False):
             gpu.set_contraction("fp32")
         if switch_engine and step == 4:
             gpu.set_contraction("sparse")
-            gpu.set_tile(1)
+            gpu.set_tile(0)
         gpu.advance_steps(4)
     traces = [gpu.seismogram(r) for r in rids]
     return gpu.get_dofs(), traces, gpu.info()["launches"]
