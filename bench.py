@@ -435,8 +435,9 @@ def main():
                     help="elastic order-5 workload: 786,432 tets, 3 layers, 4 clusters (a parity config)")
     ap.add_argument("--partition", type=int, default=1,
                     help="emulated partitioned run: P weighted parts exchanging face-local messages")
-    ap.add_argument("--tile", type=int, default=0, choices=[0, 1],
-                    help="with an explicit --contraction sparse: the neighbour kernel's 8 (0) or 4 (1) elements per CTA")
+    ap.add_argument("--tile", type=int, default=1, choices=[0, 1],
+                    help="with an explicit --contraction sparse: the neighbour kernel's 8 (0) or 4 (1, the "
+                         "library default) elements per CTA")
     ap.add_argument("--contraction", default="auto", choices=["auto", "fp32", "sparse", "tf32x3", "tf32"],
                     help="engine of the time/volume contractions: FP32 CUDA cores or tensor cores; auto runs "
                          "the autotuner over the FP32-accurate engines and the grid shapes")
