@@ -1095,7 +1095,7 @@ void contract_gradient(GradGeom g, const double* d_w, double* grad, cudaStream_t
 void adjoint_lts(lts_solver* h, int64_t n_macro, int64_t every, const double* data, double* misfit, double* grad,
                  double* synth_out, double* dq0, cudaStream_t stream, const DevBuf& d_amat, const DevBuf& d_fwd,
                  const DevBuf& d_back, const DevBuf& d_relem, const DevBuf& d_rphi, int nrec, const AdjTables& tabs,
-                 const GradGeom& geo) {
+                 const GradGeom& geo, const DevBuf& d_own, const std::vector<int64_t>& own_off) {
   const Launchers& X = h->L;
   const int64_t K = h->mesh.K;
   const int B = X.B, NB9 = 9 * B;
@@ -1259,13 +1259,15 @@ void adjoint_lts(lts_solver* h, int64_t n_macro, int64_t every, const double* da
           X.adj_pred(h->dops, aa, pa, pa.end, stream);
       } else {
         // a buffer owner differs by at most one cluster from the receivers it feeds, so
-        // the owners of this pass are the elements of clusters 0..top+1
+        // the owners of this pass are among the elements of clusters 0..top+1 (the buffer
+        // snapshots' extent); one CTA for each that has an active receiver
         const int owners = (int)h->cbeg[std::min(ph.top + 2, h->nc)];
         aa.B1s = base;
         aa.B2s = base + (size_t)owners * bs;
         aa.B3s = base + 2 * (size_t)owners * bs;
         aa.bufs = bs;
-        X.adj_nbr(h->dops, aa, pa, owners, stream);
+        aa.owners = d_own.get<int>() + own_off[ph.top];
+        X.adj_nbr(h->dops, aa, pa, (int)(own_off[ph.top + 1] - own_off[ph.top]), stream);
       }
     }
     X.adj_source(d_lq.get<float>(), nsim, relem, rphi, d_res.get<float>() + m * ns, nrec, stream);
@@ -2172,6 +2174,22 @@ int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* 
         back[8 * nk + 2 * i + 1] = i * 3 + h->mesh.nbr_orient[4 * nb + ip];
       }
     }
+    // per cluster level t, the buffer owners of a neighbour pass whose highest cluster is t
+    // that have a receiver in clusters 0..t (internal order, ascending)
+    std::vector<int> own;
+    std::vector<int64_t> own_off(1, 0);
+    for (int t = 0; t < h->nc; ++t) {
+      const int64_t nown = h->cbeg[std::min(t + 2, h->nc)], nact = h->cbeg[t + 1];
+      for (int64_t kn = 0; kn < nown; ++kn)
+        for (int i = 0; i < 4; ++i) {
+          const int k = fwd[8 * kn + 2 * i];
+          if (k >= 0 && k < nact) {
+            own.push_back((int)kn);
+            break;
+          }
+        }
+      own_off.push_back((int64_t)own.size());
+    }
     std::vector<int> relem(nrec);
     std::vector<float> rphi((size_t)nrec * B);
     for (int r = 0; r < nrec; ++r) {
@@ -2179,7 +2197,7 @@ int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* 
       for (int b = 0; b < B; ++b) rphi[(size_t)r * B + b] = (float)h->receivers[r].phi[b];
     }
     // ---- device buffers; the explicit operators (reverse sweep only) are built on the device
-    DevBuf d_amat, d_fwd, d_back, d_relem, d_rphi;
+    DevBuf d_amat, d_fwd, d_back, d_relem, d_rphi, d_own;
     GeoBufs geo_bufs;
     GradGeom geo{};
     if (grad || dq0) {
@@ -2198,13 +2216,15 @@ int lts_misfit_gradient(lts_t* h, int64_t n_steps, int64_t every, const double* 
     };
     up(d_fwd.p, fwd.data(), sizeof(int) * fwd.size());
     up(d_back.p, back.data(), sizeof(int) * back.size());
+    d_own.alloc(sizeof(int) * own.size());
+    up(d_own.p, own.data(), sizeof(int) * own.size());
     up(d_relem.p, relem.data(), sizeof(int) * nrec);
     up(d_rphi.p, rphi.data(), sizeof(float) * rphi.size());
     AdjTables tabs;
     make_adj_tables(h, tabs);
     // the phase-level sweep for every cluster count (one cluster: a macro step is one step)
     adjoint_lts(h, n_steps / period, every, data, misfit, grad, synth_out, dq0, stream, d_amat, d_fwd, d_back,
-                d_relem, d_rphi, nrec, tabs, geo);
+                d_relem, d_rphi, nrec, tabs, geo, d_own, own_off);
   });
 }
 

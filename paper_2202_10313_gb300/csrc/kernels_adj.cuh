@@ -119,6 +119,8 @@ struct AdjLtsArgs {
   const float* amat;
   const int* fwd;
   const int* back;
+  const int* owners;                  // neighbour reverse: the pass's buffer owners with an active
+                                      // receiver (one CTA each), or null: owner = CTA index
   const int* meta;
   double* W;                          // [K][AM_SIZE], per-pass sums in FP32 added in FP64
   const float *KT, *FtT, *FhT, *FbT;  // transposed operator tables (see AdjTables)
@@ -653,7 +655,7 @@ __global__ void __launch_bounds__(AdjNT<O>::value) k_adj_nbr(DevOps ops, AdjLtsA
   __shared__ float sLk[4][NB9], sX[4][NB9];
   __shared__ float sLF[4][9 * F], sXF[4][9 * F], sU[4][9 * F];
   __shared__ int sF[8], sBk[8];
-  const int kn = blockIdx.x, t = threadIdx.x, nt = blockDim.x;
+  const int kn = a.owners ? a.owners[blockIdx.x] : (int)blockIdx.x, t = threadIdx.x, nt = blockDim.x;
   if (t < 8) {
     sF[t] = a.fwd[kn * 8 + t];
     sBk[t] = a.back[kn * 8 + t];

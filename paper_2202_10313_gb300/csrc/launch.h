@@ -180,7 +180,7 @@ struct Impl {
     if (grid > 0) k_adj_pred_sp<O><<<grid, A::NT, A::TOTAL * sizeof(float), st>>>(a, p);
   }
   static void adj_nbr(const DevOps& o, const AdjLtsArgs& a, const PhaseArgs& p, int K, cudaStream_t st) {
-    k_adj_nbr<O><<<K, AdjNT<O>::value, 0, st>>>(o, a, p);
+    if (K > 0) k_adj_nbr<O><<<K, AdjNT<O>::value, 0, st>>>(o, a, p);
   }
   static void energy(const float* Q, long long qs, int nsim, int fg, const double* emat, int K, double* partial,
                      int nblocks, cudaStream_t st) {
