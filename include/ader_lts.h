@@ -194,19 +194,18 @@ int lts_transfer_bytes(lts_t* h, int64_t* h2d, int64_t* d2h);
 
 /* Contraction engine of the time and volume kernels (Sec. IV: the products of the DOFs
  * with the stiffness matrices K_c). LTS_CONTRACT_FP32: FP32 CUDA cores, dense degree
- * blocks (the paper's block sparsity; default for fused simulations).
+ * blocks (the paper's block sparsity).
  * LTS_CONTRACT_TF32X3: 5th-generation tensor cores, every operand split into two tf32
  * parts and the three leading products accumulated in FP32 (FP32-level accuracy).
  * LTS_CONTRACT_TF32: tensor cores on the rounded tf32 parts only (about 1e-3 relative
- * error per product). LTS_CONTRACT_SPARSE (default for one simulation): FP32 CUDA cores with
+ * error per product). LTS_CONTRACT_SPARSE (the default): FP32 CUDA cores with
  * the products of K_c, of the face matrices F~_i and of their transposes generated at build
  * time from the nonzero entries only (Sec. IV-A "all sparsity"), in the predict kernel and
  * in a neighbour kernel that forms X F-_{j,h} as (X F~_j) R_h (R_h the face-basis map of the
  * orientation); with fused simulations it runs (element, simulation) slots, and a
- * partitioned run keeps the other engines' neighbour kernel. With one simulation the
- * adjoint's reverse predict pass (lts_misfit_gradient) uses the same generated products
- * (their transposed forms); every other engine, and fused runs, take its dense-block
- * kernel. The tensor-core engines' surface products run on CUDA cores. Takes effect at the next lts_advance. Errors: LTS_ERR_ARG for an unknown mode or a
+ * partitioned run keeps the other engines' neighbour kernel. The adjoint's reverse predict
+ * pass (lts_misfit_gradient) uses the same generated products (their transposed forms);
+ * every other engine takes its dense-block kernel. The tensor-core engines' surface products run on CUDA cores. Takes effect at the next lts_advance. Errors: LTS_ERR_ARG for an unknown mode or a
  * mode the handle's shape has no kernel for (tensor cores: order 3 with one simulation).
  * A tensor-core wait that gives up (bounded, about one second)
  * makes the next synchronising call return LTS_ERR_TIMEOUT. */

@@ -1251,9 +1251,9 @@ void adjoint_lts(lts_solver* h, int64_t n_macro, int64_t every, const double* da
       const float* base = reinterpret_cast<const float*>(snap + snap_off[pi]);
       if (ph.kind == 1) {
         aa.Qs = base;
-        // the sparse engine's reverse predict serves one simulation; fused runs and the
-        // other engines take the dense-block kernel
-        if (nsim == 1 && h->contraction == LTS_CONTRACT_SPARSE && X.adj_pred_sp)
+        // the sparse engine's reverse predict (one or fused simulations); the other engines
+        // take the dense-block kernel
+        if (h->contraction == LTS_CONTRACT_SPARSE && X.adj_pred_sp)
           X.adj_pred_sp(aa, pa, pa.end, stream);
         else
           X.adj_pred(h->dops, aa, pa, pa.end, stream);
@@ -1387,7 +1387,7 @@ int lts_create(int order, int n_mech, int n_fused, int device, lts_t** out) {
     // one simulation: the sparse-product kernels by default (the fastest FP32 engine there;
     // with fused simulations the dense-block kernels, whose slots keep the simulations of an
     // element in the innermost 16 bytes, are faster)
-    if (h->L.predict_sp && n_fused == 1) h->contraction = LTS_CONTRACT_SPARSE;
+    if (h->L.predict_sp) h->contraction = LTS_CONTRACT_SPARSE;
     if (device >= 0) {
       ck(cudaSetDevice(device), "cudaSetDevice");
       ck(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device), "device attribute");

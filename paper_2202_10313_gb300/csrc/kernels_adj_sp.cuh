@@ -1,5 +1,5 @@
-// k_adj_pred_sp: the reverse of a predict pass of the clustered-LTS adjoint (elastic, one
-// simulation) with the operator products in generated sparse form, the counterpart of
+// k_adj_pred_sp: the reverse of a predict pass of the clustered-LTS adjoint (elastic, one or
+// fused simulations) with the operator products in generated sparse form, the counterpart of
 // k_predict_sp for the transposed scheme. The arithmetic is that of k_adj_pred (see there
 // and kernels_adj.cuh for the derivation); only the organisation differs:
 //   row phase:    thread = (part, pair), pair = (element e, quantity row r); the thread keeps
@@ -168,259 +168,266 @@ __global__ void __launch_bounds__(AdjSpCfg<O>::NT, 2) k_adj_pred_sp(AdjLtsArgs a
       sAl[e * 432 + (x / 9) * 12 + x % 9] = (k0 + e < a.end) ? __ldg(a.amat + (size_t)(k0 + e) * AM_SIZE + AM_LOC + x) : 0.f;
     }
     for (int q = tid; q < NE * 243; q += NT) sWc[q] = 0.f;
-    // D_0 = Q before the pass (this column)
     const int meta = valid ? a.meta[k] : 0;
     const int cl = meta & 0xff;
-    float T[9];
-    {
-      float v[9];
-#pragma unroll
-      for (int r = 0; r < 9; ++r) v[r] = 0.f;
-      if (valid) {
-        const float* q = a.Qs + (size_t)k * a.qs + b;
-#pragma unroll
-        for (int r = 0; r < 9; ++r) v[r] = __ldg(q + r * B);
-      }
-      if (act) {
-#pragma unroll
-        for (int r = 0; r < 9; ++r) {
-          sX[b * XP + col + r] = v[r];
-          sD[b * XP + col + r] = v[r];
-          T[r] = ph.coef[cl][0] * v[r];
-        }
-      }
-    }
-    __syncthreads();
-    {
-      // the next batch's inputs into L2 while this batch computes: operator matrices, Q,
-      // lambda and lambda_B1 (128-byte lines)
-      const int kn = k0 + gridDim.x * NE;
-      if (kn < a.end) {
-        const int nn = min(NE, a.end - kn);
-        const long long la = (long long)nn * AM_SIZE, lqn = (long long)nn * 9 * B, lQ = (long long)nn * a.qs;
-        const float* pa = a.amat + (size_t)kn * AM_SIZE;
-        const float* pq = a.Qs + (size_t)kn * a.qs;
-        const float* pl = a.lq + (size_t)kn * 9 * B;
-        const float* pb = a.lb1 + (size_t)kn * 9 * B;
-        for (long long off = 32LL * tid; off < la; off += 32LL * NT) asm volatile("prefetch.global.L2 [%0];" ::"l"(pa + off));
-        for (long long off = 32LL * tid; off < lQ; off += 32LL * NT) asm volatile("prefetch.global.L2 [%0];" ::"l"(pq + off));
-        for (long long off = 32LL * tid; off < lqn; off += 32LL * NT) {
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(pl + off));
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(pb + off));
-        }
-      }
-    }
-    const float* Sk = sStar + es * 108;
-    // ---- forward time kernel: D_{d+1} = sum_c S_c D_d K_c^T (variant d: D_d on nbasis(O - d)
-    // modes, D_{d+1} on nbasis(O - 1 - d))
-#pragma unroll 1
-    for (int d = 0; d < O - 1; ++d) {
-      if (ract) sp_time_adj<O, XP>(part, d, sX + pair, sW + pair);
-      __syncthreads();
-      const int nout = nbasis(O - 1 - d);
-      if (act) {
+    // fused runs take the simulations of the batch in turn: the operator matrices are staged
+    // once, W_c sums over the simulations (in order) and W-_i receives one addition per
+    // simulation, in order
+    for (int sim = 0; sim < a.nsim; ++sim) {
+      // this simulation's adjoints [element][simulation][9][B]
+      const size_t ao = ((size_t)k * a.nsim + sim) * (9 * B) + b;
+      // D_0 = Q before the pass (this column; simulation-blocked state, groups of G)
+      float T[9];
+      {
         float v[9];
 #pragma unroll
         for (int r = 0; r < 9; ++r) v[r] = 0.f;
-        if (b < nout) {
+        if (valid) {
+          const float* q = a.Qs + (size_t)k * a.qs + (size_t)(sim / a.G) * (9 * B * a.G) + sim % a.G + (size_t)b * a.G;
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            float y[9];
+          for (int r = 0; r < 9; ++r) v[r] = __ldg(q + (size_t)r * B * a.G);
+        }
+        if (act) {
 #pragma unroll
-            for (int s = 0; s < 9; ++s) y[s] = sW[(c * B + b) * XP + col + s];
-            star_acc<false>(Sk + c * 36, y, v);
+          for (int r = 0; r < 9; ++r) {
+            sX[b * XP + col + r] = v[r];
+            sD[b * XP + col + r] = v[r];
+            T[r] = ph.coef[cl][0] * v[r];
           }
-        }
-        const float c1 = ph.coef[cl][d + 1];
-#pragma unroll
-        for (int r = 0; r < 9; ++r) {
-          T[r] = fmaf(c1, v[r], T[r]);
-          sX[b * XP + col + r] = v[r];
-        }
-        if (d + 1 <= O - 2 && b < nout) {
-          float* dp = sD + (adj_drow(O, d + 1) + b) * XP + col;
-#pragma unroll
-          for (int r = 0; r < 9; ++r) dp[r] = v[r];
         }
       }
       __syncthreads();
-    }
-    // ---- volume: V_c = lambda K_c^T (on nbasis(O - 1) modes), mu = -sum_c S_c^T V_c,
-    // W_c -= V_c T^T
-    float lam[9], mu[9], muh[9];
-#pragma unroll
-    for (int r = 0; r < 9; ++r) lam[r] = 0.f;
-    if (valid) {
-      const float* lp = a.lq + (size_t)k * (9 * B) + b;
-#pragma unroll
-      for (int r = 0; r < 9; ++r) lam[r] = lp[r * B];
-    }
-    if (act) {
-#pragma unroll
-      for (int r = 0; r < 9; ++r) {
-        sX[b * XP + col + r] = lam[r];
-        sT[b * XP + col + r] = T[r];
+      if (sim == 0) {
+        // the next batch's inputs into L2 while this batch computes: operator matrices, Q,
+        // lambda and lambda_B1 of every simulation (128-byte lines)
+        const int kn = k0 + gridDim.x * NE;
+        if (kn < a.end) {
+          const int nn = min(NE, a.end - kn);
+          const long long la = (long long)nn * AM_SIZE, lqn = (long long)nn * a.nsim * 9 * B, lQ = (long long)nn * a.qs;
+          const float* pa = a.amat + (size_t)kn * AM_SIZE;
+          const float* pq = a.Qs + (size_t)kn * a.qs;
+          const float* pl = a.lq + (size_t)kn * a.nsim * 9 * B;
+          const float* pb = a.lb1 + (size_t)kn * a.nsim * 9 * B;
+          for (long long off = 32LL * tid; off < la; off += 32LL * NT) asm volatile("prefetch.global.L2 [%0];" ::"l"(pa + off));
+          for (long long off = 32LL * tid; off < lQ; off += 32LL * NT) asm volatile("prefetch.global.L2 [%0];" ::"l"(pq + off));
+          for (long long off = 32LL * tid; off < lqn; off += 32LL * NT) {
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(pl + off));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(pb + off));
+          }
+        }
       }
-    }
-    __syncthreads();
-    if (ract) sp_time_adj<O, XP>(part, 0, sX + pair, sW + pair);
-    __syncthreads();
-    constexpr int NV = nbasis(O - 1);
-    {
-      float w[9];
-#pragma unroll
-      for (int r = 0; r < 9; ++r) w[r] = 0.f;
-      if (act && b < NV) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
+      const float* Sk = sStar + es * 108;
+      // ---- forward time kernel: D_{d+1} = sum_c S_c D_d K_c^T (variant d: D_d on nbasis(O - d)
+      // modes, D_{d+1} on nbasis(O - 1 - d))
+#pragma unroll 1
+      for (int d = 0; d < O - 1; ++d) {
+        if (ract) sp_time_adj<O, XP>(part, d, sX + pair, sW + pair);
+        __syncthreads();
+        const int nout = nbasis(O - 1 - d);
+        if (act) {
           float v[9];
 #pragma unroll
-          for (int s = 0; s < 9; ++s) v[s] = sW[(c * B + b) * XP + col + s];
-          star_acc<true>(Sk + c * 36, v, w);
+          for (int r = 0; r < 9; ++r) v[r] = 0.f;
+          if (b < nout) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              float y[9];
+#pragma unroll
+              for (int s = 0; s < 9; ++s) y[s] = sW[(c * B + b) * XP + col + s];
+              star_acc<false>(Sk + c * 36, y, v);
+            }
+          }
+          const float c1 = ph.coef[cl][d + 1];
+#pragma unroll
+          for (int r = 0; r < 9; ++r) {
+            T[r] = fmaf(c1, v[r], T[r]);
+            sX[b * XP + col + r] = v[r];
+          }
+          if (d + 1 <= O - 2 && b < nout) {
+            float* dp = sD + (adj_drow(O, d + 1) + b) * XP + col;
+#pragma unroll
+            for (int r = 0; r < 9; ++r) dp[r] = v[r];
+          }
         }
+        __syncthreads();
       }
+      // ---- volume: V_c = lambda K_c^T (on nbasis(O - 1) modes), mu = -sum_c S_c^T V_c,
+      // W_c -= V_c T^T
+      float lam[9], mu[9], muh[9];
 #pragma unroll
-      for (int r = 0; r < 9; ++r) mu[r] = -w[r];
-    }
-    star_corr<B, XP, NE, NT>(sW, sT, 0, 0, NV, true, sWc, tid);
-    __syncthreads();
-    // ---- local surface: LF_i = lambda F~_i and TF_i = T F~_i (row phase)
-    if (ract) {
-      sp_trace<O, XP>(part, sX + pair, sW + pair);
-      sp_trace<O, XP>(part, sT + pair, sW + 4 * F * XP + pair);
-    }
-    __syncthreads();
-    // W-_i += LF_i TF_i^T: one writer per entry (one simulation, one pass)
-    for (int j = tid; j < 36 * NE; j += NT) {
-      const int e = j / 36, i = (j / 9) % 4, rb = (j / 3) % 3, sb = j % 3;
-      float acc[3][3];
+      for (int r = 0; r < 9; ++r) lam[r] = 0.f;
+      if (valid) {
+        const float* lp = a.lq + ao;
 #pragma unroll
-      for (int ii = 0; ii < 3; ++ii)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) acc[ii][q] = 0.f;
-      const float* x = sW + i * F * XP + 9 * e + 3 * rb;
-      const float* y = sW + (4 + i) * F * XP + 9 * e + 3 * sb;
-      for (int f = 0; f < F; ++f) {
-        float xv[3], yv[3];
-#pragma unroll
-        for (int ii = 0; ii < 3; ++ii) {
-          xv[ii] = x[f * XP + ii];
-          yv[ii] = y[f * XP + ii];
-        }
-#pragma unroll
-        for (int ii = 0; ii < 3; ++ii)
-#pragma unroll
-          for (int q = 0; q < 3; ++q) acc[ii][q] = fmaf(xv[ii], yv[q], acc[ii][q]);
+        for (int r = 0; r < 9; ++r) lam[r] = lp[r * B];
       }
-      if (k0 + e < a.end) {
-        double* Wk = a.W + (size_t)(k0 + e) * AM_SIZE + AM_LOC + i * 81 + (3 * rb) * 9 + 3 * sb;
-#pragma unroll
-        for (int ii = 0; ii < 3; ++ii)
-#pragma unroll
-          for (int q = 0; q < 3; ++q) atomicAdd(Wk + ii * 9 + q, (double)acc[ii][q]);
-      }
-    }
-    __syncthreads();
-    // U_i = A-_i^T LF_i per (element, face, face mode), over LF_i
-    for (int j = tid; j < NE * 4 * F; j += NT) {
-      const int e = j / (4 * F), i = (j / F) % 4, f = j % F;
-      float* lp = sW + (i * F + f) * XP + 9 * e;
-      float lf[9], u[9];
-#pragma unroll
-      for (int s = 0; s < 9; ++s) {
-        lf[s] = lp[s];
-        u[s] = 0.f;
-      }
-      const float* Am = sAl + e * 432 + i * 108;
-#pragma unroll
-      for (int s = 0; s < 9; ++s) {
-        const float4 a0 = *reinterpret_cast<const float4*>(Am + s * 12);
-        const float4 a1 = *reinterpret_cast<const float4*>(Am + s * 12 + 4);
-        const float a8 = Am[s * 12 + 8];
-        u[0] = fmaf(a0.x, lf[s], u[0]);
-        u[1] = fmaf(a0.y, lf[s], u[1]);
-        u[2] = fmaf(a0.z, lf[s], u[2]);
-        u[3] = fmaf(a0.w, lf[s], u[3]);
-        u[4] = fmaf(a1.x, lf[s], u[4]);
-        u[5] = fmaf(a1.y, lf[s], u[5]);
-        u[6] = fmaf(a1.z, lf[s], u[6]);
-        u[7] = fmaf(a1.w, lf[s], u[7]);
-        u[8] = fmaf(a8, lf[s], u[8]);
-      }
-#pragma unroll
-      for (int r = 0; r < 9; ++r) lp[r] = u[r];
-    }
-    // the adjoints of the buffers this pass wrote: lambda_B1 (+ lambda_B3) join mu,
-    // lambda_B2 is mu_half; reset here (lambda_B3 survives an accumulation)
-    float l13[9];
-#pragma unroll
-    for (int r = 0; r < 9; ++r) l13[r] = muh[r] = 0.f;
-    if (valid) {
-      const bool finer = meta & FLAG_FINER, coarser = meta & FLAG_COARSER;
-      const bool even = ph.parity[cl] == 0;
-      const size_t o = (size_t)k * (9 * B) + b;
-#pragma unroll
-      for (int r = 0; r < 9; ++r) {
-        l13[r] = a.lb1[o + r * B] + (coarser ? a.lb3[o + r * B] : 0.f);
-        if (finer) muh[r] = a.lb2[o + r * B];
-      }
-#pragma unroll
-      for (int r = 0; r < 9; ++r) {
-        a.lb1[o + r * B] = 0.f;
-        if (coarser && even) a.lb3[o + r * B] = 0.f;
-        if (finer) a.lb2[o + r * B] = 0.f;
-      }
-    }
-    __syncthreads();
-    // mu += sum_i U_i F~_i^T (row phase, into the row operand's place)
-    if (ract) sp_tproj<O, XP>(part, sW + pair, sX + pair);
-    __syncthreads();
-    // ---- reverse time kernel: G_{O-1} = c_{O-1} mu + c'_{O-1} mu_half (over this column's
-    // face sum: read and written by the same thread), then G_d = c_d mu + c'_d mu_half +
-    // sum_c S_c^T Z_c with Z_c = G_{d+1} K_c, and W_c += Z_c D_d^T
-    if (act) {
-#pragma unroll
-      for (int r = 0; r < 9; ++r) {
-        mu[r] += sX[b * XP + col + r];
-        mu[r] += l13[r];
-        sX[b * XP + col + r] = ph.coef[cl][O - 1] * mu[r] + ph.hcoef[cl][O - 1] * muh[r];
-      }
-    }
-    __syncthreads();
-    float g0[9];
-#pragma unroll 1
-    for (int d = O - 2; d >= 0; --d) {
-      if (ract) sp_kvol<O, XP>(part, d, sX + pair, sW + pair);
-      __syncthreads();
-      const int nout = nbasis(O - d);
       if (act) {
-        float gv[9];
 #pragma unroll
-        for (int r = 0; r < 9; ++r) gv[r] = ph.coef[cl][d] * mu[r] + ph.hcoef[cl][d] * muh[r];
-        // Z_c[0] = 0 (not written)
-        if (b >= 1 && b < nout) {
+        for (int r = 0; r < 9; ++r) {
+          sX[b * XP + col + r] = lam[r];
+          sT[b * XP + col + r] = T[r];
+        }
+      }
+      __syncthreads();
+      if (ract) sp_time_adj<O, XP>(part, 0, sX + pair, sW + pair);
+      __syncthreads();
+      constexpr int NV = nbasis(O - 1);
+      {
+        float w[9];
+#pragma unroll
+        for (int r = 0; r < 9; ++r) w[r] = 0.f;
+        if (act && b < NV) {
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            float z[9];
+            float v[9];
 #pragma unroll
-            for (int r = 0; r < 9; ++r) z[r] = sW[(c * B + b) * XP + col + r];
-            star_acc<true>(Sk + c * 36, z, gv);
+            for (int s = 0; s < 9; ++s) v[s] = sW[(c * B + b) * XP + col + s];
+            star_acc<true>(Sk + c * 36, v, w);
           }
         }
 #pragma unroll
-        for (int r = 0; r < 9; ++r) {
-          sX[b * XP + col + r] = gv[r];
-          g0[r] = gv[r];
+        for (int r = 0; r < 9; ++r) mu[r] = -w[r];
+      }
+      star_corr<B, XP, NE, NT>(sW, sT, 0, 0, NV, true, sWc, tid);
+      __syncthreads();
+      // ---- local surface: LF_i = lambda F~_i and TF_i = T F~_i (row phase)
+      if (ract) {
+        sp_trace<O, XP>(part, sX + pair, sW + pair);
+        sp_trace<O, XP>(part, sT + pair, sW + 4 * F * XP + pair);
+      }
+      __syncthreads();
+      // W-_i += LF_i TF_i^T: one writer per entry (the simulations in turn)
+      for (int j = tid; j < 36 * NE; j += NT) {
+        const int e = j / 36, i = (j / 9) % 4, rb = (j / 3) % 3, sb = j % 3;
+        float acc[3][3];
+#pragma unroll
+        for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+          for (int q = 0; q < 3; ++q) acc[ii][q] = 0.f;
+        const float* x = sW + i * F * XP + 9 * e + 3 * rb;
+        const float* y = sW + (4 + i) * F * XP + 9 * e + 3 * sb;
+        for (int f = 0; f < F; ++f) {
+          float xv[3], yv[3];
+#pragma unroll
+          for (int ii = 0; ii < 3; ++ii) {
+            xv[ii] = x[f * XP + ii];
+            yv[ii] = y[f * XP + ii];
+          }
+#pragma unroll
+          for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) acc[ii][q] = fmaf(xv[ii], yv[q], acc[ii][q]);
+        }
+        if (k0 + e < a.end) {
+          double* Wk = a.W + (size_t)(k0 + e) * AM_SIZE + AM_LOC + i * 81 + (3 * rb) * 9 + 3 * sb;
+#pragma unroll
+          for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) atomicAdd(Wk + ii * 9 + q, (double)acc[ii][q]);
         }
       }
-      star_corr<B, XP, NE, NT>(sW, sD, adj_drow(O, d), 1, nout, false, sWc, tid);
       __syncthreads();
-    }
-    if (valid) {
-      float* lp = a.lq + (size_t)k * (9 * B) + b;
+      // U_i = A-_i^T LF_i per (element, face, face mode), over LF_i
+      for (int j = tid; j < NE * 4 * F; j += NT) {
+        const int e = j / (4 * F), i = (j / F) % 4, f = j % F;
+        float* lp = sW + (i * F + f) * XP + 9 * e;
+        float lf[9], u[9];
 #pragma unroll
-      for (int r = 0; r < 9; ++r) lp[r * B] = lam[r] + g0[r];
-    }
+        for (int s = 0; s < 9; ++s) {
+          lf[s] = lp[s];
+          u[s] = 0.f;
+        }
+        const float* Am = sAl + e * 432 + i * 108;
+#pragma unroll
+        for (int s = 0; s < 9; ++s) {
+          const float4 a0 = *reinterpret_cast<const float4*>(Am + s * 12);
+          const float4 a1 = *reinterpret_cast<const float4*>(Am + s * 12 + 4);
+          const float a8 = Am[s * 12 + 8];
+          u[0] = fmaf(a0.x, lf[s], u[0]);
+          u[1] = fmaf(a0.y, lf[s], u[1]);
+          u[2] = fmaf(a0.z, lf[s], u[2]);
+          u[3] = fmaf(a0.w, lf[s], u[3]);
+          u[4] = fmaf(a1.x, lf[s], u[4]);
+          u[5] = fmaf(a1.y, lf[s], u[5]);
+          u[6] = fmaf(a1.z, lf[s], u[6]);
+          u[7] = fmaf(a1.w, lf[s], u[7]);
+          u[8] = fmaf(a8, lf[s], u[8]);
+        }
+#pragma unroll
+        for (int r = 0; r < 9; ++r) lp[r] = u[r];
+      }
+      // the adjoints of the buffers this pass wrote: lambda_B1 (+ lambda_B3) join mu,
+      // lambda_B2 is mu_half; reset here (lambda_B3 survives an accumulation)
+      float l13[9];
+#pragma unroll
+      for (int r = 0; r < 9; ++r) l13[r] = muh[r] = 0.f;
+      if (valid) {
+        const bool finer = meta & FLAG_FINER, coarser = meta & FLAG_COARSER;
+        const bool even = ph.parity[cl] == 0;
+        const size_t o = ao;
+#pragma unroll
+        for (int r = 0; r < 9; ++r) {
+          l13[r] = a.lb1[o + r * B] + (coarser ? a.lb3[o + r * B] : 0.f);
+          if (finer) muh[r] = a.lb2[o + r * B];
+        }
+#pragma unroll
+        for (int r = 0; r < 9; ++r) {
+          a.lb1[o + r * B] = 0.f;
+          if (coarser && even) a.lb3[o + r * B] = 0.f;
+          if (finer) a.lb2[o + r * B] = 0.f;
+        }
+      }
+      __syncthreads();
+      // mu += sum_i U_i F~_i^T (row phase, into the row operand's place)
+      if (ract) sp_tproj<O, XP>(part, sW + pair, sX + pair);
+      __syncthreads();
+      // ---- reverse time kernel: G_{O-1} = c_{O-1} mu + c'_{O-1} mu_half (over this column's
+      // face sum: read and written by the same thread), then G_d = c_d mu + c'_d mu_half +
+      // sum_c S_c^T Z_c with Z_c = G_{d+1} K_c, and W_c += Z_c D_d^T
+      if (act) {
+#pragma unroll
+        for (int r = 0; r < 9; ++r) {
+          mu[r] += sX[b * XP + col + r];
+          mu[r] += l13[r];
+          sX[b * XP + col + r] = ph.coef[cl][O - 1] * mu[r] + ph.hcoef[cl][O - 1] * muh[r];
+        }
+      }
+      __syncthreads();
+      float g0[9];
+#pragma unroll 1
+      for (int d = O - 2; d >= 0; --d) {
+        if (ract) sp_kvol<O, XP>(part, d, sX + pair, sW + pair);
+        __syncthreads();
+        const int nout = nbasis(O - d);
+        if (act) {
+          float gv[9];
+#pragma unroll
+          for (int r = 0; r < 9; ++r) gv[r] = ph.coef[cl][d] * mu[r] + ph.hcoef[cl][d] * muh[r];
+          // Z_c[0] = 0 (not written)
+          if (b >= 1 && b < nout) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              float z[9];
+#pragma unroll
+              for (int r = 0; r < 9; ++r) z[r] = sW[(c * B + b) * XP + col + r];
+              star_acc<true>(Sk + c * 36, z, gv);
+            }
+          }
+#pragma unroll
+          for (int r = 0; r < 9; ++r) {
+            sX[b * XP + col + r] = gv[r];
+            g0[r] = gv[r];
+          }
+        }
+        star_corr<B, XP, NE, NT>(sW, sD, adj_drow(O, d), 1, nout, false, sWc, tid);
+        __syncthreads();
+      }
+      if (valid) {
+        float* lp = a.lq + ao;
+#pragma unroll
+        for (int r = 0; r < 9; ++r) lp[r * B] = lam[r] + g0[r];
+      }
+    }  // simulations
     // the batch's star correlations into the FP64 totals (one addition per entry and pass)
     for (int q = tid; q < NE * 243; q += NT) {
       const int e = q / 243;

@@ -46,7 +46,7 @@ struct Launchers {
   void (*adj_src_grad)(const float* lam, int nsim, const SrcItem* items, const double* c, int n, const float* phi,
                        double* g, cudaStream_t);
   void (*adj_pred)(const DevOps&, const AdjLtsArgs&, const PhaseArgs&, int nelem, cudaStream_t);
-  // the same with generated sparse products (one simulation; nullptr for fused instantiations)
+  // the same with generated sparse products (one or fused simulations)
   void (*adj_pred_sp)(const AdjLtsArgs&, const PhaseArgs&, int nelem, cudaStream_t);
   void (*adj_nbr)(const DevOps&, const AdjLtsArgs&, const PhaseArgs&, int K, cudaStream_t);
   // face-local messages of a partitioned run (one simulation)
@@ -107,10 +107,8 @@ struct Impl {
     if constexpr (M == 0) {
       e = cudaFuncSetAttribute(k_adj_pred<O>, cudaFuncAttributeMaxDynamicSharedMemorySize, AdjPredCfg<O>::SMEM_BYTES);
       if (e != cudaSuccess) return e;
-      if constexpr (FG == 1) {
-        e = smem_attrs(k_adj_pred_sp<O>, AdjSpCfg<O>::TOTAL * sizeof(float), true);
-        if (e != cudaSuccess) return e;
-      }
+      e = smem_attrs(k_adj_pred_sp<O>, AdjSpCfg<O>::TOTAL * sizeof(float), true);
+      if (e != cudaSuccess) return e;
     }
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L->blocks_neighbour, k_neighbour<O, M, FG>, C::NTN,
                                                          L->smem_neighbour);
@@ -230,7 +228,7 @@ struct Impl {
       L.adj_source = &adj_source;
       L.adj_src_grad = &adj_src_grad;
       L.adj_pred = &adj_pred;
-      if constexpr (FG == 1) L.adj_pred_sp = &adj_pred_sp;
+      L.adj_pred_sp = &adj_pred_sp;
       L.adj_nbr = &adj_nbr;
     }
     L.energy = &energy;

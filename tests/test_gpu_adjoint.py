@@ -357,8 +357,9 @@ def _fused_inputs(m, order, F, seed):
     return q0s, srcs
 
 
-def _fused_lts(order, m, rho, lam, mu, q0s, rec, srcs, cl, dt, F):
+def _fused_lts(order, m, rho, lam, mu, q0s, rec, srcs, cl, dt, F, engine="sparse"):
     s = binding.Solver(order, 0, device=0, n_fused=F)
+    s.set_contraction(engine)
     s.set_mesh(m["xyz"], m["tet"], m["face_bc"])
     s.set_material(rho, np.sqrt((lam + 2 * mu) / rho), np.sqrt(mu / rho))
     for f, src in enumerate(srcs):
@@ -374,11 +375,13 @@ def _fused_lts(order, m, rho, lam, mu, q0s, rec, srcs, cl, dt, F):
     return s
 
 
+@pytest.mark.parametrize("engine", ["sparse", "fp32"])
 @pytest.mark.parametrize("F,clustered", [(4, True), (8, True), (4, False)])
-def test_fused_adjoint_equals_the_sum_of_single_simulation_adjoints(F, clustered):
+def test_fused_adjoint_equals_the_sum_of_single_simulation_adjoints(F, clustered, engine):
     """F simulations (own sources, initial states and data; shared material) in one adjoint
     sweep: J and the material gradient are the sums of the single-simulation values, the
-    samples and dJ/dQ0 those of each simulation (three forced clusters, or one cluster)."""
+    samples and dJ/dQ0 those of each simulation (three forced clusters, or one cluster); the
+    fused run with either reverse predict kernel, the single runs with the sparse one."""
     order = 4
     m, mat, _, rec, _ = _case(order, seed=20)
     rho, lam, mu = _rlm(mat)
@@ -386,12 +389,12 @@ def test_fused_adjoint_equals_the_sum_of_single_simulation_adjoints(F, clustered
     dt = 1.5e-4
     n = 8 if clustered else 6
     q0s, srcs = _fused_inputs(m, order, F, seed=40)
-    s = _fused_lts(order, m, rho, lam, mu, q0s, rec, srcs, cl, dt, F)
+    s = _fused_lts(order, m, rho, lam, mu, q0s, rec, srcs, cl, dt, F, engine)
     rows = n // 4 + 1 if clustered else n + 1
     _, syn = s.misfit(n, np.zeros((rows, F, 3, 3)), every=1)
     s.close()
     data = syn * 1.04 + 1e-9
-    s = _fused_lts(order, m, rho, lam, mu, q0s, rec, srcs, cl, dt, F)
+    s = _fused_lts(order, m, rho, lam, mu, q0s, rec, srcs, cl, dt, F, engine)
     J, g, syn_f, dq0 = s.misfit_gradient(n, data, every=1, want_dq0=True)
     gsrc = s.source_gradient()   # source f drives simulation f only
     s.close()
