@@ -347,7 +347,8 @@ __global__ void __launch_bounds__(SpCfg<O, M>::NT, 2) k_predict_sp(DevOps ops, D
       float Sv[NS];
 #pragma unroll
       for (int r = 0; r < NS; ++r) Sv[r] = 0.f;
-#pragma unroll
+      // one copy of the face code (the kernel is bound by instruction fetch)
+#pragma unroll 1
       for (int i = 0; i < 4; ++i) {
         const float* pp = sP + (i * B + b) * XP + es * 6;
         float W[6];
@@ -595,7 +596,8 @@ __global__ void __launch_bounds__(SpnCfg<O, M, NE_>::NT, (NE_ == 8 ? 2 : 4))
 #pragma unroll
       for (int r = 0; r < NS; ++r) Sv[r] = 0.f;
       const float* nd = sD + es * NDP;
-#pragma unroll
+      // one copy of the face code (the kernel is bound by instruction fetch)
+#pragma unroll 1
       for (int i = 0; i < 4; ++i) {
         const float* pp = sP + (i * B + b) * XP6 + es * 6;
         float W[6];
