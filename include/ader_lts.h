@@ -329,12 +329,13 @@ int lts_set_adjoint_memory(lts_t* h, uint64_t bytes);
  * every launch directly. */
 int lts_set_graphs(lts_t* h, int enable);
 
-/* Bound of the tensor-core completion waits, in SM cycles (default 2e9, about one second).
- * suppress_commit != 0 is the failure-path test: the kernels issue no tensor-core work, so
- * every wait runs out at the bound, the kernel records the timeout, releases its tensor
- * memory and returns; the next synchronising call returns LTS_ERR_TIMEOUT (and clears the
- * report) while the handle stays usable. The DOFs are then undefined. Errors: LTS_ERR_ARG
- * for cycles <= 0. */
+/* Bound of the kernels' asynchronous-completion waits, in SM cycles (default 2e9, about one
+ * second): the tensor-core completions and the sparse predict kernel's bulk DOF copies (TMA).
+ * suppress_commit != 0 is the failure-path test: the kernels issue no tensor-core work and no
+ * copy, so every wait runs out at the bound, the kernel records the timeout, releases its
+ * tensor memory and returns; the next synchronising call returns LTS_ERR_TIMEOUT (and clears
+ * the report) while the handle stays usable. The DOFs are then undefined. Errors:
+ * LTS_ERR_ARG for cycles <= 0. */
 int lts_set_wait_limit(lts_t* h, int64_t cycles, int suppress_commit);
 
 /* Autotuner over launch configurations: contraction engine (FP32 CUDA cores, sparse

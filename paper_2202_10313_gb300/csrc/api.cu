@@ -683,6 +683,9 @@ PhaseArgs phase_args(const lts_solver* h, const Phase& ph) {
     }
   }
   for (int l = 0; l < 3; ++l) pa.omega[l] = l < (int)h->omega.size() ? (float)h->omega[l] : 0.f;
+  pa.err = h->d_err;
+  pa.wait = h->wait_cycles;
+  pa.suppress = h->suppress_commit;
   pa.begin = 0;
   pa.end = (int)h->cbeg[ph.top + 1];
   for (int l = 0; l <= ph.top; ++l) {

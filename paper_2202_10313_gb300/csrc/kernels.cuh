@@ -134,6 +134,12 @@ struct PhaseArgs {
   float hcoef[MAXC][6];        // (dt_l/2)^(d+1)/(d+1)!
   int parity[MAXC];            // step index parity of each cluster in this phase
   float omega[3];
+  // bounded waits of the asynchronous copies (k_predict_sp): the device error word a kernel
+  // sets when a wait gives up, the bound in SM cycles, and the failure-path test switch
+  // (nothing is copied, so the waits run out)
+  int* err;
+  long long wait;
+  int suppress;
 };
 
 // ------------------------------------------------------------------ helpers

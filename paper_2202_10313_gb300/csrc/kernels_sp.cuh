@@ -27,6 +27,7 @@
 #pragma once
 #include "kernels.cuh"
 #include "sparse_ops.cuh"
+#include "tc.cuh"
 
 namespace ltsdev {
 
@@ -71,7 +72,9 @@ struct SpCfg {
   static constexpr int S_W = rup(S_G + 4 * F * XP, 4); // [4 F][XP]        interface states, 6 rows
   static constexpr int S_E = rup(S_W + 4 * F * XP, 4);
   static constexpr int S_META = rup(S_E + NE * EDP, 4);  // [3][NE] ints: meta, element, simulation
-  static constexpr int TOTAL = rup(S_META + 3 * NE, 4);
+  static constexpr int S_Q = rup(S_META + 3 * NE, 4);      // [NE][QS] one simulation: the batch's DOFs
+  static constexpr int S_BAR = rup(S_Q + NE * C::QS, 4);   // mbarrier of the DOF copy (8 bytes)
+  static constexpr int TOTAL = S_BAR + 4;
 };
 
 // the generated products of order O
@@ -139,6 +142,8 @@ __global__ void __launch_bounds__(SpCfg<O, M>::NT, (SpCfg<O, M>::NT >= 512 ? 1 :
   float* sE = smem + S::S_E;
   int* sMeta = reinterpret_cast<int*>(smem + S::S_META);
   int* sSlot = sMeta + NE;                    // fused: [2][NE] element, simulation of the batch's slots
+  float* sQ = smem + S::S_Q;
+  uint64_t* sBar = reinterpret_cast<uint64_t*>(smem + S::S_BAR);
   const int tid = threadIdx.x;
 
   // column task (slot, mode). One simulation: modes fastest (a warp spans at most two
@@ -158,6 +163,27 @@ __global__ void __launch_bounds__(SpCfg<O, M>::NT, (SpCfg<O, M>::NT >= 512 ? 1 :
   constexpr int RS = FUSED ? B * FUSED_GROUP : B;   // row stride of Q and the buffers
   constexpr int CS = FUSED ? FUSED_GROUP : 1;       // mode stride
   int col = es * 9;                           // this column's pair offset
+  // One simulation: a batch's elements are contiguous, so its DOFs (n x QS floats) arrive in
+  // shared memory by one bulk asynchronous copy (TMA) that thread 0 issues for the next batch
+  // as soon as the current one has read its copy, completing on an mbarrier (one phase per
+  // batch). Every wait is bounded; one that gives up sets the error word and the CTA returns.
+  auto issue_q = [&](int bt) {
+    const int e0 = ph.begin + bt * NE;
+    const uint32_t bytes = (uint32_t)min(NE, ph.end - e0) * C::QS * 4;
+    tc::fence_smem_to_async();
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(sBar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     tc::smem_u32(sQ)),
+                 "l"(st.Q + (size_t)e0 * C::QS), "r"(bytes), "r"(tc::smem_u32(sBar))
+                 : "memory");
+  };
+  uint32_t qpar = 0;
+  if constexpr (!FUSED) {
+    if (tid == 0) tc::mbar_init(sBar, 1);
+    __syncthreads();
+    if (tid == 0 && blockIdx.x < nbatch && !ph.suppress) issue_q(blockIdx.x);
+  }
 
   for (int batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
     const int t0 = batch * NE;
@@ -196,12 +222,24 @@ __global__ void __launch_bounds__(SpCfg<O, M>::NT, (SpCfg<O, M>::NT >= 512 ? 1 :
     const int fs = (FUSED && valid) ? sSlot[NE + es] : 0;
     const size_t qoff = (size_t)g * qs + Slots<FUSED>::sub(fs, NQ, B) + (size_t)b * CS;
     const size_t boff = (size_t)g * bs + Slots<FUSED>::sub(fs, 9, B) + (size_t)b * CS;
+    if constexpr (!FUSED) {
+      // the batch's DOFs have arrived (or the wait gave up: every thread leaves)
+      const bool ok = tc::mbar_wait(sBar, qpar, ph.wait);
+      qpar ^= 1;
+      if (!__syncthreads_and(ok)) {
+        if (tid == 0) {
+          atomicOr(ph.err, 1);
+          tc::mbar_wait(sBar, qpar ^ 1, ph.wait);   // the copy in flight, if any, lands first
+        }
+        return;
+      }
+    }
     float T[NQ], Th[9], Da[NA > 0 ? NA : 1];
     float v[9];
 #pragma unroll
     for (int r = 0; r < 9; ++r) v[r] = 0.f;
     if (valid) {
-      const float* q = st.Q + qoff;
+      const float* q = FUSED ? st.Q + qoff : sQ + es * C::QS + b;
 #pragma unroll
       for (int r = 0; r < 9; ++r) v[r] = q[r * RS];
 #pragma unroll
@@ -318,7 +356,7 @@ __global__ void __launch_bounds__(SpCfg<O, M>::NT, (SpCfg<O, M>::NT >= 512 ? 1 :
         for (int r = 0; r < 9; ++r) V[r] = -out[r];
 #pragma unroll
         for (int l = 0; l < M; ++l) coupling_add(V, T + 9 + 6 * l, ed[12 + 2 * l], ed[13 + 2 * l]);
-        const float* q = st.Q + qoff;
+        const float* q = FUSED ? st.Q + qoff : sQ + es * C::QS + b;
 #pragma unroll
         for (int r = 0; r < 9; ++r) acc[r] = q[r * RS] + V[r];
 #pragma unroll
@@ -344,6 +382,8 @@ __global__ void __launch_bounds__(SpCfg<O, M>::NT, (SpCfg<O, M>::NT >= 512 ? 1 :
       for (int r = 0; r < 6; ++r) wp[r] = w6[r];
     }
     __syncthreads();
+    // the batch's DOF copy has been read: the next batch's copy goes out now
+    if (!FUSED && tid == 0 && batch + (int)gridDim.x < nbatch && !ph.suppress) issue_q(batch + gridDim.x);
     // ---- projection P_i[r'][b] = sum_f W_i[r'][f] F^_i[f][b] (row phase, over Y and G)
     if (pact) sp_proj<O, XP>(part, sW + pair, sP + pair);
     __syncthreads();
@@ -371,12 +411,9 @@ __global__ void __launch_bounds__(SpCfg<O, M>::NT, (SpCfg<O, M>::NT >= 512 ? 1 :
           for (int r = 0; r < 6; ++r) q[(9 + 6 * l + r) * RS] = acc[9 + 6 * l + r] + ph.omega[l] * Sv[NS - 6 + r];
       }
     }
-    const int bn = batch + gridDim.x;                      // this CTA's next batch: its DOFs into L2
+    const int bn = batch + gridDim.x;                      // fused: the next batch's DOFs into L2
     if (bn < nbatch) {
-      if constexpr (!FUSED) {
-        const int en = ph.begin + bn * NE;
-        prefetch_batch_q<NQ, B, 1, NT>(st.Q, qs, en, 0, min(NE, ph.end - en), tid);
-      } else {
+      if constexpr (FUSED) {
         // the simulation groups from the batch's first slot to its last are contiguous
         int e0, f0, e1, f1;
         sl.decode(bn * NE, e0, f0);

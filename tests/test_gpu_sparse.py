@@ -213,3 +213,32 @@ def test_sparse_engine_empty_clusters_and_periodic_gts():
     ora.run_gts(ora.time_step_gts(0.5), 20)
     report_parity("sparse engine: periodic cube, O5, 3 mechanisms, GTS, 20 steps",
                   check_parity(gpu.get_dofs(), ora.Q, 27, TOL))
+
+
+def test_dof_copy_wait_runs_out_and_handle_recovers():
+    """Failure path of the predict kernel's asynchronous DOF copy, without a GPU fault: with
+    the copies suppressed, every bounded wait runs out at a short bound; the next
+    synchronising call reports LTS_ERR_TIMEOUT, and after restoring the defaults the same
+    handle runs correctly against the oracle."""
+    from paper_2202_10313_gb300 import binding
+    m = synth.graded_box(3, 3, 2, 200.0, 100.0, seed=7)
+    mat = synth.random_layers(m, n_layers=2, seed=3)
+    gpu, ora, _ = make_pair(5, 3, m, mat)
+    gpu.set_contraction("sparse")
+    gpu.setup_clusters(1, 0.5)
+    ora.setup_clusters(1, 0.5)
+    K = m["tet"].shape[0]
+    d0 = synth.random_dofs(K, 27, 35, seed=12)
+    gpu.set_wait_limit(200000, suppress_commit=True)
+    gpu.set_dofs(d0)
+    gpu.advance_steps(2)
+    with pytest.raises(binding.LtsError) as ei:
+        gpu.get_dofs()
+    assert ei.value.code == binding.LTS_ERR_TIMEOUT
+    gpu.set_wait_limit()
+    gpu.set_dofs(d0)
+    ora.Q = d0.copy()
+    gpu.advance_steps(2)
+    ora.run_gts(ora.time_step_gts(0.5), 2)
+    err = rel_l2_groups(gpu.get_dofs(), ora.Q, 9)
+    assert err["all"] <= TOL, err
