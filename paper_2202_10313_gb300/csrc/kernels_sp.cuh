@@ -464,7 +464,9 @@ struct SpnCfg {
   static constexpr int S_I = rup(S_D + NE * NDP, 4);                                 // [NE][9] ints
   static constexpr int S_PERM = rup(S_I + NE * 9, 4);                                // [4 NE] ints
   static constexpr int S_SLOT = rup(S_PERM + 4 * NE, 4);                             // [2][NE] ints
-  static constexpr int TOTAL = rup(S_SLOT + 2 * NE, 4);
+  static constexpr int S_Q = rup(S_SLOT + 2 * NE, 4);                                // [NE][QS] one simulation: DOFs
+  static constexpr int S_BAR = rup(S_Q + NE * C::QS, 4);                             // mbarrier (8 bytes)
+  static constexpr int TOTAL = S_BAR + 4;
   static_assert(4 * NE <= 32, "one warp sorts the face slots of a batch");
 };
 
@@ -492,6 +494,8 @@ __global__ void __launch_bounds__(SpnCfg<O, M, NE_>::NT, (NE_ == 8 ? 2 : 4))
   int* sI = reinterpret_cast<int*>(smem + S::S_I);      // per element: nbr[4], code[4], meta
   int* sPerm = reinterpret_cast<int*>(smem + S::S_PERM); // face slots ordered by the neighbour's face j
   int* sSlot = reinterpret_cast<int*>(smem + S::S_SLOT); // fused: element, simulation of the batch's slots
+  float* sQ = smem + S::S_Q;
+  uint64_t* sBar = reinterpret_cast<uint64_t*>(smem + S::S_BAR);
   const int tid = threadIdx.x;
   for (int i = tid; i < 3 * F * F; i += NT) sR[i] = ops.Rh[i];
 
@@ -507,6 +511,13 @@ __global__ void __launch_bounds__(SpnCfg<O, M, NE_>::NT, (NE_ == 8 ? 2 : 4))
   const long long qs = FUSED ? st.qs : C::QS, bs = FUSED ? st.bs : C::BUFS;
   constexpr int RS = FUSED ? B * FUSED_GROUP : B;   // row stride of Q and the buffers
   constexpr int CS = FUSED ? FUSED_GROUP : 1;       // mode stride
+  // One simulation: the batch's DOFs (read by the update, the last phase) arrive by one bulk
+  // asynchronous copy that thread 0 issues at the batch's start, completing on an mbarrier;
+  // the wait before the update is bounded, as in k_predict_sp.
+  uint32_t qpar = 0;
+  if constexpr (!FUSED) {
+    if (tid == 0) tc::mbar_init(sBar, 1);
+  }
 
   for (int batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
     const int t0 = batch * NE;
@@ -533,10 +544,17 @@ __global__ void __launch_bounds__(SpnCfg<O, M, NE_>::NT, (NE_ == 8 ? 2 : 4))
       sI[i] = v;
     }
     if constexpr (!FUSED) {
-      const int bn = batch + gridDim.x;
-      if (bn < nbatch) {
-        const int en = ph.begin + bn * NE;
-        prefetch_batch_q<NQ, B, 1, NT>(st.Q, qs, en, 0, min(NE, ph.end - en), tid);
+      // the previous batch's update has read its copy (barrier above)
+      if (tid == 0 && !ph.suppress) {
+        const int e0 = ph.begin + t0;
+        const uint32_t bytes = (uint32_t)min(NE, ph.end - e0) * C::QS * 4;
+        tc::fence_smem_to_async();
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(sBar)), "r"(bytes)
+                     : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         tc::smem_u32(sQ)),
+                     "l"(st.Q + (size_t)e0 * C::QS), "r"(bytes), "r"(tc::smem_u32(sBar))
+                     : "memory");
       }
     }
     __syncthreads();
@@ -628,12 +646,25 @@ __global__ void __launch_bounds__(SpnCfg<O, M, NE_>::NT, (NE_ == 8 ? 2 : 4))
     // ---- projection P_i[r'][b] = sum_f W_i[r'][f] F^_i[f][b] (row phase, over the gathers)
     if (pact) sp_proj<O, XP6>(part, sW + pair6, sP + pair6);
     __syncthreads();
+    if constexpr (!FUSED) {
+      // the batch's DOFs have arrived (or the wait gave up: every thread leaves)
+      const bool ok = tc::mbar_wait(sBar, qpar, ph.wait);
+      qpar ^= 1;
+      if (!__syncthreads_and(ok)) {
+        if (tid == 0) {
+          atomicOr(ph.err, 1);
+          tc::mbar_wait(sBar, qpar ^ 1, ph.wait);   // the copy in flight, if any, lands first
+        }
+        return;
+      }
+    }
     if (valid) {
       constexpr int NS = (M > 0) ? 15 : 9;
       float* q = st.Q + (size_t)g * qs + Slots<FUSED>::sub(fs, NQ, B) + (size_t)b * CS;
+      const float* qr = FUSED ? q : sQ + es * C::QS + b;
       float qv[NQ];
 #pragma unroll
-      for (int r = 0; r < NQ; ++r) qv[r] = q[r * RS];
+      for (int r = 0; r < NQ; ++r) qv[r] = qr[r * RS];
       float Sv[NS];
 #pragma unroll
       for (int r = 0; r < NS; ++r) Sv[r] = 0.f;
