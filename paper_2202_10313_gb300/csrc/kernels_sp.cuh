@@ -52,7 +52,7 @@ struct SpShape<3> {
   static constexpr int NE = 25, NPART = 1;
 };
 
-template <int O, int M>
+template <int O, int M, bool FU = false>
 struct SpCfg {
   using C = Cfg<O, M, 1>;
   static constexpr int B = C::B, F = C::F, NQ = C::NQ, NA = C::NA;
@@ -72,8 +72,13 @@ struct SpCfg {
   static constexpr int S_W = rup(S_G + 4 * F * XP, 4); // [4 F][XP]        interface states, 6 rows
   static constexpr int S_E = rup(S_W + 4 * F * XP, 4);
   static constexpr int S_META = rup(S_E + NE * EDP, 4);  // [3][NE] ints: meta, element, simulation
-  static constexpr int S_Q = rup(S_META + 3 * NE, 4);      // [NE][QS] one simulation: the batch's DOFs
-  static constexpr int S_BAR = rup(S_Q + NE * C::QS, 4);   // mbarrier of the DOF copy (8 bytes)
+  // the batch's DOFs: NE elements of QS floats (one simulation), or the simulation groups
+  // that NE consecutive (element, simulation) slots touch, at most NE / G + 2 groups of
+  // NQ x B x G floats (fused, G = FUSED_GROUP)
+  static constexpr int GB = NQ * B * FUSED_GROUP;
+  static constexpr int QBUF = FU ? (NE / FUSED_GROUP + 2) * GB : NE * C::QS;
+  static constexpr int S_Q = rup(S_META + 3 * NE, 4);      // [QBUF] the batch's DOFs
+  static constexpr int S_BAR = rup(S_Q + QBUF, 4);         // mbarrier of the DOF copy (8 bytes)
   static constexpr int TOTAL = S_BAR + 4;
 };
 
@@ -127,9 +132,9 @@ struct Slots {
 };
 
 template <int O, int M, bool FUSED>
-__global__ void __launch_bounds__(SpCfg<O, M>::NT, (SpCfg<O, M>::NT >= 512 ? 1 : 2))
+__global__ void __launch_bounds__(SpCfg<O, M, FUSED>::NT, (SpCfg<O, M, FUSED>::NT >= 512 ? 1 : 2))
     k_predict_sp(DevOps ops, DevState st, PhaseArgs ph) {
-  using S = SpCfg<O, M>;
+  using S = SpCfg<O, M, FUSED>;
   using C = typename S::C;
   constexpr int B = S::B, F = S::F, NE = S::NE, NT = S::NT, XP = S::XP, NQ = S::NQ, NA = S::NA, EDP = S::EDP;
   extern __shared__ float4 smem4[];
@@ -163,27 +168,40 @@ __global__ void __launch_bounds__(SpCfg<O, M>::NT, (SpCfg<O, M>::NT >= 512 ? 1 :
   constexpr int RS = FUSED ? B * FUSED_GROUP : B;   // row stride of Q and the buffers
   constexpr int CS = FUSED ? FUSED_GROUP : 1;       // mode stride
   int col = es * 9;                           // this column's pair offset
-  // One simulation: a batch's elements are contiguous, so its DOFs (n x QS floats) arrive in
-  // shared memory by one bulk asynchronous copy (TMA) that thread 0 issues for the next batch
-  // as soon as the current one has read its copy, completing on an mbarrier (one phase per
-  // batch). Every wait is bounded; one that gives up sets the error word and the CTA returns.
+  // A batch's DOFs arrive in shared memory by one bulk asynchronous copy (TMA) that thread 0
+  // issues for the next batch as soon as the current one has read its copy, completing on an
+  // mbarrier (one phase per batch): one simulation, the batch's contiguous elements (n x QS
+  // floats); fused simulations, the contiguous simulation groups from the batch's first slot
+  // to its last. Every wait is bounded; one that gives up sets the error word and the CTA
+  // returns.
+  constexpr int GB = S::GB;
   auto issue_q = [&](int bt) {
-    const int e0 = ph.begin + bt * NE;
-    const uint32_t bytes = (uint32_t)min(NE, ph.end - e0) * C::QS * 4;
+    const float* src;
+    uint32_t bytes;
+    if constexpr (!FUSED) {
+      const int e0 = ph.begin + bt * NE;
+      src = st.Q + (size_t)e0 * C::QS;
+      bytes = (uint32_t)min(NE, ph.end - e0) * C::QS * 4;
+    } else {
+      int e0, f0, e1, f1;
+      sl.decode(bt * NE, e0, f0);
+      sl.decode(min(sl.n, bt * NE + NE) - 1, e1, f1);
+      const int ngr = sl.nsim / FUSED_GROUP;
+      src = st.Q + (size_t)(ph.begin + e0) * qs + (size_t)(f0 / FUSED_GROUP) * GB;
+      bytes = (uint32_t)((e1 - e0) * ngr + f1 / FUSED_GROUP - f0 / FUSED_GROUP + 1) * GB * 4;
+    }
     tc::fence_smem_to_async();
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(sBar)), "r"(bytes)
                  : "memory");
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                      tc::smem_u32(sQ)),
-                 "l"(st.Q + (size_t)e0 * C::QS), "r"(bytes), "r"(tc::smem_u32(sBar))
+                 "l"(src), "r"(bytes), "r"(tc::smem_u32(sBar))
                  : "memory");
   };
   uint32_t qpar = 0;
-  if constexpr (!FUSED) {
-    if (tid == 0) tc::mbar_init(sBar, 1);
-    __syncthreads();
-    if (tid == 0 && blockIdx.x < nbatch && !ph.suppress) issue_q(blockIdx.x);
-  }
+  if (tid == 0) tc::mbar_init(sBar, 1);
+  __syncthreads();
+  if (tid == 0 && blockIdx.x < nbatch && !ph.suppress) issue_q(blockIdx.x);
 
   for (int batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
     const int t0 = batch * NE;
@@ -222,7 +240,7 @@ __global__ void __launch_bounds__(SpCfg<O, M>::NT, (SpCfg<O, M>::NT >= 512 ? 1 :
     const int fs = (FUSED && valid) ? sSlot[NE + es] : 0;
     const size_t qoff = (size_t)g * qs + Slots<FUSED>::sub(fs, NQ, B) + (size_t)b * CS;
     const size_t boff = (size_t)g * bs + Slots<FUSED>::sub(fs, 9, B) + (size_t)b * CS;
-    if constexpr (!FUSED) {
+    {
       // the batch's DOFs have arrived (or the wait gave up: every thread leaves)
       const bool ok = tc::mbar_wait(sBar, qpar, ph.wait);
       qpar ^= 1;
@@ -234,12 +252,19 @@ __global__ void __launch_bounds__(SpCfg<O, M>::NT, (SpCfg<O, M>::NT >= 512 ? 1 :
         return;
       }
     }
+    // this column's DOFs in the staged copy (row stride RS, as in Q)
+    size_t soff = (size_t)es * C::QS + b;
+    if constexpr (FUSED) {
+      const int ngr = sl.nsim / FUSED_GROUP;
+      const int gi = (g - sSlot[0]) * ngr + fs / FUSED_GROUP - sSlot[NE] / FUSED_GROUP;
+      soff = (size_t)gi * GB + (size_t)b * CS + fs % FUSED_GROUP;
+    }
     float T[NQ], Th[9], Da[NA > 0 ? NA : 1];
     float v[9];
 #pragma unroll
     for (int r = 0; r < 9; ++r) v[r] = 0.f;
     if (valid) {
-      const float* q = FUSED ? st.Q + qoff : sQ + es * C::QS + b;
+      const float* q = sQ + soff;
 #pragma unroll
       for (int r = 0; r < 9; ++r) v[r] = q[r * RS];
 #pragma unroll
@@ -356,7 +381,7 @@ __global__ void __launch_bounds__(SpCfg<O, M>::NT, (SpCfg<O, M>::NT >= 512 ? 1 :
         for (int r = 0; r < 9; ++r) V[r] = -out[r];
 #pragma unroll
         for (int l = 0; l < M; ++l) coupling_add(V, T + 9 + 6 * l, ed[12 + 2 * l], ed[13 + 2 * l]);
-        const float* q = FUSED ? st.Q + qoff : sQ + es * C::QS + b;
+        const float* q = sQ + soff;
 #pragma unroll
         for (int r = 0; r < 9; ++r) acc[r] = q[r * RS] + V[r];
 #pragma unroll
@@ -383,7 +408,7 @@ __global__ void __launch_bounds__(SpCfg<O, M>::NT, (SpCfg<O, M>::NT >= 512 ? 1 :
     }
     __syncthreads();
     // the batch's DOF copy has been read: the next batch's copy goes out now
-    if (!FUSED && tid == 0 && batch + (int)gridDim.x < nbatch && !ph.suppress) issue_q(batch + gridDim.x);
+    if (tid == 0 && batch + (int)gridDim.x < nbatch && !ph.suppress) issue_q(batch + gridDim.x);
     // ---- projection P_i[r'][b] = sum_f W_i[r'][f] F^_i[f][b] (row phase, over Y and G)
     if (pact) sp_proj<O, XP>(part, sW + pair, sP + pair);
     __syncthreads();
@@ -411,22 +436,8 @@ __global__ void __launch_bounds__(SpCfg<O, M>::NT, (SpCfg<O, M>::NT >= 512 ? 1 :
           for (int r = 0; r < 6; ++r) q[(9 + 6 * l + r) * RS] = acc[9 + 6 * l + r] + ph.omega[l] * Sv[NS - 6 + r];
       }
     }
-    const int bn = batch + gridDim.x;                      // fused: the next batch's DOFs into L2
-    if (bn < nbatch) {
-      if constexpr (FUSED) {
-        // the simulation groups from the batch's first slot to its last are contiguous
-        int e0, f0, e1, f1;
-        sl.decode(bn * NE, e0, f0);
-        sl.decode(min(sl.n, bn * NE + NE) - 1, e1, f1);
-        constexpr int GB = NQ * B * FUSED_GROUP;
-        const float* p = st.Q + (size_t)(ph.begin + e0) * qs + (size_t)(f0 / FUSED_GROUP) * GB;
-        const long long len = (long long)(e1 - e0) * qs + (long long)(f1 / FUSED_GROUP - f0 / FUSED_GROUP + 1) * GB;
-        for (long long off = 32LL * tid; off < len; off += 32LL * NT) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + off));
-      }
-    }
   }
 }
-
 
 // ------------------------------------------------------------------ neighbour kernel
 // k_neighbour_sp: the neighbour surface kernel (Sec. III-A, with the buffer chosen by the

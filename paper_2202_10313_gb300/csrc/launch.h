@@ -91,7 +91,7 @@ struct Impl {
       e = smem_attrs(k_predict_sp<O, M, FU>, L->smem_predict_sp, true);
       if (e != cudaSuccess) return e;
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L->blocks_predict_sp, k_predict_sp<O, M, FU>,
-                                                        SpCfg<O, M>::NT, L->smem_predict_sp);
+                                                        SpCfg<O, M, FU>::NT, L->smem_predict_sp);
       if (e != cudaSuccess) return e;
       e = smem_attrs(k_neighbour_sp<O, M, 8, FU>, L->smem_neighbour_sp[0], true);
       if (e != cudaSuccess) return e;
@@ -120,7 +120,8 @@ struct Impl {
     k_neighbour<O, M, FG><<<grid, C::NTN, C::N_TOTAL * sizeof(float), st>>>(o, s, p);
   }
   static void predict_sp(const DevOps& o, const DevState& s, const PhaseArgs& p, int grid, cudaStream_t st) {
-    k_predict_sp<O, M, (FG > 1)><<<grid, SpCfg<O, M>::NT, SpCfg<O, M>::TOTAL * sizeof(float), st>>>(o, s, p);
+    using S = SpCfg<O, M, (FG > 1)>;
+    k_predict_sp<O, M, (FG > 1)><<<grid, S::NT, S::TOTAL * sizeof(float), st>>>(o, s, p);
   }
   template <int NE>
   static void neighbour_sp(const DevOps& o, const DevState& s, const PhaseArgs& p, int grid, cudaStream_t st) {
@@ -206,9 +207,9 @@ struct Impl {
     }
     {
       L.predict_sp = &predict_sp;
-      L.smem_predict_sp = SpCfg<O, M>::TOTAL * sizeof(float);
-      L.NE_SP = SpCfg<O, M>::NE;
-      L.NT_SP = SpCfg<O, M>::NT;
+      L.smem_predict_sp = SpCfg<O, M, (FG > 1)>::TOTAL * sizeof(float);
+      L.NE_SP = SpCfg<O, M, (FG > 1)>::NE;
+      L.NT_SP = SpCfg<O, M, (FG > 1)>::NT;
       L.neighbour_sp[0] = &neighbour_sp<8>;
       L.neighbour_sp[1] = &neighbour_sp<4>;
       L.smem_neighbour_sp[0] = SpnCfg<O, M, 8>::TOTAL * sizeof(float);
