@@ -122,11 +122,15 @@ class ClockSampler:
 
 
 def kernel_hash():
-    """Hash of the forward kernels' source (the DRAM counters in profiles/traffic.json are valid
-    only for the code they were taken on)."""
+    """Hash of the forward kernels' source without its // comments (the DRAM counters in
+    profiles/traffic.json are valid only for the code they were taken on; a comment edit does
+    not change the code)."""
+    import re
     h = hashlib.sha256()
     for f in ("kernels.cuh", "kernels_sp.cuh", "gen_sparse.cpp"):
-        h.update(open(os.path.join(ROOT, "paper_2202_10313_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_2202_10313_gb300", "csrc", f), encoding="utf-8").read()
+        code = "\n".join(l.rstrip() for l in re.sub(r"//[^\n]*", "", src).split("\n") if l.strip())
+        h.update(code.encode("utf-8"))
     return h.hexdigest()[:16]
 
 

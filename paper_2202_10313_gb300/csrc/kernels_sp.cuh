@@ -1,6 +1,7 @@
 // k_predict_sp: the predict + local kernel (time kernel, LTS buffers, volume kernel, local
 // surface kernel; Sec. III-A and Eq. lts_buffers) with the operator products in generated
-// sparse form (one simulation).
+// sparse form (one simulation, or (element, simulation) slots of fused simulations), and
+// k_neighbour_sp, the neighbour surface kernel of the same engine (below).
 //
 // Each time derivative (and the volume / face-trace step) is done in two phases separated
 // by a barrier:
@@ -22,7 +23,8 @@
 // (consecutive modes) fall on distinct banks.
 // The local surface kernel's interface states (closed-form Riemann solver of kernels.cuh) are
 // projected the same way (row phase with the generated F^_i products), and the column phase
-// forms the flux rows per face. Receivers, sources and the neighbour kernel are those of
+// forms the flux rows per face. A batch's DOFs arrive in shared memory by one bulk
+// asynchronous copy (TMA), issued a batch ahead. Receivers and sources are those of
 // kernels.cuh.
 #pragma once
 #include "kernels.cuh"
