@@ -1,5 +1,6 @@
 """bench.py's reference arm on the host cores (no GPU): the JSON line it prints, and that
-under several ranks only rank 0 runs and prints."""
+under several ranks only rank 0 runs and prints; and the tie of its DRAM-traffic record to
+the kernel sources."""
 import json
 import os
 import subprocess
@@ -37,3 +38,26 @@ def test_reference_arm_other_ranks_exit_quietly():
     r = _run(1, 2)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_traffic_record_matches_the_kernel_sources(tmp_path, monkeypatch):
+    """The DRAM-traffic record is tied to the kernels' code: the hash ignores comments and
+    blank lines but changes with any code edit, and the committed record matches the
+    current sources (else bench.py would report roofline.traffic as null)."""
+    import json
+    import shutil
+    import bench
+    rec = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))
+    assert rec["k_predict_sp"]["kernel_hash"] == bench.kernel_hash()
+    assert rec["k_neighbour_sp"]["kernel_hash"] == bench.kernel_hash()
+    csrc = tmp_path / "paper_2202_10313_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for f in ("kernels.cuh", "kernels_sp.cuh", "gen_sparse.cpp"):
+        shutil.copy(os.path.join(bench.ROOT, "paper_2202_10313_gb300", "csrc", f), csrc / f)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.kernel_hash()
+    p = csrc / "kernels_sp.cuh"
+    p.write_text("// a comment line\n\n" + p.read_text().replace("\n}", "  // trailing note\n}", 1))
+    assert bench.kernel_hash() == h0
+    p.write_text(p.read_text().replace("NE = 14", "NE = 13", 1))
+    assert bench.kernel_hash() != h0
