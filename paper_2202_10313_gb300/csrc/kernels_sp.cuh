@@ -192,13 +192,7 @@ __global__ void __launch_bounds__(SpCfg<O, M, FUSED>::NT, (SpCfg<O, M, FUSED>::N
       src = st.Q + (size_t)(ph.begin + e0) * qs + (size_t)(f0 / FUSED_GROUP) * GB;
       bytes = (uint32_t)((e1 - e0) * ngr + f1 / FUSED_GROUP - f0 / FUSED_GROUP + 1) * GB * 4;
     }
-    tc::fence_smem_to_async();
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(sBar)), "r"(bytes)
-                 : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     tc::smem_u32(sQ)),
-                 "l"(src), "r"(bytes), "r"(tc::smem_u32(sBar))
-                 : "memory");
+    tc::bulk_load(sQ, src, bytes, sBar);
   };
   uint32_t qpar = 0;
   if (tid == 0) tc::mbar_init(sBar, 1);
@@ -560,14 +554,7 @@ __global__ void __launch_bounds__(SpnCfg<O, M, NE_>::NT, (NE_ == 8 ? 2 : 4))
       // the previous batch's update has read its copy (barrier above)
       if (tid == 0 && !ph.suppress) {
         const int e0 = ph.begin + t0;
-        const uint32_t bytes = (uint32_t)min(NE, ph.end - e0) * C::QS * 4;
-        tc::fence_smem_to_async();
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(sBar)), "r"(bytes)
-                     : "memory");
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                         tc::smem_u32(sQ)),
-                     "l"(st.Q + (size_t)e0 * C::QS), "r"(bytes), "r"(tc::smem_u32(sBar))
-                     : "memory");
+        tc::bulk_load(sQ, st.Q + (size_t)e0 * C::QS, (uint32_t)min(NE, ph.end - e0) * C::QS * 4, sBar);
       }
     }
     __syncthreads();

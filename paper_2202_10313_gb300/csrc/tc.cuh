@@ -97,6 +97,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity, long lon
   return true;
 }
 
+// ---- bulk asynchronous copy (TMA, non-tensor form): `bytes` (a multiple of 16, both
+// addresses 16-byte aligned) from global to shared memory, completing on the mbarrier; the
+// calling thread also arrives on it, announcing the bytes (a barrier of arrival count 1).
+// Orders this CTA's earlier generic-proxy accesses of the destination before the copy.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+  fence_smem_to_async();
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+               : "memory");
+}
+
 // ---- TMEM <-> registers (32x32b shape: thread i of the warp owns lane base + i)
 // 16 consecutive FP32 columns; the wait is part of the same statement, so the outputs are
 // complete when the compiler first sees them.
