@@ -210,7 +210,8 @@ __global__ void __launch_bounds__(SpCfg<O, M, FUSED>::NT, (SpCfg<O, M, FUSED>::N
       sSlot[tid] = ph.begin + e;
       sSlot[NE + tid] = f;
     }
-    __syncthreads();
+    // one simulation: the barrier of the DOF wait below follows the previous batch's update
+    if constexpr (FUSED) __syncthreads();
     if (FUSED && act) {
       // fused column tasks ordered by (element, mode, simulation): the slots of the batch that
       // share an element form a segment [s0, s1), and its B (s1 - s0) tasks take the modes in
@@ -536,11 +537,9 @@ __global__ void __launch_bounds__(SpnCfg<O, M, NE_>::NT, (NE_ == 8 ? 2 : 4))
       sSlot[tid] = ph.begin + e;
       sSlot[NE + tid] = f;
     }
-    __syncthreads();
-    for (int i = tid; i < NE * ND; i += NT) {
-      const int ee = i / ND;
-      sD[ee * NDP + i % ND] = (t0 + ee < sl.n) ? __ldg(st.ndata + (size_t)elem_of(ee) * ND + (i % ND)) : 0.f;
-    }
+    // one simulation: no barrier here. The previous batch's last shared-memory reads (sD, sP,
+    // sQ by its update) end before the barrier below, and sI is read before its states barrier
+    if constexpr (FUSED) __syncthreads();
     for (int i = tid; i < NE * 9; i += NT) {
       const int c = i % 9;
       int v = -1;
@@ -550,6 +549,7 @@ __global__ void __launch_bounds__(SpnCfg<O, M, NE_>::NT, (NE_ == 8 ? 2 : 4))
       }
       sI[i] = v;
     }
+    __syncthreads();
     if constexpr (!FUSED) {
       // the previous batch's update has read its copy (barrier above)
       if (tid == 0 && !ph.suppress) {
@@ -557,7 +557,11 @@ __global__ void __launch_bounds__(SpnCfg<O, M, NE_>::NT, (NE_ == 8 ? 2 : 4))
         tc::bulk_load(sQ, st.Q + (size_t)e0 * C::QS, (uint32_t)min(NE, ph.end - e0) * C::QS * 4, sBar);
       }
     }
-    __syncthreads();
+    // neighbour coefficients, first read by the states phase (two barriers on)
+    for (int i = tid; i < NE * ND; i += NT) {
+      const int ee = i / ND;
+      sD[ee * NDP + i % ND] = (t0 + ee < sl.n) ? __ldg(st.ndata + (size_t)elem_of(ee) * ND + (i % ND)) : 0.f;
+    }
     // face slots (element, face) sorted by the neighbour's face j (faces without one last), so
     // that the rows of a warp mostly ask for one face in the trace phase
     if (tid < 32) {
@@ -645,7 +649,8 @@ __global__ void __launch_bounds__(SpnCfg<O, M, NE_>::NT, (NE_ == 8 ? 2 : 4))
     __syncthreads();
     // ---- projection P_i[r'][b] = sum_f W_i[r'][f] F^_i[f][b] (row phase, over the gathers)
     if (pact) sp_proj<O, XP6>(part, sW + pair6, sP + pair6);
-    __syncthreads();
+    // one simulation: the barrier of the DOF wait below orders the projections and the update
+    if constexpr (FUSED) __syncthreads();
     if constexpr (!FUSED) {
       // the batch's DOFs have arrived (or the wait gave up: every thread leaves)
       const bool ok = tc::mbar_wait(sBar, qpar, ph.wait);
