@@ -537,8 +537,9 @@ __global__ void __launch_bounds__(SpnCfg<O, M, NE_>::NT, (NE_ == 8 ? 2 : 4))
       sSlot[tid] = ph.begin + e;
       sSlot[NE + tid] = f;
     }
-    // one simulation: no barrier here. The previous batch's last shared-memory reads (sD, sP,
-    // sQ by its update) end before the barrier below, and sI is read before its states barrier
+    // one simulation: no barrier here. The previous batch's update (its last reads of sD, sP
+    // and sQ) ends before the barrier below, and its last read of sI came before its states
+    // phase's barrier, so the sI writes that follow overwrite nothing still in use
     if constexpr (FUSED) __syncthreads();
     for (int i = tid; i < NE * 9; i += NT) {
       const int c = i % 9;
