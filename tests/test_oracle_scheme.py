@@ -177,6 +177,71 @@ def test_anelastic_plane_wave_decays_at_target_q():
     assert abs(a1 / a0 / want - 1) < 0.05, (a1 / a0, want)
 
 
+@pytest.mark.parametrize("order", [3, 4])
+def test_anelastic_s_plane_wave_convergence(order):
+    """Attenuating medium (Q_s = 20, Q_p = 40, three mechanisms around the wave frequency), S
+    wave along x polarised along y (Sec. III, anelastic equations with memory variables): one
+    Fourier mode of the continuum equations is a 5 x 5 linear ODE in (v_y, sigma_xy,
+    theta^l_xy),
+        rho v_y'       = d_x sigma_xy,
+        sigma_xy'      = mu d_x v_y - 2 mu sum_l Y^mu_l theta^l_xy,
+        theta^l_xy'    = omega_l (1/2 d_x v_y - theta^l_xy),
+    solved exactly by a matrix exponential. Starting from the elastic S wave with zero memory
+    variables, the oracle's velocity, stress and memory-variable errors against that solution
+    drop at rate ~O from 3x3x3 to 6x6x6 hexes; a wrong strain factor or coupling sign leaves
+    them flat."""
+    from scipy.linalg import expm
+    from oracle import physics as ph
+    qs = 20.0
+    k = 2 * np.pi
+    w = k * VS
+    lam, mu = ph.lame(RHO, VP, VS)
+    rows = (7, 3, 12, 18, 24)                 # v_y, sigma_xy, theta^1..3_xy in the state vector
+
+    def setup(n):
+        s, mesh = _cube_solver(n, order, m=3, qs=qs)
+        s.omega = ph.relaxation_frequencies(3, 0.1 * w / (2 * np.pi), 10 * w / (2 * np.pi))
+        ylam, ymu = ph.anelastic_coefficients(lam, mu, 2 * qs, qs, s.omega)
+        for e in range(mesh.K):
+            for l in range(3):
+                s.E[e, l] = ph.coupling_matrix(lam, mu, ylam[l], ymu[l])
+        return s, ymu
+
+    def exact(omega, ymu, t):
+        # amplitudes of exp(i k x); the field is their imaginary part (sin(k x) at t = 0)
+        M = np.zeros((5, 5), complex)
+        M[0, 1] = 1j * k / RHO
+        M[1, 0] = 1j * k * mu
+        for l in range(3):
+            M[1, 2 + l] = -2 * mu * ymu[l]
+            M[2 + l, 0] = 0.5j * k * omega[l]
+            M[2 + l, 2 + l] = -omega[l]
+        y = expm(M * t) @ np.array([1.0, -mu / VS, 0.0, 0.0, 0.0], complex)
+
+        def fn(x):
+            out = np.zeros((len(x), 27))
+            c, sn = np.cos(k * x[:, 0]), np.sin(k * x[:, 0])
+            for r, yy in zip(rows, y):
+                out[:, r] = yy.imag * c + yy.real * sn
+            return out
+        return fn
+
+    tend = 0.25 / VS
+    errs = []
+    for n in (3, 6):
+        s, ymu = setup(n)
+        s.project(exact(s.omega, ymu, 0.0))
+        dt = s.time_step_gts(0.5)
+        nst = int(math.ceil(tend / dt))
+        s.run_gts(tend / nst, nst)
+        ex, _ = setup(n)
+        ex.project(exact(s.omega, ymu, tend))
+        errs.append([_rel_err(s.Q, ex.Q, sl) for sl in (slice(6, 9), slice(0, 6), slice(9, 27))])
+    for e3, e6 in zip(*errs):
+        rate = math.log2(e3 / e6)
+        assert rate > order - 0.6, (errs, rate)
+
+
 def test_receiver_is_exact_point_evaluation():
     """Sampled at the start of each step, the receiver equals the DG polynomial of
     Q^n at the receiver point; mid-step samples come from the Taylor series."""
