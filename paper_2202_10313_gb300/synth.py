@@ -77,6 +77,14 @@ def periodic_cube(n, length=1.0):
     return dict(xyz=xyz, tet=tet, face_bc=bc, period=np.array([length] * 3))
 
 
+def periodic_slab(n, z_code=2, length=1.0):
+    """The cube of periodic_cube, periodic in x and y only: its planes z = 0 and z = L carry
+    boundary code z_code (2 free surface, 1 absorbing)."""
+    m = periodic_cube(n, length)
+    m["face_bc"] = _boundary_codes(m["tet"], n, n, n, [3, 3, 3, 3, z_code, z_code])
+    return m
+
+
 def graded_box(nx, ny, nz, h, hz_min, grade=4.0, jitter=0.15, seed=SEED_MESH):
     """Box [0, nx h] x [0, ny h] x [-D, 0], z-spacing growing geometrically from hz_min
     at the surface z = 0 to grade*hz_min at the bottom; vertices jittered uniformly by

@@ -242,6 +242,56 @@ def test_anelastic_s_plane_wave_convergence(order):
         assert rate > order - 0.6, (errs, rate)
 
 
+@pytest.mark.parametrize("kind", ["s", "p"])
+@pytest.mark.parametrize("order", [3, 4])
+def test_free_surface_standing_waves_converge(kind, order):
+    """Traction-free planes z = 0 and z = 1 (free-surface faces, Sec. III), periodic in x and
+    y: the standing waves v = cos(k z) cos(w t) with k = 2 pi (S: v_x with sigma_xz; P: v_z
+    with sigma_zz and sigma_xx = sigma_yy = lam / (lam + 2 mu) sigma_zz) satisfy the boundary
+    condition exactly (their traction sin(k z) vanishes on both planes). The oracle's velocity
+    and stress errors against them drop at rate ~O from 3x3x3 to 6x6x6 hexes; an absorbing or
+    a rigid treatment of those faces leaves the error flat."""
+    lam, mu = RHO * (VP ** 2 - 2 * VS ** 2), RHO * VS ** 2
+    c = VS if kind == "s" else VP
+    k = 2 * np.pi
+    w = k * c
+
+    def standing(t):
+        def fn(x):
+            out = np.zeros((len(x), 9))
+            z = x[:, 2]
+            v = np.cos(k * z) * np.cos(w * t)
+            sg = -RHO * c * np.sin(k * z) * np.sin(w * t)   # from rho v_t = d_z sigma
+            if kind == "s":
+                out[:, 6], out[:, 5] = v, sg
+            else:
+                out[:, 8], out[:, 2] = v, sg
+                out[:, 0] = out[:, 1] = sg * lam / (lam + 2 * mu)
+            return out
+        return fn
+
+    def solver(n):
+        m = synth.periodic_slab(n, z_code=2)
+        mesh = Mesh(m["xyz"], m["tet"], m["face_bc"], m["period"])
+        K = mesh.K
+        return Solver(order, 0, mesh, np.full(K, RHO), np.full(K, VP), np.full(K, VS))
+
+    tend = 0.125 / c
+    errs = []
+    for n in (3, 6):
+        s = solver(n)
+        s.project(standing(0.0))
+        dt = s.time_step_gts(0.5)
+        nst = int(math.ceil(tend / dt))
+        s.run_gts(tend / nst, nst)
+        ex = solver(n)
+        ex.project(standing(tend))
+        errs.append([_rel_err(s.Q, ex.Q, sl) for sl in (slice(6, 9), slice(0, 6))])
+    for e3, e6 in zip(*errs):
+        rate = math.log2(e3 / e6)
+        assert rate > order - 0.6, (errs, rate)
+
+
 def test_receiver_is_exact_point_evaluation():
     """Sampled at the start of each step, the receiver equals the DG polynomial of
     Q^n at the receiver point; mid-step samples come from the Taylor series."""
