@@ -77,12 +77,17 @@ def periodic_cube(n, length=1.0):
     return dict(xyz=xyz, tet=tet, face_bc=bc, period=np.array([length] * 3))
 
 
-def periodic_slab(n, z_code=2, length=1.0):
-    """The cube of periodic_cube, periodic in x and y only: its planes z = 0 and z = L carry
-    boundary code z_code (2 free surface, 1 absorbing)."""
-    m = periodic_cube(n, length)
-    m["face_bc"] = _boundary_codes(m["tet"], n, n, n, [3, 3, 3, 3, z_code, z_code])
-    return m
+def periodic_slab(n, z_code=2, length=1.0, nxy=None):
+    """[0, L]^3 as n hexes along z and nxy (default n) along x and y, 6 tets each, periodic in
+    x and y only: its planes z = 0 and z = L carry boundary code z_code (2 free surface,
+    1 absorbing)."""
+    nxy = n if nxy is None else nxy
+    xs = length * np.arange(nxy + 1) / nxy
+    zs = length * np.arange(n + 1) / n
+    xyz = _grid_vertices(xs, xs, zs)
+    tet = _kuhn_tets(nxy, nxy, n)
+    bc = _boundary_codes(tet, nxy, nxy, n, [3, 3, 3, 3, z_code, z_code])
+    return dict(xyz=xyz, tet=tet, face_bc=bc, period=np.array([length] * 3))
 
 
 def graded_box(nx, ny, nz, h, hz_min, grade=4.0, jitter=0.15, seed=SEED_MESH):
