@@ -177,7 +177,7 @@ def test_anelastic_plane_wave_decays_at_target_q():
     assert abs(a1 / a0 / want - 1) < 0.05, (a1 / a0, want)
 
 
-@pytest.mark.parametrize("order", [3, 4])
+@pytest.mark.parametrize("order", [3])
 def test_anelastic_s_plane_wave_convergence(order):
     """Attenuating medium (Q_s = 20, Q_p = 40, three mechanisms around the wave frequency), S
     wave along x polarised along y (Sec. III, anelastic equations with memory variables): one
