@@ -184,6 +184,30 @@ def test_advance_to_time_and_torch_memory():
     _check(gpu, ora)
 
 
+def test_bound_block_too_small_is_rejected_then_rebinding_works():
+    """A caller-bound device block smaller than the state is rejected with LTS_ERR_OOM when
+    the clusters are set up (the check comes before any device write); the same handle,
+    bound to a large enough block, then sets up and steps as usual."""
+    import ctypes
+    import torch
+    m = synth.graded_box(3, 3, 2, 200.0, 100.0, seed=5)
+    mat = synth.layered(m, [150.0], [1200.0, 2400.0])
+    gpu, ora, _ = make_pair(3, 0, m, mat)
+    small = torch.empty(4096, dtype=torch.uint8, device="cuda:0")
+    base = small.data_ptr() + (-small.data_ptr()) % 256
+    gpu._check(binding.lib().lts_bind_device_memory(gpu._h, ctypes.c_void_p(base), 1024))
+    with pytest.raises(binding.LtsError) as err:
+        gpu.setup_clusters(2, 0.5)
+    assert err.value.code == binding.LTS_ERR_OOM
+    gpu.use_torch_memory(2)
+    gpu.setup_clusters(2, 0.5)
+    ora.setup_clusters(2, 0.5)
+    _seed_same(gpu, ora, initial_field(9, [300.0, 300.0, -100.0], 250.0))
+    gpu.advance_steps(4)
+    ora.run_lts(4)
+    _check(gpu, ora)
+
+
 @pytest.mark.parametrize("order", [3, 5])
 def test_projection_of_polynomial_field_is_exact(order):
     """Both projection rules are exact for a degree O-1 polynomial field."""
