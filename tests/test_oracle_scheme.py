@@ -405,6 +405,74 @@ def test_material_interface_reflects_and_transmits_at_normal_incidence(kind):
         assert rate > order - 0.6, (errs, rate)
 
 
+def test_lts_across_material_interface_converges():
+    """Two LTS clusters split by a material interface (Sec. V): the P pulse of the interface
+    test above, with the slow side (vp 2,900 against 6,000, so twice the CFL step) in the
+    coarser cluster and lam = 1. The pulse crosses from the fine cluster into the coarse one
+    through the LTS buffer reads across the interface; the error against the closed-form
+    reflection and transmission drops at rate ~4 (order 4, 12 -> 24 hexes along z), and LTS
+    stays within the discretisation error of GTS. (A mistake whose effect is below the
+    discretisation error here, such as the second half-step reading B2 instead of B1 - B2,
+    is caught by the exact buffer checks of the Fig. 5 walkthrough test.)"""
+    order = 4
+    m1, m2 = (2700.0, 6000.0, 3464.0), (2000.0, 2900.0, 1674.0)      # rho, vp, vs per side
+
+    def side(m):
+        rho, vp, vs = m
+        mu = rho * vs * vs
+        lam = rho * vp * vp - 2 * mu
+        return rho * vp, vp, lam / (lam + 2 * mu)
+
+    Z1, c1, q1 = side(m1)
+    Z2, c2, q2 = side(m2)
+    R, T = (Z1 - Z2) / (Z1 + Z2), 2 * Z1 / (Z1 + Z2)
+
+    def f(s):
+        return np.exp(-((s - 0.3) / 0.1) ** 2)
+
+    def exact(t):
+        def fn(x):
+            z = x[:, 2]
+            lo = z < 0.5
+            inc, ref = f(z - c1 * t), R * f(1.0 - z - c1 * t)
+            tra = T * f(0.5 - c1 * t + c1 * (z - 0.5) / c2)
+            out = np.zeros((len(x), 9))
+            out[:, 8] = np.where(lo, inc + ref, tra)
+            out[:, 2] = np.where(lo, -Z1 * inc + Z1 * ref, -Z2 * tra)
+            out[:, 0] = out[:, 1] = out[:, 2] * np.where(lo, q1, q2)
+            return out
+        return fn
+
+    def solver(n):
+        m = synth.periodic_slab(n, z_code=1, nxy=2)
+        mesh = Mesh(m["xyz"], m["tet"], m["face_bc"], m["period"])
+        lo = mesh.centroid[:, 2] < 0.5
+        rho, vp, vs = (np.where(lo, a, b) for a, b in zip(m1, m2))
+        return Solver(order, 0, mesh, rho, vp, vs), lo
+
+    tend = 0.3 / c1
+    errs, gaps = [], []
+    for n in (12, 24):
+        s, lo = solver(n)
+        s.project(exact(0.0))
+        s.setup_clusters(2, 0.5, lam=1.0)
+        assert np.array_equal(s.clusters, np.where(lo, 0, 1))
+        nper = int(math.ceil(tend / (2 * s.delta)))
+        s.delta = tend / (2 * nper)
+        s.run_lts(2 * nper)
+        ex, _ = solver(n)
+        ex.project(exact(tend))
+        g, _ = solver(n)
+        g.project(exact(0.0))
+        g.run_gts(tend / (2 * nper), 2 * nper)
+        errs.append([_rel_err(s.Q, ex.Q, sl) for sl in (slice(6, 9), slice(0, 6))])
+        gaps.append(_rel_err(s.Q, g.Q, slice(0, 9)))
+    for e12, e24 in zip(*errs):
+        rate = math.log2(e12 / e24)
+        assert rate > order - 0.6, (errs, rate)
+    assert gaps[1] < min(errs[1])
+
+
 def test_receiver_is_exact_point_evaluation():
     """Sampled at the start of each step, the receiver equals the DG polynomial of
     Q^n at the receiver point; mid-step samples come from the Taylor series."""
